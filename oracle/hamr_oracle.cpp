@@ -1,0 +1,1192 @@
+/* hamr_oracle.cpp -- plain, slow, single-threaded FP64 CPU oracle of the
+ * H-AMR GRMHD block update (Liska et al., arXiv 1912.10192, Sec. 2).
+ *
+ * TEST INFRASTRUCTURE ONLY. It defines what the CUDA path must compute and is
+ * used by tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg.
+ * It shares no code with paper_1912_10192_gb300/csrc and neither side
+ * includes or links the other.
+ *
+ * Every function follows the paper's equations in the paper's order; readings
+ * of passages the paper leaves silent or prints garbled are marked "Reading:".
+ *
+ *   geometry         Sec. 2.2 "Coordinate System and Metric"
+ *   primitives       Sec. 2.3 (b^t, b^i, utilde^i relations; T, F*, kappa)
+ *   conserved/flux   Sec. 2.4-2.5 (U, F^j, sqrt(-g) absorbed)
+ *   reconstruction   Sec. 2.1 (PPM of primitives; MINMOD/MC as options)
+ *   Riemann solver   Sec. 2.1 (HLLE with the approximate fast speed; LLF option)
+ *   EMF / CT         Sec. 2.5 (4-flux EMF average, staggered face-B update,
+ *                    face-to-centre B average)
+ *   source           Sec. 2.5 (sqrt(-g) T^k_l Gamma^l_{nu k})
+ *   inversion        Sec. 2.6 (2-D Newton on (W, v^2); entropy backup)
+ *   floors           Sec. 2.7 (b^2/rho<50, b^2/u<750, rho>1e-7/r^2, u>1e-9/r^(10/3))
+ *   time step        Sec. 2.1 (midpoint predictor/corrector; C0 / sum 1/dt^i)
+ */
+#include "ora_real.h"
+#include "hamr_oracle.h"
+
+#include <cstdlib>
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#ifdef ORA_COUNT_FLOPS
+extern "C" {
+unsigned long long ora_flop_ctr[5] = {0, 0, 0, 0, 0};
+}
+#endif
+
+namespace {
+
+const int NG = 3;                                   /* ghost layers */
+enum { RHO = 0, UU, U1, U2, U3, B1, B2, B3, NPR };  /* primitive slots */
+enum { CRHO = 0, CEN, CS1, CS2, CS3, CENT, NCONS }; /* cell conserved slots */
+const int NFX = 8; /* face-flux slots: 0..5 as NCONS, 6/7 = the two B^i with i != dir */
+
+/* Reading (Sec. 2.2): the paper takes Christoffel symbols "by finite
+ * differences of the metric in internal coordinates" without the stencil;
+ * we use 4th-order central differences with this step in x1 and x2. */
+const double CONN_H = 1.0e-3;
+
+/* Reading (Sec. 2.6): Newton stopping rule and limits, not given in the paper. */
+const double C2P_TOL = 1.0e-12;
+const int C2P_NMAX = 30;
+const double GAMMA_MAX = 50.0;
+
+/* ------------------------------------------------------------------ */
+/* geometry (Sec. 2.2)                                                  */
+/* ------------------------------------------------------------------ */
+
+struct Geom {
+    real gcov[4][4];
+    real gcon[4][4];
+    real gdet;  /* sqrt(-g) in internal coordinates */
+    real alpha; /* lapse 1/sqrt(-g^{00}) */
+    int pole;   /* 1: an x2 face on the polar axis (sqrt(-g) = 0) */
+};
+
+/* Reflect theta into [0, pi]: ghost cells beyond the pole take the geometry
+ * of the mirrored point (transmissive polar boundary, Sec. 3.3.1). */
+static double mirror_theta(double th) {
+    const double pi = 3.14159265358979323846;
+    if (th < 0.0) return -th;
+    if (th > pi) return 2.0 * pi - th;
+    return th;
+}
+
+/* Kerr metric in Kerr-Schild coordinates (M = 1), transformed to internal
+ * coordinates x1 = log r, x2 = theta, x3 = phi. The Jacobian of x1 = log r is
+ * dr/dx1 = r, applied analytically: every covariant r index gets a factor r,
+ * every contravariant one a factor 1/r. */
+static void metric_point(const ora_desc& d, double x1, double x2, double gcov[4][4],
+                         double gcon[4][4], double* gdet) {
+    for (int m = 0; m < 4; m++)
+        for (int n = 0; n < 4; n++) gcov[m][n] = gcon[m][n] = 0.0;
+    if (d.metric == ORA_METRIC_MINKOWSKI) {
+        gcov[0][0] = gcon[0][0] = -1.0;
+        for (int i = 1; i < 4; i++) gcov[i][i] = gcon[i][i] = 1.0;
+        *gdet = 1.0;
+        return;
+    }
+    const double a = d.a;
+    const double r = std::exp(x1);
+    const double th = mirror_theta(x2);
+    const double sth = std::sin(th), cth = std::cos(th);
+    const double s2 = sth * sth;
+    const double sig = r * r + a * a * cth * cth;
+    const double del = r * r - 2.0 * r + a * a;
+    const double z = 2.0 * r / sig;
+    /* covariant KS: g_tt, g_tr, g_tphi, g_rr, g_rphi, g_thth, g_phph */
+    gcov[0][0] = -(1.0 - z);
+    gcov[0][1] = gcov[1][0] = z * r;
+    gcov[0][3] = gcov[3][0] = -z * a * s2;
+    gcov[1][1] = (1.0 + z) * r * r;
+    gcov[1][3] = gcov[3][1] = -a * s2 * (1.0 + z) * r;
+    gcov[2][2] = sig;
+    gcov[3][3] = s2 * (sig + a * a * s2 * (1.0 + z));
+    /* contravariant KS */
+    gcon[0][0] = -(1.0 + z);
+    gcon[0][1] = gcon[1][0] = z / r;
+    gcon[1][1] = del / sig / (r * r);
+    gcon[1][3] = gcon[3][1] = a / sig / r;
+    gcon[2][2] = 1.0 / sig;
+    gcon[3][3] = 1.0 / (sig * s2);
+    *gdet = r * sig * sth;
+}
+
+static void geom_point(const ora_desc& d, double x1, double x2, Geom& G) {
+    double gc[4][4], gn[4][4], gd;
+    metric_point(d, x1, x2, gc, gn, &gd);
+    for (int m = 0; m < 4; m++)
+        for (int n = 0; n < 4; n++) {
+            G.gcov[m][n] = gc[m][n];
+            G.gcon[m][n] = gn[m][n];
+        }
+    G.gdet = gd;
+    G.alpha = 1.0 / std::sqrt(-gn[0][0]);
+    G.pole = 0;
+}
+
+/* Gamma^l_{mn} = 1/2 g^{lk} (d_m g_{kn} + d_n g_{km} - d_k g_{mn}); only
+ * d/dx1 and d/dx2 are non-zero (stationary, axisymmetric metric). */
+static void conn_point(const ora_desc& d, double x1, double x2, double conn[4][4][4]) {
+    double dg[4][4][4];
+    for (int s = 0; s < 4; s++)
+        for (int m = 0; m < 4; m++)
+            for (int n = 0; n < 4; n++) dg[s][m][n] = 0.0;
+    double gc[4][4], gn[4][4], gd;
+    if (d.metric != ORA_METRIC_MINKOWSKI) {
+        const double h = CONN_H;
+        for (int s = 1; s <= 2; s++) {
+            double gp2[4][4], gp1[4][4], gm1[4][4], gm2[4][4];
+            double ex1 = (s == 1) ? h : 0.0, ex2 = (s == 2) ? h : 0.0;
+            metric_point(d, x1 + 2 * ex1, x2 + 2 * ex2, gp2, gn, &gd);
+            metric_point(d, x1 + ex1, x2 + ex2, gp1, gn, &gd);
+            metric_point(d, x1 - ex1, x2 - ex2, gm1, gn, &gd);
+            metric_point(d, x1 - 2 * ex1, x2 - 2 * ex2, gm2, gn, &gd);
+            for (int m = 0; m < 4; m++)
+                for (int n = 0; n < 4; n++)
+                    dg[s][m][n] = (-gp2[m][n] + 8.0 * gp1[m][n] - 8.0 * gm1[m][n] + gm2[m][n]) / (12.0 * h);
+        }
+    }
+    metric_point(d, x1, x2, gc, gn, &gd);
+    for (int l = 0; l < 4; l++)
+        for (int m = 0; m < 4; m++)
+            for (int n = 0; n < 4; n++) {
+                double s = 0.0;
+                for (int k = 0; k < 4; k++) s += gn[l][k] * (dg[m][k][n] + dg[n][k][m] - dg[k][m][n]);
+                conn[l][m][n] = 0.5 * s;
+            }
+}
+
+/* ------------------------------------------------------------------ */
+/* primitives -> 4-vectors (Sec. 2.3)                                   */
+/* ------------------------------------------------------------------ */
+
+struct State {
+    real ucon[4], ucov[4], bcon[4], bcov[4];
+    real bsq;
+};
+
+static void lower(const real v[4], const Geom& G, real out[4]) {
+    for (int m = 0; m < 4; m++) {
+        real s = 0.0;
+        for (int n = 0; n < 4; n++) s += G.gcov[m][n] * v[n];
+        out[m] = s;
+    }
+}
+
+/* u^mu from utilde^i: Lorentz factor wrt the normal observer
+ * Gamma = sqrt(1 + g_ij ut^i ut^j); u^t = Gamma/alpha;
+ * u^i = ut^i - Gamma alpha g^{ti}.
+ * Reading: the paper writes utilde^i = u^i + beta^i Gamma/alpha with
+ * "beta^i = g^{0i}"; the shift that makes utilde^i = gamma^i_mu u^mu hold is
+ * beta^i = alpha^2 g^{0i}, which is what is used here.
+ * b^t = B^i u_i, b^i = (B^i + b^t u^i)/u^t. */
+static void get_state(const real* pr, const Geom& G, State& s) {
+    real qsq = 0.0;
+    for (int i = 1; i < 4; i++)
+        for (int j = 1; j < 4; j++) qsq += G.gcov[i][j] * pr[U1 + i - 1] * pr[U1 + j - 1];
+    real gamma = sqrt(1.0 + qsq);
+    s.ucon[0] = gamma / G.alpha;
+    for (int i = 1; i < 4; i++) s.ucon[i] = pr[U1 + i - 1] - gamma * G.alpha * G.gcon[0][i];
+    lower(s.ucon, G, s.ucov);
+    real bt = 0.0;
+    for (int i = 1; i < 4; i++) bt += pr[B1 + i - 1] * s.ucov[i];
+    s.bcon[0] = bt;
+    for (int i = 1; i < 4; i++) s.bcon[i] = (pr[B1 + i - 1] + bt * s.ucon[i]) / s.ucon[0];
+    lower(s.bcon, G, s.bcov);
+    real bsq = 0.0;
+    for (int m = 0; m < 4; m++) bsq += s.bcon[m] * s.bcov[m];
+    s.bsq = bsq;
+}
+
+/* T^mu_nu of ideal MHD.
+ * Reading: the printed T^mu_nu omits the b^2 u^mu u_nu term; the stress
+ * tensor of the paper's own F*^{mu nu} = b^mu u^nu - b^nu u^mu contains it, so
+ * T^mu_nu = (rho + u + p + b^2) u^mu u_nu + delta^mu_nu (p + b^2/2) - b^mu b_nu. */
+static real tmunu(const real* pr, const State& s, int mu, int nu, double gam) {
+    real p = (gam - 1.0) * pr[UU];
+    real eta = pr[RHO] + pr[UU] + p + s.bsq;
+    real t = eta * s.ucon[mu] * s.ucov[nu] - s.bcon[mu] * s.bcov[nu];
+    if (mu == nu) t = t + (p + 0.5 * s.bsq);
+    return t;
+}
+
+/* U (dir = 0) or F^dir (dir = 1..3), not yet multiplied by sqrt(-g):
+ *   [rho u^dir, T^dir_t + rho u^dir, T^dir_i, kappa rho u^dir, B-flux^1..3].
+ * Reading: the energy entry is T^dir_t + rho u^dir for U and F alike (the
+ * paper evolves div(T^mu_t + rho u^mu)); the printed "+ rho u^t" in F is taken
+ * as a slip.
+ * Reading: the flux of B^i in direction j is F*^{ij} = b^i u^j - b^j u^i, the
+ * sign that makes U_B = B^i = F*^{it} obey div F* = 0; the printed
+ * "b^j u^i - b^i u^j" has the opposite sign. (For dir = 0 this gives B^i.) */
+static void prim_to_uf(const real* pr, const State& s, int dir, double gam, real out[9]) {
+    real mass = pr[RHO] * s.ucon[dir];
+    out[0] = mass;
+    out[1] = tmunu(pr, s, dir, 0, gam) + mass;
+    for (int i = 1; i < 4; i++) out[1 + i] = tmunu(pr, s, dir, i, gam);
+    real p = (gam - 1.0) * pr[UU];
+    real kappa = p / pow(pr[RHO], gam);
+    out[5] = kappa * mass;
+    for (int i = 1; i < 4; i++) out[5 + i] = s.bcon[i] * s.ucon[dir] - s.bcon[dir] * s.ucon[i];
+}
+
+/* Fastest characteristic speeds dx^dir/dt of the magnetosonic wave.
+ * Reading (Sec. 2.1 "approximation for the fast-wave speed"): the fluid-frame
+ * speed c^2 = vA^2 + cs^2 (1 - vA^2), cs^2 = gam p / w, vA^2 = b^2/(b^2 + w),
+ * w = rho + u + p, put into the dispersion relation of a sound wave,
+ * (k.u)^2 = c^2 (k.k + (k.u)^2) with k_mu = (-v, delta^dir_mu):
+ *   A v^2 - 2 B v + C = 0,
+ *   A = (u^t)^2 - c^2 ((u^t)^2 + g^tt), B = u^t u^d - c^2 (u^t u^d + g^td),
+ *   C = (u^d)^2 - c^2 ((u^d)^2 + g^dd). */
+static void vchar(const real* pr, const State& s, const Geom& G, int dir, double gam, real* vp,
+                  real* vm) {
+    real p = (gam - 1.0) * pr[UU];
+    real w = pr[RHO] + pr[UU] + p;
+    real cs2 = gam * p / w;
+    real va2 = s.bsq / (s.bsq + w);
+    real cms2 = va2 + cs2 * (1.0 - va2);
+    real ut = s.ucon[0], ud = s.ucon[dir];
+    real A = ut * ut - cms2 * (ut * ut + G.gcon[0][0]);
+    real B = ut * ud - cms2 * (ut * ud + G.gcon[0][dir]);
+    real C = ud * ud - cms2 * (ud * ud + G.gcon[dir][dir]);
+    real disc = B * B - A * C;
+    if (disc < 0.0) disc = 0.0;
+    real sd = sqrt(disc);
+    *vp = (B + sd) / A;
+    *vm = (B - sd) / A;
+}
+
+/* ------------------------------------------------------------------ */
+/* reconstruction (Sec. 2.1)                                            */
+/* ------------------------------------------------------------------ */
+
+/* Monotonised central slope (Colella-Woodward 1984 form):
+ * sign(dc) min(|dc|, 2|dl|, 2|dr|) when dl, dr have the same sign, else 0. */
+static real slope_mc(real qm, real q0, real qp) {
+    real dl = q0 - qm, dr = qp - q0;
+    if (dl * dr <= 0.0) return 0.0;
+    real dc = 0.5 * (qp - qm);
+    real m = fabs(dc);
+    if (2.0 * fabs(dl) < m) m = 2.0 * fabs(dl);
+    if (2.0 * fabs(dr) < m) m = 2.0 * fabs(dr);
+    return (dc > 0.0) ? m : -m;
+}
+
+static real slope_minmod(real qm, real q0, real qp) {
+    real dl = q0 - qm, dr = qp - q0;
+    if (dl * dr <= 0.0) return 0.0;
+    return (fabs(dl) < fabs(dr)) ? dl : dr;
+}
+
+/* Left/right edge values of every cell of a 1-D line q[0..n-1].
+ * PPM (Reading: Colella & Woodward 1984 on a uniform mesh, no flattener, no
+ * steepener, as the paper's shock tubes): interface values
+ * a_{c+1/2} = (q_c + q_{c+1})/2 - (dq_{c+1} - dq_c)/6 with monotonised slopes,
+ * then the per-cell parabola constraints. Valid for c = 2..n-3.
+ * MC / MINMOD: piecewise linear, valid for c = 1..n-2. */
+static void recon_line_impl(int recon, int n, const real* q, real* al, real* ar) {
+    if (recon == ORA_RECON_PPM) {
+        std::vector<real> dq(n, real(0.0)), ah(n, real(0.0));
+        for (int c = 1; c <= n - 2; c++) dq[c] = slope_mc(q[c - 1], q[c], q[c + 1]);
+        for (int c = 1; c <= n - 3; c++) ah[c] = 0.5 * (q[c] + q[c + 1]) - (dq[c + 1] - dq[c]) / 6.0;
+        for (int c = 2; c <= n - 3; c++) {
+            real aL = ah[c - 1], aR = ah[c], q0 = q[c];
+            if ((aR - q0) * (q0 - aL) <= 0.0) {
+                aL = q0;
+                aR = q0;
+            } else {
+                real da = aR - aL;
+                real a6 = 6.0 * (q0 - 0.5 * (aL + aR));
+                if (da * a6 > da * da)
+                    aL = 3.0 * q0 - 2.0 * aR;
+                else if (-(da * da) > da * a6)
+                    aR = 3.0 * q0 - 2.0 * aL;
+            }
+            al[c] = aL;
+            ar[c] = aR;
+        }
+    } else {
+        for (int c = 1; c <= n - 2; c++) {
+            real dq = (recon == ORA_RECON_MC) ? slope_mc(q[c - 1], q[c], q[c + 1])
+                                              : slope_minmod(q[c - 1], q[c], q[c + 1]);
+            al[c] = q[c] - 0.5 * dq;
+            ar[c] = q[c] + 0.5 * dq;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Riemann solver (Sec. 2.1)                                            */
+/* ------------------------------------------------------------------ */
+
+static int bslot(int dir, int i) { /* flux slot 6/7 of B^i for a dir-face, i != dir */
+    int t1 = (dir == 1) ? 2 : 1;
+    return (i == t1) ? 6 : 7;
+}
+
+/* HLLE flux through a dir-face, multiplied by the face sqrt(-g):
+ *   F = (cmin F_R + cmax F_L - cmax cmin (U_R - U_L)) / (cmax + cmin),
+ *   cmax = max(0, v+_L, v+_R), cmin = max(0, -v-_L, -v-_R).
+ * Reading: when cmax + cmin = 0, F = (F_L + F_R)/2.
+ * LLF: c = max(cmax, cmin), F = (F_L + F_R - c (U_R - U_L))/2. */
+static void face_flux(const ora_desc& d, const real* pl, const real* pr, const Geom& G, int dir,
+                      real F[NFX]) {
+    if (G.pole) {
+        for (int m = 0; m < NFX; m++) F[m] = 0.0;
+        return;
+    }
+    State sl, sr;
+    get_state(pl, G, sl);
+    get_state(pr, G, sr);
+    real Ul[9], Ur[9], Fl[9], Fr[9];
+    prim_to_uf(pl, sl, 0, d.gam, Ul);
+    prim_to_uf(pl, sl, dir, d.gam, Fl);
+    prim_to_uf(pr, sr, 0, d.gam, Ur);
+    prim_to_uf(pr, sr, dir, d.gam, Fr);
+    real vpl, vml, vpr, vmr;
+    vchar(pl, sl, G, dir, d.gam, &vpl, &vml);
+    vchar(pr, sr, G, dir, d.gam, &vpr, &vmr);
+    real cmax = fmax(0.0, fmax(vpl, vpr));
+    real cmin = fmax(0.0, fmax(-vml, -vmr));
+    int src[NFX] = {0, 1, 2, 3, 4, 5, 0, 0};
+    for (int i = 1, k = 6; i < 4; i++)
+        if (i != dir) src[k++] = 5 + i;
+    for (int m = 0; m < NFX; m++) {
+        int c = src[m];
+        real f;
+        if (d.riemann == ORA_FLUX_LLF) {
+            real cm = fmax(cmax, cmin);
+            f = 0.5 * (Fl[c] + Fr[c] - cm * (Ur[c] - Ul[c]));
+        } else if (cmax + cmin > 0.0) {
+            f = (cmin * Fr[c] + cmax * Fl[c] - cmax * cmin * (Ur[c] - Ul[c])) / (cmax + cmin);
+        } else {
+            f = 0.5 * (Fl[c] + Fr[c]);
+        }
+        F[m] = f * G.gdet;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* source (Sec. 2.5): Qbar_nu = sqrt(-g) T^k_l Gamma^l_{nu k}           */
+/* ------------------------------------------------------------------ */
+
+/* Reading: the paper prints the momentum component; the energy component
+ * (nu = t) follows from the same covariant divergence, and mass, entropy and
+ * B have no source. */
+static void source_terms(const ora_desc& d, const real* pr, const State& s, const Geom& G,
+                         const double conn[4][4][4], real Q[NCONS]) {
+    real T[4][4];
+    for (int k = 0; k < 4; k++)
+        for (int l = 0; l < 4; l++) T[k][l] = tmunu(pr, s, k, l, d.gam);
+    real q[4];
+    for (int nu = 0; nu < 4; nu++) {
+        real sum = 0.0;
+        for (int k = 0; k < 4; k++)
+            for (int l = 0; l < 4; l++) sum += T[k][l] * real(conn[l][nu][k]);
+        q[nu] = sum * G.gdet;
+    }
+    Q[CRHO] = 0.0;
+    Q[CEN] = q[0];
+    Q[CS1] = q[1];
+    Q[CS2] = q[2];
+    Q[CS3] = q[3];
+    Q[CENT] = 0.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* conserved -> primitive inversion (Sec. 2.6)                          */
+/* ------------------------------------------------------------------ */
+
+enum { C2P_OK = 0, C2P_ENTROPY = 1, C2P_FAIL = 2, C2P_FLOOR = 4 };
+
+/* Inverts U (sqrt(-g) weighted: rho u^t, T^t_t + rho u^t, T^t_i, kappa rho u^t)
+ * with the cell-centred B^i, for rho, u, utilde^i.
+ *
+ * Normal-observer scalars (n_mu = (-alpha, 0, 0, 0), sqrt(gamma) = sqrt(-g)/alpha):
+ *   D = rho Gamma, Q_mu = -n_nu T^nu_mu = alpha T^t_mu, Bn^i = alpha B^i,
+ *   Q.n = -alpha Q^t, Qt^2 = Q_mu Q^mu + (Q.n)^2, B^2 = g_ij Bn^i Bn^j, Q.B.
+ * Unknowns W = w Gamma^2 (w = rho + u + p) and v^2 = 1 - 1/Gamma^2:
+ *   E1: Q.n = -B^2 (1 + v^2)/2 + (Q.B)^2 / (2 W^2) - W + p
+ *   E2: Qt^2 = v^2 (B^2 + W)^2 - (Q.B)^2 (B^2 + 2W) / W^2
+ *   p  = (gam-1)/gam [ W (1 - v^2) - D sqrt(1 - v^2) ]
+ * solved by 2-D Newton-Raphson with the analytic Jacobian (energy inversion);
+ * if that fails, the entropy inversion takes p = kappa rho^gam with
+ * kappa = U_kappa / U_rho and solves E2 together with
+ * W (1 - v^2) = rho + gam/(gam-1) p, rho = D sqrt(1 - v^2) by 1-D Newton in W.
+ * Recovery: rho = D/Gamma, u = p/(gam-1),
+ *   utilde^i = Gamma/(W + B^2) (Qt^i + (Q.B) Bn^i / W),
+ *   Qt^i = (g^{i nu} + n^i n^nu) Q_nu (spatial projection of Q).
+ * Reading: tolerance |dW|/W + |dv^2| < 1e-12, at most 30 iterations,
+ * v^2 kept in [0, 1 - 1/50^2]; a failed state keeps its guess. */
+static int con2prim(const ora_desc& d, const real Ucons[NCONS], const real Bc[3], const Geom& G,
+                    real* pr, int* iters, int entropy_only = 0) {
+    const double gam = d.gam;
+    const double gfac = (gam - 1.0) / gam;
+    const double vsqmax = 1.0 - 1.0 / (GAMMA_MAX * GAMMA_MAX);
+    real alpha = G.alpha, gdet = G.gdet;
+    real D = Ucons[CRHO] * alpha / gdet;
+    real Qcov[4];
+    Qcov[0] = alpha * (Ucons[CEN] - Ucons[CRHO]) / gdet;
+    Qcov[1] = alpha * Ucons[CS1] / gdet;
+    Qcov[2] = alpha * Ucons[CS2] / gdet;
+    Qcov[3] = alpha * Ucons[CS3] / gdet;
+    real Qcon[4];
+    for (int m = 0; m < 4; m++) {
+        real s = 0.0;
+        for (int n = 0; n < 4; n++) s += G.gcon[m][n] * Qcov[n];
+        Qcon[m] = s;
+    }
+    real Bn[4] = {0.0, alpha * Bc[0], alpha * Bc[1], alpha * Bc[2]};
+    real Qdotn = -alpha * Qcon[0];
+    real Qsq = 0.0;
+    for (int m = 0; m < 4; m++) Qsq += Qcov[m] * Qcon[m];
+    real Qtsq = Qsq + Qdotn * Qdotn;
+    real Bsq = 0.0;
+    for (int i = 1; i < 4; i++)
+        for (int j = 1; j < 4; j++) Bsq += G.gcov[i][j] * Bn[i] * Bn[j];
+    real QdotB = 0.0;
+    for (int i = 1; i < 4; i++) QdotB += Qcov[i] * Bn[i];
+    real QdotBsq = QdotB * QdotB;
+
+    /* initial guess from the guess primitives */
+    real qsq = 0.0;
+    for (int i = 1; i < 4; i++)
+        for (int j = 1; j < 4; j++) qsq += G.gcov[i][j] * pr[U1 + i - 1] * pr[U1 + j - 1];
+    real gsq = 1.0 + qsq;
+    real vsq = qsq / gsq;
+    if (vsq > vsqmax) vsq = vsqmax;
+    real W = (pr[RHO] + gam * pr[UU]) * gsq;
+    real W0 = W;
+
+    int ok = 0, it = 0;
+    for (it = 1; it <= (entropy_only ? 0 : C2P_NMAX); it++) {
+        real sq = sqrt(1.0 - vsq);
+        real p = gfac * (W * (1.0 - vsq) - D * sq);
+        real W2 = W * W;
+        real BW = Bsq + W;
+        real f1 = -0.5 * Bsq * (1.0 + vsq) + QdotBsq / (2.0 * W2) - W + p - Qdotn;
+        real f2 = vsq * BW * BW - QdotBsq * (Bsq + 2.0 * W) / W2 - Qtsq;
+        real dpdW = gfac * (1.0 - vsq);
+        real dpdv = gfac * (-W + 0.5 * D / sq);
+        real j11 = -QdotBsq / (W2 * W) - 1.0 + dpdW;
+        real j12 = -0.5 * Bsq + dpdv;
+        real j21 = 2.0 * vsq * BW + 2.0 * QdotBsq * BW / (W2 * W);
+        real j22 = BW * BW;
+        real det = j11 * j22 - j12 * j21;
+        real dW = -(j22 * f1 - j12 * f2) / det;
+        real dv = -(j11 * f2 - j21 * f1) / det;
+        real Wn = W + dW;
+        real vn = vsq + dv;
+        if (vn < 0.0) vn = 0.0;
+        if (vn > vsqmax) vn = vsqmax;
+        if (!(Wn > 0.0)) break;
+        real err = fabs(Wn - W) / Wn + fabs(vn - vsq);
+        W = Wn;
+        vsq = vn;
+        if (err < C2P_TOL) {
+            ok = 1;
+            break;
+        }
+    }
+    if (it > C2P_NMAX) it = C2P_NMAX;
+    if (entropy_only) it = 0;
+    *iters = it;
+    real rho = 0.0, u = 0.0;
+    if (ok) {
+        real sq = sqrt(1.0 - vsq);
+        real p = gfac * (W * (1.0 - vsq) - D * sq);
+        rho = D * sq;
+        u = p / (gam - 1.0);
+        if (!(rho > 0.0) || !(u > 0.0)) ok = 0;
+    }
+    int status = C2P_OK;
+    if (!ok) {
+        /* entropy inversion */
+        real kappa = Ucons[CENT] / Ucons[CRHO];
+        const double gr = gam / (gam - 1.0);
+        W = W0;
+        int eok = 0;
+        for (int k = 1; k <= C2P_NMAX; k++) {
+            real W2 = W * W;
+            real BW = Bsq + W;
+            real num = Qtsq * W2 + QdotBsq * (Bsq + 2.0 * W);
+            real den = W2 * BW * BW;
+            real vs = num / den;
+            real dnum = 2.0 * Qtsq * W + 2.0 * QdotBsq;
+            real dden = 2.0 * W * BW * (Bsq + 2.0 * W);
+            real dvs = (dnum * den - num * dden) / (den * den);
+            if (vs > vsqmax) {
+                vs = vsqmax;
+                dvs = 0.0;
+            }
+            real s1 = 1.0 - vs;
+            real sq = sqrt(s1);
+            real rh = D * sq;
+            real p = kappa * pow(rh, gam);
+            real f = W * s1 - rh - gr * p;
+            real drh = -0.5 * D / sq * dvs;
+            real dp = gam * p / rh * drh;
+            real df = s1 - W * dvs - drh - gr * dp;
+            real Wn = W - f / df;
+            if (!(Wn > 0.0)) break;
+            real err = fabs(Wn - W) / Wn;
+            W = Wn;
+            if (err < C2P_TOL) {
+                eok = 1;
+                vsq = vs;
+                break;
+            }
+        }
+        if (eok) {
+            /* final consistent v^2(W) */
+            real W2 = W * W;
+            real BW = Bsq + W;
+            vsq = (Qtsq * W2 + QdotBsq * (Bsq + 2.0 * W)) / (W2 * BW * BW);
+            if (vsq > vsqmax) vsq = vsqmax;
+            real sq = sqrt(1.0 - vsq);
+            rho = D * sq;
+            u = kappa * pow(rho, gam) / (gam - 1.0);
+            if (!(rho > 0.0) || !(u > 0.0) || !(vsq >= 0.0)) eok = 0;
+        }
+        if (!eok) return C2P_FAIL; /* keep the guess */
+        status = C2P_ENTROPY;
+    }
+    real gamma = 1.0 / sqrt(1.0 - vsq);
+    real pre = gamma / (W + Bsq);
+    for (int i = 1; i < 4; i++) {
+        real Qt = Qcon[i] - alpha * G.gcon[0][i] * Qdotn;
+        pr[U1 + i - 1] = pre * (Qt + QdotB * Bn[i] / W);
+    }
+    pr[RHO] = rho;
+    pr[UU] = u;
+    return status;
+}
+
+/* Floors (Sec. 2.7): rho >= max(1e-7/r^2, b^2/50), u >= max(1e-9/r^(10/3), b^2/750).
+ * Reading / deviation: the paper injects mass and energy in the drift frame;
+ * here the floor raises rho and u and keeps utilde^i (fluid-frame injection). */
+static int apply_floors(const ora_desc& d, real* pr, const Geom& G, double r) {
+    State s;
+    get_state(pr, G, s);
+    real rhoflr = 1.0e-7 / (r * r);
+    real uflr = 1.0e-9 * std::pow(r, -10.0 / 3.0);
+    real rb = s.bsq / 50.0, ub = s.bsq / 750.0;
+    if (rb > rhoflr) rhoflr = rb;
+    if (ub > uflr) uflr = ub;
+    int hit = 0;
+    if (pr[RHO] < rhoflr) {
+        pr[RHO] = rhoflr;
+        hit = 1;
+    }
+    if (pr[UU] < uflr) {
+        pr[UU] = uflr;
+        hit = 1;
+    }
+    (void)d;
+    return hit;
+}
+
+} /* namespace */
+
+/* ------------------------------------------------------------------ */
+/* grid                                                                  */
+/* ------------------------------------------------------------------ */
+
+struct ora_grid {
+    ora_desc d;
+    int n1p, n2p, n3p;
+    long ncell;
+    std::vector<double> prim, bface;
+    std::vector<Geom> gc, gf1, gf2; /* (i,j) tables over the padded 2-D extent */
+    std::vector<double> conn;       /* 64 per (i,j) centre */
+    std::vector<double> rc;         /* r at centres */
+    std::vector<int> status;        /* per cell: OR of the inversion/floor bits of the last step */
+    long long stats[4];
+};
+
+namespace {
+
+inline long cidx(const ora_grid* g, int i, int j, int k) {
+    return ((long)(k + NG) * g->n2p + (j + NG)) * g->n1p + (i + NG);
+}
+inline long gidx(const ora_grid* g, int i, int j) { return (long)(j + NG) * g->n1p + (i + NG); }
+
+void build_geometry(ora_grid* g) {
+    const ora_desc& d = g->d;
+    long n2d = (long)g->n1p * g->n2p;
+    g->gc.resize(n2d);
+    g->gf1.resize(n2d);
+    g->gf2.resize(n2d);
+    g->conn.resize(n2d * 64);
+    g->rc.resize(n2d);
+    for (int j = -NG; j < d.n2 + NG; j++)
+        for (int i = -NG; i < d.n1 + NG; i++) {
+            long q = gidx(g, i, j);
+            double x1c = d.x1min + (i + 0.5) * d.dx1, x2c = d.x2min + (j + 0.5) * d.dx2;
+            double x1f = d.x1min + i * d.dx1, x2f = d.x2min + j * d.dx2;
+            geom_point(d, x1c, x2c, g->gc[q]);
+            geom_point(d, x1f, x2c, g->gf1[q]);
+            geom_point(d, x1c, x2f, g->gf2[q]);
+            if ((d.bc[2] == ORA_BC_POLAR && j == 0) || (d.bc[3] == ORA_BC_POLAR && j == d.n2)) {
+                g->gf2[q].pole = 1;
+                g->gf2[q].gdet = 0.0;
+            }
+            double cn[4][4][4];
+            conn_point(d, x1c, x2c, cn);
+            std::memcpy(&g->conn[q * 64], cn, sizeof(cn));
+            g->rc[q] = (d.metric == ORA_METRIC_KS) ? std::exp(x1c) : 1.0;
+        }
+}
+
+/* Boundary conditions (Sec. 3.3 transmissive pole; radial outflow; periodic
+ * phi). Reading: applied direction by direction in the order x3, x2, x1, each
+ * pass over the full padded extent of the other two directions, so corner
+ * ghosts take the composition of the three maps.
+ * Polar: ghost cell (j = -1-m, k) takes interior (j = m, k + n3/2) with
+ * utilde^2 and B^2 negated (the theta basis vector flips across the axis);
+ * ghost x2-faces likewise (Bbar^2 negated); faces on the axis hold 0.
+ * Outflow: copy the last interior cell (faces: the last interior face);
+ * OUTFLOW_NOINFLOW also clamps utilde^1 so that nothing flows in.
+ * Periodic: copy from the other end (face n equals face 0). */
+int bc_cell_src(int bc, int n, int gi) {
+    if (bc == ORA_BC_PERIODIC) return gi < 0 ? gi + n : gi - n;
+    if (bc == ORA_BC_POLAR) return gi < 0 ? -1 - gi : 2 * n - 1 - gi;
+    return gi < 0 ? 0 : n - 1;
+}
+int bc_face_src(int bc, int n, int gf) {
+    if (bc == ORA_BC_PERIODIC) return gf < 0 ? gf + n : gf - n;
+    if (bc == ORA_BC_POLAR) return gf < 0 ? -gf : 2 * n - gf;
+    return gf < 0 ? 0 : n;
+}
+
+void apply_bc(ora_grid* g, double* P, double* Bf) {
+    const ora_desc& d = g->d;
+    const long nc = g->ncell;
+    const int nn[4] = {0, d.n1, d.n2, d.n3};
+    for (int e = 3; e >= 1; e--) {
+        const int ta = (e == 1) ? 2 : 1, tb = (e == 3) ? 2 : 3;
+        for (int side = 0; side < 2; side++) {
+            const int bc = d.bc[2 * (e - 1) + side];
+            const bool polar = (bc == ORA_BC_POLAR);
+            for (int b = -NG; b < nn[tb] + NG; b++)
+                for (int a = -NG; a < nn[ta] + NG; a++) {
+                    int src_ab[4] = {0, 0, 0, 0};
+                    src_ab[ta] = a;
+                    src_ab[tb] = b;
+                    if (polar) { /* phi shift by pi across the axis (e == 2) */
+                        src_ab[3] = ((src_ab[3] + d.n3 / 2) % d.n3 + d.n3) % d.n3;
+                    }
+                    for (int m = 0; m < NG; m++) {
+                        /* cells and the cell-like face arrays (d != e) */
+                        int gi = (side == 0) ? -1 - m : nn[e] + m;
+                        int si = bc_cell_src(bc, nn[e], gi);
+                        int dd[4] = {0, 0, 0, 0}, ss[4] = {0, src_ab[1], src_ab[2], src_ab[3]};
+                        dd[ta] = a;
+                        dd[tb] = b;
+                        dd[e] = gi;
+                        ss[e] = si;
+                        long dst = cidx(g, dd[1], dd[2], dd[3]), src = cidx(g, ss[1], ss[2], ss[3]);
+                        for (int v = 0; v < NPR; v++) P[v * nc + dst] = P[v * nc + src];
+                        if (polar) {
+                            P[U2 * nc + dst] = -P[U2 * nc + dst];
+                            P[B2 * nc + dst] = -P[B2 * nc + dst];
+                        }
+                        if (bc == ORA_BC_OUTFLOW_NOINFLOW && e == 1) {
+                            if (side == 1 && P[U1 * nc + dst] < 0.0) P[U1 * nc + dst] = 0.0;
+                            if (side == 0 && P[U1 * nc + dst] > 0.0) P[U1 * nc + dst] = 0.0;
+                        }
+                        for (int f = 1; f <= 3; f++)
+                            if (f != e) Bf[(f - 1) * nc + dst] = Bf[(f - 1) * nc + src];
+                        /* the face array of direction e: ghost faces -1..-3, n+1..n+2;
+                         * periodic also copies face 0 onto face n */
+                        int gf = (side == 0) ? -1 - m : nn[e] + (bc == ORA_BC_PERIODIC ? 0 : 1) + m;
+                        if (gf >= nn[e] + NG) continue;
+                        int sf = bc_face_src(bc, nn[e], gf);
+                        dd[e] = gf;
+                        ss[e] = sf;
+                        dst = cidx(g, dd[1], dd[2], dd[3]);
+                        src = cidx(g, ss[1], ss[2], ss[3]);
+                        Bf[(e - 1) * nc + dst] = polar ? -Bf[(e - 1) * nc + src] : Bf[(e - 1) * nc + src];
+                    }
+                    if (polar) { /* the axis face itself */
+                        int dd[4] = {0, 0, 0, 0};
+                        dd[ta] = a;
+                        dd[tb] = b;
+                        dd[e] = (side == 0) ? 0 : nn[e];
+                        Bf[(e - 1) * nc + cidx(g, dd[1], dd[2], dd[3])] = 0.0;
+                    }
+                }
+        }
+    }
+}
+
+/* centre B^i = (Bbar^i_lo + Bbar^i_hi) / 2 / sqrt(-g)_centre (Sec. 2.5) */
+void centre_b(ora_grid* g, const double* Bf, int i, int j, int k, real Bc[3]) {
+    const long nc = g->ncell;
+    real gd = g->gc[gidx(g, i, j)].gdet;
+    Bc[0] = 0.5 * (real(Bf[0 * nc + cidx(g, i, j, k)]) + real(Bf[0 * nc + cidx(g, i + 1, j, k)])) / gd;
+    Bc[1] = 0.5 * (real(Bf[1 * nc + cidx(g, i, j, k)]) + real(Bf[1 * nc + cidx(g, i, j + 1, k)])) / gd;
+    Bc[2] = 0.5 * (real(Bf[2 * nc + cidx(g, i, j, k)]) + real(Bf[2 * nc + cidx(g, i, j, k + 1)])) / gd;
+}
+
+void load_prim(const ora_grid* g, const double* P, long c, real* pr) {
+    for (int v = 0; v < NPR; v++) pr[v] = P[v * g->ncell + c];
+}
+
+/* One stage of the midpoint scheme (Sec. 2.1, 2.5):
+ *   fluxes, EMFs and sources from (Pf, Bff) [ghosts filled];
+ *   Bf_out = Bf_base + dts * curl E;  U = U(P_base) + dts (-div F + Q);
+ *   P_out = con2prim(U, centre B of Bf_out), guess Pf; floors. */
+void stage(ora_grid* g, const double* Pf, const double* Bff, const double* Pb, const double* Bfb,
+           double dts, double* Pout, double* Bfout) {
+    const ora_desc& d = g->d;
+    const long nc = g->ncell;
+    const int n1 = d.n1, n2 = d.n2, n3 = d.n3;
+    const int nn[4] = {0, n1, n2, n3};
+    const double dx[4] = {0.0, d.dx1, d.dx2, d.dx3};
+
+    std::vector<double> F[4];
+    for (int dir = 1; dir <= 3; dir++) F[dir].assign((size_t)NFX * nc, 0.0);
+
+    /* fluxes: dir-faces over the interior faces, one transverse ghost layer */
+    for (int dir = 1; dir <= 3; dir++) {
+        int lo[4], hi[4]; /* inclusive face/cell ranges */
+        for (int e = 1; e <= 3; e++) {
+            lo[e] = (e == dir) ? 0 : -1;
+            hi[e] = (e == dir) ? nn[e] : nn[e];
+        }
+        int L = nn[dir] + 2 * NG;
+        std::vector<real> q(L), al(L), ar(L);
+        std::vector<real> PL((size_t)NPR * L), PR((size_t)NPR * L);
+        /* loop over lines along dir */
+        int ta = (dir == 1) ? 2 : 1, tb = (dir == 3) ? 2 : 3;
+        for (int b = lo[tb]; b <= hi[tb]; b++)
+            for (int a = lo[ta]; a <= hi[ta]; a++) {
+                for (int v = 0; v < NPR; v++) {
+                    if (v == B1 + dir - 1) continue;
+                    for (int c = 0; c < L; c++) {
+                        int ii[4];
+                        ii[dir] = c - NG;
+                        ii[ta] = a;
+                        ii[tb] = b;
+                        q[c] = Pf[v * nc + cidx(g, ii[1], ii[2], ii[3])];
+                    }
+                    recon_line_impl(d.recon, L, q.data(), al.data(), ar.data());
+                    for (int c = 0; c < L; c++) {
+                        PL[(size_t)v * L + c] = al[c];
+                        PR[(size_t)v * L + c] = ar[c];
+                    }
+                }
+                for (int f = lo[dir]; f <= hi[dir]; f++) {
+                    int ii[4];
+                    ii[dir] = f;
+                    ii[ta] = a;
+                    ii[tb] = b;
+                    long fi = cidx(g, ii[1], ii[2], ii[3]);
+                    const Geom& G = (dir == 1)   ? g->gf1[gidx(g, ii[1], ii[2])]
+                                    : (dir == 2) ? g->gf2[gidx(g, ii[1], ii[2])]
+                                                 : g->gc[gidx(g, ii[1], ii[2])];
+                    real pl[NPR], pr[NPR];
+                    int cl = f - 1 + NG, cr = f + NG; /* line positions of the two cells */
+                    for (int v = 0; v < NPR; v++) {
+                        if (v == B1 + dir - 1) continue;
+                        pl[v] = PR[(size_t)v * L + cl]; /* right edge of the left cell */
+                        pr[v] = PL[(size_t)v * L + cr]; /* left edge of the right cell */
+                    }
+                    real fx[NFX];
+                    if (G.pole) {
+                        for (int m = 0; m < NFX; m++) fx[m] = 0.0;
+                    } else {
+                        real bn = real(Bff[(dir - 1) * nc + fi]) / G.gdet;
+                        pl[B1 + dir - 1] = bn;
+                        pr[B1 + dir - 1] = bn;
+                        face_flux(d, pl, pr, G, dir, fx);
+                    }
+                    for (int m = 0; m < NFX; m++) F[dir][(size_t)m * nc + fi] = tod(fx[m]);
+                }
+            }
+    }
+
+    /* EMFs at edges (Sec. 2.5, the 4-flux average). Reading: E1 and E3 on the
+     * polar axis are 0, which keeps Bbar^2 = 0 on axis faces and div B intact. */
+    std::vector<double> E1(nc, 0.0), E2(nc, 0.0), E3(nc, 0.0);
+    auto FX = [&](int dir, int slot, int i, int j, int k) -> real {
+        return real(F[dir][(size_t)slot * nc + cidx(g, i, j, k)]);
+    };
+    const int s3B2 = bslot(3, 2), s2B3 = bslot(2, 3), s1B3 = bslot(1, 3), s3B1 = bslot(3, 1),
+              s2B1 = bslot(2, 1), s1B2 = bslot(1, 2);
+    for (int k = 0; k <= n3; k++)
+        for (int j = 0; j <= n2; j++)
+            for (int i = 0; i <= n1; i++) {
+                long e = cidx(g, i, j, k);
+                bool axis = (d.bc[2] == ORA_BC_POLAR && j == 0) || (d.bc[3] == ORA_BC_POLAR && j == n2);
+                if (i < n1) {
+                    real v = 0.25 * (FX(3, s3B2, i, j, k) + FX(3, s3B2, i, j - 1, k) - FX(2, s2B3, i, j, k - 1) -
+                                     FX(2, s2B3, i, j, k));
+                    E1[e] = axis ? 0.0 : tod(v);
+                }
+                if (j < n2) {
+                    real v = 0.25 * (FX(1, s1B3, i, j, k - 1) + FX(1, s1B3, i, j, k) - FX(3, s3B1, i, j, k) -
+                                     FX(3, s3B1, i - 1, j, k));
+                    E2[e] = tod(v);
+                }
+                if (k < n3) {
+                    real v = 0.25 * (FX(2, s2B1, i - 1, j, k) + FX(2, s2B1, i, j, k) - FX(1, s1B2, i, j, k) -
+                                     FX(1, s1B2, i, j - 1, k));
+                    E3[e] = axis ? 0.0 : tod(v);
+                }
+            }
+
+    /* staggered face update (Sec. 2.5, the three CT equations) */
+    for (int v = 0; v < 3; v++)
+        for (long c = 0; c < nc; c++) Bfout[v * nc + c] = Bfb[v * nc + c];
+    for (int k = 0; k <= n3; k++)
+        for (int j = 0; j <= n2; j++)
+            for (int i = 0; i <= n1; i++) {
+                long c = cidx(g, i, j, k);
+                if (j < n2 && k < n3) {
+                    real r = (real(E2[cidx(g, i, j, k + 1)]) - real(E2[c])) / d.dx3 -
+                             (real(E3[cidx(g, i, j + 1, k)]) - real(E3[c])) / d.dx2;
+                    Bfout[0 * nc + c] = tod(real(Bfb[0 * nc + c]) + dts * r);
+                }
+                if (i < n1 && k < n3) {
+                    bool axis = (d.bc[2] == ORA_BC_POLAR && j == 0) || (d.bc[3] == ORA_BC_POLAR && j == n2);
+                    real r = (real(E3[cidx(g, i + 1, j, k)]) - real(E3[c])) / d.dx1 -
+                             (real(E1[cidx(g, i, j, k + 1)]) - real(E1[c])) / d.dx3;
+                    Bfout[1 * nc + c] = axis ? 0.0 : tod(real(Bfb[1 * nc + c]) + dts * r);
+                }
+                if (i < n1 && j < n2) {
+                    real r = (real(E1[cidx(g, i, j + 1, k)]) - real(E1[c])) / d.dx2 -
+                             (real(E2[cidx(g, i + 1, j, k)]) - real(E2[c])) / d.dx1;
+                    Bfout[2 * nc + c] = tod(real(Bfb[2 * nc + c]) + dts * r);
+                }
+            }
+
+    /* cell update, inversion, floors */
+    for (int k = 0; k < n3; k++)
+        for (int j = 0; j < n2; j++)
+            for (int i = 0; i < n1; i++) {
+                long c = cidx(g, i, j, k);
+                long q2 = gidx(g, i, j);
+                const Geom& G = g->gc[q2];
+                real pb[NPR], pf[NPR];
+                load_prim(g, Pb, c, pb);
+                load_prim(g, Pf, c, pf);
+                State sb, sf;
+                get_state(pb, G, sb);
+                get_state(pf, G, sf);
+                real u9[9];
+                prim_to_uf(pb, sb, 0, d.gam, u9);
+                real Q[NCONS];
+                double cn[4][4][4];
+                std::memcpy(cn, &g->conn[q2 * 64], sizeof(cn));
+                source_terms(d, pf, sf, G, cn, Q);
+                real U[NCONS];
+                long c1 = cidx(g, i + 1, j, k), c2 = cidx(g, i, j + 1, k), c3 = cidx(g, i, j, k + 1);
+                for (int m = 0; m < NCONS; m++) {
+                    real div = (real(F[1][(size_t)m * nc + c1]) - real(F[1][(size_t)m * nc + c])) / dx[1] +
+                               (real(F[2][(size_t)m * nc + c2]) - real(F[2][(size_t)m * nc + c])) / dx[2] +
+                               (real(F[3][(size_t)m * nc + c3]) - real(F[3][(size_t)m * nc + c])) / dx[3];
+                    U[m] = u9[m] * G.gdet + dts * (Q[m] - div);
+                }
+                real Bc[3];
+                centre_b(g, Bfout, i, j, k, Bc);
+                real pr[NPR];
+                for (int v = 0; v < NPR; v++) pr[v] = pf[v];
+                pr[B1] = Bc[0];
+                pr[B2] = Bc[1];
+                pr[B3] = Bc[2];
+                int its = 0;
+                int st = con2prim(d, U, Bc, G, pr, &its);
+                if (st == C2P_FAIL) {
+                    for (int v = 0; v < 5; v++) pr[v] = pf[v];
+                }
+                g->stats[st == C2P_OK ? 0 : (st == C2P_ENTROPY ? 1 : 2)]++;
+                g->status[c] |= st;
+                if (d.floors && apply_floors(d, pr, G, g->rc[q2])) {
+                    g->stats[3]++;
+                    g->status[c] |= C2P_FLOOR;
+                }
+                for (int v = 0; v < NPR; v++) Pout[v * nc + c] = tod(pr[v]);
+            }
+}
+
+/* CFL time step (Sec. 2.1): per cell 1/dt = sum_i v_f^i / dx^i with
+ * v_f^i = max(|v+|, |v-|) at the cell centre; dt = C0 / max over cells.
+ * Reading: speeds are taken at cell centres from the current primitives. */
+double grid_dt(ora_grid* g) {
+    const ora_desc& d = g->d;
+    const double dx[4] = {0.0, d.dx1, d.dx2, d.dx3};
+    real invmax = 0.0;
+    for (int k = 0; k < d.n3; k++)
+        for (int j = 0; j < d.n2; j++)
+            for (int i = 0; i < d.n1; i++) {
+                const Geom& G = g->gc[gidx(g, i, j)];
+                real pr[NPR];
+                load_prim(g, g->prim.data(), cidx(g, i, j, k), pr);
+                State s;
+                get_state(pr, G, s);
+                real inv = 0.0;
+                for (int dir = 1; dir <= 3; dir++) {
+                    real vp, vm;
+                    vchar(pr, s, G, dir, d.gam, &vp, &vm);
+                    real vf = fmax(fabs(vp), fabs(vm));
+                    inv += vf / dx[dir];
+                }
+                if (inv > invmax) invmax = inv;
+            }
+    return tod(d.cour / invmax);
+}
+
+} /* namespace */
+
+/* ------------------------------------------------------------------ */
+/* C interface                                                           */
+/* ------------------------------------------------------------------ */
+
+extern "C" {
+
+void ora_geom(const ora_desc* d, double x1, double x2, double* gcov16, double* gcon16, double* gdet,
+              double* alpha) {
+    Geom G;
+    geom_point(*d, x1, x2, G);
+    for (int m = 0; m < 4; m++)
+        for (int n = 0; n < 4; n++) {
+            gcov16[4 * m + n] = tod(G.gcov[m][n]);
+            gcon16[4 * m + n] = tod(G.gcon[m][n]);
+        }
+    *gdet = tod(G.gdet);
+    *alpha = tod(G.alpha);
+}
+
+void ora_conn(const ora_desc* d, double x1, double x2, double* conn64) {
+    double cn[4][4][4];
+    conn_point(*d, x1, x2, cn);
+    std::memcpy(conn64, cn, sizeof(cn));
+}
+
+void ora_state(const ora_desc* d, const double* pr8, double x1, double x2, double* ucon4, double* ucov4,
+               double* bcon4, double* bcov4, double* bsq) {
+    Geom G;
+    geom_point(*d, x1, x2, G);
+    real pr[NPR];
+    for (int v = 0; v < NPR; v++) pr[v] = pr8[v];
+    State s;
+    get_state(pr, G, s);
+    for (int m = 0; m < 4; m++) {
+        ucon4[m] = tod(s.ucon[m]);
+        ucov4[m] = tod(s.ucov[m]);
+        bcon4[m] = tod(s.bcon[m]);
+        bcov4[m] = tod(s.bcov[m]);
+    }
+    *bsq = tod(s.bsq);
+}
+
+void ora_p2uf(const ora_desc* d, const double* pr8, double x1, double x2, int dir, double* out9) {
+    Geom G;
+    geom_point(*d, x1, x2, G);
+    real pr[NPR];
+    for (int v = 0; v < NPR; v++) pr[v] = pr8[v];
+    State s;
+    get_state(pr, G, s);
+    real o[9];
+    prim_to_uf(pr, s, dir, d->gam, o);
+    for (int m = 0; m < 9; m++) out9[m] = tod(o[m] * G.gdet);
+}
+
+void ora_vchar(const ora_desc* d, const double* pr8, double x1, double x2, int dir, double* vp, double* vm) {
+    Geom G;
+    geom_point(*d, x1, x2, G);
+    real pr[NPR];
+    for (int v = 0; v < NPR; v++) pr[v] = pr8[v];
+    State s;
+    get_state(pr, G, s);
+    real a, b;
+    vchar(pr, s, G, dir, d->gam, &a, &b);
+    *vp = tod(a);
+    *vm = tod(b);
+}
+
+void ora_face_flux(const ora_desc* d, const double* pl8, const double* pr8, double x1, double x2, int dir,
+                   double* f8) {
+    Geom G;
+    geom_point(*d, x1, x2, G);
+    real pl[NPR], pr[NPR], f[NFX];
+    for (int v = 0; v < NPR; v++) {
+        pl[v] = pl8[v];
+        pr[v] = pr8[v];
+    }
+    face_flux(*d, pl, pr, G, dir, f);
+    for (int m = 0; m < NFX; m++) f8[m] = tod(f[m]);
+}
+
+void ora_source(const ora_desc* d, const double* pr8, double x1, double x2, double* q6) {
+    Geom G;
+    geom_point(*d, x1, x2, G);
+    double cn[4][4][4];
+    conn_point(*d, x1, x2, cn);
+    real pr[NPR];
+    for (int v = 0; v < NPR; v++) pr[v] = pr8[v];
+    State s;
+    get_state(pr, G, s);
+    real Q[NCONS];
+    source_terms(*d, pr, s, G, cn, Q);
+    for (int m = 0; m < NCONS; m++) q6[m] = tod(Q[m]);
+}
+
+void ora_recon_line(int recon, int n, const double* q, double* al, double* ar) {
+    std::vector<real> qq(n), a(n, real(0.0)), b(n, real(0.0));
+    for (int c = 0; c < n; c++) {
+        qq[c] = q[c];
+        a[c] = al[c];
+        b[c] = ar[c];
+    }
+    recon_line_impl(recon, n, qq.data(), a.data(), b.data());
+    for (int c = 0; c < n; c++) {
+        al[c] = tod(a[c]);
+        ar[c] = tod(b[c]);
+    }
+}
+
+void ora_c2p_many(const ora_desc* d, long n, const double* U6, const double* Bc3, const double* x1,
+                  const double* x2, double* pr8, int* status, int* iters, int entropy_only) {
+    for (long s = 0; s < n; s++) {
+        Geom G;
+        geom_point(*d, x1[s], x2[s], G);
+        real U[NCONS], Bc[3], pr[NPR];
+        for (int m = 0; m < NCONS; m++) U[m] = U6[s * NCONS + m];
+        for (int m = 0; m < 3; m++) Bc[m] = Bc3[s * 3 + m];
+        for (int v = 0; v < NPR; v++) pr[v] = pr8[s * NPR + v];
+        pr[B1] = Bc[0];
+        pr[B2] = Bc[1];
+        pr[B3] = Bc[2];
+        int its = 0;
+        int st = con2prim(*d, U, Bc, G, pr, &its, entropy_only);
+        for (int v = 0; v < NPR; v++) pr8[s * NPR + v] = tod(pr[v]);
+        status[s] = st;
+        iters[s] = its;
+    }
+}
+
+void ora_p2u_many(const ora_desc* d, long n, const double* pr8, const double* x1, const double* x2,
+                  double* U6) {
+    for (long s = 0; s < n; s++) {
+        Geom G;
+        geom_point(*d, x1[s], x2[s], G);
+        real pr[NPR];
+        for (int v = 0; v < NPR; v++) pr[v] = pr8[s * NPR + v];
+        State st;
+        get_state(pr, G, st);
+        real o[9];
+        prim_to_uf(pr, st, 0, d->gam, o);
+        for (int m = 0; m < NCONS; m++) U6[s * NCONS + m] = tod(o[m] * G.gdet);
+    }
+}
+
+ora_grid* ora_grid_new(const ora_desc* d) {
+    ora_grid* g = new ora_grid;
+    g->d = *d;
+    g->n1p = d->n1 + 2 * NG;
+    g->n2p = d->n2 + 2 * NG;
+    g->n3p = d->n3 + 2 * NG;
+    g->ncell = (long)g->n1p * g->n2p * g->n3p;
+    g->prim.assign((size_t)NPR * g->ncell, 0.0);
+    g->bface.assign((size_t)3 * g->ncell, 0.0);
+    g->status.assign(g->ncell, 0);
+    for (int m = 0; m < 4; m++) g->stats[m] = 0;
+    build_geometry(g);
+    return g;
+}
+
+void ora_grid_free(ora_grid* g) { delete g; }
+
+void ora_grid_set(ora_grid* g, const double* prim, const double* bface) {
+    std::memcpy(g->prim.data(), prim, sizeof(double) * NPR * g->ncell);
+    std::memcpy(g->bface.data(), bface, sizeof(double) * 3 * g->ncell);
+    const long nc = g->ncell;
+    for (int k = 0; k < g->d.n3; k++)
+        for (int j = 0; j < g->d.n2; j++)
+            for (int i = 0; i < g->d.n1; i++) {
+                real Bc[3];
+                centre_b(g, g->bface.data(), i, j, k, Bc);
+                long c = cidx(g, i, j, k);
+                for (int m = 0; m < 3; m++) g->prim[(B1 + m) * nc + c] = tod(Bc[m]);
+            }
+    apply_bc(g, g->prim.data(), g->bface.data());
+}
+
+void ora_grid_get(const ora_grid* g, double* prim, double* bface) {
+    std::memcpy(prim, g->prim.data(), sizeof(double) * NPR * g->ncell);
+    std::memcpy(bface, g->bface.data(), sizeof(double) * 3 * g->ncell);
+}
+
+void ora_grid_bc(ora_grid* g) { apply_bc(g, g->prim.data(), g->bface.data()); }
+
+double ora_grid_dt(ora_grid* g) { return grid_dt(g); }
+
+/* One full midpoint step (Sec. 2.1): predictor to t + dt/2 with F(P^n),
+ * corrector from U^n to t + dt with F(P^{n+1/2}); boundaries refreshed before
+ * each stage. dt <= 0 takes the CFL step of the current state. */
+double ora_grid_step(ora_grid* g, double dt) {
+    for (int m = 0; m < 4; m++) g->stats[m] = 0;
+    std::fill(g->status.begin(), g->status.end(), 0);
+    apply_bc(g, g->prim.data(), g->bface.data());
+    if (!(dt > 0.0)) dt = grid_dt(g);
+    const size_t np = (size_t)NPR * g->ncell, nb = (size_t)3 * g->ncell;
+    std::vector<double> Ph(g->prim), Bh(g->bface), Pn(np), Bn(nb);
+    stage(g, g->prim.data(), g->bface.data(), g->prim.data(), g->bface.data(), 0.5 * dt, Ph.data(), Bh.data());
+    apply_bc(g, Ph.data(), Bh.data());
+    Pn = g->prim;
+    Bn = g->bface;
+    stage(g, Ph.data(), Bh.data(), g->prim.data(), g->bface.data(), dt, Pn.data(), Bn.data());
+    g->prim.swap(Pn);
+    g->bface.swap(Bn);
+    apply_bc(g, g->prim.data(), g->bface.data());
+    return dt;
+}
+
+void ora_grid_stats(const ora_grid* g, long long* counts4) {
+    for (int m = 0; m < 4; m++) counts4[m] = g->stats[m];
+}
+
+/* per interior cell: OR over both stages of the last step of
+ * 1 = entropy inversion used, 2 = both inversions failed, 4 = floor applied */
+void ora_grid_status(const ora_grid* g, int* out) {
+    const ora_desc& d = g->d;
+    long o = 0;
+    for (int k = 0; k < d.n3; k++)
+        for (int j = 0; j < d.n2; j++)
+            for (int i = 0; i < d.n1; i++) out[o++] = g->status[cidx(g, i, j, k)];
+}
+
+/* discrete div B per interior cell: sum_d (Bbar^d_hi - Bbar^d_lo)/dx^d */
+void ora_grid_divb(const ora_grid* g, double* divb) {
+    const ora_desc& d = g->d;
+    const long nc = g->ncell;
+    const double* B = g->bface.data();
+    long o = 0;
+    for (int k = 0; k < d.n3; k++)
+        for (int j = 0; j < d.n2; j++)
+            for (int i = 0; i < d.n1; i++) {
+                long c = cidx(g, i, j, k);
+                divb[o++] = (B[0 * nc + cidx(g, i + 1, j, k)] - B[0 * nc + c]) / d.dx1 +
+                            (B[1 * nc + cidx(g, i, j + 1, k)] - B[1 * nc + c]) / d.dx2 +
+                            (B[2 * nc + cidx(g, i, j, k + 1)] - B[2 * nc + c]) / d.dx3;
+            }
+}
+
+void ora_flops_reset(void) {
+#ifdef ORA_COUNT_FLOPS
+    for (int m = 0; m < 5; m++) ora_flop_ctr[m] = 0;
+#endif
+}
+
+void ora_flops_get(unsigned long long* out5) {
+    for (int m = 0; m < 5; m++) out5[m] = 0;
+#ifdef ORA_COUNT_FLOPS
+    for (int m = 0; m < 5; m++) out5[m] = ora_flop_ctr[m];
+#endif
+}
+
+} /* extern "C" */

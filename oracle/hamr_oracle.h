@@ -1,0 +1,82 @@
+/* hamr_oracle.h -- C interface of the plain FP64 CPU oracle.
+ *
+ * TEST INFRASTRUCTURE ONLY: only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline leg of bench.py may load this library. It shares no code with
+ * the CUDA path (paper_1912_10192_gb300/csrc) and neither includes the other.
+ *
+ * Layout used by every array argument of the grid functions ("padded"):
+ *   a cell field is [n3+6][n2+6][n1+6] doubles (3 ghost layers per side),
+ *   index ((k+3)*(n2+6) + (j+3))*(n1+6) + (i+3), i (x1 = log r) fastest.
+ *   Primitive arrays are 8 such fields: rho, u_g, utilde^1..3, B^1..3 (centre).
+ *   Face-B arrays are 3 such fields: Bbar^d stored at the lower d-face of the
+ *   cell with the same index (Bbar = sqrt(-g) B^d, the staggered CT field).
+ */
+#ifndef HAMR_ORACLE_H
+#define HAMR_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORA_BC_OUTFLOW = 0, ORA_BC_PERIODIC = 1, ORA_BC_POLAR = 2, ORA_BC_OUTFLOW_NOINFLOW = 3 };
+enum { ORA_METRIC_KS = 0, ORA_METRIC_MINKOWSKI = 1 };
+enum { ORA_RECON_PPM = 0, ORA_RECON_MC = 1, ORA_RECON_MINMOD = 2 };
+enum { ORA_FLUX_HLL = 0, ORA_FLUX_LLF = 1 };
+
+typedef struct {
+    int n1, n2, n3;                 /* interior cells per direction */
+    double x1min, x2min, x3min;     /* lower corner in internal coordinates */
+    double dx1, dx2, dx3;           /* uniform cell sizes */
+    int metric;                     /* ORA_METRIC_* */
+    double a;                       /* black-hole spin (KS) */
+    double gam;                     /* adiabatic index */
+    double cour;                    /* Courant factor C0 */
+    int recon;                      /* ORA_RECON_* */
+    int riemann;                    /* ORA_FLUX_* */
+    int bc[6];                      /* x1lo x1hi x2lo x2hi x3lo x3hi: ORA_BC_* */
+    int floors;                     /* 1: apply the density/energy floors */
+} ora_desc;
+
+/* ---- point-wise pieces (each documented in hamr_oracle.cpp) ---- */
+void ora_geom(const ora_desc* d, double x1, double x2, double* gcov16, double* gcon16,
+              double* gdet, double* alpha);
+void ora_conn(const ora_desc* d, double x1, double x2, double* conn64);
+void ora_state(const ora_desc* d, const double* pr8, double x1, double x2, double* ucon4,
+               double* ucov4, double* bcon4, double* bcov4, double* bsq);
+void ora_p2uf(const ora_desc* d, const double* pr8, double x1, double x2, int dir, double* out9);
+void ora_vchar(const ora_desc* d, const double* pr8, double x1, double x2, int dir, double* vp,
+               double* vm);
+void ora_face_flux(const ora_desc* d, const double* pl8, const double* pr8, double x1, double x2,
+                   int dir, double* f8);
+void ora_source(const ora_desc* d, const double* pr8, double x1, double x2, double* q6);
+void ora_recon_line(int recon, int n, const double* q, double* al, double* ar);
+/* con2prim on n independent states: U6 (sqrt(-g) weighted), B3 centre B^i,
+ * x1/x2 positions, pr8 in: guess, out: result; status/iters per state.
+ * entropy_only = 1 skips the energy inversion (tests of the backup path). */
+void ora_c2p_many(const ora_desc* d, long n, const double* U6, const double* B3,
+                  const double* x1, const double* x2, double* pr8, int* status, int* iters,
+                  int entropy_only);
+void ora_p2u_many(const ora_desc* d, long n, const double* pr8, const double* x1,
+                  const double* x2, double* U6);
+
+/* ---- single-block grid ---- */
+typedef struct ora_grid ora_grid;
+ora_grid* ora_grid_new(const ora_desc* d);
+void ora_grid_free(ora_grid* g);
+void ora_grid_set(ora_grid* g, const double* prim, const double* bface);
+void ora_grid_get(const ora_grid* g, double* prim, double* bface);
+void ora_grid_bc(ora_grid* g);
+double ora_grid_dt(ora_grid* g);
+double ora_grid_step(ora_grid* g, double dt);
+void ora_grid_stats(const ora_grid* g, long long* counts4);
+void ora_grid_divb(const ora_grid* g, double* divb_cells);
+void ora_grid_status(const ora_grid* g, int* status_cells);
+
+/* flop counters (meaningful only in the counting build) */
+void ora_flops_reset(void);
+void ora_flops_get(unsigned long long* out5);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

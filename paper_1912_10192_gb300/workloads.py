@@ -1,0 +1,266 @@
+"""Seeded synthetic inputs for the GRMHD block update (host-side numpy).
+
+This module generates initial states only; it holds none of the update's
+arithmetic and imports neither the CUDA binding nor the CPU oracle, so both
+sides can be fed the same bytes.
+
+* `torus_block`: Fishbone & Moncrief (1976) torus around a Kerr black hole in
+  Kerr-Schild coordinates on the log-r spherical grid of Sec. 2.2, with a
+  poloidal loop field (A_phi ~ max(rho/rho_max - 0.2, 0) at cell corners,
+  face B as its discrete curl) normalised to max p_g / max p_b = beta (the
+  same "ratio of maxima" definition the paper uses in Sec. 6.3), and a seeded
+  +/- 2% perturbation of u_g inside the torus.
+* `random_states`: random primitive states for inversion tests over the
+  ranges rho 1e-6..1, u/rho 1e-4..1e2, Lorentz factor 1..50,
+  sigma = b^2/rho 0..100, r from just inside the horizon to 100.
+
+Random numbers come from SplitMix64 (Steele, Lea & Flood 2014) of
+seed XOR global cell id, mapped to [0, 1) with the top 53 bits.
+"""
+import math
+
+import numpy as np
+
+NG = 3
+
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(x):
+    """SplitMix64 finaliser of a uint64 array (wrapping arithmetic)."""
+    with np.errstate(over="ignore"):
+        z = (np.asarray(x, dtype=np.uint64) + np.uint64(0x9E3779B97F4A7C15)) & _M64
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & _M64
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & _M64
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform01(seed, ids):
+    """xi in [0, 1) for each integer id, from SplitMix64(seed ^ id)."""
+    z = splitmix64(np.uint64(seed) ^ np.asarray(ids, dtype=np.uint64))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+class BlockGeometry:
+    """Extents of one block in internal coordinates (x1 = log r, x2 = theta, x3 = phi)."""
+
+    def __init__(self, n1, n2, n3, x1min, x1max, x2min, x2max, x3min, x3max):
+        self.n1, self.n2, self.n3 = n1, n2, n3
+        self.x1min, self.x2min, self.x3min = x1min, x2min, x3min
+        self.dx1 = (x1max - x1min) / n1
+        self.dx2 = (x2max - x2min) / n2
+        self.dx3 = (x3max - x3min) / n3
+
+    @property
+    def padded_shape(self):
+        return (self.n3 + 2 * NG, self.n2 + 2 * NG, self.n1 + 2 * NG)
+
+
+def torus_geometry(n1, n2, n3, rin=1.2, rout=50.0):
+    return BlockGeometry(n1, n2, n3, math.log(rin), math.log(rout), 0.0, math.pi, 0.0, 2.0 * math.pi)
+
+
+# --- Kerr-Schild pieces needed to express the initial state -----------------
+
+def _ks_internal(a, r, th):
+    """Non-zero covariant/contravariant KS components in (t, log r, theta, phi)."""
+    s2 = np.sin(th) ** 2
+    sig = r * r + a * a * np.cos(th) ** 2
+    z = 2.0 * r / sig
+    gcov = {
+        (0, 0): -(1.0 - z), (0, 1): z * r, (0, 3): -z * a * s2, (1, 1): (1.0 + z) * r * r,
+        (1, 3): -a * s2 * (1.0 + z) * r, (2, 2): sig, (3, 3): s2 * (sig + a * a * s2 * (1.0 + z)),
+    }
+    for (m, n) in list(gcov):
+        if m != n:
+            gcov[(n, m)] = gcov[(m, n)]
+    gtt_con = -(1.0 + z)
+    gt1_con = z / r
+    gdet = r * sig * np.sin(th)
+    return gcov, gtt_con, gt1_con, gdet
+
+
+def _fm_lnh(a, r, th, ell):
+    """Fishbone-Moncrief log-enthalpy (constant u^t u_phi = ell) in BL, up to a constant."""
+    s2 = np.sin(th) ** 2
+    sig = r * r + a * a * np.cos(th) ** 2
+    dlt = r * r - 2.0 * r + a * a
+    A = (r * r + a * a) ** 2 - dlt * a * a * s2
+    q = np.sqrt(1.0 + 4.0 * ell * ell * sig * sig * dlt / (A * A * s2))
+    return 0.5 * np.log((1.0 + q) / (sig * dlt / A)) - 0.5 * q - 2.0 * a * r * ell / A
+
+
+def fm_ell(a, rmax):
+    """u^t u_phi of the prograde circular equatorial geodesic at rmax (pressure maximum)."""
+    sr = math.sqrt(rmax)
+    return ((rmax ** 1.5 + a) * (rmax * rmax - 2.0 * a * sr + a * a)
+            / (rmax ** 1.5 * (rmax ** 1.5 - 3.0 * sr + 2.0 * a)))
+
+
+def _fm_velocity_bl(a, r, th, ell):
+    """(u^t, u^phi) in Boyer-Lindquist for the FM torus."""
+    s2 = np.sin(th) ** 2
+    sig = r * r + a * a * np.cos(th) ** 2
+    dlt = r * r - 2.0 * r + a * a
+    A = (r * r + a * a) ** 2 - dlt * a * a * s2
+    gtt = -A / (sig * dlt)
+    gtp = -2.0 * a * r / (sig * dlt)
+    gpp = (dlt - a * a * s2) / (sig * dlt * s2)
+    K = gtp * gtp - gtt * gpp
+    uphi_cov = np.sqrt((gtt + np.sqrt(gtt * gtt + 4.0 * K * ell * ell)) / (2.0 * K))
+    ut_cov = (ell - gtp * uphi_cov ** 2) / (gtt * uphi_cov)
+    ut = gtt * ut_cov + gtp * uphi_cov
+    uphi = gtp * ut_cov + gpp * uphi_cov
+    return ut, uphi
+
+
+def _bsq(a, r, th, prim_u, Bcon):
+    """b^2 for utilde^i = prim_u[0..2] and centre B^i = Bcon[0..2] (broadcast arrays)."""
+    gcov, gtt_con, gt1_con, _ = _ks_internal(a, r, th)
+    alpha = 1.0 / np.sqrt(-gtt_con)
+    qsq = sum(gcov[(i + 1, j + 1)] * prim_u[i] * prim_u[j]
+              for i in range(3) for j in range(3) if (i + 1, j + 1) in gcov)
+    gamma = np.sqrt(1.0 + qsq)
+    ucon = [gamma / alpha, prim_u[0] - gamma * alpha * gt1_con, prim_u[1], prim_u[2]]
+    ucov = [sum(gcov[(m, n)] * ucon[n] for n in range(4) if (m, n) in gcov) for m in range(4)]
+    bt = sum(Bcon[i] * ucov[i + 1] for i in range(3))
+    bcon = [bt] + [(Bcon[i] + bt * ucon[i + 1]) / ucon[0] for i in range(3)]
+    return sum(gcov[(m, n)] * bcon[m] * bcon[n] for m in range(4) for n in range(4) if (m, n) in gcov)
+
+
+def torus_block(geo, a=0.9375, gam=13.0 / 9.0, rin=6.0, rmax=12.0, beta=100.0, pert=0.02, seed=1912,
+                kappa=1.0e-3):
+    """Padded primitive (8, n3p, n2p, n1p) and face-B (3, ...) arrays of the magnetised FM torus.
+
+    Ghost zones are left at zero: each side fills them with its own boundary
+    conditions. Centre B^i (prim slots 5..7) is left at zero too: it is a
+    function of the face field, computed by each side.
+    """
+    n1, n2, n3 = geo.n1, geo.n2, geo.n3
+    shp = geo.padded_shape
+    prim = np.zeros((8,) + shp)
+    bface = np.zeros((3,) + shp)
+    ell = fm_ell(a, rmax)
+    lnh_in = _fm_lnh(a, rin, 0.5 * math.pi, ell)
+
+    i = np.arange(n1)
+    j = np.arange(n2)
+    x1 = geo.x1min + (i + 0.5) * geo.dx1
+    x2 = geo.x2min + (j + 0.5) * geo.dx2
+    R, TH = np.meshgrid(np.exp(x1), x2, indexing="xy")  # (n2, n1)
+    rplus = 1.0 + math.sqrt(1.0 - a * a)
+
+    def torus_rho_u(r, th):
+        with np.errstate(invalid="ignore", divide="ignore"):
+            lnh = np.where(r > rplus * 1.0001, _fm_lnh(a, r, th, ell) - lnh_in, -1.0)
+        inside = (r >= rin) & (lnh > 0.0)
+        hm1 = np.where(inside, np.exp(np.where(inside, lnh, 0.0)) - 1.0, 0.0)
+        rho = np.where(inside, (hm1 * (gam - 1.0) / (kappa * gam)) ** (1.0 / (gam - 1.0)), 0.0)
+        u = kappa * rho ** gam / (gam - 1.0)
+        return rho, u, inside
+
+    rho_t, u_t, inside = torus_rho_u(R, TH)
+    rhomax = rho_t.max()
+    rho_t /= rhomax
+    u_t /= rhomax
+
+    # velocities (Kerr-Schild, internal coordinates)
+    ut_bl, uphi_bl = _fm_velocity_bl(a, np.where(inside, R, 20.0), np.where(inside, TH, 1.5), ell)
+    gcov, gtt_con, gt1_con, _ = _ks_internal(a, R, TH)
+    alpha = 1.0 / np.sqrt(-gtt_con)
+    gamma_n = alpha * ut_bl  # u^t_KS = u^t_BL when u^r = 0
+    ut1 = np.where(inside, gamma_n * alpha * gt1_con, 0.0)
+    ut3 = np.where(inside, uphi_bl, 0.0)
+
+    rho_flr = 1.0e-7 / R ** 2
+    u_flr = 1.0e-9 * R ** (-10.0 / 3.0)
+    rho = np.maximum(rho_t, rho_flr)
+    u = np.maximum(u_t, u_flr)
+
+    # perturbation inside the torus, keyed by the global (block-local here) cell id
+    kk, jj, ii = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+    ids = (ii + n1 * (jj + n2 * kk)).astype(np.uint64)
+    xi = uniform01(seed, ids)
+    u3 = np.broadcast_to(u, (n3, n2, n1)).copy()
+    u3 = np.where(np.broadcast_to(inside, (n3, n2, n1)), u3 * (1.0 + pert * (2.0 * xi - 1.0)), u3)
+
+    s = (slice(None), slice(NG, NG + n2), slice(NG, NG + n1))
+    sk = (slice(NG, NG + n3), slice(NG, NG + n2), slice(NG, NG + n1))
+    prim[0][s] = rho
+    prim[1][sk] = u3
+    prim[2][s] = ut1
+    prim[3][s] = 0.0
+    prim[4][s] = ut3
+
+    # loop field: A_phi at cell corners (i-1/2, j-1/2)
+    xc1 = geo.x1min + np.arange(n1 + 1) * geo.dx1
+    xc2 = geo.x2min + np.arange(n2 + 1) * geo.dx2
+    RC, THC = np.meshgrid(np.exp(xc1), xc2, indexing="xy")  # (n2+1, n1+1)
+    rho_c, _, _ = torus_rho_u(RC, THC)
+    Aphi = np.maximum(rho_c / rhomax - 0.2, 0.0)
+    b1 = (Aphi[1:, :] - Aphi[:-1, :]) / geo.dx2        # (n2, n1+1): faces i = 0..n1
+    b2 = -(Aphi[:, 1:] - Aphi[:, :-1]) / geo.dx1       # (n2+1, n1): faces j = 0..n2
+    # axis faces carry no flux area
+    b2[0, :] = 0.0 if geo.x2min == 0.0 else b2[0, :]
+    if abs(geo.x2min + n2 * geo.dx2 - math.pi) < 1e-12:
+        b2[-1, :] = 0.0
+
+    # normalise to beta = max p_g / max p_b using centre B = <Bbar>/sqrt(-g)
+    _, _, _, gdet = _ks_internal(a, R, TH)
+    Bc1 = 0.5 * (b1[:, :-1] + b1[:, 1:]) / gdet
+    Bc2 = 0.5 * (b2[:-1, :] + b2[1:, :]) / gdet
+    bsq = _bsq(a, R, TH, (ut1, np.zeros_like(ut1), ut3), (Bc1, Bc2, np.zeros_like(Bc1)))
+    pg_max = ((gam - 1.0) * u3).max()
+    pb_max = 0.5 * bsq.max()
+    if pb_max > 0.0 and beta > 0.0:
+        fac = math.sqrt(pg_max / (beta * pb_max))
+    else:
+        fac = 0.0
+    for k in range(n3):
+        bface[0, NG + k, NG:NG + n2, NG:NG + n1 + 1] = fac * b1
+        bface[1, NG + k, NG:NG + n2 + 1, NG:NG + n1] = fac * b2
+    return prim, bface
+
+
+def random_states(n, seed, a=0.9375, rho_range=(1e-6, 1.0), urho_range=(1e-4, 1e2), lorentz_range=(1.0, 50.0),
+                  sigma_range=(0.0, 100.0), rmax=100.0):
+    """Random primitive states and positions for inversion tests.
+
+    Returns prim (n, 8) with centre B^i in slots 5..7, and x1 = log r, x2 = theta.
+    Directions of utilde^i and B^i are isotropic in the local coordinate basis
+    normalised by g_ij.
+    """
+    ids = np.arange(n, dtype=np.uint64) * np.uint64(16)
+    xi = [uniform01(seed, ids + np.uint64(m)) for m in range(12)]
+    rplus = 1.0 + math.sqrt(1.0 - a * a)
+    r = np.exp(math.log(0.9 * rplus) + xi[0] * (math.log(rmax) - math.log(0.9 * rplus)))
+    cth = 2.0 * xi[1] - 1.0
+    cth = np.clip(cth, -math.sqrt(1.0 - 1e-6), math.sqrt(1.0 - 1e-6))
+    th = np.arccos(cth)
+    rho = np.exp(np.log(rho_range[0]) + xi[2] * (np.log(rho_range[1]) - np.log(rho_range[0])))
+    u = rho * np.exp(np.log(urho_range[0]) + xi[3] * (np.log(urho_range[1]) - np.log(urho_range[0])))
+    lor = np.exp(np.log(lorentz_range[0]) + xi[4] * (np.log(lorentz_range[1]) - np.log(lorentz_range[0])))
+    sigma = sigma_range[0] + xi[5] * (sigma_range[1] - sigma_range[0])
+
+    def iso(x, y):
+        z = 2.0 * x - 1.0
+        ph = 2.0 * math.pi * y
+        s = np.sqrt(1.0 - z * z)
+        return np.stack([s * np.cos(ph), s * np.sin(ph), z])
+
+    gcov, _, _, _ = _ks_internal(a, r, th)
+
+    def gnorm(v):
+        return np.sqrt(sum(gcov[(i + 1, j + 1)] * v[i] * v[j]
+                           for i in range(3) for j in range(3) if (i + 1, j + 1) in gcov))
+
+    nu = iso(xi[6], xi[7])
+    nu = nu / gnorm(nu)
+    utl = np.sqrt(lor * lor - 1.0) * nu
+    nb = iso(xi[8], xi[9])
+    nb = nb / gnorm(nb)
+    b2unit = _bsq(a, r, th, utl, nb)
+    scale = np.sqrt(sigma * rho / b2unit)
+    B = nb * scale
+    prim = np.stack([rho, u, utl[0], utl[1], utl[2], B[0], B[1], B[2]], axis=1)
+    return prim, np.log(r), th

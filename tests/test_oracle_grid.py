@@ -1,0 +1,237 @@
+"""Grid-level pins of the oracle's step (Sec. 2.1, 2.5): constrained transport,
+conservation, free streaming, convergence order, advection and equilibrium."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1912_10192_gb300 import workloads as W
+
+NG = O.NG
+GAM = 13.0 / 9.0
+
+
+def torus_desc(n1, n2, n3, recon=O.RECON_PPM):
+    geo = W.torus_geometry(n1, n2, n3)
+    d = O.make_desc(n1, n2, n3, geo.x1min, geo.x2min, geo.x3min, geo.dx1, geo.dx2, geo.dx3,
+                    metric=O.METRIC_KS, a=0.9375, gam=GAM, cour=0.8, recon=recon,
+                    bc=(O.BC_OUTFLOW_NOINFLOW, O.BC_OUTFLOW_NOINFLOW, O.BC_POLAR, O.BC_POLAR,
+                        O.BC_PERIODIC, O.BC_PERIODIC))
+    return geo, d
+
+
+def flat_desc(n1, n2, n3, L=(1.0, 1.0, 1.0), gam=GAM, recon=O.RECON_PPM, cour=0.8):
+    return O.make_desc(n1, n2, n3, 0.0, 0.0, 0.0, L[0] / n1, L[1] / n2, L[2] / n3,
+                       metric=O.METRIC_MINKOWSKI, gam=gam, cour=cour, recon=recon,
+                       bc=(O.BC_PERIODIC,) * 6, floors=0)
+
+
+def interior(a, d):
+    return a[..., NG:NG + d.n3, NG:NG + d.n2, NG:NG + d.n1]
+
+
+def test_ct_keeps_div_b_at_roundoff_on_torus():
+    geo, d = torus_desc(32, 16, 8)
+    prim, bf = W.torus_block(geo, seed=1912)
+    g = O.Grid(d)
+    g.set(prim, bf)
+    scale = np.abs(bf).max() / min(d.dx1, d.dx2, d.dx3)
+    assert np.abs(g.divb()).max() < 1e-14 * scale
+    for _ in range(4):
+        g.step()
+    assert np.abs(g.divb()).max() < 1e-13 * scale
+
+
+def _flat_random_state(d, seed, amp=0.1):
+    rng = np.random.default_rng(seed)
+    shp = (d.n3 + 2 * NG, d.n2 + 2 * NG, d.n1 + 2 * NG)
+    prim = np.zeros((8,) + shp)
+    bf = np.zeros((3,) + shp)
+    x = (np.arange(d.n1) + 0.5) * d.dx1
+    y = (np.arange(d.n2) + 0.5) * d.dx2
+    z = (np.arange(d.n3) + 0.5) * d.dx3
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    tp = 2 * math.pi
+    s = (slice(NG, NG + d.n3), slice(NG, NG + d.n2), slice(NG, NG + d.n1))
+    prim[0][s] = 1.0 + amp * np.sin(tp * X + 1) * np.cos(tp * Y)
+    prim[1][s] = 1.0 + amp * np.cos(tp * Z + 2 * tp * X)
+    prim[2][s] = 0.3 + amp * np.sin(tp * Y)
+    prim[3][s] = -0.2 + amp * np.sin(tp * (X + Z))
+    prim[4][s] = 0.1 + amp * np.cos(tp * X)
+    # face B as the discrete curl of a periodic edge vector potential A = (A1(y,z), 0, A3(x,y))
+    xf = np.arange(d.n1) * d.dx1
+    yf = np.arange(d.n2) * d.dx2
+    zf = np.arange(d.n3) * d.dx3
+    YF, XF = np.meshgrid(yf, xf, indexing="ij")
+    a3 = 0.05 * np.sin(tp * XF) * np.sin(tp * YF) / tp          # edges (i-1/2, j-1/2), [j, i]
+    ZF, YF2 = np.meshgrid(zf, yf, indexing="ij")
+    a1 = 0.05 * np.cos(tp * YF2 + tp * ZF) / tp                # edges (j-1/2, k-1/2), [k, j]
+    b1 = (np.roll(a3, -1, axis=0) - a3) / d.dx2                 # [j, i]
+    b2 = ((np.roll(a1, -1, axis=0) - a1) / d.dx3)[:, :, None] - ((np.roll(a3, -1, axis=1) - a3) / d.dx1)[None]
+    b3 = -(np.roll(a1, -1, axis=1) - a1) / d.dx2                # [k, j]
+    bf[0][s] = np.broadcast_to(b1[None], (d.n3, d.n2, d.n1))
+    bf[1][s] = b2
+    bf[2][s] = np.broadcast_to(b3[:, :, None], (d.n3, d.n2, d.n1))
+    return prim, bf
+
+
+def _total_U(d, prim):
+    p = interior(prim, d).reshape(8, -1).T
+    n = p.shape[0]
+    U = O.p2u_many(d, p, np.zeros(n), np.zeros(n))
+    return U.sum(axis=0)
+
+
+def test_flat_periodic_box_conserves_and_keeps_div_b():
+    d = flat_desc(16, 12, 8)
+    prim, bf = _flat_random_state(d, 1)
+    g = O.Grid(d)
+    g.set(prim, bf)
+    assert np.abs(g.divb()).max() < 1e-12
+    p0, _ = g.get()
+    U0 = _total_U(d, p0)
+    for _ in range(5):
+        g.step()
+    p1, _ = g.get()
+    U1 = _total_U(d, p1)
+    assert g.stats()[1:3] == [0, 0]
+    # mass, energy, momenta: conserved to round-off (the inversion adds ~1e-14 per cell)
+    for m in range(5):
+        assert abs(U1[m] - U0[m]) < 1e-12 * np.abs(U0[:5]).max()
+    assert np.abs(g.divb()).max() < 1e-12
+
+
+def test_free_streaming_uniform_state():
+    d = flat_desc(8, 8, 8)
+    shp = (d.n3 + 2 * NG, d.n2 + 2 * NG, d.n1 + 2 * NG)
+    prim = np.zeros((8,) + shp)
+    bf = np.zeros((3,) + shp)
+    vals = [1.3, 0.7, 0.4, -0.3, 0.2]
+    for v, x in enumerate(vals):
+        prim[v][...] = x
+    bf[0][...], bf[1][...], bf[2][...] = 0.2, -0.1, 0.3
+    g = O.Grid(d)
+    g.set(prim, bf)
+    for _ in range(3):
+        g.step()
+    p, b = g.get()
+    for v, x in enumerate(vals):
+        assert np.abs(interior(p[v], d) - x).max() < 1e-13 * max(1, abs(x))
+    assert np.abs(interior(b[0], d) - 0.2).max() < 1e-15
+
+
+def _sound_wave_error(n, recon):
+    gam = 5.0 / 3.0
+    d = flat_desc(n, 1, 1, L=(1.0, 1.0 / n, 1.0 / n), gam=gam, recon=recon, cour=0.5)
+    rho0, u0, A = 1.0, 1.0, 1e-5
+    p0 = (gam - 1) * u0
+    w0 = rho0 + u0 + p0
+    cs = math.sqrt(gam * p0 / w0)
+    x = (np.arange(n) + 0.5) / n
+    shp = (d.n3 + 2 * NG, d.n2 + 2 * NG, d.n1 + 2 * NG)
+    prim = np.zeros((8,) + shp)
+    bf = np.zeros((3,) + shp)
+    # cell averages of the right-going eigenmode: drho = A rho0 cos, de = (w0/rho0) drho, v = cs drho/rho0
+    ca = (np.sin(2 * math.pi * (x + 0.5 / n)) - np.sin(2 * math.pi * (x - 0.5 / n))) * n / (2 * math.pi)
+    drho = A * rho0 * ca
+    prim[0][NG, NG, NG:NG + n] = rho0 + drho
+    prim[1][NG, NG, NG:NG + n] = u0 + (w0 / rho0 - 1.0) * drho
+    prim[2][NG, NG, NG:NG + n] = cs * drho / rho0
+    init = prim[0][NG, NG, NG:NG + n].copy()
+    g = O.Grid(d)
+    g.set(prim, bf)
+    T = 1.0 / cs
+    t = 0.0
+    while t < T - 1e-14:
+        dt = min(g.dt(), T - t)
+        g.step(dt)
+        t += dt
+    p, _ = g.get()
+    return np.abs(p[0][NG, NG, NG:NG + n] - init).mean()
+
+
+@pytest.mark.parametrize("recon", [O.RECON_PPM, O.RECON_MC])
+def test_linear_sound_wave_converges_at_second_order(recon):
+    """Sec. 6.1: linear waves converge at 2nd order (one period, flat space)."""
+    e = [_sound_wave_error(n, recon) for n in (32, 64, 128)]
+    rates = [math.log2(e[0] / e[1]), math.log2(e[1] / e[2])]
+    assert min(rates) > 1.7, (e, rates)
+
+
+def test_weak_field_is_advected_downstream():
+    """A passive transverse field in a uniform flow moves with the flow: checks the sign of
+    the induction flux F^j(B^i) = b^i u^j - b^j u^i together with the CT update."""
+    n = 64
+    d = flat_desc(n, 1, 1, L=(1.0, 1.0 / n, 1.0 / n), recon=O.RECON_PPM, cour=0.5)
+    shp = (d.n3 + 2 * NG, d.n2 + 2 * NG, d.n1 + 2 * NG)
+    prim = np.zeros((8,) + shp)
+    bf = np.zeros((3,) + shp)
+    v = 0.5
+    Wl = 1 / math.sqrt(1 - v * v)
+    prim[0][...] = 1.0
+    prim[1][...] = 1.0
+    prim[2][...] = Wl * v
+    x = (np.arange(n) + 0.5) / n
+    By = 1e-4 * np.exp(-((x - 0.3) / 0.08) ** 2)
+    bf[1][NG, NG:NG + 2, NG:NG + n] = By  # x2-faces (uniform in y)
+    g = O.Grid(d)
+    g.set(prim, bf)
+    T = 0.4 / v
+    t = 0.0
+    while t < T - 1e-14:
+        dt = min(g.dt(), T - t)
+        g.step(dt)
+        t += dt
+    _, b = g.get()
+    prof = b[1][NG, NG, NG:NG + n]
+    centre = (prof * x).sum() / prof.sum()
+    assert abs(centre - 0.7) < 0.01, centre
+
+
+def test_torus_hydrostatic_balance_converges():
+    """The FM torus is an exact equilibrium: div F - Q of the exact state, with the
+    oracle's fluxes, sources and metric, vanishes at 2nd order in the spacing."""
+    a, gam = 0.9375, GAM
+    d = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, metric=O.METRIC_KS, a=a, gam=gam)
+    ell = W.fm_ell(a, 12.0)
+    lnh_in = W._fm_lnh(a, 6.0, math.pi / 2, ell)
+    kappa = 1e-3
+
+    def prim_at(x1, x2):
+        r, th = math.exp(x1), x2
+        h = math.exp(W._fm_lnh(a, r, th, ell) - lnh_in)
+        rho = ((h - 1) * (gam - 1) / (kappa * gam)) ** (1 / (gam - 1))
+        u = kappa * rho ** gam / (gam - 1)
+        ut, up = W._fm_velocity_bl(a, np.array(r), np.array(th), ell)
+        _, gtt, gt1, _ = W._ks_internal(a, np.array(r), np.array(th))
+        al = 1 / math.sqrt(-gtt)
+        return np.array([rho, u, float(al * ut * al * gt1), 0.0, float(up), 0, 0, 0])
+
+    for (x1, x2) in [(math.log(12.0), 1.5), (math.log(9.0), 1.3)]:
+        res = []
+        for h in (1e-2, 5e-3):
+            div = np.zeros(9)
+            for dr, (o1, o2) in ((1, (h, 0)), (2, (0, h))):
+                Fp = O.p2uf(d, prim_at(x1 + o1 / 2, x2 + o2 / 2), x1 + o1 / 2, x2 + o2 / 2, dr)
+                Fm = O.p2uf(d, prim_at(x1 - o1 / 2, x2 - o2 / 2), x1 - o1 / 2, x2 - o2 / 2, dr)
+                div += (Fp - Fm) / h
+            Q = O.source(d, prim_at(x1, x2), x1, x2)
+            res.append(np.abs(div[1:5] - Q[1:5]).max() / np.abs(Q[1:5]).max())
+        assert res[0] < 1e-3 and 3.5 < res[0] / res[1] < 4.5, res
+
+
+def test_torus_step_runs_and_uses_documented_fallbacks():
+    geo, d = torus_desc(32, 16, 8)
+    prim, bf = W.torus_block(geo, seed=1912)
+    g = O.Grid(d)
+    g.set(prim, bf)
+    dt0 = g.dt()
+    assert 0.0 < dt0 < 1.0
+    for _ in range(2):
+        g.step()
+    p, b = g.get()
+    assert np.isfinite(p).all() and np.isfinite(b).all()
+    st = g.stats()
+    ncell = 2 * d.n1 * d.n2 * d.n3
+    assert st[0] > 0.85 * ncell and st[2] < 0.02 * ncell
