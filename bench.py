@@ -1,0 +1,305 @@
+#!/usr/bin/env python
+"""Benchmark of the GRMHD block update on GB300: zone-cycles per second.
+
+Workload (default): one 256 x 128 x 64 block of the magnetised Fishbone-Moncrief
+torus (Kerr-Schild a = 0.9375, r = 1.2..50 r_g log-spaced, theta 0..pi,
+phi 0..2pi, Gamma = 13/9, loop field with max p_g / max p_b = 100, 2% seeded
+u_g perturbation, seed 10192), FP64, PPM + HLL + CT + Newton inversion,
+midpoint step at the CFL time step (C0 = 0.8). A zone-cycle is one cell
+advanced one full step, predictor plus corrector (the paper's Sec. 5.3
+definition). The state (~1.4 GB with scratch) is far larger than the 129 MB
+L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own copy of the block (the
+single block does not shard; replicas, weak scaling); value = all ranks'
+zone-cycles / the slowest rank's time. `--impl reference` times the CPU
+oracle (the plain FP64 implementation the CUDA path is checked against) on
+the host cores, rank 0 only.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N1, N2, N3 = 256, 128, 64
+SEED = 10192
+METRIC = "zone-cycles/sec on 1 GB300 (plain FP64 vs chosen form at stated L1 error), % HBM roofline"
+WORKLOAD = "FM torus block 256x128x64, Kerr-Schild a=0.9375, r 1.2-50, loop field beta=100, seed 10192, FP64"
+
+# Algorithmic FP64 operations per unit of work, from the flop-counting CPU
+# oracle on the 64x32x16 torus (tests/golden/make_flop_counts.py writes them;
+# tests/test_bench_constants.py checks these copies against it).
+FLOPS_PER_FACE = 325.9           # one HLL face flux from given edge states
+FLOPS_PER_RECON_CELL = 90.16     # one cell's edge values, one direction
+FLOPS_PER_UPDATE_CELL = 694.5    # one cell: U, div F, source, inversion, floors (per stage)
+FLOPS_PER_ZONE_CYCLE = 4549.7    # one cell, one full step
+# Peaks. FP64: nominal GB300 rate (the profiling recipe's 1.25 TFLOP/s); the
+# FMA rate measured by hamr_measure_fp64_peak is reported beside it.
+FP64_NOMINAL_TFLOPS = 1.25
+# DRAM bytes per launch of the dominant kernel from one ncu capture of this
+# build (profiles/flux_torus256.md); None until captured for this build.
+NCU_TRAFFIC_PER_LAUNCH = None
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def torus_inputs(n1=N1, n2=N2, n3=N3, seed=SEED):
+    from paper_1912_10192_gb300 import workloads as W
+    geo = W.torus_geometry(n1, n2, n3)
+    prim, bf = W.torus_block(geo, seed=seed)
+    return geo, prim, bf
+
+
+TORUS_BC = (3, 3, 2, 2, 1, 1)  # no-inflow radial, polar axis, periodic phi
+
+
+def cpu_oracle_rate(n1, n2, n3, steps, warmup, seed=SEED):
+    """Oracle zone-cycles/s on a torus block (single thread)."""
+    import oracle as O
+    geo, prim, bf = torus_inputs(n1, n2, n3, seed)
+    d = O.make_desc(n1, n2, n3, geo.x1min, geo.x2min, geo.x3min, geo.dx1, geo.dx2, geo.dx3, metric=O.METRIC_KS,
+                    a=0.9375, gam=13.0 / 9.0, cour=0.8, bc=TORUS_BC)
+    g = O.Grid(d)
+    g.set(prim, bf)
+    for _ in range(warmup):
+        g.step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        g.step()
+    t = time.perf_counter() - t0
+    return n1 * n2 * n3 * steps / t, t
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    n1, n2, n3 = 64, 32, 16
+    rate, t = cpu_oracle_rate(n1, n2, n3, args.steps, args.warmup)
+    sample = ("CPU oracle (plain FP64 C++, 1 thread), torus block %dx%dx%d (the benchmark's setup at 1/64 of "
+              "its cells), %d timed steps after %d warm-up" % (n1, n2, n3, args.steps, args.warmup))
+    line = {"metric": METRIC, "value": rate, "unit": "zone-cycles/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "%dx%dx%d" % (n1, n2, n3)}, "impl": "reference",
+            "cpu_baseline": {"value": rate, "unit": "zone-cycles/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": "zone-cycles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_1912_10192_gb300 import _build, hamr
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        _build.build()
+    if dist:
+        dist.barrier()
+    geo, prim, bf = torus_inputs()
+    blk = hamr.block(N1, N2, N3, geo.x1min, geo.x2min, geo.x3min, geo.dx1, geo.dx2, geo.dx3, TORUS_BC)
+    g = hamr.Grid([blk])
+    dprim = torch.from_numpy(prim).cuda()
+    dbf = torch.from_numpy(bf).cuda()
+    stream = torch.cuda.current_stream()
+    g.set_state(dprim, dbf, stream=stream)
+    cells = N1 * N2 * N3
+    for _ in range(args.warmup):
+        g.step(stream=stream)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, device events on the launching stream
+    g.set_timing(True)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        g.step(stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        dist.barrier()
+    timing = g.timing()
+    g.set_timing(False)
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    stats = g.stats()
+    value = cells * args.steps * world / (ms_max * 1e-3)
+
+    # ---- end to end: host buffers through the C ABI, copies inside the timed region
+    e2e_steps = min(args.steps, 10)
+    hp = torch.from_numpy(prim).pin_memory().numpy()
+    hb = torch.from_numpy(bf).pin_memory().numpy()
+    op = torch.empty(prim.shape, dtype=torch.float64).pin_memory().numpy()
+    ob = torch.empty(bf.shape, dtype=torch.float64).pin_memory().numpy()
+    g2 = hamr.Grid([blk])
+    g2.set_state(hp, hb)
+    g2.step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g2.set_state(hp, hb)
+        g2.step()
+        g2.get_state(prim=op, bface=ob)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    te_t = torch.tensor([te], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
+    e2e = {"value": cells * e2e_steps * world / float(te_t.item()), "unit": "zone-cycles/s",
+           "h2d_bytes_per_step": int(hp.nbytes + hb.nbytes), "d2h_bytes_per_step": int(op.nbytes + ob.nbytes),
+           "steps": e2e_steps,
+           "path": "hamr_grid_set_state(host, pinned) + hamr_block_step + hamr_grid_get_state(host) per step"}
+    g2.close()
+
+    # ---- roofline of the dominant kernel group (FP64 pipe bound)
+    fp64_meas = hamr.measure_fp64_peak() / 1e3  # TFLOP/s
+    dom = max(((k, v) for k, v in timing.items() if k != "load"), key=lambda kv: kv[1][1])
+    name, (launches, dom_ms) = dom
+    steps = args.steps
+    faces = ((N1 + 1) * (N2 + 2) * (N3 + 2) + (N1 + 2) * (N2 + 1) * (N3 + 2) + (N1 + 2) * (N2 + 2) * (N3 + 1))
+    per_step_units = {"flux": FLOPS_PER_FACE * faces * 2,
+                      "recon": FLOPS_PER_RECON_CELL * 3 * (N1 + 2) * (N2 + 2) * (N3 + 2) * 2,
+                      "update": FLOPS_PER_UPDATE_CELL * cells * 2}
+    roofline = None
+    if name in per_step_units:
+        flops_per_launch = per_step_units[name] * steps / launches
+        avg_s = dom_ms * 1e-3 / launches
+        achieved = flops_per_launch / avg_s / 1e12
+        roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
+                    "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (profiling recipe)",
+                    "measured_fp64_fma_tflops": fp64_meas, "frac_of_measured": achieved / fp64_meas,
+                    "traffic": NCU_TRAFFIC_PER_LAUNCH, "avg_launch_ms": dom_ms / launches,
+                    "share_of_step": dom_ms / ms}
+    whole = FLOPS_PER_ZONE_CYCLE * cells * args.steps / (ms * 1e-3) / 1e12
+    launches_total = sum(v[0] for k, v in timing.items() if k != "load")
+
+    line = {"metric": METRIC, "value": value, "unit": "zone-cycles/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells_per_gpu": cells, "dt": "CFL (C0=0.8), reduced on device",
+                       "l2": "state and scratch ~1.4 GB per GPU >> 129 MB L2 (no flush needed)",
+                       "parallelism": "replicas" if world > 1 else "single block"},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches_total), "roofline": roofline,
+            "step_fp64_tflops": whole, "step_fp64_frac_nominal": whole / FP64_NOMINAL_TFLOPS,
+            "kernel_ms": {k: round(v[1], 3) for k, v in timing.items()},
+            "c2p": {k: stats[k] for k in ("c2p_ok", "c2p_entropy", "c2p_fail", "floor_hits")}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, t = cpu_oracle_rate(N1, N2, N3, 1, 0)
+        line["cpu_baseline"] = {"value": rate, "unit": "zone-cycles/s", "cores": 1, "kind": "oracle",
+                                "sample": "one oracle step of the full 256x128x64 torus block (%.1f s)" % t}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local = env_rank()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

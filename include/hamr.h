@@ -1,0 +1,203 @@
+/* hamr.h -- C ABI of the GB300-native GRMHD block-update library.
+ *
+ * The library advances ideal GRMHD on logarithmic spherical-polar
+ * Kerr-Schild grids with the finite-volume scheme of Liska et al.,
+ * "H-AMR: A New GPU-accelerated GRMHD Code for Exascale Computing With 3D
+ * Adaptive Mesh Refinement and Local Adaptive Time-stepping"
+ * (arXiv 1912.10192):
+ *   - PPM reconstruction of primitives (Sec. 2.1),
+ *   - HLLE (or LLF) fluxes with the approximate fast speed (Sec. 2.1),
+ *   - constrained transport: 4-flux EMF average, staggered face-B update and
+ *     face-to-centre average (Sec. 2.5, the CT and EMF equations),
+ *   - connection source terms sqrt(-g) T^k_l Gamma^l_{nu k} (Sec. 2.5),
+ *   - 2-D Newton-Raphson conserved-to-primitive inversion with an entropy
+ *     backup, and floors (Sec. 2.6, 2.7),
+ *   - the midpoint predictor/corrector step with the CFL time step (Sec. 2.1),
+ * advanced block by block under the AMR / local adaptive time-stepping
+ * schedule of Sec. 3.2 and 3.4.
+ *
+ * Conventions shared by every call
+ *   - Units G = M = c = 1; internal coordinates x1 = log r, x2 = theta,
+ *     x3 = phi (Sec. 2.2).
+ *   - Return value: HAMR_OK (0) or a negative HAMR_E* code; a human-readable
+ *     message of the last failure in the calling thread is hamr_last_error().
+ *     Per-cell physics failures (an inversion that does not converge, a floor)
+ *     are not call errors: they are counted in hamr_step_stats.
+ *   - Ownership: the caller owns every pointer it passes and keeps it valid
+ *     for the duration of the call (device pointers: until the stream work
+ *     it enqueued completes). The grid owns its state, scratch and geometry
+ *     tables and frees them in hamr_grid_destroy.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream). Calls enqueue work and return; results are valid once
+ *     the stream has synchronised, unless a call says it synchronises.
+ *   - State layout ("padded SoA"): a cell field of a block with n1 x n2 x n3
+ *     interior cells is an array of (n3+6)(n2+6)(n1+6) doubles (3 ghost
+ *     layers per side), index ((k+3)(n2+6) + (j+3))(n1+6) + (i+3), i fastest.
+ *     Primitive state = 8 such fields: rho, u_g, utilde^1, utilde^2,
+ *     utilde^3, B^1, B^2, B^3 (cell-centred B is derived: it is recomputed
+ *     from the face field). Face field = 3 such fields: Bbar^d = sqrt(-g) B^d
+ *     on the lower d-face of the cell with the same index.
+ */
+#ifndef HAMR_H
+#define HAMR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define HAMR_OK 0
+#define HAMR_EINVAL (-1)   /* invalid argument or descriptor */
+#define HAMR_ECUDA (-2)    /* a CUDA runtime call failed */
+#define HAMR_ENOMEM (-3)   /* device allocation failed */
+#define HAMR_ETIMEOUT (-4) /* a bounded device wait gave up */
+#define HAMR_ESTATE (-5)   /* call made in the wrong state (e.g. no initial state set) */
+
+/* ---- option enums ---- */
+#define HAMR_METRIC_KS 0        /* Kerr metric, Kerr-Schild, log-r spherical (Sec. 2.2) */
+#define HAMR_METRIC_MINKOWSKI 1 /* flat space, Cartesian (validation problems) */
+#define HAMR_RECON_PPM 0        /* piecewise parabolic (Sec. 2.1) */
+#define HAMR_RECON_MC 1         /* monotonised-central linear */
+#define HAMR_RECON_MINMOD 2     /* minmod linear */
+#define HAMR_FLUX_HLL 0         /* HLLE (Sec. 2.1) */
+#define HAMR_FLUX_LLF 1         /* local Lax-Friedrichs */
+#define HAMR_BC_OUTFLOW 0           /* zero-gradient copy */
+#define HAMR_BC_PERIODIC 1          /* periodic */
+#define HAMR_BC_POLAR 2             /* transmissive polar axis (Sec. 3.3), x2 only, n3 even */
+#define HAMR_BC_OUTFLOW_NOINFLOW 3  /* zero-gradient with utilde^1 clamped to outflow, x1 only */
+#define HAMR_PREC_FP64 0  /* every step in FP64 */
+#define HAMR_PREC_MIXED 1 /* FP32 reconstruction, fluxes and EMFs; FP64 metric, inversion, accumulation */
+
+/* One block: a box of cells uniform in the internal coordinates. */
+typedef struct {
+    int n1, n2, n3;              /* interior cells, each >= 4 */
+    double x1min, x2min, x3min;  /* lower corner */
+    double dx1, dx2, dx3;        /* cell sizes */
+    int bc[6];                   /* x1lo x1hi x2lo x2hi x3lo x3hi: HAMR_BC_* */
+} hamr_block_desc;
+
+/* A grid: physics options and its blocks. */
+typedef struct {
+    int metric;          /* HAMR_METRIC_* */
+    double a;            /* black-hole spin, |a| < 1 */
+    double gam;          /* adiabatic index (p = (gam - 1) u_g), 1 < gam <= 2 */
+    double cour;         /* Courant factor C0 of dt = C0 / max_cells sum_i v_f^i / dx^i */
+    int recon;           /* HAMR_RECON_* */
+    int riemann;         /* HAMR_FLUX_* */
+    int floors;          /* 1: apply the Sec. 2.7 floors after every inversion */
+    int precision;       /* HAMR_PREC_* */
+    int nblocks;         /* >= 1 */
+    const hamr_block_desc* blocks; /* nblocks descriptors, copied by hamr_grid_create */
+} hamr_grid_desc;
+
+/* Counters of the last step (summed over its two stages and all blocks
+ * stepped): energy inversions that converged, entropy-backup inversions,
+ * cells where both failed (their primitives keep the stage's guess), floor
+ * activations; dt of that step and the CFL dt of the resulting state. */
+typedef struct {
+    long long c2p_ok, c2p_entropy, c2p_fail, floor_hits;
+    double dt_used, dt_next;
+} hamr_step_stats;
+
+typedef struct hamr_grid hamr_grid;
+
+/* Validates the descriptor, allocates the block state, scratch and the
+ * geometry tables on the current CUDA device, and builds the tables
+ * (metric, inverse metric, sqrt(-g), lapse at cell centres and faces;
+ * Christoffel symbols at centres by 4th-order finite differences of the
+ * metric, Sec. 2.2). Synchronises the device once. Errors: HAMR_EINVAL for a
+ * bad descriptor (sizes, bc/metric mismatch, odd n3 with a polar boundary),
+ * HAMR_ENOMEM, HAMR_ECUDA. On error *out is NULL and nothing is leaked. */
+int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out);
+
+/* Frees everything the grid owns. NULL is accepted. Synchronises the device. */
+int hamr_grid_destroy(hamr_grid* g);
+
+/* Loads a block's state from `prim` (8 padded fields; slots 5..7 ignored:
+ * centre B is recomputed from the faces) and `bface` (3 padded fields).
+ * `on_device` = 0: host pointers (copied synchronously); 1: device pointers
+ * (copied on `stream`). Ghost values are ignored; boundary conditions refill
+ * them. Also computes the CFL dt of the loaded state. */
+int hamr_grid_set_state(hamr_grid* g, int block, const double* prim, const double* bface, int on_device,
+                        void* stream);
+
+/* Copies a block's state (including ghosts) out, same layout. on_device = 0
+ * synchronises the stream and writes host memory. */
+int hamr_grid_get_state(const hamr_grid* g, int block, double* prim, double* bface, int on_device,
+                        void* stream);
+
+/* One midpoint step of one block (Sec. 2.1): boundary conditions, predictor
+ * to t + dt/2 with fluxes, EMFs and sources of P^n, corrector from U^n to
+ * t + dt with those of P^{n+1/2}; each stage ends with the CT update, the
+ * inversion and the floors. dt > 0: that step; dt <= 0: the CFL step of the
+ * current state, read on the device (no host round trip). The CFL dt of the
+ * new state is reduced on the device in the same pass. stats: NULL for a
+ * fully asynchronous call; otherwise the call synchronises `stream` and fills
+ * *stats. */
+int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_stats* stats);
+
+/* Advances every block of the grid through `n_fine_substeps` substeps of the
+ * local adaptive time-stepping schedule (Sec. 3.4): a block of LAT level L
+ * (time step 2^L dt_fine) is due at substep s when s mod 2^L = 0; all due
+ * blocks of a stage run in one batched launch; coarse-fine ghost zones are
+ * filled by MINMOD prolongation with linear time interpolation and by
+ * restriction (Sec. 3.2); fluxes and EMFs are refluxed when levels
+ * synchronise. Reserved: returns HAMR_EINVAL for single-block grids. */
+int hamr_batch_step(hamr_grid* g, int n_fine_substeps, void* stream, hamr_step_stats* stats);
+
+/* Reads the accumulated counters of the last step; synchronises the device. */
+int hamr_grid_stats(const hamr_grid* g, hamr_step_stats* stats);
+
+/* ---- measurement ---- */
+/* Per-kernel device time of the grid's launches. */
+typedef struct {
+    char name[32];       /* kernel group: "bc", "recon", "flux", "emf", "ct", "update", "dt", ... */
+    long long launches;  /* kernels launched in this group since the last reset */
+    double ms;           /* summed device time (0 unless timing was enabled) */
+} hamr_kernel_time;
+
+/* enable != 0: every kernel group the grid launches is bracketed by CUDA
+ * events on the stream it runs on, so hamr_grid_timing can report device
+ * time per group (the events add no synchronisation). Launch counts are
+ * always kept. Resets the totals. */
+int hamr_grid_set_timing(hamr_grid* g, int enable);
+
+/* Synchronises the device and writes up to `max` entries (one per kernel
+ * group) to out; *n receives the number of groups. */
+int hamr_grid_timing(hamr_grid* g, hamr_kernel_time* out, int max, int* n);
+
+/* Measures the device's FP64 fused multiply-add rate (GFLOP/s, 2 flops per
+ * FMA) with a dependency-free FMA loop on every SM; synchronises `stream`.
+ * No counterpart in the paper: it is the denominator of the FP64-pipe
+ * roofline that bounds the FP64 update on this hardware. */
+int hamr_measure_fp64_peak(void* stream, double* gflops);
+
+/* ---- standalone inversion (Sec. 2.6) ---- */
+#define HAMR_C2P_ENTROPY_ONLY 1u /* skip the energy inversion (tests of the backup) */
+
+typedef struct {
+    int metric;      /* HAMR_METRIC_* */
+    double a;        /* spin (KS) */
+    double gam;      /* adiabatic index */
+    uint32_t flags;  /* HAMR_C2P_* */
+} hamr_c2p_desc;
+
+/* Inverts n conserved states on the device. All arrays are device pointers
+ * in SoA layout: U[6][n] = sqrt(-g) (rho u^t, T^t_t + rho u^t, T^t_1,
+ * T^t_2, T^t_3, kappa rho u^t); B[3][n] centre B^i; x1[n], x2[n] positions;
+ * prim[8][n] in: the guess, out: the result (slots 5..7 set to B);
+ * status[n]: 0 energy inversion, 1 entropy backup, 2 both failed (prim keeps
+ * the guess); iters[n]: Newton iterations of the energy inversion (may be
+ * NULL). Asynchronous on `stream`. */
+int hamr_con2prim(const hamr_c2p_desc* d, int64_t n, const double* U, const double* B, const double* x1,
+                  const double* x2, double* prim, int32_t* status, int32_t* iters, void* stream);
+
+/* Message of the last error in the calling thread ("" if none). */
+const char* hamr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

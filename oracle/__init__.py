@@ -58,6 +58,7 @@ def _setup(lib):
         "ora_grid_status": [C.c_void_p, _I],
         "ora_flops_reset": [],
         "ora_flops_get": [C.POINTER(C.c_ulonglong)],
+        "ora_flops_phase": [C.POINTER(C.c_ulonglong)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -244,3 +245,14 @@ def flops_get():
     out = (C.c_ulonglong * 5)()
     lib(True).ora_flops_get(out)
     return list(out)
+
+
+PHASES = ("recon", "flux", "emf", "ct", "update", "cfl")
+CLASSES = ("addmul", "div", "sqrt", "transc", "cmp")
+
+
+def flops_phase():
+    """{phase: [add/sub/mul, div, sqrt, transcendental, compare]} of the counting build."""
+    out = (C.c_ulonglong * 30)()
+    lib(True).ora_flops_phase(out)
+    return {p: list(out[5 * k:5 * k + 5]) for k, p in enumerate(PHASES)}

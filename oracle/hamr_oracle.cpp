@@ -35,6 +35,24 @@ unsigned long long ora_flop_ctr[5] = {0, 0, 0, 0, 0};
 }
 #endif
 
+/* phase attribution of the counted operations (counting build only):
+ * 0 reconstruction, 1 face fluxes, 2 EMFs, 3 CT, 4 cell update + inversion
+ * + floors, 5 CFL rate. Elements: the five counter classes. */
+static unsigned long long ora_phase_ctr[6][5];
+[[maybe_unused]] static unsigned long long ora_phase_mark[5];
+static void phase_begin() {
+#ifdef ORA_COUNT_FLOPS
+    for (int m = 0; m < 5; m++) ora_phase_mark[m] = ora_flop_ctr[m];
+#endif
+}
+static void phase_end(int ph) {
+#ifdef ORA_COUNT_FLOPS
+    for (int m = 0; m < 5; m++) ora_phase_ctr[ph][m] += ora_flop_ctr[m] - ora_phase_mark[m];
+#else
+    (void)ph;
+#endif
+}
+
 namespace {
 
 const int NG = 3;                                   /* ghost layers */
@@ -48,7 +66,7 @@ const int NFX = 8; /* face-flux slots: 0..5 as NCONS, 6/7 = the two B^i with i !
 const double CONN_H = 1.0e-3;
 
 /* Reading (Sec. 2.6): Newton stopping rule and limits, not given in the paper. */
-const double C2P_TOL = 1.0e-12;
+const double C2P_TOL = 1.0e-10;
 const int C2P_NMAX = 30;
 const double GAMMA_MAX = 50.0;
 
@@ -417,7 +435,8 @@ enum { C2P_OK = 0, C2P_ENTROPY = 1, C2P_FAIL = 2, C2P_FLOOR = 4 };
  * Recovery: rho = D/Gamma, u = p/(gam-1),
  *   utilde^i = Gamma/(W + B^2) (Qt^i + (Q.B) Bn^i / W),
  *   Qt^i = (g^{i nu} + n^i n^nu) Q_nu (spatial projection of Q).
- * Reading: tolerance |dW|/W + |dv^2| < 1e-12, at most 30 iterations,
+ * Reading: tolerance |dW|/W + |dv^2| < 1e-10 (with quadratic convergence the
+ * accepted iterate is then at round-off), at most 30 iterations,
  * v^2 kept in [0, 1 - 1/50^2]; a failed state keeps its guess. */
 static int con2prim(const ora_desc& d, const real Ucons[NCONS], const real Bc[3], const Geom& G,
                     real* pr, int* iters, int entropy_only = 0) {
@@ -763,6 +782,7 @@ void stage(ora_grid* g, const double* Pf, const double* Bff, const double* Pb, c
         int ta = (dir == 1) ? 2 : 1, tb = (dir == 3) ? 2 : 3;
         for (int b = lo[tb]; b <= hi[tb]; b++)
             for (int a = lo[ta]; a <= hi[ta]; a++) {
+                phase_begin();
                 for (int v = 0; v < NPR; v++) {
                     if (v == B1 + dir - 1) continue;
                     for (int c = 0; c < L; c++) {
@@ -778,6 +798,8 @@ void stage(ora_grid* g, const double* Pf, const double* Bff, const double* Pb, c
                         PR[(size_t)v * L + c] = ar[c];
                     }
                 }
+                phase_end(0);
+                phase_begin();
                 for (int f = lo[dir]; f <= hi[dir]; f++) {
                     int ii[4];
                     ii[dir] = f;
@@ -805,11 +827,13 @@ void stage(ora_grid* g, const double* Pf, const double* Bff, const double* Pb, c
                     }
                     for (int m = 0; m < NFX; m++) F[dir][(size_t)m * nc + fi] = tod(fx[m]);
                 }
+                phase_end(1);
             }
     }
 
     /* EMFs at edges (Sec. 2.5, the 4-flux average). Reading: E1 and E3 on the
      * polar axis are 0, which keeps Bbar^2 = 0 on axis faces and div B intact. */
+    phase_begin();
     std::vector<double> E1(nc, 0.0), E2(nc, 0.0), E3(nc, 0.0);
     auto FX = [&](int dir, int slot, int i, int j, int k) -> real {
         return real(F[dir][(size_t)slot * nc + cidx(g, i, j, k)]);
@@ -838,6 +862,8 @@ void stage(ora_grid* g, const double* Pf, const double* Bff, const double* Pb, c
                 }
             }
 
+    phase_end(2);
+    phase_begin();
     /* staggered face update (Sec. 2.5, the three CT equations) */
     for (int v = 0; v < 3; v++)
         for (long c = 0; c < nc; c++) Bfout[v * nc + c] = Bfb[v * nc + c];
@@ -863,6 +889,8 @@ void stage(ora_grid* g, const double* Pf, const double* Bff, const double* Pb, c
                 }
             }
 
+    phase_end(3);
+    phase_begin();
     /* cell update, inversion, floors */
     for (int k = 0; k < n3; k++)
         for (int j = 0; j < n2; j++)
@@ -910,6 +938,7 @@ void stage(ora_grid* g, const double* Pf, const double* Bff, const double* Pb, c
                 }
                 for (int v = 0; v < NPR; v++) Pout[v * nc + c] = tod(pr[v]);
             }
+    phase_end(4);
 }
 
 /* CFL time step (Sec. 2.1): per cell 1/dt = sum_i v_f^i / dx^i with
@@ -919,6 +948,7 @@ double grid_dt(ora_grid* g) {
     const ora_desc& d = g->d;
     const double dx[4] = {0.0, d.dx1, d.dx2, d.dx3};
     real invmax = 0.0;
+    phase_begin();
     for (int k = 0; k < d.n3; k++)
         for (int j = 0; j < d.n2; j++)
             for (int i = 0; i < d.n1; i++) {
@@ -936,6 +966,7 @@ double grid_dt(ora_grid* g) {
                 }
                 if (inv > invmax) invmax = inv;
             }
+    phase_end(5);
     return tod(d.cour / invmax);
 }
 
@@ -1180,6 +1211,13 @@ void ora_flops_reset(void) {
 #ifdef ORA_COUNT_FLOPS
     for (int m = 0; m < 5; m++) ora_flop_ctr[m] = 0;
 #endif
+    for (int p = 0; p < 6; p++)
+        for (int m = 0; m < 5; m++) ora_phase_ctr[p][m] = 0;
+}
+
+void ora_flops_phase(unsigned long long* out30) {
+    for (int p = 0; p < 6; p++)
+        for (int m = 0; m < 5; m++) out30[p * 5 + m] = ora_phase_ctr[p][m];
 }
 
 void ora_flops_get(unsigned long long* out5) {

@@ -75,6 +75,8 @@ void ora_grid_status(const ora_grid* g, int* status_cells);
 /* flop counters (meaningful only in the counting build) */
 void ora_flops_reset(void);
 void ora_flops_get(unsigned long long* out5);
+/* per phase (recon, flux, emf, ct, update, cfl) x counter class, counting build only */
+void ora_flops_phase(unsigned long long* out30);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,484 @@
+// api.cu -- the C ABI declared in include/hamr.h: grid lifetime, state I/O,
+// the per-block midpoint step and the standalone inversion.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "grmhd.cuh"
+#include "hamr_internal.h"
+
+using namespace hamr;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                                   \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) return fail(HAMR_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// launches a kernel group of `nk` kernels on stream `cs`, counted under `kind`
+// and bracketed by events when the grid's timer is on
+#define LAUNCH(g, kind, nk, cs, call)                                    \
+    do {                                                                 \
+        cudaEvent_t ea_ = nullptr, eb_ = nullptr;                        \
+        if ((g)->timer.enabled) {                                        \
+            ea_ = (g)->timer.get();                                      \
+            eb_ = (g)->timer.get();                                      \
+            cudaEventRecord(ea_, cs);                                    \
+        }                                                                \
+        CUDA_TRY(call);                                                  \
+        if ((g)->timer.enabled) {                                        \
+            cudaEventRecord(eb_, cs);                                    \
+            (g)->timer.pending.push_back({kind, ea_, eb_});              \
+        }                                                                \
+        (g)->timer.launches[kind] += (nk);                               \
+    } while (0)
+
+}  // namespace
+
+namespace {
+
+// launch accounting and optional event timing of kernel groups
+struct Timer {
+    static constexpr int NK = 8;
+    const char* names[NK] = {"dt", "bc", "recon", "flux", "emf", "ct", "update", "load"};
+    long long launches[NK] = {0};
+    double ms[NK] = {0};
+    bool enabled = false;
+    struct Pending {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void drain() {  // device must be idle
+        for (auto& p : pending) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, p.a, p.b);
+            ms[p.kind] += t;
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pending.clear();
+    }
+    void reset() {
+        for (int k = 0; k < NK; k++) {
+            launches[k] = 0;
+            ms[k] = 0.0;
+        }
+    }
+    ~Timer() {
+        for (auto& p : pending) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+enum { K_DT = 0, K_BC, K_RECON, K_FLUX, K_EMF, K_CT, K_UPDATE, K_LOAD };
+
+}  // namespace
+
+struct hamr_grid {
+    Timer timer;
+    hamr_grid_desc desc;
+    std::vector<hamr_block_desc> blocks;
+    std::vector<BlockState> st;
+    std::vector<BlockView> view;
+    std::vector<void*> arena;
+    std::vector<int> loaded;
+    PhysArgs ph;
+    int device;
+};
+
+namespace {
+
+int validate(const hamr_grid_desc* d) {
+    if (!d) return fail(HAMR_EINVAL, "descriptor is NULL");
+    if (d->nblocks < 1 || !d->blocks) return fail(HAMR_EINVAL, "nblocks must be >= 1 with a block array");
+    if (d->metric != HAMR_METRIC_KS && d->metric != HAMR_METRIC_MINKOWSKI)
+        return fail(HAMR_EINVAL, "unknown metric %d", d->metric);
+    if (d->metric == HAMR_METRIC_KS && !(std::fabs(d->a) < 1.0)) return fail(HAMR_EINVAL, "spin must satisfy |a| < 1");
+    if (!(d->gam > 1.0 && d->gam <= 2.0)) return fail(HAMR_EINVAL, "gam must be in (1, 2]");
+    if (!(d->cour > 0.0 && d->cour <= 1.0)) return fail(HAMR_EINVAL, "cour must be in (0, 1]");
+    if (d->recon < 0 || d->recon > 2) return fail(HAMR_EINVAL, "unknown recon %d", d->recon);
+    if (d->riemann < 0 || d->riemann > 1) return fail(HAMR_EINVAL, "unknown riemann %d", d->riemann);
+    if (d->precision != HAMR_PREC_FP64 && d->precision != HAMR_PREC_MIXED)
+        return fail(HAMR_EINVAL, "unknown precision %d", d->precision);
+    for (int b = 0; b < d->nblocks; b++) {
+        const hamr_block_desc& B = d->blocks[b];
+        if (B.n1 < 4 || B.n2 < 4 || B.n3 < 4) return fail(HAMR_EINVAL, "block %d: each n must be >= 4", b);
+        if ((long)(B.n1 + 6) * (B.n2 + 6) * (B.n3 + 6) > (1L << 28))
+            return fail(HAMR_EINVAL, "block %d: too many cells", b);
+        if (!(B.dx1 > 0 && B.dx2 > 0 && B.dx3 > 0)) return fail(HAMR_EINVAL, "block %d: dx must be > 0", b);
+        for (int f = 0; f < 6; f++) {
+            const int bc = B.bc[f];
+            if (bc < 0 || bc > 3) return fail(HAMR_EINVAL, "block %d: unknown bc %d", b, bc);
+            if (bc == HAMR_BC_POLAR && (f / 2) != 1) return fail(HAMR_EINVAL, "block %d: polar bc only on x2", b);
+            if (bc == HAMR_BC_OUTFLOW_NOINFLOW && (f / 2) != 0)
+                return fail(HAMR_EINVAL, "block %d: noinflow bc only on x1", b);
+            if (bc == HAMR_BC_POLAR && (B.n3 % 2) != 0) return fail(HAMR_EINVAL, "block %d: polar bc needs even n3", b);
+            if (bc == HAMR_BC_POLAR && d->metric != HAMR_METRIC_KS)
+                return fail(HAMR_EINVAL, "block %d: polar bc needs the KS metric", b);
+        }
+        if ((B.bc[0] == HAMR_BC_PERIODIC) != (B.bc[1] == HAMR_BC_PERIODIC) ||
+            (B.bc[2] == HAMR_BC_PERIODIC) != (B.bc[3] == HAMR_BC_PERIODIC) ||
+            (B.bc[4] == HAMR_BC_PERIODIC) != (B.bc[5] == HAMR_BC_PERIODIC))
+            return fail(HAMR_EINVAL, "block %d: periodic bc must be on both sides", b);
+        const double pi = 3.14159265358979323846;
+        if (B.bc[2] == HAMR_BC_POLAR && std::fabs(B.x2min) > 1e-12)
+            return fail(HAMR_EINVAL, "block %d: lower polar bc needs x2min = 0", b);
+        if (B.bc[3] == HAMR_BC_POLAR && std::fabs(B.x2min + B.n2 * B.dx2 - pi) > 1e-9)
+            return fail(HAMR_EINVAL, "block %d: upper polar bc needs x2max = pi", b);
+    }
+    return HAMR_OK;
+}
+
+void free_grid(hamr_grid* g) {
+    for (void* p : g->arena)
+        if (p) cudaFree(p);
+    delete g;
+}
+
+int alloc_block(hamr_grid* g, int b) {
+    const hamr_block_desc& B = g->blocks[b];
+    BlockView v;
+    std::memset(&v, 0, sizeof(v));
+    v.n1 = B.n1;
+    v.n2 = B.n2;
+    v.n3 = B.n3;
+    v.n1p = B.n1 + 2 * NG;
+    v.n2p = B.n2 + 2 * NG;
+    v.n3p = B.n3 + 2 * NG;
+    v.nc = (long)v.n1p * v.n2p * v.n3p;
+    v.n2d = (long)v.n1p * v.n2p;
+    v.dx1 = B.dx1;
+    v.dx2 = B.dx2;
+    v.dx3 = B.dx3;
+    v.idx1 = 1.0 / B.dx1;
+    v.idx2 = 1.0 / B.dx2;
+    v.idx3 = 1.0 / B.dx3;
+    for (int f = 0; f < 6; f++) v.bc[f] = B.bc[f];
+
+    // every field and table is padded to a whole number of 256-byte lines
+    const size_t fld = align256(sizeof(double) * (size_t)v.nc);
+    const size_t tab = align256(sizeof(double) * (size_t)v.n2d);
+    v.nc = (long)(fld / sizeof(double));   // stride between two fields
+    v.n2d = (long)(tab / sizeof(double));  // stride between two table components
+    const int nfields = 8 + 3 + 8 + 3 + 8 + 8 + 24 + 3 + 6;
+    const size_t stbytes = align256((size_t)v.nc);
+    size_t bytes = fld * nfields + stbytes + tab * (NGEOM_C + 2 * NGEOM) + 256 * 3;
+    void* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HAMR_ENOMEM, "cudaMalloc of %zu bytes for block %d failed: %s", bytes, b, cudaGetErrorString(e));
+    }
+    g->arena.push_back(base);
+    char* p = (char*)base;
+    auto take = [&](size_t n) {
+        char* r = p;
+        p += n;
+        return r;
+    };
+    BlockState s;
+    s.P = (double*)take(8 * fld);
+    s.B = (double*)take(3 * fld);
+    s.Ph = (double*)take(8 * fld);
+    s.Bh = (double*)take(3 * fld);
+    s.QL = (double*)take(8 * fld);
+    s.QR = (double*)take(8 * fld);
+    for (int d = 0; d < 3; d++) s.F[d] = (double*)take(8 * fld);
+    s.E = (double*)take(3 * fld);
+    s.Un = (double*)take(6 * fld);
+    s.status = (uint8_t*)take(stbytes);
+    s.geom_c = (double*)take(tab * NGEOM_C);
+    s.geom_f1 = (double*)take(tab * NGEOM);
+    s.geom_f2 = (double*)take(tab * NGEOM);
+    s.dscal = (double*)take(256);
+    s.dmax = (unsigned long long*)take(256);
+    s.dcnt = (unsigned long long*)take(256);
+    v.gc = s.geom_c;
+    v.gf1 = s.geom_f1;
+    v.gf2 = s.geom_f2;
+    CUDA_TRY(cudaMemset(base, 0, bytes));
+    GeomArgs A;
+    A.metric = g->desc.metric;
+    A.a = g->desc.a;
+    A.n1 = B.n1;
+    A.n2 = B.n2;
+    A.n1p = v.n1p;
+    A.n2p = v.n2p;
+    A.x1min = B.x1min;
+    A.x2min = B.x2min;
+    A.dx1 = B.dx1;
+    A.dx2 = B.dx2;
+    A.pole_lo = (B.bc[2] == HAMR_BC_POLAR);
+    A.pole_hi = (B.bc[3] == HAMR_BC_POLAR);
+    A.centre = s.geom_c;
+    A.face1 = s.geom_f1;
+    A.face2 = s.geom_f2;
+    A.table_stride = v.n2d;
+    CUDA_TRY(launch_geometry(A, 0));
+    g->st.push_back(s);
+    g->view.push_back(v);
+    g->loaded.push_back(0);
+    return HAMR_OK;
+}
+
+cudaStream_t S(void* stream) { return (cudaStream_t)stream; }
+
+// after a state load: centre B from the faces, boundaries, CFL rate
+cudaError_t load_kernels(const BlockView& v, const PhysArgs& ph, BlockState& s, cudaStream_t cs) {
+    cudaError_t e = launch_centre_b(v, s.P, s.B, cs);
+    if (e == cudaSuccess) e = launch_bc(v, s.P, s.B, cs);
+    if (e == cudaSuccess) e = launch_dt_reduce(v, ph, s.P, s.dmax, cs);
+    return e;
+}
+
+// copy between the user's padded layout (stride n1p*n2p*n3p) and the grid's (stride v.nc)
+int copy_fields(double* dst, long dstride, const double* src, long sstride, long n, int nfields, cudaMemcpyKind kind,
+                cudaStream_t s, bool sync) {
+    for (int f = 0; f < nfields; f++) {
+        if (sync)
+            CUDA_TRY(cudaMemcpy(dst + f * dstride, src + f * sstride, sizeof(double) * n, kind));
+        else
+            CUDA_TRY(cudaMemcpyAsync(dst + f * dstride, src + f * sstride, sizeof(double) * n, kind, s));
+    }
+    return HAMR_OK;
+}
+
+int check_block(const hamr_grid* g, int block) {
+    if (!g) return fail(HAMR_EINVAL, "grid is NULL");
+    if (block < 0 || block >= (int)g->blocks.size()) return fail(HAMR_EINVAL, "block %d out of range", block);
+    return HAMR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hamr_last_error(void) { return g_err.c_str(); }
+
+int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out) {
+    if (!out) return fail(HAMR_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate(d);
+    if (rc) return rc;
+    hamr_grid* g = new hamr_grid;
+    g->desc = *d;
+    g->blocks.assign(d->blocks, d->blocks + d->nblocks);
+    g->desc.blocks = g->blocks.data();
+    g->ph.gam = d->gam;
+    g->ph.cour = d->cour;
+    g->ph.recon = d->recon;
+    g->ph.riemann = d->riemann;
+    g->ph.floors = d->floors;
+    cudaGetDevice(&g->device);
+    for (int b = 0; b < d->nblocks; b++) {
+        rc = alloc_block(g, b);
+        if (rc) {
+            free_grid(g);
+            return rc;
+        }
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_grid(g);
+        return fail(HAMR_ECUDA, "geometry build failed: %s", cudaGetErrorString(e));
+    }
+    *out = g;
+    return HAMR_OK;
+}
+
+int hamr_grid_destroy(hamr_grid* g) {
+    if (!g) return HAMR_OK;
+    cudaDeviceSynchronize();
+    free_grid(g);
+    return HAMR_OK;
+}
+
+int hamr_grid_set_state(hamr_grid* g, int block, const double* prim, const double* bface, int on_device,
+                        void* stream) {
+    int rc = check_block(g, block);
+    if (rc) return rc;
+    if (!prim || !bface) return fail(HAMR_EINVAL, "prim and bface must not be NULL");
+    const BlockView& v = g->view[block];
+    BlockState& s = g->st[block];
+    const long n = (long)v.n1p * v.n2p * v.n3p;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    rc = copy_fields(s.P, v.nc, prim, n, n, 8, kind, S(stream), !on_device);
+    if (rc) return rc;
+    rc = copy_fields(s.B, v.nc, bface, n, n, 3, kind, S(stream), !on_device);
+    if (rc) return rc;
+    cudaStream_t cs = S(stream);
+    CUDA_TRY(cudaMemsetAsync(s.dmax, 0, sizeof(unsigned long long), cs));
+    LAUNCH(g, K_LOAD, 6, cs, load_kernels(v, g->ph, s, cs));
+    g->loaded[block] = 1;
+    return HAMR_OK;
+}
+
+int hamr_grid_get_state(const hamr_grid* g, int block, double* prim, double* bface, int on_device, void* stream) {
+    int rc = check_block(g, block);
+    if (rc) return rc;
+    const BlockView& v = g->view[block];
+    const BlockState& s = g->st[block];
+    const long n = (long)v.n1p * v.n2p * v.n3p;
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(S(stream)));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (prim) {
+        rc = copy_fields(prim, n, s.P, v.nc, n, 8, kind, S(stream), !on_device);
+        if (rc) return rc;
+    }
+    if (bface) {
+        rc = copy_fields(bface, n, s.B, v.nc, n, 3, kind, S(stream), !on_device);
+        if (rc) return rc;
+    }
+    return HAMR_OK;
+}
+
+int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_stats* stats) {
+    int rc = check_block(g, block);
+    if (rc) return rc;
+    if (!g->loaded[block]) return fail(HAMR_ESTATE, "block %d has no state: call hamr_grid_set_state first", block);
+    if (!std::isfinite(dt)) return fail(HAMR_EINVAL, "dt must be finite");
+    const BlockView& v = g->view[block];
+    BlockState& s = g->st[block];
+    const PhysArgs& ph = g->ph;
+    cudaStream_t cs = S(stream);
+    LAUNCH(g, K_DT, 1, cs, launch_dt_select(ph, dt, s.dscal, s.dmax, s.dcnt, s.status, v.nc, cs));
+    // predictor: P^n, B^n -> P^{n+1/2}, B^{n+1/2}
+    LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.P, s.B, cs));
+    for (int dir = 1; dir <= 3; dir++) {
+        LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.P, s.QL, s.QR, cs));
+        LAUNCH(g, K_FLUX, 1, cs, launch_flux(v, ph, dir, s.QL, s.QR, s.B, s.F[dir - 1], cs));
+    }
+    LAUNCH(g, K_EMF, 1, cs, launch_emf(v, s.F, s.E, cs));
+    LAUNCH(g, K_CT, 1, cs, launch_ct(v, s.E, s.B, s.Bh, s.dscal, 0.5, cs));
+    LAUNCH(g, K_UPDATE, 1, cs,
+           launch_update(v, ph, 0, s.P, s.P, s.F, s.Bh, s.Un, s.Ph, s.status, s.dscal, 0.5, s.dmax, s.dcnt, cs));
+    // corrector: U^n and the fluxes of P^{n+1/2} -> P^{n+1}, B^{n+1} (in place)
+    LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.Ph, s.Bh, cs));
+    for (int dir = 1; dir <= 3; dir++) {
+        LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.Ph, s.QL, s.QR, cs));
+        LAUNCH(g, K_FLUX, 1, cs, launch_flux(v, ph, dir, s.QL, s.QR, s.Bh, s.F[dir - 1], cs));
+    }
+    LAUNCH(g, K_EMF, 1, cs, launch_emf(v, s.F, s.E, cs));
+    LAUNCH(g, K_CT, 1, cs, launch_ct(v, s.E, s.B, s.B, s.dscal, 1.0, cs));
+    LAUNCH(g, K_UPDATE, 1, cs,
+           launch_update(v, ph, 1, s.P, s.Ph, s.F, s.B, s.Un, s.P, s.status, s.dscal, 1.0, s.dmax, s.dcnt, cs));
+    LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.P, s.B, cs));
+    if (stats) {
+        CUDA_TRY(cudaStreamSynchronize(cs));
+        return hamr_grid_stats(g, stats);
+    }
+    return HAMR_OK;
+}
+
+int hamr_batch_step(hamr_grid* g, int n_fine_substeps, void* stream, hamr_step_stats* stats) {
+    (void)n_fine_substeps;
+    (void)stream;
+    (void)stats;
+    if (!g) return fail(HAMR_EINVAL, "grid is NULL");
+    return fail(HAMR_EINVAL, "batched AMR/LAT stepping needs a multi-block grid");
+}
+
+int hamr_grid_set_timing(hamr_grid* g, int enable) {
+    if (!g) return fail(HAMR_EINVAL, "grid is NULL");
+    CUDA_TRY(cudaDeviceSynchronize());
+    g->timer.drain();
+    g->timer.reset();
+    g->timer.enabled = (enable != 0);
+    return HAMR_OK;
+}
+
+int hamr_grid_timing(hamr_grid* g, hamr_kernel_time* out, int max, int* n) {
+    if (!g || !n || (max > 0 && !out)) return fail(HAMR_EINVAL, "bad arguments");
+    CUDA_TRY(cudaDeviceSynchronize());
+    g->timer.drain();
+    *n = Timer::NK;
+    for (int k = 0; k < Timer::NK && k < max; k++) {
+        std::memset(out[k].name, 0, sizeof(out[k].name));
+        std::strncpy(out[k].name, g->timer.names[k], sizeof(out[k].name) - 1);
+        out[k].launches = g->timer.launches[k];
+        out[k].ms = g->timer.ms[k];
+    }
+    return HAMR_OK;
+}
+
+int hamr_measure_fp64_peak(void* stream, double* gflops) {
+    if (!gflops) return fail(HAMR_EINVAL, "gflops is NULL");
+    CUDA_TRY(measure_fp64_peak(S(stream), gflops));
+    return HAMR_OK;
+}
+
+int hamr_grid_stats(const hamr_grid* g, hamr_step_stats* stats) {
+    if (!g || !stats) return fail(HAMR_EINVAL, "grid and stats must not be NULL");
+    CUDA_TRY(cudaDeviceSynchronize());
+    std::memset(stats, 0, sizeof(*stats));
+    for (size_t b = 0; b < g->st.size(); b++) {
+        if (!g->loaded[b]) continue;
+        unsigned long long cnt[4], mx;
+        double dt;
+        CUDA_TRY(cudaMemcpy(cnt, g->st[b].dcnt, sizeof(cnt), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(&mx, g->st[b].dmax, sizeof(mx), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(&dt, g->st[b].dscal, sizeof(dt), cudaMemcpyDeviceToHost));
+        stats->c2p_ok += (long long)cnt[0];
+        stats->c2p_entropy += (long long)cnt[1];
+        stats->c2p_fail += (long long)cnt[2];
+        stats->floor_hits += (long long)cnt[3];
+        double rate;
+        std::memcpy(&rate, &mx, sizeof(rate));
+        const double dn = g->ph.cour / rate;
+        if (b == 0 || dt < stats->dt_used) stats->dt_used = dt;
+        if (b == 0 || dn < stats->dt_next) stats->dt_next = dn;
+    }
+    return HAMR_OK;
+}
+
+int hamr_con2prim(const hamr_c2p_desc* d, int64_t n, const double* U, const double* B, const double* x1,
+                  const double* x2, double* prim, int32_t* status, int32_t* iters, void* stream) {
+    if (!d) return fail(HAMR_EINVAL, "descriptor is NULL");
+    if (n < 0) return fail(HAMR_EINVAL, "n must be >= 0");
+    if (n == 0) return HAMR_OK;
+    if (!U || !B || !x1 || !x2 || !prim || !status) return fail(HAMR_EINVAL, "array argument is NULL");
+    if (d->metric != HAMR_METRIC_KS && d->metric != HAMR_METRIC_MINKOWSKI)
+        return fail(HAMR_EINVAL, "unknown metric %d", d->metric);
+    if (!(d->gam > 1.0 && d->gam <= 2.0)) return fail(HAMR_EINVAL, "gam must be in (1, 2]");
+    if (d->flags & ~HAMR_C2P_ENTROPY_ONLY) return fail(HAMR_EINVAL, "unknown flags 0x%x", d->flags);
+    CUDA_TRY(launch_con2prim(*d, n, U, B, x1, x2, prim, status, iters, S(stream)));
+    return HAMR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// c2p.cuh -- conserved-to-primitive inversion (Liska et al. 2019, Sec. 2.6).
+//
+// Primary: 2-D Newton-Raphson on W = w Gamma^2 and v^2 = 1 - 1/Gamma^2 for
+// the two scalar equations of the energy and the projected momentum in the
+// normal-observer frame (the formulation of Noble et al. 2006). Backup when
+// it fails: the entropy equation replaces the energy one, p = kappa rho^gam
+// with kappa = U_kappa / U_rho, and a 1-D Newton in W solves the projected
+// momentum equation (Noble et al. 2009). A state where both fail keeps its
+// guess.
+//
+// Stopping rule: |dW|/W + |dv^2| < 1e-10 (quadratic convergence leaves the
+// accepted iterate at round-off), at most 30 iterations; v^2 is kept
+// in [0, 1 - 1/50^2].
+#pragma once
+#include "grmhd.cuh"
+
+namespace hamr {
+
+constexpr double C2P_TOL = 1.0e-10;
+constexpr int C2P_NMAX = 30;
+constexpr double C2P_VSQMAX = 1.0 - 1.0 / (50.0 * 50.0);
+
+enum { INV_OK = 0, INV_ENTROPY = 1, INV_FAIL = 2 };
+
+// U: sqrt(-g) (rho u^t, T^t_t + rho u^t, T^t_i, kappa rho u^t); Bc: centre B^i.
+// pr: in the guess (slots 0..4), out the result (slots 0..4) unless INV_FAIL.
+__device__ __forceinline__ int invert(const double U[NCONS], const double Bc[3], const Metric<double>& m, double gam,
+                                      double pr[NPRIM], int* iters, bool entropy_only) {
+    const double gfac = (gam - 1.0) / gam;
+    const double al = m.alpha;
+    const double ig = 1.0 / m.gdet;
+    const double D = U[C_RHO] * al * ig;
+    // Q_mu = alpha T^t_mu, raised with the sparse inverse metric
+    const double Q0 = al * (U[C_EN] - U[C_RHO]) * ig;
+    const double Q1 = al * U[C_S1] * ig;
+    const double Q2 = al * U[C_S2] * ig;
+    const double Q3 = al * U[C_S3] * ig;
+    const double Qc0 = m.c00 * Q0 + m.c01 * Q1;
+    const double Qc1 = m.c01 * Q0 + m.c11 * Q1 + m.c13 * Q3;
+    const double Qc2 = m.c22 * Q2;
+    const double Qc3 = m.c13 * Q1 + m.c33 * Q3;
+    const double Bn1 = al * Bc[0], Bn2 = al * Bc[1], Bn3 = al * Bc[2];
+    const double Qdotn = -al * Qc0;
+    const double Qtsq = Q0 * Qc0 + Q1 * Qc1 + Q2 * Qc2 + Q3 * Qc3 + Qdotn * Qdotn;
+    const double Bsq = m.g11 * Bn1 * Bn1 + m.g22 * Bn2 * Bn2 + m.g33 * Bn3 * Bn3 + 2.0 * m.g13 * Bn1 * Bn3;
+    const double QdotB = Q1 * Bn1 + Q2 * Bn2 + Q3 * Bn3;
+    const double QB2 = QdotB * QdotB;
+
+    // guess
+    const double q1 = pr[U1], q2 = pr[U2], q3 = pr[U3];
+    const double qsq = m.g11 * q1 * q1 + m.g22 * q2 * q2 + m.g33 * q3 * q3 + 2.0 * m.g13 * q1 * q3;
+    const double gsq = 1.0 + qsq;
+    double vsq = fmin(qsq / gsq, C2P_VSQMAX);
+    double W = (pr[RHO] + gam * pr[UU]) * gsq;
+    const double W0 = W;
+
+    bool ok = false;
+    int it = 0;
+    if (!entropy_only) {
+        for (it = 1; it <= C2P_NMAX; it++) {
+            const double omv = 1.0 - vsq;
+            const double rs = rsqrt(omv);
+            const double sq = omv * rs;
+            const double iW = 1.0 / W;
+            const double iW2 = iW * iW;
+            const double BW = Bsq + W;
+            const double p = gfac * (W * omv - D * sq);
+            const double f1 = -0.5 * Bsq * (1.0 + vsq) + 0.5 * QB2 * iW2 - W + p - Qdotn;
+            const double f2 = vsq * BW * BW - QB2 * (Bsq + 2.0 * W) * iW2 - Qtsq;
+            const double j11 = -QB2 * iW2 * iW - 1.0 + gfac * omv;
+            const double j12 = -0.5 * Bsq + gfac * (0.5 * D * rs - W);
+            const double j21 = 2.0 * BW * (vsq + QB2 * iW2 * iW);
+            const double j22 = BW * BW;
+            const double idet = 1.0 / (j11 * j22 - j12 * j21);
+            const double dW = (j12 * f2 - j22 * f1) * idet;
+            const double dv = (j21 * f1 - j11 * f2) * idet;
+            const double Wn = W + dW;
+            const double vn = fmin(fmax(vsq + dv, 0.0), C2P_VSQMAX);
+            if (!(Wn > 0.0)) break;
+            const double err = fabs(Wn - W) + fabs(vn - vsq) * Wn;
+            W = Wn;
+            vsq = vn;
+            if (err < C2P_TOL * Wn) {
+                ok = true;
+                break;
+            }
+        }
+        if (it > C2P_NMAX) it = C2P_NMAX;
+    }
+    if (iters) *iters = it;
+    double rho = 0.0, u = 0.0;
+    if (ok) {
+        const double omv = 1.0 - vsq;
+        const double sq = sqrt(omv);
+        rho = D * sq;
+        u = gfac * (W * omv - D * sq) / (gam - 1.0);
+        ok = (rho > 0.0) && (u > 0.0);
+    }
+    int status = INV_OK;
+    if (!ok) {
+        const double kappa = U[C_ENT] / U[C_RHO];
+        const double gr = gam / (gam - 1.0);
+        W = W0;
+        bool eok = false;
+        for (int k = 1; k <= C2P_NMAX; k++) {
+            const double W2 = W * W;
+            const double BW = Bsq + W;
+            const double num = Qtsq * W2 + QB2 * (Bsq + 2.0 * W);
+            const double den = W2 * BW * BW;
+            const double iden = 1.0 / den;
+            double vs = num * iden;
+            double dvs = (2.0 * (Qtsq * W + QB2) - num * 2.0 * W * BW * (Bsq + 2.0 * W) * iden) * iden;
+            if (vs > C2P_VSQMAX) {
+                vs = C2P_VSQMAX;
+                dvs = 0.0;
+            }
+            const double s1 = 1.0 - vs;
+            const double sq = sqrt(s1);
+            const double rh = D * sq;
+            const double p = kappa * pow(rh, gam);
+            const double f = W * s1 - rh - gr * p;
+            const double drh = -0.5 * D / sq * dvs;
+            const double df = s1 - W * dvs - drh * (1.0 + gr * gam * p / rh);
+            const double Wn = W - f / df;
+            if (!(Wn > 0.0)) break;
+            const double err = fabs(Wn - W);
+            W = Wn;
+            if (err < C2P_TOL * Wn) {
+                eok = true;
+                break;
+            }
+        }
+        if (eok) {
+            const double W2 = W * W;
+            const double BW = Bsq + W;
+            vsq = fmin((Qtsq * W2 + QB2 * (Bsq + 2.0 * W)) / (W2 * BW * BW), C2P_VSQMAX);
+            const double sq = sqrt(1.0 - vsq);
+            rho = D * sq;
+            u = kappa * pow(rho, gam) / (gam - 1.0);
+            eok = (rho > 0.0) && (u > 0.0) && (vsq >= 0.0);
+        }
+        if (!eok) return INV_FAIL;
+        status = INV_ENTROPY;
+    }
+    // utilde^i = Gamma/(W + B^2) (Qt^i + (Q.B) Bn^i / W), Qt^i = Q^i - alpha g^{ti} (Q.n)
+    const double gamma = rsqrt(1.0 - vsq);
+    const double pre = gamma / (W + Bsq);
+    const double qbw = QdotB / W;
+    pr[U1] = pre * (Qc1 - al * m.c01 * Qdotn + qbw * Bn1);
+    pr[U2] = pre * (Qc2 + qbw * Bn2);
+    pr[U3] = pre * (Qc3 + qbw * Bn3);
+    pr[RHO] = rho;
+    pr[UU] = u;
+    return status;
+}
+
+}  // namespace hamr

@@ -1,0 +1,540 @@
+// step.cu -- the per-block stage kernels of the midpoint step
+// (Liska et al. 2019, Sec. 2.1 and 2.5-2.7).
+//
+// One stage = boundary conditions (3 passes) -> per direction: edge values
+// (reconstruction) and face fluxes -> edge EMFs -> CT face update ->
+// cell update + inversion + floors (+ CFL reduction in the corrector).
+// Fluxes, EMFs and edge values go through HBM: the FP64 path is bound by the
+// FP64 pipe, so every face flux and every parabola is computed exactly once
+// and re-read from memory instead of recomputed in a halo.
+#include "c2p.cuh"
+#include "grmhd.cuh"
+#include "hamr_internal.h"
+
+namespace hamr {
+namespace {
+
+constexpr int BS = 128;
+
+__device__ __forceinline__ long cidx(const BlockView& v, int i, int j, int k) {
+    return ((long)(k + NG) * v.n2p + (j + NG)) * v.n1p + (i + NG);
+}
+__device__ __forceinline__ long gidx(const BlockView& v, int i, int j) { return (long)(j + NG) * v.n1p + (i + NG); }
+
+inline unsigned nblk(long n) { return (unsigned)((n + BS - 1) / BS); }
+
+// ---------------------------------------------------------------- centre B
+// B^i = (Bbar^i_lo + Bbar^i_hi) / 2 / sqrt(-g)_centre (Sec. 2.5)
+__device__ __forceinline__ void centre_field(const BlockView& v, const double* __restrict__ B, int i, int j, int k,
+                                             double gdet, double Bc[3]) {
+    const long c = cidx(v, i, j, k);
+    const double ig = 1.0 / gdet;
+    Bc[0] = 0.5 * (B[c] + B[c + 1]) * ig;
+    Bc[1] = 0.5 * (B[v.nc + c] + B[v.nc + c + v.n1p]) * ig;
+    Bc[2] = 0.5 * (B[2 * v.nc + c] + B[2 * v.nc + c + (long)v.n1p * v.n2p]) * ig;
+}
+
+__global__ void k_centre_b(BlockView v, double* __restrict__ P, const double* __restrict__ B) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long n = (long)v.n1 * v.n2 * v.n3;
+    if (t >= n) return;
+    const int i = (int)(t % v.n1), j = (int)((t / v.n1) % v.n2), k = (int)(t / ((long)v.n1 * v.n2));
+    double Bc[3];
+    centre_field(v, B, i, j, k, v.gc[G_DET * v.n2d + gidx(v, i, j)], Bc);
+    const long c = cidx(v, i, j, k);
+    P[B1 * v.nc + c] = Bc[0];
+    P[B2 * v.nc + c] = Bc[1];
+    P[B3 * v.nc + c] = Bc[2];
+}
+
+// ---------------------------------------------------------------- boundaries
+// One pass per direction e, in the order x3, x2, x1, each over the full
+// padded extent of the other two directions. Polar (x2): ghost (j = -1-m, k)
+// takes (j = m, k + n3/2) with utilde^2, B^2 and Bbar^2 negated; axis faces 0.
+// Outflow: copy of the last interior cell/face; NOINFLOW clamps utilde^1.
+// Periodic: wrap; face n takes face 0.
+__device__ __forceinline__ int cell_src(int bc, int n, int g) {
+    if (bc == HAMR_BC_PERIODIC) return g < 0 ? g + n : g - n;
+    if (bc == HAMR_BC_POLAR) return g < 0 ? -1 - g : 2 * n - 1 - g;
+    return g < 0 ? 0 : n - 1;
+}
+__device__ __forceinline__ int face_src(int bc, int n, int g) {
+    if (bc == HAMR_BC_PERIODIC) return g < 0 ? g + n : g - n;
+    if (bc == HAMR_BC_POLAR) return g < 0 ? -g : 2 * n - g;
+    return g < 0 ? 0 : n;
+}
+
+__global__ void k_bc_pass(BlockView v, double* __restrict__ P, double* __restrict__ B, int e) {
+    const int nn[4] = {0, v.n1, v.n2, v.n3};
+    const int ta = (e == 1) ? 2 : 1, tb = (e == 3) ? 2 : 3;
+    const int na = nn[ta] + 2 * NG, nb = nn[tb] + 2 * NG;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long total = 2L * NG * na * nb;
+    if (t >= total) return;
+    const int a = (int)(t % na) - NG;
+    const int b = (int)((t / na) % nb) - NG;
+    const int m = (int)((t / ((long)na * nb)) % NG);
+    const int side = (int)(t / ((long)na * nb * NG));
+    const int bc = v.bc[2 * (e - 1) + side];
+    const bool polar = (bc == HAMR_BC_POLAR);
+    int ss[4] = {0, 0, 0, 0}, dd[4] = {0, 0, 0, 0};
+    ss[ta] = a;
+    ss[tb] = b;
+    if (polar) ss[3] = ((b + v.n3 / 2) % v.n3 + v.n3) % v.n3;
+    dd[ta] = a;
+    dd[tb] = b;
+    const int gi = (side == 0) ? -1 - m : nn[e] + m;
+    dd[e] = gi;
+    ss[e] = cell_src(bc, nn[e], gi);
+    long dst = cidx(v, dd[1], dd[2], dd[3]), src = cidx(v, ss[1], ss[2], ss[3]);
+#pragma unroll
+    for (int q = 0; q < NPRIM; q++) {
+        double x = P[q * v.nc + src];
+        if (polar && (q == U2 || q == B2)) x = -x;
+        if (q == U1 && bc == HAMR_BC_OUTFLOW_NOINFLOW && e == 1) {
+            if (side == 1 && x < 0.0) x = 0.0;
+            if (side == 0 && x > 0.0) x = 0.0;
+        }
+        P[q * v.nc + dst] = x;
+    }
+#pragma unroll
+    for (int f = 1; f <= 3; f++)
+        if (f != e) B[(f - 1) * v.nc + dst] = B[(f - 1) * v.nc + src];
+    const int gf = (side == 0) ? -1 - m : nn[e] + (bc == HAMR_BC_PERIODIC ? 0 : 1) + m;
+    if (gf < nn[e] + NG) {
+        dd[e] = gf;
+        ss[e] = face_src(bc, nn[e], gf);
+        dst = cidx(v, dd[1], dd[2], dd[3]);
+        src = cidx(v, ss[1], ss[2], ss[3]);
+        const double x = B[(e - 1) * v.nc + src];
+        B[(e - 1) * v.nc + dst] = polar ? -x : x;
+    }
+}
+
+// axis faces hold 0 (after the x2 pass wrote its ghosts)
+__global__ void k_bc_axis(BlockView v, double* __restrict__ B) {
+    const int na = v.n1 + 2 * NG, nb = v.n3 + 2 * NG;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2L * na * nb) return;
+    const int i = (int)(t % na) - NG;
+    const int k = (int)((t / na) % nb) - NG;
+    const int side = (int)(t / ((long)na * nb));
+    if (v.bc[2 + side] != HAMR_BC_POLAR) return;
+    B[v.nc + cidx(v, i, side == 0 ? 0 : v.n2, k)] = 0.0;
+}
+
+// ---------------------------------------------------------------- reconstruction
+// edge values of every cell that borders a flux face of direction dir:
+// cells -1..n_dir along dir, -1..n_e across.
+template <int DIR>
+__global__ void k_recon(BlockView v, PhysArgs ph, const double* __restrict__ P, double* __restrict__ QL,
+                        double* __restrict__ QR) {
+    const int nn[4] = {0, v.n1, v.n2, v.n3};
+    const int e1 = nn[1] + 2, e2 = nn[2] + 2, e3 = nn[3] + 2;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)e1 * e2 * e3) return;
+    const int i = (int)(t % e1) - 1, j = (int)((t / e1) % e2) - 1, k = (int)(t / ((long)e1 * e2)) - 1;
+    const long c = cidx(v, i, j, k);
+    const long st = (DIR == 1) ? 1 : ((DIR == 2) ? (long)v.n1p : (long)v.n1p * v.n2p);
+#pragma unroll
+    for (int q = 0; q < NPRIM; q++) {
+        if (q == B1 + DIR - 1) continue;
+        const double* p = P + q * v.nc + c;
+        double l, r;
+        if (ph.recon == HAMR_RECON_PPM) {
+            const double s[5] = {p[-2 * st], p[-st], p[0], p[st], p[2 * st]};
+            ppm_cell(s, l, r);
+        } else {
+            const double qm = p[-st], q0 = p[0], qp = p[st];
+            const double dq = (ph.recon == HAMR_RECON_MC) ? mc_slope(qm, q0, qp) : minmod_slope(qm, q0, qp);
+            l = q0 - 0.5 * dq;
+            r = q0 + 0.5 * dq;
+        }
+        QL[q * v.nc + c] = l;
+        QR[q * v.nc + c] = r;
+    }
+}
+
+// ---------------------------------------------------------------- fluxes
+// HLLE (or LLF) flux through every dir-face: faces 0..n_dir, -1..n_e across.
+template <int DIR>
+__global__ void __launch_bounds__(BS) k_flux(BlockView v, PhysArgs ph, const double* __restrict__ QL,
+                                             const double* __restrict__ QR, const double* __restrict__ Bf,
+                                             double* __restrict__ F) {
+    const int nn[4] = {0, v.n1, v.n2, v.n3};
+    const int e1 = (DIR == 1) ? nn[1] + 1 : nn[1] + 2;
+    const int e2 = (DIR == 2) ? nn[2] + 1 : nn[2] + 2;
+    const int e3 = (DIR == 3) ? nn[3] + 1 : nn[3] + 2;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)e1 * e2 * e3) return;
+    const int i = (int)(t % e1) - (DIR == 1 ? 0 : 1);
+    const int j = (int)((t / e1) % e2) - (DIR == 2 ? 0 : 1);
+    const int k = (int)(t / ((long)e1 * e2)) - (DIR == 3 ? 0 : 1);
+    const long c = cidx(v, i, j, k);
+    const long st = (DIR == 1) ? 1 : ((DIR == 2) ? (long)v.n1p : (long)v.n1p * v.n2p);
+    const double* tab = (DIR == 1) ? v.gf1 : ((DIR == 2) ? v.gf2 : v.gc);
+    Metric<double> m;
+    load_metric(tab, v.n2d, gidx(v, i, j), m);
+    if (m.gdet == 0.0) {  // face on the polar axis: no area
+#pragma unroll
+        for (int q = 0; q < NFLUX; q++) F[q * v.nc + c] = 0.0;
+        return;
+    }
+    double pl[NPRIM], pr[NPRIM];
+#pragma unroll
+    for (int q = 0; q < NPRIM; q++) {
+        if (q == B1 + DIR - 1) continue;
+        pl[q] = QR[q * v.nc + c - st];
+        pr[q] = QL[q * v.nc + c];
+    }
+    const double bn = Bf[(DIR - 1) * v.nc + c] / m.gdet;
+    pl[B1 + DIR - 1] = bn;
+    pr[B1 + DIR - 1] = bn;
+    const double gam = ph.gam;
+    double UL[NFLUX], FL[NFLUX], UR[NFLUX], FR[NFLUX];
+    double vpl, vml, vpr, vmr;
+    {
+        Fluid<double> s;
+        fluid_state(pl, m, s);
+        const double kap = entropy_kappa(pl, gam);
+        flux_row(pl, s, 0, DIR, gam, kap, UL);
+        flux_row(pl, s, DIR, DIR, gam, kap, FL);
+        wave_speeds(pl, s, m, DIR, gam, vpl, vml);
+    }
+    {
+        Fluid<double> s;
+        fluid_state(pr, m, s);
+        const double kap = entropy_kappa(pr, gam);
+        flux_row(pr, s, 0, DIR, gam, kap, UR);
+        flux_row(pr, s, DIR, DIR, gam, kap, FR);
+        wave_speeds(pr, s, m, DIR, gam, vpr, vmr);
+    }
+    // U's B slots: B^i for the transverse i (flux_row with d = 0 gives b^i u^t - b^t u^i = B^i)
+    const double cmax = fmax(0.0, fmax(vpl, vpr));
+    const double cmin = fmax(0.0, fmax(-vml, -vmr));
+    if (ph.riemann == HAMR_FLUX_LLF) {
+        const double cm = fmax(cmax, cmin);
+#pragma unroll
+        for (int q = 0; q < NFLUX; q++) F[q * v.nc + c] = 0.5 * (FL[q] + FR[q] - cm * (UR[q] - UL[q])) * m.gdet;
+    } else if (cmax + cmin > 0.0) {
+        const double w = m.gdet / (cmax + cmin);
+        const double cc = cmax * cmin;
+#pragma unroll
+        for (int q = 0; q < NFLUX; q++) F[q * v.nc + c] = (cmin * FR[q] + cmax * FL[q] - cc * (UR[q] - UL[q])) * w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < NFLUX; q++) F[q * v.nc + c] = 0.5 * (FL[q] + FR[q]) * m.gdet;
+    }
+}
+
+// ---------------------------------------------------------------- EMFs
+// edge EMFs as the average of the 4 neighbouring face fluxes of B (Sec. 2.5).
+// E1 and E3 on the polar axis are 0.
+__global__ void k_emf(BlockView v, const double* __restrict__ F1, const double* __restrict__ F2,
+                      const double* __restrict__ F3, double* __restrict__ E) {
+    const int e1 = v.n1 + 1, e2 = v.n2 + 1, e3 = v.n3 + 1;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)e1 * e2 * e3) return;
+    const int i = (int)(t % e1), j = (int)((t / e1) % e2), k = (int)(t / ((long)e1 * e2));
+    const long c = cidx(v, i, j, k);
+    const long sj = v.n1p, sk = (long)v.n1p * v.n2p, nc = v.nc;
+    const bool axis = (v.bc[2] == HAMR_BC_POLAR && j == 0) || (v.bc[3] == HAMR_BC_POLAR && j == v.n2);
+    // flux slots: F1 -> (B2: 6, B3: 7), F2 -> (B1: 6, B3: 7), F3 -> (B1: 6, B2: 7)
+    if (i < v.n1) {
+        const double x = 0.25 * (F3[7 * nc + c] + F3[7 * nc + c - sj] - F2[7 * nc + c - sk] - F2[7 * nc + c]);
+        E[c] = axis ? 0.0 : x;
+    }
+    if (j < v.n2) {
+        E[nc + c] = 0.25 * (F1[7 * nc + c - sk] + F1[7 * nc + c] - F3[6 * nc + c] - F3[6 * nc + c - 1]);
+    }
+    if (k < v.n3) {
+        const double x = 0.25 * (F2[6 * nc + c - 1] + F2[6 * nc + c] - F1[6 * nc + c] - F1[6 * nc + c - sj]);
+        E[2 * nc + c] = axis ? 0.0 : x;
+    }
+}
+
+// ---------------------------------------------------------------- CT
+// staggered face update Bbar += dt curl E (Sec. 2.5, the three CT equations)
+__global__ void k_ct(BlockView v, const double* __restrict__ E, const double* Bb, double* Bo,
+                     const double* __restrict__ dscal, double fac) {
+    const int e1 = v.n1 + 1, e2 = v.n2 + 1, e3 = v.n3 + 1;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)e1 * e2 * e3) return;
+    const int i = (int)(t % e1), j = (int)((t / e1) % e2), k = (int)(t / ((long)e1 * e2));
+    const long c = cidx(v, i, j, k);
+    const long sj = v.n1p, sk = (long)v.n1p * v.n2p, nc = v.nc;
+    const double dt = dscal[0] * fac;
+    const double* E1 = E;
+    const double* E2 = E + nc;
+    const double* E3 = E + 2 * nc;
+    if (j < v.n2 && k < v.n3) {
+        const double r = (E2[c + sk] - E2[c]) * v.idx3 - (E3[c + sj] - E3[c]) * v.idx2;
+        Bo[c] = Bb[c] + dt * r;
+    }
+    if (i < v.n1 && k < v.n3) {
+        const bool axis = (v.bc[2] == HAMR_BC_POLAR && j == 0) || (v.bc[3] == HAMR_BC_POLAR && j == v.n2);
+        const double r = (E3[c + 1] - E3[c]) * v.idx1 - (E1[c + sk] - E1[c]) * v.idx3;
+        Bo[nc + c] = axis ? 0.0 : Bb[nc + c] + dt * r;
+    }
+    if (i < v.n1 && j < v.n2) {
+        const double r = (E1[c + sj] - E1[c]) * v.idx2 - (E2[c + 1] - E2[c]) * v.idx1;
+        Bo[2 * nc + c] = Bb[2 * nc + c] + dt * r;
+    }
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_max(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// sum_i v_f^i / dx^i at a cell centre (Sec. 2.1 CFL condition)
+__device__ __forceinline__ double inv_dt_cell(const BlockView& v, const double pr[NPRIM], const Metric<double>& m,
+                                              double gam) {
+    Fluid<double> s;
+    fluid_state(pr, m, s);
+    double vp, vm, inv = 0.0;
+    wave_speeds(pr, s, m, 1, gam, vp, vm);
+    inv += fmax(fabs(vp), fabs(vm)) * v.idx1;
+    wave_speeds(pr, s, m, 2, gam, vp, vm);
+    inv += fmax(fabs(vp), fabs(vm)) * v.idx2;
+    wave_speeds(pr, s, m, 3, gam, vp, vm);
+    inv += fmax(fabs(vp), fabs(vm)) * v.idx3;
+    return inv;
+}
+
+// ---------------------------------------------------------------- cell update
+// U = U(P^n) + dts (Q(Pf) - div F); inversion with guess Pf; floors;
+// the corrector also reduces the CFL rate of the new state.
+__global__ void __launch_bounds__(BS) k_update(BlockView v, PhysArgs ph, int corrector, const double* Pb,
+                                               const double* __restrict__ Pf, const double* __restrict__ F1,
+                                               const double* __restrict__ F2, const double* __restrict__ F3,
+                                               const double* __restrict__ Bn, double* Un, double* Po,
+                                               uint8_t* __restrict__ status, const double* __restrict__ dscal,
+                                               double fac, unsigned long long* dmax, unsigned long long* dcnt) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long n = (long)v.n1 * v.n2 * v.n3;
+    const bool active = t < n;
+    double inv = 0.0;
+    int st = -1, fl = 0;
+    if (active) {
+        const int i = (int)(t % v.n1), j = (int)((t / v.n1) % v.n2), k = (int)(t / ((long)v.n1 * v.n2));
+        const long c = cidx(v, i, j, k);
+        const long g = gidx(v, i, j);
+        const long nc = v.nc;
+        const double gam = ph.gam;
+        Metric<double> m;
+        load_metric(v.gc, v.n2d, g, m);
+        // U^n
+        double U[NCONS];
+        if (!corrector) {
+            double pb[NPRIM];
+#pragma unroll
+            for (int q = 0; q < NPRIM; q++) pb[q] = Pb[q * nc + c];
+            Fluid<double> s;
+            fluid_state(pb, m, s);
+            double row[NFLUX];
+            flux_row(pb, s, 0, 1, gam, entropy_kappa(pb, gam), row);
+#pragma unroll
+            for (int q = 0; q < NCONS; q++) {
+                U[q] = row[q] * m.gdet;
+                Un[q * nc + c] = U[q];
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < NCONS; q++) U[q] = Un[q * nc + c];
+        }
+        double pf[NPRIM];
+#pragma unroll
+        for (int q = 0; q < NPRIM; q++) pf[q] = Pf[q * nc + c];
+        // source sqrt(-g) T^k_l Gamma^l_{nu k} at the centre, from Pf
+        double Q[4];
+        {
+            Fluid<double> s;
+            fluid_state(pf, m, s);
+            const double p = (gam - 1.0) * pf[UU];
+            const double eta = pf[RHO] + pf[UU] + p + s.bsq;
+            const double ptot = p + 0.5 * s.bsq;
+            double T[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; a++)
+#pragma unroll
+                for (int b = 0; b < 4; b++)
+                    T[a][b] = eta * s.ucon[a] * s.ucov[b] - s.bcon[a] * s.bcov[b] + ((a == b) ? ptot : 0.0);
+            const double* cn = v.gc + (long)C_CONN * v.n2d + g;
+#pragma unroll
+            for (int nu = 0; nu < 4; nu++) {
+                double acc = 0.0;
+#pragma unroll
+                for (int l = 0; l < 4; l++)
+#pragma unroll
+                    for (int kk = 0; kk < 4; kk++) acc += T[kk][l] * cn[(l * 10 + sym(nu, kk)) * v.n2d];
+                Q[nu] = acc * m.gdet;
+            }
+        }
+        const double dts = dscal[0] * fac;
+        const long sj = v.n1p, sk = (long)v.n1p * v.n2p;
+#pragma unroll
+        for (int q = 0; q < NCONS; q++) {
+            const double div = (F1[q * nc + c + 1] - F1[q * nc + c]) * v.idx1 +
+                               (F2[q * nc + c + sj] - F2[q * nc + c]) * v.idx2 +
+                               (F3[q * nc + c + sk] - F3[q * nc + c]) * v.idx3;
+            const double src = (q >= C_EN && q <= C_S3) ? Q[q - C_EN] : 0.0;
+            U[q] = U[q] + dts * (src - div);
+        }
+        double Bc[3];
+        centre_field(v, Bn, i, j, k, m.gdet, Bc);
+        double pr[NPRIM];
+#pragma unroll
+        for (int q = 0; q < NPRIM; q++) pr[q] = pf[q];
+        pr[B1] = Bc[0];
+        pr[B2] = Bc[1];
+        pr[B3] = Bc[2];
+        int its;
+        st = invert(U, Bc, m, gam, pr, &its, false);
+        uint8_t sb = (st == INV_ENTROPY) ? ST_ENTROPY : ((st == INV_FAIL) ? ST_FAIL : 0);
+        if (ph.floors) {
+            Fluid<double> s;
+            fluid_state(pr, m, s);
+            const double rf = fmax(v.gc[C_RHOFLR * v.n2d + g], s.bsq * (1.0 / 50.0));
+            const double uf = fmax(v.gc[C_UFLR * v.n2d + g], s.bsq * (1.0 / 750.0));
+            if (pr[RHO] < rf) {
+                pr[RHO] = rf;
+                fl = 1;
+            }
+            if (pr[UU] < uf) {
+                pr[UU] = uf;
+                fl = 1;
+            }
+            if (fl) sb |= ST_FLOOR;
+        }
+#pragma unroll
+        for (int q = 0; q < NPRIM; q++) Po[q * nc + c] = pr[q];
+        status[c] |= sb;
+        if (corrector) inv = inv_dt_cell(v, pr, m, gam);
+    }
+    // warp-aggregated counters and CFL max
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned long long c_ok = warp_sum((unsigned long long)(st == INV_OK));
+    const unsigned long long c_en = warp_sum((unsigned long long)(st == INV_ENTROPY));
+    const unsigned long long c_fa = warp_sum((unsigned long long)(st == INV_FAIL));
+    const unsigned long long c_fl = warp_sum((unsigned long long)fl);
+    const double wmax = warp_max(inv);
+    if (lane == 0) {
+        if (c_ok) atomicAdd(&dcnt[0], c_ok);
+        if (c_en) atomicAdd(&dcnt[1], c_en);
+        if (c_fa) atomicAdd(&dcnt[2], c_fa);
+        if (c_fl) atomicAdd(&dcnt[3], c_fl);
+        if (corrector && wmax > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(wmax));
+    }
+}
+
+__global__ void k_dt_reduce(BlockView v, PhysArgs ph, const double* __restrict__ P, unsigned long long* dmax) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long n = (long)v.n1 * v.n2 * v.n3;
+    double inv = 0.0;
+    if (t < n) {
+        const int i = (int)(t % v.n1), j = (int)((t / v.n1) % v.n2), k = (int)(t / ((long)v.n1 * v.n2));
+        const long c = cidx(v, i, j, k);
+        Metric<double> m;
+        load_metric(v.gc, v.n2d, gidx(v, i, j), m);
+        double pr[NPRIM];
+#pragma unroll
+        for (int q = 0; q < NPRIM; q++) pr[q] = P[q * v.nc + c];
+        inv = inv_dt_cell(v, pr, m, ph.gam);
+    }
+    const double wmax = warp_max(inv);
+    if ((threadIdx.x & 31u) == 0 && wmax > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(wmax));
+}
+
+// dt of this step: the caller's, or C0 / max rate of the current state;
+// resets the accumulators of the new step.
+__global__ void k_dt_select(double cour, double user_dt, double* dscal, unsigned long long* dmax,
+                            unsigned long long* dcnt) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double mx = __longlong_as_double((long long)dmax[0]);
+    dscal[0] = (user_dt > 0.0) ? user_dt : cour / mx;
+    dmax[0] = 0ull;
+    dcnt[0] = dcnt[1] = dcnt[2] = dcnt[3] = 0ull;
+}
+
+}  // namespace
+
+cudaError_t launch_centre_b(const BlockView& v, double* P, const double* B, cudaStream_t s) {
+    k_centre_b<<<nblk((long)v.n1 * v.n2 * v.n3), BS, 0, s>>>(v, P, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bc(const BlockView& v, double* P, double* B, cudaStream_t s) {
+    const int nn[4] = {0, v.n1, v.n2, v.n3};
+    for (int e = 3; e >= 1; e--) {
+        const int ta = (e == 1) ? 2 : 1, tb = (e == 3) ? 2 : 3;
+        const long total = 2L * NG * (nn[ta] + 2 * NG) * (nn[tb] + 2 * NG);
+        k_bc_pass<<<nblk(total), BS, 0, s>>>(v, P, B, e);
+        if (e == 2) k_bc_axis<<<nblk(2L * (v.n1 + 2 * NG) * (v.n3 + 2 * NG)), BS, 0, s>>>(v, B);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_recon(const BlockView& v, const PhysArgs& ph, int dir, const double* P, double* QL, double* QR,
+                         cudaStream_t s) {
+    const long n = (long)(v.n1 + 2) * (v.n2 + 2) * (v.n3 + 2);
+    if (dir == 1) k_recon<1><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
+    if (dir == 2) k_recon<2><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
+    if (dir == 3) k_recon<3><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flux(const BlockView& v, const PhysArgs& ph, int dir, const double* QL, const double* QR,
+                        const double* Bf, double* F, cudaStream_t s) {
+    const long n1 = v.n1 + (dir == 1 ? 1 : 2), n2 = v.n2 + (dir == 2 ? 1 : 2), n3 = v.n3 + (dir == 3 ? 1 : 2);
+    const long n = n1 * n2 * n3;
+    if (dir == 1) k_flux<1><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
+    if (dir == 2) k_flux<2><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
+    if (dir == 3) k_flux<3><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emf(const BlockView& v, double* const F[3], double* E, cudaStream_t s) {
+    const long n = (long)(v.n1 + 1) * (v.n2 + 1) * (v.n3 + 1);
+    k_emf<<<nblk(n), BS, 0, s>>>(v, F[0], F[1], F[2], E);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ct(const BlockView& v, const double* E, const double* Bbase, double* Bout, const double* dscal,
+                      double dt_factor, cudaStream_t s) {
+    const long n = (long)(v.n1 + 1) * (v.n2 + 1) * (v.n3 + 1);
+    k_ct<<<nblk(n), BS, 0, s>>>(v, E, Bbase, Bout, dscal, dt_factor);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(const BlockView& v, const PhysArgs& ph, int corrector, const double* Pbase,
+                          const double* Pflux, double* const F[3], const double* Bnew, double* Un, double* Pout,
+                          uint8_t* status, const double* dscal, double dt_factor, unsigned long long* dmax,
+                          unsigned long long* dcnt, cudaStream_t s) {
+    const long n = (long)v.n1 * v.n2 * v.n3;
+    k_update<<<nblk(n), BS, 0, s>>>(v, ph, corrector, Pbase, Pflux, F[0], F[1], F[2], Bnew, Un, Pout, status, dscal,
+                                    dt_factor, dmax, dcnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dt_reduce(const BlockView& v, const PhysArgs& ph, const double* P, unsigned long long* dmax,
+                             cudaStream_t s) {
+    k_dt_reduce<<<nblk((long)v.n1 * v.n2 * v.n3), BS, 0, s>>>(v, ph, P, dmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dt_select(const PhysArgs& ph, double user_dt, double* dscal, unsigned long long* dmax,
+                             unsigned long long* dcnt, uint8_t* status, long nc, cudaStream_t s) {
+    k_dt_select<<<1, 32, 0, s>>>(ph.cour, user_dt, dscal, dmax, dcnt);
+    cudaMemsetAsync(status, 0, (size_t)nc, s);
+    return cudaGetLastError();
+}
+
+}  // namespace hamr

@@ -1,0 +1,217 @@
+"""Thin ctypes binding of libhamr.so (the C ABI of include/hamr.h).
+
+Argument marshalling only: every step of the update runs in the library's
+CUDA kernels. Device memory and streams come from PyTorch (tensor data
+pointers and torch.cuda streams). The binding fails loudly if the library is
+missing; there is no CPU fallback.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhamr.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "hamr.h")
+
+OK, EINVAL, ECUDA, ENOMEM, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
+METRIC_KS, METRIC_MINKOWSKI = 0, 1
+RECON_PPM, RECON_MC, RECON_MINMOD = 0, 1, 2
+FLUX_HLL, FLUX_LLF = 0, 1
+BC_OUTFLOW, BC_PERIODIC, BC_POLAR, BC_OUTFLOW_NOINFLOW = 0, 1, 2, 3
+PREC_FP64, PREC_MIXED = 0, 1
+C2P_ENTROPY_ONLY = 1
+NG = 3
+
+
+class HamrError(RuntimeError):
+    pass
+
+
+class BlockDesc(C.Structure):
+    _fields_ = [("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int),
+                ("x1min", C.c_double), ("x2min", C.c_double), ("x3min", C.c_double),
+                ("dx1", C.c_double), ("dx2", C.c_double), ("dx3", C.c_double),
+                ("bc", C.c_int * 6)]
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("metric", C.c_int), ("a", C.c_double), ("gam", C.c_double), ("cour", C.c_double),
+                ("recon", C.c_int), ("riemann", C.c_int), ("floors", C.c_int), ("precision", C.c_int),
+                ("nblocks", C.c_int), ("blocks", C.POINTER(BlockDesc))]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("c2p_ok", C.c_longlong), ("c2p_entropy", C.c_longlong), ("c2p_fail", C.c_longlong),
+                ("floor_hits", C.c_longlong), ("dt_used", C.c_double), ("dt_next", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KernelTime(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_longlong), ("ms", C.c_double)]
+
+
+class C2PDesc(C.Structure):
+    _fields_ = [("metric", C.c_int), ("a", C.c_double), ("gam", C.c_double), ("flags", C.c_uint32)]
+
+
+_lib = None
+
+
+def header_functions():
+    """Names of the functions include/hamr.h declares."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(hamr_\w+)\s*\(", txt, re.M)))
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise HamrError("libhamr.so is not built (run __graft_entry__.build()); no fallback exists")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        D = C.POINTER(C.c_double)
+        L.hamr_grid_create.argtypes = [C.POINTER(GridDesc), C.POINTER(C.c_void_p)]
+        L.hamr_grid_destroy.argtypes = [P]
+        L.hamr_grid_set_state.argtypes = [P, C.c_int, P, P, C.c_int, P]
+        L.hamr_grid_get_state.argtypes = [P, C.c_int, P, P, C.c_int, P]
+        L.hamr_block_step.argtypes = [P, C.c_int, C.c_double, P, C.POINTER(StepStats)]
+        L.hamr_batch_step.argtypes = [P, C.c_int, P, C.POINTER(StepStats)]
+        L.hamr_grid_stats.argtypes = [P, C.POINTER(StepStats)]
+        L.hamr_con2prim.argtypes = [C.POINTER(C2PDesc), C.c_int64, P, P, P, P, P, P, P, P]
+        L.hamr_grid_set_timing.argtypes = [P, C.c_int]
+        L.hamr_grid_timing.argtypes = [P, C.POINTER(KernelTime), C.c_int, C.POINTER(C.c_int)]
+        L.hamr_measure_fp64_peak.argtypes = [P, C.POINTER(C.c_double)]
+        L.hamr_last_error.argtypes = []
+        L.hamr_last_error.restype = C.c_char_p
+        for name in header_functions():
+            if name != "hamr_last_error":
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def check(rc):
+    if rc != OK:
+        raise HamrError("hamr error %d: %s" % (rc, lib().hamr_last_error().decode()))
+    return rc
+
+
+def _ptr(x):
+    """Device/host address of a torch tensor or numpy array (contiguous)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    assert x.is_contiguous()
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+def block(n1, n2, n3, x1min, x2min, x3min, dx1, dx2, dx3, bc):
+    b = BlockDesc()
+    b.n1, b.n2, b.n3 = n1, n2, n3
+    b.x1min, b.x2min, b.x3min = x1min, x2min, x3min
+    b.dx1, b.dx2, b.dx3 = dx1, dx2, dx3
+    for m in range(6):
+        b.bc[m] = bc[m]
+    return b
+
+
+class Grid:
+    """Owner of a hamr_grid handle."""
+
+    def __init__(self, blocks, metric=METRIC_KS, a=0.9375, gam=13.0 / 9.0, cour=0.8, recon=RECON_PPM,
+                 riemann=FLUX_HLL, floors=1, precision=PREC_FP64):
+        self._blocks = (BlockDesc * len(blocks))(*blocks)
+        d = GridDesc()
+        d.metric, d.a, d.gam, d.cour = metric, a, gam, cour
+        d.recon, d.riemann, d.floors, d.precision = recon, riemann, floors, precision
+        d.nblocks = len(blocks)
+        d.blocks = self._blocks
+        self.desc = d
+        h = C.c_void_p()
+        check(lib().hamr_grid_create(C.byref(d), C.byref(h)))
+        self.h = h
+        self.blocks = list(blocks)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().hamr_grid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def padded_shape(self, b=0):
+        B = self.blocks[b]
+        return (B.n3 + 2 * NG, B.n2 + 2 * NG, B.n1 + 2 * NG)
+
+    def set_state(self, prim, bface, block=0, stream=None):
+        on_dev = 0 if isinstance(prim, np.ndarray) else 1
+        check(lib().hamr_grid_set_state(self.h, block, _ptr(prim), _ptr(bface), on_dev, _stream(stream)))
+
+    def get_state(self, block=0, prim=None, bface=None, stream=None):
+        shp = self.padded_shape(block)
+        if prim is None:
+            prim = np.zeros((8,) + shp)
+        if bface is None:
+            bface = np.zeros((3,) + shp)
+        on_dev = 0 if isinstance(prim, np.ndarray) else 1
+        check(lib().hamr_grid_get_state(self.h, block, _ptr(prim), _ptr(bface), on_dev, _stream(stream)))
+        return prim, bface
+
+    def step(self, dt=-1.0, block=0, stream=None, stats=False):
+        st = StepStats() if stats else None
+        check(lib().hamr_block_step(self.h, block, float(dt), _stream(stream), C.byref(st) if stats else None))
+        return st.as_dict() if stats else None
+
+    def batch_step(self, n_fine_substeps, stream=None, stats=False):
+        st = StepStats() if stats else None
+        check(lib().hamr_batch_step(self.h, int(n_fine_substeps), _stream(stream), C.byref(st) if stats else None))
+        return st.as_dict() if stats else None
+
+    def set_timing(self, enable):
+        check(lib().hamr_grid_set_timing(self.h, int(bool(enable))))
+
+    def timing(self):
+        """{group: (launches, ms)} of the grid's kernel groups since the last reset."""
+        arr = (KernelTime * 16)()
+        n = C.c_int()
+        check(lib().hamr_grid_timing(self.h, arr, 16, C.byref(n)))
+        return {arr[k].name.decode(): (arr[k].launches, arr[k].ms) for k in range(min(n.value, 16))}
+
+    def stats(self):
+        st = StepStats()
+        check(lib().hamr_grid_stats(self.h, C.byref(st)))
+        return st.as_dict()
+
+
+def con2prim(U, B, x1, x2, prim, status, iters=None, metric=METRIC_KS, a=0.9375, gam=13.0 / 9.0, flags=0,
+             stream=None):
+    """Inverts n states in place on the device (SoA torch tensors: U (6, n), B (3, n), prim (8, n))."""
+    d = C2PDesc()
+    d.metric, d.a, d.gam, d.flags = metric, a, gam, flags
+    n = prim.shape[1]
+    check(lib().hamr_con2prim(C.byref(d), n, _ptr(U), _ptr(B), _ptr(x1), _ptr(x2), _ptr(prim), _ptr(status),
+                              _ptr(iters), _stream(stream)))
+
+
+def measure_fp64_peak(stream=None):
+    """Measured FP64 FMA rate of the current device in GFLOP/s."""
+    g = C.c_double()
+    check(lib().hamr_measure_fp64_peak(_stream(stream), C.byref(g)))
+    return g.value
