@@ -49,7 +49,7 @@ FLOPS_PER_ZONE_CYCLE = 4549.7    # one cell, one full step
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes per launch of the dominant kernel from one ncu capture of this
 # build (profiles/flux_torus256.md); None until captured for this build.
-NCU_TRAFFIC_PER_LAUNCH = None
+NCU_TRAFFIC_PER_LAUNCH = None  # set from profiles/flux_torus256.md once captured for this build
 
 
 def env_rank():
