@@ -174,6 +174,33 @@ int hamr_grid_timing(hamr_grid* g, hamr_kernel_time* out, int max, int* n);
  * roofline that bounds the FP64 update on this hardware. */
 int hamr_measure_fp64_peak(void* stream, double* gflops);
 
+/* ---- stepping without allocation ---- */
+/* Largest block hamr_block_step_noalloc accepts: padded cells
+ * (n1+6)(n2+6)(n3+6) and padded (i, j) points (n1+6)(n2+6). */
+#define HAMR_NOALLOC_MAX_CELLS 12288
+#define HAMR_NOALLOC_MAX_PLANE 1536
+
+/* One midpoint step of one block, like hamr_grid_set_state followed by
+ * hamr_block_step, for callers that cannot allocate device memory (a host
+ * framework that owns the device's memory pool, or code that must not call
+ * cudaMalloc once it runs). No paper counterpart: it is the same step with
+ * its scratch (geometry tables, midpoint state, edge values, fluxes, EMFs,
+ * U^n cache, counters) in one file-scope device array of about 7 MB, sized
+ * for blocks up to HAMR_NOALLOC_MAX_CELLS padded cells, which every GPU
+ * that loads the library holds until the process exits. It calls no
+ * cudaMalloc or cudaFree.
+ *   d: grid descriptor with nblocks == 1 (the block stepped); FP64 only.
+ *   prim, bface: device pointers, padded SoA layout; in: the state (centre B
+ *     slots recomputed from the faces, ghosts refilled), out: the state
+ *     after the step, valid once `stream` has completed.
+ *   dt: > 0 that step; <= 0 the CFL step of the input state.
+ * Blocks above the limits return HAMR_EINVAL with a message. The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make it before any stream capture. Every call
+ * shares the array: calls whose GPU work overlaps (other streams, other
+ * threads) race and must be serialised by the caller. */
+int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, double* bface, double dt, void* stream);
+
 /* ---- standalone inversion (Sec. 2.6) ---- */
 #define HAMR_C2P_ENTROPY_ONLY 1u /* skip the energy inversion (tests of the backup) */
 

@@ -110,6 +110,16 @@ enum { K_DT = 0, K_BC, K_RECON, K_FLUX, K_EMF, K_CT, K_UPDATE, K_LOAD };
 
 }  // namespace
 
+int hamr::set_error(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
 struct hamr_grid {
     Timer timer;
     hamr_grid_desc desc;

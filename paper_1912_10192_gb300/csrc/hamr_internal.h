@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "../../include/hamr.h"
 
 namespace hamr {
@@ -62,6 +64,9 @@ struct BlockState {
 };
 
 cudaError_t launch_geometry(const GeomArgs& A, cudaStream_t s);
+
+// api.cu: records the calling thread's last-error message and returns `code`
+int set_error(int code, const char* fmt, ...);
 
 // step.cu
 cudaError_t launch_centre_b(const BlockView& v, double* P, const double* B, cudaStream_t s);

@@ -86,6 +86,7 @@ def lib():
         L.hamr_grid_set_timing.argtypes = [P, C.c_int]
         L.hamr_grid_timing.argtypes = [P, C.POINTER(KernelTime), C.c_int, C.POINTER(C.c_int)]
         L.hamr_measure_fp64_peak.argtypes = [P, C.POINTER(C.c_double)]
+        L.hamr_block_step_noalloc.argtypes = [C.POINTER(GridDesc), P, P, C.c_double, P]
         L.hamr_last_error.argtypes = []
         L.hamr_last_error.restype = C.c_char_p
         for name in header_functions():
@@ -215,3 +216,9 @@ def measure_fp64_peak(stream=None):
     g = C.c_double()
     check(lib().hamr_measure_fp64_peak(_stream(stream), C.byref(g)))
     return g.value
+
+
+def block_step_noalloc(grid, prim, bface, dt=-1.0, stream=None):
+    """One step of `grid`'s single block through hamr_block_step_noalloc, on the
+    caller's device tensors `prim` (8, ...) and `bface` (3, ...) in place."""
+    check(lib().hamr_block_step_noalloc(C.byref(grid.desc), _ptr(prim), _ptr(bface), float(dt), _stream(stream)))
