@@ -256,3 +256,88 @@ def flops_phase():
     out = (C.c_ulonglong * 30)()
     lib(True).ora_flops_phase(out)
     return {p: list(out[5 * k:5 * k + 5]) for k, p in enumerate(PHASES)}
+
+BC_BLOCK = 4
+
+
+class Block(C.Structure):
+    _fields_ = [("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int),
+                ("x1min", C.c_double), ("x2min", C.c_double), ("x3min", C.c_double),
+                ("dx1", C.c_double), ("dx2", C.c_double), ("dx3", C.c_double),
+                ("bc", C.c_int * 6), ("lat", C.c_int)]
+
+
+def make_block(n1, n2, n3, x1min, x2min, x3min, dx1, dx2, dx3, bc, lat=0):
+    b = Block()
+    b.n1, b.n2, b.n3 = n1, n2, n3
+    b.x1min, b.x2min, b.x3min = x1min, x2min, x3min
+    b.dx1, b.dx2, b.dx3 = dx1, dx2, dx3
+    for m in range(6):
+        b.bc[m] = bc[m]
+    b.lat = lat
+    return b
+
+
+_amr_ready = set()
+
+
+def _amr_setup(L):
+    if id(L) in _amr_ready:
+        return
+    P = C.c_void_p
+    L.ora_amr_new.argtypes = [C.POINTER(Desc), C.c_int, C.POINTER(Block)]
+    L.ora_amr_new.restype = C.c_void_p
+    L.ora_amr_free.argtypes = [P]
+    L.ora_amr_set.argtypes = [P, C.c_int, _D, _D]
+    L.ora_amr_get.argtypes = [P, C.c_int, _D, _D]
+    L.ora_amr_fill.argtypes = [P]
+    L.ora_amr_period.argtypes = [P, C.c_double]
+    L.ora_amr_period.restype = C.c_double
+    L.ora_amr_stats.argtypes = [P, C.POINTER(C.c_longlong)]
+    for n in ("ora_amr_free", "ora_amr_set", "ora_amr_get", "ora_amr_fill", "ora_amr_stats"):
+        getattr(L, n).restype = None
+    _amr_ready.add(id(L))
+
+
+class AmrGrid:
+    """Multi-block oracle grid (static refinement + local adaptive time steps)."""
+
+    def __init__(self, phys, blocks, counting=False):
+        self.lib = lib(counting)
+        _amr_setup(self.lib)
+        self.blocks = list(blocks)
+        self._arr = (Block * len(blocks))(*blocks)
+        self.phys = phys
+        self.h = self.lib.ora_amr_new(C.byref(phys), len(blocks), self._arr)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.lib.ora_amr_free(self.h)
+            self.h = None
+
+    def shape(self, b):
+        B = self.blocks[b]
+        return (B.n3 + 2 * NG, B.n2 + 2 * NG, B.n1 + 2 * NG)
+
+    def set(self, b, prim, bface):
+        prim = np.ascontiguousarray(prim, dtype=np.float64)
+        bface = np.ascontiguousarray(bface, dtype=np.float64)
+        assert prim.shape == (8, *self.shape(b)) and bface.shape == (3, *self.shape(b))
+        self.lib.ora_amr_set(self.h, b, _p(prim), _p(bface))
+
+    def get(self, b):
+        prim = np.zeros((8, *self.shape(b)))
+        bface = np.zeros((3, *self.shape(b)))
+        self.lib.ora_amr_get(self.h, b, _p(prim), _p(bface))
+        return prim, bface
+
+    def fill(self):
+        self.lib.ora_amr_fill(self.h)
+
+    def period(self, dt_fine=-1.0):
+        return self.lib.ora_amr_period(self.h, dt_fine)
+
+    def stats(self):
+        s = (C.c_longlong * 4)()
+        self.lib.ora_amr_stats(self.h, s)
+        return list(s)

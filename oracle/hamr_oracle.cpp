@@ -753,19 +753,18 @@ void load_prim(const ora_grid* g, const double* P, long c, real* pr) {
     for (int v = 0; v < NPR; v++) pr[v] = P[v * g->ncell + c];
 }
 
-/* One stage of the midpoint scheme (Sec. 2.1, 2.5):
- *   fluxes, EMFs and sources from (Pf, Bff) [ghosts filled];
- *   Bf_out = Bf_base + dts * curl E;  U = U(P_base) + dts (-div F + Q);
- *   P_out = con2prim(U, centre B of Bf_out), guess Pf; floors. */
-void stage(ora_grid* g, const double* Pf, const double* Bff, const double* Pb, const double* Bfb,
-           double dts, double* Pout, double* Bfout) {
+/* A stage of the midpoint scheme (Sec. 2.1, 2.5) in its four phases:
+ *   stage_fluxes: edge values and face fluxes from (Pf, Bff) [ghosts filled];
+ *   stage_emf:    edge EMFs from the face fluxes;
+ *   stage_ct:     Bf_out = Bf_base + dts * curl E;
+ *   stage_update: U = U(P_base) + dts (-div F + Q(Pf)); P_out = con2prim(U,
+ *                 centre B of Bf_out) with guess Pf; floors. */
+typedef std::vector<double> Fluxes[4];
+
+void stage_fluxes(ora_grid* g, const double* Pf, const double* Bff, Fluxes& F) {
     const ora_desc& d = g->d;
     const long nc = g->ncell;
-    const int n1 = d.n1, n2 = d.n2, n3 = d.n3;
-    const int nn[4] = {0, n1, n2, n3};
-    const double dx[4] = {0.0, d.dx1, d.dx2, d.dx3};
-
-    std::vector<double> F[4];
+    const int nn[4] = {0, d.n1, d.n2, d.n3};
     for (int dir = 1; dir <= 3; dir++) F[dir].assign((size_t)NFX * nc, 0.0);
 
     /* fluxes: dir-faces over the interior faces, one transverse ghost layer */
@@ -830,11 +829,20 @@ void stage(ora_grid* g, const double* Pf, const double* Bff, const double* Pb, c
                 phase_end(1);
             }
     }
+}
 
-    /* EMFs at edges (Sec. 2.5, the 4-flux average). Reading: E1 and E3 on the
-     * polar axis are 0, which keeps Bbar^2 = 0 on axis faces and div B intact. */
+/* EMFs at edges (Sec. 2.5, the 4-flux average). Reading: E1 and E3 on the
+ * polar axis are 0, which keeps Bbar^2 = 0 on axis faces and div B intact.
+ * E holds three fields E1, E2, E3 (edge (i, j-1/2, k-1/2) etc. at index (i,j,k)). */
+void stage_emf(ora_grid* g, const Fluxes& F, std::vector<double>& E) {
+    const ora_desc& d = g->d;
+    const long nc = g->ncell;
+    const int n1 = d.n1, n2 = d.n2, n3 = d.n3;
     phase_begin();
-    std::vector<double> E1(nc, 0.0), E2(nc, 0.0), E3(nc, 0.0);
+    E.assign((size_t)3 * nc, 0.0);
+    double* E1 = E.data();
+    double* E2 = E.data() + nc;
+    double* E3 = E.data() + 2 * nc;
     auto FX = [&](int dir, int slot, int i, int j, int k) -> real {
         return real(F[dir][(size_t)slot * nc + cidx(g, i, j, k)]);
     };
@@ -863,8 +871,17 @@ void stage(ora_grid* g, const double* Pf, const double* Bff, const double* Pb, c
             }
 
     phase_end(2);
+}
+
+/* staggered face update (Sec. 2.5, the three CT equations) */
+void stage_ct(ora_grid* g, const std::vector<double>& E, const double* Bfb, double dts, double* Bfout) {
+    const ora_desc& d = g->d;
+    const long nc = g->ncell;
+    const int n1 = d.n1, n2 = d.n2, n3 = d.n3;
+    const double* E1 = E.data();
+    const double* E2 = E.data() + nc;
+    const double* E3 = E.data() + 2 * nc;
     phase_begin();
-    /* staggered face update (Sec. 2.5, the three CT equations) */
     for (int v = 0; v < 3; v++)
         for (long c = 0; c < nc; c++) Bfout[v * nc + c] = Bfb[v * nc + c];
     for (int k = 0; k <= n3; k++)
@@ -890,8 +907,16 @@ void stage(ora_grid* g, const double* Pf, const double* Bff, const double* Pb, c
             }
 
     phase_end(3);
+}
+
+/* cell update, inversion, floors */
+void stage_update(ora_grid* g, const Fluxes& F, const double* Pb, const double* Pf, const double* Bfout, double dts,
+                  double* Pout) {
+    const ora_desc& d = g->d;
+    const long nc = g->ncell;
+    const int n1 = d.n1, n2 = d.n2, n3 = d.n3;
+    const double dx[4] = {0.0, d.dx1, d.dx2, d.dx3};
     phase_begin();
-    /* cell update, inversion, floors */
     for (int k = 0; k < n3; k++)
         for (int j = 0; j < n2; j++)
             for (int i = 0; i < n1; i++) {
@@ -939,6 +964,16 @@ void stage(ora_grid* g, const double* Pf, const double* Bff, const double* Pb, c
                 for (int v = 0; v < NPR; v++) Pout[v * nc + c] = tod(pr[v]);
             }
     phase_end(4);
+}
+
+void stage(ora_grid* g, const double* Pf, const double* Bff, const double* Pb, const double* Bfb, double dts,
+           double* Pout, double* Bfout) {
+    Fluxes F;
+    std::vector<double> E;
+    stage_fluxes(g, Pf, Bff, F);
+    stage_emf(g, F, E);
+    stage_ct(g, E, Bfb, dts, Bfout);
+    stage_update(g, F, Pb, Pf, Bfout, dts, Pout);
 }
 
 /* CFL time step (Sec. 2.1): per cell 1/dt = sum_i v_f^i / dx^i with
@@ -1228,3 +1263,839 @@ void ora_flops_get(unsigned long long* out5) {
 }
 
 } /* extern "C" */
+
+/* ================================================================== */
+/* Multi-block grids: static refinement (Sec. 3.2) and local adaptive   */
+/* time stepping (Sec. 3.4)                                             */
+/* ================================================================== */
+/*
+ * Ghost zones (Sec. 3.2): a ghost cell's centre is mapped across the
+ * receiving block's physical boundaries (outflow: the nearest interior
+ * cell; periodic: shifted by the period; polar: mirrored theta, phi + pi,
+ * utilde^2 / B^2 / Bbar^2 negated), then looked up in the block that holds
+ * it. The value is sampled from that block per dimension:
+ *   same cell size   -> the cell itself,
+ *   source finer     -> the average of the source cells it covers
+ *                       (restriction),
+ *   source coarser   -> the source cell plus delta * MINMOD slope along that
+ *                       dimension (prolongation; delta = offset of the ghost
+ *                       centre in units of the source cell).
+ * Reading: a MINMOD slope whose stencil leaves the source block's interior
+ * is 0. Ghost faces are sampled the same way without slopes; along their
+ * normal they interpolate linearly between the source face planes.
+ *
+ * Time (Sec. 3.4): blocks of LAT level L step with 2^L dt_fine at the fine
+ * substeps s with s mod 2^L = 0, coarsest level first. A ghost of block b
+ * at stage time t samples a neighbour n of coarser level by linear
+ * interpolation between n's state at the start of its step and its new
+ * state; a neighbour of the same level at the same stage state (P or the
+ * midpoint state); a neighbour of finer level at its current state.
+ *
+ * Synchronisation (Sec. 3.2, 3.4): blocks of the same level stepped together
+ * share the flux of a face (the spatially coarser side takes the average of
+ * the finer side's faces) and the EMF of an edge (every block takes the
+ * EMF of the edge's dominant block: finest cell along the edge, then finest
+ * across it, then lowest index). Across levels, at the end of each coarse
+ * step the coarse block's face fluxes and edge EMFs are replaced by the time
+ * integrals of the finer level's (refluxing), and its cells next to the
+ * corrected faces are inverted again.
+ */
+namespace {
+
+const double AMR_PI = 3.14159265358979323846;
+
+struct FaceRec {  /* a coarse face refluxed from a finer-level block */
+    int c;        /* coarse block */
+    int d, side;  /* face direction, 0 = lower face of the block, 1 = upper */
+    int i, j, k;  /* face index in c (lower-face convention) */
+    int f;        /* fine block */
+    std::vector<long> ff; /* fine face indices (padded cell index) */
+    double own[NFX], acc[NFX];
+};
+struct EdgeRec { /* a coarse edge synchronised with the dominant edge of a finer level */
+    int c, e;     /* block, edge direction */
+    int i, j, k;  /* edge index in c */
+    int f;        /* dominant block */
+    std::vector<long> fe; /* its edge indices covering this edge */
+    double own, acc;
+};
+struct SyncRec { /* same-level synchronisation: dst value := average of src values */
+    int dst, d;
+    long di;
+    int src;
+    std::vector<long> si;
+};
+
+struct AmrBlk {
+    ora_grid* g;
+    int lat;
+    long s0;
+    double lo[4], hi[4], h[4];
+    std::vector<double> Pold, Bold, Ph, Bh;
+    Fluxes F;
+    std::vector<double> E;
+};
+
+}  // namespace
+
+struct ora_amr {
+    ora_desc phys;
+    std::vector<AmrBlk> b;
+    int Lmax;
+    double dlo[4], dhi[4];
+    bool per[4];
+    long s;  /* substeps taken in the current period */
+    std::vector<FaceRec> frec;
+    std::vector<EdgeRec> erec;
+    std::vector<SyncRec> fsync, esync;
+    long long stats[4];
+};
+
+namespace {
+
+int amr_find(const ora_amr* m, const double x[4]) {
+    for (int pass = 0; pass < 2; pass++)
+        for (int n = 0; n < (int)m->b.size(); n++) {
+            const AmrBlk& B = m->b[n];
+            bool in = true;
+            for (int d = 1; d <= 3 && in; d++) {
+                double tol = 1e-9 * B.h[d];
+                if (x[d] < B.lo[d] - tol) in = false;
+                if (pass == 0 ? !(x[d] < B.hi[d] - tol) : (x[d] > B.hi[d] + tol)) in = false;
+            }
+            if (in) return n;
+        }
+    return -1;
+}
+
+/* maps x (outside block b) across b's physical boundaries; fdir = normal
+ * direction of a face point (0 for a cell centre) */
+void amr_map(const ora_amr* m, int b, double x[4], int fdir, int* neg, int* clamp) {
+    const AmrBlk& B = m->b[b];
+    *neg = 0;
+    *clamp = 0;
+    for (int d = 1; d <= 3; d++) {
+        const double q = 0.25 * B.h[d];
+        int side = -1;
+        if (x[d] < B.lo[d] - q) side = 0;
+        if (x[d] > B.hi[d] + q) side = 1;
+        if (side < 0) continue;
+        const int bc = B.g->d.bc[2 * (d - 1) + side];
+        if (bc == ORA_BC_OUTFLOW || bc == ORA_BC_OUTFLOW_NOINFLOW) {
+            if (d == fdir)
+                x[d] = side ? B.hi[d] : B.lo[d];
+            else
+                x[d] = side ? B.hi[d] - 0.5 * B.h[d] : B.lo[d] + 0.5 * B.h[d];
+            if (bc == ORA_BC_OUTFLOW_NOINFLOW && d == 1) *clamp = side ? 1 : -1;
+        } else if (bc == ORA_BC_PERIODIC) {
+            x[d] += side ? -(m->dhi[d] - m->dlo[d]) : (m->dhi[d] - m->dlo[d]);
+        } else if (bc == ORA_BC_POLAR) {
+            x[2] = side ? 2.0 * AMR_PI - x[2] : -x[2];
+            x[3] += AMR_PI;
+            *neg = 1;
+        }
+    }
+    if (m->per[3]) {
+        const double L = m->dhi[3] - m->dlo[3];
+        while (x[3] >= m->dhi[3] - 1e-12 * L) x[3] -= L;
+        while (x[3] < m->dlo[3] - 1e-12 * L) x[3] += L;
+    }
+}
+
+/* state of source n as seen by receiver b at stage sigma of substep s */
+struct Src {
+    const double *Pa, *Pb, *Ba, *Bb;
+    double w;
+    double P(long i) const { return Pb ? Pa[i] + w * (Pb[i] - Pa[i]) : Pa[i]; }
+    double B(long i) const { return Bb ? Ba[i] + w * (Bb[i] - Ba[i]) : Ba[i]; }
+};
+
+Src amr_src(const ora_amr* m, int b, int n, int sigma, long s) {
+    const AmrBlk& R = m->b[b];
+    const AmrBlk& N = m->b[n];
+    Src r;
+    r.Pb = r.Bb = nullptr;
+    r.w = 0.0;
+    if (N.lat > R.lat) {
+        r.Pa = N.Pold.data();
+        r.Ba = N.Bold.data();
+        r.Pb = N.g->prim.data();
+        r.Bb = N.g->bface.data();
+        r.w = ((double)(s - N.s0) + sigma * 0.5 * (double)(1L << R.lat)) / (double)(1L << N.lat);
+    } else if (N.lat == R.lat && sigma == 1) {
+        r.Pa = N.Ph.data();
+        r.Ba = N.Bh.data();
+    } else {
+        r.Pa = N.g->prim.data();
+        r.Ba = N.g->bface.data();
+    }
+    return r;
+}
+
+double minmod(double a, double b) {
+    if (a * b <= 0.0) return 0.0;
+    return fabs(a) < fabs(b) ? a : b;
+}
+
+/* per-dimension footprint of a target cell of size ht centred at x in block N */
+void footprint(const AmrBlk& N, const double x[4], const double ht[4], int i0[4], int cnt[4], double dl[4]) {
+    for (int d = 1; d <= 3; d++) {
+        const double hs = N.h[d];
+        const double r = ht[d] / hs;
+        dl[d] = 0.0;
+        if (r > 1.5) {
+            cnt[d] = (int)std::lround(r);
+            i0[d] = (int)std::lround((x[d] - 0.5 * ht[d] - N.lo[d]) / hs);
+        } else {
+            cnt[d] = 1;
+            i0[d] = (int)std::floor((x[d] - N.lo[d]) / hs);
+            if (r < 0.75) dl[d] = (x[d] - (N.lo[d] + (i0[d] + 0.5) * hs)) / hs;
+        }
+    }
+}
+
+void amr_sample_cell(const ora_amr* m, int n, const Src& S, const double x[4], const double ht[4], double out[NPR]) {
+    const AmrBlk& N = m->b[n];
+    const ora_grid* g = N.g;
+    const int nn[4] = {0, g->d.n1, g->d.n2, g->d.n3};
+    int i0[4], cnt[4];
+    double dl[4];
+    footprint(N, x, ht, i0, cnt, dl);
+    const long nc = g->ncell;
+    const double inv = 1.0 / (double)(cnt[1] * cnt[2] * cnt[3]);
+    for (int v = 0; v < NPR; v++) {
+        double sum = 0.0;
+        for (int c3 = 0; c3 < cnt[3]; c3++)
+            for (int c2 = 0; c2 < cnt[2]; c2++)
+                for (int c1 = 0; c1 < cnt[1]; c1++) {
+                    int ii[4] = {0, i0[1] + c1, i0[2] + c2, i0[3] + c3};
+                    long c = cidx(g, ii[1], ii[2], ii[3]);
+                    double q = S.P(v * nc + c);
+                    for (int d = 1; d <= 3; d++) {
+                        if (dl[d] == 0.0) continue;
+                        if (ii[d] - 1 < 0 || ii[d] + 1 >= nn[d]) continue;
+                        int im[4] = {0, ii[1], ii[2], ii[3]}, ip[4] = {0, ii[1], ii[2], ii[3]};
+                        im[d]--;
+                        ip[d]++;
+                        double qm = S.P(v * nc + cidx(g, im[1], im[2], im[3]));
+                        double qp = S.P(v * nc + cidx(g, ip[1], ip[2], ip[3]));
+                        q += dl[d] * minmod(q - qm, qp - q);
+                    }
+                    sum += q;
+                }
+        out[v] = sum * inv;
+    }
+}
+
+/* face value of direction fd at point x (x[fd] on a face plane) */
+double amr_sample_face(const ora_amr* m, int n, const Src& S, const double x[4], const double ht[4], int fd) {
+    const AmrBlk& N = m->b[n];
+    const ora_grid* g = N.g;
+    const long nc = g->ncell;
+    int i0[4], cnt[4];
+    double dl[4];
+    double xc[4] = {0, x[1], x[2], x[3]};
+    xc[fd] += 0.5 * ht[fd]; /* footprint along fd from the cell above the face */
+    footprint(N, xc, ht, i0, cnt, dl);
+    /* along the normal: the plane at x[fd], linearly between source planes */
+    double pos = (x[fd] - N.lo[fd]) / N.h[fd];
+    int p0 = (int)std::floor(pos + 1e-9);
+    double fr = pos - p0;
+    if (fabs(fr) < 1e-9) fr = 0.0;
+    cnt[fd] = 1;
+    const double inv = 1.0 / (double)(cnt[1] * cnt[2] * cnt[3]);
+    double sum = 0.0;
+    for (int c3 = 0; c3 < cnt[3]; c3++)
+        for (int c2 = 0; c2 < cnt[2]; c2++)
+            for (int c1 = 0; c1 < cnt[1]; c1++) {
+                int ii[4] = {0, i0[1] + c1, i0[2] + c2, i0[3] + c3};
+                ii[fd] = p0;
+                double q = S.B((fd - 1) * nc + cidx(g, ii[1], ii[2], ii[3]));
+                if (fr != 0.0) {
+                    ii[fd] = p0 + 1;
+                    double q1 = S.B((fd - 1) * nc + cidx(g, ii[1], ii[2], ii[3]));
+                    q = q + fr * (q1 - q);
+                }
+                sum += q;
+            }
+    return sum * inv;
+}
+
+void amr_fill_block(ora_amr* m, int b, int sigma, double* P, double* Bf) {
+    AmrBlk& R = m->b[b];
+    ora_grid* g = R.g;
+    const ora_desc& d = g->d;
+    const int nn[4] = {0, d.n1, d.n2, d.n3};
+    const long nc = g->ncell;
+    for (int k = -NG; k < d.n3 + NG; k++)
+        for (int j = -NG; j < d.n2 + NG; j++)
+            for (int i = -NG; i < d.n1 + NG; i++) {
+                const int ii[4] = {0, i, j, k};
+                bool ghost = false;
+                for (int e = 1; e <= 3; e++)
+                    if (ii[e] < 0 || ii[e] >= nn[e]) ghost = true;
+                const long c = cidx(g, i, j, k);
+                if (ghost) {
+                    double x[4] = {0, R.lo[1] + (i + 0.5) * R.h[1], R.lo[2] + (j + 0.5) * R.h[2],
+                                   R.lo[3] + (k + 0.5) * R.h[3]};
+                    int neg, clamp;
+                    amr_map(m, b, x, 0, &neg, &clamp);
+                    int n = amr_find(m, x);
+                    if (n < 0) continue;
+                    Src S = amr_src(m, b, n, sigma, m->s);
+                    double out[NPR];
+                    amr_sample_cell(m, n, S, x, R.h, out);
+                    if (neg) {
+                        out[U2] = -out[U2];
+                        out[B2] = -out[B2];
+                    }
+                    if (clamp > 0 && out[U1] < 0.0) out[U1] = 0.0;
+                    if (clamp < 0 && out[U1] > 0.0) out[U1] = 0.0;
+                    for (int v = 0; v < NPR; v++) P[v * nc + c] = out[v];
+                }
+                for (int fd = 1; fd <= 3; fd++) {
+                    bool owned = true;
+                    for (int e = 1; e <= 3; e++) {
+                        if (e == fd) {
+                            if (ii[e] < 0 || ii[e] > nn[e]) owned = false;
+                        } else if (ii[e] < 0 || ii[e] >= nn[e]) {
+                            owned = false;
+                        }
+                    }
+                    if (owned) continue;
+                    double x[4] = {0, R.lo[1] + (i + 0.5) * R.h[1], R.lo[2] + (j + 0.5) * R.h[2],
+                                   R.lo[3] + (k + 0.5) * R.h[3]};
+                    x[fd] = R.lo[fd] + ii[fd] * R.h[fd];
+                    int neg, clamp;
+                    amr_map(m, b, x, fd, &neg, &clamp);
+                    int n = amr_find(m, x);
+                    if (n < 0) continue;
+                    Src S = amr_src(m, b, n, sigma, m->s);
+                    double v = amr_sample_face(m, n, S, x, R.h, fd);
+                    Bf[(fd - 1) * nc + c] = (neg && fd == 2) ? -v : v;
+                }
+            }
+}
+
+/* blocks around an edge of direction e at the corner point p (p[e] = edge centre) */
+void edge_blocks(const ora_amr* m, int b, const double p[4], int e, std::vector<int>& out) {
+    const AmrBlk& B = m->b[b];
+    int a1 = (e == 1) ? 2 : 1, a2 = (e == 3) ? 2 : 3;
+    out.clear();
+    for (int sa = -1; sa <= 1; sa += 2)
+        for (int sb = -1; sb <= 1; sb += 2) {
+            double x[4] = {0, p[1], p[2], p[3]};
+            x[a1] += sa * 0.25 * B.h[a1];
+            x[a2] += sb * 0.25 * B.h[a2];
+            bool outside = false;
+            for (int d = 1; d <= 3; d++) {
+                if (m->per[d]) {
+                    const double L = m->dhi[d] - m->dlo[d];
+                    if (x[d] < m->dlo[d]) x[d] += L;
+                    if (x[d] >= m->dhi[d]) x[d] -= L;
+                } else if (x[d] < m->dlo[d] || x[d] > m->dhi[d]) {
+                    outside = true;
+                }
+            }
+            if (outside) continue;
+            int n = amr_find(m, x);
+            if (n >= 0 && std::find(out.begin(), out.end(), n) == out.end()) out.push_back(n);
+        }
+}
+
+/* dominance: finest along the edge, then finest across, then lowest index */
+bool dominates(const ora_amr* m, int a, int c, int e) {
+    const AmrBlk& A = m->b[a];
+    const AmrBlk& C = m->b[c];
+    if (A.h[e] != C.h[e]) return A.h[e] < C.h[e];
+    double va = A.h[1] * A.h[2] * A.h[3], vc = C.h[1] * C.h[2] * C.h[3];
+    if (va != vc) return va < vc;
+    return a < c;
+}
+
+/* padded index in block n of the edge segments of direction e covering the
+ * segment [p[e] - he/2, p[e] + he/2] at corner point p */
+void edge_cover(const ora_amr* m, int n, const double p[4], int e, double he, std::vector<long>& out) {
+    const AmrBlk& N = m->b[n];
+    out.clear();
+    int idx[4];
+    for (int d = 1; d <= 3; d++) {
+        if (d == e) continue;
+        double x = p[d];
+        if (m->per[d]) {
+            const double L = m->dhi[d] - m->dlo[d];
+            if (x < N.lo[d] - 1e-9 * L) x += L;
+            if (x > N.hi[d] + 1e-9 * L) x -= L;
+        }
+        idx[d] = (int)std::lround((x - N.lo[d]) / N.h[d]);
+    }
+    int cnt = (int)std::lround(he / N.h[e]);
+    if (cnt < 1) cnt = 1;
+    double x0 = p[e] - 0.5 * he;
+    if (m->per[e]) {
+        const double L = m->dhi[e] - m->dlo[e];
+        if (x0 < N.lo[e] - 1e-9 * L) x0 += L;
+        if (x0 > N.hi[e] - 1e-9 * L) x0 -= L;
+    }
+    int i0 = (int)std::lround((x0 - N.lo[e]) / N.h[e]);
+    for (int c = 0; c < cnt; c++) {
+        idx[e] = i0 + c;
+        out.push_back(cidx(N.g, idx[1], idx[2], idx[3]));
+    }
+}
+
+/* padded face indices in block n (direction d) covering a face of block b centred at p */
+void face_cover(const ora_amr* m, int n, const double p[4], int d, const double hb[4], std::vector<long>& out) {
+    const AmrBlk& N = m->b[n];
+    out.clear();
+    int i0[4], cnt[4];
+    for (int e = 1; e <= 3; e++) {
+        double x = p[e];
+        if (m->per[e]) {
+            const double L = m->dhi[e] - m->dlo[e];
+            if (x < N.lo[e] - 1e-9 * L) x += L;
+            if (x > N.hi[e] + 1e-9 * L) x -= L;
+        }
+        if (e == d) {
+            i0[e] = (int)std::lround((x - N.lo[e]) / N.h[e]);
+            cnt[e] = 1;
+        } else {
+            cnt[e] = std::max(1, (int)std::lround(hb[e] / N.h[e]));
+            i0[e] = (int)std::lround((x - 0.5 * hb[e] - N.lo[e]) / N.h[e]);
+        }
+    }
+    for (int c3 = 0; c3 < cnt[3]; c3++)
+        for (int c2 = 0; c2 < cnt[2]; c2++)
+            for (int c1 = 0; c1 < cnt[1]; c1++) out.push_back(cidx(N.g, i0[1] + c1, i0[2] + c2, i0[3] + c3));
+}
+
+bool finer(const AmrBlk& A, const AmrBlk& C) {  /* A strictly finer than C in some dimension, nowhere coarser */
+    bool st = false;
+    for (int d = 1; d <= 3; d++) {
+        if (A.h[d] > C.h[d] * (1 + 1e-9)) return false;
+        if (A.h[d] < C.h[d] * (1 - 1e-9)) st = true;
+    }
+    return st;
+}
+
+void amr_build_links(ora_amr* m) {
+    const int nb = (int)m->b.size();
+    for (int b = 0; b < nb; b++) {
+        AmrBlk& B = m->b[b];
+        const ora_desc& d = B.g->d;
+        const int nn[4] = {0, d.n1, d.n2, d.n3};
+        /* faces */
+        for (int fd = 1; fd <= 3; fd++)
+            for (int side = 0; side < 2; side++) {
+                if (d.bc[2 * (fd - 1) + side] != ORA_BC_BLOCK && d.bc[2 * (fd - 1) + side] != ORA_BC_PERIODIC) continue;
+                int t1 = (fd == 1) ? 2 : 1, t2 = (fd == 3) ? 2 : 3;
+                for (int b2 = 0; b2 < nn[t2]; b2++)
+                    for (int b1 = 0; b1 < nn[t1]; b1++) {
+                        int ii[4];
+                        ii[fd] = side ? nn[fd] : 0;
+                        ii[t1] = b1;
+                        ii[t2] = b2;
+                        double p[4] = {0, B.lo[1] + (ii[1] + 0.5) * B.h[1], B.lo[2] + (ii[2] + 0.5) * B.h[2],
+                                       B.lo[3] + (ii[3] + 0.5) * B.h[3]};
+                        p[fd] = side ? B.hi[fd] : B.lo[fd];
+                        double q[4] = {0, p[1], p[2], p[3]};
+                        q[fd] += (side ? 0.25 : -0.25) * B.h[fd];
+                        if (m->per[fd]) {
+                            const double L = m->dhi[fd] - m->dlo[fd];
+                            if (q[fd] < m->dlo[fd]) q[fd] += L;
+                            if (q[fd] >= m->dhi[fd]) q[fd] -= L;
+                        }
+                        int n = amr_find(m, q);
+                        if (n < 0 || n == b) continue;
+                        AmrBlk& N = m->b[n];
+                        if (!finer(N, B) && !(N.lat < B.lat)) continue;
+                        long fi = cidx(B.g, ii[1], ii[2], ii[3]);
+                        double pn[4] = {0, p[1], p[2], p[3]};
+                        if (m->per[fd]) {
+                            const double L = m->dhi[fd] - m->dlo[fd];
+                            if (pn[fd] < N.lo[fd] - 1e-9 * L) pn[fd] += L;
+                            if (pn[fd] > N.hi[fd] + 1e-9 * L) pn[fd] -= L;
+                        }
+                        std::vector<long> cov;
+                        face_cover(m, n, pn, fd, B.h, cov);
+                        if (N.lat == B.lat) {
+                            if (!finer(N, B)) continue;
+                            SyncRec r;
+                            r.dst = b;
+                            r.d = fd;
+                            r.di = fi;
+                            r.src = n;
+                            r.si = cov;
+                            m->fsync.push_back(r);
+                        } else {
+                            FaceRec r;
+                            r.c = b;
+                            r.d = fd;
+                            r.side = side;
+                            r.i = ii[1];
+                            r.j = ii[2];
+                            r.k = ii[3];
+                            r.f = n;
+                            r.ff = cov;
+                            m->frec.push_back(r);
+                        }
+                    }
+            }
+        /* edges on the block boundary */
+        for (int e = 1; e <= 3; e++) {
+            int a1 = (e == 1) ? 2 : 1, a2 = (e == 3) ? 2 : 3;
+            for (int k = 0; k <= nn[3]; k++)
+                for (int j = 0; j <= nn[2]; j++)
+                    for (int i = 0; i <= nn[1]; i++) {
+                        int ii[4] = {0, i, j, k};
+                        if (ii[e] >= nn[e]) continue;
+                        bool bnd = (ii[a1] == 0 || ii[a1] == nn[a1] || ii[a2] == 0 || ii[a2] == nn[a2]);
+                        if (!bnd) continue;
+                        /* axis edges hold 0 */
+                        if (e != 2 && ((d.bc[2] == ORA_BC_POLAR && j == 0) || (d.bc[3] == ORA_BC_POLAR && j == nn[2])))
+                            continue;
+                        double p[4];
+                        for (int dd = 1; dd <= 3; dd++) p[dd] = B.lo[dd] + ii[dd] * B.h[dd];
+                        p[e] += 0.5 * B.h[e];
+                        std::vector<int> around;
+                        edge_blocks(m, b, p, e, around);
+                        /* global dominant: finest time level, then spatial dominance */
+                        int gd = b;
+                        for (int n : around)
+                            if (m->b[n].lat < m->b[gd].lat || (m->b[n].lat == m->b[gd].lat && dominates(m, n, gd, e)))
+                                gd = n;
+                        /* same-level dominant */
+                        int sd = b;
+                        for (int n : around)
+                            if (m->b[n].lat == B.lat && dominates(m, n, sd, e)) sd = n;
+                        long ei = cidx(B.g, i, j, k);
+                        if (sd != b) {
+                            SyncRec r;
+                            r.dst = b;
+                            r.d = e;
+                            r.di = ei;
+                            r.src = sd;
+                            edge_cover(m, sd, p, e, B.h[e], r.si);
+                            m->esync.push_back(r);
+                        }
+                        if (m->b[gd].lat < B.lat) {
+                            EdgeRec r;
+                            r.c = b;
+                            r.e = e;
+                            r.i = i;
+                            r.j = j;
+                            r.k = k;
+                            r.f = gd;
+                            edge_cover(m, gd, p, e, B.h[e], r.fe);
+                            m->erec.push_back(r);
+                        }
+                    }
+        }
+    }
+}
+
+double amr_avg(const double* a, long off, const std::vector<long>& idx) {
+    double s = 0.0;
+    for (long q : idx) s += a[off + q];
+    return s * (1.0 / (double)idx.size());
+}
+
+/* fluxes and EMFs of one stage of a group of same-level blocks, synchronised */
+void amr_fluxes_group(ora_amr* m, const std::vector<int>& grp, int sigma) {
+    const int lat = m->b[grp[0]].lat;
+    for (int b : grp) {
+        AmrBlk& B = m->b[b];
+        double* Pf = sigma ? B.Ph.data() : B.g->prim.data();
+        double* Bff = sigma ? B.Bh.data() : B.g->bface.data();
+        amr_fill_block(m, b, sigma, Pf, Bff);
+    }
+    for (int b : grp) {
+        AmrBlk& B = m->b[b];
+        const double* Pf = sigma ? B.Ph.data() : B.g->prim.data();
+        const double* Bff = sigma ? B.Bh.data() : B.g->bface.data();
+        stage_fluxes(B.g, Pf, Bff, B.F);
+    }
+    for (const SyncRec& r : m->fsync) {
+        if (m->b[r.dst].lat != lat) continue;
+        AmrBlk& D = m->b[r.dst];
+        const AmrBlk& S = m->b[r.src];
+        for (int q = 0; q < NFX; q++)
+            D.F[r.d][(size_t)q * D.g->ncell + r.di] = amr_avg(S.F[r.d].data(), (long)q * S.g->ncell, r.si);
+    }
+    for (int b : grp) stage_emf(m->b[b].g, m->b[b].F, m->b[b].E);
+    std::vector<double> vals(m->esync.size());
+    for (size_t q = 0; q < m->esync.size(); q++) {  /* read all, then write: sources may be synced too */
+        const SyncRec& r = m->esync[q];
+        if (m->b[r.dst].lat != lat) continue;
+        const AmrBlk& S = m->b[r.src];
+        vals[q] = amr_avg(S.E.data(), (long)(r.d - 1) * S.g->ncell, r.si);
+    }
+    for (size_t q = 0; q < m->esync.size(); q++) {
+        const SyncRec& r = m->esync[q];
+        if (m->b[r.dst].lat != lat) continue;
+        AmrBlk& D = m->b[r.dst];
+        D.E[(size_t)(r.d - 1) * D.g->ncell + r.di] = vals[q];
+    }
+}
+
+/* one midpoint step of every block of a same-level group (Sec. 2.1) */
+void amr_step_group(ora_amr* m, const std::vector<int>& grp, double dtf) {
+    for (int b : grp) {
+        AmrBlk& B = m->b[b];
+        B.Pold = B.g->prim;
+        B.Bold = B.g->bface;
+        B.s0 = m->s;
+    }
+    amr_fluxes_group(m, grp, 0);
+    for (int b : grp) {
+        AmrBlk& B = m->b[b];
+        const double dt = dtf * (double)(1L << B.lat);
+        stage_ct(B.g, B.E, B.Bold.data(), 0.5 * dt, B.Bh.data());
+        stage_update(B.g, B.F, B.Pold.data(), B.Pold.data(), B.Bh.data(), 0.5 * dt, B.Ph.data());
+    }
+    amr_fluxes_group(m, grp, 1);
+    const int lat = m->b[grp[0]].lat;
+    /* reflux records: the coarse side's own integral, the fine side's accumulation */
+    for (FaceRec& r : m->frec) {
+        if (m->b[r.c].lat == lat) {
+            const AmrBlk& C = m->b[r.c];
+            const double dt = dtf * (double)(1L << C.lat);
+            long fi = cidx(C.g, r.i, r.j, r.k);
+            for (int q = 0; q < NFX; q++) {
+                r.own[q] = dt * C.F[r.d][(size_t)q * C.g->ncell + fi];
+                r.acc[q] = 0.0;
+            }
+        }
+    }
+    for (EdgeRec& r : m->erec) {
+        if (m->b[r.c].lat == lat) {
+            const AmrBlk& C = m->b[r.c];
+            const double dt = dtf * (double)(1L << C.lat);
+            r.own = dt * C.E[(size_t)(r.e - 1) * C.g->ncell + cidx(C.g, r.i, r.j, r.k)];
+            r.acc = 0.0;
+        }
+    }
+    for (FaceRec& r : m->frec) {
+        if (m->b[r.f].lat == lat) {
+            const AmrBlk& F = m->b[r.f];
+            const double dt = dtf * (double)(1L << F.lat);
+            for (int q = 0; q < NFX; q++) r.acc[q] += dt * amr_avg(F.F[r.d].data(), (long)q * F.g->ncell, r.ff);
+        }
+    }
+    for (EdgeRec& r : m->erec) {
+        if (m->b[r.f].lat == lat) {
+            const AmrBlk& F = m->b[r.f];
+            const double dt = dtf * (double)(1L << F.lat);
+            r.acc += dt * amr_avg(F.E.data(), (long)(r.e - 1) * F.g->ncell, r.fe);
+        }
+    }
+    for (int b : grp) {
+        AmrBlk& B = m->b[b];
+        const double dt = dtf * (double)(1L << B.lat);
+        stage_ct(B.g, B.E, B.Bold.data(), dt, B.g->bface.data());
+        stage_update(B.g, B.F, B.Pold.data(), B.Ph.data(), B.g->bface.data(), dt, B.g->prim.data());
+    }
+}
+
+/* end of a coarse step (Sec. 3.2 refluxing, Sec. 3.4 flux correction): the
+ * coarse block's face fluxes and edge EMFs are replaced by the time
+ * integrals of the finer level's; the cells next to changed faces are
+ * inverted again from U(P) + the flux correction. */
+void amr_reflux(ora_amr* m, int c) {
+    AmrBlk& C = m->b[c];
+    ora_grid* g = C.g;
+    const ora_desc& d = g->d;
+    const long nc = g->ncell;
+    std::vector<double> dU((size_t)NCONS * nc, 0.0), dE((size_t)3 * nc, 0.0);
+    std::vector<char> mark(nc, 0);
+    bool any = false;
+    for (const FaceRec& r : m->frec) {
+        if (r.c != c) continue;
+        int ii[4] = {0, r.i, r.j, r.k};
+        if (r.side == 1) ii[r.d]--;
+        long cc = cidx(g, ii[1], ii[2], ii[3]);
+        const double sgn = r.side ? -1.0 : 1.0;
+        for (int q = 0; q < NCONS; q++) dU[(size_t)q * nc + cc] += sgn * (r.acc[q] - r.own[q]) / C.h[r.d];
+        mark[cc] = 1;
+        any = true;
+    }
+    for (const EdgeRec& r : m->erec) {
+        if (r.c != c) continue;
+        dE[(size_t)(r.e - 1) * nc + cidx(g, r.i, r.j, r.k)] = r.acc - r.own;
+        any = true;
+    }
+    if (!any) return;
+    std::vector<double> Bnew(g->bface.size());
+    stage_ct(g, dE, g->bface.data(), 1.0, Bnew.data());
+    for (int k = 0; k < d.n3; k++)
+        for (int j = 0; j < d.n2; j++)
+            for (int i = 0; i < d.n1; i++) {
+                long cc = cidx(g, i, j, k);
+                if (Bnew[cc] != g->bface[cc] || Bnew[cidx(g, i + 1, j, k)] != g->bface[cidx(g, i + 1, j, k)] ||
+                    Bnew[nc + cc] != g->bface[nc + cc] ||
+                    Bnew[nc + cidx(g, i, j + 1, k)] != g->bface[nc + cidx(g, i, j + 1, k)] ||
+                    Bnew[2 * nc + cc] != g->bface[2 * nc + cc] ||
+                    Bnew[2 * nc + cidx(g, i, j, k + 1)] != g->bface[2 * nc + cidx(g, i, j, k + 1)])
+                    mark[cc] = 1;
+            }
+    /* U of the marked cells with the field before the correction */
+    std::vector<double> U0((size_t)NCONS * nc, 0.0);
+    for (int k = 0; k < d.n3; k++)
+        for (int j = 0; j < d.n2; j++)
+            for (int i = 0; i < d.n1; i++) {
+                long cc = cidx(g, i, j, k);
+                if (!mark[cc]) continue;
+                const Geom& G = g->gc[gidx(g, i, j)];
+                real pr[NPR];
+                load_prim(g, g->prim.data(), cc, pr);
+                State st;
+                get_state(pr, G, st);
+                real u9[9];
+                prim_to_uf(pr, st, 0, d.gam, u9);
+                for (int q = 0; q < NCONS; q++) U0[(size_t)q * nc + cc] = tod(u9[q] * G.gdet);
+            }
+    g->bface.swap(Bnew);
+    for (int k = 0; k < d.n3; k++)
+        for (int j = 0; j < d.n2; j++)
+            for (int i = 0; i < d.n1; i++) {
+                long cc = cidx(g, i, j, k);
+                if (!mark[cc]) continue;
+                const Geom& G = g->gc[gidx(g, i, j)];
+                real U[NCONS];
+                for (int q = 0; q < NCONS; q++) U[q] = U0[(size_t)q * nc + cc] + dU[(size_t)q * nc + cc];
+                real Bc[3];
+                centre_b(g, g->bface.data(), i, j, k, Bc);
+                real pr[NPR], p0[NPR];
+                load_prim(g, g->prim.data(), cc, pr);
+                for (int v = 0; v < NPR; v++) p0[v] = pr[v];
+                pr[B1] = Bc[0];
+                pr[B2] = Bc[1];
+                pr[B3] = Bc[2];
+                int its = 0;
+                int st = con2prim(d, U, Bc, G, pr, &its);
+                if (st == C2P_FAIL)
+                    for (int v = 0; v < 5; v++) pr[v] = p0[v];
+                m->stats[st == C2P_OK ? 0 : (st == C2P_ENTROPY ? 1 : 2)]++;
+                if (d.floors && apply_floors(d, pr, G, g->rc[gidx(g, i, j)])) m->stats[3]++;
+                for (int v = 0; v < NPR; v++) g->prim[v * nc + cc] = tod(pr[v]);
+            }
+}
+
+}  // namespace
+
+extern "C" {
+
+ora_amr* ora_amr_new(const ora_desc* phys, int nb, const ora_block* blocks) {
+    ora_amr* m = new ora_amr;
+    m->phys = *phys;
+    m->Lmax = 0;
+    m->s = 0;
+    for (int q = 0; q < 4; q++) m->stats[q] = 0;
+    for (int d = 1; d <= 3; d++) {
+        m->dlo[d] = 1e300;
+        m->dhi[d] = -1e300;
+        m->per[d] = false;
+    }
+    for (int n = 0; n < nb; n++) {
+        const ora_block& o = blocks[n];
+        ora_desc d = *phys;
+        d.n1 = o.n1;
+        d.n2 = o.n2;
+        d.n3 = o.n3;
+        d.x1min = o.x1min;
+        d.x2min = o.x2min;
+        d.x3min = o.x3min;
+        d.dx1 = o.dx1;
+        d.dx2 = o.dx2;
+        d.dx3 = o.dx3;
+        for (int f = 0; f < 6; f++) d.bc[f] = o.bc[f];
+        AmrBlk B;
+        B.g = ora_grid_new(&d);
+        B.lat = o.lat;
+        B.s0 = 0;
+        const double x0[4] = {0, o.x1min, o.x2min, o.x3min};
+        const double hh[4] = {0, o.dx1, o.dx2, o.dx3};
+        const int nn[4] = {0, o.n1, o.n2, o.n3};
+        for (int e = 1; e <= 3; e++) {
+            B.lo[e] = x0[e];
+            B.h[e] = hh[e];
+            B.hi[e] = x0[e] + nn[e] * hh[e];
+            m->dlo[e] = std::min(m->dlo[e], B.lo[e]);
+            m->dhi[e] = std::max(m->dhi[e], B.hi[e]);
+            if (o.bc[2 * (e - 1)] == ORA_BC_PERIODIC) m->per[e] = true;
+        }
+        B.Ph.assign(B.g->prim.size(), 0.0);
+        B.Bh.assign(B.g->bface.size(), 0.0);
+        B.Pold = B.g->prim;
+        B.Bold = B.g->bface;
+        m->Lmax = std::max(m->Lmax, o.lat);
+        m->b.push_back(B);
+    }
+    amr_build_links(m);
+    return m;
+}
+
+void ora_amr_free(ora_amr* m) {
+    for (AmrBlk& B : m->b) ora_grid_free(B.g);
+    delete m;
+}
+
+void ora_amr_set(ora_amr* m, int b, const double* prim, const double* bface) {
+    ora_grid* g = m->b[b].g;
+    std::memcpy(g->prim.data(), prim, sizeof(double) * NPR * g->ncell);
+    std::memcpy(g->bface.data(), bface, sizeof(double) * 3 * g->ncell);
+    const long nc = g->ncell;
+    for (int k = 0; k < g->d.n3; k++)
+        for (int j = 0; j < g->d.n2; j++)
+            for (int i = 0; i < g->d.n1; i++) {
+                real Bc[3];
+                centre_b(g, g->bface.data(), i, j, k, Bc);
+                for (int q = 0; q < 3; q++) g->prim[(B1 + q) * nc + cidx(g, i, j, k)] = tod(Bc[q]);
+            }
+}
+
+void ora_amr_get(const ora_amr* m, int b, double* prim, double* bface) { ora_grid_get(m->b[b].g, prim, bface); }
+
+void ora_amr_fill(ora_amr* m) {
+    /* every source at its current state: all blocks are at the same time */
+    for (AmrBlk& B : m->b) {
+        B.Pold = B.g->prim;
+        B.Bold = B.g->bface;
+        B.s0 = 0;
+    }
+    m->s = 0;
+    for (int b = 0; b < (int)m->b.size(); b++) amr_fill_block(m, b, 0, m->b[b].g->prim.data(), m->b[b].g->bface.data());
+}
+
+double ora_amr_period(ora_amr* m, double dtf) {
+    for (int q = 0; q < 4; q++) m->stats[q] = 0;
+    if (!(dtf > 0.0)) {
+        dtf = 1e300;
+        for (AmrBlk& B : m->b) dtf = std::min(dtf, grid_dt(B.g) / (double)(1L << B.lat));
+    }
+    const long S = 1L << m->Lmax;
+    for (long s = 0; s < S; s++) {
+        m->s = s;
+        for (int L = m->Lmax; L >= 0; L--) {
+            if (s % (1L << L) != 0) continue;
+            std::vector<int> grp;
+            for (int b = 0; b < (int)m->b.size(); b++)
+                if (m->b[b].lat == L) grp.push_back(b);
+            if (grp.empty()) continue;
+            for (int b : grp) std::fill(m->b[b].g->status.begin(), m->b[b].g->status.end(), 0);
+            amr_step_group(m, grp, dtf);
+            for (int b : grp)
+                for (int q = 0; q < 4; q++) m->stats[q] += m->b[b].g->stats[q], m->b[b].g->stats[q] = 0;
+        }
+        for (int c = 0; c < (int)m->b.size(); c++)
+            if ((s + 1) % (1L << m->b[c].lat) == 0) amr_reflux(m, c);
+    }
+    m->s = 0;
+    return dtf;
+}
+
+void ora_amr_stats(const ora_amr* m, long long* counts4) {
+    for (int q = 0; q < 4; q++) counts4[q] = m->stats[q];
+}
+
+}  /* extern "C" */

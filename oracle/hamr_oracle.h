@@ -18,7 +18,7 @@
 extern "C" {
 #endif
 
-enum { ORA_BC_OUTFLOW = 0, ORA_BC_PERIODIC = 1, ORA_BC_POLAR = 2, ORA_BC_OUTFLOW_NOINFLOW = 3 };
+enum { ORA_BC_OUTFLOW = 0, ORA_BC_PERIODIC = 1, ORA_BC_POLAR = 2, ORA_BC_OUTFLOW_NOINFLOW = 3, ORA_BC_BLOCK = 4 };
 enum { ORA_METRIC_KS = 0, ORA_METRIC_MINKOWSKI = 1 };
 enum { ORA_RECON_PPM = 0, ORA_RECON_MC = 1, ORA_RECON_MINMOD = 2 };
 enum { ORA_FLUX_HLL = 0, ORA_FLUX_LLF = 1 };
@@ -71,6 +71,30 @@ double ora_grid_step(ora_grid* g, double dt);
 void ora_grid_stats(const ora_grid* g, long long* counts4);
 void ora_grid_divb(const ora_grid* g, double* divb_cells);
 void ora_grid_status(const ora_grid* g, int* status_cells);
+
+/* ---- multi-block grid: static refinement + local adaptive time steps ----
+ * Blocks tile the domain; a face with bc ORA_BC_BLOCK takes its ghosts from
+ * the neighbouring blocks, other faces map ghost positions across the
+ * physical boundary (outflow, periodic, polar) before looking up the block
+ * that holds them. lat = LAT level: the block steps with 2^lat dt_fine. */
+typedef struct {
+    int n1, n2, n3;
+    double x1min, x2min, x3min, dx1, dx2, dx3;
+    int bc[6];
+    int lat;
+} ora_block;
+typedef struct ora_amr ora_amr;
+/* phys: metric, a, gam, cour, recon, riemann, floors of `phys` are used */
+ora_amr* ora_amr_new(const ora_desc* phys, int nb, const ora_block* blocks);
+void ora_amr_free(ora_amr* m);
+void ora_amr_set(ora_amr* m, int b, const double* prim, const double* bface);
+void ora_amr_get(const ora_amr* m, int b, double* prim, double* bface);
+/* fills every block's ghosts from the current state (no stepping) */
+void ora_amr_fill(ora_amr* m);
+/* advances the grid by one schedule period (2^Lmax fine substeps);
+ * dt_fine <= 0: the CFL fine step min_b dt_b / 2^lat_b; returns dt_fine */
+double ora_amr_period(ora_amr* m, double dt_fine);
+void ora_amr_stats(const ora_amr* m, long long* counts4);
 
 /* flop counters (meaningful only in the counting build) */
 void ora_flops_reset(void);

@@ -264,3 +264,106 @@ def random_states(n, seed, a=0.9375, rho_range=(1e-6, 1.0), urho_range=(1e-4, 1e
     B = nb * scale
     prim = np.stack([rho, u, utl[0], utl[1], utl[2], B[0], B[1], B[2]], axis=1)
     return prim, np.log(r), th
+
+
+# --- multi-block inputs ------------------------------------------------------
+#
+# A block is described by a plain dict: n1, n2, n3, x1min, x2min, x3min, dx1,
+# dx2, dx3, bc (6 ints: 0 outflow, 1 periodic, 2 polar, 3 no-inflow outflow,
+# 4 neighbouring block) and lat (local time-step level).
+
+BC_BLOCK = 4
+
+
+def _edges(lo, h, n):
+    return lo + np.arange(n + 1) * h
+
+
+def _centres(lo, h, n):
+    return lo + (np.arange(n) + 0.5) * h
+
+
+def flat_box_tree(base=(2, 2, 2), n=8, refine=((0, 0, 0),), lat_coarse=1, lat_fine=0, L=1.0):
+    """Periodic unit box of base[0] x base[1] x base[2] blocks of n^3 cells;
+    the listed base blocks are split into 8 children of n^3 cells (2x finer)."""
+    blocks = []
+    hb = [L / base[d] for d in range(3)]
+    for kb in range(base[2]):
+        for jb in range(base[1]):
+            for ib in range(base[0]):
+                lo = (ib * hb[0], jb * hb[1], kb * hb[2])
+                if (ib, jb, kb) in refine:
+                    for kc in range(2):
+                        for jc in range(2):
+                            for ic in range(2):
+                                blocks.append(dict(n1=n, n2=n, n3=n, x1min=lo[0] + ic * hb[0] / 2,
+                                                   x2min=lo[1] + jc * hb[1] / 2, x3min=lo[2] + kc * hb[2] / 2,
+                                                   dx1=hb[0] / (2 * n), dx2=hb[1] / (2 * n), dx3=hb[2] / (2 * n),
+                                                   bc=[1, 1, 1, 1, 1, 1], lat=lat_fine))
+                else:
+                    blocks.append(dict(n1=n, n2=n, n3=n, x1min=lo[0], x2min=lo[1], x3min=lo[2], dx1=hb[0] / n,
+                                       dx2=hb[1] / n, dx3=hb[2] / n, bc=[1, 1, 1, 1, 1, 1], lat=lat_coarse))
+    _mark_block_faces(blocks, periodic=(True, True, True))
+    return blocks
+
+
+def _mark_block_faces(blocks, periodic):
+    """Faces interior to the domain get BC_BLOCK; faces on the domain boundary
+    keep their bc (periodic ones too: the neighbour across the period is
+    found by position)."""
+    lo = [min(b["x%dmin" % (d + 1)] for b in blocks) for d in range(3)]
+    hi = [max(b["x%dmin" % (d + 1)] + b["n%d" % (d + 1)] * b["dx%d" % (d + 1)] for b in blocks) for d in range(3)]
+    for b in blocks:
+        for d in range(3):
+            blo = b["x%dmin" % (d + 1)]
+            bhi = blo + b["n%d" % (d + 1)] * b["dx%d" % (d + 1)]
+            tol = 1e-9 * (hi[d] - lo[d])
+            if blo > lo[d] + tol:
+                b["bc"][2 * d] = BC_BLOCK
+            if bhi < hi[d] - tol:
+                b["bc"][2 * d + 1] = BC_BLOCK
+
+
+def flat_box_state(blocks, gam=5.0 / 3.0, amp=0.1, bamp=0.05, L=1.0):
+    """Smooth periodic state on each block: padded prim and face-B arrays.
+    Face B is the discrete curl of an edge vector potential whose components
+    do not vary along their own direction (A1(y,z), A2(z,x), A3(x,y)), so the
+    flux of a coarse face is exactly the sum of its finer faces'."""
+    tp = 2.0 * math.pi / L
+    A1 = lambda y, z: bamp * np.cos(tp * y + tp * z) / tp
+    A2 = lambda z, x: bamp * np.sin(tp * z) * np.cos(tp * x) / tp
+    A3 = lambda x, y: bamp * np.sin(tp * x) * np.sin(tp * y) / tp
+    out = []
+    for b in blocks:
+        n1, n2, n3 = b["n1"], b["n2"], b["n3"]
+        x = _centres(b["x1min"], b["dx1"], n1)
+        y = _centres(b["x2min"], b["dx2"], n2)
+        z = _centres(b["x3min"], b["dx3"], n3)
+        Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+        shp = (n3 + 2 * NG, n2 + 2 * NG, n1 + 2 * NG)
+        prim = np.zeros((8,) + shp)
+        bf = np.zeros((3,) + shp)
+        s = (slice(NG, NG + n3), slice(NG, NG + n2), slice(NG, NG + n1))
+        prim[0][s] = 1.0 + amp * np.sin(tp * X + 1.0) * np.cos(tp * Y)
+        prim[1][s] = 1.0 + amp * np.cos(tp * Z + 2 * tp * X)
+        prim[2][s] = 0.3 + amp * np.sin(tp * Y)
+        prim[3][s] = -0.2 + amp * np.sin(tp * (X + Z))
+        prim[4][s] = 0.1 + amp * np.cos(tp * X)
+        xe = _edges(b["x1min"], b["dx1"], n1)
+        ye = _edges(b["x2min"], b["dx2"], n2)
+        ze = _edges(b["x3min"], b["dx3"], n3)
+        # Bbar1 on x-faces (xe[i], y_c, z_c), i = 0..n1: dA3/dy - dA2/dz
+        Zc, Yc, Xe = np.meshgrid(z, y, xe, indexing="ij")
+        b1 = ((A3(Xe, Yc + 0.5 * b["dx2"]) - A3(Xe, Yc - 0.5 * b["dx2"])) / b["dx2"]
+              - (A2(Zc + 0.5 * b["dx3"], Xe) - A2(Zc - 0.5 * b["dx3"], Xe)) / b["dx3"])
+        Zc, Ye, Xc = np.meshgrid(z, ye, x, indexing="ij")
+        b2 = ((A1(Ye, Zc + 0.5 * b["dx3"]) - A1(Ye, Zc - 0.5 * b["dx3"])) / b["dx3"]
+              - (A3(Xc + 0.5 * b["dx1"], Ye) - A3(Xc - 0.5 * b["dx1"], Ye)) / b["dx1"])
+        Ze, Yc, Xc = np.meshgrid(ze, y, x, indexing="ij")
+        b3 = ((A2(Ze, Xc + 0.5 * b["dx1"]) - A2(Ze, Xc - 0.5 * b["dx1"])) / b["dx1"]
+              - (A1(Yc + 0.5 * b["dx2"], Ze) - A1(Yc - 0.5 * b["dx2"], Ze)) / b["dx2"])
+        bf[0][NG:NG + n3, NG:NG + n2, NG:NG + n1 + 1] = b1
+        bf[1][NG:NG + n3, NG:NG + n2 + 1, NG:NG + n1] = b2
+        bf[2][NG:NG + n3 + 1, NG:NG + n2, NG:NG + n1] = b3
+        out.append((prim, bf))
+    return out

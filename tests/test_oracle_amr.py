@@ -1,0 +1,216 @@
+"""Pins of the oracle's multi-block step (Sec. 3.2 AMR, Sec. 3.4 LAT):
+equivalence with the single-block step, conservation and div B to round-off
+across refinement and time-level jumps (refluxing), consistent shared faces,
+free streaming through the jumps."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1912_10192_gb300 import workloads as W
+
+from helpers import NG, TORUS_BC, face_interior, torus_case
+
+FLAT = dict(metric=O.METRIC_MINKOWSKI, gam=5.0 / 3.0, cour=0.5, recon=O.RECON_PPM, riemann=O.FLUX_HLL, floors=0)
+
+
+def ora_blocks(blocks):
+    return [O.make_block(b["n1"], b["n2"], b["n3"], b["x1min"], b["x2min"], b["x3min"], b["dx1"], b["dx2"],
+                         b["dx3"], b["bc"], b["lat"]) for b in blocks]
+
+
+def amr_from(blocks, states, phys):
+    a = O.AmrGrid(phys, ora_blocks(blocks))
+    for i, (p, bf) in enumerate(states):
+        a.set(i, p, bf)
+    return a
+
+
+def totals(a, blocks, phys):
+    tot = np.zeros(6)
+    divmax = 0.0
+    for i, b in enumerate(blocks):
+        p, bf = a.get(i)
+        n1, n2, n3 = b["n1"], b["n2"], b["n3"]
+        pr = p[:, NG:NG + n3, NG:NG + n2, NG:NG + n1].reshape(8, -1).T
+        U = O.p2u_many(phys, pr, np.zeros(len(pr)), np.zeros(len(pr)))
+        tot += U.sum(0) * b["dx1"] * b["dx2"] * b["dx3"]
+        s = NG
+        div = ((bf[0][s:s + n3, s:s + n2, s + 1:s + n1 + 1] - bf[0][s:s + n3, s:s + n2, s:s + n1]) / b["dx1"]
+               + (bf[1][s:s + n3, s + 1:s + n2 + 1, s:s + n1] - bf[1][s:s + n3, s:s + n2, s:s + n1]) / b["dx2"]
+               + (bf[2][s + 1:s + n3 + 1, s:s + n2, s:s + n1] - bf[2][s:s + n3, s:s + n2, s:s + n1]) / b["dx3"])
+        divmax = max(divmax, np.abs(div).max())
+    return tot, divmax
+
+
+def test_single_block_through_the_multiblock_path_is_the_single_block_step():
+    geo, d, prim, bf = torus_case(32, 16, 8, seed=3)
+    g = O.Grid(d)
+    g.set(prim, bf)
+    p0, b0 = g.get()
+    a = O.AmrGrid(d, [O.make_block(32, 16, 8, d.x1min, d.x2min, d.x3min, d.dx1, d.dx2, d.dx3, TORUS_BC, 0)])
+    a.set(0, prim, bf)
+    a.fill()
+    pa, ba = a.get(0)
+    assert np.array_equal(pa, p0) and np.array_equal(ba, b0)  # ghost mapping = boundary conditions
+    assert g.step() == a.period()
+    p1, b1 = g.get()
+    pa1, ba1 = a.get(0)
+    s = (slice(None), slice(NG, NG + 8), slice(NG, NG + 16), slice(NG, NG + 32))
+    assert np.array_equal(pa1[s], p1[s])
+    for x, y in zip(face_interior(ba1, d), face_interior(b1, d)):
+        assert np.array_equal(x, y)
+
+
+def test_torus_split_into_eight_blocks_matches_the_single_block():
+    """Same-level blocks exchange exact copies (periodic phi and the polar
+    mirror cross block boundaries); only ulp-level differences of geometry
+    tables evaluated at block-relative coordinates remain."""
+    N1, N2, N3 = 32, 16, 8
+    geo, d, prim, bf = torus_case(N1, N2, N3, seed=3)
+    n1, n2, n3 = N1 // 2, N2 // 2, N3 // 2
+    blocks, cut = [], []
+    for kb in range(2):
+        for jb in range(2):
+            for ib in range(2):
+                bc = [4] * 6
+                bc[0 + ib] = O.BC_OUTFLOW_NOINFLOW
+                bc[2 + jb] = O.BC_POLAR
+                bc[4 + kb] = O.BC_PERIODIC
+                blocks.append(O.make_block(n1, n2, n3, d.x1min + ib * n1 * d.dx1, d.x2min + jb * n2 * d.dx2,
+                                           d.x3min + kb * n3 * d.dx3, d.dx1, d.dx2, d.dx3, bc, 0))
+                cut.append((ib * n1, jb * n2, kb * n3))
+    a = O.AmrGrid(d, blocks)
+    for b, (i0, j0, k0) in enumerate(cut):
+        pb = np.zeros((8, n3 + 6, n2 + 6, n1 + 6))
+        bb = np.zeros((3, n3 + 6, n2 + 6, n1 + 6))
+        pb[:, 3:3 + n3, 3:3 + n2, 3:3 + n1] = prim[:, 3 + k0:3 + k0 + n3, 3 + j0:3 + j0 + n2, 3 + i0:3 + i0 + n1]
+        bb[:, 3:4 + n3, 3:4 + n2, 3:4 + n1] = bf[:, 3 + k0:4 + k0 + n3, 3 + j0:4 + j0 + n2, 3 + i0:4 + i0 + n1]
+        a.set(b, pb, bb)
+    g = O.Grid(d)
+    g.set(prim, bf)
+    for _ in range(2):
+        assert abs(g.step() - a.period()) == 0.0
+    p1, b1 = g.get()
+    num = np.zeros(8)
+    den = np.zeros(8)
+    for b, (i0, j0, k0) in enumerate(cut):
+        pb, bb = a.get(b)
+        x = pb[:, 3:3 + n3, 3:3 + n2, 3:3 + n1]
+        y = p1[:, 3 + k0:3 + k0 + n3, 3 + j0:3 + j0 + n2, 3 + i0:3 + i0 + n1]
+        num += np.abs(x - y).reshape(8, -1).sum(1)
+        den += np.abs(y).reshape(8, -1).sum(1)
+    rel = num[:5].sum() / den[:5].sum()
+    assert rel < 1e-13 and (num[:5] / den[:5]).max() < 1e-11
+
+
+@pytest.mark.parametrize("tree", ["two_levels", "three_time_levels"])
+def test_refined_box_conserves_and_keeps_div_b(tree):
+    if tree == "two_levels":
+        blocks = W.flat_box_tree(base=(2, 2, 2), n=8, refine=[(0, 0, 0)], lat_coarse=1, lat_fine=0)
+    else:
+        blocks = W.flat_box_tree(base=(4, 2, 2), n=6, refine=[(0, 0, 0)], lat_coarse=1, lat_fine=0)
+        for b in blocks:  # base blocks two columns away from the refined one step with 4 dt_fine
+            if b["x1min"] >= 0.5 - 1e-12 and b["x1min"] < 0.75 - 1e-12:
+                b["lat"] = 2
+    states = W.flat_box_state(blocks)
+    phys = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, **FLAT)
+    a = amr_from(blocks, states, phys)
+    t0, d0 = totals(a, blocks, phys)
+    assert d0 < 1e-13
+    for _ in range(2):
+        a.period()
+    t1, d1 = totals(a, blocks, phys)
+    assert np.abs(t1[:5] - t0[:5]).max() < 1e-14 * np.abs(t0[:5]).max()
+    assert d1 < 1e-13
+    # shared faces agree: every face on a block boundary equals the area
+    # average of the finer side's faces covering it
+    _check_shared_faces(a, blocks)
+
+
+def _check_shared_faces(a, blocks):
+    states = [a.get(i)[1] for i in range(len(blocks))]
+
+    def face_val(i, d, pos):
+        """mean face value of block i, direction d, over the box pos = ((lo,hi) x3)"""
+        b = blocks[i]
+        lo = [b["x1min"], b["x2min"], b["x3min"]]
+        h = [b["dx1"], b["dx2"], b["dx3"]]
+        idx = []
+        for e in range(3):
+            if e == d:
+                idx.append([int(round((pos[e][0] - lo[e]) / h[e]))])
+            else:
+                i0 = int(round((pos[e][0] - lo[e]) / h[e]))
+                i1 = int(round((pos[e][1] - lo[e]) / h[e]))
+                idx.append(list(range(i0, i1)))
+        vals = [states[i][d][NG + k, NG + j, NG + ii] for k in idx[2] for j in idx[1] for ii in idx[0]]
+        return np.mean(vals)
+
+    worst = 0.0
+    for i, b in enumerate(blocks):
+        lo = [b["x1min"], b["x2min"], b["x3min"]]
+        h = [b["dx1"], b["dx2"], b["dx3"]]
+        n = [b["n1"], b["n2"], b["n3"]]
+        for d in range(3):
+            # upper face plane of block i, compared with the block above (periodic wrap)
+            plane = lo[d] + n[d] * h[d]
+            if plane > 1.0 - 1e-12:
+                plane_other = 0.0
+            else:
+                plane_other = plane
+            for j, c in enumerate(blocks):
+                clo = [c["x1min"], c["x2min"], c["x3min"]]
+                ch = [c["dx1"], c["dx2"], c["dx3"]]
+                cn = [c["n1"], c["n2"], c["n3"]]
+                if abs(clo[d] - plane_other) > 1e-12:
+                    continue
+                t = [e for e in range(3) if e != d]
+                ov = []
+                for e in t:
+                    a0 = max(lo[e], clo[e])
+                    a1 = min(lo[e] + n[e] * h[e], clo[e] + cn[e] * ch[e])
+                    ov.append((a0, a1))
+                if any(x1 - x0 < 1e-12 for x0, x1 in ov):
+                    continue
+                hc = [max(h[e], ch[e]) for e in range(3)]
+                (a0, a1), (c0, c1) = ov
+                ea, ec = t
+                na = int(round((a1 - a0) / hc[ea]))
+                nc_ = int(round((c1 - c0) / hc[ec]))
+                for qa in range(na):
+                    for qc in range(nc_):
+                        box = [None, None, None]
+                        box[d] = (plane, plane)
+                        box[ea] = (a0 + qa * hc[ea], a0 + (qa + 1) * hc[ea])
+                        box[ec] = (c0 + qc * hc[ec], c0 + (qc + 1) * hc[ec])
+                        v1 = face_val(i, d, box)
+                        box2 = list(box)
+                        box2[d] = (plane_other, plane_other)
+                        v2 = face_val(j, d, box2)
+                        worst = max(worst, abs(v1 - v2))
+    assert worst < 1e-13, worst
+
+
+def test_uniform_state_streams_through_refinement_and_time_levels():
+    blocks = W.flat_box_tree(base=(2, 2, 2), n=6, refine=[(0, 0, 0)], lat_coarse=1, lat_fine=0)
+    phys = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, **FLAT)
+    vals = [1.3, 0.7, 0.4, -0.3, 0.2]
+    states = []
+    for b in blocks:
+        shp = (b["n3"] + 6, b["n2"] + 6, b["n1"] + 6)
+        p = np.zeros((8,) + shp)
+        bf = np.zeros((3,) + shp)
+        for v, x in enumerate(vals):
+            p[v][...] = x
+        bf[0][...], bf[1][...], bf[2][...] = 0.2, -0.1, 0.3
+        states.append((p, bf))
+    a = amr_from(blocks, states, phys)
+    a.period()
+    a.period()
+    for i, b in enumerate(blocks):
+        p, bf = a.get(i)
+        s = (slice(NG, NG + b["n3"]), slice(NG, NG + b["n2"]), slice(NG, NG + b["n1"]))
+        for v, x in enumerate(vals):
+            assert np.abs(p[v][s] - x).max() < 1e-13
