@@ -1425,6 +1425,15 @@ Src amr_src(const ora_amr* m, int b, int n, int sigma, long s) {
     } else if (N.lat == R.lat && sigma == 1) {
         r.Pa = N.Ph.data();
         r.Ba = N.Bh.data();
+    } else if (N.lat < R.lat && sigma == 1) {
+        /* a finer neighbour has not yet advanced (coarse first): its state at
+         * the receiver's midpoint is extrapolated linearly in time from its
+         * last two states, t - 2^Ln and t */
+        r.Pa = N.Pold.data();
+        r.Ba = N.Bold.data();
+        r.Pb = N.g->prim.data();
+        r.Bb = N.g->bface.data();
+        r.w = 1.0 + 0.5 * (double)(1L << R.lat) / (double)(1L << N.lat);
     } else {
         r.Pa = N.g->prim.data();
         r.Ba = N.g->bface.data();
@@ -1449,7 +1458,8 @@ void footprint(const AmrBlk& N, const double x[4], const double ht[4], int i0[4]
         } else {
             cnt[d] = 1;
             i0[d] = (int)std::floor((x[d] - N.lo[d]) / hs);
-            if (r < 0.75) dl[d] = (x[d] - (N.lo[d] + (i0[d] + 0.5) * hs)) / hs;
+            /* offset of the target centre in source cells, a multiple of 1/8 */
+            if (r < 0.75) dl[d] = std::nearbyint(8.0 * (x[d] - (N.lo[d] + (i0[d] + 0.5) * hs)) / hs) / 8.0;
         }
     }
 }
@@ -1470,7 +1480,8 @@ void amr_sample_cell(const ora_amr* m, int n, const Src& S, const double x[4], c
                 for (int c1 = 0; c1 < cnt[1]; c1++) {
                     int ii[4] = {0, i0[1] + c1, i0[2] + c2, i0[3] + c3};
                     long c = cidx(g, ii[1], ii[2], ii[3]);
-                    double q = S.P(v * nc + c);
+                    const double q0 = S.P(v * nc + c);
+                    double q = q0;
                     for (int d = 1; d <= 3; d++) {
                         if (dl[d] == 0.0) continue;
                         if (ii[d] - 1 < 0 || ii[d] + 1 >= nn[d]) continue;
@@ -1479,7 +1490,7 @@ void amr_sample_cell(const ora_amr* m, int n, const Src& S, const double x[4], c
                         ip[d]++;
                         double qm = S.P(v * nc + cidx(g, im[1], im[2], im[3]));
                         double qp = S.P(v * nc + cidx(g, ip[1], ip[2], ip[3]));
-                        q += dl[d] * minmod(q - qm, qp - q);
+                        q += dl[d] * minmod(q0 - qm, qp - q0);
                     }
                     sum += q;
                 }
@@ -1500,8 +1511,11 @@ double amr_sample_face(const ora_amr* m, int n, const Src& S, const double x[4],
     /* along the normal: the plane at x[fd], linearly between source planes */
     double pos = (x[fd] - N.lo[fd]) / N.h[fd];
     int p0 = (int)std::floor(pos + 1e-9);
-    double fr = pos - p0;
-    if (fabs(fr) < 1e-9) fr = 0.0;
+    double fr = std::nearbyint(8.0 * (pos - p0)) / 8.0; /* a multiple of 1/8 */
+    if (fr >= 1.0) {
+        p0 += 1;
+        fr = 0.0;
+    }
     cnt[fd] = 1;
     const double inv = 1.0 / (double)(cnt[1] * cnt[2] * cnt[3]);
     double sum = 0.0;
@@ -2052,6 +2066,10 @@ void ora_amr_set(ora_amr* m, int b, const double* prim, const double* bface) {
                 centre_b(g, g->bface.data(), i, j, k, Bc);
                 for (int q = 0; q < 3; q++) g->prim[(B1 + q) * nc + cidx(g, i, j, k)] = tod(Bc[q]);
             }
+    /* no history yet: the previous state is the loaded one */
+    m->b[b].Pold = g->prim;
+    m->b[b].Bold = g->bface;
+    m->b[b].s0 = 0;
 }
 
 void ora_amr_get(const ora_amr* m, int b, double* prim, double* bface) { ora_grid_get(m->b[b].g, prim, bface); }

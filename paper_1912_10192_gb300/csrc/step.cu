@@ -34,8 +34,7 @@ __device__ __forceinline__ void centre_field(const BlockView& v, const double* _
     Bc[2] = 0.5 * (B[2 * v.nc + c] + B[2 * v.nc + c + (long)v.n1p * v.n2p]) * ig;
 }
 
-__global__ void k_centre_b(BlockView v, double* __restrict__ P, const double* __restrict__ B) {
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_centre_b(const BlockView& v, double* __restrict__ P, const double* __restrict__ B, long t) {
     const long n = (long)v.n1 * v.n2 * v.n3;
     if (t >= n) return;
     const int i = (int)(t % v.n1), j = (int)((t / v.n1) % v.n2), k = (int)(t / ((long)v.n1 * v.n2));
@@ -46,6 +45,11 @@ __global__ void k_centre_b(BlockView v, double* __restrict__ P, const double* __
     P[B2 * v.nc + c] = Bc[1];
     P[B3 * v.nc + c] = Bc[2];
 }
+
+__global__ void k_centre_b(BlockView v, double* __restrict__ P, const double* __restrict__ B) {
+    b_centre_b(v, P, B, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 
 // ---------------------------------------------------------------- boundaries
 // One pass per direction e, in the order x3, x2, x1, each over the full
@@ -127,11 +131,10 @@ __global__ void k_bc_axis(BlockView v, double* __restrict__ B) {
 // edge values of every cell that borders a flux face of direction dir:
 // cells -1..n_dir along dir, -1..n_e across.
 template <int DIR>
-__global__ void k_recon(BlockView v, PhysArgs ph, const double* __restrict__ P, double* __restrict__ QL,
-                        double* __restrict__ QR) {
+__device__ __forceinline__ void b_recon(const BlockView& v, PhysArgs ph, const double* __restrict__ P, double* __restrict__ QL,
+                        double* __restrict__ QR, long t) {
     const int nn[4] = {0, v.n1, v.n2, v.n3};
     const int e1 = nn[1] + 2, e2 = nn[2] + 2, e3 = nn[3] + 2;
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long)e1 * e2 * e3) return;
     const int i = (int)(t % e1) - 1, j = (int)((t / e1) % e2) - 1, k = (int)(t / ((long)e1 * e2)) - 1;
     const long c = cidx(v, i, j, k);
@@ -155,17 +158,23 @@ __global__ void k_recon(BlockView v, PhysArgs ph, const double* __restrict__ P, 
     }
 }
 
+template <int DIR>
+__global__ void k_recon(BlockView v, PhysArgs ph, const double* __restrict__ P, double* __restrict__ QL,
+                        double* __restrict__ QR) {
+    b_recon<DIR>(v, ph, P, QL, QR, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+
 // ---------------------------------------------------------------- fluxes
 // HLLE (or LLF) flux through every dir-face: faces 0..n_dir, -1..n_e across.
 template <int DIR>
-__global__ void __launch_bounds__(BS) k_flux(BlockView v, PhysArgs ph, const double* __restrict__ QL,
+__device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const double* __restrict__ QL,
                                              const double* __restrict__ QR, const double* __restrict__ Bf,
-                                             double* __restrict__ F) {
+                                             double* __restrict__ F, long t) {
     const int nn[4] = {0, v.n1, v.n2, v.n3};
     const int e1 = (DIR == 1) ? nn[1] + 1 : nn[1] + 2;
     const int e2 = (DIR == 2) ? nn[2] + 1 : nn[2] + 2;
     const int e3 = (DIR == 3) ? nn[3] + 1 : nn[3] + 2;
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long)e1 * e2 * e3) return;
     const int i = (int)(t % e1) - (DIR == 1 ? 0 : 1);
     const int j = (int)((t / e1) % e2) - (DIR == 2 ? 0 : 1);
@@ -227,13 +236,20 @@ __global__ void __launch_bounds__(BS) k_flux(BlockView v, PhysArgs ph, const dou
     }
 }
 
+template <int DIR>
+__global__ void __launch_bounds__(BS) k_flux(BlockView v, PhysArgs ph, const double* __restrict__ QL,
+                                             const double* __restrict__ QR, const double* __restrict__ Bf,
+                                             double* __restrict__ F) {
+    b_flux<DIR>(v, ph, QL, QR, Bf, F, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+
 // ---------------------------------------------------------------- EMFs
 // edge EMFs as the average of the 4 neighbouring face fluxes of B (Sec. 2.5).
 // E1 and E3 on the polar axis are 0.
-__global__ void k_emf(BlockView v, const double* __restrict__ F1, const double* __restrict__ F2,
-                      const double* __restrict__ F3, double* __restrict__ E) {
+__device__ __forceinline__ void b_emf(const BlockView& v, const double* __restrict__ F1, const double* __restrict__ F2,
+                      const double* __restrict__ F3, double* __restrict__ E, long t) {
     const int e1 = v.n1 + 1, e2 = v.n2 + 1, e3 = v.n3 + 1;
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long)e1 * e2 * e3) return;
     const int i = (int)(t % e1), j = (int)((t / e1) % e2), k = (int)(t / ((long)e1 * e2));
     const long c = cidx(v, i, j, k);
@@ -253,12 +269,17 @@ __global__ void k_emf(BlockView v, const double* __restrict__ F1, const double* 
     }
 }
 
+__global__ void k_emf(BlockView v, const double* __restrict__ F1, const double* __restrict__ F2,
+                      const double* __restrict__ F3, double* __restrict__ E) {
+    b_emf(v, F1, F2, F3, E, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+
 // ---------------------------------------------------------------- CT
 // staggered face update Bbar += dt curl E (Sec. 2.5, the three CT equations)
-__global__ void k_ct(BlockView v, const double* __restrict__ E, const double* Bb, double* Bo,
-                     const double* __restrict__ dscal, double fac) {
+__device__ __forceinline__ void b_ct(const BlockView& v, const double* __restrict__ E, const double* Bb, double* Bo,
+                     const double* __restrict__ dscal, double fac, long t) {
     const int e1 = v.n1 + 1, e2 = v.n2 + 1, e3 = v.n3 + 1;
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long)e1 * e2 * e3) return;
     const int i = (int)(t % e1), j = (int)((t / e1) % e2), k = (int)(t / ((long)e1 * e2));
     const long c = cidx(v, i, j, k);
@@ -281,6 +302,12 @@ __global__ void k_ct(BlockView v, const double* __restrict__ E, const double* Bb
         Bo[2 * nc + c] = Bb[2 * nc + c] + dt * r;
     }
 }
+
+__global__ void k_ct(BlockView v, const double* __restrict__ E, const double* Bb, double* Bo,
+                     const double* __restrict__ dscal, double fac) {
+    b_ct(v, E, Bb, Bo, dscal, fac, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ double warp_max(double x) {
@@ -312,13 +339,12 @@ __device__ __forceinline__ double inv_dt_cell(const BlockView& v, const double p
 // ---------------------------------------------------------------- cell update
 // U = U(P^n) + dts (Q(Pf) - div F); inversion with guess Pf; floors;
 // the corrector also reduces the CFL rate of the new state.
-__global__ void __launch_bounds__(BS) k_update(BlockView v, PhysArgs ph, int corrector, const double* Pb,
+__device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int corrector, const double* Pb,
                                                const double* __restrict__ Pf, const double* __restrict__ F1,
                                                const double* __restrict__ F2, const double* __restrict__ F3,
                                                const double* __restrict__ Bn, double* Un, double* Po,
                                                uint8_t* __restrict__ status, const double* __restrict__ dscal,
-                                               double fac, unsigned long long* dmax, unsigned long long* dcnt) {
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+                                               double fac, unsigned long long* dmax, unsigned long long* dcnt, long t) {
     const long n = (long)v.n1 * v.n2 * v.n3;
     const bool active = t < n;
     double inv = 0.0;
@@ -435,8 +461,17 @@ __global__ void __launch_bounds__(BS) k_update(BlockView v, PhysArgs ph, int cor
     }
 }
 
-__global__ void k_dt_reduce(BlockView v, PhysArgs ph, const double* __restrict__ P, unsigned long long* dmax) {
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(BS) k_update(BlockView v, PhysArgs ph, int corrector, const double* Pb,
+                                               const double* __restrict__ Pf, const double* __restrict__ F1,
+                                               const double* __restrict__ F2, const double* __restrict__ F3,
+                                               const double* __restrict__ Bn, double* Un, double* Po,
+                                               uint8_t* __restrict__ status, const double* __restrict__ dscal,
+                                               double fac, unsigned long long* dmax, unsigned long long* dcnt) {
+    b_update(v, ph, corrector, Pb, Pf, F1, F2, F3, Bn, Un, Po, status, dscal, fac, dmax, dcnt, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+
+__device__ __forceinline__ void b_dt_reduce(const BlockView& v, PhysArgs ph, const double* __restrict__ P, unsigned long long* dmax, long t) {
     const long n = (long)v.n1 * v.n2 * v.n3;
     double inv = 0.0;
     if (t < n) {
@@ -452,6 +487,11 @@ __global__ void k_dt_reduce(BlockView v, PhysArgs ph, const double* __restrict__
     const double wmax = warp_max(inv);
     if ((threadIdx.x & 31u) == 0 && wmax > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(wmax));
 }
+
+__global__ void k_dt_reduce(BlockView v, PhysArgs ph, const double* __restrict__ P, unsigned long long* dmax) {
+    b_dt_reduce(v, ph, P, dmax, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 
 // dt of this step: the caller's, or C0 / max rate of the current state;
 // resets the accumulators of the new step.

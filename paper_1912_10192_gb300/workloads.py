@@ -284,9 +284,11 @@ def _centres(lo, h, n):
 
 
 def flat_box_tree(base=(2, 2, 2), n=8, refine=((0, 0, 0),), lat_coarse=1, lat_fine=0, L=1.0):
-    """Periodic unit box of base[0] x base[1] x base[2] blocks of n^3 cells;
-    the listed base blocks are split into 8 children of n^3 cells (2x finer)."""
+    """Periodic unit box of base[0] x base[1] x base[2] blocks of n^3 cells (n
+    may be a triple); the listed base blocks are split into 8 children with
+    the same cell counts (2x finer)."""
     blocks = []
+    nn = (n, n, n) if isinstance(n, int) else tuple(n)
     hb = [L / base[d] for d in range(3)]
     for kb in range(base[2]):
         for jb in range(base[1]):
@@ -296,13 +298,14 @@ def flat_box_tree(base=(2, 2, 2), n=8, refine=((0, 0, 0),), lat_coarse=1, lat_fi
                     for kc in range(2):
                         for jc in range(2):
                             for ic in range(2):
-                                blocks.append(dict(n1=n, n2=n, n3=n, x1min=lo[0] + ic * hb[0] / 2,
+                                blocks.append(dict(n1=nn[0], n2=nn[1], n3=nn[2], x1min=lo[0] + ic * hb[0] / 2,
                                                    x2min=lo[1] + jc * hb[1] / 2, x3min=lo[2] + kc * hb[2] / 2,
-                                                   dx1=hb[0] / (2 * n), dx2=hb[1] / (2 * n), dx3=hb[2] / (2 * n),
-                                                   bc=[1, 1, 1, 1, 1, 1], lat=lat_fine))
+                                                   dx1=hb[0] / (2 * nn[0]), dx2=hb[1] / (2 * nn[1]),
+                                                   dx3=hb[2] / (2 * nn[2]), bc=[1, 1, 1, 1, 1, 1], lat=lat_fine))
                 else:
-                    blocks.append(dict(n1=n, n2=n, n3=n, x1min=lo[0], x2min=lo[1], x3min=lo[2], dx1=hb[0] / n,
-                                       dx2=hb[1] / n, dx3=hb[2] / n, bc=[1, 1, 1, 1, 1, 1], lat=lat_coarse))
+                    blocks.append(dict(n1=nn[0], n2=nn[1], n3=nn[2], x1min=lo[0], x2min=lo[1], x3min=lo[2],
+                                       dx1=hb[0] / nn[0], dx2=hb[1] / nn[1], dx3=hb[2] / nn[2],
+                                       bc=[1, 1, 1, 1, 1, 1], lat=lat_coarse))
     _mark_block_faces(blocks, periodic=(True, True, True))
     return blocks
 
