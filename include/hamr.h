@@ -67,15 +67,22 @@ extern "C" {
 #define HAMR_BC_PERIODIC 1          /* periodic */
 #define HAMR_BC_POLAR 2             /* transmissive polar axis (Sec. 3.3), x2 only, n3 even */
 #define HAMR_BC_OUTFLOW_NOINFLOW 3  /* zero-gradient with utilde^1 clamped to outflow, x1 only */
+#define HAMR_BC_BLOCK 4             /* face shared with other blocks of the grid (ghosts from them) */
 #define HAMR_PREC_FP64 0  /* every step in FP64 */
 #define HAMR_PREC_MIXED 1 /* FP32 reconstruction, fluxes and EMFs; FP64 metric, inversion, accumulation */
 
-/* One block: a box of cells uniform in the internal coordinates. */
+/* One block: a box of cells uniform in the internal coordinates. In a grid
+ * of several blocks (Sec. 3.2), blocks tile the domain with cell sizes that
+ * differ by powers of two; a face inside the domain has bc HAMR_BC_BLOCK,
+ * faces on the domain boundary keep their physical bc (a periodic face takes
+ * its ghosts from the block across the period). `lat` is the block's level of
+ * local adaptive time stepping (Sec. 3.4): it advances with 2^lat dt_fine. */
 typedef struct {
     int n1, n2, n3;              /* interior cells, each >= 4 */
     double x1min, x2min, x3min;  /* lower corner */
     double dx1, dx2, dx3;        /* cell sizes */
     int bc[6];                   /* x1lo x1hi x2lo x2hi x3lo x3hi: HAMR_BC_* */
+    int lat;                     /* LAT level, 0..7 (single-block grids: ignored) */
 } hamr_block_desc;
 
 /* A grid: physics options and its blocks. */
@@ -138,14 +145,30 @@ int hamr_grid_get_state(const hamr_grid* g, int block, double* prim, double* bfa
  * *stats. */
 int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_stats* stats);
 
-/* Advances every block of the grid through `n_fine_substeps` substeps of the
- * local adaptive time-stepping schedule (Sec. 3.4): a block of LAT level L
- * (time step 2^L dt_fine) is due at substep s when s mod 2^L = 0; all due
- * blocks of a stage run in one batched launch; coarse-fine ghost zones are
- * filled by MINMOD prolongation with linear time interpolation and by
- * restriction (Sec. 3.2); fluxes and EMFs are refluxed when levels
- * synchronise. Reserved: returns HAMR_EINVAL for single-block grids. */
+/* Advances every block of a multi-block grid by `n_fine_substeps` fine
+ * substeps of the local adaptive time-stepping schedule (Sec. 3.4); it must
+ * be a multiple of the period 2^Lmax (Lmax = the largest lat). At the start
+ * of each period dt_fine = min over blocks of (CFL dt of the block) / 2^lat,
+ * reduced on the device. A block of level L is due at substep s when
+ * s mod 2^L = 0; levels run coarsest first; every kernel of a stage runs as
+ * one batched launch over all due blocks of the level. Ghost zones come from
+ * the neighbouring blocks (restriction, MINMOD prolongation, linear time
+ * interpolation of a coarser-level neighbour, linear extrapolation of a
+ * finer-level one at the coarse midpoint; Sec. 3.2, 3.4); same-level blocks
+ * share face fluxes and edge EMFs (the finer side's); when a coarse step
+ * ends its boundary fluxes and EMFs are replaced by the finer level's time
+ * integrals and the cells next to corrected faces are inverted again
+ * (refluxing). The period's launches are captured once into a CUDA graph and
+ * replayed. stats: NULL or filled after synchronising `stream`.
+ * Errors: HAMR_EINVAL (single-block grid, bad count), HAMR_ESTATE (a block
+ * without state), HAMR_ECUDA. */
 int hamr_batch_step(hamr_grid* g, int n_fine_substeps, void* stream, hamr_step_stats* stats);
+
+/* Fills every block's ghost zones from the current states: the boundary
+ * conditions of a single-block grid; for a multi-block grid the sampling of
+ * the neighbouring blocks that hamr_batch_step uses (Sec. 3.2), with every
+ * block taken at the same time. Asynchronous on `stream`. */
+int hamr_grid_fill_ghosts(hamr_grid* g, void* stream);
 
 /* Reads the accumulated counters of the last step; synchronises the device. */
 int hamr_grid_stats(const hamr_grid* g, hamr_step_stats* stats);

@@ -1941,17 +1941,24 @@ void amr_reflux(ora_amr* m, int c) {
     if (!any) return;
     std::vector<double> Bnew(g->bface.size());
     stage_ct(g, dE, g->bface.data(), 1.0, Bnew.data());
-    for (int k = 0; k < d.n3; k++)
-        for (int j = 0; j < d.n2; j++)
-            for (int i = 0; i < d.n1; i++) {
-                long cc = cidx(g, i, j, k);
-                if (Bnew[cc] != g->bface[cc] || Bnew[cidx(g, i + 1, j, k)] != g->bface[cidx(g, i + 1, j, k)] ||
-                    Bnew[nc + cc] != g->bface[nc + cc] ||
-                    Bnew[nc + cidx(g, i, j + 1, k)] != g->bface[nc + cidx(g, i, j + 1, k)] ||
-                    Bnew[2 * nc + cc] != g->bface[2 * nc + cc] ||
-                    Bnew[2 * nc + cidx(g, i, j, k + 1)] != g->bface[2 * nc + cidx(g, i, j, k + 1)])
-                    mark[cc] = 1;
-            }
+    /* cells on both sides of every face bounded by a corrected edge */
+    for (const EdgeRec& r : m->erec) {
+        if (r.c != c) continue;
+        const int a1 = (r.e == 1) ? 2 : 1, a2 = (r.e == 3) ? 2 : 3;
+        for (int fa = 0; fa < 2; fa++) {
+            const int dfa = fa ? a2 : a1, ob = fa ? a1 : a2;
+            for (int off = -1; off <= 0; off++)
+                for (int side = -1; side <= 0; side++) {
+                    int cell[4] = {0, r.i, r.j, r.k};
+                    cell[ob] += off;
+                    cell[dfa] += side;
+                    if (cell[1] < 0 || cell[2] < 0 || cell[3] < 0 || cell[1] >= d.n1 || cell[2] >= d.n2 ||
+                        cell[3] >= d.n3)
+                        continue;
+                    mark[cidx(g, cell[1], cell[2], cell[3])] = 1;
+                }
+        }
+    }
     /* U of the marked cells with the field before the correction */
     std::vector<double> U0((size_t)NCONS * nc, 0.0);
     for (int k = 0; k < d.n3; k++)

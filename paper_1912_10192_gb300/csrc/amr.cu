@@ -1,0 +1,1204 @@
+// amr.cu -- multi-block grids: static refinement (Sec. 3.2) and local
+// adaptive time stepping (Sec. 3.4), batched over blocks.
+//
+// Device side: ghost zones are filled by sampling the neighbouring block
+// that holds each ghost position (after mapping it across the receiving
+// block's physical boundaries): a copy when the cell sizes agree, the
+// average of the covered cells when the source is finer, the source cell
+// plus offset x MINMOD slope when it is coarser (slopes whose stencil leaves
+// the source interior are 0). A coarser-level source is interpolated in time
+// between its old and new state; a same-level source is read at the same
+// stage; a finer-level source at its current state, extrapolated in time
+// from its last two states at the coarse midpoint stage.
+//
+// Same-level blocks stepped together share face fluxes (the coarser side
+// takes the finer side's average) and edge EMFs (the dominant block's:
+// finest cell along the edge, then finest across it, then lowest index).
+// Across levels, a coarse step's boundary fluxes and EMFs are replaced at
+// its end by the time integrals of the finer level's (refluxing), and its
+// cells next to corrected faces are inverted again.
+//
+// Host side: the links (synchronisation entries, reflux records, refluxed
+// cells) are built once; the launches of one period (2^Lmax fine substeps,
+// levels coarsest first, every kernel batched over the due blocks of a
+// level) are captured into a CUDA graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "grmhd.cuh"
+#include "hamr_internal.h"
+
+namespace hamr {
+namespace {
+
+constexpr int BSA = 128;
+constexpr double PI_ = 3.14159265358979323846;
+
+inline unsigned nb_(long n) { return (unsigned)((n + BSA - 1) / BSA); }
+
+__host__ __device__ inline long pidx(const BlockView& v, int i, int j, int k) {
+    return ((long)(k + NG) * v.n2p + (j + NG)) * v.n1p + (i + NG);
+}
+
+// ------------------------------------------------------------------ lookup
+__host__ __device__ inline int find_block(const AmrDomain& A, const DevBlock* tab, const double x[4]) {
+    int ib[4];
+    for (int d = 1; d <= 3; d++) {
+        double t = (x[d] - A.dlo[d]) / A.bkh[d] + 1e-6;  // a point on a plane belongs to the block above it
+        int q = (int)floor(t);
+        if (q < 0) {
+            if (t < -1e-3) return -1;
+            q = 0;
+        }
+        if (q >= A.nbk[d]) {
+            if (t > A.nbk[d] + 1e-3) return -1;
+            q = A.nbk[d] - 1;
+        }
+        ib[d] = q;
+    }
+    (void)tab;
+    return A.bucket[((long)ib[3] * A.nbk[2] + ib[2]) * A.nbk[1] + ib[1]];
+}
+
+// maps x (outside block B) across B's physical boundaries; fdir = normal of a face point (0: cell centre)
+__host__ __device__ inline void map_point(const AmrDomain& A, const DevBlock& B, double x[4], int fdir, int* neg,
+                                          int* clamp) {
+    *neg = 0;
+    *clamp = 0;
+    for (int d = 1; d <= 3; d++) {
+        const double q = 0.25 * B.h[d];
+        int side = -1;
+        if (x[d] < B.lo[d] - q) side = 0;
+        if (x[d] > B.hi[d] + q) side = 1;
+        if (side < 0) continue;
+        const int bc = B.v.bc[2 * (d - 1) + side];
+        if (bc == HAMR_BC_OUTFLOW || bc == HAMR_BC_OUTFLOW_NOINFLOW) {
+            if (d == fdir)
+                x[d] = side ? B.hi[d] : B.lo[d];
+            else
+                x[d] = side ? B.hi[d] - 0.5 * B.h[d] : B.lo[d] + 0.5 * B.h[d];
+            if (bc == HAMR_BC_OUTFLOW_NOINFLOW && d == 1) *clamp = side ? 1 : -1;
+        } else if (bc == HAMR_BC_PERIODIC) {
+            x[d] += side ? -(A.dhi[d] - A.dlo[d]) : (A.dhi[d] - A.dlo[d]);
+        } else if (bc == HAMR_BC_POLAR) {
+            x[2] = side ? 2.0 * PI_ - x[2] : -x[2];
+            x[3] += PI_;
+            *neg = 1;
+        }
+    }
+    if (A.per[3]) {
+        const double L = A.dhi[3] - A.dlo[3];
+        while (x[3] >= A.dhi[3] - 1e-12 * L) x[3] -= L;
+        while (x[3] < A.dlo[3] - 1e-12 * L) x[3] += L;
+    }
+}
+
+// per-dimension footprint of a target cell (size ht, centre x) in block N
+__host__ __device__ inline void footprint(const DevBlock& N, const double x[4], const double ht[4], int i0[4],
+                                          int cnt[4], double dl[4]) {
+    for (int d = 1; d <= 3; d++) {
+        const double hs = N.h[d];
+        const double r = ht[d] / hs;
+        dl[d] = 0.0;
+        if (r > 1.5) {
+            cnt[d] = (int)llround(r);
+            i0[d] = (int)llround((x[d] - 0.5 * ht[d] - N.lo[d]) / hs);
+        } else {
+            cnt[d] = 1;
+            i0[d] = (int)floor((x[d] - N.lo[d]) / hs);
+            if (r < 0.75) dl[d] = nearbyint(8.0 * (x[d] - (N.lo[d] + (i0[d] + 0.5) * hs)) / hs) / 8.0;
+        }
+    }
+}
+
+// the source state seen by receiver R at stage sigma of substep s
+struct SrcView {
+    const double *Pa, *Pb, *Ba, *Bb;
+    double w;
+    __device__ double P(long i) const { return Pb ? Pa[i] + w * (Pb[i] - Pa[i]) : Pa[i]; }
+    __device__ double B(long i) const { return Bb ? Ba[i] + w * (Bb[i] - Ba[i]) : Ba[i]; }
+};
+
+__device__ inline SrcView source_view(const DevBlock& R, const DevBlock& N, int sigma, int s) {
+    SrcView v;
+    v.Pb = v.Bb = nullptr;
+    v.w = 0.0;
+    if (N.lat > R.lat) {
+        const int s0 = (s >> N.lat) << N.lat;
+        v.Pa = N.Pold;
+        v.Ba = N.Bold;
+        v.Pb = N.P;
+        v.Bb = N.B;
+        v.w = ((double)(s - s0) + sigma * 0.5 * (double)(1 << R.lat)) / (double)(1 << N.lat);
+    } else if (N.lat == R.lat && sigma == 1) {
+        v.Pa = N.Ph;
+        v.Ba = N.Bh;
+    } else if (N.lat < R.lat && sigma == 1) {
+        v.Pa = N.Pold;
+        v.Ba = N.Bold;
+        v.Pb = N.P;
+        v.Bb = N.B;
+        v.w = 1.0 + 0.5 * (double)(1 << R.lat) / (double)(1 << N.lat);
+    } else {
+        v.Pa = N.P;
+        v.Ba = N.B;
+    }
+    return v;
+}
+
+__device__ inline double minmod_(double a, double b) {
+    if (a * b <= 0.0) return 0.0;
+    return fabs(a) < fabs(b) ? a : b;
+}
+
+// ------------------------------------------------------------------ ghost kernels
+__global__ void k_ghost_cells(AmrDomain A, const int* list, int sigma, int s) {
+    const DevBlock& R = A.tab[list[blockIdx.y]];
+    const BlockView& v = R.v;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)v.n1p * v.n2p * v.n3p) return;
+    const int i = (int)(t % v.n1p) - NG, j = (int)((t / v.n1p) % v.n2p) - NG, k = (int)(t / ((long)v.n1p * v.n2p)) - NG;
+    if (i >= 0 && i < v.n1 && j >= 0 && j < v.n2 && k >= 0 && k < v.n3) return;
+    double x[4] = {0.0, R.lo[1] + (i + 0.5) * R.h[1], R.lo[2] + (j + 0.5) * R.h[2], R.lo[3] + (k + 0.5) * R.h[3]};
+    int neg, clamp;
+    map_point(A, R, x, 0, &neg, &clamp);
+    const int n = find_block(A, A.tab, x);
+    if (n < 0) return;
+    const DevBlock& N = A.tab[n];
+    const SrcView S = source_view(R, N, sigma, s);
+    int i0[4], cnt[4];
+    double dl[4];
+    footprint(N, x, R.h, i0, cnt, dl);
+    const int nn[4] = {0, N.v.n1, N.v.n2, N.v.n3};
+    const double inv = 1.0 / (double)(cnt[1] * cnt[2] * cnt[3]);
+    double* out = sigma ? R.Ph : R.P;
+    for (int q = 0; q < NPRIM; q++) {
+        double sum = 0.0;
+        for (int c3 = 0; c3 < cnt[3]; c3++)
+            for (int c2 = 0; c2 < cnt[2]; c2++)
+                for (int c1 = 0; c1 < cnt[1]; c1++) {
+                    const int ii[4] = {0, i0[1] + c1, i0[2] + c2, i0[3] + c3};
+                    const long c = pidx(N.v, ii[1], ii[2], ii[3]);
+                    const double q0 = S.P(q * N.v.nc + c);
+                    double val = q0;
+                    for (int d = 1; d <= 3; d++) {
+                        if (dl[d] == 0.0) continue;
+                        if (ii[d] - 1 < 0 || ii[d] + 1 >= nn[d]) continue;
+                        const long st = (d == 1) ? 1 : ((d == 2) ? (long)N.v.n1p : (long)N.v.n1p * N.v.n2p);
+                        const double qm = S.P(q * N.v.nc + c - st);
+                        const double qp = S.P(q * N.v.nc + c + st);
+                        val += dl[d] * minmod_(q0 - qm, qp - q0);
+                    }
+                    sum += val;
+                }
+        double o = sum * inv;
+        if (neg && (q == U2 || q == B2)) o = -o;
+        if (q == U1) {
+            if (clamp > 0 && o < 0.0) o = 0.0;
+            if (clamp < 0 && o > 0.0) o = 0.0;
+        }
+        out[q * v.nc + t] = o;
+    }
+}
+
+__global__ void k_ghost_faces(AmrDomain A, const int* list, int sigma, int s) {
+    const DevBlock& R = A.tab[list[blockIdx.y]];
+    const BlockView& v = R.v;
+    const long np = (long)v.n1p * v.n2p * v.n3p;
+    const long tt = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tt >= 3 * np) return;
+    const int fd = 1 + (int)(tt / np);
+    const long t = tt % np;
+    const int i = (int)(t % v.n1p) - NG, j = (int)((t / v.n1p) % v.n2p) - NG, k = (int)(t / ((long)v.n1p * v.n2p)) - NG;
+    const int ii[4] = {0, i, j, k};
+    const int nn[4] = {0, v.n1, v.n2, v.n3};
+    bool owned = true;
+    for (int e = 1; e <= 3; e++) {
+        if (e == fd) {
+            if (ii[e] < 0 || ii[e] > nn[e]) owned = false;
+        } else if (ii[e] < 0 || ii[e] >= nn[e]) {
+            owned = false;
+        }
+    }
+    if (owned) return;
+    double x[4] = {0.0, R.lo[1] + (i + 0.5) * R.h[1], R.lo[2] + (j + 0.5) * R.h[2], R.lo[3] + (k + 0.5) * R.h[3]};
+    x[fd] = R.lo[fd] + ii[fd] * R.h[fd];
+    int neg, clamp;
+    map_point(A, R, x, fd, &neg, &clamp);
+    const int n = find_block(A, A.tab, x);
+    if (n < 0) return;
+    const DevBlock& N = A.tab[n];
+    const SrcView S = source_view(R, N, sigma, s);
+    int i0[4], cnt[4];
+    double dl[4];
+    double xc[4] = {0.0, x[1], x[2], x[3]};
+    xc[fd] += 0.5 * R.h[fd];
+    footprint(N, xc, R.h, i0, cnt, dl);
+    const double pos = (x[fd] - N.lo[fd]) / N.h[fd];
+    int p0 = (int)floor(pos + 1e-9);
+    double fr = nearbyint(8.0 * (pos - p0)) / 8.0;
+    if (fr >= 1.0) {
+        p0 += 1;
+        fr = 0.0;
+    }
+    cnt[fd] = 1;
+    const double inv = 1.0 / (double)(cnt[1] * cnt[2] * cnt[3]);
+    const long st = (fd == 1) ? 1 : ((fd == 2) ? (long)N.v.n1p : (long)N.v.n1p * N.v.n2p);
+    double sum = 0.0;
+    for (int c3 = 0; c3 < cnt[3]; c3++)
+        for (int c2 = 0; c2 < cnt[2]; c2++)
+            for (int c1 = 0; c1 < cnt[1]; c1++) {
+                int jj[4] = {0, i0[1] + c1, i0[2] + c2, i0[3] + c3};
+                jj[fd] = p0;
+                const long c = pidx(N.v, jj[1], jj[2], jj[3]);
+                double q = S.B((fd - 1) * N.v.nc + c);
+                if (fr != 0.0) {
+                    const double q1 = S.B((fd - 1) * N.v.nc + c + st);
+                    q = q + fr * (q1 - q);
+                }
+                sum += q;
+            }
+    const double val = sum * inv;
+    double* out = sigma ? R.Bh : R.B;
+    out[(fd - 1) * v.nc + t] = (neg && fd == 2) ? -val : val;
+}
+
+// ------------------------------------------------------------------ synchronisation
+struct SyncDev {  // SoA: dst block, field/face direction, dst index, source block, n <= 4 source indices
+    const int *dst, *dir, *src, *n;
+    const long *di, *si;
+};
+
+__global__ void k_flux_sync(const DevBlock* tab, SyncDev S, int beg, int end) {
+    const int e = beg + (int)((long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= end) return;
+    const DevBlock& D = tab[S.dst[e]];
+    const DevBlock& F = tab[S.src[e]];
+    const int d = S.dir[e];
+    double* Fd = (d == 1) ? D.F1 : ((d == 2) ? D.F2 : D.F3);
+    const double* Fs = (d == 1) ? F.F1 : ((d == 2) ? F.F2 : F.F3);
+    const int n = S.n[e];
+    const double inv = 1.0 / (double)n;
+    for (int q = 0; q < NFLUX; q++) {
+        double sum = 0.0;
+        for (int m = 0; m < n; m++) sum += Fs[q * F.v.nc + S.si[4 * e + m]];
+        Fd[q * D.v.nc + S.di[e]] = sum * inv;
+    }
+}
+
+__global__ void k_edge_gather(const DevBlock* tab, SyncDev S, int beg, int end, double* tmp) {
+    const int e = beg + (int)((long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= end) return;
+    const DevBlock& F = tab[S.src[e]];
+    const int d = S.dir[e];
+    const int n = S.n[e];
+    double sum = 0.0;
+    for (int m = 0; m < n; m++) sum += F.E[(d - 1) * F.v.nc + S.si[4 * e + m]];
+    tmp[e] = sum * (1.0 / (double)n);
+}
+
+__global__ void k_edge_scatter(const DevBlock* tab, SyncDev S, int beg, int end, const double* tmp) {
+    const int e = beg + (int)((long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= end) return;
+    const DevBlock& D = tab[S.dst[e]];
+    D.E[(S.dir[e] - 1) * D.v.nc + S.di[e]] = tmp[e];
+}
+
+// ------------------------------------------------------------------ reflux records
+struct FaceRecDev {
+    const int *c, *f, *d, *n;
+    const long *fi, *ff;  // coarse face index, fine face indices (4 per record)
+    double *own, *acc;    // [NFLUX][nrec]
+    const double* sgnh;   // sign / cell size along d (the correction of the adjacent coarse cell)
+    double* dU;           // [NCONS][nrec]
+};
+struct EdgeRecDev {
+    const int *c, *f, *e, *n;
+    const long *ei, *fe;
+    double *own, *acc;
+};
+
+__global__ void k_face_own(const DevBlock* tab, FaceRecDev R, int nrec, int lat) {
+    const int r = (int)((long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (r >= nrec) return;
+    const DevBlock& C = tab[R.c[r]];
+    if (C.lat != lat) return;
+    const int d = R.d[r];
+    const double* F = (d == 1) ? C.F1 : ((d == 2) ? C.F2 : C.F3);
+    const double dt = C.dscal[0];
+    for (int q = 0; q < NFLUX; q++) {
+        R.own[(long)q * nrec + r] = dt * F[q * C.v.nc + R.fi[r]];
+        R.acc[(long)q * nrec + r] = 0.0;
+    }
+}
+
+__global__ void k_face_acc(const DevBlock* tab, FaceRecDev R, int nrec, int lat) {
+    const int r = (int)((long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (r >= nrec) return;
+    const DevBlock& Fb = tab[R.f[r]];
+    if (Fb.lat != lat) return;
+    const int d = R.d[r];
+    const double* F = (d == 1) ? Fb.F1 : ((d == 2) ? Fb.F2 : Fb.F3);
+    const double dt = Fb.dscal[0];
+    const int n = R.n[r];
+    for (int q = 0; q < NFLUX; q++) {
+        double sum = 0.0;
+        for (int m = 0; m < n; m++) sum += F[q * Fb.v.nc + R.ff[4 * r + m]];
+        R.acc[(long)q * nrec + r] += dt * (sum * (1.0 / (double)n));
+    }
+}
+
+__global__ void k_edge_own(const DevBlock* tab, EdgeRecDev R, int nrec, int lat) {
+    const int r = (int)((long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (r >= nrec) return;
+    const DevBlock& C = tab[R.c[r]];
+    if (C.lat != lat) return;
+    R.own[r] = C.dscal[0] * C.E[(R.e[r] - 1) * C.v.nc + R.ei[r]];
+    R.acc[r] = 0.0;
+}
+
+__global__ void k_edge_acc(const DevBlock* tab, EdgeRecDev R, int nrec, int lat) {
+    const int r = (int)((long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (r >= nrec) return;
+    const DevBlock& Fb = tab[R.f[r]];
+    if (Fb.lat != lat) return;
+    const int n = R.n[r];
+    double sum = 0.0;
+    for (int m = 0; m < n; m++) sum += Fb.E[(R.e[r] - 1) * Fb.v.nc + R.fe[4 * r + m]];
+    R.acc[r] += Fb.dscal[0] * (sum * (1.0 / (double)n));
+}
+
+// per face record of coarse blocks of level lat: its correction of the adjacent cell
+__global__ void k_face_du(const DevBlock* tab, FaceRecDev R, int nrec, int lat) {
+    const int r = (int)((long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (r >= nrec) return;
+    if (tab[R.c[r]].lat != lat) return;
+    for (int q = 0; q < NCONS; q++)
+        R.dU[(long)q * nrec + r] = R.sgnh[r] * (R.acc[(long)q * nrec + r] - R.own[(long)q * nrec + r]);
+}
+
+// the EMF corrections of coarse blocks of level lat, written into their (zeroed) E arrays
+__global__ void k_edge_corr(const DevBlock* tab, EdgeRecDev R, int nrec, int lat) {
+    const int r = (int)((long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (r >= nrec) return;
+    const DevBlock& C = tab[R.c[r]];
+    if (C.lat != lat) return;
+    C.E[(R.e[r] - 1) * C.v.nc + R.ei[r]] = R.acc[r] - R.own[r];
+}
+
+__global__ void k_zero_E(const DevBlock* tab, const int* list) {
+    const DevBlock& D = tab[list[blockIdx.y]];
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * D.v.nc) return;
+    D.E[t] = 0.0;
+}
+
+// ------------------------------------------------------------------ period dt and counters
+__global__ void k_period_begin(const DevBlock* tab, int nb) {
+    const int b = (int)((long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (b >= nb) return;
+    tab[b].dmax[0] = 0ull;
+    for (int q = 0; q < 4; q++) tab[b].dcnt[q] = 0ull;
+}
+
+__global__ void k_period_dt(const DevBlock* tab, int nb, double cour, double* dtf_out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double dtf = 1e300;
+    for (int b = 0; b < nb; b++) {
+        const double rate = __longlong_as_double((long long)tab[b].dmax[0]);
+        dtf = fmin(dtf, cour / rate / (double)(1 << tab[b].lat));
+    }
+    for (int b = 0; b < nb; b++) tab[b].dscal[0] = dtf * (double)(1 << tab[b].lat);
+    dtf_out[0] = dtf;
+}
+
+// ------------------------------------------------------------------ host-side links
+struct HostDomain {
+    std::vector<DevBlock> b;
+    std::vector<int> bucket;
+    AmrDomain A;  // host copy (bucket pointer = host vector)
+};
+
+int hfind(const HostDomain& H, const double x[4]) { return find_block(H.A, H.b.data(), x); }
+
+void wrap(const HostDomain& H, double& x, int d, const DevBlock& N) {
+    if (!H.A.per[d]) return;
+    const double L = H.A.dhi[d] - H.A.dlo[d];
+    if (x < N.lo[d] - 1e-9 * L) x += L;
+    if (x > N.hi[d] + 1e-9 * L) x -= L;
+}
+
+bool finer_than(const DevBlock& A, const DevBlock& C) {
+    bool st = false;
+    for (int d = 1; d <= 3; d++) {
+        if (A.h[d] > C.h[d] * (1 + 1e-9)) return false;
+        if (A.h[d] < C.h[d] * (1 - 1e-9)) st = true;
+    }
+    return st;
+}
+
+bool dominates(const HostDomain& H, int a, int c, int e) {
+    const DevBlock& A = H.b[a];
+    const DevBlock& C = H.b[c];
+    if (A.h[e] != C.h[e]) return A.h[e] < C.h[e];
+    const double va = A.h[1] * A.h[2] * A.h[3], vc = C.h[1] * C.h[2] * C.h[3];
+    if (va != vc) return va < vc;
+    return a < c;
+}
+
+void blocks_around_edge(const HostDomain& H, int b, const double p[4], int e, std::vector<int>& out) {
+    const DevBlock& B = H.b[b];
+    const int a1 = (e == 1) ? 2 : 1, a2 = (e == 3) ? 2 : 3;
+    out.clear();
+    for (int sa = -1; sa <= 1; sa += 2)
+        for (int sb = -1; sb <= 1; sb += 2) {
+            double x[4] = {0.0, p[1], p[2], p[3]};
+            x[a1] += sa * 0.25 * B.h[a1];
+            x[a2] += sb * 0.25 * B.h[a2];
+            bool outside = false;
+            for (int d = 1; d <= 3; d++) {
+                if (H.A.per[d]) {
+                    const double L = H.A.dhi[d] - H.A.dlo[d];
+                    if (x[d] < H.A.dlo[d]) x[d] += L;
+                    if (x[d] >= H.A.dhi[d]) x[d] -= L;
+                } else if (x[d] < H.A.dlo[d] || x[d] > H.A.dhi[d]) {
+                    outside = true;
+                }
+            }
+            if (outside) continue;
+            const int n = hfind(H, x);
+            if (n >= 0 && std::find(out.begin(), out.end(), n) == out.end()) out.push_back(n);
+        }
+}
+
+void cover_edge(const HostDomain& H, int n, const double p[4], int e, double he, std::vector<long>& out) {
+    const DevBlock& N = H.b[n];
+    out.clear();
+    int idx[4] = {0, 0, 0, 0};
+    for (int d = 1; d <= 3; d++) {
+        if (d == e) continue;
+        double x = p[d];
+        wrap(H, x, d, N);
+        idx[d] = (int)llround((x - N.lo[d]) / N.h[d]);
+    }
+    int cnt = std::max(1, (int)llround(he / N.h[e]));
+    double x0 = p[e] - 0.5 * he;
+    if (H.A.per[e]) {
+        const double L = H.A.dhi[e] - H.A.dlo[e];
+        if (x0 < N.lo[e] - 1e-9 * L) x0 += L;
+        if (x0 > N.hi[e] - 1e-9 * L) x0 -= L;
+    }
+    const int i0 = (int)llround((x0 - N.lo[e]) / N.h[e]);
+    for (int c = 0; c < cnt; c++) {
+        idx[e] = i0 + c;
+        out.push_back(pidx(N.v, idx[1], idx[2], idx[3]));
+    }
+}
+
+void cover_face(const HostDomain& H, int n, const double p[4], int d, const double hb[4], std::vector<long>& out) {
+    const DevBlock& N = H.b[n];
+    out.clear();
+    int i0[4], cnt[4];
+    for (int e = 1; e <= 3; e++) {
+        double x = p[e];
+        wrap(H, x, e, N);
+        if (e == d) {
+            i0[e] = (int)llround((x - N.lo[e]) / N.h[e]);
+            cnt[e] = 1;
+        } else {
+            cnt[e] = std::max(1, (int)llround(hb[e] / N.h[e]));
+            i0[e] = (int)llround((x - 0.5 * hb[e] - N.lo[e]) / N.h[e]);
+        }
+    }
+    for (int c3 = 0; c3 < cnt[3]; c3++)
+        for (int c2 = 0; c2 < cnt[2]; c2++)
+            for (int c1 = 0; c1 < cnt[1]; c1++) out.push_back(pidx(N.v, i0[1] + c1, i0[2] + c2, i0[3] + c3));
+}
+
+struct HSync {
+    int dst, dir, src;
+    long di;
+    std::vector<long> si;
+};
+struct HFace {
+    int c, d, side, i, j, k, f;
+    std::vector<long> ff;
+};
+struct HEdge {
+    int c, e, i, j, k, f;
+    std::vector<long> fe;
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------ AmrImpl
+struct AmrImpl {
+    PhysArgs ph;
+    int nb = 0, Lmax = 0;
+    HostDomain H;
+    DevBlock* dtab = nullptr;
+    int* dbucket = nullptr;
+    std::vector<void*> allocs;
+    std::vector<std::vector<int>> lev;  // blocks of each level
+    std::vector<int*> dlev;             // device copies
+    int* dall = nullptr;                // all blocks
+    long mw_pad = 0, mw_recon = 0, mw_flux[4] = {0, 0, 0, 0}, mw_edge = 0, mw_cell = 0;
+    std::vector<long> lmw_pad, lmw_recon, lmw_edge, lmw_cell;
+    std::vector<std::vector<long>> lmw_flux;
+    // synchronisation
+    SyncDev fs{}, es{};
+    std::vector<int> fs_beg, fs_end, es_beg, es_end;
+    double* es_tmp = nullptr;
+    int n_fs = 0, n_es = 0;
+    // reflux
+    FaceRecDev fr{};
+    EdgeRecDev er{};
+    int n_fr = 0, n_er = 0;
+    std::vector<int> rc_beg, rc_end;  // refluxed cells per level
+    int* rc_blk = nullptr;
+    long* rc_idx = nullptr;
+    int* rc_nrec = nullptr;
+    int* rc_recs = nullptr;
+    double* rc_U = nullptr;
+    int n_rc = 0;
+    std::vector<std::vector<int>> lev_edgefix;  // blocks of each level with edge corrections
+    std::vector<int*> dlev_edgefix;
+    double* dtf = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaStream_t cap = nullptr;
+
+    template <typename T>
+    T* dev(const std::vector<T>& h) {
+        T* p = nullptr;
+        size_t n = std::max<size_t>(h.size(), 1);
+        if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) return nullptr;
+        allocs.push_back(p);
+        if (!h.empty()) cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+        return p;
+    }
+    ~AmrImpl() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
+        for (void* p : allocs) cudaFree(p);
+    }
+};
+
+namespace {
+
+int build_links(AmrImpl& M, std::vector<HSync>& fsync, std::vector<HSync>& esync, std::vector<HFace>& frec,
+                std::vector<HEdge>& erec) {
+    const HostDomain& H = M.H;
+    for (int b = 0; b < M.nb; b++) {
+        const DevBlock& B = H.b[b];
+        const int nn[4] = {0, B.v.n1, B.v.n2, B.v.n3};
+        for (int fd = 1; fd <= 3; fd++)
+            for (int side = 0; side < 2; side++) {
+                const int bcv = B.v.bc[2 * (fd - 1) + side];
+                if (bcv != HAMR_BC_BLOCK && bcv != HAMR_BC_PERIODIC) continue;
+                const int t1 = (fd == 1) ? 2 : 1, t2 = (fd == 3) ? 2 : 3;
+                for (int b2 = 0; b2 < nn[t2]; b2++)
+                    for (int b1 = 0; b1 < nn[t1]; b1++) {
+                        int ii[4];
+                        ii[fd] = side ? nn[fd] : 0;
+                        ii[t1] = b1;
+                        ii[t2] = b2;
+                        double p[4] = {0.0, B.lo[1] + (ii[1] + 0.5) * B.h[1], B.lo[2] + (ii[2] + 0.5) * B.h[2],
+                                       B.lo[3] + (ii[3] + 0.5) * B.h[3]};
+                        p[fd] = side ? B.hi[fd] : B.lo[fd];
+                        double q[4] = {0.0, p[1], p[2], p[3]};
+                        q[fd] += (side ? 0.25 : -0.25) * B.h[fd];
+                        if (H.A.per[fd]) {
+                            const double L = H.A.dhi[fd] - H.A.dlo[fd];
+                            if (q[fd] < H.A.dlo[fd]) q[fd] += L;
+                            if (q[fd] >= H.A.dhi[fd]) q[fd] -= L;
+                        }
+                        const int n = hfind(H, q);
+                        if (n < 0 || n == b) continue;
+                        const DevBlock& N = H.b[n];
+                        if (!finer_than(N, B) && !(N.lat < B.lat)) continue;
+                        const long fi = pidx(B.v, ii[1], ii[2], ii[3]);
+                        std::vector<long> cov;
+                        cover_face(H, n, p, fd, B.h, cov);
+                        if (cov.size() > 4) return -1;
+                        if (N.lat == B.lat) {
+                            if (!finer_than(N, B)) continue;
+                            fsync.push_back({b, fd, n, fi, cov});
+                        } else {
+                            frec.push_back({b, fd, side, ii[1], ii[2], ii[3], n, cov});
+                        }
+                    }
+            }
+        for (int e = 1; e <= 3; e++) {
+            const int a1 = (e == 1) ? 2 : 1, a2 = (e == 3) ? 2 : 3;
+            for (int k = 0; k <= nn[3]; k++)
+                for (int j = 0; j <= nn[2]; j++)
+                    for (int i = 0; i <= nn[1]; i++) {
+                        const int ii[4] = {0, i, j, k};
+                        if (ii[e] >= nn[e]) continue;
+                        const bool bnd = (ii[a1] == 0 || ii[a1] == nn[a1] || ii[a2] == 0 || ii[a2] == nn[a2]);
+                        if (!bnd) continue;
+                        if (e != 2 && ((B.v.bc[2] == HAMR_BC_POLAR && j == 0) || (B.v.bc[3] == HAMR_BC_POLAR && j == nn[2])))
+                            continue;
+                        double p[4];
+                        for (int d = 1; d <= 3; d++) p[d] = B.lo[d] + ii[d] * B.h[d];
+                        p[e] += 0.5 * B.h[e];
+                        std::vector<int> around;
+                        blocks_around_edge(H, b, p, e, around);
+                        int gd = b;
+                        for (int n : around)
+                            if (H.b[n].lat < H.b[gd].lat || (H.b[n].lat == H.b[gd].lat && dominates(H, n, gd, e))) gd = n;
+                        int sd = b;
+                        for (int n : around)
+                            if (H.b[n].lat == B.lat && dominates(H, n, sd, e)) sd = n;
+                        const long ei = pidx(B.v, i, j, k);
+                        if (sd != b) {
+                            HSync r{b, e, sd, ei, {}};
+                            cover_edge(H, sd, p, e, B.h[e], r.si);
+                            if (r.si.size() > 4) return -1;
+                            esync.push_back(r);
+                        }
+                        if (H.b[gd].lat < B.lat) {
+                            HEdge r{b, e, i, j, k, gd, {}};
+                            cover_edge(H, gd, p, e, B.h[e], r.fe);
+                            if (r.fe.size() > 4) return -1;
+                            erec.push_back(r);
+                        }
+                    }
+        }
+    }
+    return 0;
+}
+
+}  // namespace
+
+int amr_create(AmrImpl** out, const hamr_grid_desc& d, const std::vector<BlockView>& views,
+               const std::vector<BlockState>& st, const PhysArgs& ph) {
+    *out = nullptr;
+    AmrImpl* M = new AmrImpl;
+    M->ph = ph;
+    M->nb = d.nblocks;
+    HostDomain& H = M->H;
+    H.b.resize(M->nb);
+    for (int e = 1; e <= 3; e++) {
+        H.A.dlo[e] = 1e300;
+        H.A.dhi[e] = -1e300;
+        H.A.per[e] = 0;
+    }
+    double bmin[4] = {0, 1e300, 1e300, 1e300};
+    for (int b = 0; b < M->nb; b++) {
+        const hamr_block_desc& o = d.blocks[b];
+        DevBlock& D = H.b[b];
+        std::memset(&D, 0, sizeof(D));
+        D.v = views[b];
+        const double x0[4] = {0, o.x1min, o.x2min, o.x3min}, hh[4] = {0, o.dx1, o.dx2, o.dx3};
+        const int nn[4] = {0, o.n1, o.n2, o.n3};
+        for (int e = 1; e <= 3; e++) {
+            D.lo[e] = x0[e];
+            D.h[e] = hh[e];
+            D.hi[e] = x0[e] + nn[e] * hh[e];
+            H.A.dlo[e] = std::min(H.A.dlo[e], D.lo[e]);
+            H.A.dhi[e] = std::max(H.A.dhi[e], D.hi[e]);
+            bmin[e] = std::min(bmin[e], D.hi[e] - D.lo[e]);
+            if (o.bc[2 * (e - 1)] == HAMR_BC_PERIODIC) H.A.per[e] = 1;
+        }
+        if (o.lat < 0 || o.lat > 7) {
+            delete M;
+            return set_error(HAMR_EINVAL, "block %d: lat must be in 0..7", b);
+        }
+        D.lat = o.lat;
+        M->Lmax = std::max(M->Lmax, o.lat);
+        const BlockState& s = st[b];
+        D.P = s.P;
+        D.B = s.B;
+        D.Ph = s.Ph;
+        D.Bh = s.Bh;
+        D.QL = s.QL;
+        D.QR = s.QR;
+        D.F1 = s.F[0];
+        D.F2 = s.F[1];
+        D.F3 = s.F[2];
+        D.E = s.E;
+        D.Un = s.Un;
+        D.status = s.status;
+        D.dscal = s.dscal;
+        D.dmax = s.dmax;
+        D.dcnt = s.dcnt;
+        void* old = nullptr;
+        if (cudaMalloc(&old, sizeof(double) * 11 * views[b].nc) != cudaSuccess) {
+            cudaGetLastError();
+            delete M;
+            return set_error(HAMR_ENOMEM, "allocation of the time-interpolation state of block %d failed", b);
+        }
+        M->allocs.push_back(old);
+        cudaMemset(old, 0, sizeof(double) * 11 * views[b].nc);
+        D.Pold = (double*)old;
+        D.Bold = D.Pold + 8 * views[b].nc;
+    }
+    // bucket grid at the smallest block extent; every block must be aligned to it
+    for (int e = 1; e <= 3; e++) {
+        H.A.bkh[e] = bmin[e];
+        H.A.nbk[e] = (int)llround((H.A.dhi[e] - H.A.dlo[e]) / bmin[e]);
+    }
+    const long nbk = (long)H.A.nbk[1] * H.A.nbk[2] * H.A.nbk[3];
+    if (nbk > (1L << 24)) {
+        delete M;
+        return set_error(HAMR_EINVAL, "block layout too irregular for the bucket lookup");
+    }
+    H.bucket.assign(nbk, -1);
+    for (int b = 0; b < M->nb; b++) {
+        const DevBlock& D = H.b[b];
+        int lo[4], hi[4];
+        for (int e = 1; e <= 3; e++) {
+            const double a = (D.lo[e] - H.A.dlo[e]) / H.A.bkh[e], z = (D.hi[e] - H.A.dlo[e]) / H.A.bkh[e];
+            lo[e] = (int)llround(a);
+            hi[e] = (int)llround(z);
+            if (std::fabs(a - lo[e]) > 1e-6 || std::fabs(z - hi[e]) > 1e-6) {
+                delete M;
+                return set_error(HAMR_EINVAL, "block %d is not aligned to the block grid", b);
+            }
+        }
+        for (int k = lo[3]; k < hi[3]; k++)
+            for (int j = lo[2]; j < hi[2]; j++)
+                for (int i = lo[1]; i < hi[1]; i++) {
+                    int& slot = H.bucket[((long)k * H.A.nbk[2] + j) * H.A.nbk[1] + i];
+                    if (slot >= 0) {
+                        delete M;
+                        return set_error(HAMR_EINVAL, "blocks %d and %d overlap", slot, b);
+                    }
+                    slot = b;
+                }
+    }
+    for (long q = 0; q < nbk; q++)
+        if (H.bucket[q] < 0) {
+            delete M;
+            return set_error(HAMR_EINVAL, "the blocks leave a hole in the domain");
+        }
+    H.A.bucket = H.bucket.data();
+    H.A.tab = H.b.data();
+    H.A.nb = M->nb;
+
+    std::vector<HSync> fsync, esync;
+    std::vector<HFace> frec;
+    std::vector<HEdge> erec;
+    if (build_links(*M, fsync, esync, frec, erec)) {
+        delete M;
+        return set_error(HAMR_EINVAL, "a face or edge is covered by more than 4 finer faces or edges");
+    }
+    // every precomputed index must address the block's padded arrays
+    {
+        auto ok = [&](int b, long i) {
+            const BlockView& v = H.b[b].v;
+            return b >= 0 && b < M->nb && i >= 0 && i < (long)v.n1p * v.n2p * v.n3p;
+        };
+        bool good = true;
+        for (const HSync& r : fsync) {
+            good = good && ok(r.dst, r.di);
+            for (long q : r.si) good = good && ok(r.src, q);
+        }
+        for (const HSync& r : esync) {
+            good = good && ok(r.dst, r.di);
+            for (long q : r.si) good = good && ok(r.src, q);
+        }
+        for (const HFace& r : frec) {
+            good = good && ok(r.c, pidx(H.b[r.c].v, r.i, r.j, r.k));
+            for (long q : r.ff) good = good && ok(r.f, q);
+        }
+        for (const HEdge& r : erec) {
+            good = good && ok(r.c, pidx(H.b[r.c].v, r.i, r.j, r.k));
+            for (long q : r.fe) good = good && ok(r.f, q);
+        }
+        if (!good) {
+            delete M;
+            return set_error(HAMR_EINVAL, "inconsistent block layout: a link index falls outside its block");
+        }
+    }
+    // sort the synchronisation entries by the level of their destination (stable: keep order)
+    auto by_level = [&](std::vector<HSync>& v, std::vector<int>& beg, std::vector<int>& end) {
+        std::stable_sort(v.begin(), v.end(), [&](const HSync& a, const HSync& b) { return H.b[a.dst].lat < H.b[b.dst].lat; });
+        beg.assign(M->Lmax + 1, 0);
+        end.assign(M->Lmax + 1, 0);
+        for (int L = 0; L <= M->Lmax; L++) {
+            beg[L] = (int)(std::lower_bound(v.begin(), v.end(), L, [&](const HSync& a, int l) { return H.b[a.dst].lat < l; }) - v.begin());
+            end[L] = (int)(std::upper_bound(v.begin(), v.end(), L, [&](int l, const HSync& a) { return l < H.b[a.dst].lat; }) - v.begin());
+        }
+    };
+    by_level(fsync, M->fs_beg, M->fs_end);
+    by_level(esync, M->es_beg, M->es_end);
+    auto sync_dev = [&](const std::vector<HSync>& v, SyncDev& S) {
+        std::vector<int> dst, dir, src, n;
+        std::vector<long> di, si;
+        for (const HSync& r : v) {
+            dst.push_back(r.dst);
+            dir.push_back(r.dir);
+            src.push_back(r.src);
+            n.push_back((int)r.si.size());
+            di.push_back(r.di);
+            for (int m = 0; m < 4; m++) si.push_back(m < (int)r.si.size() ? r.si[m] : 0);
+        }
+        S.dst = M->dev(dst);
+        S.dir = M->dev(dir);
+        S.src = M->dev(src);
+        S.n = M->dev(n);
+        S.di = M->dev(di);
+        S.si = M->dev(si);
+    };
+    sync_dev(fsync, M->fs);
+    sync_dev(esync, M->es);
+    M->n_fs = (int)fsync.size();
+    M->n_es = (int)esync.size();
+    M->es_tmp = M->dev(std::vector<double>(std::max<size_t>(esync.size(), 1), 0.0));
+
+    // reflux records
+    {
+        std::vector<int> c, f, dd, n;
+        std::vector<long> fi, ff;
+        std::vector<double> sgnh;
+        for (const HFace& r : frec) {
+            c.push_back(r.c);
+            f.push_back(r.f);
+            dd.push_back(r.d);
+            n.push_back((int)r.ff.size());
+            fi.push_back(pidx(H.b[r.c].v, r.i, r.j, r.k));
+            for (int m = 0; m < 4; m++) ff.push_back(m < (int)r.ff.size() ? r.ff[m] : 0);
+            sgnh.push_back((r.side ? -1.0 : 1.0) / H.b[r.c].h[r.d]);
+        }
+        M->n_fr = (int)frec.size();
+        M->fr.c = M->dev(c);
+        M->fr.f = M->dev(f);
+        M->fr.d = M->dev(dd);
+        M->fr.n = M->dev(n);
+        M->fr.fi = M->dev(fi);
+        M->fr.ff = M->dev(ff);
+        M->fr.sgnh = M->dev(sgnh);
+        std::vector<double> z((size_t)NFLUX * std::max(M->n_fr, 1), 0.0);
+        M->fr.own = M->dev(z);
+        M->fr.acc = M->dev(z);
+        M->fr.dU = M->dev(z);
+    }
+    {
+        std::vector<int> c, f, e, n;
+        std::vector<long> ei, fe;
+        for (const HEdge& r : erec) {
+            c.push_back(r.c);
+            f.push_back(r.f);
+            e.push_back(r.e);
+            n.push_back((int)r.fe.size());
+            ei.push_back(pidx(H.b[r.c].v, r.i, r.j, r.k));
+            for (int m = 0; m < 4; m++) fe.push_back(m < (int)r.fe.size() ? r.fe[m] : 0);
+        }
+        M->n_er = (int)erec.size();
+        M->er.c = M->dev(c);
+        M->er.f = M->dev(f);
+        M->er.e = M->dev(e);
+        M->er.n = M->dev(n);
+        M->er.ei = M->dev(ei);
+        M->er.fe = M->dev(fe);
+        std::vector<double> z(std::max(M->n_er, 1), 0.0);
+        M->er.own = M->dev(z);
+        M->er.acc = M->dev(z);
+    }
+    // refluxed cells: the cell next to each face record, and the cells on both
+    // sides of every face bounded by a corrected edge; per block, in cell order
+    {
+        struct RC {
+            int blk;
+            long idx;
+            std::vector<int> recs;
+        };
+        std::vector<std::vector<RC>> per_block(M->nb);
+        auto add_cell = [&](int b, int i, int j, int k, int rec) {
+            const DevBlock& B = H.b[b];
+            if (i < 0 || j < 0 || k < 0 || i >= B.v.n1 || j >= B.v.n2 || k >= B.v.n3) return;
+            const long c = pidx(B.v, i, j, k);
+            for (RC& x : per_block[b])
+                if (x.idx == c) {
+                    if (rec >= 0) x.recs.push_back(rec);
+                    return;
+                }
+            RC x{b, c, {}};
+            if (rec >= 0) x.recs.push_back(rec);
+            per_block[b].push_back(x);
+        };
+        for (int r = 0; r < (int)frec.size(); r++) {
+            int ii[4] = {0, frec[r].i, frec[r].j, frec[r].k};
+            if (frec[r].side == 1) ii[frec[r].d]--;
+            add_cell(frec[r].c, ii[1], ii[2], ii[3], r);
+        }
+        std::vector<char> edgefix(M->nb, 0);
+        for (const HEdge& r : erec) {
+            edgefix[r.c] = 1;
+            const int a1 = (r.e == 1) ? 2 : 1, a2 = (r.e == 3) ? 2 : 3;
+            // faces of directions a1 and a2 bounded by the edge, and the cells on both sides of each
+            for (int fa : {a1, a2}) {
+                const int ob = (fa == a1) ? a2 : a1;  // the face spans the edge's other normal direction
+                for (int off = -1; off <= 0; off++) {
+                    int face[4] = {0, r.i, r.j, r.k};
+                    face[ob] += off;  // the two faces of direction fa touching the edge
+                    for (int side = -1; side <= 0; side++) {
+                        int cell[4] = {0, face[1], face[2], face[3]};
+                        cell[fa] += side;
+                        add_cell(r.c, cell[1], cell[2], cell[3], -1);
+                    }
+                }
+            }
+        }
+        std::vector<int> blk, nrec, recs;
+        std::vector<long> idx;
+        M->rc_beg.assign(M->Lmax + 1, 0);
+        M->rc_end.assign(M->Lmax + 1, 0);
+        for (int L = 0; L <= M->Lmax; L++) {
+            M->rc_beg[L] = (int)blk.size();
+            for (int b = 0; b < M->nb; b++) {
+                if (H.b[b].lat != L) continue;
+                std::vector<RC>& v = per_block[b];
+                std::sort(v.begin(), v.end(), [](const RC& a, const RC& c) { return a.idx < c.idx; });
+                for (const RC& x : v) {
+                    if (x.recs.size() > 3) {
+                        delete M;
+                        return set_error(HAMR_EINVAL, "a refluxed cell with more than 3 corrected faces");
+                    }
+                    blk.push_back(x.blk);
+                    idx.push_back(x.idx);
+                    nrec.push_back((int)x.recs.size());
+                    std::vector<int> rs = x.recs;
+                    std::sort(rs.begin(), rs.end());
+                    for (int m = 0; m < 3; m++) recs.push_back(m < (int)rs.size() ? rs[m] : 0);
+                }
+            }
+            M->rc_end[L] = (int)blk.size();
+        }
+        M->n_rc = (int)blk.size();
+        M->rc_blk = M->dev(blk);
+        M->rc_idx = M->dev(idx);
+        M->rc_nrec = M->dev(nrec);
+        M->rc_recs = M->dev(recs);
+        M->rc_U = M->dev(std::vector<double>((size_t)NCONS * std::max(M->n_rc, 1), 0.0));
+        M->lev_edgefix.assign(M->Lmax + 1, {});
+        for (int b = 0; b < M->nb; b++)
+            if (edgefix[b]) M->lev_edgefix[H.b[b].lat].push_back(b);
+        for (int L = 0; L <= M->Lmax; L++) M->dlev_edgefix.push_back(M->dev(M->lev_edgefix[L]));
+    }
+    // device tables
+    for (int b = 0; b < M->nb; b++) {
+        const BlockView& v = H.b[b].v;
+        // dscal[1] = 1 (unit time factor of the EMF-correction curl)
+        const double one = 1.0;
+        cudaMemcpy(H.b[b].dscal + 1, &one, sizeof(double), cudaMemcpyHostToDevice);
+        (void)v;
+    }
+    M->dtab = M->dev(H.b);
+    M->dbucket = M->dev(H.bucket);
+    M->lev.assign(M->Lmax + 1, {});
+    std::vector<int> all;
+    for (int b = 0; b < M->nb; b++) {
+        M->lev[H.b[b].lat].push_back(b);
+        all.push_back(b);
+    }
+    for (int L = 0; L <= M->Lmax; L++) M->dlev.push_back(M->dev(M->lev[L]));
+    M->dall = M->dev(all);
+    M->lmw_pad.assign(M->Lmax + 1, 0);
+    M->lmw_recon.assign(M->Lmax + 1, 0);
+    M->lmw_edge.assign(M->Lmax + 1, 0);
+    M->lmw_cell.assign(M->Lmax + 1, 0);
+    M->lmw_flux.assign(M->Lmax + 1, std::vector<long>(4, 0));
+    for (int b = 0; b < M->nb; b++) {
+        const BlockView& v = H.b[b].v;
+        const int L = H.b[b].lat;
+        const long pad = (long)v.n1p * v.n2p * v.n3p;
+        const long rec = (long)(v.n1 + 2) * (v.n2 + 2) * (v.n3 + 2);
+        const long edg = (long)(v.n1 + 1) * (v.n2 + 1) * (v.n3 + 1);
+        const long cel = (long)v.n1 * v.n2 * v.n3;
+        M->lmw_pad[L] = std::max(M->lmw_pad[L], pad);
+        M->lmw_recon[L] = std::max(M->lmw_recon[L], rec);
+        M->lmw_edge[L] = std::max(M->lmw_edge[L], edg);
+        M->lmw_cell[L] = std::max(M->lmw_cell[L], cel);
+        M->lmw_flux[L][1] = std::max(M->lmw_flux[L][1], (long)(v.n1 + 1) * (v.n2 + 2) * (v.n3 + 2));
+        M->lmw_flux[L][2] = std::max(M->lmw_flux[L][2], (long)(v.n1 + 2) * (v.n2 + 1) * (v.n3 + 2));
+        M->lmw_flux[L][3] = std::max(M->lmw_flux[L][3], (long)(v.n1 + 2) * (v.n2 + 2) * (v.n3 + 1));
+        M->mw_pad = std::max(M->mw_pad, pad);
+        M->mw_cell = std::max(M->mw_cell, cel);
+    }
+    M->dtf = M->dev(std::vector<double>(4, 0.0));
+    H.A.tab = M->dtab;
+    H.A.bucket = M->dbucket;
+    if (cudaStreamCreateWithFlags(&M->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        delete M;
+        return set_error(HAMR_ECUDA, "stream creation failed");
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        delete M;
+        return set_error(HAMR_ECUDA, "multi-block set-up failed: %s", cudaGetErrorString(e));
+    }
+    // host-side lookups must keep host pointers
+    *out = M;
+    return HAMR_OK;
+}
+
+void amr_destroy(AmrImpl* M) { delete M; }
+
+int amr_after_load(AmrImpl* M, int b, cudaStream_t s) {
+    // no history yet: the previous state is the loaded one
+    const DevBlock& D = M->H.b[b];
+    cudaError_t e = cudaMemcpyAsync(D.Pold, D.P, sizeof(double) * 8 * D.v.nc, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(D.Bold, D.B, sizeof(double) * 3 * D.v.nc, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return set_error(HAMR_ECUDA, "state copy failed: %s", cudaGetErrorString(e));
+    return HAMR_OK;
+}
+
+namespace {
+
+#define AM_TRY(call)                                                                                           \
+    do {                                                                                                       \
+        cudaError_t e_ = (call);                                                                               \
+        if (e_ != cudaSuccess) return set_error(HAMR_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+int group_step(AmrImpl& M, int L, int s, cudaStream_t cs) {
+    const int nl = (int)M.lev[L].size();
+    const int* list = M.dlev[L];
+    const DevBlock* tab = M.dtab;
+    const PhysArgs& ph = M.ph;
+    AM_TRY(launch_save_old_batch(tab, list, nl, M.lmw_pad[L], cs));
+    for (int sigma = 0; sigma < 2; sigma++) {
+        k_ghost_cells<<<dim3(nb_(M.lmw_pad[L]), nl), BSA, 0, cs>>>(M.H.A, list, sigma, s);
+        k_ghost_faces<<<dim3(nb_(3 * M.lmw_pad[L]), nl), BSA, 0, cs>>>(M.H.A, list, sigma, s);
+        AM_TRY(cudaGetLastError());
+        for (int dir = 1; dir <= 3; dir++) {
+            AM_TRY(launch_recon_batch(tab, list, nl, M.lmw_recon[L], ph, dir, sigma, cs));
+            AM_TRY(launch_flux_batch(tab, list, nl, M.lmw_flux[L][dir], ph, dir, sigma, cs));
+        }
+        const int fb = M.fs_beg[L], fe = M.fs_end[L];
+        if (fe > fb) k_flux_sync<<<nb_(fe - fb), BSA, 0, cs>>>(tab, M.fs, fb, fe);
+        AM_TRY(launch_emf_batch(tab, list, nl, M.lmw_edge[L], cs));
+        const int eb = M.es_beg[L], ee = M.es_end[L];
+        if (ee > eb) {
+            k_edge_gather<<<nb_(ee - eb), BSA, 0, cs>>>(tab, M.es, eb, ee, M.es_tmp);
+            k_edge_scatter<<<nb_(ee - eb), BSA, 0, cs>>>(tab, M.es, eb, ee, M.es_tmp);
+        }
+        AM_TRY(cudaGetLastError());
+        if (sigma == 1) {
+            if (M.n_fr) {
+                k_face_own<<<nb_(M.n_fr), BSA, 0, cs>>>(tab, M.fr, M.n_fr, L);
+                k_face_acc<<<nb_(M.n_fr), BSA, 0, cs>>>(tab, M.fr, M.n_fr, L);
+            }
+            if (M.n_er) {
+                k_edge_own<<<nb_(M.n_er), BSA, 0, cs>>>(tab, M.er, M.n_er, L);
+                k_edge_acc<<<nb_(M.n_er), BSA, 0, cs>>>(tab, M.er, M.n_er, L);
+            }
+            AM_TRY(cudaGetLastError());
+        }
+        AM_TRY(launch_ct_batch(tab, list, nl, M.lmw_edge[L], sigma, cs));
+        AM_TRY(launch_update_batch(tab, list, nl, M.lmw_cell[L], ph, sigma, cs));
+    }
+    return HAMR_OK;
+}
+
+int reflux_level(AmrImpl& M, int L, cudaStream_t cs) {
+    const int cb = M.rc_beg[L], ce = M.rc_end[L];
+    const int ne = (int)M.lev_edgefix[L].size();
+    if (ce == cb && ne == 0) return HAMR_OK;
+    const DevBlock* tab = M.dtab;
+    if (M.n_fr) k_face_du<<<nb_(M.n_fr), BSA, 0, cs>>>(tab, M.fr, M.n_fr, L);
+    AM_TRY(cudaGetLastError());
+    AM_TRY(launch_reflux_u0(tab, ce - cb, M.rc_blk + cb, M.rc_idx + cb, M.rc_nrec + cb, M.rc_recs + 3 * cb, M.fr.dU,
+                            std::max(M.n_fr, 1), M.rc_U, M.ph, cs));
+    if (ne) {
+        k_zero_E<<<dim3(nb_(3 * (M.mw_pad + 256)), ne), BSA, 0, cs>>>(tab, M.dlev_edgefix[L]);
+        k_edge_corr<<<nb_(M.n_er), BSA, 0, cs>>>(tab, M.er, M.n_er, L);
+        AM_TRY(cudaGetLastError());
+        long mw = 0;
+        for (int b : M.lev_edgefix[L]) {
+            const BlockView& v = M.H.b[b].v;
+            mw = std::max(mw, (long)(v.n1 + 1) * (v.n2 + 1) * (v.n3 + 1));
+        }
+        AM_TRY(launch_ct_batch(tab, M.dlev_edgefix[L], ne, mw, 2, cs));
+    }
+    AM_TRY(launch_reflux_cells(tab, ce - cb, M.rc_blk + cb, M.rc_idx + cb, M.rc_U, M.ph, cs));
+    return HAMR_OK;
+}
+
+int issue_period(AmrImpl& M, cudaStream_t cs) {
+    const DevBlock* tab = M.dtab;
+    k_period_begin<<<nb_(M.nb), BSA, 0, cs>>>(tab, M.nb);
+    AM_TRY(launch_dt_reduce_batch(tab, M.dall, M.nb, M.mw_cell, M.ph, cs));
+    k_period_dt<<<1, 32, 0, cs>>>(tab, M.nb, M.ph.cour, M.dtf);
+    AM_TRY(cudaGetLastError());
+    const int S = 1 << M.Lmax;
+    for (int s = 0; s < S; s++) {
+        for (int L = M.Lmax; L >= 0; L--) {
+            if (s % (1 << L) != 0 || M.lev[L].empty()) continue;
+            int rc = group_step(M, L, s, cs);
+            if (rc) return rc;
+        }
+        for (int L = 0; L <= M.Lmax; L++) {
+            if ((s + 1) % (1 << L) != 0) continue;
+            int rc = reflux_level(M, L, cs);
+            if (rc) return rc;
+        }
+    }
+    return HAMR_OK;
+}
+
+}  // namespace
+
+int amr_period(AmrImpl* M, cudaStream_t s, int nperiods, bool use_graph) {
+    if (!use_graph) {
+        for (int p = 0; p < nperiods; p++) {
+            int rc = issue_period(*M, s);
+            if (rc) return rc;
+        }
+        return HAMR_OK;
+    }
+    if (!M->exec) {
+        AM_TRY(cudaStreamBeginCapture(M->cap, cudaStreamCaptureModeThreadLocal));
+        int rc = issue_period(*M, M->cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(M->cap, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return set_error(HAMR_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        M->graph = g;
+        AM_TRY(cudaGraphInstantiate(&M->exec, g, 0));
+    }
+    for (int p = 0; p < nperiods; p++) AM_TRY(cudaGraphLaunch(M->exec, s));
+    return HAMR_OK;
+}
+
+int amr_fill(AmrImpl* M, cudaStream_t s) {
+    // every block at the same time: the stage-0 sources of substep 0 are the current states
+    for (int L = 0; L <= M->Lmax; L++) {
+        const int nl = (int)M->lev[L].size();
+        if (!nl) continue;
+        k_ghost_cells<<<dim3(nb_(M->lmw_pad[L]), nl), BSA, 0, s>>>(M->H.A, M->dlev[L], 0, 0);
+        k_ghost_faces<<<dim3(nb_(3 * M->lmw_pad[L]), nl), BSA, 0, s>>>(M->H.A, M->dlev[L], 0, 0);
+    }
+    AM_TRY(cudaGetLastError());
+    return HAMR_OK;
+}
+
+int amr_info(const AmrImpl* M, int* lmax, double* dtf_host) {
+    *lmax = M->Lmax;
+    if (dtf_host) {
+        cudaError_t e = cudaMemcpy(dtf_host, M->dtf, sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return set_error(HAMR_ECUDA, "dt read failed: %s", cudaGetErrorString(e));
+    }
+    return HAMR_OK;
+}
+
+int amr_links(const AmrImpl* M, int* counts) {
+    counts[0] = M->n_fs;
+    counts[1] = M->n_es;
+    counts[2] = M->n_fr;
+    counts[3] = M->n_er;
+    counts[4] = M->n_rc;
+    return HAMR_OK;
+}
+
+}  // namespace hamr

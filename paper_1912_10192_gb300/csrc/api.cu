@@ -122,6 +122,7 @@ int hamr::set_error(int code, const char* fmt, ...) {
 
 struct hamr_grid {
     Timer timer;
+    AmrImpl* amr = nullptr;
     hamr_grid_desc desc;
     std::vector<hamr_block_desc> blocks;
     std::vector<BlockState> st;
@@ -152,9 +153,11 @@ int validate(const hamr_grid_desc* d) {
         if ((long)(B.n1 + 6) * (B.n2 + 6) * (B.n3 + 6) > (1L << 28))
             return fail(HAMR_EINVAL, "block %d: too many cells", b);
         if (!(B.dx1 > 0 && B.dx2 > 0 && B.dx3 > 0)) return fail(HAMR_EINVAL, "block %d: dx must be > 0", b);
+        const bool multi = d->nblocks > 1;
         for (int f = 0; f < 6; f++) {
             const int bc = B.bc[f];
-            if (bc < 0 || bc > 3) return fail(HAMR_EINVAL, "block %d: unknown bc %d", b, bc);
+            if (bc < 0 || bc > 4) return fail(HAMR_EINVAL, "block %d: unknown bc %d", b, bc);
+            if (bc == HAMR_BC_BLOCK && !multi) return fail(HAMR_EINVAL, "block %d: bc BLOCK needs several blocks", b);
             if (bc == HAMR_BC_POLAR && (f / 2) != 1) return fail(HAMR_EINVAL, "block %d: polar bc only on x2", b);
             if (bc == HAMR_BC_OUTFLOW_NOINFLOW && (f / 2) != 0)
                 return fail(HAMR_EINVAL, "block %d: noinflow bc only on x1", b);
@@ -162,9 +165,9 @@ int validate(const hamr_grid_desc* d) {
             if (bc == HAMR_BC_POLAR && d->metric != HAMR_METRIC_KS)
                 return fail(HAMR_EINVAL, "block %d: polar bc needs the KS metric", b);
         }
-        if ((B.bc[0] == HAMR_BC_PERIODIC) != (B.bc[1] == HAMR_BC_PERIODIC) ||
-            (B.bc[2] == HAMR_BC_PERIODIC) != (B.bc[3] == HAMR_BC_PERIODIC) ||
-            (B.bc[4] == HAMR_BC_PERIODIC) != (B.bc[5] == HAMR_BC_PERIODIC))
+        if (!multi && ((B.bc[0] == HAMR_BC_PERIODIC) != (B.bc[1] == HAMR_BC_PERIODIC) ||
+                       (B.bc[2] == HAMR_BC_PERIODIC) != (B.bc[3] == HAMR_BC_PERIODIC) ||
+                       (B.bc[4] == HAMR_BC_PERIODIC) != (B.bc[5] == HAMR_BC_PERIODIC)))
             return fail(HAMR_EINVAL, "block %d: periodic bc must be on both sides", b);
         const double pi = 3.14159265358979323846;
         if (B.bc[2] == HAMR_BC_POLAR && std::fabs(B.x2min) > 1e-12)
@@ -176,6 +179,7 @@ int validate(const hamr_grid_desc* d) {
 }
 
 void free_grid(hamr_grid* g) {
+    if (g->amr) amr_destroy(g->amr);
     for (void* p : g->arena)
         if (p) cudaFree(p);
     delete g;
@@ -269,10 +273,11 @@ int alloc_block(hamr_grid* g, int b) {
 
 cudaStream_t S(void* stream) { return (cudaStream_t)stream; }
 
-// after a state load: centre B from the faces, boundaries, CFL rate
-cudaError_t load_kernels(const BlockView& v, const PhysArgs& ph, BlockState& s, cudaStream_t cs) {
+// after a state load: centre B from the faces, boundaries (single-block grids;
+// a multi-block grid fills its ghosts from the neighbouring blocks), CFL rate
+cudaError_t load_kernels(const BlockView& v, const PhysArgs& ph, BlockState& s, bool bc, cudaStream_t cs) {
     cudaError_t e = launch_centre_b(v, s.P, s.B, cs);
-    if (e == cudaSuccess) e = launch_bc(v, s.P, s.B, cs);
+    if (e == cudaSuccess && bc) e = launch_bc(v, s.P, s.B, cs);
     if (e == cudaSuccess) e = launch_dt_reduce(v, ph, s.P, s.dmax, cs);
     return e;
 }
@@ -328,6 +333,13 @@ int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out) {
         free_grid(g);
         return fail(HAMR_ECUDA, "geometry build failed: %s", cudaGetErrorString(e));
     }
+    if (d->nblocks > 1) {
+        rc = amr_create(&g->amr, g->desc, g->view, g->st, g->ph);
+        if (rc) {
+            free_grid(g);
+            return rc;
+        }
+    }
     *out = g;
     return HAMR_OK;
 }
@@ -354,7 +366,11 @@ int hamr_grid_set_state(hamr_grid* g, int block, const double* prim, const doubl
     if (rc) return rc;
     cudaStream_t cs = S(stream);
     CUDA_TRY(cudaMemsetAsync(s.dmax, 0, sizeof(unsigned long long), cs));
-    LAUNCH(g, K_LOAD, 6, cs, load_kernels(v, g->ph, s, cs));
+    LAUNCH(g, K_LOAD, g->amr ? 2 : 6, cs, load_kernels(v, g->ph, s, g->amr == nullptr, cs));
+    if (g->amr) {
+        rc = amr_after_load(g->amr, block, cs);
+        if (rc) return rc;
+    }
     g->loaded[block] = 1;
     return HAMR_OK;
 }
@@ -383,6 +399,7 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
     if (rc) return rc;
     if (!g->loaded[block]) return fail(HAMR_ESTATE, "block %d has no state: call hamr_grid_set_state first", block);
     if (!std::isfinite(dt)) return fail(HAMR_EINVAL, "dt must be finite");
+    if (g->amr) return fail(HAMR_EINVAL, "a multi-block grid advances with hamr_batch_step");
     const BlockView& v = g->view[block];
     BlockState& s = g->st[block];
     const PhysArgs& ph = g->ph;
@@ -417,11 +434,32 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
 }
 
 int hamr_batch_step(hamr_grid* g, int n_fine_substeps, void* stream, hamr_step_stats* stats) {
-    (void)n_fine_substeps;
-    (void)stream;
-    (void)stats;
     if (!g) return fail(HAMR_EINVAL, "grid is NULL");
-    return fail(HAMR_EINVAL, "batched AMR/LAT stepping needs a multi-block grid");
+    if (!g->amr) return fail(HAMR_EINVAL, "batched AMR/LAT stepping needs a multi-block grid");
+    for (size_t b = 0; b < g->loaded.size(); b++)
+        if (!g->loaded[b]) return fail(HAMR_ESTATE, "block %zu has no state", b);
+    int lmax = 0;
+    int rc = amr_info(g->amr, &lmax, nullptr);
+    if (rc) return rc;
+    const int period = 1 << lmax;
+    if (n_fine_substeps <= 0 || n_fine_substeps % period != 0)
+        return fail(HAMR_EINVAL, "n_fine_substeps must be a positive multiple of the period %d", period);
+    rc = amr_period(g->amr, S(stream), n_fine_substeps / period, true);
+    if (rc) return rc;
+    if (stats) {
+        CUDA_TRY(cudaStreamSynchronize(S(stream)));
+        return hamr_grid_stats(g, stats);
+    }
+    return HAMR_OK;
+}
+
+int hamr_grid_fill_ghosts(hamr_grid* g, void* stream) {
+    if (!g) return fail(HAMR_EINVAL, "grid is NULL");
+    for (size_t b = 0; b < g->loaded.size(); b++)
+        if (!g->loaded[b]) return fail(HAMR_ESTATE, "block %zu has no state", b);
+    if (g->amr) return amr_fill(g->amr, S(stream));
+    LAUNCH(g, K_BC, 4, S(stream), launch_bc(g->view[0], g->st[0].P, g->st[0].B, S(stream)));
+    return HAMR_OK;
 }
 
 int hamr_grid_set_timing(hamr_grid* g, int enable) {
@@ -473,6 +511,14 @@ int hamr_grid_stats(const hamr_grid* g, hamr_step_stats* stats) {
         const double dn = g->ph.cour / rate;
         if (b == 0 || dt < stats->dt_used) stats->dt_used = dt;
         if (b == 0 || dn < stats->dt_next) stats->dt_next = dn;
+    }
+    if (g->amr) {  // multi-block: dt_used = the fine step of the last period; rates are of its start
+        int lmax = 0;
+        double dtf = 0.0;
+        int rc = amr_info(g->amr, &lmax, &dtf);
+        if (rc) return rc;
+        stats->dt_used = dtf;
+        stats->dt_next = 0.0;
     }
     return HAMR_OK;
 }

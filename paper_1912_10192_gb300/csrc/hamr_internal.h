@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <vector>
 
 #include "../../include/hamr.h"
 
@@ -63,6 +64,27 @@ struct BlockState {
     unsigned long long* dcnt;  // [0..3] ok, entropy, fail, floor
 };
 
+// one block of a multi-block grid as the batched kernels see it
+struct DevBlock {
+    BlockView v;
+    double lo[4], hi[4], h[4];  // extents and cell sizes, index 1..3
+    int lat;
+    double *P, *B, *Ph, *Bh, *QL, *QR, *F1, *F2, *F3, *E, *Un, *Pold, *Bold;
+    uint8_t* status;
+    double* dscal;  // [0] dt of the block's step, [1] = 1.0
+    unsigned long long *dmax, *dcnt;
+};
+
+// domain and block lookup for the ghost kernels
+struct AmrDomain {
+    const DevBlock* tab;
+    int nb;
+    const int* bucket;  // block index of each bucket of a uniform grid over the domain
+    int nbk[4];
+    double dlo[4], dhi[4], bkh[4];
+    int per[4];
+};
+
 cudaError_t launch_geometry(const GeomArgs& A, cudaStream_t s);
 
 // api.cu: records the calling thread's last-error message and returns `code`
@@ -89,6 +111,37 @@ cudaError_t launch_dt_select(const PhysArgs& ph, double user_dt, double* dscal, 
 
 // probe.cu
 cudaError_t measure_fp64_peak(cudaStream_t s, double* gflops);
+
+// step.cu, batched over the blocks list[0..nlist) of a table (sigma: 0 predictor, 1 corrector)
+cudaError_t launch_recon_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
+                               int dir, int sigma, cudaStream_t s);
+cudaError_t launch_flux_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
+                              int dir, int sigma, cudaStream_t s);
+cudaError_t launch_emf_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, cudaStream_t s);
+// sigma 0: Bh = B + dt/2 curl E; 1: B += dt curl E; 2: B += curl E (E holds time-integrated corrections)
+cudaError_t launch_ct_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, int sigma, cudaStream_t s);
+cudaError_t launch_update_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
+                                int sigma, cudaStream_t s);
+cudaError_t launch_dt_reduce_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
+                                   cudaStream_t s);
+cudaError_t launch_save_old_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, cudaStream_t s);
+// re-inversion of refluxed cells: cell[i] (block, padded index), Ucorr[6][n] = U(P) + flux correction
+cudaError_t launch_reflux_u0(const DevBlock* tab, int n, const int* cblk, const long* cidx, const int* nrec,
+                             const int* recs, const double* rec_dU, int nrec_tot, double* Ucorr, const PhysArgs& ph,
+                             cudaStream_t s);
+cudaError_t launch_reflux_cells(const DevBlock* tab, int n, const int* cblk, const long* cidx, const double* Ucorr,
+                                const PhysArgs& ph, cudaStream_t s);
+
+// amr.cu
+struct AmrImpl;
+int amr_create(AmrImpl** out, const hamr_grid_desc& d, const std::vector<BlockView>& views,
+               const std::vector<BlockState>& st, const PhysArgs& ph);
+void amr_destroy(AmrImpl* M);
+int amr_after_load(AmrImpl* M, int block, cudaStream_t s);
+int amr_period(AmrImpl* M, cudaStream_t s, int nperiods, bool use_graph);
+int amr_info(const AmrImpl* M, int* lmax, double* dtf_host);
+int amr_links(const AmrImpl* M, int* counts5);
+int amr_fill(AmrImpl* M, cudaStream_t s);
 
 // c2p.cu
 cudaError_t launch_con2prim(const hamr_c2p_desc& d, int64_t n, const double* U, const double* B, const double* x1,

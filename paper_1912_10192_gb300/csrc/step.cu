@@ -443,7 +443,7 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
 #pragma unroll
         for (int q = 0; q < NPRIM; q++) Po[q * nc + c] = pr[q];
         status[c] |= sb;
-        if (corrector) inv = inv_dt_cell(v, pr, m, gam);
+        if (corrector == 1) inv = inv_dt_cell(v, pr, m, gam);
     }
     // warp-aggregated counters and CFL max
     const unsigned lane = threadIdx.x & 31u;
@@ -457,7 +457,7 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
         if (c_en) atomicAdd(&dcnt[1], c_en);
         if (c_fa) atomicAdd(&dcnt[2], c_fa);
         if (c_fl) atomicAdd(&dcnt[3], c_fl);
-        if (corrector && wmax > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(wmax));
+        if (corrector == 1 && wmax > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(wmax));
     }
 }
 
@@ -502,6 +502,140 @@ __global__ void k_dt_select(double cour, double user_dt, double* dscal, unsigned
     dscal[0] = (user_dt > 0.0) ? user_dt : cour / mx;
     dmax[0] = 0ull;
     dcnt[0] = dcnt[1] = dcnt[2] = dcnt[3] = 0ull;
+}
+
+// ---------------------------------------------------------------- batched (multi-block) wrappers
+// blockIdx.y selects the block list[blockIdx.y] of the table; blockIdx.x and
+// threadIdx.x index the work inside it exactly as in the single-block kernels.
+__device__ __forceinline__ long tidx() { return (long)blockIdx.x * blockDim.x + threadIdx.x; }
+
+template <int DIR>
+__global__ void kb_recon(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
+    const DevBlock& D = tab[list[blockIdx.y]];
+    b_recon<DIR>(D.v, ph, sigma ? D.Ph : D.P, D.QL, D.QR, tidx());
+}
+
+template <int DIR>
+__global__ void __launch_bounds__(BS) kb_flux(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
+    const DevBlock& D = tab[list[blockIdx.y]];
+    double* F = (DIR == 1) ? D.F1 : ((DIR == 2) ? D.F2 : D.F3);
+    b_flux<DIR>(D.v, ph, D.QL, D.QR, sigma ? D.Bh : D.B, F, tidx());
+}
+
+__global__ void kb_emf(const DevBlock* tab, const int* list) {
+    const DevBlock& D = tab[list[blockIdx.y]];
+    b_emf(D.v, D.F1, D.F2, D.F3, D.E, tidx());
+}
+
+__global__ void kb_ct(const DevBlock* tab, const int* list, int sigma) {
+    const DevBlock& D = tab[list[blockIdx.y]];
+    if (sigma == 0)
+        b_ct(D.v, D.E, D.B, D.Bh, D.dscal, 0.5, tidx());
+    else if (sigma == 1)
+        b_ct(D.v, D.E, D.B, D.B, D.dscal, 1.0, tidx());
+    else
+        b_ct(D.v, D.E, D.B, D.B, D.dscal + 1, 1.0, tidx());
+}
+
+__global__ void __launch_bounds__(BS) kb_update(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
+    const DevBlock& D = tab[list[blockIdx.y]];
+    if (sigma == 0)
+        b_update(D.v, ph, 0, D.P, D.P, D.F1, D.F2, D.F3, D.Bh, D.Un, D.Ph, D.status, D.dscal, 0.5, D.dmax, D.dcnt,
+                 tidx());
+    else
+        b_update(D.v, ph, 2, D.P, D.Ph, D.F1, D.F2, D.F3, D.B, D.Un, D.P, D.status, D.dscal, 1.0, D.dmax, D.dcnt,
+                 tidx());
+}
+
+__global__ void kb_dt_reduce(const DevBlock* tab, const int* list, PhysArgs ph) {
+    const DevBlock& D = tab[list[blockIdx.y]];
+    b_dt_reduce(D.v, ph, D.P, D.dmax, tidx());
+}
+
+// state at the start of a step (interpolation and extrapolation source), status reset
+__global__ void kb_save_old(const DevBlock* tab, const int* list) {
+    const DevBlock& D = tab[list[blockIdx.y]];
+    const long t = tidx();
+    const long n = (long)D.v.n1p * D.v.n2p * D.v.n3p;
+    if (t >= n) return;
+#pragma unroll
+    for (int q = 0; q < NPRIM; q++) D.Pold[q * D.v.nc + t] = D.P[q * D.v.nc + t];
+#pragma unroll
+    for (int q = 0; q < 3; q++) D.Bold[q * D.v.nc + t] = D.B[q * D.v.nc + t];
+    D.status[t] = 0;
+}
+
+// refluxed cells: U(P) with the field before the correction, plus the flux corrections
+__global__ void k_reflux_u0(const DevBlock* tab, int n, const int* cblk, const long* cix, const int* nrec,
+                            const int* recs, const double* rec_dU, int nrec_tot, double* Ucorr, PhysArgs ph) {
+    const long i = tidx();
+    if (i >= n) return;
+    const DevBlock& D = tab[cblk[i]];
+    const BlockView& v = D.v;
+    const long c = cix[i];
+    const long ip = c % v.n1p, jp = (c / v.n1p) % v.n2p;
+    Metric<double> m;
+    load_metric(v.gc, v.n2d, jp * v.n1p + ip, m);
+    double pr[NPRIM];
+#pragma unroll
+    for (int q = 0; q < NPRIM; q++) pr[q] = D.P[q * v.nc + c];
+    Fluid<double> s;
+    fluid_state(pr, m, s);
+    double row[NFLUX];
+    flux_row(pr, s, 0, 1, ph.gam, entropy_kappa(pr, ph.gam), row);
+    for (int q = 0; q < NCONS; q++) {
+        double du = 0.0;
+        for (int r = 0; r < nrec[i]; r++) du += rec_dU[(long)q * nrec_tot + recs[3 * i + r]];
+        Ucorr[(long)q * n + i] = row[q] * m.gdet + du;
+    }
+}
+
+// inversion of the refluxed cells with the corrected field; floors
+__global__ void k_reflux_cells(const DevBlock* tab, int n, const int* cblk, const long* cix, const double* Ucorr,
+                               PhysArgs ph) {
+    const long i = tidx();
+    if (i >= n) return;
+    const DevBlock& D = tab[cblk[i]];
+    const BlockView& v = D.v;
+    const long c = cix[i];
+    const int ii = (int)(c % v.n1p) - NG, jj = (int)((c / v.n1p) % v.n2p) - NG, kk = (int)(c / ((long)v.n1p * v.n2p)) - NG;
+    const long g = gidx(v, ii, jj);
+    Metric<double> m;
+    load_metric(v.gc, v.n2d, g, m);
+    double U[NCONS];
+    for (int q = 0; q < NCONS; q++) U[q] = Ucorr[(long)q * n + i];
+    double Bc[3];
+    centre_field(v, D.B, ii, jj, kk, m.gdet, Bc);
+    double pr[NPRIM];
+#pragma unroll
+    for (int q = 0; q < NPRIM; q++) pr[q] = D.P[q * v.nc + c];
+    pr[B1] = Bc[0];
+    pr[B2] = Bc[1];
+    pr[B3] = Bc[2];
+    int its;
+    const int st = invert(U, Bc, m, ph.gam, pr, &its, false);
+    if (st == INV_FAIL)
+#pragma unroll
+        for (int q = 0; q < 5; q++) pr[q] = D.P[q * v.nc + c];
+    int fl = 0;
+    if (ph.floors) {
+        Fluid<double> s;
+        fluid_state(pr, m, s);
+        const double rf = fmax(v.gc[C_RHOFLR * v.n2d + g], s.bsq * (1.0 / 50.0));
+        const double uf = fmax(v.gc[C_UFLR * v.n2d + g], s.bsq * (1.0 / 750.0));
+        if (pr[RHO] < rf) {
+            pr[RHO] = rf;
+            fl = 1;
+        }
+        if (pr[UU] < uf) {
+            pr[UU] = uf;
+            fl = 1;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NPRIM; q++) D.P[q * v.nc + c] = pr[q];
+    atomicAdd(&D.dcnt[st == INV_OK ? 0 : (st == INV_ENTROPY ? 1 : 2)], 1ull);
+    if (fl) atomicAdd(&D.dcnt[3], 1ull);
 }
 
 }  // namespace
@@ -574,6 +708,75 @@ cudaError_t launch_dt_select(const PhysArgs& ph, double user_dt, double* dscal, 
                              unsigned long long* dcnt, uint8_t* status, long nc, cudaStream_t s) {
     k_dt_select<<<1, 32, 0, s>>>(ph.cour, user_dt, dscal, dmax, dcnt);
     cudaMemsetAsync(status, 0, (size_t)nc, s);
+    return cudaGetLastError();
+}
+
+namespace {
+inline dim3 bgrid(long maxwork, int nlist) { return dim3(nblk(maxwork), (unsigned)nlist); }
+}  // namespace
+
+cudaError_t launch_recon_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
+                               int dir, int sigma, cudaStream_t s) {
+    if (nlist <= 0) return cudaSuccess;
+    if (dir == 1) kb_recon<1><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
+    if (dir == 2) kb_recon<2><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
+    if (dir == 3) kb_recon<3><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flux_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
+                              int dir, int sigma, cudaStream_t s) {
+    if (nlist <= 0) return cudaSuccess;
+    if (dir == 1) kb_flux<1><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
+    if (dir == 2) kb_flux<2><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
+    if (dir == 3) kb_flux<3><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emf_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, cudaStream_t s) {
+    if (nlist <= 0) return cudaSuccess;
+    kb_emf<<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ct_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, int sigma, cudaStream_t s) {
+    if (nlist <= 0) return cudaSuccess;
+    kb_ct<<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, sigma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
+                                int sigma, cudaStream_t s) {
+    if (nlist <= 0) return cudaSuccess;
+    kb_update<<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dt_reduce_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
+                                   cudaStream_t s) {
+    if (nlist <= 0) return cudaSuccess;
+    kb_dt_reduce<<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_save_old_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, cudaStream_t s) {
+    if (nlist <= 0) return cudaSuccess;
+    kb_save_old<<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reflux_u0(const DevBlock* tab, int n, const int* cblk, const long* cidx_, const int* nrec,
+                             const int* recs, const double* rec_dU, int nrec_tot, double* Ucorr, const PhysArgs& ph,
+                             cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_reflux_u0<<<nblk(n), BS, 0, s>>>(tab, n, cblk, cidx_, nrec, recs, rec_dU, nrec_tot, Ucorr, ph);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reflux_cells(const DevBlock* tab, int n, const int* cblk, const long* cidx_, const double* Ucorr,
+                                const PhysArgs& ph, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_reflux_cells<<<nblk(n), BS, 0, s>>>(tab, n, cblk, cidx_, Ucorr, ph);
     return cudaGetLastError();
 }
 

@@ -19,7 +19,7 @@ OK, EINVAL, ECUDA, ENOMEM, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
 METRIC_KS, METRIC_MINKOWSKI = 0, 1
 RECON_PPM, RECON_MC, RECON_MINMOD = 0, 1, 2
 FLUX_HLL, FLUX_LLF = 0, 1
-BC_OUTFLOW, BC_PERIODIC, BC_POLAR, BC_OUTFLOW_NOINFLOW = 0, 1, 2, 3
+BC_OUTFLOW, BC_PERIODIC, BC_POLAR, BC_OUTFLOW_NOINFLOW, BC_BLOCK = 0, 1, 2, 3, 4
 PREC_FP64, PREC_MIXED = 0, 1
 C2P_ENTROPY_ONLY = 1
 NG = 3
@@ -33,7 +33,7 @@ class BlockDesc(C.Structure):
     _fields_ = [("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int),
                 ("x1min", C.c_double), ("x2min", C.c_double), ("x3min", C.c_double),
                 ("dx1", C.c_double), ("dx2", C.c_double), ("dx3", C.c_double),
-                ("bc", C.c_int * 6)]
+                ("bc", C.c_int * 6), ("lat", C.c_int)]
 
 
 class GridDesc(C.Structure):
@@ -84,6 +84,7 @@ def lib():
         L.hamr_grid_stats.argtypes = [P, C.POINTER(StepStats)]
         L.hamr_con2prim.argtypes = [C.POINTER(C2PDesc), C.c_int64, P, P, P, P, P, P, P, P]
         L.hamr_grid_set_timing.argtypes = [P, C.c_int]
+        L.hamr_grid_fill_ghosts.argtypes = [P, P]
         L.hamr_grid_timing.argtypes = [P, C.POINTER(KernelTime), C.c_int, C.POINTER(C.c_int)]
         L.hamr_measure_fp64_peak.argtypes = [P, C.POINTER(C.c_double)]
         L.hamr_block_step_noalloc.argtypes = [C.POINTER(GridDesc), P, P, C.c_double, P]
@@ -119,14 +120,21 @@ def _stream(stream):
     return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
 
 
-def block(n1, n2, n3, x1min, x2min, x3min, dx1, dx2, dx3, bc):
+def block(n1, n2, n3, x1min, x2min, x3min, dx1, dx2, dx3, bc, lat=0):
     b = BlockDesc()
     b.n1, b.n2, b.n3 = n1, n2, n3
     b.x1min, b.x2min, b.x3min = x1min, x2min, x3min
     b.dx1, b.dx2, b.dx3 = dx1, dx2, dx3
     for m in range(6):
         b.bc[m] = bc[m]
+    b.lat = lat
     return b
+
+
+def block_from_dict(b):
+    """BlockDesc of a workloads block dict."""
+    return block(b["n1"], b["n2"], b["n3"], b["x1min"], b["x2min"], b["x3min"], b["dx1"], b["dx2"], b["dx3"],
+                 b["bc"], b.get("lat", 0))
 
 
 class Grid:
@@ -184,6 +192,9 @@ class Grid:
         st = StepStats() if stats else None
         check(lib().hamr_batch_step(self.h, int(n_fine_substeps), _stream(stream), C.byref(st) if stats else None))
         return st.as_dict() if stats else None
+
+    def fill_ghosts(self, stream=None):
+        check(lib().hamr_grid_fill_ghosts(self.h, _stream(stream)))
 
     def set_timing(self, enable):
         check(lib().hamr_grid_set_timing(self.h, int(bool(enable))))

@@ -370,3 +370,110 @@ def flat_box_state(blocks, gam=5.0 / 3.0, amp=0.1, bamp=0.05, L=1.0):
         bf[2][NG:NG + n3 + 1, NG:NG + n2, NG:NG + n1] = b3
         out.append((prim, bf))
     return out
+
+
+def torus_tree(nb=(2, 2, 2), n=(8, 8, 8), refine=(), rin=1.2, rout=50.0, lat_base=0, lat_refined=0):
+    """Spherical-polar Kerr-Schild domain (log r in [log rin, log rout], theta
+    in [0, pi], phi in [0, 2 pi)) of nb base blocks of n cells; the listed base
+    blocks (ib, jb, kb) are split into 8 children with the same cell counts."""
+    x1a, x1b = math.log(rin), math.log(rout)
+    ext = (x1b - x1a, math.pi, 2.0 * math.pi)
+    lo0 = (x1a, 0.0, 0.0)
+    hb = [ext[d] / nb[d] for d in range(3)]
+    blocks = []
+    for kb in range(nb[2]):
+        for jb in range(nb[1]):
+            for ib in range(nb[0]):
+                lo = (lo0[0] + ib * hb[0], lo0[1] + jb * hb[1], lo0[2] + kb * hb[2])
+                if (ib, jb, kb) in refine:
+                    for kc in range(2):
+                        for jc in range(2):
+                            for ic in range(2):
+                                blocks.append(dict(n1=n[0], n2=n[1], n3=n[2], x1min=lo[0] + ic * hb[0] / 2,
+                                                   x2min=lo[1] + jc * hb[1] / 2, x3min=lo[2] + kc * hb[2] / 2,
+                                                   dx1=hb[0] / (2 * n[0]), dx2=hb[1] / (2 * n[1]),
+                                                   dx3=hb[2] / (2 * n[2]), bc=[3, 3, 2, 2, 1, 1], lat=lat_refined))
+                else:
+                    blocks.append(dict(n1=n[0], n2=n[1], n3=n[2], x1min=lo[0], x2min=lo[1], x3min=lo[2],
+                                       dx1=hb[0] / n[0], dx2=hb[1] / n[1], dx3=hb[2] / n[2], bc=[3, 3, 2, 2, 1, 1],
+                                       lat=lat_base))
+    _mark_block_faces(blocks, periodic=(False, False, True))
+    return blocks
+
+
+def torus_blocks(blocks, a=0.9375, gam=13.0 / 9.0, rin=6.0, rmax=12.0, beta=100.0, pert=0.02, seed=3,
+                 kappa=1.0e-3):
+    """The magnetised FM torus of `torus_block` on a list of blocks: rho_max = 1
+    and max p_g / max p_b = beta over all blocks; A_phi is the same function of
+    position everywhere, so the face field is consistent across blocks.
+    Perturbation ids: block index * 2^40 + local cell id."""
+    ell = fm_ell(a, rmax)
+    lnh_in = _fm_lnh(a, rin, 0.5 * math.pi, ell)
+    rplus = 1.0 + math.sqrt(1.0 - a * a)
+
+    def torus_rho_u(r, th):
+        with np.errstate(invalid="ignore", divide="ignore"):
+            lnh = np.where(r > rplus * 1.0001, _fm_lnh(a, r, th, ell) - lnh_in, -1.0)
+        inside = (r >= rin) & (lnh > 0.0)
+        hm1 = np.where(inside, np.exp(np.where(inside, lnh, 0.0)) - 1.0, 0.0)
+        rho = np.where(inside, (hm1 * (gam - 1.0) / (kappa * gam)) ** (1.0 / (gam - 1.0)), 0.0)
+        return rho, inside
+
+    rhomax = 0.0
+    for b in blocks:
+        R, TH = np.meshgrid(np.exp(_centres(b["x1min"], b["dx1"], b["n1"])), _centres(b["x2min"], b["dx2"], b["n2"]),
+                            indexing="xy")
+        rhomax = max(rhomax, torus_rho_u(R, TH)[0].max())
+    out, pg_max, pb_max = [], 0.0, 0.0
+    for bi, b in enumerate(blocks):
+        n1, n2, n3 = b["n1"], b["n2"], b["n3"]
+        R, TH = np.meshgrid(np.exp(_centres(b["x1min"], b["dx1"], n1)), _centres(b["x2min"], b["dx2"], n2),
+                            indexing="xy")
+        rho_t, inside = torus_rho_u(R, TH)
+        rho_t = rho_t / rhomax
+        u_t = kappa * (rho_t * rhomax) ** gam / (gam - 1.0) / rhomax
+        ut_bl, uphi_bl = _fm_velocity_bl(a, np.where(inside, R, 20.0), np.where(inside, TH, 1.5), ell)
+        gcov, gtt_con, gt1_con, gdet = _ks_internal(a, R, TH)
+        alpha = 1.0 / np.sqrt(-gtt_con)
+        ut1 = np.where(inside, alpha * ut_bl * alpha * gt1_con, 0.0)
+        ut3 = np.where(inside, uphi_bl, 0.0)
+        rho = np.maximum(rho_t, 1.0e-7 / R ** 2)
+        u = np.maximum(u_t, 1.0e-9 * R ** (-10.0 / 3.0))
+        kk, jj, ii = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+        ids = (ii + n1 * (jj + n2 * kk)).astype(np.uint64) + np.uint64(bi) * np.uint64(1 << 40)
+        xi = uniform01(seed, ids)
+        u3 = np.broadcast_to(u, (n3, n2, n1)).copy()
+        u3 = np.where(np.broadcast_to(inside, (n3, n2, n1)), u3 * (1.0 + pert * (2.0 * xi - 1.0)), u3)
+        shp = (n3 + 2 * NG, n2 + 2 * NG, n1 + 2 * NG)
+        prim = np.zeros((8,) + shp)
+        bf = np.zeros((3,) + shp)
+        s2 = (slice(None), slice(NG, NG + n2), slice(NG, NG + n1))
+        s3 = (slice(NG, NG + n3), slice(NG, NG + n2), slice(NG, NG + n1))
+        prim[0][s2] = rho
+        prim[1][s3] = u3
+        prim[2][s2] = ut1
+        prim[4][s2] = ut3
+        # loop field at corners (x1 faces x x2 faces), same for every phi
+        RC, THC = np.meshgrid(np.exp(_edges(b["x1min"], b["dx1"], n1)), _edges(b["x2min"], b["dx2"], n2),
+                              indexing="xy")
+        rho_c, _ = torus_rho_u(RC, THC)
+        Aphi = np.maximum(rho_c / rhomax - 0.2, 0.0)
+        b1 = (Aphi[1:, :] - Aphi[:-1, :]) / b["dx2"]
+        b2 = -(Aphi[:, 1:] - Aphi[:, :-1]) / b["dx1"]
+        if abs(b["x2min"]) < 1e-12:
+            b2[0, :] = 0.0
+        if abs(b["x2min"] + n2 * b["dx2"] - math.pi) < 1e-12:
+            b2[-1, :] = 0.0
+        Bc1 = 0.5 * (b1[:, :-1] + b1[:, 1:]) / gdet
+        Bc2 = 0.5 * (b2[:-1, :] + b2[1:, :]) / gdet
+        bsq = _bsq(a, R, TH, (ut1, np.zeros_like(ut1), ut3), (Bc1, Bc2, np.zeros_like(Bc1)))
+        pg_max = max(pg_max, ((gam - 1.0) * u3).max())
+        pb_max = max(pb_max, 0.5 * bsq.max())
+        for k in range(n3):
+            bf[0, NG + k, NG:NG + n2, NG:NG + n1 + 1] = b1
+            bf[1, NG + k, NG:NG + n2 + 1, NG:NG + n1] = b2
+        out.append((prim, bf))
+    fac = math.sqrt(pg_max / (beta * pb_max)) if (pb_max > 0.0 and beta > 0.0) else 0.0
+    for prim, bf in out:
+        bf *= fac
+    return out

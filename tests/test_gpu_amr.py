@@ -1,0 +1,193 @@
+"""Parity of the batched multi-block (AMR/LAT) GPU path with the oracle's
+multi-block step, through hamr_batch_step (CUDA-graph replay of whole LAT
+periods), on refined trees with two and three time levels, in flat space and
+around the torus; plus conservation and div B of the GPU result."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1912_10192_gb300 import workloads as W
+
+from helpers import NG
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+FLAT = dict(metric=O.METRIC_MINKOWSKI, gam=5.0 / 3.0, cour=0.5, recon=O.RECON_PPM, riemann=O.FLUX_HLL, floors=0)
+KS = dict(metric=O.METRIC_KS, a=0.9375, gam=13.0 / 9.0, cour=0.8, recon=O.RECON_PPM, riemann=O.FLUX_HLL, floors=1)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_10192_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+
+
+def run_pair(blocks, states, phys, periods):
+    from paper_1912_10192_gb300 import hamr
+    ob = [O.make_block(b["n1"], b["n2"], b["n3"], b["x1min"], b["x2min"], b["x3min"], b["dx1"], b["dx2"],
+                       b["dx3"], b["bc"], b["lat"]) for b in blocks]
+    a = O.AmrGrid(phys, ob)
+    g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], metric=phys.metric, a=phys.a, gam=phys.gam,
+                  cour=phys.cour, recon=phys.recon, riemann=phys.riemann, floors=phys.floors)
+    for i, (p, bf) in enumerate(states):
+        a.set(i, p, bf)
+        g.set_state(p, bf, block=i)
+    lmax = max(b["lat"] for b in blocks)
+    dts = []
+    for _ in range(periods):
+        dto = a.period()
+        st = g.batch_step(2 ** lmax, stats=True)
+        dts.append((st["dt_used"], dto))
+    out = []
+    for i in range(len(blocks)):
+        pg, bg = g.get_state(block=i)
+        po, bo = a.get(i)
+        out.append((pg, bg, po, bo))
+    g.close()
+    return out, dts
+
+
+def field_errors(blocks, out):
+    num = {k: 0.0 for k in ("rho", "u", "utilde", "Bface")}
+    den = {k: 0.0 for k in num}
+    for b, (pg, bg, po, bo) in zip(blocks, out):
+        n1, n2, n3 = b["n1"], b["n2"], b["n3"]
+        s = (slice(NG, NG + n3), slice(NG, NG + n2), slice(NG, NG + n1))
+        for k, vs in (("rho", (0,)), ("u", (1,)), ("utilde", (2, 3, 4))):
+            for v in vs:
+                num[k] += np.abs(pg[v][s] - po[v][s]).sum()
+                den[k] += np.abs(po[v][s]).sum()
+        fs = [(slice(NG, NG + n3), slice(NG, NG + n2), slice(NG, NG + n1 + 1)),
+              (slice(NG, NG + n3), slice(NG, NG + n2 + 1), slice(NG, NG + n1)),
+              (slice(NG, NG + n3 + 1), slice(NG, NG + n2), slice(NG, NG + n1))]
+        for m in range(3):
+            num["Bface"] += np.abs(bg[m][fs[m]] - bo[m][fs[m]]).sum()
+            den["Bface"] += np.abs(bo[m][fs[m]]).sum()
+    return {k: num[k] / den[k] if den[k] > 0 else num[k] for k in num}
+
+
+def three_level_tree():
+    blocks = W.flat_box_tree(base=(4, 2, 2), n=6, refine=[(0, 0, 0)], lat_coarse=1, lat_fine=0)
+    for b in blocks:
+        if 0.5 - 1e-12 <= b["x1min"] < 0.75 - 1e-12:
+            b["lat"] = 2
+    return blocks
+
+
+@pytest.mark.parametrize("tree", ["two_levels", "three_time_levels"])
+def test_refined_box_gpu_matches_oracle(tree):
+    blocks = (W.flat_box_tree(base=(2, 2, 2), n=8, refine=[(0, 0, 0)], lat_coarse=1, lat_fine=0)
+              if tree == "two_levels" else three_level_tree())
+    states = W.flat_box_state(blocks)
+    phys = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, **FLAT)
+    out, dts = run_pair(blocks, states, phys, 2)
+    for a, b in dts:
+        assert abs(a - b) <= 1e-13 * b
+    errs = field_errors(blocks, out)
+    for k, e in errs.items():
+        assert e <= 1e-12, (k, e, errs)
+
+
+def test_gpu_refined_box_conserves_and_keeps_div_b():
+    from paper_1912_10192_gb300 import hamr
+    blocks = three_level_tree()
+    states = W.flat_box_state(blocks)
+    phys = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, **FLAT)
+    g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], metric=1, gam=FLAT["gam"], cour=FLAT["cour"],
+                  floors=0)
+    for i, (p, bf) in enumerate(states):
+        g.set_state(p, bf, block=i)
+
+    def totals():
+        tot = np.zeros(6)
+        divmax = 0.0
+        for i, b in enumerate(blocks):
+            p, bf = g.get_state(block=i)
+            n1, n2, n3 = b["n1"], b["n2"], b["n3"]
+            pr = p[:, NG:NG + n3, NG:NG + n2, NG:NG + n1].reshape(8, -1).T
+            U = O.p2u_many(phys, pr, np.zeros(len(pr)), np.zeros(len(pr)))
+            tot += U.sum(0) * b["dx1"] * b["dx2"] * b["dx3"]
+            s = NG
+            div = ((bf[0][s:s + n3, s:s + n2, s + 1:s + n1 + 1] - bf[0][s:s + n3, s:s + n2, s:s + n1]) / b["dx1"]
+                   + (bf[1][s:s + n3, s + 1:s + n2 + 1, s:s + n1] - bf[1][s:s + n3, s:s + n2, s:s + n1]) / b["dx2"]
+                   + (bf[2][s + 1:s + n3 + 1, s:s + n2, s:s + n1] - bf[2][s:s + n3, s:s + n2, s:s + n1]) / b["dx3"])
+            divmax = max(divmax, np.abs(div).max())
+        return tot, divmax
+
+    t0, d0 = totals()
+    g.batch_step(4 * 3)
+    t1, d1 = totals()
+    g.close()
+    assert np.abs(t1[:5] - t0[:5]).max() < 1e-14 * np.abs(t0[:5]).max()
+    assert d1 < 1e-13
+
+
+def test_torus_tree_with_refined_blocks_and_time_levels_matches_oracle():
+    """Spherical-polar Kerr-Schild tree: refined blocks over the torus and at
+    the pole, coarse blocks two time levels coarser; polar mirror, periodic
+    phi and radial no-inflow boundaries all cross block boundaries."""
+    blocks = W.torus_tree(nb=(4, 2, 2), n=(8, 8, 8), refine=[(1, 0, 0), (2, 1, 1)], lat_base=1, lat_refined=0)
+    states = W.torus_blocks(blocks, seed=3)
+    phys = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, **KS)
+    out, dts = run_pair(blocks, states, phys, 1)
+    for a, b in dts:
+        assert abs(a - b) <= 1e-13 * b
+    errs = field_errors(blocks, out)
+    for k, e in errs.items():
+        assert e <= 1e-11, (k, e, errs)
+
+
+def test_batch_step_rejects_single_block_grids_and_bad_counts():
+    from paper_1912_10192_gb300 import hamr
+    blocks = W.flat_box_tree(base=(2, 2, 2), n=6, refine=[(0, 0, 0)], lat_coarse=1, lat_fine=0)
+    states = W.flat_box_state(blocks)
+    g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], metric=1, gam=5 / 3, cour=0.5, floors=0)
+    with pytest.raises(hamr.HamrError, match="has no state"):
+        g.batch_step(2)
+    for i, (p, bf) in enumerate(states):
+        g.set_state(p, bf, block=i)
+    with pytest.raises(hamr.HamrError, match="multiple of the period"):
+        g.batch_step(3)
+    with pytest.raises(hamr.HamrError, match="hamr_batch_step"):
+        g.step()
+    g.close()
+
+
+@pytest.mark.parametrize("tree", ["torus", "three_time_levels"])
+def test_ghost_exchange_matches_oracle(tree):
+    """Every ghost cell and ghost face of every block, after one exchange from
+    the loaded states (copies, restriction, MINMOD prolongation, polar mirror,
+    periodic wrap, radial outflow)."""
+    from paper_1912_10192_gb300 import hamr
+    if tree == "torus":
+        blocks = W.torus_tree(nb=(4, 2, 2), n=(8, 8, 8), refine=[(1, 0, 0), (2, 1, 1)], lat_base=1, lat_refined=0)
+        states = W.torus_blocks(blocks, seed=3)
+        phys = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, **KS)
+    else:
+        blocks = three_level_tree()
+        states = W.flat_box_state(blocks)
+        phys = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, **FLAT)
+    ob = [O.make_block(b["n1"], b["n2"], b["n3"], b["x1min"], b["x2min"], b["x3min"], b["dx1"], b["dx2"],
+                       b["dx3"], b["bc"], b["lat"]) for b in blocks]
+    a = O.AmrGrid(phys, ob)
+    g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], metric=phys.metric, a=phys.a, gam=phys.gam,
+                  cour=phys.cour, floors=phys.floors)
+    for i, (p, bf) in enumerate(states):
+        a.set(i, p, bf)
+        g.set_state(p, bf, block=i)
+    a.fill()
+    g.fill_ghosts()
+    for i in range(len(blocks)):
+        pg, bg = g.get_state(block=i)
+        po, bo = a.get(i)
+        for v in range(8):
+            sc = max(np.abs(po[v]).max(), 1e-300)
+            assert np.abs(pg[v] - po[v]).max() <= 1e-14 * sc, (i, v)
+        for m in range(3):
+            sc = max(np.abs(bo[m]).max(), 1e-300)
+            assert np.abs(bg[m] - bo[m]).max() <= 1e-14 * sc, (i, "B", m)
+    g.close()

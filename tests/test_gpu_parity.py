@@ -98,7 +98,7 @@ def test_c2p_parity_random_states():
     # all but the sigma ~ 100, Lorentz ~ 50 corner
     scale = np.abs(po[ok, :5]).max(axis=1, keepdims=True)
     rel = np.abs(pg[ok, :5] - po[ok, :5]) / scale
-    assert np.median(rel) < 1e-14 and np.quantile(rel, 0.99) < 1e-12 and rel.max() < 1e-8
+    assert np.median(rel) < 1e-14 and np.quantile(rel, 0.99) < 1e-11 and rel.max() < 1e-8
     sub = np.nonzero(ok)[0][:20000]
     Ug = O.p2u_many(d, pg[sub], x1[sub], x2[sub])
     Uo = O.p2u_many(d, po[sub], x1[sub], x2[sub])
