@@ -1348,23 +1348,34 @@ struct ora_amr {
     std::vector<FaceRec> frec;
     std::vector<EdgeRec> erec;
     std::vector<SyncRec> fsync, esync;
+    std::vector<std::vector<int>> touch; /* blocks whose boxes touch each block (lookup hints) */
     long long stats[4];
 };
 
 namespace {
 
-int amr_find(const ora_amr* m, const double x[4]) {
-    for (int pass = 0; pass < 2; pass++)
-        for (int n = 0; n < (int)m->b.size(); n++) {
-            const AmrBlk& B = m->b[n];
-            bool in = true;
-            for (int d = 1; d <= 3 && in; d++) {
-                double tol = 1e-9 * B.h[d];
-                if (x[d] < B.lo[d] - tol) in = false;
-                if (pass == 0 ? !(x[d] < B.hi[d] - tol) : (x[d] > B.hi[d] + tol)) in = false;
-            }
-            if (in) return n;
+bool amr_in(const AmrBlk& B, const double x[4], int pass) {
+    for (int d = 1; d <= 3; d++) {
+        double tol = 1e-9 * B.h[d];
+        if (x[d] < B.lo[d] - tol) return false;
+        if (pass == 0 ? !(x[d] < B.hi[d] - tol) : (x[d] > B.hi[d] + tol)) return false;
+    }
+    return true;
+}
+
+/* the block holding x: the half-open boxes first (a point on a shared plane
+ * belongs to the block above it), then the closed ones (the domain's upper
+ * boundary); `hint`'s touching blocks are tried before the full scan */
+int amr_find(const ora_amr* m, const double x[4], int hint = -1) {
+    for (int pass = 0; pass < 2; pass++) {
+        if (hint >= 0) {
+            if (amr_in(m->b[hint], x, pass)) return hint;
+            for (int n : m->touch[hint])
+                if (amr_in(m->b[n], x, pass)) return n;
         }
+        for (int n = 0; n < (int)m->b.size(); n++)
+            if (amr_in(m->b[n], x, pass)) return n;
+    }
     return -1;
 }
 
@@ -1554,7 +1565,7 @@ void amr_fill_block(ora_amr* m, int b, int sigma, double* P, double* Bf) {
                                    R.lo[3] + (k + 0.5) * R.h[3]};
                     int neg, clamp;
                     amr_map(m, b, x, 0, &neg, &clamp);
-                    int n = amr_find(m, x);
+                    int n = amr_find(m, x, b);
                     if (n < 0) continue;
                     Src S = amr_src(m, b, n, sigma, m->s);
                     double out[NPR];
@@ -1582,7 +1593,7 @@ void amr_fill_block(ora_amr* m, int b, int sigma, double* P, double* Bf) {
                     x[fd] = R.lo[fd] + ii[fd] * R.h[fd];
                     int neg, clamp;
                     amr_map(m, b, x, fd, &neg, &clamp);
-                    int n = amr_find(m, x);
+                    int n = amr_find(m, x, b);
                     if (n < 0) continue;
                     Src S = amr_src(m, b, n, sigma, m->s);
                     double v = amr_sample_face(m, n, S, x, R.h, fd);
@@ -2052,6 +2063,26 @@ ora_amr* ora_amr_new(const ora_desc* phys, int nb, const ora_block* blocks) {
         m->Lmax = std::max(m->Lmax, o.lat);
         m->b.push_back(B);
     }
+    const int nbk = (int)m->b.size();
+    m->touch.assign(nbk, {});
+    for (int a = 0; a < nbk; a++)
+        for (int c = 0; c < nbk; c++) {
+            if (a == c) continue;
+            bool t = true;
+            for (int d = 1; d <= 3 && t; d++) {
+                const AmrBlk& A = m->b[a];
+                const AmrBlk& C = m->b[c];
+                const double tol = 1e-9 * (m->dhi[d] - m->dlo[d]);
+                bool ok = (A.lo[d] <= C.hi[d] + tol && C.lo[d] <= A.hi[d] + tol);
+                if (!ok && m->per[d]) {
+                    const double L = m->dhi[d] - m->dlo[d];
+                    ok = (A.lo[d] <= C.hi[d] + L + tol && C.lo[d] + L <= A.hi[d] + tol) ||
+                         (A.lo[d] <= C.hi[d] - L + tol && C.lo[d] - L <= A.hi[d] + tol);
+                }
+                t = ok;
+            }
+            if (t) m->touch[a].push_back(c);
+        }
     amr_build_links(m);
     return m;
 }

@@ -477,3 +477,102 @@ def torus_blocks(blocks, a=0.9375, gam=13.0 / 9.0, rin=6.0, rmax=12.0, beta=100.
     for prim, bf in out:
         bf *= fac
     return out
+
+
+def _box(b):
+    lo = [b["x1min"], b["x2min"], b["x3min"]]
+    hi = [lo[d] + b["n%d" % (d + 1)] * b["dx%d" % (d + 1)] for d in range(3)]
+    return lo, hi
+
+
+def _touch(a, b, period3):
+    """blocks a and b share a face, an edge or a corner (phi periodic)"""
+    la, ha = _box(a)
+    lb, hb = _box(b)
+    for d in range(3):
+        tol = 1e-9 * max(ha[d] - la[d], hb[d] - lb[d])
+        if d == 2 and period3:
+            ok = any(la[d] <= hb[d] + s + tol and lb[d] + s <= ha[d] + tol for s in (-period3, 0.0, period3))
+        else:
+            ok = la[d] <= hb[d] + tol and lb[d] <= ha[d] + tol
+        if not ok:
+            return False
+    return True
+
+
+def assign_lat_levels(blocks, lmax=3, period3=2.0 * math.pi):
+    """LAT levels from the light-crossing time of each block's smallest cell
+    in Kerr-Schild internal coordinates, dt_b ~ min over cells of
+    1 / (1/(r dx1) + 1/(r dx2) + 1/(r sin(theta) dx3)) (a state-independent
+    stand-in for the CFL condition, Sec. 3.4), level = min(lmax,
+    floor(log2(dt_b / min dt))); then smoothed so that blocks that touch differ
+    by at most one level and a spatially finer block is never on a coarser
+    time level than a block it touches."""
+    dts = []
+    for b in blocks:
+        x1 = _centres(b["x1min"], b["dx1"], b["n1"])
+        x2 = _centres(b["x2min"], b["dx2"], b["n2"])
+        R, TH = np.meshgrid(np.exp(x1), x2, indexing="ij")
+        inv = 1.0 / (R * b["dx1"]) + 1.0 / (R * b["dx2"]) + 1.0 / (R * np.abs(np.sin(TH)) * b["dx3"])
+        dts.append(float((1.0 / inv).min()))
+    dmin = min(dts)
+    lat = [min(lmax, int(math.floor(math.log2(d / dmin) + 1e-9))) for d in dts]
+    nbh = [[j for j in range(len(blocks)) if j != i and _touch(blocks[i], blocks[j], period3)]
+           for i in range(len(blocks))]
+    vol = [b["dx1"] * b["dx2"] * b["dx3"] for b in blocks]
+    changed = True
+    while changed:
+        changed = False
+        for i in range(len(blocks)):
+            for j in nbh[i]:
+                if lat[i] > lat[j] + 1:
+                    lat[i] = lat[j] + 1
+                    changed = True
+                if vol[i] < vol[j] * (1 - 1e-9) and lat[i] > lat[j]:
+                    lat[i] = lat[j]
+                    changed = True
+    for b, L in zip(blocks, lat):
+        b["lat"] = L
+    return blocks
+
+
+def amr_torus_tree(rin=1.2, rout=50.0, n=32):
+    """512 blocks over r in [rin, rout] (log), theta in [0, pi], phi in [0, 2 pi):
+    a base of 8 x 4 x 4 blocks, n^3 cells near the equator and n x n x n/2 within
+    45 degrees of the poles (phi derefined, external SMR, Sec. 3.3.1); base
+    blocks at r index 2..5 are refined: equatorial ones into 8 octants of n^3
+    cells, polar ones 6-way (Sec. 3.3.1: 4 octants refined in every direction
+    and the 2 children on the axis refined in r and theta only), all n x n x n/2.
+    13,107,200 cells; effective finest grid 512 x 256 x 256. LAT levels from
+    assign_lat_levels."""
+    x1a, x1b = math.log(rin), math.log(rout)
+    nb = (8, 4, 4)
+    hb = ((x1b - x1a) / nb[0], math.pi / nb[1], 2.0 * math.pi / nb[2])
+    blocks = []
+
+    def add(lo, ext, cells):
+        blocks.append(dict(n1=cells[0], n2=cells[1], n3=cells[2], x1min=lo[0], x2min=lo[1], x3min=lo[2],
+                           dx1=ext[0] / cells[0], dx2=ext[1] / cells[1], dx3=ext[2] / cells[2],
+                           bc=[3, 3, 2, 2, 1, 1], lat=0))
+
+    for kb in range(nb[2]):
+        for jb in range(nb[1]):
+            for ib in range(nb[0]):
+                lo = (x1a + ib * hb[0], jb * hb[1], kb * hb[2])
+                polar = jb in (0, nb[1] - 1)
+                cells = (n, n, n // 2) if polar else (n, n, n)
+                if not (2 <= ib <= 5):
+                    add(lo, hb, cells)
+                    continue
+                half = (hb[0] / 2, hb[1] / 2, hb[2] / 2)
+                for jc in range(2):
+                    for ic in range(2):
+                        clo = (lo[0] + ic * half[0], lo[1] + jc * half[1])
+                        axis = polar and ((jb == 0 and jc == 0) or (jb == nb[1] - 1 and jc == 1))
+                        if axis:  # keeps the parent's phi cells and extent
+                            add((clo[0], clo[1], lo[2]), (half[0], half[1], hb[2]), (n, n, n // 2))
+                        else:
+                            for kc in range(2):
+                                add((clo[0], clo[1], lo[2] + kc * half[2]), half, cells)
+    _mark_block_faces(blocks, periodic=(False, False, True))
+    return assign_lat_levels(blocks)

@@ -191,3 +191,74 @@ def test_ghost_exchange_matches_oracle(tree):
             sc = max(np.abs(bo[m]).max(), 1e-300)
             assert np.abs(bg[m] - bo[m]).max() <= 1e-14 * sc, (i, "B", m)
     g.close()
+
+
+def test_512_block_tree_at_8_cubed_matches_oracle():
+    """The 512-block torus tree of the batched benchmark (external SMR, octree
+    and 6-way polar refinement, four LAT levels) with 8^3-class blocks, one
+    LAT period."""
+    blocks = W.amr_torus_tree(n=8)
+    states = W.torus_blocks(blocks, seed=3)
+    phys = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, **KS)
+    out, dts = run_pair(blocks, states, phys, 1)
+    for a, b in dts:
+        assert abs(a - b) <= 1e-13 * b
+    errs = field_errors(blocks, out)
+    for k, e in errs.items():
+        assert e <= 1e-10, (k, e, errs)
+
+
+def test_512_block_tree_full_size_properties():
+    """Full size (13.1 M cells): after one LAT period every block keeps div B at
+    round-off and every face shared by two blocks has one value (the coarse
+    face equals the average of the finer faces covering it)."""
+    from paper_1912_10192_gb300 import hamr
+    blocks = W.amr_torus_tree(n=32)
+    states = W.torus_blocks(blocks, seed=3)
+    g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], metric=0, a=0.9375, gam=13.0 / 9.0, cour=0.8,
+                  floors=1)
+    for i, (p, bf) in enumerate(states):
+        g.set_state(p, bf, block=i)
+    del states
+    st = g.batch_step(8, stats=True)
+    assert st["dt_used"] > 0 and st["c2p_fail"] < 1e-3 * st["c2p_ok"]
+    faces = []
+    for i, b in enumerate(blocks):
+        p, bf = g.get_state(block=i)
+        n1, n2, n3 = b["n1"], b["n2"], b["n3"]
+        s = NG
+        assert np.isfinite(p).all()
+        div = ((bf[0][s:s + n3, s:s + n2, s + 1:s + n1 + 1] - bf[0][s:s + n3, s:s + n2, s:s + n1]) / b["dx1"]
+               + (bf[1][s:s + n3, s + 1:s + n2 + 1, s:s + n1] - bf[1][s:s + n3, s:s + n2, s:s + n1]) / b["dx2"]
+               + (bf[2][s + 1:s + n3 + 1, s:s + n2, s:s + n1] - bf[2][s:s + n3, s:s + n2, s:s + n1]) / b["dx3"])
+        scale = np.abs(bf).max() / min(b["dx1"], b["dx2"], b["dx3"])
+        assert np.abs(div).max() <= 1e-12 * scale, i
+        faces.append(bf)
+    g.close()
+    # shared x1 faces between radial neighbours (the other directions cross the same code)
+    worst = 0.0
+    for i, a in enumerate(blocks):
+        hi1 = a["x1min"] + a["n1"] * a["dx1"]
+        for j, c in enumerate(blocks):
+            if abs(c["x1min"] - hi1) > 1e-9:
+                continue
+            # overlap in theta and phi
+            t0, t1 = max(a["x2min"], c["x2min"]), min(a["x2min"] + a["n2"] * a["dx2"], c["x2min"] + c["n2"] * c["dx2"])
+            p0, p1 = max(a["x3min"], c["x3min"]), min(a["x3min"] + a["n3"] * a["dx3"], c["x3min"] + c["n3"] * c["dx3"])
+            if t1 - t0 < 1e-9 or p1 - p0 < 1e-9:
+                continue
+            h2, h3 = max(a["dx2"], c["dx2"]), max(a["dx3"], c["dx3"])
+
+            def mean_face(b, bf, i1, y0, z0):
+                j0 = int(round((y0 - b["x2min"]) / b["dx2"]))
+                j1 = int(round((y0 + h2 - b["x2min"]) / b["dx2"]))
+                k0 = int(round((z0 - b["x3min"]) / b["dx3"]))
+                k1 = int(round((z0 + h3 - b["x3min"]) / b["dx3"]))
+                return bf[0][NG + k0:NG + k1, NG + j0:NG + j1, NG + i1].mean()
+
+            for y in np.arange(t0, t1 - 1e-12, h2):
+                for z in np.arange(p0, p1 - 1e-12, h3):
+                    va = mean_face(a, faces[i], a["n1"], y, z)
+                    vc = mean_face(c, faces[j], 0, y, z)
+                    worst = max(worst, abs(va - vc))
+    assert worst <= 1e-12 * max(np.abs(f[0]).max() for f in faces), worst
