@@ -157,6 +157,60 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def field_l1(pa, ba, pr, br):
+    """Relative L1 per primitive field over the interior (utilde and face B as one field each)."""
+    ng = 3
+    sl = (slice(ng, ng + N3), slice(ng, ng + N2), slice(ng, ng + N1))
+
+    def l1(vs, a, r):
+        return float(sum(np.abs(a[v][sl] - r[v][sl]).sum() for v in vs) / sum(np.abs(r[v][sl]).sum() for v in vs))
+    fa = [ba[0][ng:ng + N3, ng:ng + N2, ng:ng + N1 + 1], ba[1][ng:ng + N3, ng:ng + N2 + 1, ng:ng + N1],
+          ba[2][ng:ng + N3 + 1, ng:ng + N2, ng:ng + N1]]
+    fr = [br[0][ng:ng + N3, ng:ng + N2, ng:ng + N1 + 1], br[1][ng:ng + N3, ng:ng + N2 + 1, ng:ng + N1],
+          br[2][ng:ng + N3 + 1, ng:ng + N2, ng:ng + N1]]
+    return {"rho": l1((0,), pa, pr), "u": l1((1,), pa, pr), "utilde": l1((2, 3, 4), pa, pr),
+            "Bface": float(sum(np.abs(x - y).sum() for x, y in zip(fa, fr)) / sum(np.abs(y).sum() for y in fr))}
+
+
+def mixed_leg(args, hamr, torch, blk, dprim, dbf, g64, stream, cells, world, dist):
+    """Times the mixed-precision form on the benchmark workload (same protocol as
+    the FP64 leg) and states its relative L1 error per field against the FP64
+    state after the same number of steps from the same initial state."""
+    gm = hamr.Grid([blk], precision=hamr.PREC_MIXED)
+    gm.set_state(dprim, dbf, stream=stream)
+    for _ in range(args.warmup):
+        gm.step(stream=stream)
+    torch.cuda.synchronize()
+    gm.set_timing(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        gm.step(stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    timing = gm.timing()
+    gm.set_timing(False)
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    pm, bm = gm.get_state()
+    p64, b64 = g64.get_state()
+    gm.close()
+    return {"form": "mixed: FP32 reconstruction, face fluxes and edge EMFs; FP64 metric, U^n, update, "
+                    "connection source, CT curl and inversion",
+            "value": cells * args.steps * world / (ms_max * 1e-3), "unit": "zone-cycles/s",
+            "ms_per_step": ms_max / args.steps, "dtype": "f32+f64",
+            "l1_vs_fp64": dict(field_l1(pm, bm, p64, b64), steps=args.warmup + args.steps),
+            "kernel_ms": {k: round(v[1], 3) for k, v in timing.items()},
+            "gpu_launches": int(sum(v[0] for k, v in timing.items() if k != "load"))}
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_1912_10192_gb300 import _build, hamr
@@ -210,6 +264,11 @@ def run_ours(args, rank, world, local):
     ms_max = float(t.item())
     stats = g.stats()
     value = cells * args.steps * world / (ms_max * 1e-3)
+
+    # ---- chosen form: the same workload with FP32 reconstruction, fluxes and EMFs
+    chosen = None
+    if not args.fp64_only:
+        chosen = mixed_leg(args, hamr, torch, blk, dprim, dbf, g, stream, cells, world, dist)
 
     # ---- end to end: host buffers through the C ABI, copies inside the timed region
     e2e_steps = min(args.steps, 10)
@@ -271,7 +330,8 @@ def run_ours(args, rank, world, local):
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches_total), "roofline": roofline,
             "step_fp64_tflops": whole, "step_fp64_frac_nominal": whole / FP64_NOMINAL_TFLOPS,
             "kernel_ms": {k: round(v[1], 3) for k, v in timing.items()},
-            "c2p": {k: stats[k] for k in ("c2p_ok", "c2p_entropy", "c2p_fail", "floor_hits")}}
+            "c2p": {k: stats[k] for k in ("c2p_ok", "c2p_entropy", "c2p_fail", "floor_hits")},
+            "chosen_form": chosen}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, t = cpu_oracle_rate(N1, N2, N3, 1, 0)
         line["cpu_baseline"] = {"value": rate, "unit": "zone-cycles/s", "cores": 1, "kind": "oracle",
@@ -291,6 +351,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-precision leg")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

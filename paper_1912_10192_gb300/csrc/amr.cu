@@ -1074,7 +1074,7 @@ int group_step(AmrImpl& M, int L, int s, cudaStream_t cs) {
         }
         const int fb = M.fs_beg[L], fe = M.fs_end[L];
         if (fe > fb) k_flux_sync<<<nb_(fe - fb), BSA, 0, cs>>>(tab, M.fs, fb, fe);
-        AM_TRY(launch_emf_batch(tab, list, nl, M.lmw_edge[L], cs));
+        AM_TRY(launch_emf_batch(tab, list, nl, M.lmw_edge[L], ph.mixed, cs));
         const int eb = M.es_beg[L], ee = M.es_end[L];
         if (ee > eb) {
             k_edge_gather<<<nb_(ee - eb), BSA, 0, cs>>>(tab, M.es, eb, ee, M.es_tmp);

@@ -320,6 +320,7 @@ int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out) {
     g->ph.recon = d->recon;
     g->ph.riemann = d->riemann;
     g->ph.floors = d->floors;
+    g->ph.mixed = (d->precision == HAMR_PREC_MIXED);
     cudaGetDevice(&g->device);
     for (int b = 0; b < d->nblocks; b++) {
         rc = alloc_block(g, b);
@@ -411,7 +412,7 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
         LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.P, s.QL, s.QR, cs));
         LAUNCH(g, K_FLUX, 1, cs, launch_flux(v, ph, dir, s.QL, s.QR, s.B, s.F[dir - 1], cs));
     }
-    LAUNCH(g, K_EMF, 1, cs, launch_emf(v, s.F, s.E, cs));
+    LAUNCH(g, K_EMF, 1, cs, launch_emf(v, s.F, s.E, ph.mixed, cs));
     LAUNCH(g, K_CT, 1, cs, launch_ct(v, s.E, s.B, s.Bh, s.dscal, 0.5, cs));
     LAUNCH(g, K_UPDATE, 1, cs,
            launch_update(v, ph, 0, s.P, s.P, s.F, s.Bh, s.Un, s.Ph, s.status, s.dscal, 0.5, s.dmax, s.dcnt, cs));
@@ -421,7 +422,7 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
         LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.Ph, s.QL, s.QR, cs));
         LAUNCH(g, K_FLUX, 1, cs, launch_flux(v, ph, dir, s.QL, s.QR, s.Bh, s.F[dir - 1], cs));
     }
-    LAUNCH(g, K_EMF, 1, cs, launch_emf(v, s.F, s.E, cs));
+    LAUNCH(g, K_EMF, 1, cs, launch_emf(v, s.F, s.E, ph.mixed, cs));
     LAUNCH(g, K_CT, 1, cs, launch_ct(v, s.E, s.B, s.B, s.dscal, 1.0, cs));
     LAUNCH(g, K_UPDATE, 1, cs,
            launch_update(v, ph, 1, s.P, s.Ph, s.F, s.B, s.Un, s.P, s.status, s.dscal, 1.0, s.dmax, s.dcnt, cs));

@@ -40,6 +40,7 @@ struct PhysArgs {
     int recon;
     int riemann;
     int floors;
+    int mixed;  // 1: reconstruction and face fluxes in FP32 (HAMR_PREC_MIXED)
 };
 
 // device scratch/state of one block
@@ -97,7 +98,7 @@ cudaError_t launch_recon(const BlockView& v, const PhysArgs& ph, int dir, const 
                          cudaStream_t s);
 cudaError_t launch_flux(const BlockView& v, const PhysArgs& ph, int dir, const double* QL, const double* QR,
                         const double* Bf, double* F, cudaStream_t s);
-cudaError_t launch_emf(const BlockView& v, double* const F[3], double* E, cudaStream_t s);
+cudaError_t launch_emf(const BlockView& v, double* const F[3], double* E, int mixed, cudaStream_t s);
 cudaError_t launch_ct(const BlockView& v, const double* E, const double* Bbase, double* Bout, const double* dscal,
                       double dt_factor, cudaStream_t s);
 cudaError_t launch_update(const BlockView& v, const PhysArgs& ph, int corrector, const double* Pbase,
@@ -117,7 +118,8 @@ cudaError_t launch_recon_batch(const DevBlock* tab, const int* list, int nlist, 
                                int dir, int sigma, cudaStream_t s);
 cudaError_t launch_flux_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
                               int dir, int sigma, cudaStream_t s);
-cudaError_t launch_emf_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, cudaStream_t s);
+cudaError_t launch_emf_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, int mixed,
+                             cudaStream_t s);
 // sigma 0: Bh = B + dt/2 curl E; 1: B += dt curl E; 2: B += curl E (E holds time-integrated corrections)
 cudaError_t launch_ct_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, int sigma, cudaStream_t s);
 cudaError_t launch_update_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,

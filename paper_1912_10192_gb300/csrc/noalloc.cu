@@ -146,6 +146,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     ph.recon = d->recon;
     ph.riemann = d->riemann;
     ph.floors = d->floors;
+    ph.mixed = 0;
 
     // the array keeps the previous call's contents: clear what must start at zero
     NA_TRY(cudaMemsetAsync(s.Ph, 0, sizeof(double) * 11 * v.nc, cs));
@@ -181,7 +182,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
         NA_TRY(launch_recon(v, ph, dir, s.P, s.QL, s.QR, cs));
         NA_TRY(launch_flux(v, ph, dir, s.QL, s.QR, s.B, s.F[dir - 1], cs));
     }
-    NA_TRY(launch_emf(v, s.F, s.E, cs));
+    NA_TRY(launch_emf(v, s.F, s.E, ph.mixed, cs));
     NA_TRY(launch_ct(v, s.E, s.B, s.Bh, s.dscal, 0.5, cs));
     NA_TRY(launch_update(v, ph, 0, s.P, s.P, s.F, s.Bh, s.Un, s.Ph, s.status, s.dscal, 0.5, s.dmax, s.dcnt, cs));
     // corrector
@@ -190,7 +191,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
         NA_TRY(launch_recon(v, ph, dir, s.Ph, s.QL, s.QR, cs));
         NA_TRY(launch_flux(v, ph, dir, s.QL, s.QR, s.Bh, s.F[dir - 1], cs));
     }
-    NA_TRY(launch_emf(v, s.F, s.E, cs));
+    NA_TRY(launch_emf(v, s.F, s.E, ph.mixed, cs));
     NA_TRY(launch_ct(v, s.E, s.B, s.B, s.dscal, 1.0, cs));
     NA_TRY(launch_update(v, ph, 1, s.P, s.Ph, s.F, s.B, s.Un, s.P, s.status, s.dscal, 1.0, s.dmax, s.dcnt, cs));
     NA_TRY(launch_bc(v, s.P, s.B, cs));

@@ -7,8 +7,11 @@
 // Fluxes, EMFs and edge values go through HBM: the FP64 path is bound by the
 // FP64 pipe, so every face flux and every parabola is computed exactly once
 // and re-read from memory instead of recomputed in a halo.
+#include <type_traits>
+
 #include "c2p.cuh"
 #include "grmhd.cuh"
+
 #include "hamr_internal.h"
 
 namespace hamr {
@@ -130,7 +133,7 @@ __global__ void k_bc_axis(BlockView v, double* __restrict__ B) {
 // ---------------------------------------------------------------- reconstruction
 // edge values of every cell that borders a flux face of direction dir:
 // cells -1..n_dir along dir, -1..n_e across.
-template <int DIR>
+template <int DIR, typename T>
 __device__ __forceinline__ void b_recon(const BlockView& v, PhysArgs ph, const double* __restrict__ P, double* __restrict__ QL,
                         double* __restrict__ QR, long t) {
     const int nn[4] = {0, v.n1, v.n2, v.n3};
@@ -143,31 +146,36 @@ __device__ __forceinline__ void b_recon(const BlockView& v, PhysArgs ph, const d
     for (int q = 0; q < NPRIM; q++) {
         if (q == B1 + DIR - 1) continue;
         const double* p = P + q * v.nc + c;
-        double l, r;
+        // FP32: the stencil is taken relative to the cell value (differences formed in FP64),
+        // so rounding scales with the local variation, not with the value itself.
+        constexpr bool dev = !std::is_same<T, double>::value;
+        const double base = dev ? p[0] : 0.0;
+        auto at = [&](long o) -> T { return dev ? (T)(p[o] - base) : (T)p[o]; };
+        T l, r;
         if (ph.recon == HAMR_RECON_PPM) {
-            const double s[5] = {p[-2 * st], p[-st], p[0], p[st], p[2 * st]};
+            const T s[5] = {at(-2 * st), at(-st), at(0), at(st), at(2 * st)};
             ppm_cell(s, l, r);
         } else {
-            const double qm = p[-st], q0 = p[0], qp = p[st];
-            const double dq = (ph.recon == HAMR_RECON_MC) ? mc_slope(qm, q0, qp) : minmod_slope(qm, q0, qp);
-            l = q0 - 0.5 * dq;
-            r = q0 + 0.5 * dq;
+            const T qm = at(-st), q0 = at(0), qp = at(st);
+            const T dq = (ph.recon == HAMR_RECON_MC) ? mc_slope(qm, q0, qp) : minmod_slope(qm, q0, qp);
+            l = q0 - T(0.5) * dq;
+            r = q0 + T(0.5) * dq;
         }
-        QL[q * v.nc + c] = l;
-        QR[q * v.nc + c] = r;
+        QL[q * v.nc + c] = dev ? base + (double)l : (double)l;
+        QR[q * v.nc + c] = dev ? base + (double)r : (double)r;
     }
 }
 
-template <int DIR>
+template <int DIR, typename T>
 __global__ void k_recon(BlockView v, PhysArgs ph, const double* __restrict__ P, double* __restrict__ QL,
                         double* __restrict__ QR) {
-    b_recon<DIR>(v, ph, P, QL, QR, (long)blockIdx.x * blockDim.x + threadIdx.x);
+    b_recon<DIR, T>(v, ph, P, QL, QR, (long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 
 // ---------------------------------------------------------------- fluxes
 // HLLE (or LLF) flux through every dir-face: faces 0..n_dir, -1..n_e across.
-template <int DIR>
+template <int DIR, typename T>
 __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const double* __restrict__ QL,
                                              const double* __restrict__ QR, const double* __restrict__ Bf,
                                              double* __restrict__ F, long t) {
@@ -182,71 +190,76 @@ __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const do
     const long c = cidx(v, i, j, k);
     const long st = (DIR == 1) ? 1 : ((DIR == 2) ? (long)v.n1p : (long)v.n1p * v.n2p);
     const double* tab = (DIR == 1) ? v.gf1 : ((DIR == 2) ? v.gf2 : v.gc);
-    Metric<double> m;
+    Metric<T> m;
     load_metric(tab, v.n2d, gidx(v, i, j), m);
-    if (m.gdet == 0.0) {  // face on the polar axis: no area
+    if (m.gdet == T(0)) {  // face on the polar axis: no area
 #pragma unroll
         for (int q = 0; q < NFLUX; q++) F[q * v.nc + c] = 0.0;
         return;
     }
-    double pl[NPRIM], pr[NPRIM];
+    T pl[NPRIM], pr[NPRIM];
 #pragma unroll
     for (int q = 0; q < NPRIM; q++) {
         if (q == B1 + DIR - 1) continue;
-        pl[q] = QR[q * v.nc + c - st];
-        pr[q] = QL[q * v.nc + c];
+        pl[q] = (T)QR[q * v.nc + c - st];
+        pr[q] = (T)QL[q * v.nc + c];
     }
-    const double bn = Bf[(DIR - 1) * v.nc + c] / m.gdet;
+    const T bn = (T)Bf[(DIR - 1) * v.nc + c] / m.gdet;
     pl[B1 + DIR - 1] = bn;
     pr[B1 + DIR - 1] = bn;
-    const double gam = ph.gam;
-    double UL[NFLUX], FL[NFLUX], UR[NFLUX], FR[NFLUX];
-    double vpl, vml, vpr, vmr;
+    const T gam = (T)ph.gam;
+    T UL[NFLUX], FL[NFLUX], UR[NFLUX], FR[NFLUX];
+    T vpl, vml, vpr, vmr;
     {
-        Fluid<double> s;
+        Fluid<T> s;
         fluid_state(pl, m, s);
-        const double kap = entropy_kappa(pl, gam);
+        const T kap = entropy_kappa(pl, gam);
         flux_row(pl, s, 0, DIR, gam, kap, UL);
         flux_row(pl, s, DIR, DIR, gam, kap, FL);
         wave_speeds(pl, s, m, DIR, gam, vpl, vml);
     }
     {
-        Fluid<double> s;
+        Fluid<T> s;
         fluid_state(pr, m, s);
-        const double kap = entropy_kappa(pr, gam);
+        const T kap = entropy_kappa(pr, gam);
         flux_row(pr, s, 0, DIR, gam, kap, UR);
         flux_row(pr, s, DIR, DIR, gam, kap, FR);
         wave_speeds(pr, s, m, DIR, gam, vpr, vmr);
     }
     // U's B slots: B^i for the transverse i (flux_row with d = 0 gives b^i u^t - b^t u^i = B^i)
-    const double cmax = fmax(0.0, fmax(vpl, vpr));
-    const double cmin = fmax(0.0, fmax(-vml, -vmr));
+    const T cmax = fmax(T(0), fmax(vpl, vpr));
+    const T cmin = fmax(T(0), fmax(-vml, -vmr));
     if (ph.riemann == HAMR_FLUX_LLF) {
-        const double cm = fmax(cmax, cmin);
+        const T cm = fmax(cmax, cmin);
 #pragma unroll
-        for (int q = 0; q < NFLUX; q++) F[q * v.nc + c] = 0.5 * (FL[q] + FR[q] - cm * (UR[q] - UL[q])) * m.gdet;
-    } else if (cmax + cmin > 0.0) {
-        const double w = m.gdet / (cmax + cmin);
-        const double cc = cmax * cmin;
+        for (int q = 0; q < NFLUX; q++)
+            F[q * v.nc + c] = (double)(T(0.5) * (FL[q] + FR[q] - cm * (UR[q] - UL[q])) * m.gdet);
+    } else if (cmax + cmin > T(0)) {
+        const T w = m.gdet / (cmax + cmin);
+        const T cc = cmax * cmin;
 #pragma unroll
-        for (int q = 0; q < NFLUX; q++) F[q * v.nc + c] = (cmin * FR[q] + cmax * FL[q] - cc * (UR[q] - UL[q])) * w;
+        for (int q = 0; q < NFLUX; q++)
+            F[q * v.nc + c] = (double)((cmin * FR[q] + cmax * FL[q] - cc * (UR[q] - UL[q])) * w);
     } else {
 #pragma unroll
-        for (int q = 0; q < NFLUX; q++) F[q * v.nc + c] = 0.5 * (FL[q] + FR[q]) * m.gdet;
+        for (int q = 0; q < NFLUX; q++) F[q * v.nc + c] = (double)(T(0.5) * (FL[q] + FR[q]) * m.gdet);
     }
 }
 
-template <int DIR>
+template <int DIR, typename T>
 __global__ void __launch_bounds__(BS) k_flux(BlockView v, PhysArgs ph, const double* __restrict__ QL,
                                              const double* __restrict__ QR, const double* __restrict__ Bf,
                                              double* __restrict__ F) {
-    b_flux<DIR>(v, ph, QL, QR, Bf, F, (long)blockIdx.x * blockDim.x + threadIdx.x);
+    b_flux<DIR, T>(v, ph, QL, QR, Bf, F, (long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 
 // ---------------------------------------------------------------- EMFs
 // edge EMFs as the average of the 4 neighbouring face fluxes of B (Sec. 2.5).
-// E1 and E3 on the polar axis are 0.
+// E1 and E3 on the polar axis are 0. With T = float (mixed precision) the
+// average is formed in FP32; every face shares the one stored edge value, so
+// the FP64 curl in the CT update still keeps div B at FP64 roundoff.
+template <typename T>
 __device__ __forceinline__ void b_emf(const BlockView& v, const double* __restrict__ F1, const double* __restrict__ F2,
                       const double* __restrict__ F3, double* __restrict__ E, long t) {
     const int e1 = v.n1 + 1, e2 = v.n2 + 1, e3 = v.n3 + 1;
@@ -255,23 +268,26 @@ __device__ __forceinline__ void b_emf(const BlockView& v, const double* __restri
     const long c = cidx(v, i, j, k);
     const long sj = v.n1p, sk = (long)v.n1p * v.n2p, nc = v.nc;
     const bool axis = (v.bc[2] == HAMR_BC_POLAR && j == 0) || (v.bc[3] == HAMR_BC_POLAR && j == v.n2);
+    const T q = T(0.25);
     // flux slots: F1 -> (B2: 6, B3: 7), F2 -> (B1: 6, B3: 7), F3 -> (B1: 6, B2: 7)
     if (i < v.n1) {
-        const double x = 0.25 * (F3[7 * nc + c] + F3[7 * nc + c - sj] - F2[7 * nc + c - sk] - F2[7 * nc + c]);
-        E[c] = axis ? 0.0 : x;
+        const T x = q * ((T)F3[7 * nc + c] + (T)F3[7 * nc + c - sj] - (T)F2[7 * nc + c - sk] - (T)F2[7 * nc + c]);
+        E[c] = axis ? 0.0 : (double)x;
     }
     if (j < v.n2) {
-        E[nc + c] = 0.25 * (F1[7 * nc + c - sk] + F1[7 * nc + c] - F3[6 * nc + c] - F3[6 * nc + c - 1]);
+        E[nc + c] = (double)(q * ((T)F1[7 * nc + c - sk] + (T)F1[7 * nc + c] - (T)F3[6 * nc + c] -
+                                  (T)F3[6 * nc + c - 1]));
     }
     if (k < v.n3) {
-        const double x = 0.25 * (F2[6 * nc + c - 1] + F2[6 * nc + c] - F1[6 * nc + c] - F1[6 * nc + c - sj]);
-        E[2 * nc + c] = axis ? 0.0 : x;
+        const T x = q * ((T)F2[6 * nc + c - 1] + (T)F2[6 * nc + c] - (T)F1[6 * nc + c] - (T)F1[6 * nc + c - sj]);
+        E[2 * nc + c] = axis ? 0.0 : (double)x;
     }
 }
 
+template <typename T>
 __global__ void k_emf(BlockView v, const double* __restrict__ F1, const double* __restrict__ F2,
                       const double* __restrict__ F3, double* __restrict__ E) {
-    b_emf(v, F1, F2, F3, E, (long)blockIdx.x * blockDim.x + threadIdx.x);
+    b_emf<T>(v, F1, F2, F3, E, (long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 
@@ -509,22 +525,23 @@ __global__ void k_dt_select(double cour, double user_dt, double* dscal, unsigned
 // threadIdx.x index the work inside it exactly as in the single-block kernels.
 __device__ __forceinline__ long tidx() { return (long)blockIdx.x * blockDim.x + threadIdx.x; }
 
-template <int DIR>
+template <int DIR, typename T>
 __global__ void kb_recon(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
     const DevBlock& D = tab[list[blockIdx.y]];
-    b_recon<DIR>(D.v, ph, sigma ? D.Ph : D.P, D.QL, D.QR, tidx());
+    b_recon<DIR, T>(D.v, ph, sigma ? D.Ph : D.P, D.QL, D.QR, tidx());
 }
 
-template <int DIR>
+template <int DIR, typename T>
 __global__ void __launch_bounds__(BS) kb_flux(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
     const DevBlock& D = tab[list[blockIdx.y]];
     double* F = (DIR == 1) ? D.F1 : ((DIR == 2) ? D.F2 : D.F3);
-    b_flux<DIR>(D.v, ph, D.QL, D.QR, sigma ? D.Bh : D.B, F, tidx());
+    b_flux<DIR, T>(D.v, ph, D.QL, D.QR, sigma ? D.Bh : D.B, F, tidx());
 }
 
+template <typename T>
 __global__ void kb_emf(const DevBlock* tab, const int* list) {
     const DevBlock& D = tab[list[blockIdx.y]];
-    b_emf(D.v, D.F1, D.F2, D.F3, D.E, tidx());
+    b_emf<T>(D.v, D.F1, D.F2, D.F3, D.E, tidx());
 }
 
 __global__ void kb_ct(const DevBlock* tab, const int* list, int sigma) {
@@ -659,9 +676,15 @@ cudaError_t launch_bc(const BlockView& v, double* P, double* B, cudaStream_t s) 
 cudaError_t launch_recon(const BlockView& v, const PhysArgs& ph, int dir, const double* P, double* QL, double* QR,
                          cudaStream_t s) {
     const long n = (long)(v.n1 + 2) * (v.n2 + 2) * (v.n3 + 2);
-    if (dir == 1) k_recon<1><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
-    if (dir == 2) k_recon<2><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
-    if (dir == 3) k_recon<3><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
+    if (ph.mixed) {
+        if (dir == 1) k_recon<1, float><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
+        if (dir == 2) k_recon<2, float><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
+        if (dir == 3) k_recon<3, float><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
+    } else {
+        if (dir == 1) k_recon<1, double><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
+        if (dir == 2) k_recon<2, double><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
+        if (dir == 3) k_recon<3, double><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
+    }
     return cudaGetLastError();
 }
 
@@ -669,15 +692,24 @@ cudaError_t launch_flux(const BlockView& v, const PhysArgs& ph, int dir, const d
                         const double* Bf, double* F, cudaStream_t s) {
     const long n1 = v.n1 + (dir == 1 ? 1 : 2), n2 = v.n2 + (dir == 2 ? 1 : 2), n3 = v.n3 + (dir == 3 ? 1 : 2);
     const long n = n1 * n2 * n3;
-    if (dir == 1) k_flux<1><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
-    if (dir == 2) k_flux<2><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
-    if (dir == 3) k_flux<3><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
+    if (ph.mixed) {
+        if (dir == 1) k_flux<1, float><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
+        if (dir == 2) k_flux<2, float><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
+        if (dir == 3) k_flux<3, float><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
+    } else {
+        if (dir == 1) k_flux<1, double><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
+        if (dir == 2) k_flux<2, double><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
+        if (dir == 3) k_flux<3, double><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_emf(const BlockView& v, double* const F[3], double* E, cudaStream_t s) {
+cudaError_t launch_emf(const BlockView& v, double* const F[3], double* E, int mixed, cudaStream_t s) {
     const long n = (long)(v.n1 + 1) * (v.n2 + 1) * (v.n3 + 1);
-    k_emf<<<nblk(n), BS, 0, s>>>(v, F[0], F[1], F[2], E);
+    if (mixed)
+        k_emf<float><<<nblk(n), BS, 0, s>>>(v, F[0], F[1], F[2], E);
+    else
+        k_emf<double><<<nblk(n), BS, 0, s>>>(v, F[0], F[1], F[2], E);
     return cudaGetLastError();
 }
 
@@ -718,24 +750,42 @@ inline dim3 bgrid(long maxwork, int nlist) { return dim3(nblk(maxwork), (unsigne
 cudaError_t launch_recon_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
                                int dir, int sigma, cudaStream_t s) {
     if (nlist <= 0) return cudaSuccess;
-    if (dir == 1) kb_recon<1><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
-    if (dir == 2) kb_recon<2><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
-    if (dir == 3) kb_recon<3><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
+    const dim3 g = bgrid(maxwork, nlist);
+    if (ph.mixed) {
+        if (dir == 1) kb_recon<1, float><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 2) kb_recon<2, float><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 3) kb_recon<3, float><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+    } else {
+        if (dir == 1) kb_recon<1, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 2) kb_recon<2, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 3) kb_recon<3, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_flux_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
                               int dir, int sigma, cudaStream_t s) {
     if (nlist <= 0) return cudaSuccess;
-    if (dir == 1) kb_flux<1><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
-    if (dir == 2) kb_flux<2><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
-    if (dir == 3) kb_flux<3><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
+    const dim3 g = bgrid(maxwork, nlist);
+    if (ph.mixed) {
+        if (dir == 1) kb_flux<1, float><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 2) kb_flux<2, float><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 3) kb_flux<3, float><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+    } else {
+        if (dir == 1) kb_flux<1, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 2) kb_flux<2, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 3) kb_flux<3, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_emf_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, cudaStream_t s) {
+cudaError_t launch_emf_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, int mixed,
+                             cudaStream_t s) {
     if (nlist <= 0) return cudaSuccess;
-    kb_emf<<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list);
+    if (mixed)
+        kb_emf<float><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list);
+    else
+        kb_emf<double><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list);
     return cudaGetLastError();
 }
 

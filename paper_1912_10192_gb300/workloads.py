@@ -576,3 +576,175 @@ def amr_torus_tree(rin=1.2, rout=50.0, n=32):
                                 add((clo[0], clo[1], lo[2] + kc * half[2]), half, cells)
     _mark_block_faces(blocks, periodic=(False, False, True))
     return assign_lat_levels(blocks)
+
+
+# --- tilted thin disk --------------------------------------------------------
+
+def disk_geometry(n1=448, n2=192, n3=384, rin=1.2, rout=200.0):
+    return BlockGeometry(n1, n2, n3, math.log(rin), math.log(rout), 0.0, math.pi, 0.0, 2.0 * math.pi)
+
+
+def _trig_theta(th):
+    """sin, cos of theta with the polar axis (0 or pi) mapped to exactly 0, +-1."""
+    s, c = np.sin(th), np.cos(th)
+    ax0 = np.abs(th) < 1e-12
+    ax1 = np.abs(th - math.pi) < 1e-12
+    s = np.where(ax0 | ax1, 0.0, s)
+    c = np.where(ax0, 1.0, np.where(ax1, -1.0, c))
+    return s, c
+
+
+def tilted_disk_block(geo, a=0.9375, gam=13.0 / 9.0, hr=0.03, tilt_deg=65.0, beta=10.0, rd_in=6.0,
+                      rd_out=100.0, pert=0.02, seed=4):
+    """Padded primitive (8, n3p, n2p, n1p) and face-B (3, ...) arrays of a thin
+    disk whose midplane is tilted by tilt_deg about the x axis.
+
+    In the disk frame (normal n = (0, -sin tilt, cos tilt), height
+    z' = r_vec . n, cylindrical radius R' = |r_vec - z' n|, scale height
+    H = hr R'):
+      rho = R'^-3/2 exp(-z'^2 / 2H^2) T(R'),  T = exp(-(rd_in/R')^6 - (R'/rd_out)^6),
+      normalised to max rho = 1;
+      p_g = rho c_s^2 / Gamma with c_s = hr v_K, v_K = R'^-1/2 (u_g = p_g/(Gamma-1)),
+      with a seeded +/- pert perturbation of u_g;
+      rotation at Omega = R'^-3/2 about n: coordinate velocity V = Omega n x r_vec
+      (purely tangential, so dr/dt = 0), u^t from the metric normalisation and
+      utilde^i = u^i + alpha^2 u^t g^{ti}; velocities only where the disk
+      density exceeds 1e-6 of its maximum and r > 3.
+    Field: toroidal about n, from the edge vector potential A = A_R' R'_hat with
+    A_R' = sqrt(pi) H sqrt(2 p_mid(R')/beta) erf(z' / 2H), so that
+    B_phi' = dA_R'/dz' = sqrt(2 p_g / beta) locally; face fluxes are the
+    discrete curl of the covariant edge components (divergence-free to
+    roundoff, zero on the polar axis), then normalised to
+    max p_g / max p_b = beta over the block.
+    Atmosphere and floors as in torus_block. Position geometry (r_vec, R', z')
+    is flat-space spherical in (r, theta, phi).
+    """
+    n1, n2, n3 = geo.n1, geo.n2, geo.n3
+    shp = geo.padded_shape
+    prim = np.zeros((8,) + shp)
+    bface = np.zeros((3,) + shp)
+    tl = math.radians(tilt_deg)
+    nvec = np.array([0.0, -math.sin(tl), math.cos(tl)])
+
+    x1c = _centres(geo.x1min, geo.dx1, n1)
+    x2c = _centres(geo.x2min, geo.dx2, n2)
+    x3c = _centres(geo.x3min, geo.dx3, n3)
+    x1e = _edges(geo.x1min, geo.dx1, n1)
+    x2e = _edges(geo.x2min, geo.dx2, n2)
+    x3e = _edges(geo.x3min, geo.dx3, n3)[:n3]  # phi edge n3 is edge 0 (periodic)
+
+    def frame(r, th, ph):
+        s, c = _trig_theta(th)
+        cp, sp = np.cos(ph), np.sin(ph)
+        rhat = np.stack(np.broadcast_arrays(s * cp, s * sp, c))
+        thhat = np.stack(np.broadcast_arrays(c * cp, c * sp, -s))
+        phhat = np.stack(np.broadcast_arrays(-sp, cp, 0.0 * s))
+        rv = r * rhat
+        zp = nvec[0] * rv[0] + nvec[1] * rv[1] + nvec[2] * rv[2]
+        rperp = rv - zp * nvec[:, None, None]
+        Rp = np.sqrt(np.maximum(r * r - zp * zp, 0.0))
+        return s, rhat, thhat, phhat, rv, zp, rperp, Rp
+
+    def taper(Rp):
+        with np.errstate(divide="ignore", over="ignore"):
+            return np.exp(-(rd_in / np.maximum(Rp, 1e-3)) ** 6 - (Rp / rd_out) ** 6)
+
+    def rho_disk(Rp, zp):
+        Rs = np.maximum(Rp, 1e-3)
+        H = hr * Rs
+        return Rs ** -1.5 * np.exp(-zp * zp / (2.0 * H * H)) * taper(Rp)
+
+    # normalisation: the maximum sits on the midplane, max over R' of R'^-3/2 T(R')
+    Rg = np.exp(np.linspace(0.0, math.log(2.0 * rd_out), 20001))
+    rho0 = float((Rg ** -1.5 * taper(Rg)).max())
+
+    R2, TH2 = np.meshgrid(np.exp(x1c), x2c, indexing="xy")  # (n2, n1) centres
+    gcov, gtt_con, gt1_con, gdet = _ks_internal(a, R2, TH2)
+    alpha = 1.0 / np.sqrt(-gtt_con)
+    rho_flr = 1.0e-7 / R2 ** 2
+    u_flr = 1.0e-9 * R2 ** (-10.0 / 3.0)
+    pgmax = 0.0
+    sl = (slice(NG, NG + n2), slice(NG, NG + n1))
+    for k in range(n3):
+        s, rhat, thhat, phhat, rv, zp, rperp, Rp = frame(R2, TH2, x3c[k])
+        rho_d = rho_disk(Rp, zp) / rho0
+        cs2 = hr * hr / np.maximum(Rp, 1e-3)
+        u_d = rho_d * cs2 / gam / (gam - 1.0)
+        ids = (np.arange(n1)[None, :] + n1 * (np.arange(n2)[:, None] + n2 * k)).astype(np.uint64)
+        xi = uniform01(seed, ids)
+        disk = (rho_d > 1e-6) & (R2 > 3.0)
+        u_d = np.where(disk, u_d * (1.0 + pert * (2.0 * xi - 1.0)), u_d)
+        rho = np.maximum(rho_d, rho_flr)
+        u = np.maximum(u_d, u_flr)
+        # tilted Keplerian rotation, coordinate velocity dx^i/dt
+        Om = np.maximum(Rp, 1e-3) ** -1.5
+        V = Om * np.cross(nvec[:, None, None], rv, axis=0)
+        V2 = (V * thhat).sum(axis=0) / R2
+        V3 = np.where(s > 0.0, (V * phhat).sum(axis=0) / (R2 * np.where(s > 0.0, s, 1.0)), 0.0)
+        norm = -(gcov[(0, 0)] + 2.0 * gcov[(0, 3)] * V3 + gcov[(2, 2)] * V2 * V2 + gcov[(3, 3)] * V3 * V3)
+        ok = disk & (norm > 0.0)
+        ut = np.where(ok, 1.0 / np.sqrt(np.where(ok, norm, 1.0)), 0.0)
+        prim[0, NG + k][sl] = rho
+        prim[1, NG + k][sl] = u
+        prim[2, NG + k][sl] = np.where(ok, alpha * alpha * ut * gt1_con, 0.0)
+        prim[3, NG + k][sl] = ut * V2
+        prim[4, NG + k][sl] = ut * V3
+        pgmax = max(pgmax, float(((gam - 1.0) * u).max()))
+
+    # edge vector potential, covariant components in (x1, x2, x3)
+    def a_cov(r, th, ph, comp):
+        s, rhat, thhat, phhat, rv, zp, rperp, Rp = frame(r, th, ph)
+        Rs = np.maximum(Rp, 1e-3)
+        H = hr * Rs
+        pmid = Rs ** -1.5 * taper(Rp) / rho0 * (hr * hr / Rs) / gam
+        amp = math.sqrt(math.pi) * H * np.sqrt(2.0 * pmid / beta) * _erf(zp / (2.0 * H))
+        Rhat = rperp / Rs
+        e = (rhat * r, thhat * r, phhat * (r * s))[comp]
+        return amp * (Rhat * e).sum(axis=0)
+
+    A1 = np.empty((n3, n2 + 1, n1))
+    A2 = np.empty((n3, n2, n1 + 1))
+    A3 = np.empty((n3, n2 + 1, n1 + 1))
+    Rc1, Te1 = np.meshgrid(np.exp(x1c), x2e, indexing="xy")
+    Re2, Tc2 = np.meshgrid(np.exp(x1e), x2c, indexing="xy")
+    Re3, Te3 = np.meshgrid(np.exp(x1e), x2e, indexing="xy")
+    for k in range(n3):
+        A1[k] = a_cov(Rc1, Te1, x3e[k], 0)
+        A2[k] = a_cov(Re2, Tc2, x3e[k], 1)
+        A3[k] = a_cov(Re3, Te3, x3c[k], 2)
+    A1p = np.concatenate([A1, A1[:1]], axis=0)  # edge k = n3 is edge 0
+    A2p = np.concatenate([A2, A2[:1]], axis=0)
+    # Bbar^1 = d2 A3 - d3 A2 at x1 faces (n3, n2, n1+1)
+    b1 = (A3[:, 1:, :] - A3[:, :-1, :]) / geo.dx2 - (A2p[1:] - A2p[:-1]) / geo.dx3
+    # Bbar^2 = d3 A1 - d1 A3 at x2 faces (n3, n2+1, n1)
+    b2 = (A1p[1:] - A1p[:-1]) / geo.dx3 - (A3[:, :, 1:] - A3[:, :, :-1]) / geo.dx1
+    # Bbar^3 = d1 A2 - d2 A1 at x3 faces (n3, n2, n1)
+    b3 = (A2[:, :, 1:] - A2[:, :, :-1]) / geo.dx1 - (A1[:, 1:, :] - A1[:, :-1, :]) / geo.dx2
+    if geo.x2min == 0.0:
+        b2[:, 0, :] = 0.0
+    if abs(geo.x2min + n2 * geo.dx2 - math.pi) < 1e-12:
+        b2[:, -1, :] = 0.0
+
+    # normalise to max p_g / max p_b = beta with centre B = <Bbar>/sqrt(-g)
+    pbmax = 0.0
+    for k in range(n3):
+        kp = (k + 1) % n3
+        Bc1 = 0.5 * (b1[k, :, :-1] + b1[k, :, 1:]) / gdet
+        Bc2 = 0.5 * (b2[k, :-1, :] + b2[k, 1:, :]) / gdet
+        Bc3 = 0.5 * (b3[k] + b3[kp]) / gdet
+        pu = (prim[2, NG + k][sl], prim[3, NG + k][sl], prim[4, NG + k][sl])
+        pbmax = max(pbmax, float(0.5 * _bsq(a, R2, TH2, pu, (Bc1, Bc2, Bc3)).max()))
+    fac = math.sqrt(pgmax / (beta * pbmax)) if (pbmax > 0.0 and beta > 0.0) else 0.0
+    bface[0, NG:NG + n3, NG:NG + n2, NG:NG + n1 + 1] = fac * b1
+    bface[1, NG:NG + n3, NG:NG + n2 + 1, NG:NG + n1] = fac * b2
+    bface[2, NG:NG + n3, NG:NG + n2, NG:NG + n1] = fac * b3
+    return prim, bface
+
+
+def _erf(x):
+    """Vectorised error function (scipy when present, else math.erf per element)."""
+    try:
+        from scipy.special import erf as serf
+        return serf(x)
+    except ImportError:  # pragma: no cover
+        return np.vectorize(math.erf)(x)

@@ -1,0 +1,172 @@
+"""Mixed-precision form of the block step: reconstruction, face fluxes and
+edge EMFs in FP32; metric tables, U^n, the conserved update with its
+connection source, the CT curl and the inversion in FP64.
+
+Error measure: relative L1 per primitive field, sum|x - ref| / sum|ref| over
+interior cells (the utilde and face-B vectors as one field each).
+
+* Against the FP64 CPU oracle on the 64x32x16 torus (1 and 10 steps) and on a
+  reduced tilted disk, with the bars stated below.
+* Against the FP64 CUDA path (itself checked against the oracle to 1e-12)
+  on the tilted thin disk after 100 steps: the density bar is 1e-6.
+* div B stays at FP64 roundoff: each edge EMF is stored once and shared by
+  every face that takes its curl.
+
+Bars. FP32 unit roundoff is u = 2^-24 = 6.0e-8. The edge values carry
+O(u |dq|) error (they are formed relative to the cell value), a face flux
+O(u |F|); a step changes a cell by dt/dx sum(F), so the density gains
+O(u) relative error per step, of random sign from step to step. Two fields
+amplify it: the velocity where the field dominates the inertia (the
+momentum-flux error is O(u b^2) against a momentum O(rho); sigma = b^2/rho
+reaches the floor cap of 50, and 99% of the utilde error sits in cells with
+rho < 1e-6), and u_g where it is a small remainder of the total energy (a
+cold, rotating flow: in the thin disk the kinetic energy is ~ (h/r)^-2 ~ 1e3
+times the thermal one). The bars are about 10x the errors measured on GB300
+(FP64 against the same oracle: <= 1e-13):
+
+  torus 64x32x16, 1 step     rho 1.0e-9  u_g 6.1e-8  utilde 1.1e-6  Bbar 2.1e-9
+  torus 64x32x16, 10 steps   rho 5.4e-9  u_g 2.0e-7  utilde 1.9e-6  Bbar 8.3e-9
+  disk 56x24x48, 10 steps    rho 4.7e-8  u_g 2.0e-5  utilde 4.3e-6  Bbar 1.1e-8
+  disk 448x192x384, 100 steps against FP64:
+                             rho 6.3e-8  u_g 1.7e-4  utilde 4.5e-6  Bbar 8.4e-9
+
+and for the full disk the density bar is the 1e-6 target itself.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1912_10192_gb300 import workloads as W
+
+from helpers import NG, TORUS_BC, face_interior, interior, rel_l1, torus_case
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+BAR_TORUS_1 = {"rho": 1e-8, "u": 1e-6, "utilde": 1e-5, "Bface": 2e-8}
+BAR_TORUS_10 = {"rho": 5e-8, "u": 2e-6, "utilde": 2e-5, "Bface": 1e-7}
+BAR_DISK_10 = {"rho": 5e-7, "u": 2e-4, "utilde": 5e-5, "Bface": 1e-7}
+BAR_DISK_100 = {"rho": 1e-6, "u": 2e-3, "utilde": 5e-5, "Bface": 1e-7}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_10192_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+
+
+def grid(d, precision):
+    from paper_1912_10192_gb300 import hamr
+    b = hamr.block(d.n1, d.n2, d.n3, d.x1min, d.x2min, d.x3min, d.dx1, d.dx2, d.dx3, tuple(d.bc))
+    return hamr.Grid([b], metric=d.metric, a=d.a, gam=d.gam, cour=d.cour, recon=d.recon, riemann=d.riemann,
+                     floors=d.floors, precision=precision)
+
+
+def disk_case(n1, n2, n3, seed=4):
+    geo = W.disk_geometry(n1, n2, n3)
+    prim, bf = W.tilted_disk_block(geo, seed=seed)
+    d = O.make_desc(n1, n2, n3, geo.x1min, geo.x2min, geo.x3min, geo.dx1, geo.dx2, geo.dx3, metric=O.METRIC_KS,
+                    a=0.9375, gam=13.0 / 9.0, cour=0.8, bc=TORUS_BC)
+    return geo, d, prim, bf
+
+
+def run_gpu(d, prim, bf, nsteps, precision, dts=None):
+    g = grid(d, precision)
+    g.set_state(torch.from_numpy(prim).cuda(), torch.from_numpy(bf).cuda())
+    used = []
+    for n in range(nsteps):
+        st = g.step(-1.0 if dts is None else dts[n], stats=True)
+        used.append(st["dt_used"])
+    p, b = g.get_state()
+    g.close()
+    return p, b, used
+
+
+def errors(d, p, b, pr, br):
+    e = {"rho": rel_l1(interior(p[0], d), interior(pr[0], d)),
+         "u": rel_l1(interior(p[1], d), interior(pr[1], d))}
+    num = sum(np.abs(interior(p[v], d) - interior(pr[v], d)).sum() for v in (2, 3, 4))
+    den = sum(np.abs(interior(pr[v], d)).sum() for v in (2, 3, 4))
+    e["utilde"] = num / den
+    f, fr = face_interior(b, d), face_interior(br, d)
+    e["Bface"] = sum(np.abs(x - y).sum() for x, y in zip(f, fr)) / sum(np.abs(y).sum() for y in fr)
+    return e
+
+
+def div_b(d, b):
+    """max |discrete div Bbar| over interior cells, relative to max |Bbar| / dx."""
+    f = face_interior(b, d)
+    div = ((f[0][:, :, 1:] - f[0][:, :, :-1]) / d.dx1 + (f[1][:, 1:, :] - f[1][:, :-1, :]) / d.dx2
+           + (f[2][1:] - f[2][:-1]) / d.dx3)
+    scale = max(np.abs(x).max() for x in f) / min(d.dx1, d.dx2, d.dx3)
+    return np.abs(div).max() / scale
+
+
+@pytest.mark.parametrize("nsteps,bar", [(1, BAR_TORUS_1), (10, BAR_TORUS_10)])
+def test_mixed_vs_oracle_torus(nsteps, bar):
+    _, d, prim, bf = torus_case(64, 32, 16, seed=1912)
+    p, b, used = run_gpu(d, prim, bf, nsteps, precision=1)
+    og = O.Grid(d)
+    og.set(prim, bf)
+    for n in range(nsteps):
+        og.step(used[n])  # the oracle takes the mixed run's dt: the comparison is of the update alone
+    po, bo = og.get()
+    e = errors(d, p, b, po, bo)
+    print("mixed vs oracle, torus 64x32x16, %d steps:" % nsteps, e)
+    for k, v in e.items():
+        assert v <= bar[k], (k, v, e)
+
+
+def test_mixed_keeps_div_b_at_fp64_roundoff():
+    _, d, prim, bf = torus_case(64, 32, 16, seed=1912)
+    p, b, _ = run_gpu(d, prim, bf, 10, precision=1)
+    p64, b64, _ = run_gpu(d, prim, bf, 10, precision=0)
+    dm, d64, d0 = div_b(d, b), div_b(d, b64), div_b(d, bf)
+    print("relative max div B: initial %.3e, FP64 %.3e, mixed %.3e" % (d0, d64, dm))
+    assert dm <= max(4.0 * d64, 1e-14), (dm, d64, d0)
+
+
+def test_disk_fp64_parity_with_oracle():
+    """The tilted-disk state through the FP64 path: the 1e-12 bar of the FP64 parity tests."""
+    _, d, prim, bf = disk_case(56, 24, 48)
+    p, b, used = run_gpu(d, prim, bf, 1, precision=0)
+    og = O.Grid(d)
+    og.set(prim, bf)
+    dto = og.step()
+    assert abs(used[0] - dto) <= 1e-12 * dto, (used[0], dto)
+    po, bo = og.get()
+    e = errors(d, p, b, po, bo)
+    print("FP64 vs oracle, tilted disk 56x24x48, 1 step:", e)
+    for k, v in e.items():
+        assert v <= 1e-12, (k, v, e)
+
+
+def test_mixed_vs_oracle_disk_small():
+    _, d, prim, bf = disk_case(56, 24, 48)
+    p, b, used = run_gpu(d, prim, bf, 10, precision=1)
+    og = O.Grid(d)
+    og.set(prim, bf)
+    for n in range(10):
+        og.step(used[n])
+    po, bo = og.get()
+    e = errors(d, p, b, po, bo)
+    print("mixed vs oracle, tilted disk 56x24x48, 10 steps:", e)
+    for k, v in e.items():
+        assert v <= BAR_DISK_10[k], (k, v, e)
+
+
+def test_mixed_vs_fp64_disk_100_steps():
+    """Tilted thin disk 448x192x384 (h/r 0.03, tilt 65 deg, toroidal field beta 10, a 0.9375, r 1.2-200,
+    seed 4), 100 steps each at its own CFL dt: relative L1 of the mixed form against the FP64 path."""
+    _, d, prim, bf = disk_case(448, 192, 384)
+    p64, b64, dt64 = run_gpu(d, prim, bf, 100, precision=0)
+    pm, bm, dtm = run_gpu(d, prim, bf, 100, precision=1)
+    e = errors(d, pm, bm, p64, b64)
+    print("mixed vs FP64, tilted disk 448x192x384, 100 steps:", e,
+          "relative difference of the elapsed time:", abs(sum(dtm) - sum(dt64)) / sum(dt64))
+    for k, v in e.items():
+        assert v <= BAR_DISK_100[k], (k, v, e)
+    assert div_b(d, bm) <= max(4.0 * div_b(d, b64), 1e-14)
