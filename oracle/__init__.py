@@ -46,6 +46,8 @@ def _setup(lib):
         "ora_recon_line": [C.c_int, C.c_int, _D, _D, _D],
         "ora_c2p_many": [P, C.c_long, _D, _D, _D, _D, _D, _I, _I, C.c_int],
         "ora_p2u_many": [P, C.c_long, _D, _D, _D, _D],
+        "ora_mlp_features": [P, C.c_long, _D, _D, _D, _D, _D],
+        "ora_mlp_targets": [P, C.c_long, _D, _D, _D, _D],
         "ora_grid_new": [P],
         "ora_grid_free": [C.c_void_p],
         "ora_grid_set": [C.c_void_p, _D, _D],
@@ -182,6 +184,29 @@ def p2u_many(d, pr, x1, x2):
     U = np.zeros((n, 6))
     lib().ora_p2u_many(C.byref(d), n, _p(pr), _p(x1), _p(x2), _p(U))
     return U
+
+
+def mlp_features(d, U, B, x1, x2):
+    """(n, 6) conserved, (n, 3) centre B, positions -> (n, 10) network inputs (FP64)."""
+    n = U.shape[0]
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    x1 = np.ascontiguousarray(x1, dtype=np.float64)
+    x2 = np.ascontiguousarray(x2, dtype=np.float64)
+    f = np.zeros((n, 10))
+    lib().ora_mlp_features(C.byref(d), n, _p(U), _p(B), _p(x1), _p(x2), _p(f))
+    return f
+
+
+def mlp_targets(d, pr, x1, x2):
+    """(n, 8) primitives, positions -> (n, 2) targets ln(W/D), ln Gamma^2 (FP64)."""
+    n = pr.shape[0]
+    pr = np.ascontiguousarray(pr, dtype=np.float64)
+    x1 = np.ascontiguousarray(x1, dtype=np.float64)
+    x2 = np.ascontiguousarray(x2, dtype=np.float64)
+    y = np.zeros((n, 2))
+    lib().ora_mlp_targets(C.byref(d), n, _p(pr), _p(x1), _p(x2), _p(y))
+    return y
 
 
 class Grid:

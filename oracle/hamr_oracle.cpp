@@ -1150,6 +1150,91 @@ void ora_p2u_many(const ora_desc* d, long n, const double* pr8, const double* x1
     }
 }
 
+/* ================================================================== */
+/* Inputs and targets of the learned inversion guess.
+ *
+ * The network maps a conserved state (with its metric) to an initial guess
+ * for the Newton inversion of Sec. 2.6. Its ten inputs are the scalars the
+ * inversion works with, made dimensionless with D where they carry the
+ * density scale (rho -> lambda rho, u -> lambda u, B -> sqrt(lambda) B
+ * leaves W / D and v^2 unchanged), plus four metric invariants:
+ *   f0 = ln D
+ *   f1 = ln((-Q.n - D) / D)              energy beyond rest mass, per D
+ *   f2 = ln(Qt^2 / D^2 + 1e-30)
+ *   f3 = (Q.B)^2 / (Qt^2 B^2 + 1e-300)   cos^2 of the angle of Qt and B
+ *   f4 = ln(U_kappa / U_rho) + (gam - 1) ln D = ln(kappa D^(gam - 1))
+ *   f5 = ln(B^2 / D + 1e-30)
+ *   f6 = alpha
+ *   f7 = ln(beta_i beta^i + 1e-30),  beta^i = alpha^2 g^{ti}
+ *   f8 = ln sqrt(gamma) = ln(sqrt(-g) / alpha)
+ *   f9 = x1 (= ln r in Kerr-Schild)
+ * (f1 is floored at ln 1e-30.) Targets: y0 = ln(W / D) = ln(h Gamma),
+ * h = 1 + gam u / rho, and y1 = ln Gamma^2 = ln(1 + g_ij utilde^i utilde^j),
+ * from which the guess is W = D e^y0, v^2 = 1 - e^-y1.
+ * Reading: the paper has no learned guess; these definitions are this
+ * project's. */
+void ora_mlp_features(const ora_desc* d, long n, const double* U6, const double* Bc3, const double* x1,
+                      const double* x2, double* f10) {
+    for (long s = 0; s < n; s++) {
+        Geom G;
+        geom_point(*d, x1[s], x2[s], G);
+        const double* U = U6 + s * NCONS;
+        const double* Bc = Bc3 + s * 3;
+        const double alpha = tod(G.alpha), gdet = tod(G.gdet);
+        const double D = U[CRHO] * alpha / gdet;
+        double Qcov[4] = {alpha * (U[CEN] - U[CRHO]) / gdet, alpha * U[CS1] / gdet, alpha * U[CS2] / gdet,
+                          alpha * U[CS3] / gdet};
+        double Qcon[4];
+        for (int m = 0; m < 4; m++) {
+            double t = 0.0;
+            for (int k = 0; k < 4; k++) t += tod(G.gcon[m][k]) * Qcov[k];
+            Qcon[m] = t;
+        }
+        const double Qdotn = -alpha * Qcon[0];
+        double Qsq = 0.0;
+        for (int m = 0; m < 4; m++) Qsq += Qcov[m] * Qcon[m];
+        const double Qtsq = Qsq + Qdotn * Qdotn;
+        const double Bn[4] = {0.0, alpha * Bc[0], alpha * Bc[1], alpha * Bc[2]};
+        double Bsq = 0.0, QdotB = 0.0;
+        for (int i = 1; i < 4; i++) {
+            QdotB += Qcov[i] * Bn[i];
+            for (int j = 1; j < 4; j++) Bsq += tod(G.gcov[i][j]) * Bn[i] * Bn[j];
+        }
+        double beta[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = 1; i < 4; i++) beta[i] = alpha * alpha * tod(G.gcon[0][i]);
+        double bsq = 0.0;
+        for (int i = 1; i < 4; i++)
+            for (int j = 1; j < 4; j++) bsq += tod(G.gcov[i][j]) * beta[i] * beta[j];
+        double* f = f10 + s * 10;
+        f[0] = std::log(D);
+        f[1] = std::log(std::max(-Qdotn - D, 1e-30 * D) / D);
+        f[2] = std::log(Qtsq / (D * D) + 1e-30);
+        f[3] = QdotB * QdotB / (Qtsq * Bsq + 1e-300);
+        f[4] = std::log(U[CENT] / U[CRHO]) + (d->gam - 1.0) * std::log(D);
+        f[5] = std::log(Bsq / D + 1e-30);
+        f[6] = alpha;
+        f[7] = std::log(bsq + 1e-30);
+        f[8] = std::log(gdet / alpha);
+        f[9] = x1[s];
+    }
+}
+
+void ora_mlp_targets(const ora_desc* d, long n, const double* pr8, const double* x1, const double* x2,
+                     double* y2) {
+    for (long s = 0; s < n; s++) {
+        Geom G;
+        geom_point(*d, x1[s], x2[s], G);
+        const double* pr = pr8 + s * NPR;
+        double qsq = 0.0;
+        for (int i = 1; i < 4; i++)
+            for (int j = 1; j < 4; j++) qsq += tod(G.gcov[i][j]) * pr[U1 + i - 1] * pr[U1 + j - 1];
+        const double gamma = std::sqrt(1.0 + qsq);
+        const double h = 1.0 + d->gam * pr[UU] / pr[RHO];
+        y2[s * 2 + 0] = std::log(h * gamma);
+        y2[s * 2 + 1] = std::log(1.0 + qsq);
+    }
+}
+
 ora_grid* ora_grid_new(const ora_desc* d) {
     ora_grid* g = new ora_grid;
     g->d = *d;

@@ -96,6 +96,14 @@ void ora_amr_fill(ora_amr* m);
 double ora_amr_period(ora_amr* m, double dt_fine);
 void ora_amr_stats(const ora_amr* m, long long* counts4);
 
+/* learned inversion guess: the ten inputs of n conserved states (U6 and Bc3
+ * as in ora_c2p_many; f10 is n x 10) and the two targets of n primitive
+ * states (pr8 n x 8; y2 is n x 2), defined in hamr_oracle.cpp */
+void ora_mlp_features(const ora_desc* d, long n, const double* U6, const double* Bc3, const double* x1,
+                      const double* x2, double* f10);
+void ora_mlp_targets(const ora_desc* d, long n, const double* pr8, const double* x1, const double* x2,
+                     double* y2);
+
 /* flop counters (meaningful only in the counting build) */
 void ora_flops_reset(void);
 void ora_flops_get(unsigned long long* out5);
