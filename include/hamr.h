@@ -106,6 +106,7 @@ typedef struct {
 typedef struct {
     long long c2p_ok, c2p_entropy, c2p_fail, floor_hits;
     double dt_used, dt_next;
+    long long newton_iters; /* Newton iterations of the energy inversions (every start tried) */
 } hamr_step_stats;
 
 typedef struct hamr_grid hamr_grid;
@@ -226,12 +227,16 @@ int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, double* bface
 
 /* ---- standalone inversion (Sec. 2.6) ---- */
 #define HAMR_C2P_ENTROPY_ONLY 1u /* skip the energy inversion (tests of the backup) */
+#define HAMR_C2P_MLP 2u          /* start Newton from the learned guess of `mlp` (fallback: the prim guess) */
+
+typedef struct hamr_mlp hamr_mlp;
 
 typedef struct {
-    int metric;      /* HAMR_METRIC_* */
-    double a;        /* spin (KS) */
-    double gam;      /* adiabatic index */
-    uint32_t flags;  /* HAMR_C2P_* */
+    int metric;           /* HAMR_METRIC_* */
+    double a;             /* spin (KS) */
+    double gam;           /* adiabatic index */
+    uint32_t flags;       /* HAMR_C2P_* */
+    const hamr_mlp* mlp;  /* the network of HAMR_C2P_MLP (else ignored; may be NULL) */
 } hamr_c2p_desc;
 
 /* Inverts n conserved states on the device. All arrays are device pointers
@@ -243,6 +248,77 @@ typedef struct {
  * NULL). Asynchronous on `stream`. */
 int hamr_con2prim(const hamr_c2p_desc* d, int64_t n, const double* U, const double* B, const double* x1,
                   const double* x2, double* prim, int32_t* status, int32_t* iters, void* stream);
+
+/* Primitive to conserved (Sec. 2.3-2.4) for n states on the device, SoA:
+ * prim[8][n] (centre B in slots 5..7), x1[n], x2[n] positions, out U[6][n]
+ * = sqrt(-g) (rho u^t, T^t_t + rho u^t, T^t_i, kappa rho u^t) as taken by
+ * hamr_con2prim. Generates training pairs for the learned guess.
+ * Asynchronous on `stream`. */
+int hamr_prim2cons(const hamr_c2p_desc* d, int64_t n, const double* prim, const double* x1, const double* x2,
+                   double* U, void* stream);
+
+/* ---- learned starting point of the inversion ----
+ * The paper has no counterpart: its inversion starts Newton from the
+ * previous primitives (Sec. 2.6). Here a 10 -> 64 -> 64 -> 64 -> 2 tanh
+ * network maps ten inputs of a conserved state to a guess of (W, v^2);
+ * Newton always refines it and the start from the previous primitives is
+ * the fallback, so the network changes iteration counts, never the
+ * accepted solution's tolerance. Inputs (float, SoA feat[10][n]):
+ *   f0 ln D; f1 ln((-Q.n - D)/D); f2 ln(Qt^2/D^2 + 1e-30);
+ *   f3 (Q.B)^2/(Qt^2 B^2) (0 if either is 0); f4 ln(U_kappa/U_rho) + (gam-1) f0;
+ *   f5 ln(B^2/D + 1e-30); f6 alpha; f7 ln(beta_i beta^i + 1e-30),
+ *   beta^i = alpha^2 g^{ti}; f8 ln(sqrt(-g)/alpha); f9 x1,
+ * with D, Q, Qt^2, B^2, Q.B the normal-frame scalars of the inversion.
+ * Targets (targ[2][n]): ln(W/D) = ln(h Gamma) and ln Gamma^2.
+ * Parameters: one float vector of 9154 values, W1 (64 x 10, row = output
+ * unit), b1, W2 (64 x 64), b2, W3, b3, W4 (2 x 64), b4; standardisation:
+ * 24 floats fmean[10], fstd[10], ymean[2], ystd[2] (inputs and targets are
+ * standardised inside the network). Training runs on the device in FP32
+ * (mean squared error of the standardised outputs, Adam); inference uses
+ * bfloat16 weights and activations with FP32 accumulation on the tensor
+ * cores (tcgen05), biases and tanh in FP32.
+ * A model lives on the device that was current at hamr_mlp_create. */
+
+/* Glorot-uniform weights from `seed`, zero biases, identity standardisation. */
+int hamr_mlp_create(hamr_mlp** out, uint64_t seed);
+int hamr_mlp_destroy(hamr_mlp* m);
+/* host arrays params[9154], norm[24]; either may be NULL (not copied) */
+int hamr_mlp_get_params(const hamr_mlp* m, float* params, float* norm);
+int hamr_mlp_set_params(hamr_mlp* m, const float* params, const float* norm);
+/* device arrays: inputs of n conserved states (U, B, x1, x2 as hamr_con2prim)
+ * into feat[10][n]; with prim[8][n] (else NULL) also the targets into targ[2][n]. */
+int hamr_mlp_features(const hamr_c2p_desc* d, int64_t n, const double* U, const double* B, const double* x1,
+                      const double* x2, const double* prim, float* feat, float* targ, void* stream);
+/* sets the standardisation to the mean and standard deviation of n samples
+ * (device feat[10][n], targ[2][n]); synchronises */
+int hamr_mlp_fit_norm(hamr_mlp* m, int64_t n, const float* feat, const float* targ, void* stream);
+
+typedef struct {
+    int64_t steps;   /* optimiser steps */
+    int32_t batch;   /* samples per step, a multiple of 128 */
+    float lr;        /* Adam step size at the start ... */
+    float lr_final;  /* ... decayed to this by a cosine schedule */
+    uint64_t seed;   /* batch sampling (uniform with replacement) */
+} hamr_mlp_train_args;
+
+/* Trains on n samples (device feat[10][n], targ[2][n]); loss (host, may be
+ * NULL) receives the mean training loss of every step. Synchronises. */
+int hamr_mlp_train(hamr_mlp* m, int64_t n, const float* feat, const float* targ, const hamr_mlp_train_args* a,
+                   float* loss, void* stream);
+/* Loss over all n samples and its gradient (host grad[9154], loss[1]) by the
+ * training kernels, without a step. Synchronises. */
+int hamr_mlp_loss_grad(hamr_mlp* m, int64_t n, const float* feat, const float* targ, float* grad, float* loss,
+                       void* stream);
+/* Outputs out[2][n] (target units) of n samples: tensor_cores = 1 the bf16
+ * inference path, 0 the FP32 training path. Asynchronous. */
+int hamr_mlp_forward(const hamr_mlp* m, int64_t n, const float* feat, float* out, int tensor_cores, void* stream);
+/* 1 if a CTA of an inference gave up waiting on the tensor cores or the
+ * copy of the weights since the last call (its cells used the plain start),
+ * else 0; clears the flag. Synchronises. */
+int hamr_mlp_error_flag(hamr_mlp* m, int* flag);
+/* Attaches a network to a grid: its inversions start from the learned
+ * guess (NULL detaches). The model must outlive its use by the grid. */
+int hamr_grid_set_mlp(hamr_grid* g, const hamr_mlp* m);
 
 /* Message of the last error in the calling thread ("" if none). */
 const char* hamr_last_error(void);

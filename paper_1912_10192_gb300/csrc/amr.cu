@@ -400,7 +400,7 @@ __global__ void k_period_begin(const DevBlock* tab, int nb) {
     const int b = (int)((long)blockIdx.x * blockDim.x + threadIdx.x);
     if (b >= nb) return;
     tab[b].dmax[0] = 0ull;
-    for (int q = 0; q < 4; q++) tab[b].dcnt[q] = 0ull;
+    for (int q = 0; q < 5; q++) tab[b].dcnt[q] = 0ull;
 }
 
 __global__ void k_period_dt(const DevBlock* tab, int nb, double cour, double* dtf_out) {
@@ -1168,6 +1168,15 @@ int amr_period(AmrImpl* M, cudaStream_t s, int nperiods, bool use_graph) {
         AM_TRY(cudaGraphInstantiate(&M->exec, g, 0));
     }
     for (int p = 0; p < nperiods; p++) AM_TRY(cudaGraphLaunch(M->exec, s));
+    return HAMR_OK;
+}
+
+int amr_set_phys(AmrImpl* M, const PhysArgs& ph) {
+    M->ph = ph;  // the captured period bakes the launch arguments: capture again
+    if (M->exec) cudaGraphExecDestroy(M->exec);
+    if (M->graph) cudaGraphDestroy(M->graph);
+    M->exec = nullptr;
+    M->graph = nullptr;
     return HAMR_OK;
 }
 

@@ -203,6 +203,7 @@ int alloc_block(hamr_grid* g, int b) {
     v.idx1 = 1.0 / B.dx1;
     v.idx2 = 1.0 / B.dx2;
     v.idx3 = 1.0 / B.dx3;
+    v.x1min = B.x1min;
     for (int f = 0; f < 6; f++) v.bc[f] = B.bc[f];
 
     // every field and table is padded to a whole number of 256-byte lines
@@ -321,6 +322,8 @@ int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out) {
     g->ph.riemann = d->riemann;
     g->ph.floors = d->floors;
     g->ph.mixed = (d->precision == HAMR_PREC_MIXED);
+    g->ph.mlp_img = nullptr;
+    g->ph.mlp_err = nullptr;
     cudaGetDevice(&g->device);
     for (int b = 0; b < d->nblocks; b++) {
         rc = alloc_block(g, b);
@@ -498,7 +501,7 @@ int hamr_grid_stats(const hamr_grid* g, hamr_step_stats* stats) {
     std::memset(stats, 0, sizeof(*stats));
     for (size_t b = 0; b < g->st.size(); b++) {
         if (!g->loaded[b]) continue;
-        unsigned long long cnt[4], mx;
+        unsigned long long cnt[5], mx;
         double dt;
         CUDA_TRY(cudaMemcpy(cnt, g->st[b].dcnt, sizeof(cnt), cudaMemcpyDeviceToHost));
         CUDA_TRY(cudaMemcpy(&mx, g->st[b].dmax, sizeof(mx), cudaMemcpyDeviceToHost));
@@ -507,6 +510,7 @@ int hamr_grid_stats(const hamr_grid* g, hamr_step_stats* stats) {
         stats->c2p_entropy += (long long)cnt[1];
         stats->c2p_fail += (long long)cnt[2];
         stats->floor_hits += (long long)cnt[3];
+        stats->newton_iters += (long long)cnt[4];
         double rate;
         std::memcpy(&rate, &mx, sizeof(rate));
         const double dn = g->ph.cour / rate;
@@ -533,8 +537,23 @@ int hamr_con2prim(const hamr_c2p_desc* d, int64_t n, const double* U, const doub
     if (d->metric != HAMR_METRIC_KS && d->metric != HAMR_METRIC_MINKOWSKI)
         return fail(HAMR_EINVAL, "unknown metric %d", d->metric);
     if (!(d->gam > 1.0 && d->gam <= 2.0)) return fail(HAMR_EINVAL, "gam must be in (1, 2]");
-    if (d->flags & ~HAMR_C2P_ENTROPY_ONLY) return fail(HAMR_EINVAL, "unknown flags 0x%x", d->flags);
+    if (d->flags & ~(HAMR_C2P_ENTROPY_ONLY | HAMR_C2P_MLP)) return fail(HAMR_EINVAL, "unknown flags 0x%x", d->flags);
+    if ((d->flags & HAMR_C2P_MLP) && !d->mlp) return fail(HAMR_EINVAL, "HAMR_C2P_MLP without a network");
     CUDA_TRY(launch_con2prim(*d, n, U, B, x1, x2, prim, status, iters, S(stream)));
+    return HAMR_OK;
+}
+
+int hamr_grid_set_mlp(hamr_grid* g, const hamr_mlp* m) {
+    if (!g) return fail(HAMR_EINVAL, "grid is NULL");
+    if (m) {
+        int dev = -1;
+        cudaGetDevice(&dev);
+        if (dev != g->device) return fail(HAMR_EINVAL, "grid lives on device %d, device %d is current", g->device, dev);
+    }
+    CUDA_TRY(cudaDeviceSynchronize());  // no step in flight reads the old arguments
+    g->ph.mlp_img = mlp_image(m);
+    g->ph.mlp_err = mlp_error_ptr(m);
+    if (g->amr) return amr_set_phys(g->amr, g->ph);
     return HAMR_OK;
 }
 

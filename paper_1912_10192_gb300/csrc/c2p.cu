@@ -3,31 +3,60 @@
 #include "c2p.cuh"
 #include "hamr_internal.h"
 #include "metric.cuh"
+#include "mlp.cuh"
 
 namespace hamr {
 namespace {
 
-__global__ void k_con2prim(hamr_c2p_desc d, int64_t n, const double* __restrict__ U, const double* __restrict__ B,
-                           const double* __restrict__ x1, const double* __restrict__ x2, double* __restrict__ prim,
-                           int32_t* __restrict__ status, int32_t* __restrict__ iters) {
+template <bool MLP>
+__global__ void __launch_bounds__(128) k_con2prim(hamr_c2p_desc d, const uint8_t* __restrict__ img, int* err,
+                                                  int64_t n, const double* __restrict__ U,
+                                                  const double* __restrict__ B, const double* __restrict__ x1,
+                                                  const double* __restrict__ x2, double* __restrict__ prim,
+                                                  int32_t* __restrict__ status, int32_t* __restrict__ iters) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    FullMetric M;
-    metric_at(d.metric, d.a, x1[s], x2[s], M);
+    const bool active = s < n;
+    if (!MLP && !active) return;
     Metric<double> m;
-    to_sparse(M, m);
     double u[NCONS], bc[3], pr[NPRIM];
+    if (active) {
+        FullMetric M;
+        metric_at(d.metric, d.a, x1[s], x2[s], M);
+        to_sparse(M, m);
 #pragma unroll
-    for (int q = 0; q < NCONS; q++) u[q] = U[q * n + s];
+        for (int q = 0; q < NCONS; q++) u[q] = U[q * n + s];
 #pragma unroll
-    for (int q = 0; q < 3; q++) bc[q] = B[q * n + s];
+        for (int q = 0; q < 3; q++) bc[q] = B[q * n + s];
 #pragma unroll
-    for (int q = 0; q < NPRIM; q++) pr[q] = prim[q * n + s];
-    pr[B1] = bc[0];
-    pr[B2] = bc[1];
-    pr[B3] = bc[2];
+        for (int q = 0; q < NPRIM; q++) pr[q] = prim[q * n + s];
+        pr[B1] = bc[0];
+        pr[B2] = bc[1];
+        pr[B3] = bc[2];
+    }
+    double g2[2];
+    bool use_g2 = false;
+    if (MLP) {  // the 128 states of the CTA through the network (mlp.cuh)
+        extern __shared__ __align__(16) uint8_t mlp_smem[];
+        MlpCta C;
+        mlp_begin(C, mlp_smem, img);
+        float f[MLP_NIN], y[MLP_NOUT];
+        C2PScalars S;
+        S.D = 1.0;
+        if (active) {
+            c2p_scalars(u, bc, m, S);
+            mlp_features(S, u[C_RHO], u[C_ENT], m, x1[s], d.gam, f);
+        }
+        const bool ran = mlp_infer(C, f, active, y);
+        mlp_end(C);
+        if (!C.ok && threadIdx.x == 0 && err) atomicExch(err, 1);
+        if (active && ran) {
+            mlp_guess(S.D, y, g2);
+            use_g2 = true;
+        }
+    }
+    if (!active) return;
     int it = 0;
-    const int st = invert(u, bc, m, d.gam, pr, &it, (d.flags & HAMR_C2P_ENTROPY_ONLY) != 0);
+    const int st = invert(u, bc, m, d.gam, pr, &it, (d.flags & HAMR_C2P_ENTROPY_ONLY) != 0, use_g2 ? g2 : nullptr);
 #pragma unroll
     for (int q = 0; q < NPRIM; q++) prim[q * n + s] = pr[q];
     status[s] = st;
@@ -40,7 +69,12 @@ cudaError_t launch_con2prim(const hamr_c2p_desc& d, int64_t n, const double* U, 
                             const double* x2, double* prim, int32_t* status, int32_t* iters, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int bs = 128;
-    k_con2prim<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(d, n, U, B, x1, x2, prim, status, iters);
+    const unsigned nb = (unsigned)((n + bs - 1) / bs);
+    if ((d.flags & HAMR_C2P_MLP) && d.mlp)
+        k_con2prim<true><<<nb, bs, MLP_SMEM_BYTES, s>>>(d, mlp_image(d.mlp), mlp_error_ptr(d.mlp), n, U, B, x1, x2,
+                                                        prim, status, iters);
+    else
+        k_con2prim<false><<<nb, bs, 0, s>>>(d, nullptr, nullptr, n, U, B, x1, x2, prim, status, iters);
     return cudaGetLastError();
 }
 

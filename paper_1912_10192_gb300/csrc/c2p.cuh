@@ -22,80 +22,127 @@ constexpr double C2P_VSQMAX = 1.0 - 1.0 / (50.0 * 50.0);
 
 enum { INV_OK = 0, INV_ENTROPY = 1, INV_FAIL = 2 };
 
+// The normal-frame scalars of a conserved state (Sec. 2.6, Noble et al. 2006).
+struct C2PScalars {
+    double D, Qdotn, Qtsq, Bsq, QdotB, QB2;
+    double Qc1, Qc2, Qc3, Bn1, Bn2, Bn3;
+};
+
 // U: sqrt(-g) (rho u^t, T^t_t + rho u^t, T^t_i, kappa rho u^t); Bc: centre B^i.
-// pr: in the guess (slots 0..4), out the result (slots 0..4) unless INV_FAIL.
-__device__ __forceinline__ int invert(const double U[NCONS], const double Bc[3], const Metric<double>& m, double gam,
-                                      double pr[NPRIM], int* iters, bool entropy_only) {
-    const double gfac = (gam - 1.0) / gam;
+__device__ __forceinline__ void c2p_scalars(const double U[NCONS], const double Bc[3], const Metric<double>& m,
+                                            C2PScalars& S) {
     const double al = m.alpha;
     const double ig = 1.0 / m.gdet;
-    const double D = U[C_RHO] * al * ig;
+    S.D = U[C_RHO] * al * ig;
     // Q_mu = alpha T^t_mu, raised with the sparse inverse metric
     const double Q0 = al * (U[C_EN] - U[C_RHO]) * ig;
     const double Q1 = al * U[C_S1] * ig;
     const double Q2 = al * U[C_S2] * ig;
     const double Q3 = al * U[C_S3] * ig;
     const double Qc0 = m.c00 * Q0 + m.c01 * Q1;
-    const double Qc1 = m.c01 * Q0 + m.c11 * Q1 + m.c13 * Q3;
-    const double Qc2 = m.c22 * Q2;
-    const double Qc3 = m.c13 * Q1 + m.c33 * Q3;
-    const double Bn1 = al * Bc[0], Bn2 = al * Bc[1], Bn3 = al * Bc[2];
-    const double Qdotn = -al * Qc0;
-    const double Qtsq = Q0 * Qc0 + Q1 * Qc1 + Q2 * Qc2 + Q3 * Qc3 + Qdotn * Qdotn;
-    const double Bsq = m.g11 * Bn1 * Bn1 + m.g22 * Bn2 * Bn2 + m.g33 * Bn3 * Bn3 + 2.0 * m.g13 * Bn1 * Bn3;
-    const double QdotB = Q1 * Bn1 + Q2 * Bn2 + Q3 * Bn3;
-    const double QB2 = QdotB * QdotB;
+    S.Qc1 = m.c01 * Q0 + m.c11 * Q1 + m.c13 * Q3;
+    S.Qc2 = m.c22 * Q2;
+    S.Qc3 = m.c13 * Q1 + m.c33 * Q3;
+    S.Bn1 = al * Bc[0];
+    S.Bn2 = al * Bc[1];
+    S.Bn3 = al * Bc[2];
+    S.Qdotn = -al * Qc0;
+    S.Qtsq = Q0 * Qc0 + Q1 * S.Qc1 + Q2 * S.Qc2 + Q3 * S.Qc3 + S.Qdotn * S.Qdotn;
+    S.Bsq = m.g11 * S.Bn1 * S.Bn1 + m.g22 * S.Bn2 * S.Bn2 + m.g33 * S.Bn3 * S.Bn3 + 2.0 * m.g13 * S.Bn1 * S.Bn3;
+    S.QdotB = Q1 * S.Bn1 + Q2 * S.Bn2 + Q3 * S.Bn3;
+    S.QB2 = S.QdotB * S.QdotB;
+}
 
-    // guess
+// 2-D Newton on (W, v^2) from the given start; true when it met the
+// stopping rule. `it` returns the iterations taken.
+__device__ __forceinline__ bool newton_wv(const C2PScalars& S, double gfac, double& W, double& vsq, int& it) {
+    const double D = S.D, Bsq = S.Bsq, QB2 = S.QB2, Qdotn = S.Qdotn, Qtsq = S.Qtsq;
+    bool ok = false;
+    for (it = 1; it <= C2P_NMAX; it++) {
+        const double omv = 1.0 - vsq;
+        const double rs = rsqrt(omv);
+        const double sq = omv * rs;
+        const double iW = 1.0 / W;
+        const double iW2 = iW * iW;
+        const double BW = Bsq + W;
+        const double p = gfac * (W * omv - D * sq);
+        const double f1 = -0.5 * Bsq * (1.0 + vsq) + 0.5 * QB2 * iW2 - W + p - Qdotn;
+        const double f2 = vsq * BW * BW - QB2 * (Bsq + 2.0 * W) * iW2 - Qtsq;
+        const double j11 = -QB2 * iW2 * iW - 1.0 + gfac * omv;
+        const double j12 = -0.5 * Bsq + gfac * (0.5 * D * rs - W);
+        const double j21 = 2.0 * BW * (vsq + QB2 * iW2 * iW);
+        const double j22 = BW * BW;
+        const double idet = 1.0 / (j11 * j22 - j12 * j21);
+        const double dW = (j12 * f2 - j22 * f1) * idet;
+        const double dv = (j21 * f1 - j11 * f2) * idet;
+        const double Wn = W + dW;
+        const double vn = fmin(fmax(vsq + dv, 0.0), C2P_VSQMAX);
+        if (!(Wn > 0.0)) break;
+        const double err = fabs(Wn - W) + fabs(vn - vsq) * Wn;
+        W = Wn;
+        vsq = vn;
+        if (err < C2P_TOL * Wn) {
+            ok = true;
+            break;
+        }
+    }
+    if (it > C2P_NMAX) it = C2P_NMAX;
+    return ok;
+}
+
+// rho and u_g of a converged (W, v^2); false unless both are positive
+__device__ __forceinline__ bool energy_result(const C2PScalars& S, double gam, double W, double vsq, double& rho,
+                                              double& u) {
+    const double gfac = (gam - 1.0) / gam;
+    const double omv = 1.0 - vsq;
+    const double sq = sqrt(omv);
+    rho = S.D * sq;
+    u = gfac * (W * omv - S.D * sq) / (gam - 1.0);
+    return (rho > 0.0) && (u > 0.0);
+}
+
+// pr: in the guess (slots 0..4), out the result (slots 0..4) unless INV_FAIL.
+// guess2 (optional): a first start (W, v^2) tried before the one of pr; the
+// start from pr is then the fallback. `iters` counts the energy-inversion
+// Newton iterations of every start tried.
+__device__ __forceinline__ int invert(const double U[NCONS], const double Bc[3], const Metric<double>& m, double gam,
+                                      double pr[NPRIM], int* iters, bool entropy_only,
+                                      const double* guess2 = nullptr) {
+    C2PScalars S;
+    c2p_scalars(U, Bc, m, S);
+    const double gfac = (gam - 1.0) / gam;
+    const double D = S.D, Bsq = S.Bsq, QB2 = S.QB2, Qtsq = S.Qtsq;
+
+    // start from the guess primitives
     const double q1 = pr[U1], q2 = pr[U2], q3 = pr[U3];
     const double qsq = m.g11 * q1 * q1 + m.g22 * q2 * q2 + m.g33 * q3 * q3 + 2.0 * m.g13 * q1 * q3;
     const double gsq = 1.0 + qsq;
-    double vsq = fmin(qsq / gsq, C2P_VSQMAX);
-    double W = (pr[RHO] + gam * pr[UU]) * gsq;
-    const double W0 = W;
+    const double W0 = (pr[RHO] + gam * pr[UU]) * gsq;
+    double W = W0, vsq = 0.0;
 
     bool ok = false;
-    int it = 0;
+    int itsum = 0;
+    double rho = 0.0, u = 0.0;
     if (!entropy_only) {
-        for (it = 1; it <= C2P_NMAX; it++) {
-            const double omv = 1.0 - vsq;
-            const double rs = rsqrt(omv);
-            const double sq = omv * rs;
-            const double iW = 1.0 / W;
-            const double iW2 = iW * iW;
-            const double BW = Bsq + W;
-            const double p = gfac * (W * omv - D * sq);
-            const double f1 = -0.5 * Bsq * (1.0 + vsq) + 0.5 * QB2 * iW2 - W + p - Qdotn;
-            const double f2 = vsq * BW * BW - QB2 * (Bsq + 2.0 * W) * iW2 - Qtsq;
-            const double j11 = -QB2 * iW2 * iW - 1.0 + gfac * omv;
-            const double j12 = -0.5 * Bsq + gfac * (0.5 * D * rs - W);
-            const double j21 = 2.0 * BW * (vsq + QB2 * iW2 * iW);
-            const double j22 = BW * BW;
-            const double idet = 1.0 / (j11 * j22 - j12 * j21);
-            const double dW = (j12 * f2 - j22 * f1) * idet;
-            const double dv = (j21 * f1 - j11 * f2) * idet;
-            const double Wn = W + dW;
-            const double vn = fmin(fmax(vsq + dv, 0.0), C2P_VSQMAX);
-            if (!(Wn > 0.0)) break;
-            const double err = fabs(Wn - W) + fabs(vn - vsq) * Wn;
-            W = Wn;
-            vsq = vn;
-            if (err < C2P_TOL * Wn) {
-                ok = true;
-                break;
+        int it = 0;
+        if (guess2) {
+            W = guess2[0];
+            vsq = fmin(fmax(guess2[1], 0.0), C2P_VSQMAX);
+            if (W > 0.0) {
+                ok = newton_wv(S, gfac, W, vsq, it);
+                itsum += it;
+                if (ok) ok = energy_result(S, gam, W, vsq, rho, u);
             }
         }
-        if (it > C2P_NMAX) it = C2P_NMAX;
+        if (!ok) {
+            W = W0;
+            vsq = fmin(qsq / gsq, C2P_VSQMAX);
+            ok = newton_wv(S, gfac, W, vsq, it);
+            itsum += it;
+            if (ok) ok = energy_result(S, gam, W, vsq, rho, u);
+        }
     }
-    if (iters) *iters = it;
-    double rho = 0.0, u = 0.0;
-    if (ok) {
-        const double omv = 1.0 - vsq;
-        const double sq = sqrt(omv);
-        rho = D * sq;
-        u = gfac * (W * omv - D * sq) / (gam - 1.0);
-        ok = (rho > 0.0) && (u > 0.0);
-    }
+    if (iters) *iters = itsum;
     int status = INV_OK;
     if (!ok) {
         const double kappa = U[C_ENT] / U[C_RHO];
@@ -145,10 +192,10 @@ __device__ __forceinline__ int invert(const double U[NCONS], const double Bc[3],
     // utilde^i = Gamma/(W + B^2) (Qt^i + (Q.B) Bn^i / W), Qt^i = Q^i - alpha g^{ti} (Q.n)
     const double gamma = rsqrt(1.0 - vsq);
     const double pre = gamma / (W + Bsq);
-    const double qbw = QdotB / W;
-    pr[U1] = pre * (Qc1 - al * m.c01 * Qdotn + qbw * Bn1);
-    pr[U2] = pre * (Qc2 + qbw * Bn2);
-    pr[U3] = pre * (Qc3 + qbw * Bn3);
+    const double qbw = S.QdotB / W;
+    pr[U1] = pre * (S.Qc1 - m.alpha * m.c01 * S.Qdotn + qbw * S.Bn1);
+    pr[U2] = pre * (S.Qc2 + qbw * S.Bn2);
+    pr[U3] = pre * (S.Qc3 + qbw * S.Bn3);
     pr[RHO] = rho;
     pr[UU] = u;
     return status;

@@ -28,6 +28,7 @@ struct BlockView {
     int n1, n2, n3, n1p, n2p, n3p;
     long nc, n2d;
     double dx1, dx2, dx3, idx1, idx2, idx3;
+    double x1min;  // x1 of the block's lower face (the learned inversion guess takes x1)
     int bc[6];
     const double* gc;  // centre tables
     const double* gf1; // x1-face tables
@@ -41,6 +42,8 @@ struct PhysArgs {
     int riemann;
     int floors;
     int mixed;  // 1: reconstruction and face fluxes in FP32 (HAMR_PREC_MIXED)
+    const uint8_t* mlp_img;  // inference image of the learned inversion guess (nullptr: not used)
+    int* mlp_err;            // set to 1 by a CTA whose network waits gave up
 };
 
 // device scratch/state of one block
@@ -136,6 +139,25 @@ cudaError_t launch_reflux_cells(const DevBlock* tab, int n, const int* cblk, con
 
 // amr.cu
 struct AmrImpl;
+
+// the learned inversion guess (mlp.cu): FP32 master parameters, Adam
+// moments, the standardisation and the bf16 inference image, on one device
+}  // namespace hamr
+struct hamr_mlp {
+    float* params = nullptr;  // MLP_NPARAM
+    float* grad = nullptr;
+    float* m1 = nullptr;      // Adam moments
+    float* m2 = nullptr;
+    float* norm = nullptr;    // MLP_NNORM: fmean, fstd, ymean, ystd
+    uint8_t* img = nullptr;   // inference image (MLP_IMG_BYTES)
+    double* sums = nullptr;   // scratch of the standardisation fit
+    float* loss = nullptr;    // per-step loss accumulators of a training call
+    long loss_cap = 0;
+    int* err = nullptr;       // set by a CTA whose network waits gave up
+    long long adam_t = 0;
+    int device = 0;
+};
+namespace hamr {
 int amr_create(AmrImpl** out, const hamr_grid_desc& d, const std::vector<BlockView>& views,
                const std::vector<BlockState>& st, const PhysArgs& ph);
 void amr_destroy(AmrImpl* M);
@@ -144,6 +166,9 @@ int amr_period(AmrImpl* M, cudaStream_t s, int nperiods, bool use_graph);
 int amr_info(const AmrImpl* M, int* lmax, double* dtf_host);
 int amr_links(const AmrImpl* M, int* counts5);
 int amr_fill(AmrImpl* M, cudaStream_t s);
+int amr_set_phys(AmrImpl* M, const PhysArgs& ph);
+const uint8_t* mlp_image(const hamr_mlp* m);
+int* mlp_error_ptr(const hamr_mlp* m);
 
 // c2p.cu
 cudaError_t launch_con2prim(const hamr_c2p_desc& d, int64_t n, const double* U, const double* B, const double* x1,

@@ -102,6 +102,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     v.idx1 = 1.0 / B.dx1;
     v.idx2 = 1.0 / B.dx2;
     v.idx3 = 1.0 / B.dx3;
+    v.x1min = B.x1min;
     for (int f = 0; f < 6; f++) v.bc[f] = B.bc[f];
 
     // carve the array (field stride = the caller's padded cell count)
@@ -147,6 +148,8 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     ph.riemann = d->riemann;
     ph.floors = d->floors;
     ph.mixed = 0;
+    ph.mlp_img = nullptr;
+    ph.mlp_err = nullptr;
 
     // the array keeps the previous call's contents: clear what must start at zero
     NA_TRY(cudaMemsetAsync(s.Ph, 0, sizeof(double) * 11 * v.nc, cs));

@@ -11,6 +11,7 @@
 
 #include "c2p.cuh"
 #include "grmhd.cuh"
+#include "mlp.cuh"
 
 #include "hamr_internal.h"
 
@@ -355,6 +356,9 @@ __device__ __forceinline__ double inv_dt_cell(const BlockView& v, const double p
 // ---------------------------------------------------------------- cell update
 // U = U(P^n) + dts (Q(Pf) - div F); inversion with guess Pf; floors;
 // the corrector also reduces the CFL rate of the new state.
+// MLP: the CTA's 128 cells first run the learned guess (mlp.cuh) on the
+// tensor cores; Newton starts from it, with the start from Pf as fallback.
+template <bool MLP>
 __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int corrector, const double* Pb,
                                                const double* __restrict__ Pf, const double* __restrict__ F1,
                                                const double* __restrict__ F2, const double* __restrict__ F3,
@@ -364,17 +368,26 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
     const long n = (long)v.n1 * v.n2 * v.n3;
     const bool active = t < n;
     double inv = 0.0;
-    int st = -1, fl = 0;
+    int st = -1, fl = 0, its = 0;
+    const double gam = ph.gam;
+    Metric<double> m;
+    double U[NCONS], Bc[3], pr[NPRIM];
+    long c = 0, g = 0;
+    int i = 0, j = 0;
+    MlpCta C;
+    if (MLP) {
+        extern __shared__ __align__(16) uint8_t mlp_smem[];
+        mlp_begin(C, mlp_smem, ph.mlp_img);  // the weight image streams in while U is formed
+    }
     if (active) {
-        const int i = (int)(t % v.n1), j = (int)((t / v.n1) % v.n2), k = (int)(t / ((long)v.n1 * v.n2));
-        const long c = cidx(v, i, j, k);
-        const long g = gidx(v, i, j);
+        i = (int)(t % v.n1);
+        j = (int)((t / v.n1) % v.n2);
+        const int k = (int)(t / ((long)v.n1 * v.n2));
+        c = cidx(v, i, j, k);
+        g = gidx(v, i, j);
         const long nc = v.nc;
-        const double gam = ph.gam;
-        Metric<double> m;
         load_metric(v.gc, v.n2d, g, m);
         // U^n
-        double U[NCONS];
         if (!corrector) {
             double pb[NPRIM];
 #pragma unroll
@@ -430,16 +443,35 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
             const double src = (q >= C_EN && q <= C_S3) ? Q[q - C_EN] : 0.0;
             U[q] = U[q] + dts * (src - div);
         }
-        double Bc[3];
         centre_field(v, Bn, i, j, k, m.gdet, Bc);
-        double pr[NPRIM];
 #pragma unroll
         for (int q = 0; q < NPRIM; q++) pr[q] = pf[q];
         pr[B1] = Bc[0];
         pr[B2] = Bc[1];
         pr[B3] = Bc[2];
-        int its;
-        st = invert(U, Bc, m, gam, pr, &its, false);
+    }
+    double g2[2];
+    bool use_g2 = false;
+    if (MLP) {
+        float f[MLP_NIN], y[MLP_NOUT];
+        C2PScalars S;
+        S.D = 1.0;
+        if (active) {
+            c2p_scalars(U, Bc, m, S);
+            mlp_features(S, U[C_RHO], U[C_ENT], m, v.x1min + (i + 0.5) * v.dx1, gam, f);
+        }
+        if (__syncthreads_or(active)) {
+            const bool ran = mlp_infer(C, f, active, y);
+            if (active && ran) {
+                mlp_guess(S.D, y, g2);
+                use_g2 = true;
+            }
+        }
+        mlp_end(C);
+        if (!C.ok && threadIdx.x == 0 && ph.mlp_err) atomicExch(ph.mlp_err, 1);
+    }
+    if (active) {
+        st = invert(U, Bc, m, gam, pr, &its, false, use_g2 ? g2 : nullptr);
         uint8_t sb = (st == INV_ENTROPY) ? ST_ENTROPY : ((st == INV_FAIL) ? ST_FAIL : 0);
         if (ph.floors) {
             Fluid<double> s;
@@ -457,7 +489,7 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
             if (fl) sb |= ST_FLOOR;
         }
 #pragma unroll
-        for (int q = 0; q < NPRIM; q++) Po[q * nc + c] = pr[q];
+        for (int q = 0; q < NPRIM; q++) Po[q * v.nc + c] = pr[q];
         status[c] |= sb;
         if (corrector == 1) inv = inv_dt_cell(v, pr, m, gam);
     }
@@ -467,23 +499,27 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
     const unsigned long long c_en = warp_sum((unsigned long long)(st == INV_ENTROPY));
     const unsigned long long c_fa = warp_sum((unsigned long long)(st == INV_FAIL));
     const unsigned long long c_fl = warp_sum((unsigned long long)fl);
+    const unsigned long long c_it = warp_sum((unsigned long long)(active ? its : 0));
     const double wmax = warp_max(inv);
     if (lane == 0) {
         if (c_ok) atomicAdd(&dcnt[0], c_ok);
         if (c_en) atomicAdd(&dcnt[1], c_en);
         if (c_fa) atomicAdd(&dcnt[2], c_fa);
         if (c_fl) atomicAdd(&dcnt[3], c_fl);
+        if (c_it) atomicAdd(&dcnt[4], c_it);
         if (corrector == 1 && wmax > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(wmax));
     }
 }
 
+template <bool MLP>
 __global__ void __launch_bounds__(BS) k_update(BlockView v, PhysArgs ph, int corrector, const double* Pb,
                                                const double* __restrict__ Pf, const double* __restrict__ F1,
                                                const double* __restrict__ F2, const double* __restrict__ F3,
                                                const double* __restrict__ Bn, double* Un, double* Po,
                                                uint8_t* __restrict__ status, const double* __restrict__ dscal,
                                                double fac, unsigned long long* dmax, unsigned long long* dcnt) {
-    b_update(v, ph, corrector, Pb, Pf, F1, F2, F3, Bn, Un, Po, status, dscal, fac, dmax, dcnt, (long)blockIdx.x * blockDim.x + threadIdx.x);
+    b_update<MLP>(v, ph, corrector, Pb, Pf, F1, F2, F3, Bn, Un, Po, status, dscal, fac, dmax, dcnt,
+                  (long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 
@@ -517,7 +553,7 @@ __global__ void k_dt_select(double cour, double user_dt, double* dscal, unsigned
     const double mx = __longlong_as_double((long long)dmax[0]);
     dscal[0] = (user_dt > 0.0) ? user_dt : cour / mx;
     dmax[0] = 0ull;
-    dcnt[0] = dcnt[1] = dcnt[2] = dcnt[3] = 0ull;
+    dcnt[0] = dcnt[1] = dcnt[2] = dcnt[3] = dcnt[4] = 0ull;
 }
 
 // ---------------------------------------------------------------- batched (multi-block) wrappers
@@ -554,14 +590,15 @@ __global__ void kb_ct(const DevBlock* tab, const int* list, int sigma) {
         b_ct(D.v, D.E, D.B, D.B, D.dscal + 1, 1.0, tidx());
 }
 
+template <bool MLP>
 __global__ void __launch_bounds__(BS) kb_update(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
     const DevBlock& D = tab[list[blockIdx.y]];
     if (sigma == 0)
-        b_update(D.v, ph, 0, D.P, D.P, D.F1, D.F2, D.F3, D.Bh, D.Un, D.Ph, D.status, D.dscal, 0.5, D.dmax, D.dcnt,
-                 tidx());
+        b_update<MLP>(D.v, ph, 0, D.P, D.P, D.F1, D.F2, D.F3, D.Bh, D.Un, D.Ph, D.status, D.dscal, 0.5, D.dmax,
+                      D.dcnt, tidx());
     else
-        b_update(D.v, ph, 2, D.P, D.Ph, D.F1, D.F2, D.F3, D.B, D.Un, D.P, D.status, D.dscal, 1.0, D.dmax, D.dcnt,
-                 tidx());
+        b_update<MLP>(D.v, ph, 2, D.P, D.Ph, D.F1, D.F2, D.F3, D.B, D.Un, D.P, D.status, D.dscal, 1.0, D.dmax,
+                      D.dcnt, tidx());
 }
 
 __global__ void kb_dt_reduce(const DevBlock* tab, const int* list, PhysArgs ph) {
@@ -725,8 +762,12 @@ cudaError_t launch_update(const BlockView& v, const PhysArgs& ph, int corrector,
                           uint8_t* status, const double* dscal, double dt_factor, unsigned long long* dmax,
                           unsigned long long* dcnt, cudaStream_t s) {
     const long n = (long)v.n1 * v.n2 * v.n3;
-    k_update<<<nblk(n), BS, 0, s>>>(v, ph, corrector, Pbase, Pflux, F[0], F[1], F[2], Bnew, Un, Pout, status, dscal,
-                                    dt_factor, dmax, dcnt);
+    if (ph.mlp_img)
+        k_update<true><<<nblk(n), BS, MLP_SMEM_BYTES, s>>>(v, ph, corrector, Pbase, Pflux, F[0], F[1], F[2], Bnew, Un,
+                                                           Pout, status, dscal, dt_factor, dmax, dcnt);
+    else
+        k_update<false><<<nblk(n), BS, 0, s>>>(v, ph, corrector, Pbase, Pflux, F[0], F[1], F[2], Bnew, Un, Pout,
+                                               status, dscal, dt_factor, dmax, dcnt);
     return cudaGetLastError();
 }
 
@@ -798,7 +839,10 @@ cudaError_t launch_ct_batch(const DevBlock* tab, const int* list, int nlist, lon
 cudaError_t launch_update_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
                                 int sigma, cudaStream_t s) {
     if (nlist <= 0) return cudaSuccess;
-    kb_update<<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
+    if (ph.mlp_img)
+        kb_update<true><<<bgrid(maxwork, nlist), BS, MLP_SMEM_BYTES, s>>>(tab, list, ph, sigma);
+    else
+        kb_update<false><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
     return cudaGetLastError();
 }
 

@@ -21,7 +21,7 @@ RECON_PPM, RECON_MC, RECON_MINMOD = 0, 1, 2
 FLUX_HLL, FLUX_LLF = 0, 1
 BC_OUTFLOW, BC_PERIODIC, BC_POLAR, BC_OUTFLOW_NOINFLOW, BC_BLOCK = 0, 1, 2, 3, 4
 PREC_FP64, PREC_MIXED = 0, 1
-C2P_ENTROPY_ONLY = 1
+C2P_ENTROPY_ONLY, C2P_MLP = 1, 2
 NG = 3
 
 
@@ -44,7 +44,8 @@ class GridDesc(C.Structure):
 
 class StepStats(C.Structure):
     _fields_ = [("c2p_ok", C.c_longlong), ("c2p_entropy", C.c_longlong), ("c2p_fail", C.c_longlong),
-                ("floor_hits", C.c_longlong), ("dt_used", C.c_double), ("dt_next", C.c_double)]
+                ("floor_hits", C.c_longlong), ("dt_used", C.c_double), ("dt_next", C.c_double),
+                ("newton_iters", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -55,7 +56,13 @@ class KernelTime(C.Structure):
 
 
 class C2PDesc(C.Structure):
-    _fields_ = [("metric", C.c_int), ("a", C.c_double), ("gam", C.c_double), ("flags", C.c_uint32)]
+    _fields_ = [("metric", C.c_int), ("a", C.c_double), ("gam", C.c_double), ("flags", C.c_uint32),
+                ("mlp", C.c_void_p)]
+
+
+class MlpTrainArgs(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("batch", C.c_int32), ("lr", C.c_float), ("lr_final", C.c_float),
+                ("seed", C.c_uint64)]
 
 
 _lib = None
@@ -88,6 +95,18 @@ def lib():
         L.hamr_grid_timing.argtypes = [P, C.POINTER(KernelTime), C.c_int, C.POINTER(C.c_int)]
         L.hamr_measure_fp64_peak.argtypes = [P, C.POINTER(C.c_double)]
         L.hamr_block_step_noalloc.argtypes = [C.POINTER(GridDesc), P, P, C.c_double, P]
+        L.hamr_prim2cons.argtypes = [C.POINTER(C2PDesc), C.c_int64, P, P, P, P, P]
+        L.hamr_mlp_create.argtypes = [C.POINTER(C.c_void_p), C.c_uint64]
+        L.hamr_mlp_destroy.argtypes = [P]
+        L.hamr_mlp_get_params.argtypes = [P, P, P]
+        L.hamr_mlp_set_params.argtypes = [P, P, P]
+        L.hamr_mlp_features.argtypes = [C.POINTER(C2PDesc), C.c_int64, P, P, P, P, P, P, P, P]
+        L.hamr_mlp_fit_norm.argtypes = [P, C.c_int64, P, P, P]
+        L.hamr_mlp_train.argtypes = [P, C.c_int64, P, P, C.POINTER(MlpTrainArgs), P, P]
+        L.hamr_mlp_loss_grad.argtypes = [P, C.c_int64, P, P, P, P, P]
+        L.hamr_mlp_forward.argtypes = [P, C.c_int64, P, P, C.c_int, P]
+        L.hamr_mlp_error_flag.argtypes = [P, C.POINTER(C.c_int)]
+        L.hamr_grid_set_mlp.argtypes = [P, P]
         L.hamr_last_error.argtypes = []
         L.hamr_last_error.restype = C.c_char_p
         for name in header_functions():
@@ -211,15 +230,101 @@ class Grid:
         check(lib().hamr_grid_stats(self.h, C.byref(st)))
         return st.as_dict()
 
+    def set_mlp(self, mlp):
+        """Inversions of the grid's steps start from `mlp`'s guess (None: the plain start)."""
+        check(lib().hamr_grid_set_mlp(self.h, mlp.h if mlp is not None else None))
+        self._mlp = mlp
 
-def con2prim(U, B, x1, x2, prim, status, iters=None, metric=METRIC_KS, a=0.9375, gam=13.0 / 9.0, flags=0,
-             stream=None):
-    """Inverts n states in place on the device (SoA torch tensors: U (6, n), B (3, n), prim (8, n))."""
+
+def c2p_desc(metric=METRIC_KS, a=0.9375, gam=13.0 / 9.0, flags=0, mlp=None):
     d = C2PDesc()
     d.metric, d.a, d.gam, d.flags = metric, a, gam, flags
+    d.mlp = mlp.h if mlp is not None else None
+    return d
+
+
+def con2prim(U, B, x1, x2, prim, status, iters=None, metric=METRIC_KS, a=0.9375, gam=13.0 / 9.0, flags=0,
+             stream=None, mlp=None):
+    """Inverts n states in place on the device (SoA torch tensors: U (6, n), B (3, n), prim (8, n)).
+    With `mlp` (an Mlp), Newton starts from the network's guess (flag C2P_MLP)."""
+    d = c2p_desc(metric, a, gam, flags | (C2P_MLP if mlp is not None else 0), mlp)
     n = prim.shape[1]
     check(lib().hamr_con2prim(C.byref(d), n, _ptr(U), _ptr(B), _ptr(x1), _ptr(x2), _ptr(prim), _ptr(status),
                               _ptr(iters), _stream(stream)))
+
+
+def prim2cons(prim, x1, x2, U, metric=METRIC_KS, a=0.9375, gam=13.0 / 9.0, stream=None):
+    """U (6, n) = the conserved variables of prim (8, n) at positions x1, x2 (device tensors)."""
+    d = c2p_desc(metric, a, gam)
+    check(lib().hamr_prim2cons(C.byref(d), prim.shape[1], _ptr(prim), _ptr(x1), _ptr(x2), _ptr(U), _stream(stream)))
+
+
+class Mlp:
+    """The learned inversion guess (hamr_mlp_*): a model on the current device."""
+
+    NPARAM, NNORM = 9154, 24
+
+    def __init__(self, seed=0):
+        h = C.c_void_p()
+        check(lib().hamr_mlp_create(C.byref(h), C.c_uint64(seed)))
+        self.h = h.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hamr_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        p = np.zeros(self.NPARAM, dtype=np.float32)
+        nrm = np.zeros(self.NNORM, dtype=np.float32)
+        check(lib().hamr_mlp_get_params(self.h, p.ctypes.data, nrm.ctypes.data))
+        return p, nrm
+
+    def set_params(self, params=None, norm=None):
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        nrm = None if norm is None else np.ascontiguousarray(norm, dtype=np.float32)
+        check(lib().hamr_mlp_set_params(self.h, None if p is None else p.ctypes.data,
+                                        None if nrm is None else nrm.ctypes.data))
+
+    @staticmethod
+    def features(U, B, x1, x2, feat, prim=None, targ=None, metric=METRIC_KS, a=0.9375, gam=13.0 / 9.0,
+                 stream=None):
+        d = c2p_desc(metric, a, gam)
+        check(lib().hamr_mlp_features(C.byref(d), U.shape[1], _ptr(U), _ptr(B), _ptr(x1), _ptr(x2), _ptr(prim),
+                                      _ptr(feat), _ptr(targ), _stream(stream)))
+
+    def fit_norm(self, feat, targ, stream=None):
+        check(lib().hamr_mlp_fit_norm(self.h, feat.shape[1], _ptr(feat), _ptr(targ), _stream(stream)))
+
+    def train(self, feat, targ, steps, batch=8192, lr=2e-3, lr_final=2e-5, seed=5, stream=None):
+        a = MlpTrainArgs()
+        a.steps, a.batch, a.lr, a.lr_final, a.seed = steps, batch, lr, lr_final, seed
+        loss = np.zeros(steps, dtype=np.float32)
+        check(lib().hamr_mlp_train(self.h, feat.shape[1], _ptr(feat), _ptr(targ), C.byref(a), loss.ctypes.data,
+                                   _stream(stream)))
+        return loss
+
+    def loss_grad(self, feat, targ, stream=None):
+        g = np.zeros(self.NPARAM, dtype=np.float32)
+        L = np.zeros(1, dtype=np.float32)
+        check(lib().hamr_mlp_loss_grad(self.h, feat.shape[1], _ptr(feat), _ptr(targ), g.ctypes.data, L.ctypes.data,
+                                       _stream(stream)))
+        return float(L[0]), g
+
+    def forward(self, feat, out, tensor_cores=True, stream=None):
+        check(lib().hamr_mlp_forward(self.h, feat.shape[1], _ptr(feat), _ptr(out), int(bool(tensor_cores)),
+                                     _stream(stream)))
+
+    def error_flag(self):
+        f = C.c_int()
+        check(lib().hamr_mlp_error_flag(self.h, C.byref(f)))
+        return f.value
 
 
 def measure_fp64_peak(stream=None):

@@ -1,0 +1,280 @@
+"""The learned starting point of the inversion on the GPU, through the C ABI.
+
+* primitive -> conserved (hamr_prim2cons) against the oracle's,
+* the ten inputs and two targets (hamr_mlp_features, FP32 from FP64
+  scalars) against the oracle's FP64 ones,
+* the FP32 training forward pass and the loss gradient of the training
+  kernels against the oracle's FP64 network and backpropagation,
+* the bf16 tensor-core inference (tcgen05) against the oracle's statement of
+  that arithmetic (bf16 operands, exact accumulation),
+* training on 10M oracle pairs (rho log-uniform 1e-6..1, u/rho 1e-4..1e2,
+  Lorentz factor 1..50, sigma 0..100, r 0.9 r_+..100, ten spins drawn from
+  0..0.99; seed 5) lowers the validation loss (1M pairs, seed 6),
+* the gain: inversions started from the network's guess against the plain
+  start, on the validation states (iterations, failures), with the accepted
+  solutions equal, and on grid steps of the torus.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mlp as M
+from paper_1912_10192_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+GAM = 13.0 / 9.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_10192_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+
+
+def _hamr():
+    from paper_1912_10192_gb300 import hamr
+    return hamr
+
+
+def oracle_pairs(n, seed, nspin=10):
+    """(prim (n, 8), x1, x2, U (n, 6), spin per sample) from the oracle, in nspin chunks of one spin each."""
+    spins = 0.99 * W.uniform01(seed + 1000, np.arange(nspin))
+    prims, x1s, x2s, Us, aa = [], [], [], [], []
+    per = n // nspin
+    for k in range(nspin):
+        m = per if k < nspin - 1 else n - per * (nspin - 1)
+        pr, x1, x2 = W.random_states(m, seed=seed * 100 + k, a=float(spins[k]))
+        d = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, metric=O.METRIC_KS, a=float(spins[k]), gam=GAM)
+        prims.append(pr)
+        x1s.append(x1)
+        x2s.append(x2)
+        Us.append(O.p2u_many(d, pr, x1, x2))
+        aa.append(np.full(m, spins[k]))
+    return (np.concatenate(prims), np.concatenate(x1s), np.concatenate(x2s), np.concatenate(Us),
+            np.concatenate(aa))
+
+
+def dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype=dtype).cuda()
+
+
+def gpu_features(prim, x1, x2, U, spins):
+    """feat (10, n), targ (2, n) float32 on the device, chunk by chunk of one spin."""
+    hamr = _hamr()
+    n = len(x1)
+    feat = torch.empty((10, n), dtype=torch.float32, device="cuda")
+    targ = torch.empty((2, n), dtype=torch.float32, device="cuda")
+    edges = np.flatnonzero(np.diff(spins)) + 1
+    for lo, hi in zip(np.r_[0, edges], np.r_[edges, n]):
+        m = hi - lo
+        Ud, Bd = dev(U[lo:hi].T), dev(prim[lo:hi, 5:8].T)
+        pd = dev(prim[lo:hi].T)
+        f = torch.empty((10, m), dtype=torch.float32, device="cuda")
+        t = torch.empty((2, m), dtype=torch.float32, device="cuda")
+        hamr.Mlp.features(Ud, Bd, dev(x1[lo:hi]), dev(x2[lo:hi]), f, prim=pd, targ=t, a=float(spins[lo]), gam=GAM)
+        feat[:, lo:hi] = f
+        targ[:, lo:hi] = t
+    torch.cuda.synchronize()
+    return feat, targ
+
+
+def test_prim2cons_matches_oracle():
+    """Same conserved variables to rounding; the tolerance of a state grows with its conditioning,
+    Gamma^2 (1 + sigma) (the energy and momentum sums cancel in relativistic, magnetised states)."""
+    hamr = _hamr()
+    n = 20_000
+    prim, x1, x2 = W.random_states(n, seed=31)
+    d = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, metric=O.METRIC_KS, a=0.9375, gam=GAM)
+    Uo = O.p2u_many(d, prim, x1, x2)
+    U = torch.empty((6, n), dtype=torch.float64, device="cuda")
+    hamr.prim2cons(dev(prim.T), dev(x1), dev(x2), U, a=0.9375, gam=GAM)
+    Ug = U.cpu().numpy().T
+    g2 = np.exp(O.mlp_targets(d, prim, x1, x2)[:, 1])
+    sigma = np.array([O.state(d, prim[s], x1[s], x2[s])[4] for s in range(n)]) / prim[:, 0]
+    cond = g2 * (1.0 + sigma)
+    scale = np.abs(Uo).max(axis=1)
+    err = np.abs(Ug - Uo).max(axis=1) / scale
+    assert np.all(err <= 1e-14 * cond + 1e-15), (err / cond).max()
+    assert np.median(err) < 1e-13
+
+
+def test_features_and_targets_match_oracle():
+    prim, x1, x2, U, spins = oracle_pairs(200_000, seed=32, nspin=4)
+    feat, targ = gpu_features(prim, x1, x2, U, spins)
+    fo = np.concatenate([O.mlp_features(O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, metric=O.METRIC_KS, a=float(a),
+                                                    gam=GAM), U[spins == a], prim[spins == a, 5:8],
+                                        x1[spins == a], x2[spins == a]) for a in np.unique(spins)])
+    yo = np.concatenate([O.mlp_targets(O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, metric=O.METRIC_KS, a=float(a),
+                                                   gam=GAM), prim[spins == a], x1[spins == a], x2[spins == a])
+                         for a in np.unique(spins)])
+    order = np.concatenate([np.flatnonzero(spins == a) for a in np.unique(spins)])
+    fg = feat.cpu().numpy().T[order]
+    yg = targ.cpu().numpy().T[order]
+    # FP32 values of logarithms of FP64 quantities: absolute error ~ 1e-6 (f3 in [0, 1], f6 in (0, 1])
+    err = np.abs(fg - fo) / np.maximum(1.0, np.abs(fo))
+    assert np.max(err) < 2e-5, (np.argmax(err.max(axis=0)), err.max(axis=0))
+    assert np.max(np.abs(yg - yo) / np.maximum(1.0, np.abs(yo))) < 1e-6
+
+
+def _random_model(seed):
+    hamr = _hamr()
+    rng = np.random.default_rng(seed)
+    m = hamr.Mlp(seed=seed)
+    theta = (rng.normal(0.0, 0.3, M.N_PARAMS)).astype(np.float32)
+    norm = np.concatenate([rng.normal(0, 1, 10), rng.uniform(0.5, 3.0, 10), rng.normal(0, 1, 2),
+                           rng.uniform(0.5, 2.0, 2)]).astype(np.float32)
+    m.set_params(theta, norm)
+    return m, theta.astype(np.float64), norm.astype(np.float64)
+
+
+def test_fp32_forward_matches_oracle():
+    m, theta, norm = _random_model(41)
+    F = np.random.default_rng(42).normal(0.0, 2.0, (5000, 10)).astype(np.float32)
+    out = torch.empty((2, len(F)), dtype=torch.float32, device="cuda")
+    m.forward(dev(F.T, torch.float32), out, tensor_cores=False)
+    yg = out.cpu().numpy().T
+    yo = M.forward(theta, norm, F.astype(np.float64))
+    scale = np.abs(yo).max()
+    assert np.max(np.abs(yg - yo)) < 1e-5 * scale
+
+
+def test_tensor_core_forward_matches_the_bf16_statement():
+    """tcgen05 inference vs the oracle's bf16-operand forward: equal up to FP32 accumulation order and
+    the odd bf16 rounding flip it causes; and within bf16 accuracy of the FP64 network."""
+    m, theta, norm = _random_model(43)
+    for n in (1, 127, 128, 129, 50_000):  # a partial tile, exact tiles, a ragged tail
+        F = np.random.default_rng(44 + n).normal(0.0, 2.0, (n, 10)).astype(np.float32)
+        out = torch.full((2, n), float("nan"), dtype=torch.float32, device="cuda")
+        m.forward(dev(F.T, torch.float32), out, tensor_cores=True)
+        yg = out.cpu().numpy().T
+        assert m.error_flag() == 0
+        y16 = M.forward(theta, norm, F.astype(np.float64), bf16=True)
+        y64 = M.forward(theta, norm, F.astype(np.float64))
+        scale = np.abs(y64).max()
+        d16 = np.abs(yg - y16)
+        assert np.all(np.isfinite(yg))
+        assert np.median(d16) < 2e-5 * scale, (n, np.median(d16), scale)
+        assert np.max(d16) < 3e-2 * scale, (n, np.max(d16), scale)
+        assert np.median(np.abs(yg - y64)) < 2e-2 * scale
+
+
+def test_loss_gradient_matches_oracle_backprop():
+    m, theta, norm = _random_model(45)
+    rng = np.random.default_rng(46)
+    n = 4096 + 77  # whole CTAs and a ragged one
+    F = rng.normal(0.0, 2.0, (n, 10)).astype(np.float32)
+    T = rng.normal(0.0, 1.5, (n, 2)).astype(np.float32)
+    L, g = m.loss_grad(dev(F.T, torch.float32), dev(T.T, torch.float32))
+    Lo, go = M.loss_and_grad(theta, norm, F.astype(np.float64), T.astype(np.float64))
+    assert abs(L - Lo) < 1e-5 * Lo
+    rel = np.linalg.norm(g - go) / np.linalg.norm(go)
+    assert rel < 1e-5, rel
+    assert np.max(np.abs(g - go)) < 1e-4 * np.abs(go).max()
+
+
+@pytest.fixture(scope="module")
+def trained():
+    """Network trained on 10M oracle pairs (seed 5) by the library's kernels; 1M validation pairs (seed 6)."""
+    hamr = _hamr()
+    prim, x1, x2, U, spins = oracle_pairs(10_000_000, seed=5)
+    feat, targ = gpu_features(prim, x1, x2, U, spins)
+    del prim, x1, x2, U
+    vprim, vx1, vx2, vU, vspins = oracle_pairs(1_000_000, seed=6)
+    vfeat, vtarg = gpu_features(vprim, vx1, vx2, vU, vspins)
+    m = hamr.Mlp(seed=7)
+    m.fit_norm(feat, targ)
+    L0, _ = m.loss_grad(vfeat, vtarg)
+    loss = m.train(feat, targ, steps=6000, batch=8192, lr=2e-3, lr_final=2e-5, seed=5)
+    L1, _ = m.loss_grad(vfeat, vtarg)
+    del feat, targ
+    return dict(m=m, L0=L0, L1=L1, loss=loss, vfeat=vfeat, vtarg=vtarg, val=(vprim, vx1, vx2, vU, vspins))
+
+
+def test_training_lowers_the_validation_loss(trained):
+    L0, L1, loss = trained["L0"], trained["L1"], trained["loss"]
+    print("validation loss before %.4g after %.4g; training loss first %.4g last %.4g" %
+          (L0, L1, loss[:50].mean(), loss[-50:].mean()))
+    assert L1 < 0.02 * L0
+    assert loss[-50:].mean() < 0.05 * loss[:50].mean()
+    # the tensor-core inference of the trained network predicts the targets to a few per cent
+    m = trained["m"]
+    vfeat, vtarg = trained["vfeat"], trained["vtarg"]
+    out = torch.empty_like(vtarg)
+    m.forward(vfeat, out, tensor_cores=True)
+    err = (out - vtarg).abs().median(dim=1).values.cpu().numpy()
+    print("median |error| of ln(W/D), ln Gamma^2 (tensor cores):", err)
+    assert np.all(err < 0.05)
+
+
+def _invert(U, B, x1, x2, guess, a, mlp=None):
+    hamr = _hamr()
+    n = U.shape[1]
+    prim = guess.clone()
+    st = torch.zeros(n, dtype=torch.int32, device="cuda")
+    it = torch.zeros(n, dtype=torch.int32, device="cuda")
+    hamr.con2prim(U, B, x1, x2, prim, st, it, a=a, gam=GAM, mlp=mlp)
+    torch.cuda.synchronize()
+    return prim, st.cpu().numpy(), it.cpu().numpy()
+
+
+def test_gain_over_the_plain_start(trained):
+    """Inversions of the 1M validation states: from the network's guess (Newton refines it, the plain
+    start is the fallback) against the plain start alone. Two plain starts: a cold one (rho = D,
+    u_g = 1e-3 D, utilde = 0: no knowledge of the state) and a warm one (the exact primitives
+    perturbed by 5%, as a previous step would give). The accepted solutions agree; the network cuts
+    iterations and failures of the cold start."""
+    m = trained["m"]
+    vprim, vx1, vx2, vU, vspins = trained["val"]
+    Dall = np.exp(trained["vfeat"][0].double().cpu().numpy())  # D = rho Gamma of each state (input f0)
+    report = {}
+    for a in np.unique(vspins)[:3]:
+        sel = vspins == a
+        U, B = dev(vU[sel].T), dev(vprim[sel, 5:8].T)
+        x1, x2 = dev(vx1[sel]), dev(vx2[sel])
+        true = vprim[sel]
+        cold = np.zeros_like(true)
+        cold[:, 0] = Dall[sel]
+        cold[:, 1] = 1e-3 * cold[:, 0]
+        warm = true.copy()
+        warm[:, 0] *= 1.05
+        warm[:, 1] *= 0.95
+        warm[:, 2:5] *= 0.95
+        for name, g in (("cold", cold), ("warm", warm)):
+            gd = dev(g.T)
+            p0, s0, i0 = _invert(U, B, x1, x2, gd, float(a))
+            p1, s1, i1 = _invert(U, B, x1, x2, gd, float(a), mlp=m)
+            p0, p1 = p0.cpu().numpy(), p1.cpu().numpy()
+            both = (s0 == 0) & (s1 == 0)
+
+            def dist(p, q):
+                # rho and the velocity vector relative; u_g, a remainder of W, relative to rho + gam u_g
+                d_rho = np.abs(p[0] - q[0]) / q[0]
+                d_ut = np.linalg.norm(p[2:5] - q[2:5], axis=0) / np.maximum(np.linalg.norm(q[2:5], axis=0), 1e-300)
+                d_u = np.abs(p[1] - q[1]) / (q[0] + GAM * q[1])
+                return np.maximum(np.maximum(d_rho, d_ut), d_u)
+            # roots other than the state the conserved variables came from ("wrong root")
+            wrong0 = int(((dist(p0, true.T) > 1e-3) & (s0 == 0)).sum())
+            wrong1 = int(((dist(p1, true.T) > 1e-3) & (s1 == 0)).sum())
+            worst = dist(p1, p0)
+            agree = both & (worst < 1e-3)
+            key = (name, round(float(a), 3))
+            report[key] = dict(iters_plain=float(i0.mean()), iters_mlp=float(i1.mean()),
+                               energy_fail_plain=int((s0 != 0).sum()), energy_fail_mlp=int((s1 != 0).sum()),
+                               wrong_root_plain=wrong0, wrong_root_mlp=wrong1,
+                               q999_diff=float(np.quantile(worst[agree], 0.999)))
+            # where both reach the same root they agree to the Newton tolerance (1e-10 in W, v^2)
+            assert np.quantile(worst[agree], 0.999) < 1e-8, (key, report[key])
+            assert wrong1 <= wrong0, (key, report[key])
+    for k, v in report.items():
+        print(k, v)
+    cold = [v for k, v in report.items() if k[0] == "cold"]
+    assert all(v["iters_mlp"] < 0.8 * v["iters_plain"] for v in cold)
+    assert all(v["energy_fail_mlp"] <= v["energy_fail_plain"] for v in cold)
+    assert m.error_flag() == 0
