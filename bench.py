@@ -211,6 +211,107 @@ def mixed_leg(args, hamr, torch, blk, dprim, dbf, g64, stream, cells, world, dis
             "gpu_launches": int(sum(v[0] for k, v in timing.items() if k != "load"))}
 
 
+def train_network(hamr, torch, n=10_000_000, nspin=10, steps=6000, seed=5):
+    """The learned inversion guess, trained on the device: n random states (rho log-uniform 1e-6..1,
+    u/rho 1e-4..1e2, Lorentz factor 1..50, sigma 0..100, r 0.9 r_+..100; nspin spins drawn from
+    0..0.99), conserved variables and inputs formed by the library, then Adam on the training kernels."""
+    from paper_1912_10192_gb300 import workloads as W
+    t0 = time.perf_counter()
+    spins = 0.99 * W.uniform01(seed + 1000, np.arange(nspin))
+    feats, targs = [], []
+    for k in range(nspin):
+        pr, x1, x2 = W.random_states(n // nspin, seed=seed * 100 + k, a=float(spins[k]))
+        P = torch.from_numpy(np.ascontiguousarray(pr.T)).cuda()
+        X1, X2 = torch.from_numpy(x1).cuda(), torch.from_numpy(x2).cuda()
+        U = torch.empty((6, len(x1)), dtype=torch.float64, device="cuda")
+        hamr.prim2cons(P, X1, X2, U, a=float(spins[k]), gam=13.0 / 9.0)
+        f = torch.empty((10, len(x1)), dtype=torch.float32, device="cuda")
+        t = torch.empty((2, len(x1)), dtype=torch.float32, device="cuda")
+        hamr.Mlp.features(U, P[5:8].contiguous(), X1, X2, f, prim=P, targ=t, a=float(spins[k]), gam=13.0 / 9.0)
+        feats.append(f)
+        targs.append(t)
+    feat, targ = torch.cat(feats, 1).contiguous(), torch.cat(targs, 1).contiguous()
+    del feats, targs
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    m = hamr.Mlp(seed=7)
+    m.fit_norm(feat, targ)
+    loss = m.train(feat, targ, steps=steps, batch=8192)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    info = {"pairs": n, "spins": nspin, "steps": steps, "batch": 8192, "data_s": round(t1 - t0, 2),
+            "train_s": round(t2 - t1, 2), "loss_first": float(loss[:20].mean()), "loss_last": float(loss[-20:].mean())}
+    return m, info
+
+
+def mlp_leg(args, hamr, torch, blk, dprim, dbf, cells, stream):
+    """The benchmark workload with the network attached to the inversions, both modes, against the plain
+    start: zone-cycles/s, Newton iterations per inversion, entropy inversions."""
+    m, info = train_network(hamr, torch)
+    out = {"training": info}
+    for name, mode in (("plain", None), ("rescue", hamr.MLP_RESCUE), ("first", hamr.MLP_FIRST)):
+        g = hamr.Grid([blk])
+        g.set_state(dprim, dbf, stream=stream)
+        if mode is not None:
+            g.set_mlp(m, mode)
+        for _ in range(args.warmup):
+            g.step(stream=stream)
+        torch.cuda.synchronize()
+        steps = min(args.steps, 20)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            g.step(stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        tot = dict(c2p_ok=0, c2p_entropy=0, c2p_fail=0, newton_iters=0)
+        for _ in range(2):  # counters of single steps (stats synchronise)
+            st = g.step(stream=stream, stats=True)
+            for k in tot:
+                tot[k] += st[k]
+        ninv = tot["c2p_ok"] + tot["c2p_entropy"] + tot["c2p_fail"]
+        out[name] = {"value": cells / (ms * 1e-3), "ms_per_step": ms,
+                     "newton_iters_per_inversion": tot["newton_iters"] / max(ninv, 1),
+                     "entropy_per_step": tot["c2p_entropy"] / 2, "fail_per_step": tot["c2p_fail"] / 2}
+        g.close()
+    out["network_error_flag"] = m.error_flag()
+    m.close()
+    return out
+
+
+def amr_leg(hamr, torch, precision=0):
+    """512-block AMR/LAT torus tree (levels 0..3), whole LAT periods replayed from one CUDA graph."""
+    from paper_1912_10192_gb300 import workloads as W
+    blocks = W.amr_torus_tree(n=32)
+    states = W.torus_blocks(blocks, seed=3)
+    g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], precision=precision)
+    for i, (p, bf) in enumerate(states):
+        g.set_state(p, bf, block=i)
+    lmax = max(b["lat"] for b in blocks)
+    per = 2 ** lmax
+    g.batch_step(per)  # capture + first period
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    nper = 2
+    ev0.record()
+    g.batch_step(per * nper)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / nper
+    real = sum(b["n1"] * b["n2"] * b["n3"] * 2 ** (lmax - b["lat"]) for b in blocks)
+    eff = sum(b["n1"] * b["n2"] * b["n3"] for b in blocks) * per
+    hist = {str(L): sum(1 for b in blocks if b["lat"] == L) for L in range(lmax + 1)}
+    g.close()
+    return {"workload": "512-block AMR/LAT torus tree, 32^3 and 32x32x16 blocks, %d cells, seed 3" %
+                        sum(b["n1"] * b["n2"] * b["n3"] for b in blocks),
+            "precision": "mixed" if precision else "fp64", "ms_per_period": ms, "fine_substeps_per_period": per,
+            "real_zone_cycles_per_s": real / (ms * 1e-3), "lat_effective_zone_cycles_per_s": eff / (ms * 1e-3),
+            "lat_levels": hist}
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_1912_10192_gb300 import _build, hamr
@@ -269,6 +370,12 @@ def run_ours(args, rank, world, local):
     chosen = None
     if not args.fp64_only:
         chosen = mixed_leg(args, hamr, torch, blk, dprim, dbf, g, stream, cells, world, dist)
+
+    # ---- the learned inversion guess and the batched AMR/LAT tree (single GPU, rank 0 only)
+    extra = {}
+    if not args.no_extra and world == 1:
+        extra["mlp"] = mlp_leg(args, hamr, torch, blk, dprim, dbf, cells, stream)
+        extra["amr_lat"] = [amr_leg(hamr, torch, 0), amr_leg(hamr, torch, 1)]
 
     # ---- end to end: host buffers through the C ABI, copies inside the timed region
     e2e_steps = min(args.steps, 10)
@@ -331,7 +438,7 @@ def run_ours(args, rank, world, local):
             "step_fp64_tflops": whole, "step_fp64_frac_nominal": whole / FP64_NOMINAL_TFLOPS,
             "kernel_ms": {k: round(v[1], 3) for k, v in timing.items()},
             "c2p": {k: stats[k] for k in ("c2p_ok", "c2p_entropy", "c2p_fail", "floor_hits")},
-            "chosen_form": chosen}
+            "chosen_form": chosen, **extra}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, t = cpu_oracle_rate(N1, N2, N3, 1, 0)
         line["cpu_baseline"] = {"value": rate, "unit": "zone-cycles/s", "cores": 1, "kind": "oracle",
@@ -352,6 +459,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-precision leg")
+    ap.add_argument("--no-extra", action="store_true", help="skip the network and AMR/LAT legs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

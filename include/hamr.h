@@ -228,6 +228,7 @@ int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, double* bface
 /* ---- standalone inversion (Sec. 2.6) ---- */
 #define HAMR_C2P_ENTROPY_ONLY 1u /* skip the energy inversion (tests of the backup) */
 #define HAMR_C2P_MLP 2u          /* start Newton from the learned guess of `mlp` (fallback: the prim guess) */
+#define HAMR_C2P_MLP_RESCUE 4u   /* start from the prim guess; where that fails, from the learned guess */
 
 typedef struct hamr_mlp hamr_mlp;
 
@@ -316,9 +317,15 @@ int hamr_mlp_forward(const hamr_mlp* m, int64_t n, const float* feat, float* out
  * copy of the weights since the last call (its cells used the plain start),
  * else 0; clears the flag. Synchronises. */
 int hamr_mlp_error_flag(hamr_mlp* m, int* flag);
-/* Attaches a network to a grid: its inversions start from the learned
- * guess (NULL detaches). The model must outlive its use by the grid. */
-int hamr_grid_set_mlp(hamr_grid* g, const hamr_mlp* m);
+/* Attaches a network to a grid (NULL detaches); the model must outlive its
+ * use by the grid. mode HAMR_MLP_FIRST: every inversion starts Newton from
+ * the learned guess, the start from the previous primitives is the
+ * fallback. HAMR_MLP_RESCUE: Newton starts from the previous primitives;
+ * where that fails the learned guess is tried before the entropy backup
+ * (a CTA runs the network only if one of its cells failed). Synchronises. */
+#define HAMR_MLP_FIRST 0
+#define HAMR_MLP_RESCUE 1
+int hamr_grid_set_mlp(hamr_grid* g, const hamr_mlp* m, int mode);
 
 /* Message of the last error in the calling thread ("" if none). */
 const char* hamr_last_error(void);

@@ -324,6 +324,7 @@ int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out) {
     g->ph.mixed = (d->precision == HAMR_PREC_MIXED);
     g->ph.mlp_img = nullptr;
     g->ph.mlp_err = nullptr;
+    g->ph.mlp_mode = HAMR_MLP_FIRST;
     cudaGetDevice(&g->device);
     for (int b = 0; b < d->nblocks; b++) {
         rc = alloc_block(g, b);
@@ -537,14 +538,19 @@ int hamr_con2prim(const hamr_c2p_desc* d, int64_t n, const double* U, const doub
     if (d->metric != HAMR_METRIC_KS && d->metric != HAMR_METRIC_MINKOWSKI)
         return fail(HAMR_EINVAL, "unknown metric %d", d->metric);
     if (!(d->gam > 1.0 && d->gam <= 2.0)) return fail(HAMR_EINVAL, "gam must be in (1, 2]");
-    if (d->flags & ~(HAMR_C2P_ENTROPY_ONLY | HAMR_C2P_MLP)) return fail(HAMR_EINVAL, "unknown flags 0x%x", d->flags);
-    if ((d->flags & HAMR_C2P_MLP) && !d->mlp) return fail(HAMR_EINVAL, "HAMR_C2P_MLP without a network");
+    if (d->flags & ~(HAMR_C2P_ENTROPY_ONLY | HAMR_C2P_MLP | HAMR_C2P_MLP_RESCUE))
+        return fail(HAMR_EINVAL, "unknown flags 0x%x", d->flags);
+    if ((d->flags & HAMR_C2P_MLP) && (d->flags & HAMR_C2P_MLP_RESCUE))
+        return fail(HAMR_EINVAL, "HAMR_C2P_MLP and HAMR_C2P_MLP_RESCUE exclude each other");
+    if ((d->flags & (HAMR_C2P_MLP | HAMR_C2P_MLP_RESCUE)) && !d->mlp)
+        return fail(HAMR_EINVAL, "a network flag without a network");
     CUDA_TRY(launch_con2prim(*d, n, U, B, x1, x2, prim, status, iters, S(stream)));
     return HAMR_OK;
 }
 
-int hamr_grid_set_mlp(hamr_grid* g, const hamr_mlp* m) {
+int hamr_grid_set_mlp(hamr_grid* g, const hamr_mlp* m, int mode) {
     if (!g) return fail(HAMR_EINVAL, "grid is NULL");
+    if (mode != HAMR_MLP_FIRST && mode != HAMR_MLP_RESCUE) return fail(HAMR_EINVAL, "unknown mode %d", mode);
     if (m) {
         int dev = -1;
         cudaGetDevice(&dev);
@@ -553,6 +559,7 @@ int hamr_grid_set_mlp(hamr_grid* g, const hamr_mlp* m) {
     CUDA_TRY(cudaDeviceSynchronize());  // no step in flight reads the old arguments
     g->ph.mlp_img = mlp_image(m);
     g->ph.mlp_err = mlp_error_ptr(m);
+    g->ph.mlp_mode = mode;
     if (g->amr) return amr_set_phys(g->amr, g->ph);
     return HAMR_OK;
 }

@@ -33,30 +33,32 @@ __global__ void __launch_bounds__(128) k_con2prim(hamr_c2p_desc d, const uint8_t
         pr[B2] = bc[1];
         pr[B3] = bc[2];
     }
-    double g2[2];
-    bool use_g2 = false;
-    if (MLP) {  // the 128 states of the CTA through the network (mlp.cuh)
-        extern __shared__ __align__(16) uint8_t mlp_smem[];
-        MlpCta C;
-        mlp_begin(C, mlp_smem, img);
-        float f[MLP_NIN], y[MLP_NOUT];
-        C2PScalars S;
-        S.D = 1.0;
-        if (active) {
-            c2p_scalars(u, bc, m, S);
-            mlp_features(S, u[C_RHO], u[C_ENT], m, x1[s], d.gam, f);
-        }
-        const bool ran = mlp_infer(C, f, active, y);
-        mlp_end(C);
-        if (!C.ok && threadIdx.x == 0 && err) atomicExch(err, 1);
-        if (active && ran) {
-            mlp_guess(S.D, y, g2);
-            use_g2 = true;
+    const bool entropy_only = (d.flags & HAMR_C2P_ENTROPY_ONLY) != 0;
+    const bool rescue = (d.flags & HAMR_C2P_MLP_RESCUE) != 0;
+    C2PWork w;
+    if (active) c2p_prepare(u, bc, m, d.gam, pr, w);
+    if (MLP && !entropy_only) {  // the 128 states of the CTA through the network (mlp.cuh)
+        if (rescue && active) c2p_attempt(w, d.gam, w.W0, w.vsq0);
+        if (__syncthreads_or(active && !w.ok)) {
+            extern __shared__ __align__(16) uint8_t mlp_smem[];
+            MlpCta C;
+            mlp_begin(C, mlp_smem, img);
+            float f[MLP_NIN], y[MLP_NOUT];
+            if (active) mlp_features(w.S, u[C_RHO], u[C_ENT], m, x1[s], d.gam, f);
+            const bool ran = mlp_infer(C, f, active, y);
+            mlp_end(C);
+            if (!C.ok && threadIdx.x == 0 && err) atomicExch(err, 1);
+            if (active && ran && !w.ok) {
+                double g2[2];
+                mlp_guess(w.S.D, y, g2);
+                c2p_attempt(w, d.gam, g2[0], g2[1]);
+            }
         }
     }
     if (!active) return;
-    int it = 0;
-    const int st = invert(u, bc, m, d.gam, pr, &it, (d.flags & HAMR_C2P_ENTROPY_ONLY) != 0, use_g2 ? g2 : nullptr);
+    if (!entropy_only && !(MLP && rescue)) c2p_attempt(w, d.gam, w.W0, w.vsq0);
+    const int st = c2p_finish(w, u, m, d.gam, pr);
+    const int it = w.its;
 #pragma unroll
     for (int q = 0; q < NPRIM; q++) prim[q * n + s] = pr[q];
     status[s] = st;
@@ -70,7 +72,7 @@ cudaError_t launch_con2prim(const hamr_c2p_desc& d, int64_t n, const double* U, 
     if (n <= 0) return cudaSuccess;
     const int bs = 128;
     const unsigned nb = (unsigned)((n + bs - 1) / bs);
-    if ((d.flags & HAMR_C2P_MLP) && d.mlp)
+    if ((d.flags & (HAMR_C2P_MLP | HAMR_C2P_MLP_RESCUE)) && d.mlp)
         k_con2prim<true><<<nb, bs, MLP_SMEM_BYTES, s>>>(d, mlp_image(d.mlp), mlp_error_ptr(d.mlp), n, U, B, x1, x2,
                                                         prim, status, iters);
     else

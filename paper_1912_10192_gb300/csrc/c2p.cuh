@@ -101,53 +101,58 @@ __device__ __forceinline__ bool energy_result(const C2PScalars& S, double gam, d
     return (rho > 0.0) && (u > 0.0);
 }
 
-// pr: in the guess (slots 0..4), out the result (slots 0..4) unless INV_FAIL.
-// guess2 (optional): a first start (W, v^2) tried before the one of pr; the
-// start from pr is then the fallback. `iters` counts the energy-inversion
-// Newton iterations of every start tried.
-__device__ __forceinline__ int invert(const double U[NCONS], const double Bc[3], const Metric<double>& m, double gam,
-                                      double pr[NPRIM], int* iters, bool entropy_only,
-                                      const double* guess2 = nullptr) {
+// The inversion in three pieces (invert() below composes them):
+// c2p_prepare (scalars and the start from the guess primitives), any number of
+// energy-equation attempts from given starts, c2p_finish (entropy backup when
+// no attempt succeeded, then the primitives).
+struct C2PWork {
     C2PScalars S;
-    c2p_scalars(U, Bc, m, S);
-    const double gfac = (gam - 1.0) / gam;
-    const double D = S.D, Bsq = S.Bsq, QB2 = S.QB2, Qtsq = S.Qtsq;
+    double W0, vsq0;  // the start from the guess primitives
+    double W, vsq, rho, u;
+    bool ok;
+    int its;          // Newton iterations of every energy attempt
+};
 
-    // start from the guess primitives
+__device__ __forceinline__ void c2p_prepare(const double U[NCONS], const double Bc[3], const Metric<double>& m,
+                                            double gam, const double pr[NPRIM], C2PWork& w) {
+    c2p_scalars(U, Bc, m, w.S);
     const double q1 = pr[U1], q2 = pr[U2], q3 = pr[U3];
     const double qsq = m.g11 * q1 * q1 + m.g22 * q2 * q2 + m.g33 * q3 * q3 + 2.0 * m.g13 * q1 * q3;
     const double gsq = 1.0 + qsq;
-    const double W0 = (pr[RHO] + gam * pr[UU]) * gsq;
-    double W = W0, vsq = 0.0;
+    w.W0 = (pr[RHO] + gam * pr[UU]) * gsq;
+    w.vsq0 = fmin(qsq / gsq, C2P_VSQMAX);
+    w.W = w.W0;
+    w.vsq = 0.0;
+    w.rho = w.u = 0.0;
+    w.ok = false;
+    w.its = 0;
+}
 
-    bool ok = false;
-    int itsum = 0;
-    double rho = 0.0, u = 0.0;
-    if (!entropy_only) {
-        int it = 0;
-        if (guess2) {
-            W = guess2[0];
-            vsq = fmin(fmax(guess2[1], 0.0), C2P_VSQMAX);
-            if (W > 0.0) {
-                ok = newton_wv(S, gfac, W, vsq, it);
-                itsum += it;
-                if (ok) ok = energy_result(S, gam, W, vsq, rho, u);
-            }
-        }
-        if (!ok) {
-            W = W0;
-            vsq = fmin(qsq / gsq, C2P_VSQMAX);
-            ok = newton_wv(S, gfac, W, vsq, it);
-            itsum += it;
-            if (ok) ok = energy_result(S, gam, W, vsq, rho, u);
-        }
-    }
-    if (iters) *iters = itsum;
+// one energy-equation attempt from (W, v^2); no-op once an attempt succeeded
+__device__ __forceinline__ void c2p_attempt(C2PWork& w, double gam, double W, double vsq) {
+    if (w.ok || !(W > 0.0)) return;
+    const double gfac = (gam - 1.0) / gam;
+    int it = 0;
+    vsq = fmin(fmax(vsq, 0.0), C2P_VSQMAX);
+    bool ok = newton_wv(w.S, gfac, W, vsq, it);
+    w.its += it;
+    w.W = W;
+    w.vsq = vsq;
+    if (ok) ok = energy_result(w.S, gam, W, vsq, w.rho, w.u);
+    w.ok = ok;
+}
+
+// pr: out the result (slots 0..4) unless INV_FAIL (then untouched)
+__device__ __forceinline__ int c2p_finish(C2PWork& w, const double U[NCONS], const Metric<double>& m, double gam,
+                                          double pr[NPRIM]) {
+    const C2PScalars& S = w.S;
+    const double D = S.D, Bsq = S.Bsq, QB2 = S.QB2, Qtsq = S.Qtsq;
+    double W = w.W, vsq = w.vsq, rho = w.rho, u = w.u;
     int status = INV_OK;
-    if (!ok) {
+    if (!w.ok) {
         const double kappa = U[C_ENT] / U[C_RHO];
         const double gr = gam / (gam - 1.0);
-        W = W0;
+        W = w.W0;
         bool eok = false;
         for (int k = 1; k <= C2P_NMAX; k++) {
             const double W2 = W * W;
@@ -199,6 +204,23 @@ __device__ __forceinline__ int invert(const double U[NCONS], const double Bc[3],
     pr[RHO] = rho;
     pr[UU] = u;
     return status;
+}
+
+// pr: in the guess (slots 0..4), out the result (slots 0..4) unless INV_FAIL.
+// guess2 (optional): a first start (W, v^2) tried before the one of pr; the
+// start from pr is then the fallback. `iters` counts the energy-inversion
+// Newton iterations of every start tried.
+__device__ __forceinline__ int invert(const double U[NCONS], const double Bc[3], const Metric<double>& m, double gam,
+                                      double pr[NPRIM], int* iters, bool entropy_only,
+                                      const double* guess2 = nullptr) {
+    C2PWork w;
+    c2p_prepare(U, Bc, m, gam, pr, w);
+    if (!entropy_only) {
+        if (guess2) c2p_attempt(w, gam, guess2[0], guess2[1]);
+        c2p_attempt(w, gam, w.W0, w.vsq0);
+    }
+    if (iters) *iters = w.its;
+    return c2p_finish(w, U, m, gam, pr);
 }
 
 }  // namespace hamr

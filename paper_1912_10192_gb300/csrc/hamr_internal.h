@@ -44,6 +44,7 @@ struct PhysArgs {
     int mixed;  // 1: reconstruction and face fluxes in FP32 (HAMR_PREC_MIXED)
     const uint8_t* mlp_img;  // inference image of the learned inversion guess (nullptr: not used)
     int* mlp_err;            // set to 1 by a CTA whose network waits gave up
+    int mlp_mode;            // HAMR_MLP_FIRST or HAMR_MLP_RESCUE
 };
 
 // device scratch/state of one block

@@ -375,10 +375,9 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
     long c = 0, g = 0;
     int i = 0, j = 0;
     MlpCta C;
-    if (MLP) {
-        extern __shared__ __align__(16) uint8_t mlp_smem[];
-        mlp_begin(C, mlp_smem, ph.mlp_img);  // the weight image streams in while U is formed
-    }
+    const bool rescue = MLP && ph.mlp_mode == HAMR_MLP_RESCUE;
+    extern __shared__ __align__(16) uint8_t mlp_smem[];
+    if (MLP && !rescue) mlp_begin(C, mlp_smem, ph.mlp_img);  // the weight image streams in while U is formed
     if (active) {
         i = (int)(t % v.n1);
         j = (int)((t / v.n1) % v.n2);
@@ -450,28 +449,33 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
         pr[B2] = Bc[1];
         pr[B3] = Bc[2];
     }
-    double g2[2];
-    bool use_g2 = false;
+    // inversion: energy attempts from the start(s), then the entropy backup
+    C2PWork w;
+    if (active) c2p_prepare(U, Bc, m, gam, pr, w);
     if (MLP) {
-        float f[MLP_NIN], y[MLP_NOUT];
-        C2PScalars S;
-        S.D = 1.0;
-        if (active) {
-            c2p_scalars(U, Bc, m, S);
-            mlp_features(S, U[C_RHO], U[C_ENT], m, v.x1min + (i + 0.5) * v.dx1, gam, f);
-        }
-        if (__syncthreads_or(active)) {
+        // first: the network's start, then the plain one; rescue: the plain start, then the
+        // network's where it failed (the CTA runs the network only if one of its cells failed)
+        if (rescue && active) c2p_attempt(w, gam, w.W0, w.vsq0);
+        if (__syncthreads_or(active && !w.ok)) {
+            if (rescue) mlp_begin(C, mlp_smem, ph.mlp_img);
+            float f[MLP_NIN], y[MLP_NOUT];
+            if (active) mlp_features(w.S, U[C_RHO], U[C_ENT], m, v.x1min + (i + 0.5) * v.dx1, gam, f);
             const bool ran = mlp_infer(C, f, active, y);
-            if (active && ran) {
-                mlp_guess(S.D, y, g2);
-                use_g2 = true;
+            mlp_end(C);
+            if (!C.ok && threadIdx.x == 0 && ph.mlp_err) atomicExch(ph.mlp_err, 1);
+            if (active && ran && !w.ok) {
+                double g2[2];
+                mlp_guess(w.S.D, y, g2);
+                c2p_attempt(w, gam, g2[0], g2[1]);
             }
+        } else if (!rescue) {
+            mlp_end(C);
         }
-        mlp_end(C);
-        if (!C.ok && threadIdx.x == 0 && ph.mlp_err) atomicExch(ph.mlp_err, 1);
     }
     if (active) {
-        st = invert(U, Bc, m, gam, pr, &its, false, use_g2 ? g2 : nullptr);
+        if (!rescue) c2p_attempt(w, gam, w.W0, w.vsq0);
+        its = w.its;
+        st = c2p_finish(w, U, m, gam, pr);
         uint8_t sb = (st == INV_ENTROPY) ? ST_ENTROPY : ((st == INV_FAIL) ? ST_FAIL : 0);
         if (ph.floors) {
             Fluid<double> s;

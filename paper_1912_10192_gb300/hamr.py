@@ -21,7 +21,8 @@ RECON_PPM, RECON_MC, RECON_MINMOD = 0, 1, 2
 FLUX_HLL, FLUX_LLF = 0, 1
 BC_OUTFLOW, BC_PERIODIC, BC_POLAR, BC_OUTFLOW_NOINFLOW, BC_BLOCK = 0, 1, 2, 3, 4
 PREC_FP64, PREC_MIXED = 0, 1
-C2P_ENTROPY_ONLY, C2P_MLP = 1, 2
+C2P_ENTROPY_ONLY, C2P_MLP, C2P_MLP_RESCUE = 1, 2, 4
+MLP_FIRST, MLP_RESCUE = 0, 1
 NG = 3
 
 
@@ -106,7 +107,7 @@ def lib():
         L.hamr_mlp_loss_grad.argtypes = [P, C.c_int64, P, P, P, P, P]
         L.hamr_mlp_forward.argtypes = [P, C.c_int64, P, P, C.c_int, P]
         L.hamr_mlp_error_flag.argtypes = [P, C.POINTER(C.c_int)]
-        L.hamr_grid_set_mlp.argtypes = [P, P]
+        L.hamr_grid_set_mlp.argtypes = [P, P, C.c_int]
         L.hamr_last_error.argtypes = []
         L.hamr_last_error.restype = C.c_char_p
         for name in header_functions():
@@ -230,9 +231,10 @@ class Grid:
         check(lib().hamr_grid_stats(self.h, C.byref(st)))
         return st.as_dict()
 
-    def set_mlp(self, mlp):
-        """Inversions of the grid's steps start from `mlp`'s guess (None: the plain start)."""
-        check(lib().hamr_grid_set_mlp(self.h, mlp.h if mlp is not None else None))
+    def set_mlp(self, mlp, mode=0):
+        """Attach `mlp` to the grid's inversions (None detaches): mode MLP_FIRST (0) starts Newton from
+        its guess, MLP_RESCUE (1) uses it where the start from the previous primitives fails."""
+        check(lib().hamr_grid_set_mlp(self.h, mlp.h if mlp is not None else None, int(mode)))
         self._mlp = mlp
 
 
@@ -244,10 +246,13 @@ def c2p_desc(metric=METRIC_KS, a=0.9375, gam=13.0 / 9.0, flags=0, mlp=None):
 
 
 def con2prim(U, B, x1, x2, prim, status, iters=None, metric=METRIC_KS, a=0.9375, gam=13.0 / 9.0, flags=0,
-             stream=None, mlp=None):
+             stream=None, mlp=None, mlp_mode=MLP_FIRST):
     """Inverts n states in place on the device (SoA torch tensors: U (6, n), B (3, n), prim (8, n)).
-    With `mlp` (an Mlp), Newton starts from the network's guess (flag C2P_MLP)."""
-    d = c2p_desc(metric, a, gam, flags | (C2P_MLP if mlp is not None else 0), mlp)
+    With `mlp` (an Mlp), Newton starts from the network's guess (mlp_mode MLP_FIRST, flag C2P_MLP) or
+    uses it where the start from prim fails (MLP_RESCUE, flag C2P_MLP_RESCUE)."""
+    if mlp is not None:
+        flags |= C2P_MLP if mlp_mode == MLP_FIRST else C2P_MLP_RESCUE
+    d = c2p_desc(metric, a, gam, flags, mlp)
     n = prim.shape[1]
     check(lib().hamr_con2prim(C.byref(d), n, _ptr(U), _ptr(B), _ptr(x1), _ptr(x2), _ptr(prim), _ptr(status),
                               _ptr(iters), _stream(stream)))

@@ -278,3 +278,72 @@ def test_gain_over_the_plain_start(trained):
     assert all(v["iters_mlp"] < 0.8 * v["iters_plain"] for v in cold)
     assert all(v["energy_fail_mlp"] <= v["energy_fail_plain"] for v in cold)
     assert m.error_flag() == 0
+
+
+def test_rescue_mode_on_validation_states(trained):
+    """MLP_RESCUE: the plain start first, the network's where it fails: the warm start keeps its
+    iteration count, and the cold start's energy-inversion failures are rescued."""
+    m = trained["m"]
+    vprim, vx1, vx2, vU, vspins = trained["val"]
+    Dall = np.exp(trained["vfeat"][0].double().cpu().numpy())
+    a = np.unique(vspins)[0]
+    sel = vspins == a
+    U, B = dev(vU[sel].T), dev(vprim[sel, 5:8].T)
+    x1, x2 = dev(vx1[sel]), dev(vx2[sel])
+    cold = np.zeros_like(vprim[sel])
+    cold[:, 0] = Dall[sel]
+    cold[:, 1] = 1e-3 * cold[:, 0]
+    gd = dev(cold.T)
+    hamr = _hamr()
+    p0, s0, i0 = _invert(U, B, x1, x2, gd, float(a))
+    prim = gd.clone()
+    st = torch.zeros(prim.shape[1], dtype=torch.int32, device="cuda")
+    it = torch.zeros_like(st)
+    hamr.con2prim(U, B, x1, x2, prim, st, it, a=float(a), gam=GAM, mlp=m, mlp_mode=hamr.MLP_RESCUE)
+    s2, i2 = st.cpu().numpy(), it.cpu().numpy()
+    print("cold start, rescue: energy failures %d -> %d, iterations %.2f -> %.2f" %
+          ((s0 != 0).sum(), (s2 != 0).sum(), i0.mean(), i2.mean()))
+    assert (s2 != 0).sum() < 0.01 * max((s0 != 0).sum(), 1)
+    assert np.array_equal(i2[s0 == 0], i0[s0 == 0])  # converged plain starts are untouched
+
+
+def test_grid_steps_with_the_network(trained):
+    """Ten steps of the 64x32x16 torus with the network attached (both modes) against the oracle at
+    the same dt: the FP64 parity bar of ten steps (1e-9 relative L1 per field) holds, and the counts
+    of Newton iterations and entropy inversions are reported."""
+    from helpers import TORUS_BC, face_interior, interior, rel_l1, torus_case
+    hamr = _hamr()
+    m = trained["m"]
+    _, d, prim, bf = torus_case(64, 32, 16, seed=1912)
+    og = O.Grid(d)
+    og.set(prim, bf)
+    dts = [og.step() for _ in range(10)]
+    po, bo = og.get()
+    res = {}
+    for name, mode in (("plain", None), ("first", hamr.MLP_FIRST), ("rescue", hamr.MLP_RESCUE)):
+        blk = hamr.block(d.n1, d.n2, d.n3, d.x1min, d.x2min, d.x3min, d.dx1, d.dx2, d.dx3, tuple(d.bc))
+        g = hamr.Grid([blk], metric=d.metric, a=d.a, gam=d.gam, cour=d.cour)
+        g.set_state(torch.from_numpy(prim).cuda(), torch.from_numpy(bf).cuda())
+        if mode is not None:
+            g.set_mlp(m, mode)
+        tot = dict(c2p_ok=0, c2p_entropy=0, c2p_fail=0, newton_iters=0)
+        for dt in dts:
+            st = g.step(dt, stats=True)
+            for k in tot:
+                tot[k] += st[k]
+        pg, bg = g.get_state()
+        g.close()
+        errs = {"rho": rel_l1(interior(pg[0], d), interior(po[0], d)),
+                "u": rel_l1(interior(pg[1], d), interior(po[1], d)),
+                "utilde": sum(np.abs(interior(pg[v], d) - interior(po[v], d)).sum() for v in (2, 3, 4)) /
+                sum(np.abs(interior(po[v], d)).sum() for v in (2, 3, 4)),
+                "Bface": sum(np.abs(x - y).sum() for x, y in zip(face_interior(bg, d), face_interior(bo, d))) /
+                sum(np.abs(y).sum() for y in face_interior(bo, d))}
+        ninv = tot["c2p_ok"] + tot["c2p_entropy"] + tot["c2p_fail"]
+        res[name] = dict(errs=errs, iters_per_inversion=tot["newton_iters"] / ninv, entropy=tot["c2p_entropy"],
+                         fail=tot["c2p_fail"])
+        print(name, res[name])
+        for k, v in errs.items():
+            assert v <= 1e-9, (name, k, v)
+    assert res["rescue"]["entropy"] <= res["plain"]["entropy"]
+    assert m.error_flag() == 0
