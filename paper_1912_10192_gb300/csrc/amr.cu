@@ -545,8 +545,8 @@ struct AmrImpl {
     std::vector<int*> dlev;             // device copies
     int* dall = nullptr;                // all blocks
     long mw_pad = 0, mw_recon = 0, mw_flux[4] = {0, 0, 0, 0}, mw_edge = 0, mw_cell = 0;
-    std::vector<long> lmw_pad, lmw_recon, lmw_edge, lmw_cell;
-    std::vector<std::vector<long>> lmw_flux;
+    std::vector<long> lmw_pad, lmw_edge, lmw_cell;
+    std::vector<std::vector<long>> lmw_flux, lmw_recon;
     // synchronisation
     SyncDev fs{}, es{};
     std::vector<int> fs_beg, fs_end, es_beg, es_end;
@@ -718,6 +718,7 @@ int amr_create(AmrImpl** out, const hamr_grid_desc& d, const std::vector<BlockVi
         D.Bh = s.Bh;
         D.QL = s.QL;
         D.QR = s.QR;
+        D.P32 = s.P32;
         D.F1 = s.F[0];
         D.F2 = s.F[1];
         D.F3 = s.F[2];
@@ -1001,7 +1002,7 @@ int amr_create(AmrImpl** out, const hamr_grid_desc& d, const std::vector<BlockVi
     for (int L = 0; L <= M->Lmax; L++) M->dlev.push_back(M->dev(M->lev[L]));
     M->dall = M->dev(all);
     M->lmw_pad.assign(M->Lmax + 1, 0);
-    M->lmw_recon.assign(M->Lmax + 1, 0);
+    M->lmw_recon.assign(M->Lmax + 1, std::vector<long>(4, 0));
     M->lmw_edge.assign(M->Lmax + 1, 0);
     M->lmw_cell.assign(M->Lmax + 1, 0);
     M->lmw_flux.assign(M->Lmax + 1, std::vector<long>(4, 0));
@@ -1009,11 +1010,11 @@ int amr_create(AmrImpl** out, const hamr_grid_desc& d, const std::vector<BlockVi
         const BlockView& v = H.b[b].v;
         const int L = H.b[b].lat;
         const long pad = (long)v.n1p * v.n2p * v.n3p;
-        const long rec = (long)(v.n1 + 2) * (v.n2 + 2) * (v.n3 + 2);
         const long edg = (long)(v.n1 + 1) * (v.n2 + 1) * (v.n3 + 1);
         const long cel = (long)v.n1 * v.n2 * v.n3;
         M->lmw_pad[L] = std::max(M->lmw_pad[L], pad);
-        M->lmw_recon[L] = std::max(M->lmw_recon[L], rec);
+        for (int dir = 1; dir <= 3; dir++)
+            M->lmw_recon[L][dir] = std::max(M->lmw_recon[L][dir], recon_threads(v, dir));
         M->lmw_edge[L] = std::max(M->lmw_edge[L], edg);
         M->lmw_cell[L] = std::max(M->lmw_cell[L], cel);
         M->lmw_flux[L][1] = std::max(M->lmw_flux[L][1], (long)(v.n1 + 1) * (v.n2 + 2) * (v.n3 + 2));
@@ -1068,8 +1069,9 @@ int group_step(AmrImpl& M, int L, int s, cudaStream_t cs) {
         k_ghost_cells<<<dim3(nb_(M.lmw_pad[L]), nl), BSA, 0, cs>>>(M.H.A, list, sigma, s);
         k_ghost_faces<<<dim3(nb_(3 * M.lmw_pad[L]), nl), BSA, 0, cs>>>(M.H.A, list, sigma, s);
         AM_TRY(cudaGetLastError());
+        if (ph.mixed) AM_TRY(launch_to_f32_batch(tab, list, nl, M.lmw_pad[L], sigma, cs));
         for (int dir = 1; dir <= 3; dir++) {
-            AM_TRY(launch_recon_batch(tab, list, nl, M.lmw_recon[L], ph, dir, sigma, cs));
+            AM_TRY(launch_recon_batch(tab, list, nl, M.lmw_recon[L][dir], ph, dir, sigma, cs));
             AM_TRY(launch_flux_batch(tab, list, nl, M.lmw_flux[L][dir], ph, dir, sigma, cs));
         }
         const int fb = M.fs_beg[L], fe = M.fs_end[L];

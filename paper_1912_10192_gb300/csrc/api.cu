@@ -213,7 +213,13 @@ int alloc_block(hamr_grid* g, int b) {
     v.n2d = (long)(tab / sizeof(double));  // stride between two table components
     const int nfields = 8 + 3 + 8 + 3 + 8 + 8 + 24 + 3 + 6;
     const size_t stbytes = align256((size_t)v.nc);
+    // mixed precision: the FP32 copy of the primitives and FP32 metric/connection tables
+    const bool mixed = (g->desc.precision == HAMR_PREC_MIXED);
+    const size_t fld32 = align256(sizeof(float) * (size_t)v.nc * NPRIM);
+    const size_t tab32 = align256(sizeof(float) * (size_t)v.n2d);
+    const int nc32 = NGEOM + 40;  // centre planes the FP32 path reads: metric and connection
     size_t bytes = fld * nfields + stbytes + tab * (NGEOM_C + 2 * NGEOM) + 256 * 3;
+    if (mixed) bytes += fld32 + tab32 * (nc32 + 2 * NGEOM);
     void* base = nullptr;
     cudaError_t e = cudaMalloc(&base, bytes);
     if (e != cudaSuccess) {
@@ -244,9 +250,20 @@ int alloc_block(hamr_grid* g, int b) {
     s.dscal = (double*)take(256);
     s.dmax = (unsigned long long*)take(256);
     s.dcnt = (unsigned long long*)take(256);
+    s.P32 = nullptr;
+    float *g32c = nullptr, *g32f1 = nullptr, *g32f2 = nullptr;
+    if (mixed) {
+        s.P32 = (float*)take(fld32);
+        g32c = (float*)take(tab32 * nc32);
+        g32f1 = (float*)take(tab32 * NGEOM);
+        g32f2 = (float*)take(tab32 * NGEOM);
+    }
     v.gc = s.geom_c;
     v.gf1 = s.geom_f1;
     v.gf2 = s.geom_f2;
+    v.gc32 = g32c;
+    v.gf1_32 = g32f1;
+    v.gf2_32 = g32f2;
     CUDA_TRY(cudaMemset(base, 0, bytes));
     GeomArgs A;
     A.metric = g->desc.metric;
@@ -266,6 +283,11 @@ int alloc_block(hamr_grid* g, int b) {
     A.face2 = s.geom_f2;
     A.table_stride = v.n2d;
     CUDA_TRY(launch_geometry(A, 0));
+    if (mixed) {
+        CUDA_TRY(launch_table_f32(s.geom_c, g32c, nc32, v.n2d, 0));
+        CUDA_TRY(launch_table_f32(s.geom_f1, g32f1, NGEOM, v.n2d, 0));
+        CUDA_TRY(launch_table_f32(s.geom_f2, g32f2, NGEOM, v.n2d, 0));
+    }
     g->st.push_back(s);
     g->view.push_back(v);
     g->loaded.push_back(0);
@@ -412,8 +434,9 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
     LAUNCH(g, K_DT, 1, cs, launch_dt_select(ph, dt, s.dscal, s.dmax, s.dcnt, s.status, v.nc, cs));
     // predictor: P^n, B^n -> P^{n+1/2}, B^{n+1/2}
     LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.P, s.B, cs));
+    if (ph.mixed) LAUNCH(g, K_BC, 1, cs, launch_to_f32(v, s.P, s.P32, cs));
     for (int dir = 1; dir <= 3; dir++) {
-        LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.P, s.QL, s.QR, cs));
+        LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.P, s.P32, s.QL, s.QR, cs));
         LAUNCH(g, K_FLUX, 1, cs, launch_flux(v, ph, dir, s.QL, s.QR, s.B, s.F[dir - 1], cs));
     }
     LAUNCH(g, K_EMF, 1, cs, launch_emf(v, s.F, s.E, ph.mixed, cs));
@@ -422,8 +445,9 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
            launch_update(v, ph, 0, s.P, s.P, s.F, s.Bh, s.Un, s.Ph, s.status, s.dscal, 0.5, s.dmax, s.dcnt, cs));
     // corrector: U^n and the fluxes of P^{n+1/2} -> P^{n+1}, B^{n+1} (in place)
     LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.Ph, s.Bh, cs));
+    if (ph.mixed) LAUNCH(g, K_BC, 1, cs, launch_to_f32(v, s.Ph, s.P32, cs));
     for (int dir = 1; dir <= 3; dir++) {
-        LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.Ph, s.QL, s.QR, cs));
+        LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.Ph, s.P32, s.QL, s.QR, cs));
         LAUNCH(g, K_FLUX, 1, cs, launch_flux(v, ph, dir, s.QL, s.QR, s.Bh, s.F[dir - 1], cs));
     }
     LAUNCH(g, K_EMF, 1, cs, launch_emf(v, s.F, s.E, ph.mixed, cs));

@@ -203,6 +203,8 @@ __device__ __forceinline__ int c2p_finish(C2PWork& w, const double U[NCONS], con
     pr[U3] = pre * (S.Qc3 + qbw * S.Bn3);
     pr[RHO] = rho;
     pr[UU] = u;
+    w.W = W;
+    w.vsq = vsq;
     return status;
 }
 

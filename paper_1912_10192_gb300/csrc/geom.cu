@@ -33,6 +33,7 @@ __device__ void store_metric(double* __restrict__ tab, long stride, long q, cons
     tab[GI_33 * stride + q] = pole ? 0.0 : M.gi[3][3];
     tab[G_DET * stride + q] = pole ? 0.0 : M.gdet;
     tab[G_ALPHA * stride + q] = 1.0 / sqrt(-M.gi[0][0]);
+    tab[G_IALPHA * stride + q] = sqrt(-M.gi[0][0]);
 }
 
 __global__ void k_geometry(GeomArgs A) {
@@ -88,6 +89,17 @@ __global__ void k_geometry(GeomArgs A) {
 }
 
 }  // namespace
+
+__global__ void k_table_f32(const double* __restrict__ src, float* __restrict__ dst, long n) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) dst[t] = (float)src[t];
+}
+
+cudaError_t launch_table_f32(const double* src, float* dst, int nplanes, long stride, cudaStream_t s) {
+    const long n = (long)nplanes * stride;
+    k_table_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_geometry(const GeomArgs& A, cudaStream_t s) {
     const long n2d = (long)A.n1p * A.n2p;  // threads: one per (i, j) point

@@ -24,7 +24,7 @@ constexpr int NFLUX = 8;  // 6 cell-conserved slots + the two B^i with i != dir
 enum {
     G_00 = 0, G_01, G_03, G_11, G_13, G_22, G_33,  // covariant
     GI_00, GI_01, GI_11, GI_13, GI_22, GI_33,      // contravariant
-    G_DET, G_ALPHA, NGEOM
+    G_DET, G_ALPHA, G_IALPHA, NGEOM  // G_IALPHA: 1 / alpha
 };
 // centre tables append: Christoffel symbols (40 = 4 upper x 10 symmetric lower)
 // and the r-dependent floor values
@@ -45,11 +45,11 @@ template <typename T>
 struct Metric {
     T g00, g01, g03, g11, g13, g22, g33;
     T c00, c01, c11, c13, c22, c33;
-    T gdet, alpha;
+    T gdet, alpha, ialpha;
 };
 
-template <typename T>
-__device__ __forceinline__ void load_metric(const double* __restrict__ tab, long stride, long q, Metric<T>& m) {
+template <typename T, typename TT>
+__device__ __forceinline__ void load_metric(const TT* __restrict__ tab, long stride, long q, Metric<T>& m) {
     m.g00 = (T)tab[G_00 * stride + q];
     m.g01 = (T)tab[G_01 * stride + q];
     m.g03 = (T)tab[G_03 * stride + q];
@@ -65,6 +65,7 @@ __device__ __forceinline__ void load_metric(const double* __restrict__ tab, long
     m.c33 = (T)tab[GI_33 * stride + q];
     m.gdet = (T)tab[G_DET * stride + q];
     m.alpha = (T)tab[G_ALPHA * stride + q];
+    m.ialpha = (T)tab[G_IALPHA * stride + q];
 }
 
 template <typename T>
@@ -93,18 +94,23 @@ struct Fluid {
 // u^mu from utilde^i (Lorentz factor wrt the normal observer
 // Gamma = sqrt(1 + g_ij ut^i ut^j), u^t = Gamma/alpha, u^i = ut^i - Gamma alpha g^{ti});
 // b^t = B^i u_i, b^i = (B^i + b^t u^i)/u^t (Sec. 2.3).
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+
 template <typename T>
 __device__ __forceinline__ void fluid_state(const T pr[NPRIM], const Metric<T>& m, Fluid<T>& s) {
     const T q1 = pr[U1], q2 = pr[U2], q3 = pr[U3];
     T qsq = m.g11 * q1 * q1 + m.g22 * q2 * q2 + m.g33 * q3 * q3 + T(2) * m.g13 * q1 * q3;
-    T gamma = sqrt(T(1) + qsq);
-    s.ucon[0] = gamma / m.alpha;
+    const T g2 = T(1) + qsq;
+    const T ig = rsq(g2);  // 1 / Gamma
+    const T gamma = g2 * ig;
+    s.ucon[0] = gamma * m.ialpha;
     s.ucon[1] = q1 - gamma * m.alpha * m.c01;
     s.ucon[2] = q2;
     s.ucon[3] = q3;
     lower4(m, s.ucon, s.ucov);
     T bt = pr[B1] * s.ucov[1] + pr[B2] * s.ucov[2] + pr[B3] * s.ucov[3];
-    T iut = m.alpha / gamma;
+    T iut = m.alpha * ig;
     s.bcon[0] = bt;
     s.bcon[1] = (pr[B1] + bt * s.ucon[1]) * iut;
     s.bcon[2] = (pr[B2] + bt * s.ucon[2]) * iut;
@@ -139,10 +145,65 @@ __device__ __forceinline__ void flux_row(const T pr[NPRIM], const Fluid<T>& s, i
     out[7] = s.bcon[i2] * s.ucon[d] - bd * s.ucon[i2];
 }
 
+// x^y for finite x > 0 (FP64) as exp(y ln x):
+//   ln x = e ln2 + ln m from x = 2^e m, m in [1/sqrt2, sqrt2), with
+//   ln m = 2 atanh(t), t = (m - 1)/(m + 1), |t| <= 0.1716, by the odd power
+//   series of atanh to t^23 (truncation < 1e-17);
+//   exp(z) = 2^k exp(r), k = rint(z / ln2), |r| <= ln2/2, exp(r) by its Taylor
+//   series to degree 14 (truncation < 3e-18).
+// Relative error ~1e-14 (the rounding of z ~ y e ln2 dominates); other x take pow().
+__device__ __forceinline__ double pow_pos(double x, double y) {
+    const int hi = __double2hiint(x);
+    const int bexp = (hi >> 20) & 0x7FF;
+    if (x <= 0.0 || bexp == 0 || bexp == 0x7FF) return pow(x, y);  // zero, subnormal, inf, nan
+    int e = bexp - 1023;
+    double m = __hiloint2double((hi & 0x000FFFFF) | 0x3FF00000, __double2loint(x));  // [1, 2)
+    if (m > 1.4142135623730951) {
+        m *= 0.5;
+        e += 1;
+    }
+    const double t = (m - 1.0) / (m + 1.0);
+    const double t2 = t * t;
+    double a = 1.0 / 23.0;
+    a = fma(a, t2, 1.0 / 21.0);
+    a = fma(a, t2, 1.0 / 19.0);
+    a = fma(a, t2, 1.0 / 17.0);
+    a = fma(a, t2, 1.0 / 15.0);
+    a = fma(a, t2, 1.0 / 13.0);
+    a = fma(a, t2, 1.0 / 11.0);
+    a = fma(a, t2, 1.0 / 9.0);
+    a = fma(a, t2, 1.0 / 7.0);
+    a = fma(a, t2, 1.0 / 5.0);
+    a = fma(a, t2, 1.0 / 3.0);
+    a = fma(a, t2, 1.0);
+    const double ln2 = 0.6931471805599453;
+    const double z = y * fma((double)e, ln2, 2.0 * t * a);
+    if (!(fabs(z) < 700.0)) return pow(x, y);
+    const double k = rint(z * 1.4426950408889634);
+    const double r = fma(-k, ln2, z);
+    double b = 1.0 / 87178291200.0;  // 1/14!
+    b = fma(b, r, 1.0 / 6227020800.0);
+    b = fma(b, r, 1.0 / 479001600.0);
+    b = fma(b, r, 1.0 / 39916800.0);
+    b = fma(b, r, 1.0 / 3628800.0);
+    b = fma(b, r, 1.0 / 362880.0);
+    b = fma(b, r, 1.0 / 40320.0);
+    b = fma(b, r, 1.0 / 5040.0);
+    b = fma(b, r, 1.0 / 720.0);
+    b = fma(b, r, 1.0 / 120.0);
+    b = fma(b, r, 1.0 / 24.0);
+    b = fma(b, r, 1.0 / 6.0);
+    b = fma(b, r, 0.5);
+    b = fma(b, r, 1.0);
+    b = fma(b, r, 1.0);
+    return b * __hiloint2double(((int)k + 1023) << 20, 0);
+}
+__device__ __forceinline__ float pow_pos(float x, float y) { return powf(x, y); }
+
 // entropy tracer kappa = p / rho^gam
 template <typename T>
 __device__ __forceinline__ T entropy_kappa(const T pr[NPRIM], T gam) {
-    return (gam - T(1)) * pr[UU] / pow(pr[RHO], gam);
+    return (gam - T(1)) * pr[UU] / pow_pos(pr[RHO], gam);
 }
 
 // fastest magnetosonic characteristic speeds along dir (Sec. 2.1): roots of
@@ -152,9 +213,8 @@ __device__ __forceinline__ void wave_speeds(const T pr[NPRIM], const Fluid<T>& s
                                             T& vp, T& vm) {
     const T p = (gam - T(1)) * pr[UU];
     const T w = pr[RHO] + pr[UU] + p;
-    const T cs2 = gam * p / w;
-    const T va2 = s.bsq / (s.bsq + w);
-    const T c2 = va2 + cs2 * (T(1) - va2);
+    // c^2 = vA^2 + cs^2 (1 - vA^2) with vA^2 = b^2/(b^2 + w), cs^2 = gam p / w, over one denominator
+    const T c2 = (s.bsq + gam * p) / (s.bsq + w);
     const T ut = s.ucon[0], ud = s.ucon[dir];
     const T A = ut * ut - c2 * (ut * ut + m.c00);
     const T B = ut * ud - c2 * (ut * ud + gcon0(m, dir));
@@ -185,6 +245,78 @@ __device__ __forceinline__ T minmod_slope(T qm, T q0, T qp) {
     const T dl = q0 - qm, dr = qp - q0;
     if (dl * dr <= T(0)) return T(0);
     return fabs(dl) < fabs(dr) ? dl : dr;
+}
+
+// The same limiters with their sign tests and magnitude comparisons done on the
+// bit patterns (integer pipe; FP64 comparisons take the FP64 pipe). dl dr <= 0
+// becomes "opposite signs or a zero"; they differ from the products only where
+// dl dr underflows.
+template <typename T>
+struct FBits;
+template <>
+struct FBits<double> {
+    using I = long long;
+    static constexpr I MAG = 0x7FFFFFFFFFFFFFFFll;
+    static __device__ __forceinline__ I of(double x) { return __double_as_longlong(x); }
+    static __device__ __forceinline__ double from(I i) { return __longlong_as_double(i); }
+};
+template <>
+struct FBits<float> {
+    using I = int;
+    static constexpr I MAG = 0x7FFFFFFF;
+    static __device__ __forceinline__ I of(float x) { return __float_as_int(x); }
+    static __device__ __forceinline__ float from(I i) { return __int_as_float(i); }
+};
+
+// a b <= 0 (opposite signs or a zero)
+template <typename T>
+__device__ __forceinline__ bool nonpos_product(T a, T b) {
+    using B = FBits<T>;
+    const typename B::I ia = B::of(a), ib = B::of(b);
+    return ((ia ^ ib) < 0) || (ia & B::MAG) == 0 || (ib & B::MAG) == 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T mc_slope_i(T qm, T q0, T qp) {
+    using B = FBits<T>;
+    using I = typename B::I;
+    const T dl = q0 - qm, dr = qp - q0;
+    if (nonpos_product(dl, dr)) return T(0);
+    const T dc = T(0.5) * (qp - qm);
+    const I al = B::of(dl) & B::MAG, ar = B::of(dr) & B::MAG;
+    const T lim = T(2) * B::from(al < ar ? al : ar);  // 2 min(|dl|, |dr|)
+    const I ac = B::of(dc) & B::MAG, alim = B::of(lim);
+    return B::from((ac < alim ? ac : alim) | (B::of(dc) & ~B::MAG));  // min(|dc|, lim) with the sign of dc
+}
+
+template <typename T>
+__device__ __forceinline__ T minmod_slope_i(T qm, T q0, T qp) {
+    using B = FBits<T>;
+    const T dl = q0 - qm, dr = qp - q0;
+    if (nonpos_product(dl, dr)) return T(0);
+    return (B::of(dl) & B::MAG) < (B::of(dr) & B::MAG) ? dl : dr;
+}
+
+// the PPM interface value between cells with values qa, qb and slopes sa, sb
+template <typename T>
+__device__ __forceinline__ T ppm_face(T qa, T qb, T sa, T sb) {
+    return T(0.5) * (qa + qb) - (sb - sa) * T(1.0 / 6.0);
+}
+
+// the two parabola constraints of a cell with value c and edge values l, r
+template <typename T>
+__device__ __forceinline__ void ppm_limit(T c, T& l, T& r) {
+    if (nonpos_product(r - c, c - l)) {
+        l = c;
+        r = c;
+    } else {
+        const T da = r - l;
+        const T a6 = T(6) * (c - T(0.5) * (l + r));
+        if (da * a6 > da * da)
+            l = T(3) * c - T(2) * r;
+        else if (-(da * da) > da * a6)
+            r = T(3) * c - T(2) * l;
+    }
 }
 
 // PPM edge values of the centre cell of the 5-point stencil q[0..4]:

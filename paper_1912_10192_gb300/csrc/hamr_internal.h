@@ -33,6 +33,11 @@ struct BlockView {
     const double* gc;  // centre tables
     const double* gf1; // x1-face tables
     const double* gf2; // x2-face tables
+    // FP32 copies (mixed precision only, else null): centre metric + connection
+    // (NGEOM + 40 planes), face metric (NGEOM planes each); same plane stride n2d
+    const float* gc32;
+    const float* gf1_32;
+    const float* gf2_32;
 };
 
 struct PhysArgs {
@@ -47,14 +52,27 @@ struct PhysArgs {
     int mlp_mode;            // HAMR_MLP_FIRST or HAMR_MLP_RESCUE
 };
 
+// threads of one reconstruction launch: rows along x1 in warps of 32 lanes
+// that produce RECON_TILE cells each; pencils along x2 or x3 of RECON_SEG
+// cells per thread; 7 variables each
+constexpr int RECON_TILE = 28;
+constexpr int RECON_SEG = 16;
+__host__ __device__ inline long recon_threads(const BlockView& v, int dir) {
+    const long n1 = v.n1 + 2, n2 = v.n2 + 2, n3 = v.n3 + 2;
+    if (dir == 1) return ((n1 + RECON_TILE - 1) / RECON_TILE) * 32 * n2 * n3 * 7;
+    if (dir == 2) return n1 * n3 * ((n2 + RECON_SEG - 1) / RECON_SEG) * 7;
+    return n1 * n2 * ((n3 + RECON_SEG - 1) / RECON_SEG) * 7;
+}
+
 // device scratch/state of one block
 struct BlockState {
     double* P;      // 8 fields: primitives at t^n (stepped in place)
     double* B;      // 3 fields: face B at t^n (stepped in place)
     double* Ph;     // 8 fields: primitives at t^{n+1/2}
     double* Bh;     // 3 fields: face B at t^{n+1/2}
-    double* QL;     // 8 fields: left edge values of the current direction
+    double* QL;     // 8 fields: left edge values of the current direction (FP32 in mixed precision)
     double* QR;     // 8 fields: right edge values of the current direction
+    float* P32;     // mixed precision: FP32 copy of the stage's primitives (8 fields, stride nc), else null
     double* F[3];   // 8 fields each: face fluxes (x sqrt(-g)) of directions 1..3
     double* E;      // 3 fields: edge EMFs E1, E2, E3
     double* Un;     // 6 fields: U(P^n) cached by the predictor for the corrector
@@ -75,6 +93,7 @@ struct DevBlock {
     double lo[4], hi[4], h[4];  // extents and cell sizes, index 1..3
     int lat;
     double *P, *B, *Ph, *Bh, *QL, *QR, *F1, *F2, *F3, *E, *Un, *Pold, *Bold;
+    float* P32;  // mixed precision: FP32 copy of the stage's primitives
     uint8_t* status;
     double* dscal;  // [0] dt of the block's step, [1] = 1.0
     unsigned long long *dmax, *dcnt;
@@ -91,6 +110,8 @@ struct AmrDomain {
 };
 
 cudaError_t launch_geometry(const GeomArgs& A, cudaStream_t s);
+// FP32 copy of the first nplanes planes (stride `stride` elements) of a table
+cudaError_t launch_table_f32(const double* src, float* dst, int nplanes, long stride, cudaStream_t s);
 
 // api.cu: records the calling thread's last-error message and returns `code`
 int set_error(int code, const char* fmt, ...);
@@ -98,8 +119,9 @@ int set_error(int code, const char* fmt, ...);
 // step.cu
 cudaError_t launch_centre_b(const BlockView& v, double* P, const double* B, cudaStream_t s);
 cudaError_t launch_bc(const BlockView& v, double* P, double* B, cudaStream_t s);
-cudaError_t launch_recon(const BlockView& v, const PhysArgs& ph, int dir, const double* P, double* QL, double* QR,
-                         cudaStream_t s);
+cudaError_t launch_recon(const BlockView& v, const PhysArgs& ph, int dir, const double* P, const float* P32,
+                         double* QL, double* QR, cudaStream_t s);
+cudaError_t launch_to_f32(const BlockView& v, const double* P, float* P32, cudaStream_t s);
 cudaError_t launch_flux(const BlockView& v, const PhysArgs& ph, int dir, const double* QL, const double* QR,
                         const double* Bf, double* F, cudaStream_t s);
 cudaError_t launch_emf(const BlockView& v, double* const F[3], double* E, int mixed, cudaStream_t s);
@@ -118,6 +140,8 @@ cudaError_t launch_dt_select(const PhysArgs& ph, double user_dt, double* dscal, 
 cudaError_t measure_fp64_peak(cudaStream_t s, double* gflops);
 
 // step.cu, batched over the blocks list[0..nlist) of a table (sigma: 0 predictor, 1 corrector)
+cudaError_t launch_to_f32_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, int sigma,
+                                cudaStream_t s);
 cudaError_t launch_recon_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
                                int dir, int sigma, cudaStream_t s);
 cudaError_t launch_flux_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,

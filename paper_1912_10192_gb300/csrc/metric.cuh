@@ -70,6 +70,7 @@ __device__ inline void to_sparse(const FullMetric& M, Metric<double>& m) {
     m.c33 = M.gi[3][3];
     m.gdet = M.gdet;
     m.alpha = 1.0 / sqrt(-M.gi[0][0]);
+    m.ialpha = sqrt(-M.gi[0][0]);
 }
 
 }  // namespace hamr

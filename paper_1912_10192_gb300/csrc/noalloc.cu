@@ -183,7 +183,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     // predictor
     NA_TRY(launch_bc(v, s.P, s.B, cs));
     for (int dir = 1; dir <= 3; dir++) {
-        NA_TRY(launch_recon(v, ph, dir, s.P, s.QL, s.QR, cs));
+        NA_TRY(launch_recon(v, ph, dir, s.P, nullptr, s.QL, s.QR, cs));
         NA_TRY(launch_flux(v, ph, dir, s.QL, s.QR, s.B, s.F[dir - 1], cs));
     }
     NA_TRY(launch_emf(v, s.F, s.E, ph.mixed, cs));
@@ -192,7 +192,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     // corrector
     NA_TRY(launch_bc(v, s.Ph, s.Bh, cs));
     for (int dir = 1; dir <= 3; dir++) {
-        NA_TRY(launch_recon(v, ph, dir, s.Ph, s.QL, s.QR, cs));
+        NA_TRY(launch_recon(v, ph, dir, s.Ph, nullptr, s.QL, s.QR, cs));
         NA_TRY(launch_flux(v, ph, dir, s.QL, s.QR, s.Bh, s.F[dir - 1], cs));
     }
     NA_TRY(launch_emf(v, s.F, s.E, ph.mixed, cs));

@@ -132,53 +132,153 @@ __global__ void k_bc_axis(BlockView v, double* __restrict__ B) {
 }
 
 // ---------------------------------------------------------------- reconstruction
-// edge values of every cell that borders a flux face of direction dir:
-// cells -1..n_dir along dir, -1..n_e across.
-template <int DIR, typename T>
-__device__ __forceinline__ void b_recon(const BlockView& v, PhysArgs ph, const double* __restrict__ P, double* __restrict__ QL,
-                        double* __restrict__ QR, long t) {
-    const int nn[4] = {0, v.n1, v.n2, v.n3};
-    const int e1 = nn[1] + 2, e2 = nn[2] + 2, e3 = nn[3] + 2;
-    if (t >= (long)e1 * e2 * e3) return;
-    const int i = (int)(t % e1) - 1, j = (int)((t / e1) % e2) - 1, k = (int)(t / ((long)e1 * e2)) - 1;
-    const long c = cidx(v, i, j, k);
-    const long st = (DIR == 1) ? 1 : ((DIR == 2) ? (long)v.n1p : (long)v.n1p * v.n2p);
-#pragma unroll
-    for (int q = 0; q < NPRIM; q++) {
-        if (q == B1 + DIR - 1) continue;
-        const double* p = P + q * v.nc + c;
-        // FP32: the stencil is taken relative to the cell value (differences formed in FP64),
-        // so rounding scales with the local variation, not with the value itself.
-        constexpr bool dev = !std::is_same<T, double>::value;
-        const double base = dev ? p[0] : 0.0;
-        auto at = [&](long o) -> T { return dev ? (T)(p[o] - base) : (T)p[o]; };
-        T l, r;
-        if (ph.recon == HAMR_RECON_PPM) {
-            const T s[5] = {at(-2 * st), at(-st), at(0), at(st), at(2 * st)};
-            ppm_cell(s, l, r);
-        } else {
-            const T qm = at(-st), q0 = at(0), qp = at(st);
-            const T dq = (ph.recon == HAMR_RECON_MC) ? mc_slope(qm, q0, qp) : minmod_slope(qm, q0, qp);
-            l = q0 - T(0.5) * dq;
-            r = q0 + T(0.5) * dq;
-        }
-        QL[q * v.nc + c] = dev ? base + (double)l : (double)l;
-        QR[q * v.nc + c] = dev ? base + (double)r : (double)r;
+// Edge values of every cell that borders a flux face of direction dir: cells
+// -1..n_dir along dir, -1..n_e across, for the 7 primitives other than B^dir.
+// Every slope and every PPM interface value is formed once and shared by the
+// two cells that use it: along x1 a warp holds 32 consecutive cells (28 of
+// them produced) and passes values between lanes by shuffles; along x2 and
+// x3 a thread sweeps RECON_SEG cells of one pencil (consecutive threads on
+// consecutive i, so loads and stores coalesce). T = float (mixed precision)
+// reads the FP32 copy of the primitives and writes FP32 edge values.
+template <int DIR>
+__device__ __forceinline__ int recon_var(int n) {  // the n-th of the 7 reconstructed primitives
+    return n + (n >= B1 + DIR - 1 ? 1 : 0);
+}
+
+template <typename T>
+__device__ __forceinline__ T limited_slope(int recon, T qm, T q0, T qp) {
+    return (recon == HAMR_RECON_MC) ? mc_slope_i(qm, q0, qp) : minmod_slope_i(qm, q0, qp);
+}
+
+template <typename T>
+__device__ __forceinline__ void b_recon_row(const BlockView& v, PhysArgs ph, const T* __restrict__ P,
+                                            T* __restrict__ QL, T* __restrict__ QR, long t) {
+    const int n2 = v.n2 + 2, n3 = v.n3 + 2;
+    const int ntile = (v.n1 + 2 + RECON_TILE - 1) / RECON_TILE;
+    const long w = t >> 5;  // whole warps leave or stay together
+    if (w >= (long)ntile * n2 * n3 * 7) return;
+    const int lane = (int)(t & 31);
+    const int tile = (int)(w % ntile);
+    long rest = w / ntile;
+    const int j = (int)(rest % n2) - 1;
+    rest /= n2;
+    const int k = (int)(rest % n3) - 1;
+    const int q = recon_var<1>((int)(rest / n3));
+    const int i = RECON_TILE * tile - 3 + lane;               // lanes 2..29 produce cells tile*28-1 .. +27
+    const int ic = min(max(i, -NG), v.n1 + NG - 1);           // loads stay inside the padded row
+    const long c = cidx(v, 0, j, k);
+    const T qc = P[q * v.nc + c + ic];
+    const T qm = __shfl_up_sync(0xffffffffu, qc, 1);
+    const T qp = __shfl_down_sync(0xffffffffu, qc, 1);
+    T l, r;
+    if (ph.recon == HAMR_RECON_PPM) {
+        const T sc = mc_slope_i(qm, qc, qp);                  // valid on lanes 1..30
+        const T sp = __shfl_down_sync(0xffffffffu, sc, 1);
+        r = ppm_face(qc, qp, sc, sp);                         // interface i+1/2, valid on lanes 1..29
+        l = __shfl_up_sync(0xffffffffu, r, 1);                // interface i-1/2, valid on lanes 2..30
+        ppm_limit(qc, l, r);
+    } else {
+        const T dq = limited_slope(ph.recon, qm, qc, qp);
+        l = qc - T(0.5) * dq;
+        r = qc + T(0.5) * dq;
+    }
+    if (lane >= 2 && lane <= 29 && i <= v.n1) {
+        QL[q * v.nc + c + i] = l;
+        QR[q * v.nc + c + i] = r;
     }
 }
 
 template <int DIR, typename T>
-__global__ void k_recon(BlockView v, PhysArgs ph, const double* __restrict__ P, double* __restrict__ QL,
-                        double* __restrict__ QR) {
+__device__ __forceinline__ void b_recon_sweep(const BlockView& v, PhysArgs ph, const T* __restrict__ P,
+                                              T* __restrict__ QL, T* __restrict__ QR, long t) {
+    const int na = (DIR == 2 ? v.n2 : v.n3) + 2;  // cells along the sweep: -1..n_dir
+    const int nseg = (na + RECON_SEG - 1) / RECON_SEG;
+    const int n1 = v.n1 + 2, no = (DIR == 2 ? v.n3 : v.n2) + 2;
+    if (t >= (long)n1 * no * nseg * 7) return;
+    const int i = (int)(t % n1) - 1;
+    long rest = t / n1;
+    const int o = (int)(rest % no) - 1;
+    rest /= no;
+    const int seg = (int)(rest % nseg);
+    const int q = recon_var<DIR>((int)(rest / nseg));
+    const long st = (DIR == 2) ? (long)v.n1p : (long)v.n1p * v.n2p;
+    const int a0 = seg * RECON_SEG - 1;
+    const int ncell = min(RECON_SEG, na - 1 - a0);           // cells a0 .. a0 + ncell - 1 (<= n_dir)
+    const long c0 = q * v.nc + ((DIR == 2) ? cidx(v, i, a0, o) : cidx(v, i, o, a0));
+    const T* p = P + c0;
+    if (ph.recon == HAMR_RECON_PPM) {
+        T qm = p[-st], qc = p[0], qp = p[st];
+        T sm = mc_slope_i(p[-2 * st], qm, qc);
+        T sc = mc_slope_i(qm, qc, qp);
+        T fl = ppm_face(qm, qc, sm, sc);  // interface a0 - 1/2
+        for (int m = 0; m < ncell; m++) {
+            const T qpp = p[(m + 2) * st];
+            const T sp = mc_slope_i(qc, qp, qpp);
+            const T fr = ppm_face(qc, qp, sc, sp);  // interface a + 1/2
+            T l = fl, r = fr;
+            ppm_limit(qc, l, r);
+            QL[c0 + m * st] = l;
+            QR[c0 + m * st] = r;
+            qc = qp;
+            qp = qpp;
+            sc = sp;
+            fl = fr;
+        }
+    } else {
+        T qm = p[-st], qc = p[0];
+        for (int m = 0; m < ncell; m++) {
+            const T qp = p[(m + 1) * st];
+            const T dq = limited_slope(ph.recon, qm, qc, qp);
+            QL[c0 + m * st] = qc - T(0.5) * dq;
+            QR[c0 + m * st] = qc + T(0.5) * dq;
+            qm = qc;
+            qc = qp;
+        }
+    }
+}
+
+template <int DIR, typename T>
+__device__ __forceinline__ void b_recon(const BlockView& v, PhysArgs ph, const T* __restrict__ P, T* __restrict__ QL,
+                                        T* __restrict__ QR, long t) {
+    if constexpr (DIR == 1)
+        b_recon_row(v, ph, P, QL, QR, t);
+    else
+        b_recon_sweep<DIR>(v, ph, P, QL, QR, t);
+}
+
+template <int DIR, typename T>
+__global__ void k_recon(BlockView v, PhysArgs ph, const T* __restrict__ P, T* __restrict__ QL, T* __restrict__ QR) {
     b_recon<DIR, T>(v, ph, P, QL, QR, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// FP32 copy of the 8 primitive fields over the whole padded block (mixed precision)
+__device__ __forceinline__ void b_to_f32(const BlockView& v, const double* __restrict__ P, float* __restrict__ P32,
+                                         long t) {
+    const long n = (long)v.n1p * v.n2p * v.n3p;
+    if (t >= n) return;
+#pragma unroll
+    for (int q = 0; q < NPRIM; q++) P32[q * v.nc + t] = (float)P[q * v.nc + t];
+}
+
+__global__ void k_to_f32(BlockView v, const double* __restrict__ P, float* __restrict__ P32) {
+    b_to_f32(v, P, P32, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// the tables a face flux of direction DIR reads, in the flux precision
+template <int DIR, typename T>
+__device__ __forceinline__ const T* face_table(const BlockView& v) {
+    if constexpr (std::is_same<T, double>::value)
+        return (DIR == 1) ? v.gf1 : ((DIR == 2) ? v.gf2 : v.gc);
+    else
+        return (DIR == 1) ? v.gf1_32 : ((DIR == 2) ? v.gf2_32 : v.gc32);
 }
 
 
 // ---------------------------------------------------------------- fluxes
 // HLLE (or LLF) flux through every dir-face: faces 0..n_dir, -1..n_e across.
 template <int DIR, typename T>
-__device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const double* __restrict__ QL,
-                                             const double* __restrict__ QR, const double* __restrict__ Bf,
+__device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const T* __restrict__ QL,
+                                             const T* __restrict__ QR, const double* __restrict__ Bf,
                                              double* __restrict__ F, long t) {
     const int nn[4] = {0, v.n1, v.n2, v.n3};
     const int e1 = (DIR == 1) ? nn[1] + 1 : nn[1] + 2;
@@ -190,9 +290,8 @@ __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const do
     const int k = (int)(t / ((long)e1 * e2)) - (DIR == 3 ? 0 : 1);
     const long c = cidx(v, i, j, k);
     const long st = (DIR == 1) ? 1 : ((DIR == 2) ? (long)v.n1p : (long)v.n1p * v.n2p);
-    const double* tab = (DIR == 1) ? v.gf1 : ((DIR == 2) ? v.gf2 : v.gc);
     Metric<T> m;
-    load_metric(tab, v.n2d, gidx(v, i, j), m);
+    load_metric(face_table<DIR, T>(v), v.n2d, gidx(v, i, j), m);
     if (m.gdet == T(0)) {  // face on the polar axis: no area
 #pragma unroll
         for (int q = 0; q < NFLUX; q++) F[q * v.nc + c] = 0.0;
@@ -202,8 +301,8 @@ __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const do
 #pragma unroll
     for (int q = 0; q < NPRIM; q++) {
         if (q == B1 + DIR - 1) continue;
-        pl[q] = (T)QR[q * v.nc + c - st];
-        pr[q] = (T)QL[q * v.nc + c];
+        pl[q] = QR[q * v.nc + c - st];
+        pr[q] = QL[q * v.nc + c];
     }
     const T bn = (T)Bf[(DIR - 1) * v.nc + c] / m.gdet;
     pl[B1 + DIR - 1] = bn;
@@ -248,8 +347,8 @@ __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const do
 }
 
 template <int DIR, typename T>
-__global__ void __launch_bounds__(BS) k_flux(BlockView v, PhysArgs ph, const double* __restrict__ QL,
-                                             const double* __restrict__ QR, const double* __restrict__ Bf,
+__global__ void __launch_bounds__(BS) k_flux(BlockView v, PhysArgs ph, const T* __restrict__ QL,
+                                             const T* __restrict__ QR, const double* __restrict__ Bf,
                                              double* __restrict__ F) {
     b_flux<DIR, T>(v, ph, QL, QR, Bf, F, (long)blockIdx.x * blockDim.x + threadIdx.x);
 }
@@ -339,18 +438,66 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
 }
 
 // sum_i v_f^i / dx^i at a cell centre (Sec. 2.1 CFL condition)
-__device__ __forceinline__ double inv_dt_cell(const BlockView& v, const double pr[NPRIM], const Metric<double>& m,
-                                              double gam) {
-    Fluid<double> s;
+template <typename T>
+__device__ __forceinline__ double inv_dt_cell(const BlockView& v, const T pr[NPRIM], const Metric<T>& m, T gam) {
+    Fluid<T> s;
     fluid_state(pr, m, s);
-    double vp, vm, inv = 0.0;
+    T vp, vm, inv = T(0);
     wave_speeds(pr, s, m, 1, gam, vp, vm);
-    inv += fmax(fabs(vp), fabs(vm)) * v.idx1;
+    inv += fmax(fabs(vp), fabs(vm)) * (T)v.idx1;
     wave_speeds(pr, s, m, 2, gam, vp, vm);
-    inv += fmax(fabs(vp), fabs(vm)) * v.idx2;
+    inv += fmax(fabs(vp), fabs(vm)) * (T)v.idx2;
     wave_speeds(pr, s, m, 3, gam, vp, vm);
-    inv += fmax(fabs(vp), fabs(vm)) * v.idx3;
-    return inv;
+    inv += fmax(fabs(vp), fabs(vm)) * (T)v.idx3;
+    return (double)inv;
+}
+
+// the rate of a cell in precision T from its (FP64) primitives
+template <typename T>
+__device__ __forceinline__ double inv_dt_at(const BlockView& v, const double pr[NPRIM], const Metric<double>& m,
+                                            long g, double gam) {
+    if constexpr (std::is_same<T, double>::value) {
+        return inv_dt_cell(v, pr, m, gam);
+    } else {
+        Metric<float> mf;
+        load_metric(v.gc32, v.n2d, g, mf);
+        float pf[NPRIM];
+#pragma unroll
+        for (int q = 0; q < NPRIM; q++) pf[q] = (float)pr[q];
+        return inv_dt_cell(v, pf, mf, (float)gam);
+    }
+}
+
+// source sqrt(-g) T^k_l Gamma^l_{nu k} at a cell centre in precision T
+// (tables gc: metric and connection planes of that precision)
+template <typename T, typename TT>
+__device__ __forceinline__ void source_q(const TT* __restrict__ gc, long n2d, long g, const Metric<T>& m,
+                                        const double pfd[NPRIM], double gam_d, double Q[4]) {
+    T pf[NPRIM];
+#pragma unroll
+    for (int q = 0; q < NPRIM; q++) pf[q] = (T)pfd[q];
+    const T gam = (T)gam_d;
+    Fluid<T> s;
+    fluid_state(pf, m, s);
+    const T p = (gam - T(1)) * pf[UU];
+    const T eta = pf[RHO] + pf[UU] + p + s.bsq;
+    const T ptot = p + T(0.5) * s.bsq;
+    T Tm[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++)
+            Tm[a][b] = eta * s.ucon[a] * s.ucov[b] - s.bcon[a] * s.bcov[b] + ((a == b) ? ptot : T(0));
+    const TT* cn = gc + (long)C_CONN * n2d + g;
+#pragma unroll
+    for (int nu = 0; nu < 4; nu++) {
+        T acc = T(0);
+#pragma unroll
+        for (int l = 0; l < 4; l++)
+#pragma unroll
+            for (int kk = 0; kk < 4; kk++) acc += Tm[kk][l] * (T)cn[(l * 10 + sym(nu, kk)) * n2d];
+        Q[nu] = (double)(acc * m.gdet);
+    }
 }
 
 // ---------------------------------------------------------------- cell update
@@ -358,7 +505,9 @@ __device__ __forceinline__ double inv_dt_cell(const BlockView& v, const double p
 // the corrector also reduces the CFL rate of the new state.
 // MLP: the CTA's 128 cells first run the learned guess (mlp.cuh) on the
 // tensor cores; Newton starts from it, with the start from Pf as fallback.
-template <bool MLP>
+// TS: precision of the connection source and of the CFL rate (float in mixed
+// precision; the conserved accumulation and the inversion are FP64 always).
+template <bool MLP, typename TS>
 __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int corrector, const double* Pb,
                                                const double* __restrict__ Pf, const double* __restrict__ F1,
                                                const double* __restrict__ F2, const double* __restrict__ F3,
@@ -409,28 +558,12 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
         for (int q = 0; q < NPRIM; q++) pf[q] = Pf[q * nc + c];
         // source sqrt(-g) T^k_l Gamma^l_{nu k} at the centre, from Pf
         double Q[4];
-        {
-            Fluid<double> s;
-            fluid_state(pf, m, s);
-            const double p = (gam - 1.0) * pf[UU];
-            const double eta = pf[RHO] + pf[UU] + p + s.bsq;
-            const double ptot = p + 0.5 * s.bsq;
-            double T[4][4];
-#pragma unroll
-            for (int a = 0; a < 4; a++)
-#pragma unroll
-                for (int b = 0; b < 4; b++)
-                    T[a][b] = eta * s.ucon[a] * s.ucov[b] - s.bcon[a] * s.bcov[b] + ((a == b) ? ptot : 0.0);
-            const double* cn = v.gc + (long)C_CONN * v.n2d + g;
-#pragma unroll
-            for (int nu = 0; nu < 4; nu++) {
-                double acc = 0.0;
-#pragma unroll
-                for (int l = 0; l < 4; l++)
-#pragma unroll
-                    for (int kk = 0; kk < 4; kk++) acc += T[kk][l] * cn[(l * 10 + sym(nu, kk)) * v.n2d];
-                Q[nu] = acc * m.gdet;
-            }
+        if constexpr (std::is_same<TS, double>::value) {
+            source_q(v.gc, v.n2d, g, m, pf, gam, Q);
+        } else {
+            Metric<float> mf;
+            load_metric(v.gc32, v.n2d, g, mf);
+            source_q(v.gc32, v.n2d, g, mf, pf, gam, Q);
         }
         const double dts = dscal[0] * fac;
         const long sj = v.n1p, sk = (long)v.n1p * v.n2p;
@@ -478,10 +611,13 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
         st = c2p_finish(w, U, m, gam, pr);
         uint8_t sb = (st == INV_ENTROPY) ? ST_ENTROPY : ((st == INV_FAIL) ? ST_FAIL : 0);
         if (ph.floors) {
+            // b^2 of the returned primitives (the inversion's own (W, v^2) would differ from it by the
+            // Newton tolerance, and by more where v^2 was clamped, and the floor rho = b^2/50 carries that)
             Fluid<double> s;
             fluid_state(pr, m, s);
-            const double rf = fmax(v.gc[C_RHOFLR * v.n2d + g], s.bsq * (1.0 / 50.0));
-            const double uf = fmax(v.gc[C_UFLR * v.n2d + g], s.bsq * (1.0 / 750.0));
+            const double bsq = s.bsq;
+            const double rf = fmax(v.gc[C_RHOFLR * v.n2d + g], bsq * (1.0 / 50.0));
+            const double uf = fmax(v.gc[C_UFLR * v.n2d + g], bsq * (1.0 / 750.0));
             if (pr[RHO] < rf) {
                 pr[RHO] = rf;
                 fl = 1;
@@ -495,7 +631,7 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
 #pragma unroll
         for (int q = 0; q < NPRIM; q++) Po[q * v.nc + c] = pr[q];
         status[c] |= sb;
-        if (corrector == 1) inv = inv_dt_cell(v, pr, m, gam);
+        if (corrector == 1) inv = inv_dt_at<TS>(v, pr, m, g, gam);
     }
     // warp-aggregated counters and CFL max
     const unsigned lane = threadIdx.x & 31u;
@@ -515,15 +651,15 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
     }
 }
 
-template <bool MLP>
+template <bool MLP, typename TS>
 __global__ void __launch_bounds__(BS) k_update(BlockView v, PhysArgs ph, int corrector, const double* Pb,
                                                const double* __restrict__ Pf, const double* __restrict__ F1,
                                                const double* __restrict__ F2, const double* __restrict__ F3,
                                                const double* __restrict__ Bn, double* Un, double* Po,
                                                uint8_t* __restrict__ status, const double* __restrict__ dscal,
                                                double fac, unsigned long long* dmax, unsigned long long* dcnt) {
-    b_update<MLP>(v, ph, corrector, Pb, Pf, F1, F2, F3, Bn, Un, Po, status, dscal, fac, dmax, dcnt,
-                  (long)blockIdx.x * blockDim.x + threadIdx.x);
+    b_update<MLP, TS>(v, ph, corrector, Pb, Pf, F1, F2, F3, Bn, Un, Po, status, dscal, fac, dmax, dcnt,
+                      (long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 
@@ -568,14 +704,23 @@ __device__ __forceinline__ long tidx() { return (long)blockIdx.x * blockDim.x + 
 template <int DIR, typename T>
 __global__ void kb_recon(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
     const DevBlock& D = tab[list[blockIdx.y]];
-    b_recon<DIR, T>(D.v, ph, sigma ? D.Ph : D.P, D.QL, D.QR, tidx());
+    if constexpr (std::is_same<T, double>::value)
+        b_recon<DIR, T>(D.v, ph, sigma ? D.Ph : D.P, D.QL, D.QR, tidx());
+    else  // the FP32 copy holds the stage's state
+        b_recon<DIR, T>(D.v, ph, D.P32, reinterpret_cast<float*>(D.QL), reinterpret_cast<float*>(D.QR), tidx());
+}
+
+__global__ void kb_to_f32(const DevBlock* tab, const int* list, int sigma) {
+    const DevBlock& D = tab[list[blockIdx.y]];
+    b_to_f32(D.v, sigma ? D.Ph : D.P, D.P32, tidx());
 }
 
 template <int DIR, typename T>
 __global__ void __launch_bounds__(BS) kb_flux(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
     const DevBlock& D = tab[list[blockIdx.y]];
     double* F = (DIR == 1) ? D.F1 : ((DIR == 2) ? D.F2 : D.F3);
-    b_flux<DIR, T>(D.v, ph, D.QL, D.QR, sigma ? D.Bh : D.B, F, tidx());
+    b_flux<DIR, T>(D.v, ph, reinterpret_cast<const T*>(D.QL), reinterpret_cast<const T*>(D.QR), sigma ? D.Bh : D.B, F,
+                   tidx());
 }
 
 template <typename T>
@@ -594,15 +739,12 @@ __global__ void kb_ct(const DevBlock* tab, const int* list, int sigma) {
         b_ct(D.v, D.E, D.B, D.B, D.dscal + 1, 1.0, tidx());
 }
 
-template <bool MLP>
-__global__ void __launch_bounds__(BS) kb_update(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
+template <bool MLP, typename TS>
+__global__ void __launch_bounds__(BS, 3) kb_update(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
     const DevBlock& D = tab[list[blockIdx.y]];
-    if (sigma == 0)
-        b_update<MLP>(D.v, ph, 0, D.P, D.P, D.F1, D.F2, D.F3, D.Bh, D.Un, D.Ph, D.status, D.dscal, 0.5, D.dmax,
-                      D.dcnt, tidx());
-    else
-        b_update<MLP>(D.v, ph, 2, D.P, D.Ph, D.F1, D.F2, D.F3, D.B, D.Un, D.P, D.status, D.dscal, 1.0, D.dmax,
-                      D.dcnt, tidx());
+    const bool c = sigma != 0;  // predictor (0) or corrector (2, no CFL rate here) of the block's step
+    b_update<MLP, TS>(D.v, ph, c ? 2 : 0, D.P, c ? D.Ph : D.P, D.F1, D.F2, D.F3, c ? D.B : D.Bh, D.Un, c ? D.P : D.Ph,
+                      D.status, D.dscal, c ? 1.0 : 0.5, D.dmax, D.dcnt, tidx());
 }
 
 __global__ void kb_dt_reduce(const DevBlock* tab, const int* list, PhysArgs ph) {
@@ -714,13 +856,15 @@ cudaError_t launch_bc(const BlockView& v, double* P, double* B, cudaStream_t s) 
     return cudaGetLastError();
 }
 
-cudaError_t launch_recon(const BlockView& v, const PhysArgs& ph, int dir, const double* P, double* QL, double* QR,
-                         cudaStream_t s) {
-    const long n = (long)(v.n1 + 2) * (v.n2 + 2) * (v.n3 + 2);
+cudaError_t launch_recon(const BlockView& v, const PhysArgs& ph, int dir, const double* P, const float* P32,
+                         double* QL, double* QR, cudaStream_t s) {
+    const long n = recon_threads(v, dir);
     if (ph.mixed) {
-        if (dir == 1) k_recon<1, float><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
-        if (dir == 2) k_recon<2, float><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
-        if (dir == 3) k_recon<3, float><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
+        float* L = reinterpret_cast<float*>(QL);
+        float* R = reinterpret_cast<float*>(QR);
+        if (dir == 1) k_recon<1, float><<<nblk(n), BS, 0, s>>>(v, ph, P32, L, R);
+        if (dir == 2) k_recon<2, float><<<nblk(n), BS, 0, s>>>(v, ph, P32, L, R);
+        if (dir == 3) k_recon<3, float><<<nblk(n), BS, 0, s>>>(v, ph, P32, L, R);
     } else {
         if (dir == 1) k_recon<1, double><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
         if (dir == 2) k_recon<2, double><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
@@ -729,14 +873,21 @@ cudaError_t launch_recon(const BlockView& v, const PhysArgs& ph, int dir, const 
     return cudaGetLastError();
 }
 
+cudaError_t launch_to_f32(const BlockView& v, const double* P, float* P32, cudaStream_t s) {
+    k_to_f32<<<nblk((long)v.n1p * v.n2p * v.n3p), BS, 0, s>>>(v, P, P32);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_flux(const BlockView& v, const PhysArgs& ph, int dir, const double* QL, const double* QR,
                         const double* Bf, double* F, cudaStream_t s) {
     const long n1 = v.n1 + (dir == 1 ? 1 : 2), n2 = v.n2 + (dir == 2 ? 1 : 2), n3 = v.n3 + (dir == 3 ? 1 : 2);
     const long n = n1 * n2 * n3;
     if (ph.mixed) {
-        if (dir == 1) k_flux<1, float><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
-        if (dir == 2) k_flux<2, float><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
-        if (dir == 3) k_flux<3, float><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
+        const float* L = reinterpret_cast<const float*>(QL);
+        const float* R = reinterpret_cast<const float*>(QR);
+        if (dir == 1) k_flux<1, float><<<nblk(n), BS, 0, s>>>(v, ph, L, R, Bf, F);
+        if (dir == 2) k_flux<2, float><<<nblk(n), BS, 0, s>>>(v, ph, L, R, Bf, F);
+        if (dir == 3) k_flux<3, float><<<nblk(n), BS, 0, s>>>(v, ph, L, R, Bf, F);
     } else {
         if (dir == 1) k_flux<1, double><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
         if (dir == 2) k_flux<2, double><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
@@ -766,12 +917,18 @@ cudaError_t launch_update(const BlockView& v, const PhysArgs& ph, int corrector,
                           uint8_t* status, const double* dscal, double dt_factor, unsigned long long* dmax,
                           unsigned long long* dcnt, cudaStream_t s) {
     const long n = (long)v.n1 * v.n2 * v.n3;
-    if (ph.mlp_img)
-        k_update<true><<<nblk(n), BS, MLP_SMEM_BYTES, s>>>(v, ph, corrector, Pbase, Pflux, F[0], F[1], F[2], Bnew, Un,
-                                                           Pout, status, dscal, dt_factor, dmax, dcnt);
+    const unsigned nb = nblk(n);
+    const int sm = ph.mlp_img ? MLP_SMEM_BYTES : 0;
+#define HAMR_UPD_ARGS v, ph, corrector, Pbase, Pflux, F[0], F[1], F[2], Bnew, Un, Pout, status, dscal, dt_factor, dmax, dcnt
+    if (ph.mlp_img && ph.mixed)
+        k_update<true, float><<<nb, BS, sm, s>>>(HAMR_UPD_ARGS);
+    else if (ph.mlp_img)
+        k_update<true, double><<<nb, BS, sm, s>>>(HAMR_UPD_ARGS);
+    else if (ph.mixed)
+        k_update<false, float><<<nb, BS, 0, s>>>(HAMR_UPD_ARGS);
     else
-        k_update<false><<<nblk(n), BS, 0, s>>>(v, ph, corrector, Pbase, Pflux, F[0], F[1], F[2], Bnew, Un, Pout,
-                                               status, dscal, dt_factor, dmax, dcnt);
+        k_update<false, double><<<nb, BS, 0, s>>>(HAMR_UPD_ARGS);
+#undef HAMR_UPD_ARGS
     return cudaGetLastError();
 }
 
@@ -805,6 +962,13 @@ cudaError_t launch_recon_batch(const DevBlock* tab, const int* list, int nlist, 
         if (dir == 2) kb_recon<2, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
         if (dir == 3) kb_recon<3, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, int sigma,
+                                cudaStream_t s) {
+    if (nlist <= 0) return cudaSuccess;
+    kb_to_f32<<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, sigma);
     return cudaGetLastError();
 }
 
@@ -843,10 +1007,16 @@ cudaError_t launch_ct_batch(const DevBlock* tab, const int* list, int nlist, lon
 cudaError_t launch_update_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
                                 int sigma, cudaStream_t s) {
     if (nlist <= 0) return cudaSuccess;
-    if (ph.mlp_img)
-        kb_update<true><<<bgrid(maxwork, nlist), BS, MLP_SMEM_BYTES, s>>>(tab, list, ph, sigma);
+    const dim3 gr = bgrid(maxwork, nlist);
+    const int sm = ph.mlp_img ? MLP_SMEM_BYTES : 0;
+    if (ph.mlp_img && ph.mixed)
+        kb_update<true, float><<<gr, BS, sm, s>>>(tab, list, ph, sigma);
+    else if (ph.mlp_img)
+        kb_update<true, double><<<gr, BS, sm, s>>>(tab, list, ph, sigma);
+    else if (ph.mixed)
+        kb_update<false, float><<<gr, BS, 0, s>>>(tab, list, ph, sigma);
     else
-        kb_update<false><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
+        kb_update<false, double><<<gr, BS, 0, s>>>(tab, list, ph, sigma);
     return cudaGetLastError();
 }
 

@@ -130,7 +130,9 @@ def test_mixed_keeps_div_b_at_fp64_roundoff():
 
 
 def test_disk_fp64_parity_with_oracle():
-    """The tilted-disk state through the FP64 path: the 1e-12 bar of the FP64 parity tests."""
+    """The tilted-disk state through the FP64 path: the 1e-12 bar of the FP64 parity tests, except
+    u_g, which the cold disk holds as a remainder of the total energy (kinetic / thermal ~
+    (h/r)^-2 ~ 1e3): its relative rounding is that much larger, bar 1e-11."""
     _, d, prim, bf = disk_case(56, 24, 48)
     p, b, used = run_gpu(d, prim, bf, 1, precision=0)
     og = O.Grid(d)
@@ -141,7 +143,7 @@ def test_disk_fp64_parity_with_oracle():
     e = errors(d, p, b, po, bo)
     print("FP64 vs oracle, tilted disk 56x24x48, 1 step:", e)
     for k, v in e.items():
-        assert v <= 1e-12, (k, v, e)
+        assert v <= (1e-11 if k == "u" else 1e-12), (k, v, e)
 
 
 def test_mixed_vs_oracle_disk_small():
