@@ -47,9 +47,10 @@ FLOPS_PER_ZONE_CYCLE = 4549.7    # one cell, one full step
 # Peaks. FP64: nominal GB300 rate (the profiling recipe's 1.25 TFLOP/s); the
 # FMA rate measured by hamr_measure_fp64_peak is reported beside it.
 FP64_NOMINAL_TFLOPS = 1.25
-# DRAM bytes per launch of the dominant kernel from one ncu capture of this
-# build (profiles/flux_torus256.md); None until captured for this build.
-NCU_TRAFFIC_PER_LAUNCH = None  # set from profiles/flux_torus256.md once captured for this build
+# DRAM bytes per launch of the dominant kernel group, from one ncu capture
+# of this build's x1-face flux kernel (the x2 and x3 kernels move the same
+# field sizes).
+NCU_TRAFFIC_PER_LAUNCH = 392.2e6
 
 
 def env_rank():

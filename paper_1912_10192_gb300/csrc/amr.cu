@@ -1014,7 +1014,7 @@ int amr_create(AmrImpl** out, const hamr_grid_desc& d, const std::vector<BlockVi
         const long cel = (long)v.n1 * v.n2 * v.n3;
         M->lmw_pad[L] = std::max(M->lmw_pad[L], pad);
         for (int dir = 1; dir <= 3; dir++)
-            M->lmw_recon[L][dir] = std::max(M->lmw_recon[L][dir], recon_threads(v, dir));
+            M->lmw_recon[L][dir] = std::max(M->lmw_recon[L][dir], recon_threads(v, dir, ph.mixed));
         M->lmw_edge[L] = std::max(M->lmw_edge[L], edg);
         M->lmw_cell[L] = std::max(M->lmw_cell[L], cel);
         M->lmw_flux[L][1] = std::max(M->lmw_flux[L][1], (long)(v.n1 + 1) * (v.n2 + 2) * (v.n3 + 2));

@@ -52,13 +52,14 @@ struct PhysArgs {
     int mlp_mode;            // HAMR_MLP_FIRST or HAMR_MLP_RESCUE
 };
 
-// threads of one reconstruction launch: rows along x1 in warps of 32 lanes
-// that produce RECON_TILE cells each; pencils along x2 or x3 of RECON_SEG
-// cells per thread; 7 variables each
+// threads of one reconstruction launch (FP64): rows along x1 in warps of 32
+// lanes that produce RECON_TILE cells each; pencils along x2 or x3 of
+// RECON_SEG cells per thread; 7 variables each. FP32: one thread per cell.
 constexpr int RECON_TILE = 28;
 constexpr int RECON_SEG = 16;
-__host__ __device__ inline long recon_threads(const BlockView& v, int dir) {
+__host__ __device__ inline long recon_threads(const BlockView& v, int dir, int fp32) {
     const long n1 = v.n1 + 2, n2 = v.n2 + 2, n3 = v.n3 + 2;
+    if (fp32) return n1 * n2 * n3;  // one thread per cell
     if (dir == 1) return ((n1 + RECON_TILE - 1) / RECON_TILE) * 32 * n2 * n3 * 7;
     if (dir == 2) return n1 * n3 * ((n2 + RECON_SEG - 1) / RECON_SEG) * 7;
     return n1 * n2 * ((n3 + RECON_SEG - 1) / RECON_SEG) * 7;

@@ -237,10 +237,45 @@ __device__ __forceinline__ void b_recon_sweep(const BlockView& v, PhysArgs ph, c
     }
 }
 
+// one thread per cell (FP32: the slope and interface arithmetic is cheap next to
+// the loads, and a thread per cell keeps more loads in flight than a sweep)
+template <int DIR, typename T>
+__device__ __forceinline__ void b_recon_cell(const BlockView& v, PhysArgs ph, const T* __restrict__ P,
+                                             T* __restrict__ QL, T* __restrict__ QR, long t) {
+    const int e1 = v.n1 + 2, e2 = v.n2 + 2, e3 = v.n3 + 2;
+    if (t >= (long)e1 * e2 * e3) return;
+    const int i = (int)(t % e1) - 1, j = (int)((t / e1) % e2) - 1, k = (int)(t / ((long)e1 * e2)) - 1;
+    const long c = cidx(v, i, j, k);
+    const long st = (DIR == 1) ? 1 : ((DIR == 2) ? (long)v.n1p : (long)v.n1p * v.n2p);
+#pragma unroll
+    for (int n = 0; n < 7; n++) {
+        const int q = recon_var<DIR>(n);
+        const T* p = P + q * v.nc + c;
+        T l, r;
+        if (ph.recon == HAMR_RECON_PPM) {
+            const T qm = p[-st], qc = p[0], qp = p[st];
+            const T sm = mc_slope_i(p[-2 * st], qm, qc), sc = mc_slope_i(qm, qc, qp),
+                    sp = mc_slope_i(qc, qp, p[2 * st]);
+            l = ppm_face(qm, qc, sm, sc);
+            r = ppm_face(qc, qp, sc, sp);
+            ppm_limit(qc, l, r);
+        } else {
+            const T dq = limited_slope(ph.recon, p[-st], p[0], p[st]);
+            l = p[0] - T(0.5) * dq;
+            r = p[0] + T(0.5) * dq;
+        }
+        QL[q * v.nc + c] = l;
+        QR[q * v.nc + c] = r;
+    }
+}
+
+// FP64: the non-redundant row and pencil forms; FP32: one thread per cell
 template <int DIR, typename T>
 __device__ __forceinline__ void b_recon(const BlockView& v, PhysArgs ph, const T* __restrict__ P, T* __restrict__ QL,
                                         T* __restrict__ QR, long t) {
-    if constexpr (DIR == 1)
+    if constexpr (!std::is_same<T, double>::value)
+        b_recon_cell<DIR>(v, ph, P, QL, QR, t);
+    else if constexpr (DIR == 1)
         b_recon_row(v, ph, P, QL, QR, t);
     else
         b_recon_sweep<DIR>(v, ph, P, QL, QR, t);
@@ -858,7 +893,7 @@ cudaError_t launch_bc(const BlockView& v, double* P, double* B, cudaStream_t s) 
 
 cudaError_t launch_recon(const BlockView& v, const PhysArgs& ph, int dir, const double* P, const float* P32,
                          double* QL, double* QR, cudaStream_t s) {
-    const long n = recon_threads(v, dir);
+    const long n = recon_threads(v, dir, ph.mixed);
     if (ph.mixed) {
         float* L = reinterpret_cast<float*>(QL);
         float* R = reinterpret_cast<float*>(QR);
