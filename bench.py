@@ -292,23 +292,32 @@ def amr_leg(hamr, torch, precision=0):
         g.set_state(p, bf, block=i)
     lmax = max(b["lat"] for b in blocks)
     per = 2 ** lmax
-    g.batch_step(per)  # capture + first period
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
     nper = 2
-    ev0.record()
-    g.batch_step(per * nper)
-    ev1.record()
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / nper
+
+    def time_periods():
+        g.batch_step(per)  # capture (after any change of launch shapes) + one period
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        g.batch_step(per * nper)
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / nper
+    ms_default = time_periods()
+    tune = g.autotune()
+    ms = time_periods()
     real = sum(b["n1"] * b["n2"] * b["n3"] * 2 ** (lmax - b["lat"]) for b in blocks)
     eff = sum(b["n1"] * b["n2"] * b["n3"] for b in blocks) * per
     hist = {str(L): sum(1 for b in blocks if b["lat"] == L) for L in range(lmax + 1)}
     g.close()
     return {"workload": "512-block AMR/LAT torus tree, 32^3 and 32x32x16 blocks, %d cells, seed 3" %
                         sum(b["n1"] * b["n2"] * b["n3"] for b in blocks),
-            "precision": "mixed" if precision else "fp64", "ms_per_period": ms, "fine_substeps_per_period": per,
+            "precision": "mixed" if precision else "fp64", "ms_per_period": ms,
+            "ms_per_period_default_shapes": ms_default,
+            "launch_shapes": {k: tune[k] for k in ("recon_seg", "bs_recon", "bs_flux", "bs_update")},
+            "autotune_ms": {k: [round(x, 3) for x in tune[k]] for k in ("ms_seg", "ms_recon", "ms_flux", "ms_update")},
+            "fine_substeps_per_period": per,
             "real_zone_cycles_per_s": real / (ms * 1e-3), "lat_effective_zone_cycles_per_s": eff / (ms * 1e-3),
             "lat_levels": hist}
 

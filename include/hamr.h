@@ -327,6 +327,29 @@ int hamr_mlp_error_flag(hamr_mlp* m, int* flag);
 #define HAMR_MLP_RESCUE 1
 int hamr_grid_set_mlp(hamr_grid* g, const hamr_mlp* m, int mode);
 
+/* ---- launch-shape autotuner (no paper counterpart) ----
+ * Times the grid's reconstruction, face-flux and cell-update kernels on its
+ * current state for each candidate launch shape and keeps the fastest:
+ * cells per thread of the x2/x3 reconstruction sweeps (8, 16, 32; FP64),
+ * then threads per CTA of the reconstruction and flux kernels (64, 128, 256)
+ * and of the cell update (64, 128; 128 while a network is attached). Shapes
+ * change no result bit. The timed launches write only scratch (edge values,
+ * fluxes, the midpoint state); call it after a first step or period so the
+ * state and dt are representative. Synchronises; a multi-block grid
+ * captures its period graph again on the next hamr_batch_step. */
+typedef struct {
+    int recon_seg, bs_recon, bs_flux, bs_update; /* the chosen shapes */
+    float ms_seg[3];    /* reconstruction, sweeps of 8, 16, 32 cells (128 threads per CTA) */
+    float ms_recon[3];  /* reconstruction, 64, 128, 256 threads per CTA (chosen sweep) */
+    float ms_flux[3];   /* face fluxes, 64, 128, 256 threads per CTA */
+    float ms_update[2]; /* cell update (predictor), 64, 128 threads per CTA */
+} hamr_tune_report;
+
+int hamr_grid_autotune(hamr_grid* g, void* stream, hamr_tune_report* report);
+/* The grid's current launch shapes (defaults 16, 128, 128, 128) into report
+ * (timings zero). */
+int hamr_grid_launch_shapes(const hamr_grid* g, hamr_tune_report* report);
+
 /* Message of the last error in the calling thread ("" if none). */
 const char* hamr_last_error(void);
 

@@ -1014,7 +1014,7 @@ int amr_create(AmrImpl** out, const hamr_grid_desc& d, const std::vector<BlockVi
         const long cel = (long)v.n1 * v.n2 * v.n3;
         M->lmw_pad[L] = std::max(M->lmw_pad[L], pad);
         for (int dir = 1; dir <= 3; dir++)
-            M->lmw_recon[L][dir] = std::max(M->lmw_recon[L][dir], recon_threads(v, dir, ph.mixed));
+            M->lmw_recon[L][dir] = std::max(M->lmw_recon[L][dir], recon_threads(v, dir, ph.mixed, ph.recon_seg));
         M->lmw_edge[L] = std::max(M->lmw_edge[L], edg);
         M->lmw_cell[L] = std::max(M->lmw_cell[L], cel);
         M->lmw_flux[L][1] = std::max(M->lmw_flux[L][1], (long)(v.n1 + 1) * (v.n2 + 2) * (v.n3 + 2));
@@ -1175,11 +1175,75 @@ int amr_period(AmrImpl* M, cudaStream_t s, int nperiods, bool use_graph) {
 
 int amr_set_phys(AmrImpl* M, const PhysArgs& ph) {
     M->ph = ph;  // the captured period bakes the launch arguments: capture again
+    for (int L = 0; L <= M->Lmax; L++)
+        for (int dir = 1; dir <= 3; dir++) {
+            long mw = 0;
+            for (int b : M->lev[L]) mw = std::max(mw, recon_threads(M->H.b[b].v, dir, ph.mixed, ph.recon_seg));
+            M->lmw_recon[L][dir] = mw;
+        }
     if (M->exec) cudaGraphExecDestroy(M->exec);
     if (M->graph) cudaGraphDestroy(M->graph);
     M->exec = nullptr;
     M->graph = nullptr;
     return HAMR_OK;
+}
+
+// Time (ms, summed over levels) of one kernel group of the batched step on the
+// current state, predictor stage: 0 reconstruction, 1 face fluxes, 2 cell
+// update. Writes only scratch (edge values, fluxes, the midpoint state, the
+// U^n cache, counters and status bits, which the next period resets).
+int amr_time_group(AmrImpl* M, const PhysArgs& ph, int which, cudaStream_t cs, float* ms) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    AM_TRY(cudaEventCreate(&a));
+    AM_TRY(cudaEventCreate(&b));
+    float total = 0.0f;
+    const DevBlock* tab = M->dtab;
+    int rc = HAMR_OK;
+    for (int L = 0; L <= M->Lmax && rc == HAMR_OK; L++) {
+        const int nl = (int)M->lev[L].size();
+        if (!nl) continue;
+        const int* list = M->dlev[L];
+        long mwr[4];
+        for (int dir = 1; dir <= 3; dir++) {
+            mwr[dir] = 0;
+            for (int bb : M->lev[L]) mwr[dir] = std::max(mwr[dir], recon_threads(M->H.b[bb].v, dir, ph.mixed,
+                                                                                 ph.recon_seg));
+        }
+        auto timed = [&](auto launch) {
+            cudaEventRecord(a, cs);
+            cudaError_t e = launch();
+            cudaEventRecord(b, cs);
+            if (e != cudaSuccess) return set_error(HAMR_ECUDA, "launch failed: %s", cudaGetErrorString(e));
+            e = cudaEventSynchronize(b);
+            if (e != cudaSuccess) return set_error(HAMR_ECUDA, "timing failed: %s", cudaGetErrorString(e));
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, a, b);
+            total += t;
+            return (int)HAMR_OK;
+        };
+        if (ph.mixed) {
+            cudaError_t e = launch_to_f32_batch(tab, list, nl, M->lmw_pad[L], 0, cs);
+            if (e != cudaSuccess) rc = set_error(HAMR_ECUDA, "launch failed: %s", cudaGetErrorString(e));
+        }
+        for (int dir = 1; dir <= 3 && rc == HAMR_OK; dir++) {
+            auto rec = [&]() { return launch_recon_batch(tab, list, nl, mwr[dir], ph, dir, 0, cs); };
+            auto flx = [&]() { return launch_flux_batch(tab, list, nl, M->lmw_flux[L][dir], ph, dir, 0, cs); };
+            if (which == 0) {
+                rc = timed(rec);
+            } else {
+                cudaError_t e = rec();
+                if (e == cudaSuccess && which == 1) rc = timed(flx);
+                else if (e == cudaSuccess) e = flx();
+                if (e != cudaSuccess) rc = set_error(HAMR_ECUDA, "launch failed: %s", cudaGetErrorString(e));
+            }
+        }
+        if (rc == HAMR_OK && which == 2)
+            rc = timed([&]() { return launch_update_batch(tab, list, nl, M->lmw_cell[L], ph, 0, cs); });
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *ms = total;
+    return rc;
 }
 
 int amr_fill(AmrImpl* M, cudaStream_t s) {

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -347,6 +348,7 @@ int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out) {
     g->ph.mlp_img = nullptr;
     g->ph.mlp_err = nullptr;
     g->ph.mlp_mode = HAMR_MLP_FIRST;
+    default_launch_shapes(g->ph);
     cudaGetDevice(&g->device);
     for (int b = 0; b < d->nblocks; b++) {
         rc = alloc_block(g, b);
@@ -569,6 +571,112 @@ int hamr_con2prim(const hamr_c2p_desc* d, int64_t n, const double* U, const doub
     if ((d->flags & (HAMR_C2P_MLP | HAMR_C2P_MLP_RESCUE)) && !d->mlp)
         return fail(HAMR_EINVAL, "a network flag without a network");
     CUDA_TRY(launch_con2prim(*d, n, U, B, x1, x2, prim, status, iters, S(stream)));
+    return HAMR_OK;
+}
+
+namespace {
+// time (ms) of one kernel group on the single-block grid's current state (see amr_time_group)
+int time_group_block(hamr_grid* g, const PhysArgs& ph, int which, cudaStream_t cs, float* ms) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    CUDA_TRY(cudaEventCreate(&a));
+    CUDA_TRY(cudaEventCreate(&b));
+    float total = 0.0f;
+    for (size_t k = 0; k < g->st.size(); k++) {
+        BlockState& s = g->st[k];
+        const BlockView& v = g->view[k];
+        if (ph.mixed) CUDA_TRY(launch_to_f32(v, s.P, s.P32, cs));
+        for (int dir = 1; dir <= 3; dir++) {
+            if (which == 0) CUDA_TRY(cudaEventRecord(a, cs));
+            CUDA_TRY(launch_recon(v, ph, dir, s.P, s.P32, s.QL, s.QR, cs));
+            if (which == 1) CUDA_TRY(cudaEventRecord(a, cs));
+            if (which != 0) CUDA_TRY(launch_flux(v, ph, dir, s.QL, s.QR, s.B, s.F[dir - 1], cs));
+            if (which <= 1) {
+                float t = 0.0f;
+                CUDA_TRY(cudaEventRecord(b, cs));
+                CUDA_TRY(cudaEventSynchronize(b));
+                CUDA_TRY(cudaEventElapsedTime(&t, a, b));
+                total += t;
+            }
+        }
+        if (which == 2) {
+            float t = 0.0f;
+            CUDA_TRY(cudaEventRecord(a, cs));
+            CUDA_TRY(launch_update(v, ph, 0, s.P, s.P, s.F, s.B, s.Un, s.Ph, s.status, s.dscal, 0.5, s.dmax, s.dcnt,
+                                   cs));
+            CUDA_TRY(cudaEventRecord(b, cs));
+            CUDA_TRY(cudaEventSynchronize(b));
+            CUDA_TRY(cudaEventElapsedTime(&t, a, b));
+            total += t;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *ms = total;
+    return HAMR_OK;
+}
+
+// best of three timed repetitions after one warm-up
+int time_group(hamr_grid* g, const PhysArgs& ph, int which, cudaStream_t cs, float* best) {
+    *best = 1e30f;
+    for (int r = 0; r < 4; r++) {
+        float t = 0.0f;
+        int rc = g->amr ? amr_time_group(g->amr, ph, which, cs, &t) : time_group_block(g, ph, which, cs, &t);
+        if (rc) return rc;
+        if (r > 0) *best = std::min(*best, t);
+    }
+    return HAMR_OK;
+}
+}  // namespace
+
+int hamr_grid_autotune(hamr_grid* g, void* stream, hamr_tune_report* rep) {
+    if (!g || !rep) return fail(HAMR_EINVAL, "grid and report must not be NULL");
+    for (size_t b = 0; b < g->loaded.size(); b++)
+        if (!g->loaded[b]) return fail(HAMR_ESTATE, "block %zu has no state", b);
+    cudaStream_t cs = S(stream);
+    CUDA_TRY(cudaDeviceSynchronize());
+    std::memset(rep, 0, sizeof(*rep));
+    // the timed update uses the dt of the last step; the CFL rate that the next step
+    // reads (dmax) is not touched
+    PhysArgs ph = g->ph;
+    const int segs[3] = {8, 16, 32}, bss[3] = {64, 128, 256}, bsu[2] = {64, 128};
+    int rc;
+    ph.bs_recon = 128;
+    for (int c = 0; c < 3; c++) {
+        ph.recon_seg = segs[c];
+        if ((rc = time_group(g, ph, 0, cs, &rep->ms_seg[c]))) return rc;
+    }
+    ph.recon_seg = segs[std::min_element(rep->ms_seg, rep->ms_seg + 3) - rep->ms_seg];
+    for (int c = 0; c < 3; c++) {
+        ph.bs_recon = bss[c];
+        if ((rc = time_group(g, ph, 0, cs, &rep->ms_recon[c]))) return rc;
+    }
+    ph.bs_recon = bss[std::min_element(rep->ms_recon, rep->ms_recon + 3) - rep->ms_recon];
+    for (int c = 0; c < 3; c++) {
+        ph.bs_flux = bss[c];
+        if ((rc = time_group(g, ph, 1, cs, &rep->ms_flux[c]))) return rc;
+    }
+    ph.bs_flux = bss[std::min_element(rep->ms_flux, rep->ms_flux + 3) - rep->ms_flux];
+    for (int c = 0; c < 2; c++) {
+        ph.bs_update = bsu[c];
+        if ((rc = time_group(g, ph, 2, cs, &rep->ms_update[c]))) return rc;
+    }
+    ph.bs_update = ph.mlp_img ? 128 : bsu[std::min_element(rep->ms_update, rep->ms_update + 2) - rep->ms_update];
+    rep->recon_seg = ph.recon_seg;
+    rep->bs_recon = ph.bs_recon;
+    rep->bs_flux = ph.bs_flux;
+    rep->bs_update = ph.bs_update;
+    g->ph = ph;
+    if (g->amr) return amr_set_phys(g->amr, g->ph);
+    return HAMR_OK;
+}
+
+int hamr_grid_launch_shapes(const hamr_grid* g, hamr_tune_report* rep) {
+    if (!g || !rep) return fail(HAMR_EINVAL, "grid and report must not be NULL");
+    std::memset(rep, 0, sizeof(*rep));
+    rep->recon_seg = g->ph.recon_seg;
+    rep->bs_recon = g->ph.bs_recon;
+    rep->bs_flux = g->ph.bs_flux;
+    rep->bs_update = g->ph.bs_update;
     return HAMR_OK;
 }
 

@@ -50,19 +50,29 @@ struct PhysArgs {
     const uint8_t* mlp_img;  // inference image of the learned inversion guess (nullptr: not used)
     int* mlp_err;            // set to 1 by a CTA whose network waits gave up
     int mlp_mode;            // HAMR_MLP_FIRST or HAMR_MLP_RESCUE
+    // launch shapes (hamr_grid_autotune): threads per CTA of the reconstruction,
+    // flux and cell-update kernels, cells per thread of the x2/x3 sweeps
+    int bs_recon, bs_flux, bs_update, recon_seg;
 };
 
 // threads of one reconstruction launch (FP64): rows along x1 in warps of 32
 // lanes that produce RECON_TILE cells each; pencils along x2 or x3 of
 // RECON_SEG cells per thread; 7 variables each. FP32: one thread per cell.
 constexpr int RECON_TILE = 28;
-constexpr int RECON_SEG = 16;
-__host__ __device__ inline long recon_threads(const BlockView& v, int dir, int fp32) {
+constexpr int RECON_SEG = 16;  // default sweep length
+__host__ __device__ inline long recon_threads(const BlockView& v, int dir, int fp32, int seg) {
     const long n1 = v.n1 + 2, n2 = v.n2 + 2, n3 = v.n3 + 2;
     if (fp32) return n1 * n2 * n3;  // one thread per cell
     if (dir == 1) return ((n1 + RECON_TILE - 1) / RECON_TILE) * 32 * n2 * n3 * 7;
-    if (dir == 2) return n1 * n3 * ((n2 + RECON_SEG - 1) / RECON_SEG) * 7;
-    return n1 * n2 * ((n3 + RECON_SEG - 1) / RECON_SEG) * 7;
+    if (dir == 2) return n1 * n3 * ((n2 + seg - 1) / seg) * 7;
+    return n1 * n2 * ((n3 + seg - 1) / seg) * 7;
+}
+// the launch-shape defaults (what hamr_grid_autotune starts from)
+inline void default_launch_shapes(PhysArgs& ph) {
+    ph.bs_recon = 128;
+    ph.bs_flux = 128;
+    ph.bs_update = 128;
+    ph.recon_seg = RECON_SEG;
 }
 
 // device scratch/state of one block
@@ -193,6 +203,7 @@ int amr_info(const AmrImpl* M, int* lmax, double* dtf_host);
 int amr_links(const AmrImpl* M, int* counts5);
 int amr_fill(AmrImpl* M, cudaStream_t s);
 int amr_set_phys(AmrImpl* M, const PhysArgs& ph);
+int amr_time_group(AmrImpl* M, const PhysArgs& ph, int which, cudaStream_t cs, float* ms);
 const uint8_t* mlp_image(const hamr_mlp* m);
 int* mlp_error_ptr(const hamr_mlp* m);
 

@@ -151,6 +151,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     ph.mlp_img = nullptr;
     ph.mlp_err = nullptr;
     ph.mlp_mode = HAMR_MLP_FIRST;
+    default_launch_shapes(ph);
 
     // the array keeps the previous call's contents: clear what must start at zero
     NA_TRY(cudaMemsetAsync(s.Ph, 0, sizeof(double) * 11 * v.nc, cs));

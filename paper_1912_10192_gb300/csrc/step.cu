@@ -25,7 +25,7 @@ __device__ __forceinline__ long cidx(const BlockView& v, int i, int j, int k) {
 }
 __device__ __forceinline__ long gidx(const BlockView& v, int i, int j) { return (long)(j + NG) * v.n1p + (i + NG); }
 
-inline unsigned nblk(long n) { return (unsigned)((n + BS - 1) / BS); }
+inline unsigned nblk(long n, int bs = BS) { return (unsigned)((n + bs - 1) / bs); }
 
 // ---------------------------------------------------------------- centre B
 // B^i = (Bbar^i_lo + Bbar^i_hi) / 2 / sqrt(-g)_centre (Sec. 2.5)
@@ -137,7 +137,7 @@ __global__ void k_bc_axis(BlockView v, double* __restrict__ B) {
 // Every slope and every PPM interface value is formed once and shared by the
 // two cells that use it: along x1 a warp holds 32 consecutive cells (28 of
 // them produced) and passes values between lanes by shuffles; along x2 and
-// x3 a thread sweeps RECON_SEG cells of one pencil (consecutive threads on
+// x3 a thread sweeps recon_seg cells of one pencil (consecutive threads on
 // consecutive i, so loads and stores coalesce). T = float (mixed precision)
 // reads the FP32 copy of the primitives and writes FP32 edge values.
 template <int DIR>
@@ -192,7 +192,8 @@ template <int DIR, typename T>
 __device__ __forceinline__ void b_recon_sweep(const BlockView& v, PhysArgs ph, const T* __restrict__ P,
                                               T* __restrict__ QL, T* __restrict__ QR, long t) {
     const int na = (DIR == 2 ? v.n2 : v.n3) + 2;  // cells along the sweep: -1..n_dir
-    const int nseg = (na + RECON_SEG - 1) / RECON_SEG;
+    const int seglen = ph.recon_seg;
+    const int nseg = (na + seglen - 1) / seglen;
     const int n1 = v.n1 + 2, no = (DIR == 2 ? v.n3 : v.n2) + 2;
     if (t >= (long)n1 * no * nseg * 7) return;
     const int i = (int)(t % n1) - 1;
@@ -202,8 +203,8 @@ __device__ __forceinline__ void b_recon_sweep(const BlockView& v, PhysArgs ph, c
     const int seg = (int)(rest % nseg);
     const int q = recon_var<DIR>((int)(rest / nseg));
     const long st = (DIR == 2) ? (long)v.n1p : (long)v.n1p * v.n2p;
-    const int a0 = seg * RECON_SEG - 1;
-    const int ncell = min(RECON_SEG, na - 1 - a0);           // cells a0 .. a0 + ncell - 1 (<= n_dir)
+    const int a0 = seg * seglen - 1;
+    const int ncell = min(seglen, na - 1 - a0);           // cells a0 .. a0 + ncell - 1 (<= n_dir)
     const long c0 = q * v.nc + ((DIR == 2) ? cidx(v, i, a0, o) : cidx(v, i, o, a0));
     const T* p = P + c0;
     if (ph.recon == HAMR_RECON_PPM) {
@@ -382,7 +383,7 @@ __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const T*
 }
 
 template <int DIR, typename T>
-__global__ void __launch_bounds__(BS) k_flux(BlockView v, PhysArgs ph, const T* __restrict__ QL,
+__global__ void __launch_bounds__(256) k_flux(BlockView v, PhysArgs ph, const T* __restrict__ QL,
                                              const T* __restrict__ QR, const double* __restrict__ Bf,
                                              double* __restrict__ F) {
     b_flux<DIR, T>(v, ph, QL, QR, Bf, F, (long)blockIdx.x * blockDim.x + threadIdx.x);
@@ -751,7 +752,7 @@ __global__ void kb_to_f32(const DevBlock* tab, const int* list, int sigma) {
 }
 
 template <int DIR, typename T>
-__global__ void __launch_bounds__(BS) kb_flux(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
+__global__ void __launch_bounds__(256) kb_flux(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
     const DevBlock& D = tab[list[blockIdx.y]];
     double* F = (DIR == 1) ? D.F1 : ((DIR == 2) ? D.F2 : D.F3);
     b_flux<DIR, T>(D.v, ph, reinterpret_cast<const T*>(D.QL), reinterpret_cast<const T*>(D.QR), sigma ? D.Bh : D.B, F,
@@ -893,17 +894,19 @@ cudaError_t launch_bc(const BlockView& v, double* P, double* B, cudaStream_t s) 
 
 cudaError_t launch_recon(const BlockView& v, const PhysArgs& ph, int dir, const double* P, const float* P32,
                          double* QL, double* QR, cudaStream_t s) {
-    const long n = recon_threads(v, dir, ph.mixed);
+    const long n = recon_threads(v, dir, ph.mixed, ph.recon_seg);
+    const unsigned nb = nblk(n, ph.bs_recon);
+    const int bs = ph.bs_recon;
     if (ph.mixed) {
         float* L = reinterpret_cast<float*>(QL);
         float* R = reinterpret_cast<float*>(QR);
-        if (dir == 1) k_recon<1, float><<<nblk(n), BS, 0, s>>>(v, ph, P32, L, R);
-        if (dir == 2) k_recon<2, float><<<nblk(n), BS, 0, s>>>(v, ph, P32, L, R);
-        if (dir == 3) k_recon<3, float><<<nblk(n), BS, 0, s>>>(v, ph, P32, L, R);
+        if (dir == 1) k_recon<1, float><<<nb, bs, 0, s>>>(v, ph, P32, L, R);
+        if (dir == 2) k_recon<2, float><<<nb, bs, 0, s>>>(v, ph, P32, L, R);
+        if (dir == 3) k_recon<3, float><<<nb, bs, 0, s>>>(v, ph, P32, L, R);
     } else {
-        if (dir == 1) k_recon<1, double><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
-        if (dir == 2) k_recon<2, double><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
-        if (dir == 3) k_recon<3, double><<<nblk(n), BS, 0, s>>>(v, ph, P, QL, QR);
+        if (dir == 1) k_recon<1, double><<<nb, bs, 0, s>>>(v, ph, P, QL, QR);
+        if (dir == 2) k_recon<2, double><<<nb, bs, 0, s>>>(v, ph, P, QL, QR);
+        if (dir == 3) k_recon<3, double><<<nb, bs, 0, s>>>(v, ph, P, QL, QR);
     }
     return cudaGetLastError();
 }
@@ -917,16 +920,18 @@ cudaError_t launch_flux(const BlockView& v, const PhysArgs& ph, int dir, const d
                         const double* Bf, double* F, cudaStream_t s) {
     const long n1 = v.n1 + (dir == 1 ? 1 : 2), n2 = v.n2 + (dir == 2 ? 1 : 2), n3 = v.n3 + (dir == 3 ? 1 : 2);
     const long n = n1 * n2 * n3;
+    const unsigned nb = nblk(n, ph.bs_flux);
+    const int bs = ph.bs_flux;
     if (ph.mixed) {
         const float* L = reinterpret_cast<const float*>(QL);
         const float* R = reinterpret_cast<const float*>(QR);
-        if (dir == 1) k_flux<1, float><<<nblk(n), BS, 0, s>>>(v, ph, L, R, Bf, F);
-        if (dir == 2) k_flux<2, float><<<nblk(n), BS, 0, s>>>(v, ph, L, R, Bf, F);
-        if (dir == 3) k_flux<3, float><<<nblk(n), BS, 0, s>>>(v, ph, L, R, Bf, F);
+        if (dir == 1) k_flux<1, float><<<nb, bs, 0, s>>>(v, ph, L, R, Bf, F);
+        if (dir == 2) k_flux<2, float><<<nb, bs, 0, s>>>(v, ph, L, R, Bf, F);
+        if (dir == 3) k_flux<3, float><<<nb, bs, 0, s>>>(v, ph, L, R, Bf, F);
     } else {
-        if (dir == 1) k_flux<1, double><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
-        if (dir == 2) k_flux<2, double><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
-        if (dir == 3) k_flux<3, double><<<nblk(n), BS, 0, s>>>(v, ph, QL, QR, Bf, F);
+        if (dir == 1) k_flux<1, double><<<nb, bs, 0, s>>>(v, ph, QL, QR, Bf, F);
+        if (dir == 2) k_flux<2, double><<<nb, bs, 0, s>>>(v, ph, QL, QR, Bf, F);
+        if (dir == 3) k_flux<3, double><<<nb, bs, 0, s>>>(v, ph, QL, QR, Bf, F);
     }
     return cudaGetLastError();
 }
@@ -952,17 +957,18 @@ cudaError_t launch_update(const BlockView& v, const PhysArgs& ph, int corrector,
                           uint8_t* status, const double* dscal, double dt_factor, unsigned long long* dmax,
                           unsigned long long* dcnt, cudaStream_t s) {
     const long n = (long)v.n1 * v.n2 * v.n3;
-    const unsigned nb = nblk(n);
+    const int bs = ph.mlp_img ? MLP_ROWS : ph.bs_update;  // the network needs one row per thread of 128
+    const unsigned nb = nblk(n, bs);
     const int sm = ph.mlp_img ? MLP_SMEM_BYTES : 0;
 #define HAMR_UPD_ARGS v, ph, corrector, Pbase, Pflux, F[0], F[1], F[2], Bnew, Un, Pout, status, dscal, dt_factor, dmax, dcnt
     if (ph.mlp_img && ph.mixed)
-        k_update<true, float><<<nb, BS, sm, s>>>(HAMR_UPD_ARGS);
+        k_update<true, float><<<nb, bs, sm, s>>>(HAMR_UPD_ARGS);
     else if (ph.mlp_img)
-        k_update<true, double><<<nb, BS, sm, s>>>(HAMR_UPD_ARGS);
+        k_update<true, double><<<nb, bs, sm, s>>>(HAMR_UPD_ARGS);
     else if (ph.mixed)
-        k_update<false, float><<<nb, BS, 0, s>>>(HAMR_UPD_ARGS);
+        k_update<false, float><<<nb, bs, 0, s>>>(HAMR_UPD_ARGS);
     else
-        k_update<false, double><<<nb, BS, 0, s>>>(HAMR_UPD_ARGS);
+        k_update<false, double><<<nb, bs, 0, s>>>(HAMR_UPD_ARGS);
 #undef HAMR_UPD_ARGS
     return cudaGetLastError();
 }
@@ -981,21 +987,22 @@ cudaError_t launch_dt_select(const PhysArgs& ph, double user_dt, double* dscal, 
 }
 
 namespace {
-inline dim3 bgrid(long maxwork, int nlist) { return dim3(nblk(maxwork), (unsigned)nlist); }
+inline dim3 bgrid(long maxwork, int nlist, int bs = BS) { return dim3(nblk(maxwork, bs), (unsigned)nlist); }
 }  // namespace
 
 cudaError_t launch_recon_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
                                int dir, int sigma, cudaStream_t s) {
     if (nlist <= 0) return cudaSuccess;
-    const dim3 g = bgrid(maxwork, nlist);
+    const int bs = ph.bs_recon;
+    const dim3 g = bgrid(maxwork, nlist, bs);
     if (ph.mixed) {
-        if (dir == 1) kb_recon<1, float><<<g, BS, 0, s>>>(tab, list, ph, sigma);
-        if (dir == 2) kb_recon<2, float><<<g, BS, 0, s>>>(tab, list, ph, sigma);
-        if (dir == 3) kb_recon<3, float><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 1) kb_recon<1, float><<<g, bs, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 2) kb_recon<2, float><<<g, bs, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 3) kb_recon<3, float><<<g, bs, 0, s>>>(tab, list, ph, sigma);
     } else {
-        if (dir == 1) kb_recon<1, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
-        if (dir == 2) kb_recon<2, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
-        if (dir == 3) kb_recon<3, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 1) kb_recon<1, double><<<g, bs, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 2) kb_recon<2, double><<<g, bs, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 3) kb_recon<3, double><<<g, bs, 0, s>>>(tab, list, ph, sigma);
     }
     return cudaGetLastError();
 }
@@ -1010,15 +1017,16 @@ cudaError_t launch_to_f32_batch(const DevBlock* tab, const int* list, int nlist,
 cudaError_t launch_flux_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
                               int dir, int sigma, cudaStream_t s) {
     if (nlist <= 0) return cudaSuccess;
-    const dim3 g = bgrid(maxwork, nlist);
+    const int bs = ph.bs_flux;
+    const dim3 g = bgrid(maxwork, nlist, bs);
     if (ph.mixed) {
-        if (dir == 1) kb_flux<1, float><<<g, BS, 0, s>>>(tab, list, ph, sigma);
-        if (dir == 2) kb_flux<2, float><<<g, BS, 0, s>>>(tab, list, ph, sigma);
-        if (dir == 3) kb_flux<3, float><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 1) kb_flux<1, float><<<g, bs, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 2) kb_flux<2, float><<<g, bs, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 3) kb_flux<3, float><<<g, bs, 0, s>>>(tab, list, ph, sigma);
     } else {
-        if (dir == 1) kb_flux<1, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
-        if (dir == 2) kb_flux<2, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
-        if (dir == 3) kb_flux<3, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 1) kb_flux<1, double><<<g, bs, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 2) kb_flux<2, double><<<g, bs, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 3) kb_flux<3, double><<<g, bs, 0, s>>>(tab, list, ph, sigma);
     }
     return cudaGetLastError();
 }
@@ -1042,16 +1050,17 @@ cudaError_t launch_ct_batch(const DevBlock* tab, const int* list, int nlist, lon
 cudaError_t launch_update_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
                                 int sigma, cudaStream_t s) {
     if (nlist <= 0) return cudaSuccess;
-    const dim3 gr = bgrid(maxwork, nlist);
+    const int bs = ph.mlp_img ? MLP_ROWS : ph.bs_update;
+    const dim3 gr = bgrid(maxwork, nlist, bs);
     const int sm = ph.mlp_img ? MLP_SMEM_BYTES : 0;
     if (ph.mlp_img && ph.mixed)
-        kb_update<true, float><<<gr, BS, sm, s>>>(tab, list, ph, sigma);
+        kb_update<true, float><<<gr, bs, sm, s>>>(tab, list, ph, sigma);
     else if (ph.mlp_img)
-        kb_update<true, double><<<gr, BS, sm, s>>>(tab, list, ph, sigma);
+        kb_update<true, double><<<gr, bs, sm, s>>>(tab, list, ph, sigma);
     else if (ph.mixed)
-        kb_update<false, float><<<gr, BS, 0, s>>>(tab, list, ph, sigma);
+        kb_update<false, float><<<gr, bs, 0, s>>>(tab, list, ph, sigma);
     else
-        kb_update<false, double><<<gr, BS, 0, s>>>(tab, list, ph, sigma);
+        kb_update<false, double><<<gr, bs, 0, s>>>(tab, list, ph, sigma);
     return cudaGetLastError();
 }
 

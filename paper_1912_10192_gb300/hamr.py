@@ -61,6 +61,17 @@ class C2PDesc(C.Structure):
                 ("mlp", C.c_void_p)]
 
 
+class TuneReport(C.Structure):
+    _fields_ = [("recon_seg", C.c_int), ("bs_recon", C.c_int), ("bs_flux", C.c_int), ("bs_update", C.c_int),
+                ("ms_seg", C.c_float * 3), ("ms_recon", C.c_float * 3), ("ms_flux", C.c_float * 3),
+                ("ms_update", C.c_float * 2)]
+
+    def as_dict(self):
+        return {"recon_seg": self.recon_seg, "bs_recon": self.bs_recon, "bs_flux": self.bs_flux,
+                "bs_update": self.bs_update, "ms_seg": list(self.ms_seg), "ms_recon": list(self.ms_recon),
+                "ms_flux": list(self.ms_flux), "ms_update": list(self.ms_update)}
+
+
 class MlpTrainArgs(C.Structure):
     _fields_ = [("steps", C.c_int64), ("batch", C.c_int32), ("lr", C.c_float), ("lr_final", C.c_float),
                 ("seed", C.c_uint64)]
@@ -108,6 +119,8 @@ def lib():
         L.hamr_mlp_forward.argtypes = [P, C.c_int64, P, P, C.c_int, P]
         L.hamr_mlp_error_flag.argtypes = [P, C.POINTER(C.c_int)]
         L.hamr_grid_set_mlp.argtypes = [P, P, C.c_int]
+        L.hamr_grid_autotune.argtypes = [P, P, C.POINTER(TuneReport)]
+        L.hamr_grid_launch_shapes.argtypes = [P, C.POINTER(TuneReport)]
         L.hamr_last_error.argtypes = []
         L.hamr_last_error.restype = C.c_char_p
         for name in header_functions():
@@ -230,6 +243,17 @@ class Grid:
         st = StepStats()
         check(lib().hamr_grid_stats(self.h, C.byref(st)))
         return st.as_dict()
+
+    def autotune(self, stream=None):
+        """Pick the fastest launch shapes for this grid's kernels on its current state (hamr_grid_autotune)."""
+        r = TuneReport()
+        check(lib().hamr_grid_autotune(self.h, _stream(stream), C.byref(r)))
+        return r.as_dict()
+
+    def launch_shapes(self):
+        r = TuneReport()
+        check(lib().hamr_grid_launch_shapes(self.h, C.byref(r)))
+        return r.as_dict()
 
     def set_mlp(self, mlp, mode=0):
         """Attach `mlp` to the grid's inversions (None detaches): mode MLP_FIRST (0) starts Newton from
