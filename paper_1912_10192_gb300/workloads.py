@@ -748,3 +748,91 @@ def _erf(x):
         return serf(x)
     except ImportError:  # pragma: no cover
         return np.vectorize(math.erf)(x)
+
+
+# --- spherical accretion ------------------------------------------------------
+
+def _bondi_theta(c2, gam):
+    """Theta = p/rho of a polytrope with sound speed squared c2 (c2 = gam Theta / h, h = 1 + gam Theta/(gam - 1))."""
+    return c2 / (gam * (1.0 - c2 / (gam - 1.0)))
+
+
+def bondi_profile(r, rc=8.0, gam=4.0 / 3.0, rho_c=1.0):
+    """Relativistic spherical accretion onto a Schwarzschild hole (Michel 1972), M = 1.
+
+    Sonic point rc: u_c^2 = 1/(2 rc), c_s^2 = u_c^2 / (1 - 3 u_c^2). Along the
+    flow rho u r^2 and h^2 (1 - 2/r + u^2) are constant (u = -u^r > 0, the
+    radial 4-velocity, the same in Schwarzschild and Kerr-Schild time), and
+    p = K rho^gam. Returns rho, u (inflow speed u = -u^r) and Theta = p/rho
+    at radii r (the subsonic root outside rc, the supersonic one inside).
+    """
+    r = np.atleast_1d(np.asarray(r, dtype=np.float64))
+    uc2 = 1.0 / (2.0 * rc)
+    cs2 = uc2 / (1.0 - 3.0 * uc2)
+    th_c = _bondi_theta(cs2, gam)
+    K = th_c / rho_c ** (gam - 1.0)
+    uc = math.sqrt(uc2)
+    mdot = rho_c * uc * rc * rc
+    hc = 1.0 + gam * th_c / (gam - 1.0)
+    bern = hc * hc * (1.0 - 2.0 / rc + uc2)
+
+    def f(lnrho, rr):
+        rho = math.exp(lnrho)
+        th = K * rho ** (gam - 1.0)
+        h = 1.0 + gam * th / (gam - 1.0)
+        u = mdot / (rho * rr * rr)
+        return h * h * (1.0 - 2.0 / rr + u * u) - bern
+
+    out_rho = np.empty_like(r)
+    for n, rr in enumerate(r):
+        # f(ln rho) is convex in ln rho with its minimum at the sonic condition; bracket both roots
+        lo, hi = math.log(rho_c) - 40.0, math.log(rho_c) + 40.0
+        a, b = lo, hi
+        for _ in range(200):  # golden-section search for the minimum
+            m1 = a + 0.381966 * (b - a)
+            m2 = b - 0.381966 * (b - a)
+            if f(m1, rr) < f(m2, rr):
+                b = m2
+            else:
+                a = m1
+        xm = 0.5 * (a + b)
+        if abs(rr - rc) < 1e-12:
+            out_rho[n] = math.exp(xm)
+            continue
+        a, b = (xm, hi) if rr > rc else (lo, xm)  # subsonic (denser) outside, supersonic inside
+        fa = f(a, rr)
+        for _ in range(200):  # bisection
+            mid = 0.5 * (a + b)
+            fm = f(mid, rr)
+            if (fm > 0) == (fa > 0):
+                a, fa = mid, fm
+            else:
+                b = mid
+        out_rho[n] = math.exp(0.5 * (a + b))
+    th = K * out_rho ** (gam - 1.0)
+    u = mdot / (out_rho * r * r)
+    return out_rho, u, th
+
+
+def bondi_block(geo, rc=8.0, gam=4.0 / 3.0):
+    """Padded primitive and (zero) face-B arrays of the Michel solution on a
+    Kerr-Schild a = 0 block (x1 = log r): rho, u_g = p/(gam - 1) and
+    utilde^1 = u^1 + alpha^2 u^t g^{t1} with u^1 = u^r / r, u^t from the
+    normalisation; utilde^2 = utilde^3 = 0."""
+    n1, n2, n3 = geo.n1, geo.n2, geo.n3
+    prim = np.zeros((8,) + geo.padded_shape)
+    bface = np.zeros((3,) + geo.padded_shape)
+    # every cell of the padded block (ghosts too: the x1 ghosts then start at the solution)
+    x1 = geo.x1min + (np.arange(-NG, n1 + NG) + 0.5) * geo.dx1
+    r = np.exp(x1)
+    rho, u, th = bondi_profile(r, rc=rc, gam=gam)
+    # Kerr-Schild a = 0 in (t, log r): g_tt = -(1 - 2/r), g_t1 = 2, g_11 = (1 + 2/r) r^2; g^tt = -(1 + 2/r), g^t1 = 2/r^2
+    u1 = -u / r
+    A, Bq, Cq = -(1.0 - 2.0 / r), 2.0 * 2.0 * u1, (1.0 + 2.0 / r) * r * r * u1 * u1 + 1.0
+    ut = (-Bq - np.sqrt(Bq * Bq - 4.0 * A * Cq)) / (2.0 * A)
+    alpha2 = 1.0 / (1.0 + 2.0 / r)
+    ut1 = u1 + alpha2 * ut * (2.0 / (r * r))
+    prim[0] = rho[None, None, :]
+    prim[1] = (rho * th / (gam - 1.0))[None, None, :]
+    prim[2] = ut1[None, None, :]
+    return prim, bface

@@ -172,3 +172,30 @@ def test_mixed_vs_fp64_disk_100_steps():
     for k, v in e.items():
         assert v <= BAR_DISK_100[k], (k, v, e)
     assert div_b(d, bm) <= max(4.0 * div_b(d, b64), 1e-14)
+
+
+def test_mixed_tree_periods_vs_oracle():
+    """The batched AMR/LAT path in mixed precision against the oracle's FP64 multi-block step: a torus
+    tree with a refined block and two time levels, two LAT periods, the torus 10-step bars."""
+    import test_gpu_amr as A
+    from paper_1912_10192_gb300 import hamr
+    blocks = W.torus_tree(nb=(2, 2, 2), n=(8, 8, 8), refine=((0, 1, 0),), lat_base=1, lat_refined=0)
+    states = W.torus_blocks(blocks, seed=3)
+    ob = [O.make_block(b["n1"], b["n2"], b["n3"], b["x1min"], b["x2min"], b["x3min"], b["dx1"], b["dx2"],
+                       b["dx3"], b["bc"], b["lat"]) for b in blocks]
+    d = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, **A.KS)
+    a = O.AmrGrid(d, ob)
+    g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], metric=d.metric, a=d.a, gam=d.gam, cour=d.cour,
+                  recon=d.recon, riemann=d.riemann, floors=d.floors, precision=1)
+    for i, (p, bf) in enumerate(states):
+        a.set(i, p, bf)
+        g.set_state(p, bf, block=i)
+    for _ in range(2):
+        dto = a.period()
+        g.batch_step(2)
+    out = [(*g.get_state(block=i), *a.get(i)) for i in range(len(blocks))]
+    g.close()
+    errs = A.field_errors(blocks, out)
+    print("mixed tree vs oracle, 2 periods:", errs)
+    for k, v in errs.items():
+        assert v <= BAR_TORUS_10[k], (k, v, errs)

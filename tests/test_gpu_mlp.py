@@ -347,3 +347,38 @@ def test_grid_steps_with_the_network(trained):
             assert v <= 1e-9, (name, k, v)
     assert res["rescue"]["entropy"] <= res["plain"]["entropy"]
     assert m.error_flag() == 0
+
+
+def test_tree_periods_with_the_network(trained):
+    """The batched AMR/LAT path with the network attached (FIRST mode) against the oracle's plain
+    multi-block step: a torus tree with a refined block and two time levels, two LAT periods, the
+    FP64 10-step bar (both converge to the same roots)."""
+    import test_gpu_amr as A
+    hamr = _hamr()
+    blocks = W.torus_tree(nb=(2, 2, 2), n=(8, 8, 8), refine=((0, 1, 0),), lat_base=1, lat_refined=0)
+    states = W.torus_blocks(blocks, seed=3)
+    ob = [O.make_block(b["n1"], b["n2"], b["n3"], b["x1min"], b["x2min"], b["x3min"], b["dx1"], b["dx2"],
+                       b["dx3"], b["bc"], b["lat"]) for b in blocks]
+    phys = A.KS
+    d = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, **phys)
+    a = O.AmrGrid(d, ob)
+    g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], metric=d.metric, a=d.a, gam=d.gam, cour=d.cour,
+                  recon=d.recon, riemann=d.riemann, floors=d.floors)
+    for i, (p, bf) in enumerate(states):
+        a.set(i, p, bf)
+        g.set_state(p, bf, block=i)
+    g.set_mlp(trained["m"], hamr.MLP_FIRST)
+    for _ in range(2):
+        a.period()
+        st = g.batch_step(2, stats=True)
+    out = []
+    for i in range(len(blocks)):
+        pg, bg = g.get_state(block=i)
+        po, bo = a.get(i)
+        out.append((pg, bg, po, bo))
+    g.close()
+    errs = A.field_errors(blocks, out)
+    print("tree with the network vs oracle:", errs, "iterations", st["newton_iters"])
+    for k, v in errs.items():
+        assert v <= 1e-9, (k, v, errs)
+    assert trained["m"].error_flag() == 0

@@ -223,3 +223,30 @@ def test_llf_and_minmod_options_parity():
     geo, d, prim, bf = torus_case(32, 16, 8, seed=9, recon=O.RECON_MINMOD, riemann=O.FLUX_LLF)
     pg, bg, po, bo, _, _ = run_both(d, prim, bf, 2)
     assert_parity(*field_errors(d, pg, bg, po, bo), 1e-11)
+
+
+def test_bondi_and_shock_tube_parity():
+    """The FP64 path against the oracle on the two validation set-ups of the oracle's pins: Michel
+    accretion (Kerr-Schild a = 0, theta band, zero-gradient boundaries) and the relativistic blast
+    wave (flat space, periodic transverse directions), ten steps each at the 10-step bar."""
+    geo = W.BlockGeometry(64, 4, 4, math.log(1.8), math.log(20.0), math.pi / 2 - 0.2, math.pi / 2 + 0.2, 0.0, 0.2)
+    prim, bf = W.bondi_block(geo)
+    d = O.make_desc(64, 4, 4, geo.x1min, geo.x2min, geo.x3min, geo.dx1, geo.dx2, geo.dx3, metric=O.METRIC_KS,
+                    a=0.0, gam=4.0 / 3.0, cour=0.8, bc=(0, 0, 0, 0, 1, 1), floors=0)
+    pg, bg, po, bo, dts, _ = run_both(d, prim, bf, 10)
+    errs, _ = field_errors(d, pg, bg, po, bo)
+    for k in ("rho", "u", "utilde"):
+        assert errs[k] <= 1e-9, (k, errs)
+    assert not np.any(bg) and not np.any(bo)  # no field: it stays zero
+
+    n1, gam = 200, 5.0 / 3.0
+    d = O.make_desc(n1, 4, 4, 0.0, 0.0, 0.0, 1.0 / n1, 1.0, 1.0, metric=O.METRIC_MINKOWSKI, gam=gam, cour=0.5,
+                    recon=O.RECON_PPM, riemann=O.FLUX_HLL, bc=(0, 0, 1, 1, 1, 1), floors=0)
+    prim = np.zeros((8, 10, 10, n1 + 2 * NG))
+    x = (np.arange(-NG, n1 + NG) + 0.5) / n1
+    prim[0][...] = np.where(x < 0.5, 10.0, 1.0)[None, None, :]
+    prim[1][...] = (np.where(x < 0.5, 13.33, 1e-6) / (gam - 1.0))[None, None, :]
+    pg, bg, po, bo, dts, _ = run_both(d, prim, np.zeros((3,) + prim.shape[1:]), 10)
+    errs, _ = field_errors(d, pg, bg, po, bo)
+    for k in ("rho", "u", "utilde"):
+        assert errs[k] <= 1e-9, (k, errs)

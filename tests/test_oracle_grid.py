@@ -235,3 +235,103 @@ def test_torus_step_runs_and_uses_documented_fallbacks():
     st = g.stats()
     ncell = 2 * d.n1 * d.n2 * d.n3
     assert st[0] > 0.85 * ncell and st[2] < 0.02 * ncell
+
+
+def _bondi_run(n1, recon, T=5.0):
+    from paper_1912_10192_gb300 import workloads as W
+    geo = W.BlockGeometry(n1, 4, 4, math.log(1.8), math.log(20.0), math.pi / 2 - 0.2, math.pi / 2 + 0.2, 0.0, 0.2)
+    prim, bf = W.bondi_block(geo)
+    d = O.make_desc(n1, 4, 4, geo.x1min, geo.x2min, geo.x3min, geo.dx1, geo.dx2, geo.dx3, metric=O.METRIC_KS, a=0.0,
+                    gam=4.0 / 3.0, cour=0.8, recon=recon, bc=(0, 0, 0, 0, 1, 1), floors=0)
+    g = O.Grid(d)
+    g.set(prim, bf)
+    t = 0.0
+    while t < T:
+        t += g.step()
+    p, _ = g.get()
+    r = np.exp(geo.x1min + (np.arange(n1) + 0.5) * geo.dx1)
+    e = (p[0][NG + 1, NG + 2, NG:NG + n1] - prim[0][NG, NG, NG:NG + n1]) / prim[0][NG, NG, NG:NG + n1]
+    return r, e, g.stats()
+
+
+def test_bondi_inflow_stays_stationary():
+    """Michel's spherical accretion onto a Schwarzschild hole (rc = 8, Gamma = 4/3), r 1.8..20 in a
+    theta band with zero-gradient boundaries, t = 5: the exact solution is a steady state of the
+    scheme up to truncation. With MC slopes the density error over r 2.5..16 is < 1e-4 and falls
+    with resolution; with PPM the subsonic part (r > 9) stays within 1e-5, while the supersonic part
+    carries an odd-even pattern of first-order amplitude (the centred PPM interface values do not see
+    that mode, and fully upwind fluxes do not damp it), which this test bounds at 2e-2 and halves
+    with the cell size."""
+    r64, e64, st = _bondi_run(64, O.RECON_MC)
+    r128, e128, _ = _bondi_run(128, O.RECON_MC)
+    assert st[1] == 0 and st[2] == 0  # every inversion by the energy equation
+    s64, s128 = (r64 > 2.5) & (r64 < 16), (r128 > 2.5) & (r128 < 16)
+    m64, m128 = np.abs(e64[s64]).mean(), np.abs(e128[s128]).mean()
+    assert m64 < 1e-4 and m128 < 0.75 * m64, (m64, m128)
+    r64, p64, _ = _bondi_run(64, O.RECON_PPM)
+    r128, p128, _ = _bondi_run(128, O.RECON_PPM)
+    assert np.abs(p64[(r64 > 9) & (r64 < 16)]).mean() < 1e-5
+    a64 = np.abs(p64[(r64 > 2.5) & (r64 < 7)]).mean()
+    a128 = np.abs(p128[(r128 > 2.5) & (r128 < 7)]).mean()
+    assert a64 < 2e-2 and 1.6 < a64 / a128 < 2.6, (a64, a128)
+
+
+def _shock_tube(n1, recon, T=0.4):
+    """Marti & Mueller (1999) problem 1 along x1 of a flat-space block: rho 10, p 13.33 | rho 1, p 1e-6,
+    Gamma 5/3, at rest, interface at x = 0.5; L1 errors of rho and v against the exact solution."""
+    import srhd_exact as X
+    gam = 5.0 / 3.0
+    d = O.make_desc(n1, 4, 4, 0.0, 0.0, 0.0, 1.0 / n1, 1.0, 1.0, metric=O.METRIC_MINKOWSKI, gam=gam, cour=0.5,
+                    recon=recon, riemann=O.FLUX_HLL, bc=(0, 0, 1, 1, 1, 1), floors=0)
+    prim = np.zeros((8, 10, 10, n1 + 2 * NG))
+    x = (np.arange(-NG, n1 + NG) + 0.5) / n1
+    left = x < 0.5
+    prim[0][...] = np.where(left, 10.0, 1.0)[None, None, :]
+    prim[1][...] = (np.where(left, 13.33, 1e-6) / (gam - 1.0))[None, None, :]
+    g = O.Grid(d)
+    g.set(prim, np.zeros((3,) + prim.shape[1:]))
+    t = 0.0
+    while t < T - 1e-13:
+        t += g.step(min(g.dt(), T - t))
+    p, _ = g.get()
+    L, R = X.State(10.0, 13.33, 0.0, gam), X.State(1.0, 1e-6, 0.0, gam)
+    xc = (np.arange(n1) + 0.5) / n1
+    ex = np.array([X.sample(L, R, (xx - 0.5) / T) for xx in xc])
+    rho = p[0][NG + 1, NG + 1, NG:NG + n1]
+    ut = p[2][NG + 1, NG + 1, NG:NG + n1]
+    v = ut / np.sqrt(1.0 + ut * ut)
+    return np.abs(rho - ex[:, 0]).mean(), np.abs(v - ex[:, 2]).mean()
+
+
+def test_exact_riemann_solver_reference():
+    """The exact solver itself: Newtonian limit against Toro's Sod values (pressures scaled by 1e-5),
+    Marti & Mueller's problem 1 star state, and Rankine-Hugoniot across its shock."""
+    import srhd_exact as X
+    s = 1e-5
+    ps, vs, SL, SR, _, vsr = X.solve(X.State(1.0, s, 0.0, 1.4), X.State(0.125, 0.1 * s, 0.0, 1.4))
+    assert abs(ps / s - 0.30313) < 2e-5 and abs(vs / math.sqrt(s) - 0.92745) < 5e-5
+    assert abs(SL.rho - 0.42632) < 2e-5 and abs(SR.rho - 0.26557) < 2e-5
+    L, R = X.State(10.0, 13.33, 0.0, 5.0 / 3.0), X.State(1.0, 1e-6, 0.0, 5.0 / 3.0)
+    ps, vs, SL, SR, _, vsr = X.solve(L, R)
+    assert abs(ps - 1.448) < 1e-3 and abs(vs - 0.714) < 1e-3 and abs(SR.rho - 5.07) < 1e-2 and abs(vsr - 0.828) < 1e-3
+
+    def uf(st):
+        W, h = st.W, st.h
+        return ((st.rho * W, st.rho * h * W * W * st.v, st.rho * h * W * W - st.p),
+                (st.rho * W * st.v, st.rho * h * W * W * st.v * st.v + st.p, st.rho * h * W * W * st.v))
+    (ua, fa), (ub, fb) = uf(R), uf(SR)
+    for q in range(3):
+        assert abs((fb[q] - vsr * ub[q]) - (fa[q] - vsr * ua[q])) < 1e-12 * max(1.0, abs(fa[q]))
+
+
+def test_relativistic_shock_tube_converges_to_the_exact_solution():
+    """Shock capturing (Sec. 2.1: PPM or MINMOD edge values, HLL fluxes) on the relativistic blast of
+    Marti & Mueller problem 1 at t = 0.4: first-order convergence of the L1 errors toward the exact
+    solution (shocks and the contact are smeared over a fixed number of cells), PPM sharper than
+    MINMOD."""
+    e100 = _shock_tube(100, O.RECON_PPM)
+    e200 = _shock_tube(200, O.RECON_PPM)
+    m200 = _shock_tube(200, O.RECON_MINMOD)
+    assert e200[0] < 0.07 and e200[1] < 0.01, e200
+    assert e200[0] < 0.65 * e100[0] and e200[1] < 0.65 * e100[1], (e100, e200)
+    assert m200[0] > 1.5 * e200[0], (m200, e200)
