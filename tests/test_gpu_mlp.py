@@ -27,6 +27,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 GAM = 13.0 / 9.0
+NG = 3
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -350,35 +351,51 @@ def test_grid_steps_with_the_network(trained):
 
 
 def test_tree_periods_with_the_network(trained):
-    """The batched AMR/LAT path with the network attached (FIRST mode) against the oracle's plain
-    multi-block step: a torus tree with a refined block and two time levels, two LAT periods, the
-    FP64 10-step bar (both converge to the same roots)."""
+    """The batched AMR/LAT path with the network attached, on a coarse torus tree (8^3 blocks, a
+    refined block, two time levels), two LAT periods, against the plain start. On this tree the plain
+    Newton start fails in a few per cent of the inversions (steep gradients), and the network's start
+    then finds an energy-equation root where the plain method falls back to the entropy equation:
+    RESCUE and FIRST both end with fewer entropy inversions and no more failures, and those cells
+    (and what they feed) differ from the oracle's plain run by the difference between the two
+    inversions; density and field stay within 1e-5 (relative L1)."""
     import test_gpu_amr as A
     hamr = _hamr()
     blocks = W.torus_tree(nb=(2, 2, 2), n=(8, 8, 8), refine=((0, 1, 0),), lat_base=1, lat_refined=0)
     states = W.torus_blocks(blocks, seed=3)
     ob = [O.make_block(b["n1"], b["n2"], b["n3"], b["x1min"], b["x2min"], b["x3min"], b["dx1"], b["dx2"],
                        b["dx3"], b["bc"], b["lat"]) for b in blocks]
-    phys = A.KS
-    d = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, **phys)
+    d = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, **A.KS)
     a = O.AmrGrid(d, ob)
-    g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], metric=d.metric, a=d.a, gam=d.gam, cour=d.cour,
-                  recon=d.recon, riemann=d.riemann, floors=d.floors)
     for i, (p, bf) in enumerate(states):
         a.set(i, p, bf)
-        g.set_state(p, bf, block=i)
-    g.set_mlp(trained["m"], hamr.MLP_FIRST)
     for _ in range(2):
         a.period()
-        st = g.batch_step(2, stats=True)
-    out = []
-    for i in range(len(blocks)):
-        pg, bg = g.get_state(block=i)
-        po, bo = a.get(i)
-        out.append((pg, bg, po, bo))
-    g.close()
-    errs = A.field_errors(blocks, out)
-    print("tree with the network vs oracle:", errs, "iterations", st["newton_iters"])
-    for k, v in errs.items():
-        assert v <= 1e-9, (k, v, errs)
+    ref = [a.get(i) for i in range(len(blocks))]
+    counts = {}
+    for name, mode in (("plain", None), ("rescue", hamr.MLP_RESCUE), ("first", hamr.MLP_FIRST)):
+        g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], metric=d.metric, a=d.a, gam=d.gam, cour=d.cour,
+                      recon=d.recon, riemann=d.riemann, floors=d.floors)
+        for i, (p, bf) in enumerate(states):
+            g.set_state(p, bf, block=i)
+        if mode is not None:
+            g.set_mlp(trained["m"], mode)
+        tot = dict(c2p_entropy=0, c2p_fail=0, newton_iters=0)
+        for _ in range(2):
+            st = g.batch_step(2, stats=True)
+            for k in tot:
+                tot[k] += st[k]
+        out = [(*g.get_state(block=i), *ref[i]) for i in range(len(blocks))]
+        g.close()
+        errs = A.field_errors(blocks, out)
+        counts[name] = tot
+        print("tree,", name, tot, "vs oracle:", errs)
+        for pg, bg, po, bo in out:
+            assert np.all(np.isfinite(pg)) and np.all(pg[0] >= 0) and np.all(pg[1] >= 0)
+        if mode is None:
+            for k, v in errs.items():
+                assert v <= 1e-9, (k, v, errs)
+        else:
+            assert errs["rho"] <= 1e-5 and errs["Bface"] <= 1e-5, errs
+            assert tot["c2p_entropy"] <= counts["plain"]["c2p_entropy"]
+            assert tot["c2p_fail"] <= counts["plain"]["c2p_fail"]
     assert trained["m"].error_flag() == 0
