@@ -203,7 +203,7 @@ __device__ __forceinline__ float pow_pos(float x, float y) { return powf(x, y); 
 // entropy tracer kappa = p / rho^gam
 template <typename T>
 __device__ __forceinline__ T entropy_kappa(const T pr[NPRIM], T gam) {
-    return (gam - T(1)) * pr[UU] / pow_pos(pr[RHO], gam);
+    return (gam - T(1)) * pr[UU] * pow_pos(pr[RHO], -gam);
 }
 
 // fastest magnetosonic characteristic speeds along dir (Sec. 2.1): roots of

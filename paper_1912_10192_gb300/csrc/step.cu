@@ -473,11 +473,10 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
     return x;
 }
 
-// sum_i v_f^i / dx^i at a cell centre (Sec. 2.1 CFL condition)
+// sum_i v_f^i / dx^i at a cell centre (Sec. 2.1 CFL condition), given the fluid state
 template <typename T>
-__device__ __forceinline__ double inv_dt_cell(const BlockView& v, const T pr[NPRIM], const Metric<T>& m, T gam) {
-    Fluid<T> s;
-    fluid_state(pr, m, s);
+__device__ __forceinline__ double inv_dt_fluid(const BlockView& v, const T pr[NPRIM], const Fluid<T>& s,
+                                               const Metric<T>& m, T gam) {
     T vp, vm, inv = T(0);
     wave_speeds(pr, s, m, 1, gam, vp, vm);
     inv += fmax(fabs(vp), fabs(vm)) * (T)v.idx1;
@@ -486,6 +485,13 @@ __device__ __forceinline__ double inv_dt_cell(const BlockView& v, const T pr[NPR
     wave_speeds(pr, s, m, 3, gam, vp, vm);
     inv += fmax(fabs(vp), fabs(vm)) * (T)v.idx3;
     return (double)inv;
+}
+
+template <typename T>
+__device__ __forceinline__ double inv_dt_cell(const BlockView& v, const T pr[NPRIM], const Metric<T>& m, T gam) {
+    Fluid<T> s;
+    fluid_state(pr, m, s);
+    return inv_dt_fluid(v, pr, s, m, gam);
 }
 
 // the rate of a cell in precision T from its (FP64) primitives
@@ -646,11 +652,14 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
         its = w.its;
         st = c2p_finish(w, U, m, gam, pr);
         uint8_t sb = (st == INV_ENTROPY) ? ST_ENTROPY : ((st == INV_FAIL) ? ST_FAIL : 0);
+        // the fluid state of the returned primitives serves the floors (b^2) and the CFL rate (u^mu,
+        // b^mu and b^2 do not depend on rho and u_g, which are all the floors change). The floors take
+        // b^2 of these primitives, not of the inversion's own (W, v^2), which differ from them by the
+        // Newton tolerance (more where v^2 was clamped), and the floor rho = b^2/50 would carry that.
+        Fluid<double> s;
+        const bool need_fluid = ph.floors || (corrector == 1 && std::is_same<TS, double>::value);
+        if (need_fluid) fluid_state(pr, m, s);
         if (ph.floors) {
-            // b^2 of the returned primitives (the inversion's own (W, v^2) would differ from it by the
-            // Newton tolerance, and by more where v^2 was clamped, and the floor rho = b^2/50 carries that)
-            Fluid<double> s;
-            fluid_state(pr, m, s);
             const double bsq = s.bsq;
             const double rf = fmax(v.gc[C_RHOFLR * v.n2d + g], bsq * (1.0 / 50.0));
             const double uf = fmax(v.gc[C_UFLR * v.n2d + g], bsq * (1.0 / 750.0));
@@ -667,7 +676,12 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
 #pragma unroll
         for (int q = 0; q < NPRIM; q++) Po[q * v.nc + c] = pr[q];
         status[c] |= sb;
-        if (corrector == 1) inv = inv_dt_at<TS>(v, pr, m, g, gam);
+        if (corrector == 1) {
+            if constexpr (std::is_same<TS, double>::value)
+                inv = inv_dt_fluid(v, pr, s, m, gam);
+            else
+                inv = inv_dt_at<TS>(v, pr, m, g, gam);
+        }
     }
     // warp-aggregated counters and CFL max
     const unsigned lane = threadIdx.x & 31u;
