@@ -16,6 +16,7 @@ BC_OUTFLOW, BC_PERIODIC, BC_POLAR, BC_OUTFLOW_NOINFLOW = 0, 1, 2, 3
 METRIC_KS, METRIC_MINKOWSKI = 0, 1
 RECON_PPM, RECON_MC, RECON_MINMOD = 0, 1, 2
 FLUX_HLL, FLUX_LLF = 0, 1
+EMF_AVERAGE, EMF_UPWIND = 0, 1
 
 
 class Desc(C.Structure):
@@ -24,7 +25,7 @@ class Desc(C.Structure):
                 ("dx1", C.c_double), ("dx2", C.c_double), ("dx3", C.c_double),
                 ("metric", C.c_int), ("a", C.c_double), ("gam", C.c_double),
                 ("cour", C.c_double), ("recon", C.c_int), ("riemann", C.c_int),
-                ("bc", C.c_int * 6), ("floors", C.c_int)]
+                ("bc", C.c_int * 6), ("floors", C.c_int), ("emf", C.c_int)]
 
 
 _libs = {}
@@ -88,7 +89,7 @@ def _p(a):
 
 def make_desc(n1, n2, n3, x1min, x2min, x3min, dx1, dx2, dx3, metric=METRIC_KS, a=0.0,
               gam=13.0 / 9.0, cour=0.8, recon=RECON_PPM, riemann=FLUX_HLL, bc=(0, 0, 0, 0, 1, 1),
-              floors=1):
+              floors=1, emf=EMF_AVERAGE):
     d = Desc()
     d.n1, d.n2, d.n3 = n1, n2, n3
     d.x1min, d.x2min, d.x3min = x1min, x2min, x3min
@@ -98,6 +99,7 @@ def make_desc(n1, n2, n3, x1min, x2min, x3min, dx1, dx2, dx3, metric=METRIC_KS, 
     for m in range(6):
         d.bc[m] = bc[m]
     d.floors = floors
+    d.emf = emf
     return d
 
 

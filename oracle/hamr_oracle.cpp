@@ -833,8 +833,52 @@ void stage_fluxes(ora_grid* g, const double* Pf, const double* Bff, Fluxes& F) {
 
 /* EMFs at edges (Sec. 2.5, the 4-flux average). Reading: E1 and E3 on the
  * polar axis are 0, which keeps Bbar^2 = 0 on axis faces and div B intact.
- * E holds three fields E1, E2, E3 (edge (i, j-1/2, k-1/2) etc. at index (i,j,k)). */
-void stage_emf(ora_grid* g, const Fluxes& F, std::vector<double>& E) {
+ * E holds three fields E1, E2, E3 (edge (i, j-1/2, k-1/2) etc. at index (i,j,k)).
+ *
+ * Upwinded EMFs (the paper's usual setting, the figure caption of Sec. 2.5
+ * and the text after the EMF equations: Gardiner & Stone 2005). For an
+ * edge between directions p and q, with e_p the EMF value a p-face carries
+ * (its B-flux entry with the EMF's sign), e_q likewise, and E_c the EMF of
+ * the cell-centred state (sqrt(-g)(b^m u^n - b^n u^m) for the edge's
+ * component), the average of the four faces gets two corrections:
+ *   E = 1/4 [sum of the 4 face values]
+ *     + 1/4 [D_q(q-3/4) - D_q(q-1/4)] + 1/4 [D_p(p-3/4) - D_p(p-1/4)],
+ *   D_q(q-1/4) = E_c(c, q) - e_q(c, q-1/2),  D_q(q-3/4) = e_q(c, q-1/2) - E_c(c, q-1)
+ * (half-cell differences toward the edge along q) taken in the cell column
+ * c = p-1 or p upwind of the mass flux through the p-face next to it (the
+ * average of both when that flux is zero); D_p likewise along p, upwind of
+ * the mass flux through the q-faces. */
+namespace {
+/* E_c of the three edge components at every cell of the padded block from the stage state */
+void cell_emfs(ora_grid* g, const double* P, std::vector<double>& Ec) {
+    const ora_desc& d = g->d;
+    const long nc = g->ncell;
+    Ec.assign((size_t)3 * nc, 0.0);
+    for (int k = -1; k <= d.n3; k++)
+        for (int j = -1; j <= d.n2; j++)
+            for (int i = -1; i <= d.n1; i++) {
+                long c = cidx(g, i, j, k);
+                const Geom& G = g->gc[gidx(g, i, j)];
+                real pr[NPR];
+                load_prim(g, P, c, pr);
+                State s;
+                get_state(pr, G, s);
+                /* E1 ~ b^2 u^3 - b^3 u^2, E2 ~ b^3 u^1 - b^1 u^3, E3 ~ b^1 u^2 - b^2 u^1, times sqrt(-g) */
+                Ec[c] = tod((s.bcon[2] * s.ucon[3] - s.bcon[3] * s.ucon[2]) * G.gdet);
+                Ec[nc + c] = tod((s.bcon[3] * s.ucon[1] - s.bcon[1] * s.ucon[3]) * G.gdet);
+                Ec[2 * nc + c] = tod((s.bcon[1] * s.ucon[2] - s.bcon[2] * s.ucon[1]) * G.gdet);
+            }
+}
+
+/* upwind choice of two half-cell differences by the sign of a mass flux */
+real upwind(real mass_flux, real lower, real upper) {
+    if (mass_flux > 0.0) return lower;
+    if (mass_flux < 0.0) return upper;
+    return 0.5 * (lower + upper);
+}
+}  // namespace
+
+void stage_emf(ora_grid* g, const Fluxes& F, const double* Pf, std::vector<double>& E) {
     const ora_desc& d = g->d;
     const long nc = g->ncell;
     const int n1 = d.n1, n2 = d.n2, n3 = d.n3;
@@ -848,6 +892,30 @@ void stage_emf(ora_grid* g, const Fluxes& F, std::vector<double>& E) {
     };
     const int s3B2 = bslot(3, 2), s2B3 = bslot(2, 3), s1B3 = bslot(1, 3), s3B1 = bslot(3, 1),
               s2B1 = bslot(2, 1), s1B2 = bslot(1, 2);
+    std::vector<double> Ec;
+    const bool up = (d.emf == ORA_EMF_UPWIND);
+    if (up) cell_emfs(g, Pf, Ec);
+    /* the Gardiner-Stone corrections of one edge: component a (0..2) with face directions p, q;
+     * ep(dp, dq) / eq(dp, dq): the p- / q-face values at offsets from the edge's cell (i, j, k),
+     * mass fluxes likewise; ec(dp, dq) the cell-centred EMF */
+    auto gs = [&](int a, int p, int q, int i, int j, int k, auto ep, auto eq) -> real {
+        int I[4] = {0, i, j, k};
+        auto at = [&](int dp, int dq) {  /* cell index offset along p and q */
+            int J[4] = {0, I[1], I[2], I[3]};
+            J[p] += dp;
+            J[q] += dq;
+            return cidx(g, J[1], J[2], J[3]);
+        };
+        auto ec = [&](int dp, int dq) { return real(Ec[(size_t)a * nc + at(dp, dq)]); };
+        auto mp = [&](int dp, int dq) { return real(F[p][at(dp, dq)]); }; /* mass flux through a p-face */
+        auto mq = [&](int dp, int dq) { return real(F[q][at(dp, dq)]); };
+        /* along q, column c = p-1 (dp = -1) or p (dp = 0), upwind of the p-face mass flux */
+        real dq_lo = upwind(mp(0, -1), eq(-1, 0) - ec(-1, -1), eq(0, 0) - ec(0, -1)); /* D_q(q-3/4) */
+        real dq_hi = upwind(mp(0, 0), ec(-1, 0) - eq(-1, 0), ec(0, 0) - eq(0, 0));   /* D_q(q-1/4) */
+        real dp_lo = upwind(mq(-1, 0), ep(0, -1) - ec(-1, -1), ep(0, 0) - ec(-1, 0)); /* D_p(p-3/4) */
+        real dp_hi = upwind(mq(0, 0), ec(0, -1) - ep(0, -1), ec(0, 0) - ep(0, 0));   /* D_p(p-1/4) */
+        return 0.25 * (dq_lo - dq_hi) + 0.25 * (dp_lo - dp_hi);
+    };
     for (int k = 0; k <= n3; k++)
         for (int j = 0; j <= n2; j++)
             for (int i = 0; i <= n1; i++) {
@@ -856,16 +924,28 @@ void stage_emf(ora_grid* g, const Fluxes& F, std::vector<double>& E) {
                 if (i < n1) {
                     real v = 0.25 * (FX(3, s3B2, i, j, k) + FX(3, s3B2, i, j - 1, k) - FX(2, s2B3, i, j, k - 1) -
                                      FX(2, s2B3, i, j, k));
+                    if (up) /* p = x2 faces (value -F2(B3)), q = x3 faces (value F3(B2)) */
+                        v = v + gs(0, 2, 3, i, j, k,
+                                   [&](int dp, int dq) { return -FX(2, s2B3, i, j + dp, k + dq); },
+                                   [&](int dp, int dq) { return FX(3, s3B2, i, j + dp, k + dq); });
                     E1[e] = axis ? 0.0 : tod(v);
                 }
                 if (j < n2) {
                     real v = 0.25 * (FX(1, s1B3, i, j, k - 1) + FX(1, s1B3, i, j, k) - FX(3, s3B1, i, j, k) -
                                      FX(3, s3B1, i - 1, j, k));
+                    if (up) /* p = x1 faces (value F1(B3)), q = x3 faces (value -F3(B1)) */
+                        v = v + gs(1, 1, 3, i, j, k,
+                                   [&](int dp, int dq) { return FX(1, s1B3, i + dp, j, k + dq); },
+                                   [&](int dp, int dq) { return -FX(3, s3B1, i + dp, j, k + dq); });
                     E2[e] = tod(v);
                 }
                 if (k < n3) {
                     real v = 0.25 * (FX(2, s2B1, i - 1, j, k) + FX(2, s2B1, i, j, k) - FX(1, s1B2, i, j, k) -
                                      FX(1, s1B2, i, j - 1, k));
+                    if (up) /* p = x1 faces (value -F1(B2)), q = x2 faces (value F2(B1)) */
+                        v = v + gs(2, 1, 2, i, j, k,
+                                   [&](int dp, int dq) { return -FX(1, s1B2, i + dp, j + dq, k); },
+                                   [&](int dp, int dq) { return FX(2, s2B1, i + dp, j + dq, k); });
                     E3[e] = axis ? 0.0 : tod(v);
                 }
             }
@@ -971,7 +1051,7 @@ void stage(ora_grid* g, const double* Pf, const double* Bff, const double* Pb, c
     Fluxes F;
     std::vector<double> E;
     stage_fluxes(g, Pf, Bff, F);
-    stage_emf(g, F, E);
+    stage_emf(g, F, Pf, E);
     stage_ct(g, E, Bfb, dts, Bfout);
     stage_update(g, F, Pb, Pf, Bfout, dts, Pout);
 }
@@ -1932,7 +2012,7 @@ void amr_fluxes_group(ora_amr* m, const std::vector<int>& grp, int sigma) {
         for (int q = 0; q < NFX; q++)
             D.F[r.d][(size_t)q * D.g->ncell + r.di] = amr_avg(S.F[r.d].data(), (long)q * S.g->ncell, r.si);
     }
-    for (int b : grp) stage_emf(m->b[b].g, m->b[b].F, m->b[b].E);
+    for (int b : grp) stage_emf(m->b[b].g, m->b[b].F, sigma ? m->b[b].Ph.data() : m->b[b].g->prim.data(), m->b[b].E);
     std::vector<double> vals(m->esync.size());
     for (size_t q = 0; q < m->esync.size(); q++) {  /* read all, then write: sources may be synced too */
         const SyncRec& r = m->esync[q];

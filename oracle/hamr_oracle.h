@@ -22,6 +22,7 @@ enum { ORA_BC_OUTFLOW = 0, ORA_BC_PERIODIC = 1, ORA_BC_POLAR = 2, ORA_BC_OUTFLOW
 enum { ORA_METRIC_KS = 0, ORA_METRIC_MINKOWSKI = 1 };
 enum { ORA_RECON_PPM = 0, ORA_RECON_MC = 1, ORA_RECON_MINMOD = 2 };
 enum { ORA_FLUX_HLL = 0, ORA_FLUX_LLF = 1 };
+enum { ORA_EMF_AVERAGE = 0, ORA_EMF_UPWIND = 1 };
 
 typedef struct {
     int n1, n2, n3;                 /* interior cells per direction */
@@ -35,6 +36,7 @@ typedef struct {
     int riemann;                    /* ORA_FLUX_* */
     int bc[6];                      /* x1lo x1hi x2lo x2hi x3lo x3hi: ORA_BC_* */
     int floors;                     /* 1: apply the density/energy floors */
+    int emf;                        /* ORA_EMF_*: edge EMFs as the 4-flux average or upwinded */
 } ora_desc;
 
 /* ---- point-wise pieces (each documented in hamr_oracle.cpp) ---- */

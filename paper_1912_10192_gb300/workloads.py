@@ -836,3 +836,32 @@ def bondi_block(geo, rc=8.0, gam=4.0 / 3.0):
     prim[1] = (rho * th / (gam - 1.0))[None, None, :]
     prim[2] = ut1[None, None, :]
     return prim, bface
+
+
+# --- field-loop advection (flat space) ------------------------------------------
+
+def field_loop_block(n1, n2, n3=4, L=1.0, R=0.3, A0=1e-3, rho=1.0, p=0.1, v=(0.4, 0.2), gam=5.0 / 3.0):
+    """A weak cylindrical field loop (A_3 = A0 (R - r) inside r < R, r from the box centre) in a
+    uniform flow with 3-velocity v in a periodic L x L box (x1, x2; n3 cells of size 1 along x3).
+    Face B is the discrete curl of A_3 at the x3-edges (divergence-free to round-off); returns
+    the padded primitive and face arrays and the cell sizes."""
+    dx1, dx2 = L / n1, L / n2
+    shp = (n3 + 2 * NG, n2 + 2 * NG, n1 + 2 * NG)
+    prim = np.zeros((8,) + shp)
+    bface = np.zeros((3,) + shp)
+    W = 1.0 / math.sqrt(1.0 - v[0] * v[0] - v[1] * v[1])
+    prim[0][...] = rho
+    prim[1][...] = p / (gam - 1.0)
+    prim[2][...] = W * v[0]
+    prim[3][...] = W * v[1]
+    xe = np.arange(n1 + 1) * dx1 - 0.5 * L
+    ye = np.arange(n2 + 1) * dx2 - 0.5 * L
+    X, Y = np.meshgrid(xe, ye, indexing="xy")  # edges (i-1/2, j-1/2): (n2+1, n1+1)
+    r = np.sqrt(X * X + Y * Y)
+    A = np.where(r < R, A0 * (R - r), 0.0)
+    b1 = (A[1:, :] - A[:-1, :]) / dx2        # Bbar^1 = dA3/dx2 on x1 faces i = 0..n1: (n2, n1+1)
+    b2 = -(A[:, 1:] - A[:, :-1]) / dx1       # Bbar^2 = -dA3/dx1 on x2 faces j = 0..n2: (n2+1, n1)
+    for k in range(n3):
+        bface[0, NG + k, NG:NG + n2, NG:NG + n1 + 1] = b1
+        bface[1, NG + k, NG:NG + n2 + 1, NG:NG + n1] = b2
+    return prim, bface, dx1, dx2

@@ -31,8 +31,10 @@ def interior(a, d):
     return a[..., NG:NG + d.n3, NG:NG + d.n2, NG:NG + d.n1]
 
 
-def test_ct_keeps_div_b_at_roundoff_on_torus():
+@pytest.mark.parametrize("emf", [O.EMF_AVERAGE, O.EMF_UPWIND])
+def test_ct_keeps_div_b_at_roundoff_on_torus(emf):
     geo, d = torus_desc(32, 16, 8)
+    d.emf = emf
     prim, bf = W.torus_block(geo, seed=1912)
     g = O.Grid(d)
     g.set(prim, bf)
@@ -335,3 +337,53 @@ def test_relativistic_shock_tube_converges_to_the_exact_solution():
     assert e200[0] < 0.07 and e200[1] < 0.01, e200
     assert e200[0] < 0.65 * e100[0] and e200[1] < 0.65 * e100[1], (e100, e200)
     assert m200[0] > 1.5 * e200[0], (m200, e200)
+
+
+def _field_loop(n, emf, v=(0.4, 0.4)):
+    prim, bf, dx1, dx2 = W.field_loop_block(n, n, v=v)
+    d = O.make_desc(n, n, 4, -0.5, -0.5, 0.0, dx1, dx2, 1.0, metric=O.METRIC_MINKOWSKI, gam=5.0 / 3.0, cour=0.5,
+                    bc=(1, 1, 1, 1, 1, 1), floors=0, emf=emf)
+    g = O.Grid(d)
+    g.set(prim, bf)
+    T = 1.0 / v[0]  # one crossing along x1 and x2: the loop is back where it started
+    t = 0.0
+    while t < T - 1e-13:
+        t += g.step(min(g.dt(), T - t))
+    _, b = g.get()
+    f = [(b[0][NG + 1, NG:NG + n, NG:NG + n + 1], bf[0][NG + 1, NG:NG + n, NG:NG + n + 1]),
+         (b[1][NG + 1, NG:NG + n + 1, NG:NG + n], bf[1][NG + 1, NG:NG + n + 1, NG:NG + n])]
+    err = sum(np.abs(x - x0).sum() for x, x0 in f) / sum(np.abs(x0).sum() for _, x0 in f)
+    me = sum((x * x).sum() for x, _ in f) / sum((x0 * x0).sum() for _, x0 in f)
+    scale = np.abs(bf).max() / min(dx1, dx2)
+    return err, me, np.abs(g.divb()).max() / scale, np.abs(b[2]).max()
+
+
+def test_upwinded_emfs_reduce_to_the_average_for_uniform_emf():
+    """A uniform magnetised flow: every face and cell EMF is equal, the Gardiner-Stone corrections
+    vanish, and both EMF forms give the same step to round-off."""
+    d = flat_desc(8, 8, 8)
+    shp = (14, 14, 14)
+    prim = np.zeros((8,) + shp)
+    bf = np.zeros((3,) + shp)
+    prim[0][...], prim[1][...], prim[2][...], prim[3][...], prim[4][...] = 1.0, 0.5, 0.3, -0.2, 0.1
+    bf[0][...], bf[1][...], bf[2][...] = 0.2, -0.1, 0.05
+    res = []
+    for emf in (O.EMF_AVERAGE, O.EMF_UPWIND):
+        d.emf = emf
+        g = O.Grid(d)
+        g.set(prim, bf)
+        g.step(0.01)
+        res.append(g.get())
+    assert np.abs(res[0][0] - res[1][0]).max() < 1e-15 and np.abs(res[0][1] - res[1][1]).max() < 1e-15
+
+
+def test_field_loop_is_cleaner_with_upwinded_emfs():
+    """Gardiner & Stone (2005) field-loop advection in flat space (weak loop, beta >> 1, diagonal
+    flow, one crossing of the periodic box): with upwinded EMFs the loop returns closer to its start
+    (L1 of the face field), with div B at round-off and no field along x3 in both forms."""
+    e_avg, me_avg, div_avg, b3_avg = _field_loop(32, O.EMF_AVERAGE)
+    e_up, me_up, div_up, b3_up = _field_loop(32, O.EMF_UPWIND)
+    assert e_up < 0.6 * e_avg, (e_up, e_avg)
+    assert me_up > 0.8 and me_avg > 0.8, (me_up, me_avg)
+    assert div_up < 1e-13 and div_avg < 1e-13
+    assert b3_up == 0.0 and b3_avg == 0.0
