@@ -68,6 +68,8 @@ extern "C" {
 #define HAMR_BC_POLAR 2             /* transmissive polar axis (Sec. 3.3), x2 only, n3 even */
 #define HAMR_BC_OUTFLOW_NOINFLOW 3  /* zero-gradient with utilde^1 clamped to outflow, x1 only */
 #define HAMR_BC_BLOCK 4             /* face shared with other blocks of the grid (ghosts from them) */
+#define HAMR_EMF_AVERAGE 0 /* the 4-flux average of Sec. 2.5 */
+#define HAMR_EMF_UPWIND 1  /* the average plus Gardiner & Stone (2005) upwind corrections (the paper's usual setting) */
 #define HAMR_PREC_FP64 0  /* every step in FP64 */
 #define HAMR_PREC_MIXED 1 /* FP32 reconstruction, fluxes and EMFs; FP64 metric, inversion, accumulation */
 
@@ -97,6 +99,7 @@ typedef struct {
     int precision;       /* HAMR_PREC_* */
     int nblocks;         /* >= 1 */
     const hamr_block_desc* blocks; /* nblocks descriptors, copied by hamr_grid_create */
+    int emf;             /* HAMR_EMF_*: edge EMFs (Sec. 2.5) */
 } hamr_grid_desc;
 
 /* Counters of the last step (summed over its two stages and all blocks

@@ -545,7 +545,7 @@ struct AmrImpl {
     std::vector<int*> dlev;             // device copies
     int* dall = nullptr;                // all blocks
     long mw_pad = 0, mw_recon = 0, mw_flux[4] = {0, 0, 0, 0}, mw_edge = 0, mw_cell = 0;
-    std::vector<long> lmw_pad, lmw_edge, lmw_cell;
+    std::vector<long> lmw_pad, lmw_edge, lmw_cell, lmw_ext;
     std::vector<std::vector<long>> lmw_flux, lmw_recon;
     // synchronisation
     SyncDev fs{}, es{};
@@ -1005,6 +1005,7 @@ int amr_create(AmrImpl** out, const hamr_grid_desc& d, const std::vector<BlockVi
     M->lmw_recon.assign(M->Lmax + 1, std::vector<long>(4, 0));
     M->lmw_edge.assign(M->Lmax + 1, 0);
     M->lmw_cell.assign(M->Lmax + 1, 0);
+    M->lmw_ext.assign(M->Lmax + 1, 0);
     M->lmw_flux.assign(M->Lmax + 1, std::vector<long>(4, 0));
     for (int b = 0; b < M->nb; b++) {
         const BlockView& v = H.b[b].v;
@@ -1017,6 +1018,7 @@ int amr_create(AmrImpl** out, const hamr_grid_desc& d, const std::vector<BlockVi
             M->lmw_recon[L][dir] = std::max(M->lmw_recon[L][dir], recon_threads(v, dir, ph.mixed, ph.recon_seg));
         M->lmw_edge[L] = std::max(M->lmw_edge[L], edg);
         M->lmw_cell[L] = std::max(M->lmw_cell[L], cel);
+        M->lmw_ext[L] = std::max(M->lmw_ext[L], (long)(v.n1 + 2) * (v.n2 + 2) * (v.n3 + 2));
         M->lmw_flux[L][1] = std::max(M->lmw_flux[L][1], (long)(v.n1 + 1) * (v.n2 + 2) * (v.n3 + 2));
         M->lmw_flux[L][2] = std::max(M->lmw_flux[L][2], (long)(v.n1 + 2) * (v.n2 + 1) * (v.n3 + 2));
         M->lmw_flux[L][3] = std::max(M->lmw_flux[L][3], (long)(v.n1 + 2) * (v.n2 + 2) * (v.n3 + 1));
@@ -1076,7 +1078,7 @@ int group_step(AmrImpl& M, int L, int s, cudaStream_t cs) {
         }
         const int fb = M.fs_beg[L], fe = M.fs_end[L];
         if (fe > fb) k_flux_sync<<<nb_(fe - fb), BSA, 0, cs>>>(tab, M.fs, fb, fe);
-        AM_TRY(launch_emf_batch(tab, list, nl, M.lmw_edge[L], ph.mixed, cs));
+        AM_TRY(launch_emf_batch(tab, list, nl, M.lmw_edge[L], ph.mixed, ph.emf, M.lmw_ext[L], sigma, cs));
         const int eb = M.es_beg[L], ee = M.es_end[L];
         if (ee > eb) {
             k_edge_gather<<<nb_(ee - eb), BSA, 0, cs>>>(tab, M.es, eb, ee, M.es_tmp);

@@ -148,6 +148,7 @@ int validate(const hamr_grid_desc* d) {
     if (d->riemann < 0 || d->riemann > 1) return fail(HAMR_EINVAL, "unknown riemann %d", d->riemann);
     if (d->precision != HAMR_PREC_FP64 && d->precision != HAMR_PREC_MIXED)
         return fail(HAMR_EINVAL, "unknown precision %d", d->precision);
+    if (d->emf != HAMR_EMF_AVERAGE && d->emf != HAMR_EMF_UPWIND) return fail(HAMR_EINVAL, "unknown emf %d", d->emf);
     for (int b = 0; b < d->nblocks; b++) {
         const hamr_block_desc& B = d->blocks[b];
         if (B.n1 < 4 || B.n2 < 4 || B.n3 < 4) return fail(HAMR_EINVAL, "block %d: each n must be >= 4", b);
@@ -349,6 +350,7 @@ int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out) {
     g->ph.mlp_err = nullptr;
     g->ph.mlp_mode = HAMR_MLP_FIRST;
     default_launch_shapes(g->ph);
+    g->ph.emf = d->emf;
     cudaGetDevice(&g->device);
     for (int b = 0; b < d->nblocks; b++) {
         rc = alloc_block(g, b);
@@ -441,7 +443,7 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
         LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.P, s.P32, s.QL, s.QR, cs));
         LAUNCH(g, K_FLUX, 1, cs, launch_flux(v, ph, dir, s.QL, s.QR, s.B, s.F[dir - 1], cs));
     }
-    LAUNCH(g, K_EMF, 1, cs, launch_emf(v, s.F, s.E, ph.mixed, cs));
+    LAUNCH(g, K_EMF, 1, cs, launch_emf(v, s.F, s.E, ph.mixed, s.P, ph.emf ? s.QL : nullptr, cs));
     LAUNCH(g, K_CT, 1, cs, launch_ct(v, s.E, s.B, s.Bh, s.dscal, 0.5, cs));
     LAUNCH(g, K_UPDATE, 1, cs,
            launch_update(v, ph, 0, s.P, s.P, s.F, s.Bh, s.Un, s.Ph, s.status, s.dscal, 0.5, s.dmax, s.dcnt, cs));
@@ -452,7 +454,7 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
         LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.Ph, s.P32, s.QL, s.QR, cs));
         LAUNCH(g, K_FLUX, 1, cs, launch_flux(v, ph, dir, s.QL, s.QR, s.Bh, s.F[dir - 1], cs));
     }
-    LAUNCH(g, K_EMF, 1, cs, launch_emf(v, s.F, s.E, ph.mixed, cs));
+    LAUNCH(g, K_EMF, 1, cs, launch_emf(v, s.F, s.E, ph.mixed, s.Ph, ph.emf ? s.QL : nullptr, cs));
     LAUNCH(g, K_CT, 1, cs, launch_ct(v, s.E, s.B, s.B, s.dscal, 1.0, cs));
     LAUNCH(g, K_UPDATE, 1, cs,
            launch_update(v, ph, 1, s.P, s.Ph, s.F, s.B, s.Un, s.P, s.status, s.dscal, 1.0, s.dmax, s.dcnt, cs));

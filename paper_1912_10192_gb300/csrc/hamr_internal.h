@@ -53,6 +53,7 @@ struct PhysArgs {
     // launch shapes (hamr_grid_autotune): threads per CTA of the reconstruction,
     // flux and cell-update kernels, cells per thread of the x2/x3 sweeps
     int bs_recon, bs_flux, bs_update, recon_seg;
+    int emf;  // HAMR_EMF_*
 };
 
 // threads of one reconstruction launch (FP64): rows along x1 in warps of 32
@@ -135,7 +136,9 @@ cudaError_t launch_recon(const BlockView& v, const PhysArgs& ph, int dir, const 
 cudaError_t launch_to_f32(const BlockView& v, const double* P, float* P32, cudaStream_t s);
 cudaError_t launch_flux(const BlockView& v, const PhysArgs& ph, int dir, const double* QL, const double* QR,
                         const double* Bf, double* F, cudaStream_t s);
-cudaError_t launch_emf(const BlockView& v, double* const F[3], double* E, int mixed, cudaStream_t s);
+// upwinded EMFs when Ec (3 fields of scratch, stride nc) is given: the cell EMFs of P go there first
+cudaError_t launch_emf(const BlockView& v, double* const F[3], double* E, int mixed, const double* P, double* Ec,
+                       cudaStream_t s);
 cudaError_t launch_ct(const BlockView& v, const double* E, const double* Bbase, double* Bout, const double* dscal,
                       double dt_factor, cudaStream_t s);
 cudaError_t launch_update(const BlockView& v, const PhysArgs& ph, int corrector, const double* Pbase,
@@ -157,8 +160,8 @@ cudaError_t launch_recon_batch(const DevBlock* tab, const int* list, int nlist, 
                                int dir, int sigma, cudaStream_t s);
 cudaError_t launch_flux_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
                               int dir, int sigma, cudaStream_t s);
-cudaError_t launch_emf_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, int mixed,
-                             cudaStream_t s);
+cudaError_t launch_emf_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, int mixed, int upwind,
+                             long maxcells, int sigma, cudaStream_t s);
 // sigma 0: Bh = B + dt/2 curl E; 1: B += dt curl E; 2: B += curl E (E holds time-integrated corrections)
 cudaError_t launch_ct_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, int sigma, cudaStream_t s);
 cudaError_t launch_update_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,

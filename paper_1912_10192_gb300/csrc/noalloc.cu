@@ -80,6 +80,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     if ((B.bc[2] == HAMR_BC_POLAR || B.bc[3] == HAMR_BC_POLAR) && (B.n3 % 2 != 0 || d->metric != HAMR_METRIC_KS))
         return set_error(HAMR_EINVAL, "polar bc needs even n3 and the KS metric");
     if (d->precision != HAMR_PREC_FP64) return set_error(HAMR_EINVAL, "the no-allocation step is FP64 only");
+    if (d->emf != HAMR_EMF_AVERAGE && d->emf != HAMR_EMF_UPWIND) return set_error(HAMR_EINVAL, "unknown emf %d", d->emf);
 
     double* base = nullptr;
     int rc = setup(&base);
@@ -152,6 +153,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     ph.mlp_err = nullptr;
     ph.mlp_mode = HAMR_MLP_FIRST;
     default_launch_shapes(ph);
+    ph.emf = d->emf;
 
     // the array keeps the previous call's contents: clear what must start at zero
     NA_TRY(cudaMemsetAsync(s.Ph, 0, sizeof(double) * 11 * v.nc, cs));
@@ -187,7 +189,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
         NA_TRY(launch_recon(v, ph, dir, s.P, nullptr, s.QL, s.QR, cs));
         NA_TRY(launch_flux(v, ph, dir, s.QL, s.QR, s.B, s.F[dir - 1], cs));
     }
-    NA_TRY(launch_emf(v, s.F, s.E, ph.mixed, cs));
+    NA_TRY(launch_emf(v, s.F, s.E, ph.mixed, s.P, ph.emf ? s.QL : nullptr, cs));
     NA_TRY(launch_ct(v, s.E, s.B, s.Bh, s.dscal, 0.5, cs));
     NA_TRY(launch_update(v, ph, 0, s.P, s.P, s.F, s.Bh, s.Un, s.Ph, s.status, s.dscal, 0.5, s.dmax, s.dcnt, cs));
     // corrector
@@ -196,7 +198,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
         NA_TRY(launch_recon(v, ph, dir, s.Ph, nullptr, s.QL, s.QR, cs));
         NA_TRY(launch_flux(v, ph, dir, s.QL, s.QR, s.Bh, s.F[dir - 1], cs));
     }
-    NA_TRY(launch_emf(v, s.F, s.E, ph.mixed, cs));
+    NA_TRY(launch_emf(v, s.F, s.E, ph.mixed, s.Ph, ph.emf ? s.QL : nullptr, cs));
     NA_TRY(launch_ct(v, s.E, s.B, s.B, s.dscal, 1.0, cs));
     NA_TRY(launch_update(v, ph, 1, s.P, s.Ph, s.F, s.B, s.Un, s.P, s.status, s.dscal, 1.0, s.dmax, s.dcnt, cs));
     NA_TRY(launch_bc(v, s.P, s.B, cs));

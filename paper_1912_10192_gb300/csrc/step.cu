@@ -395,35 +395,99 @@ __global__ void __launch_bounds__(256) k_flux(BlockView v, PhysArgs ph, const T*
 // E1 and E3 on the polar axis are 0. With T = float (mixed precision) the
 // average is formed in FP32; every face shares the one stored edge value, so
 // the FP64 curl in the CT update still keeps div B at FP64 roundoff.
+//
+// Upwinded EMFs (Ec != nullptr; Gardiner & Stone 2005, the paper's usual
+// setting): for an edge between face directions p and q, with e_p / e_q the
+// EMF values the p- / q-faces carry and Ec the EMF of the cell-centred state,
+//   E = average + 1/4 [D_q(q-3/4) - D_q(q-1/4)] + 1/4 [D_p(p-3/4) - D_p(p-1/4)],
+//   D_q(q-1/4) = Ec(c, q) - e_q(c, q-1/2), D_q(q-3/4) = e_q(c, q-1/2) - Ec(c, q-1),
+// in the cell column c (p-1 or p) upwind of the mass flux through the p-face
+// beside the edge (both averaged when it is zero); D_p likewise.
+
+// the cell-centred EMFs sqrt(-g)(b^2 u^3 - b^3 u^2, b^3 u^1 - b^1 u^3, b^1 u^2 - b^2 u^1)
+// of every cell -1..n of the block, from the stage state (centre B in slots 5..7)
+__device__ __forceinline__ void b_cell_emf(const BlockView& v, const double* __restrict__ P, double* __restrict__ Ec,
+                                           long t) {
+    const int e1 = v.n1 + 2, e2 = v.n2 + 2, e3 = v.n3 + 2;
+    if (t >= (long)e1 * e2 * e3) return;
+    const int i = (int)(t % e1) - 1, j = (int)((t / e1) % e2) - 1, k = (int)(t / ((long)e1 * e2)) - 1;
+    const long c = cidx(v, i, j, k);
+    Metric<double> m;
+    load_metric(v.gc, v.n2d, gidx(v, i, j), m);
+    double pr[NPRIM];
+#pragma unroll
+    for (int q = 0; q < NPRIM; q++) pr[q] = P[q * v.nc + c];
+    Fluid<double> s;
+    fluid_state(pr, m, s);
+    Ec[c] = (s.bcon[2] * s.ucon[3] - s.bcon[3] * s.ucon[2]) * m.gdet;
+    Ec[v.nc + c] = (s.bcon[3] * s.ucon[1] - s.bcon[1] * s.ucon[3]) * m.gdet;
+    Ec[2 * v.nc + c] = (s.bcon[1] * s.ucon[2] - s.bcon[2] * s.ucon[1]) * m.gdet;
+}
+
+__global__ void k_cell_emf(BlockView v, const double* __restrict__ P, double* __restrict__ Ec) {
+    b_cell_emf(v, P, Ec, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <typename T>
+__device__ __forceinline__ T upwind_pick(T mass_flux, T lower, T upper) {
+    return mass_flux > T(0) ? lower : (mass_flux < T(0) ? upper : T(0.5) * (lower + upper));
+}
+
+// the Gardiner-Stone corrections of one edge. Offsets are cells along p and q from the
+// edge's cell c: sp, sq the index strides of p and q; Fp / Fq the flux arrays of the p / q
+// faces, slp / slq their B-flux slots with signs gp / gq (the EMF a face carries is g F[sl]);
+// ec the cell-EMF field of the component
+template <typename T>
+__device__ __forceinline__ T gs_correction(long c, long sp, long sq, long nc, const double* __restrict__ Fp,
+                                           const double* __restrict__ Fq, int slp, int slq, T gp, T gq,
+                                           const double* __restrict__ ec) {
+    auto ep = [&](long o) { return gp * (T)Fp[slp * nc + c + o]; };  // p-face value at cell offset o
+    auto eq = [&](long o) { return gq * (T)Fq[slq * nc + c + o]; };
+    auto E = [&](long o) { return (T)ec[c + o]; };
+    auto mp = [&](long o) { return (T)Fp[c + o]; };  // mass flux (slot 0) through a p-face
+    auto mq = [&](long o) { return (T)Fq[c + o]; };
+    const T dq_lo = upwind_pick(mp(-sq), eq(-sp) - E(-sp - sq), eq(0) - E(-sq));  // D_q(q-3/4)
+    const T dq_hi = upwind_pick(mp(0), E(-sp) - eq(-sp), E(0) - eq(0));           // D_q(q-1/4)
+    const T dp_lo = upwind_pick(mq(-sp), ep(-sq) - E(-sp - sq), ep(0) - E(-sp));  // D_p(p-3/4)
+    const T dp_hi = upwind_pick(mq(0), E(-sq) - ep(-sq), E(0) - ep(0));           // D_p(p-1/4)
+    return T(0.25) * (dq_lo - dq_hi) + T(0.25) * (dp_lo - dp_hi);
+}
+
 template <typename T>
 __device__ __forceinline__ void b_emf(const BlockView& v, const double* __restrict__ F1, const double* __restrict__ F2,
-                      const double* __restrict__ F3, double* __restrict__ E, long t) {
+                      const double* __restrict__ F3, double* __restrict__ E, const double* __restrict__ Ec, long t) {
     const int e1 = v.n1 + 1, e2 = v.n2 + 1, e3 = v.n3 + 1;
     if (t >= (long)e1 * e2 * e3) return;
     const int i = (int)(t % e1), j = (int)((t / e1) % e2), k = (int)(t / ((long)e1 * e2));
     const long c = cidx(v, i, j, k);
-    const long sj = v.n1p, sk = (long)v.n1p * v.n2p, nc = v.nc;
+    const long si = 1, sj = v.n1p, sk = (long)v.n1p * v.n2p, nc = v.nc;
     const bool axis = (v.bc[2] == HAMR_BC_POLAR && j == 0) || (v.bc[3] == HAMR_BC_POLAR && j == v.n2);
     const T q = T(0.25);
     // flux slots: F1 -> (B2: 6, B3: 7), F2 -> (B1: 6, B3: 7), F3 -> (B1: 6, B2: 7)
     if (i < v.n1) {
-        const T x = q * ((T)F3[7 * nc + c] + (T)F3[7 * nc + c - sj] - (T)F2[7 * nc + c - sk] - (T)F2[7 * nc + c]);
+        T x = q * ((T)F3[7 * nc + c] + (T)F3[7 * nc + c - sj] - (T)F2[7 * nc + c - sk] - (T)F2[7 * nc + c]);
+        // p = x2 faces (value -F2(B3)), q = x3 faces (value F3(B2))
+        if (Ec) x += gs_correction<T>(c, sj, sk, nc, F2, F3, 7, 7, T(-1), T(1), Ec);
         E[c] = axis ? 0.0 : (double)x;
     }
     if (j < v.n2) {
-        E[nc + c] = (double)(q * ((T)F1[7 * nc + c - sk] + (T)F1[7 * nc + c] - (T)F3[6 * nc + c] -
-                                  (T)F3[6 * nc + c - 1]));
+        T x = q * ((T)F1[7 * nc + c - sk] + (T)F1[7 * nc + c] - (T)F3[6 * nc + c] - (T)F3[6 * nc + c - si]);
+        // p = x1 faces (value F1(B3)), q = x3 faces (value -F3(B1))
+        if (Ec) x += gs_correction<T>(c, si, sk, nc, F1, F3, 7, 6, T(1), T(-1), Ec + nc);
+        E[nc + c] = (double)x;
     }
     if (k < v.n3) {
-        const T x = q * ((T)F2[6 * nc + c - 1] + (T)F2[6 * nc + c] - (T)F1[6 * nc + c] - (T)F1[6 * nc + c - sj]);
+        T x = q * ((T)F2[6 * nc + c - si] + (T)F2[6 * nc + c] - (T)F1[6 * nc + c] - (T)F1[6 * nc + c - sj]);
+        // p = x1 faces (value -F1(B2)), q = x2 faces (value F2(B1))
+        if (Ec) x += gs_correction<T>(c, si, sj, nc, F1, F2, 6, 6, T(-1), T(1), Ec + 2 * nc);
         E[2 * nc + c] = axis ? 0.0 : (double)x;
     }
 }
 
 template <typename T>
 __global__ void k_emf(BlockView v, const double* __restrict__ F1, const double* __restrict__ F2,
-                      const double* __restrict__ F3, double* __restrict__ E) {
-    b_emf<T>(v, F1, F2, F3, E, (long)blockIdx.x * blockDim.x + threadIdx.x);
+                      const double* __restrict__ F3, double* __restrict__ E, const double* __restrict__ Ec) {
+    b_emf<T>(v, F1, F2, F3, E, Ec, (long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 
@@ -774,9 +838,15 @@ __global__ void __launch_bounds__(256) kb_flux(const DevBlock* tab, const int* l
 }
 
 template <typename T>
-__global__ void kb_emf(const DevBlock* tab, const int* list) {
+__global__ void kb_emf(const DevBlock* tab, const int* list, int upwind) {
     const DevBlock& D = tab[list[blockIdx.y]];
-    b_emf<T>(D.v, D.F1, D.F2, D.F3, D.E, tidx());
+    b_emf<T>(D.v, D.F1, D.F2, D.F3, D.E, upwind ? D.QL : nullptr, tidx());
+}
+
+// cell EMFs of the stage state into the edge-value scratch (free once the fluxes exist)
+__global__ void kb_cell_emf(const DevBlock* tab, const int* list, int sigma) {
+    const DevBlock& D = tab[list[blockIdx.y]];
+    b_cell_emf(D.v, sigma ? D.Ph : D.P, D.QL, tidx());
 }
 
 __global__ void kb_ct(const DevBlock* tab, const int* list, int sigma) {
@@ -950,12 +1020,16 @@ cudaError_t launch_flux(const BlockView& v, const PhysArgs& ph, int dir, const d
     return cudaGetLastError();
 }
 
-cudaError_t launch_emf(const BlockView& v, double* const F[3], double* E, int mixed, cudaStream_t s) {
+cudaError_t launch_emf(const BlockView& v, double* const F[3], double* E, int mixed, const double* P, double* Ec,
+                       cudaStream_t s) {
     const long n = (long)(v.n1 + 1) * (v.n2 + 1) * (v.n3 + 1);
+    if (Ec) {  // upwinded EMFs: the cell EMFs of the stage state P first
+        k_cell_emf<<<nblk((long)(v.n1 + 2) * (v.n2 + 2) * (v.n3 + 2)), BS, 0, s>>>(v, P, Ec);
+    }
     if (mixed)
-        k_emf<float><<<nblk(n), BS, 0, s>>>(v, F[0], F[1], F[2], E);
+        k_emf<float><<<nblk(n), BS, 0, s>>>(v, F[0], F[1], F[2], E, Ec);
     else
-        k_emf<double><<<nblk(n), BS, 0, s>>>(v, F[0], F[1], F[2], E);
+        k_emf<double><<<nblk(n), BS, 0, s>>>(v, F[0], F[1], F[2], E, Ec);
     return cudaGetLastError();
 }
 
@@ -1045,13 +1119,14 @@ cudaError_t launch_flux_batch(const DevBlock* tab, const int* list, int nlist, l
     return cudaGetLastError();
 }
 
-cudaError_t launch_emf_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, int mixed,
-                             cudaStream_t s) {
+cudaError_t launch_emf_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, int mixed, int upwind,
+                             long maxcells, int sigma, cudaStream_t s) {
     if (nlist <= 0) return cudaSuccess;
+    if (upwind) kb_cell_emf<<<bgrid(maxcells, nlist), BS, 0, s>>>(tab, list, sigma);
     if (mixed)
-        kb_emf<float><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list);
+        kb_emf<float><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, upwind);
     else
-        kb_emf<double><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list);
+        kb_emf<double><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, upwind);
     return cudaGetLastError();
 }
 
