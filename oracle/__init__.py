@@ -25,7 +25,7 @@ class Desc(C.Structure):
                 ("dx1", C.c_double), ("dx2", C.c_double), ("dx3", C.c_double),
                 ("metric", C.c_int), ("a", C.c_double), ("gam", C.c_double),
                 ("cour", C.c_double), ("recon", C.c_int), ("riemann", C.c_int),
-                ("bc", C.c_int * 6), ("floors", C.c_int), ("emf", C.c_int)]
+                ("bc", C.c_int * 6), ("floors", C.c_int), ("emf", C.c_int), ("flatten", C.c_int)]
 
 
 _libs = {}
@@ -45,6 +45,8 @@ def _setup(lib):
         "ora_face_flux": [P, _D, _D, C.c_double, C.c_double, C.c_int, _D],
         "ora_source": [P, _D, C.c_double, C.c_double, _D],
         "ora_recon_line": [C.c_int, C.c_int, _D, _D, _D],
+        "ora_flatten_line": [C.c_int, C.c_double, _D, _D, _D],
+        "ora_recon_line_flat": [C.c_int, _D, _D, _D, _D],
         "ora_c2p_many": [P, C.c_long, _D, _D, _D, _D, _D, _I, _I, C.c_int],
         "ora_p2u_many": [P, C.c_long, _D, _D, _D, _D],
         "ora_mlp_features": [P, C.c_long, _D, _D, _D, _D, _D],
@@ -89,7 +91,7 @@ def _p(a):
 
 def make_desc(n1, n2, n3, x1min, x2min, x3min, dx1, dx2, dx3, metric=METRIC_KS, a=0.0,
               gam=13.0 / 9.0, cour=0.8, recon=RECON_PPM, riemann=FLUX_HLL, bc=(0, 0, 0, 0, 1, 1),
-              floors=1, emf=EMF_AVERAGE):
+              floors=1, emf=EMF_AVERAGE, flatten=0):
     d = Desc()
     d.n1, d.n2, d.n3 = n1, n2, n3
     d.x1min, d.x2min, d.x3min = x1min, x2min, x3min
@@ -100,6 +102,7 @@ def make_desc(n1, n2, n3, x1min, x2min, x3min, dx1, dx2, dx3, metric=METRIC_KS, 
         d.bc[m] = bc[m]
     d.floors = floors
     d.emf = emf
+    d.flatten = flatten
     return d
 
 
@@ -160,6 +163,25 @@ def recon_line(recon, q):
     al = np.full_like(q, np.nan)
     ar = np.full_like(q, np.nan)
     lib().ora_recon_line(recon, len(q), _p(q), _p(al), _p(ar))
+    return al, ar
+
+
+def flatten_line(gam, u, w):
+    """Shock flattening coefficients of a line (PPM, Colella & Woodward 1984)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    f = np.zeros_like(u)
+    lib().ora_flatten_line(len(u), gam, _p(u), _p(w), _p(f))
+    return f
+
+
+def recon_line_flat(q, f):
+    """PPM edge values of a line with flattening coefficients f."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    al = np.full_like(q, np.nan)
+    ar = np.full_like(q, np.nan)
+    lib().ora_recon_line_flat(len(q), _p(q), _p(f), _p(al), _p(ar))
     return al, ar
 
 

@@ -303,13 +303,45 @@ static real slope_minmod(real qm, real q0, real qp) {
  * a_{c+1/2} = (q_c + q_{c+1})/2 - (dq_{c+1} - dq_c)/6 with monotonised slopes,
  * then the per-cell parabola constraints. Valid for c = 2..n-3.
  * MC / MINMOD: piecewise linear, valid for c = 1..n-2. */
-static void recon_line_impl(int recon, int n, const real* q, real* al, real* ar) {
+/* Shock flattening coefficient of every cell of a line (Colella & Woodward 1984,
+ * their flattening of the interface values near strong shocks), from the
+ * internal energy u (p = (gam - 1) u) and the velocity primitive w along the
+ * line. Reading: a cell sits in a shock when the pressure jumps across it by
+ * more than 0.33 of the smaller neighbour, |p(c+1) - p(c-1)| >
+ * 0.33 min(p(c+1), p(c-1)), and the flow converges there, w(c-1) > w(c+1);
+ * then f = 10 (dp1 / dp2 - 3/4) clamped to [0, 1], dp1 = p(c+1) - p(c-1),
+ * dp2 = p(c+2) - p(c-2) (a sharp jump gives dp1 = dp2, f = 1; a linear ramp
+ * dp2 = 2 dp1, f = 0). The coefficient stays with its cell: Colella & Woodward
+ * also take the larger coefficient of the upwind neighbour, whose stencil
+ * would reach past three ghost layers. Gas pressure only (no magnetic term).
+ * Valid for c = 2..n-3; f = 0 elsewhere. */
+static void flatten_line(int n, real gam, const real* u, const real* w, real* f) {
+    for (int c = 0; c < n; c++) f[c] = 0.0;
+    for (int c = 2; c <= n - 3; c++) {
+        real pm = (gam - 1.0) * u[c - 1], pp = (gam - 1.0) * u[c + 1];
+        real dp1 = pp - pm;
+        real dp2 = (gam - 1.0) * (u[c + 2] - u[c - 2]);
+        real pmin = pm < pp ? pm : pp;
+        if (fabs(dp1) > 0.33 * pmin && w[c - 1] > w[c + 1] && dp2 != 0.0) {
+            real x = 10.0 * (dp1 / dp2 - 0.75);
+            f[c] = x < 0.0 ? real(0.0) : (x > 1.0 ? real(1.0) : x);
+        }
+    }
+}
+
+/* flat: optional per-cell flattening coefficients f in [0, 1] (Colella & Woodward 1984): the
+ * interface values become f q + (1 - f) a before the parabola constraints */
+static void recon_line_impl(int recon, int n, const real* q, real* al, real* ar, const real* flat = nullptr) {
     if (recon == ORA_RECON_PPM) {
         std::vector<real> dq(n, real(0.0)), ah(n, real(0.0));
         for (int c = 1; c <= n - 2; c++) dq[c] = slope_mc(q[c - 1], q[c], q[c + 1]);
         for (int c = 1; c <= n - 3; c++) ah[c] = 0.5 * (q[c] + q[c + 1]) - (dq[c + 1] - dq[c]) / 6.0;
         for (int c = 2; c <= n - 3; c++) {
             real aL = ah[c - 1], aR = ah[c], q0 = q[c];
+            if (flat) {
+                aL = flat[c] * q0 + (1.0 - flat[c]) * aL;
+                aR = flat[c] * q0 + (1.0 - flat[c]) * aR;
+            }
             if ((aR - q0) * (q0 - aL) <= 0.0) {
                 aL = q0;
                 aR = q0;
@@ -779,9 +811,23 @@ void stage_fluxes(ora_grid* g, const double* Pf, const double* Bff, Fluxes& F) {
         std::vector<real> PL((size_t)NPR * L), PR((size_t)NPR * L);
         /* loop over lines along dir */
         int ta = (dir == 1) ? 2 : 1, tb = (dir == 3) ? 2 : 3;
+        std::vector<real> flat(L, real(0.0));
         for (int b = lo[tb]; b <= hi[tb]; b++)
             for (int a = lo[ta]; a <= hi[ta]; a++) {
                 phase_begin();
+                if (d.flatten && d.recon == ORA_RECON_PPM) {
+                    std::vector<real> uu(L), ww(L);
+                    for (int c = 0; c < L; c++) {
+                        int ii[4];
+                        ii[dir] = c - NG;
+                        ii[ta] = a;
+                        ii[tb] = b;
+                        const size_t ci = cidx(g, ii[1], ii[2], ii[3]);
+                        uu[c] = Pf[UU * nc + ci];
+                        ww[c] = Pf[(U1 + dir - 1) * nc + ci];
+                    }
+                    flatten_line(L, d.gam, uu.data(), ww.data(), flat.data());
+                }
                 for (int v = 0; v < NPR; v++) {
                     if (v == B1 + dir - 1) continue;
                     for (int c = 0; c < L; c++) {
@@ -791,7 +837,8 @@ void stage_fluxes(ora_grid* g, const double* Pf, const double* Bff, Fluxes& F) {
                         ii[tb] = b;
                         q[c] = Pf[v * nc + cidx(g, ii[1], ii[2], ii[3])];
                     }
-                    recon_line_impl(d.recon, L, q.data(), al.data(), ar.data());
+                    recon_line_impl(d.recon, L, q.data(), al.data(), ar.data(),
+                                    (d.flatten && d.recon == ORA_RECON_PPM) ? flat.data() : nullptr);
                     for (int c = 0; c < L; c++) {
                         PL[(size_t)v * L + c] = al[c];
                         PR[(size_t)v * L + c] = ar[c];
@@ -1189,6 +1236,31 @@ void ora_recon_line(int recon, int n, const double* q, double* al, double* ar) {
         b[c] = ar[c];
     }
     recon_line_impl(recon, n, qq.data(), a.data(), b.data());
+    for (int c = 0; c < n; c++) {
+        al[c] = tod(a[c]);
+        ar[c] = tod(b[c]);
+    }
+}
+
+void ora_flatten_line(int n, double gam, const double* u, const double* w, double* f) {
+    std::vector<real> uu(n), ww(n), ff(n);
+    for (int c = 0; c < n; c++) {
+        uu[c] = u[c];
+        ww[c] = w[c];
+    }
+    flatten_line(n, gam, uu.data(), ww.data(), ff.data());
+    for (int c = 0; c < n; c++) f[c] = tod(ff[c]);
+}
+
+void ora_recon_line_flat(int n, const double* q, const double* f, double* al, double* ar) {
+    std::vector<real> qq(n), ff(n), a(n, real(0.0)), b(n, real(0.0));
+    for (int c = 0; c < n; c++) {
+        qq[c] = q[c];
+        ff[c] = f[c];
+        a[c] = al[c];
+        b[c] = ar[c];
+    }
+    recon_line_impl(ORA_RECON_PPM, n, qq.data(), a.data(), b.data(), ff.data());
     for (int c = 0; c < n; c++) {
         al[c] = tod(a[c]);
         ar[c] = tod(b[c]);

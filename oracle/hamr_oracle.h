@@ -37,6 +37,7 @@ typedef struct {
     int bc[6];                      /* x1lo x1hi x2lo x2hi x3lo x3hi: ORA_BC_* */
     int floors;                     /* 1: apply the density/energy floors */
     int emf;                        /* ORA_EMF_*: edge EMFs as the 4-flux average or upwinded */
+    int flatten;                    /* 1: PPM shock flattening (Colella & Woodward 1984) */
 } ora_desc;
 
 /* ---- point-wise pieces (each documented in hamr_oracle.cpp) ---- */
@@ -52,6 +53,10 @@ void ora_face_flux(const ora_desc* d, const double* pl8, const double* pr8, doub
                    int dir, double* f8);
 void ora_source(const ora_desc* d, const double* pr8, double x1, double x2, double* q6);
 void ora_recon_line(int recon, int n, const double* q, double* al, double* ar);
+/* PPM shock flattening: coefficients of a line from u and the velocity
+ * primitive along it, and PPM edge values with given coefficients */
+void ora_flatten_line(int n, double gam, const double* u, const double* w, double* f);
+void ora_recon_line_flat(int n, const double* q, const double* f, double* al, double* ar);
 /* con2prim on n independent states: U6 (sqrt(-g) weighted), B3 centre B^i,
  * x1/x2 positions, pr8 in: guess, out: result; status/iters per state.
  * entropy_only = 1 skips the energy inversion (tests of the backup path). */

@@ -865,3 +865,17 @@ def field_loop_block(n1, n2, n3=4, L=1.0, R=0.3, A0=1e-3, rho=1.0, p=0.1, v=(0.4
         bface[0, NG + k, NG:NG + n2, NG:NG + n1 + 1] = b1
         bface[1, NG + k, NG:NG + n2 + 1, NG:NG + n1] = b2
     return prim, bface, dx1, dx2
+
+
+def riemann_block(n1, left, right, n2=4, n3=4, x0=0.5, gam=5.0 / 3.0):
+    """A one-dimensional Riemann problem along x1 of a unit flat-space box: states (rho, p, v) left
+    and right of x = x0 (v the x1 3-velocity), uniform across x2 and x3 (n2 x n3 cells). Returns
+    the padded primitive array and zero face B."""
+    shp = (n3 + 2 * NG, n2 + 2 * NG, n1 + 2 * NG)
+    prim = np.zeros((8,) + shp)
+    x = (np.arange(-NG, n1 + NG) + 0.5) / n1
+    on_left = x < x0
+    for q, (a, b) in enumerate([(left[0], right[0]), (left[1] / (gam - 1.0), right[1] / (gam - 1.0)),
+                                (left[2] / math.sqrt(1.0 - left[2] ** 2), right[2] / math.sqrt(1.0 - right[2] ** 2))]):
+        prim[q][...] = np.where(on_left, a, b)[None, None, :]
+    return prim, np.zeros((3,) + shp)
