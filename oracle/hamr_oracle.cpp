@@ -309,9 +309,13 @@ static real slope_minmod(real qm, real q0, real qp) {
  * line. Reading: a cell sits in a shock when the pressure jumps across it by
  * more than 0.33 of the smaller neighbour, |p(c+1) - p(c-1)| >
  * 0.33 min(p(c+1), p(c-1)), and the flow converges there, w(c-1) > w(c+1);
- * then f = 10 (dp1 / dp2 - 3/4) clamped to [0, 1], dp1 = p(c+1) - p(c-1),
- * dp2 = p(c+2) - p(c-2) (a sharp jump gives dp1 = dp2, f = 1; a linear ramp
- * dp2 = 2 dp1, f = 0). The coefficient stays with its cell: Colella & Woodward
+ * then f = 10 (|dp1| / |dp2| - 3/4) clamped to [0, 1], dp1 = p(c+1) - p(c-1),
+ * dp2 = p(c+2) - p(c-2) (a sharp jump gives |dp1| = |dp2|, f = 1; a linear
+ * ramp |dp2| = 2 |dp1|, f = 0). Reading: the ratio is taken in magnitude and
+ * dp2 = 0 counts as an infinitely sharp jump (f = 1). On a monotone profile
+ * this is the signed ratio; at a narrow pressure peak (two shocks leaving a
+ * collision) p(c+2) - p(c-2) vanishes up to rounding, and the signed ratio
+ * would jump between plus and minus infinity on the rounding noise. The coefficient stays with its cell: Colella & Woodward
  * also take the larger coefficient of the upwind neighbour, whose stencil
  * would reach past three ghost layers. Gas pressure only (no magnetic term).
  * Valid for c = 2..n-3; f = 0 elsewhere. */
@@ -322,9 +326,14 @@ static void flatten_line(int n, real gam, const real* u, const real* w, real* f)
         real dp1 = pp - pm;
         real dp2 = (gam - 1.0) * (u[c + 2] - u[c - 2]);
         real pmin = pm < pp ? pm : pp;
-        if (fabs(dp1) > 0.33 * pmin && w[c - 1] > w[c + 1] && dp2 != 0.0) {
-            real x = 10.0 * (dp1 / dp2 - 0.75);
-            f[c] = x < 0.0 ? real(0.0) : (x > 1.0 ? real(1.0) : x);
+        real a1 = fabs(dp1), a2 = fabs(dp2);
+        if (a1 > 0.33 * pmin && w[c - 1] > w[c + 1]) {
+            if (a2 == 0.0) {
+                f[c] = 1.0;
+            } else {
+                real x = 10.0 * (a1 / a2 - 0.75);
+                f[c] = x < 0.0 ? real(0.0) : (x > 1.0 ? real(1.0) : x);
+            }
         }
     }
 }

@@ -46,6 +46,20 @@ def test_partial_coefficient_and_two_cell_shock():
     assert f.tolist() == [0, 0, 0, 1, 0, 0, 0]
 
 
+def test_narrow_pressure_peak_is_flattened_whatever_the_rounding_noise():
+    """Two streams meeting: a two-cell pressure peak. For the peak cells p(c+2) - p(c-2) is zero,
+    or rounding noise after a step; the coefficient (magnitude ratio) is 1 on the peak and its
+    flanks either way, and 0 away from it."""
+    conv = np.linspace(0.5, -0.5, 10)
+    base = np.array([0.01] * 4 + [0.7, 0.7] + [0.01] * 4)
+    want = [0, 0, 0, 1, 1, 1, 1, 0, 0, 0]
+    assert _coef(base, conv).tolist() == want
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        noisy = base * (1.0 + 1e-15 * rng.standard_normal(10))
+        assert _coef(noisy, conv).tolist() == want
+
+
 def test_reconstruction_at_the_coefficient_ends():
     rng = np.random.default_rng(5)
     q = np.cumsum(rng.normal(size=40))
