@@ -100,6 +100,10 @@ typedef struct {
     int nblocks;         /* >= 1 */
     const hamr_block_desc* blocks; /* nblocks descriptors, copied by hamr_grid_create */
     int emf;             /* HAMR_EMF_*: edge EMFs (Sec. 2.5) */
+    int flatten;         /* 1: PPM shock flattener (Sec. 2.1, Colella & Woodward 1984): where a
+                            pressure jump above 0.33 of the lower side meets converging flow,
+                            the interface values of the cell move toward its value; ignored
+                            unless recon is HAMR_RECON_PPM. 0 or 1, else HAMR_EINVAL */
 } hamr_grid_desc;
 
 /* Counters of the last step (summed over its two stages and all blocks

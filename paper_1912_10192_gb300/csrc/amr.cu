@@ -1073,6 +1073,7 @@ int group_step(AmrImpl& M, int L, int s, cudaStream_t cs) {
         AM_TRY(cudaGetLastError());
         if (ph.mixed) AM_TRY(launch_to_f32_batch(tab, list, nl, M.lmw_pad[L], sigma, cs));
         for (int dir = 1; dir <= 3; dir++) {
+            if (ph.flatten) AM_TRY(launch_flatten_batch(tab, list, nl, M.lmw_ext[L], ph, dir, sigma, cs));
             AM_TRY(launch_recon_batch(tab, list, nl, M.lmw_recon[L][dir], ph, dir, sigma, cs));
             AM_TRY(launch_flux_batch(tab, list, nl, M.lmw_flux[L][dir], ph, dir, sigma, cs));
         }
@@ -1228,7 +1229,11 @@ int amr_time_group(AmrImpl* M, const PhysArgs& ph, int which, cudaStream_t cs, f
             if (e != cudaSuccess) rc = set_error(HAMR_ECUDA, "launch failed: %s", cudaGetErrorString(e));
         }
         for (int dir = 1; dir <= 3 && rc == HAMR_OK; dir++) {
-            auto rec = [&]() { return launch_recon_batch(tab, list, nl, mwr[dir], ph, dir, 0, cs); };
+            auto rec = [&]() {
+                cudaError_t e = ph.flatten ? launch_flatten_batch(tab, list, nl, M->lmw_ext[L], ph, dir, 0, cs)
+                                           : cudaSuccess;
+                return e == cudaSuccess ? launch_recon_batch(tab, list, nl, mwr[dir], ph, dir, 0, cs) : e;
+            };
             auto flx = [&]() { return launch_flux_batch(tab, list, nl, M->lmw_flux[L][dir], ph, dir, 0, cs); };
             if (which == 0) {
                 rc = timed(rec);

@@ -149,6 +149,7 @@ int validate(const hamr_grid_desc* d) {
     if (d->precision != HAMR_PREC_FP64 && d->precision != HAMR_PREC_MIXED)
         return fail(HAMR_EINVAL, "unknown precision %d", d->precision);
     if (d->emf != HAMR_EMF_AVERAGE && d->emf != HAMR_EMF_UPWIND) return fail(HAMR_EINVAL, "unknown emf %d", d->emf);
+    if (d->flatten != 0 && d->flatten != 1) return fail(HAMR_EINVAL, "flatten must be 0 or 1, got %d", d->flatten);
     for (int b = 0; b < d->nblocks; b++) {
         const hamr_block_desc& B = d->blocks[b];
         if (B.n1 < 4 || B.n2 < 4 || B.n3 < 4) return fail(HAMR_EINVAL, "block %d: each n must be >= 4", b);
@@ -351,6 +352,7 @@ int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out) {
     g->ph.mlp_mode = HAMR_MLP_FIRST;
     default_launch_shapes(g->ph);
     g->ph.emf = d->emf;
+    g->ph.flatten = (d->flatten && d->recon == HAMR_RECON_PPM) ? 1 : 0;
     cudaGetDevice(&g->device);
     for (int b = 0; b < d->nblocks; b++) {
         rc = alloc_block(g, b);
@@ -440,10 +442,11 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
     LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.P, s.B, cs));
     if (ph.mixed) LAUNCH(g, K_BC, 1, cs, launch_to_f32(v, s.P, s.P32, cs));
     for (int dir = 1; dir <= 3; dir++) {
+        if (ph.flatten) LAUNCH(g, K_RECON, 1, cs, launch_flatten(v, ph, dir, s.P, s.P32, s.QL, cs));
         LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.P, s.P32, s.QL, s.QR, cs));
         LAUNCH(g, K_FLUX, 1, cs, launch_flux(v, ph, dir, s.QL, s.QR, s.B, s.F[dir - 1], cs));
     }
-    LAUNCH(g, K_EMF, 1, cs, launch_emf(v, s.F, s.E, ph.mixed, s.P, ph.emf ? s.QL : nullptr, cs));
+    LAUNCH(g, K_EMF, ph.emf ? 2 : 1, cs, launch_emf(v, s.F, s.E, ph.mixed, s.P, ph.emf ? s.QL : nullptr, cs));
     LAUNCH(g, K_CT, 1, cs, launch_ct(v, s.E, s.B, s.Bh, s.dscal, 0.5, cs));
     LAUNCH(g, K_UPDATE, 1, cs,
            launch_update(v, ph, 0, s.P, s.P, s.F, s.Bh, s.Un, s.Ph, s.status, s.dscal, 0.5, s.dmax, s.dcnt, cs));
@@ -451,10 +454,11 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
     LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.Ph, s.Bh, cs));
     if (ph.mixed) LAUNCH(g, K_BC, 1, cs, launch_to_f32(v, s.Ph, s.P32, cs));
     for (int dir = 1; dir <= 3; dir++) {
+        if (ph.flatten) LAUNCH(g, K_RECON, 1, cs, launch_flatten(v, ph, dir, s.Ph, s.P32, s.QL, cs));
         LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.Ph, s.P32, s.QL, s.QR, cs));
         LAUNCH(g, K_FLUX, 1, cs, launch_flux(v, ph, dir, s.QL, s.QR, s.Bh, s.F[dir - 1], cs));
     }
-    LAUNCH(g, K_EMF, 1, cs, launch_emf(v, s.F, s.E, ph.mixed, s.Ph, ph.emf ? s.QL : nullptr, cs));
+    LAUNCH(g, K_EMF, ph.emf ? 2 : 1, cs, launch_emf(v, s.F, s.E, ph.mixed, s.Ph, ph.emf ? s.QL : nullptr, cs));
     LAUNCH(g, K_CT, 1, cs, launch_ct(v, s.E, s.B, s.B, s.dscal, 1.0, cs));
     LAUNCH(g, K_UPDATE, 1, cs,
            launch_update(v, ph, 1, s.P, s.Ph, s.F, s.B, s.Un, s.P, s.status, s.dscal, 1.0, s.dmax, s.dcnt, cs));
@@ -589,6 +593,7 @@ int time_group_block(hamr_grid* g, const PhysArgs& ph, int which, cudaStream_t c
         if (ph.mixed) CUDA_TRY(launch_to_f32(v, s.P, s.P32, cs));
         for (int dir = 1; dir <= 3; dir++) {
             if (which == 0) CUDA_TRY(cudaEventRecord(a, cs));
+            if (ph.flatten) CUDA_TRY(launch_flatten(v, ph, dir, s.P, s.P32, s.QL, cs));
             CUDA_TRY(launch_recon(v, ph, dir, s.P, s.P32, s.QL, s.QR, cs));
             if (which == 1) CUDA_TRY(cudaEventRecord(a, cs));
             if (which != 0) CUDA_TRY(launch_flux(v, ph, dir, s.QL, s.QR, s.B, s.F[dir - 1], cs));

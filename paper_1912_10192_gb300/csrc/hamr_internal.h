@@ -53,7 +53,8 @@ struct PhysArgs {
     // launch shapes (hamr_grid_autotune): threads per CTA of the reconstruction,
     // flux and cell-update kernels, cells per thread of the x2/x3 sweeps
     int bs_recon, bs_flux, bs_update, recon_seg;
-    int emf;  // HAMR_EMF_*
+    int emf;      // HAMR_EMF_*
+    int flatten;  // 1: PPM shock flattening (only set with HAMR_RECON_PPM)
 };
 
 // threads of one reconstruction launch (FP64): rows along x1 in warps of 32
@@ -134,6 +135,9 @@ cudaError_t launch_bc(const BlockView& v, double* P, double* B, cudaStream_t s);
 cudaError_t launch_recon(const BlockView& v, const PhysArgs& ph, int dir, const double* P, const float* P32,
                          double* QL, double* QR, cudaStream_t s);
 cudaError_t launch_to_f32(const BlockView& v, const double* P, float* P32, cudaStream_t s);
+// PPM shock-flattening coefficients of direction dir into the B^dir field of QL (before launch_recon)
+cudaError_t launch_flatten(const BlockView& v, const PhysArgs& ph, int dir, const double* P, const float* P32,
+                           double* QL, cudaStream_t s);
 cudaError_t launch_flux(const BlockView& v, const PhysArgs& ph, int dir, const double* QL, const double* QR,
                         const double* Bf, double* F, cudaStream_t s);
 // upwinded EMFs when Ec (3 fields of scratch, stride nc) is given: the cell EMFs of P go there first
@@ -158,6 +162,9 @@ cudaError_t launch_to_f32_batch(const DevBlock* tab, const int* list, int nlist,
                                 cudaStream_t s);
 cudaError_t launch_recon_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
                                int dir, int sigma, cudaStream_t s);
+// maxcells: largest (n1 + 2)(n2 + 2)(n3 + 2) of the listed blocks
+cudaError_t launch_flatten_batch(const DevBlock* tab, const int* list, int nlist, long maxcells, const PhysArgs& ph,
+                                 int dir, int sigma, cudaStream_t s);
 cudaError_t launch_flux_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
                               int dir, int sigma, cudaStream_t s);
 cudaError_t launch_emf_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, int mixed, int upwind,

@@ -81,6 +81,8 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
         return set_error(HAMR_EINVAL, "polar bc needs even n3 and the KS metric");
     if (d->precision != HAMR_PREC_FP64) return set_error(HAMR_EINVAL, "the no-allocation step is FP64 only");
     if (d->emf != HAMR_EMF_AVERAGE && d->emf != HAMR_EMF_UPWIND) return set_error(HAMR_EINVAL, "unknown emf %d", d->emf);
+    if (d->flatten != 0 && d->flatten != 1)
+        return set_error(HAMR_EINVAL, "flatten must be 0 or 1, got %d", d->flatten);
 
     double* base = nullptr;
     int rc = setup(&base);
@@ -154,6 +156,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     ph.mlp_mode = HAMR_MLP_FIRST;
     default_launch_shapes(ph);
     ph.emf = d->emf;
+    ph.flatten = (d->flatten && d->recon == HAMR_RECON_PPM) ? 1 : 0;
 
     // the array keeps the previous call's contents: clear what must start at zero
     NA_TRY(cudaMemsetAsync(s.Ph, 0, sizeof(double) * 11 * v.nc, cs));
@@ -186,6 +189,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     // predictor
     NA_TRY(launch_bc(v, s.P, s.B, cs));
     for (int dir = 1; dir <= 3; dir++) {
+        if (ph.flatten) NA_TRY(launch_flatten(v, ph, dir, s.P, nullptr, s.QL, cs));
         NA_TRY(launch_recon(v, ph, dir, s.P, nullptr, s.QL, s.QR, cs));
         NA_TRY(launch_flux(v, ph, dir, s.QL, s.QR, s.B, s.F[dir - 1], cs));
     }
@@ -195,6 +199,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     // corrector
     NA_TRY(launch_bc(v, s.Ph, s.Bh, cs));
     for (int dir = 1; dir <= 3; dir++) {
+        if (ph.flatten) NA_TRY(launch_flatten(v, ph, dir, s.Ph, nullptr, s.QL, cs));
         NA_TRY(launch_recon(v, ph, dir, s.Ph, nullptr, s.QL, s.QR, cs));
         NA_TRY(launch_flux(v, ph, dir, s.QL, s.QR, s.Bh, s.F[dir - 1], cs));
     }

@@ -140,6 +140,61 @@ __global__ void k_bc_axis(BlockView v, double* __restrict__ B) {
 // x3 a thread sweeps recon_seg cells of one pencil (consecutive threads on
 // consecutive i, so loads and stores coalesce). T = float (mixed precision)
 // reads the FP32 copy of the primitives and writes FP32 edge values.
+// Shock flattening (Colella & Woodward 1984), optional with PPM: a coefficient
+// f in [0, 1] per cell of the reconstruction range, from p = (gam - 1) u and
+// the velocity primitive w along dir. A relative pressure jump across the
+// cell above 0.33 of the smaller neighbour with converging flow (w(c-1) >
+// w(c+1)) marks a shock; f = 10 (|dp1| / |dp2| - 3/4) clamped to [0, 1], dp1 =
+// p(c+1) - p(c-1), dp2 = p(c+2) - p(c-2), and f = 1 for dp2 = 0 (the ratio in
+// magnitude: at a narrow pressure peak dp2 is zero up to rounding, and a
+// signed ratio would follow the rounding noise). The coefficient stays with its cell
+// (no max with the upwind neighbour: its stencil would pass three ghost
+// layers). It is written to the B^dir field of QL, which the reconstruction
+// of dir leaves unused; the reconstruction blends both interface values of
+// the cell toward its value, f q + (1 - f) a, before the parabola constraints.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
+template <int DIR, typename T>
+__device__ __forceinline__ void b_flatten(const BlockView& v, PhysArgs ph, const T* __restrict__ P,
+                                          T* __restrict__ Fl, long t) {
+    const int e1 = v.n1 + 2, e2 = v.n2 + 2, e3 = v.n3 + 2;
+    if (t >= (long)e1 * e2 * e3) return;
+    const int i = (int)(t % e1) - 1, j = (int)((t / e1) % e2) - 1, k = (int)(t / ((long)e1 * e2)) - 1;
+    const long c = cidx(v, i, j, k);
+    const long st = (DIR == 1) ? 1 : ((DIR == 2) ? (long)v.n1p : (long)v.n1p * v.n2p);
+    const T* u = P + UU * v.nc + c;
+    const T* w = P + (U1 + DIR - 1) * v.nc + c;
+    const T gm1 = (T)(ph.gam - 1.0);
+    // products rounded on their own (no contraction into the differences)
+    const T pm = mul_rn(gm1, u[-st]), pp = mul_rn(gm1, u[st]);
+    const T dp1 = pp - pm;
+    const T dp2 = mul_rn(gm1, u[2 * st] - u[-2 * st]);
+    const T pmin = pm < pp ? pm : pp;
+    const T a1 = fabs(dp1), a2 = fabs(dp2);
+    T f = T(0);
+    if (a1 > mul_rn(T(0.33), pmin) && w[-st] > w[st]) {
+        if (a2 == T(0)) {
+            f = T(1);
+        } else {
+            const T x = mul_rn(T(10), a1 / a2 - T(0.75));
+            f = x < T(0) ? T(0) : (x > T(1) ? T(1) : x);
+        }
+    }
+    Fl[c] = f;
+}
+
+template <int DIR, typename T>
+__global__ void k_flatten(BlockView v, PhysArgs ph, const T* __restrict__ P, T* __restrict__ Fl) {
+    b_flatten<DIR, T>(v, ph, P, Fl, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <typename T>
+__device__ __forceinline__ void flatten_edges(T f, T qc, T& l, T& r) {
+    l = f * qc + (T(1) - f) * l;
+    r = f * qc + (T(1) - f) * r;
+}
+
 template <int DIR>
 __device__ __forceinline__ int recon_var(int n) {  // the n-th of the 7 reconstructed primitives
     return n + (n >= B1 + DIR - 1 ? 1 : 0);
@@ -176,6 +231,7 @@ __device__ __forceinline__ void b_recon_row(const BlockView& v, PhysArgs ph, con
         const T sp = __shfl_down_sync(0xffffffffu, sc, 1);
         r = ppm_face(qc, qp, sc, sp);                         // interface i+1/2, valid on lanes 1..29
         l = __shfl_up_sync(0xffffffffu, r, 1);                // interface i-1/2, valid on lanes 2..30
+        if (ph.flatten) flatten_edges(QL[(B1 + 0) * v.nc + c + ic], qc, l, r);
         ppm_limit(qc, l, r);
     } else {
         const T dq = limited_slope(ph.recon, qm, qc, qp);
@@ -217,6 +273,7 @@ __device__ __forceinline__ void b_recon_sweep(const BlockView& v, PhysArgs ph, c
             const T sp = mc_slope_i(qc, qp, qpp);
             const T fr = ppm_face(qc, qp, sc, sp);  // interface a + 1/2
             T l = fl, r = fr;
+            if (ph.flatten) flatten_edges(QL[(B1 + DIR - 1) * v.nc + c0 - q * v.nc + m * st], qc, l, r);
             ppm_limit(qc, l, r);
             QL[c0 + m * st] = l;
             QR[c0 + m * st] = r;
@@ -259,6 +316,7 @@ __device__ __forceinline__ void b_recon_cell(const BlockView& v, PhysArgs ph, co
                     sp = mc_slope_i(qc, qp, p[2 * st]);
             l = ppm_face(qm, qc, sm, sc);
             r = ppm_face(qc, qp, sc, sp);
+            if (ph.flatten) flatten_edges(QL[(B1 + DIR - 1) * v.nc + c], qc, l, r);
             ppm_limit(qc, l, r);
         } else {
             const T dq = limited_slope(ph.recon, p[-st], p[0], p[st]);
@@ -824,6 +882,15 @@ __global__ void kb_recon(const DevBlock* tab, const int* list, PhysArgs ph, int 
         b_recon<DIR, T>(D.v, ph, D.P32, reinterpret_cast<float*>(D.QL), reinterpret_cast<float*>(D.QR), tidx());
 }
 
+template <int DIR, typename T>
+__global__ void kb_flatten(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
+    const DevBlock& D = tab[list[blockIdx.y]];
+    if constexpr (std::is_same<T, double>::value)
+        b_flatten<DIR, T>(D.v, ph, sigma ? D.Ph : D.P, D.QL + (long)(B1 + DIR - 1) * D.v.nc, tidx());
+    else
+        b_flatten<DIR, T>(D.v, ph, D.P32, reinterpret_cast<float*>(D.QL) + (long)(B1 + DIR - 1) * D.v.nc, tidx());
+}
+
 __global__ void kb_to_f32(const DevBlock* tab, const int* list, int sigma) {
     const DevBlock& D = tab[list[blockIdx.y]];
     b_to_f32(D.v, sigma ? D.Ph : D.P, D.P32, tidx());
@@ -976,6 +1043,23 @@ cudaError_t launch_bc(const BlockView& v, double* P, double* B, cudaStream_t s) 
     return cudaGetLastError();
 }
 
+cudaError_t launch_flatten(const BlockView& v, const PhysArgs& ph, int dir, const double* P, const float* P32,
+                           double* QL, cudaStream_t s) {
+    const long n = (long)(v.n1 + 2) * (v.n2 + 2) * (v.n3 + 2);
+    const long off = (long)(B1 + dir - 1) * v.nc;
+    if (ph.mixed) {
+        float* F = reinterpret_cast<float*>(QL) + off;
+        if (dir == 1) k_flatten<1, float><<<nblk(n), BS, 0, s>>>(v, ph, P32, F);
+        if (dir == 2) k_flatten<2, float><<<nblk(n), BS, 0, s>>>(v, ph, P32, F);
+        if (dir == 3) k_flatten<3, float><<<nblk(n), BS, 0, s>>>(v, ph, P32, F);
+    } else {
+        if (dir == 1) k_flatten<1, double><<<nblk(n), BS, 0, s>>>(v, ph, P, QL + off);
+        if (dir == 2) k_flatten<2, double><<<nblk(n), BS, 0, s>>>(v, ph, P, QL + off);
+        if (dir == 3) k_flatten<3, double><<<nblk(n), BS, 0, s>>>(v, ph, P, QL + off);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_recon(const BlockView& v, const PhysArgs& ph, int dir, const double* P, const float* P32,
                          double* QL, double* QR, cudaStream_t s) {
     const long n = recon_threads(v, dir, ph.mixed, ph.recon_seg);
@@ -1091,6 +1175,22 @@ cudaError_t launch_recon_batch(const DevBlock* tab, const int* list, int nlist, 
         if (dir == 1) kb_recon<1, double><<<g, bs, 0, s>>>(tab, list, ph, sigma);
         if (dir == 2) kb_recon<2, double><<<g, bs, 0, s>>>(tab, list, ph, sigma);
         if (dir == 3) kb_recon<3, double><<<g, bs, 0, s>>>(tab, list, ph, sigma);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flatten_batch(const DevBlock* tab, const int* list, int nlist, long maxcells, const PhysArgs& ph,
+                                 int dir, int sigma, cudaStream_t s) {
+    if (nlist <= 0) return cudaSuccess;
+    const dim3 g = bgrid(maxcells, nlist);
+    if (ph.mixed) {
+        if (dir == 1) kb_flatten<1, float><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 2) kb_flatten<2, float><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 3) kb_flatten<3, float><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+    } else {
+        if (dir == 1) kb_flatten<1, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 2) kb_flatten<2, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
+        if (dir == 3) kb_flatten<3, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
     }
     return cudaGetLastError();
 }

@@ -41,7 +41,8 @@ class BlockDesc(C.Structure):
 class GridDesc(C.Structure):
     _fields_ = [("metric", C.c_int), ("a", C.c_double), ("gam", C.c_double), ("cour", C.c_double),
                 ("recon", C.c_int), ("riemann", C.c_int), ("floors", C.c_int), ("precision", C.c_int),
-                ("nblocks", C.c_int), ("blocks", C.POINTER(BlockDesc)), ("emf", C.c_int)]
+                ("nblocks", C.c_int), ("blocks", C.POINTER(BlockDesc)), ("emf", C.c_int),
+                ("flatten", C.c_int)]
 
 
 class StepStats(C.Structure):
@@ -175,12 +176,13 @@ class Grid:
     """Owner of a hamr_grid handle."""
 
     def __init__(self, blocks, metric=METRIC_KS, a=0.9375, gam=13.0 / 9.0, cour=0.8, recon=RECON_PPM,
-                 riemann=FLUX_HLL, floors=1, precision=PREC_FP64, emf=EMF_AVERAGE):
+                 riemann=FLUX_HLL, floors=1, precision=PREC_FP64, emf=EMF_AVERAGE, flatten=0):
         self._blocks = (BlockDesc * len(blocks))(*blocks)
         d = GridDesc()
         d.metric, d.a, d.gam, d.cour = metric, a, gam, cour
         d.recon, d.riemann, d.floors, d.precision = recon, riemann, floors, precision
         d.emf = emf
+        d.flatten = flatten
         d.nblocks = len(blocks)
         d.blocks = self._blocks
         self.desc = d
