@@ -17,6 +17,7 @@ METRIC_KS, METRIC_MINKOWSKI = 0, 1
 RECON_PPM, RECON_MC, RECON_MINMOD = 0, 1, 2
 FLUX_HLL, FLUX_LLF = 0, 1
 EMF_AVERAGE, EMF_UPWIND = 0, 1
+INV_NEWTON, INV_AITKEN = 0, 1
 
 
 class Desc(C.Structure):
@@ -25,7 +26,8 @@ class Desc(C.Structure):
                 ("dx1", C.c_double), ("dx2", C.c_double), ("dx3", C.c_double),
                 ("metric", C.c_int), ("a", C.c_double), ("gam", C.c_double),
                 ("cour", C.c_double), ("recon", C.c_int), ("riemann", C.c_int),
-                ("bc", C.c_int * 6), ("floors", C.c_int), ("emf", C.c_int), ("flatten", C.c_int)]
+                ("bc", C.c_int * 6), ("floors", C.c_int), ("emf", C.c_int), ("flatten", C.c_int),
+                ("inversion", C.c_int)]
 
 
 _libs = {}
@@ -46,6 +48,7 @@ def _setup(lib):
         "ora_source": [P, _D, C.c_double, C.c_double, _D],
         "ora_recon_line": [C.c_int, C.c_int, _D, _D, _D],
         "ora_flatten_line": [C.c_int, C.c_double, _D, _D, _D],
+        "ora_nh_map": [C.c_double] * 7 + [_D],
         "ora_recon_line_flat": [C.c_int, _D, _D, _D, _D],
         "ora_c2p_many": [P, C.c_long, _D, _D, _D, _D, _D, _I, _I, C.c_int],
         "ora_p2u_many": [P, C.c_long, _D, _D, _D, _D],
@@ -91,7 +94,7 @@ def _p(a):
 
 def make_desc(n1, n2, n3, x1min, x2min, x3min, dx1, dx2, dx3, metric=METRIC_KS, a=0.0,
               gam=13.0 / 9.0, cour=0.8, recon=RECON_PPM, riemann=FLUX_HLL, bc=(0, 0, 0, 0, 1, 1),
-              floors=1, emf=EMF_AVERAGE, flatten=0):
+              floors=1, emf=EMF_AVERAGE, flatten=0, inversion=0):
     d = Desc()
     d.n1, d.n2, d.n3 = n1, n2, n3
     d.x1min, d.x2min, d.x3min = x1min, x2min, x3min
@@ -103,6 +106,7 @@ def make_desc(n1, n2, n3, x1min, x2min, x3min, dx1, dx2, dx3, metric=METRIC_KS, 
     d.floors = floors
     d.emf = emf
     d.flatten = flatten
+    d.inversion = inversion
     return d
 
 
@@ -164,6 +168,13 @@ def recon_line(recon, q):
     ar = np.full_like(q, np.nan)
     lib().ora_recon_line(recon, len(q), _p(q), _p(al), _p(ar))
     return al, ar
+
+
+def nh_map(E, S2, T2, B2, D, gam, p):
+    """Newman-Hamlin pressure map of the Aitken inversion -> (W, v^2, next p); W = -1 if invalid."""
+    out = np.zeros(3)
+    lib().ora_nh_map(E, S2, T2, B2, D, gam, p, _p(out))
+    return out
 
 
 def flatten_line(gam, u, w):

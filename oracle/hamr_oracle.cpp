@@ -479,6 +479,87 @@ enum { C2P_OK = 0, C2P_ENTROPY = 1, C2P_FAIL = 2, C2P_FLOOR = 4 };
  * Reading: tolerance |dW|/W + |dv^2| < 1e-10 (with quadratic convergence the
  * accepted iterate is then at round-off), at most 30 iterations,
  * v^2 kept in [0, 1 - 1/50^2]; a failed state keeps its guess. */
+/* The pressure map of Newman & Hamlin (2014), the Aitken-accelerated
+ * inversion the paper names beside Newton (Sec. 2.6). With E = -Q.n,
+ * S^2 = Qt^2, T = Q.B, E1 and E2 above combine, for a trial pressure p, into
+ * a cubic in phi = W + B^2:
+ *   phi^3 - a phi^2 + d = 0,  a = E + p + B^2/2,  d = (S^2 B^2 - T^2)/2 >= 0
+ * (E1 rewritten with B.v = T/W and v^2 from E2). Its largest root is
+ * phi = (a/3)(1 + 2 cos(acos(1 - 27 d / (2 a^3)) / 3)); then W = phi - B^2,
+ * v^2 from E2 solved for v^2, and the ideal-gas pressure of (W, v^2) is the
+ * image of p. A real root >= 2a/3 needs a^3 >= 27 d / 4: the argument of
+ * acos is clamped to [-1, 1] (the caller keeps p above that bound).
+ * Returns false when W <= 0 or a value is not finite. */
+static bool nh_map(real E, real S2, real T2, real B2, real D, double gfac, double vsqmax, real p, real* W, real* vsq,
+                   real* pn) {
+    real a = E + p + 0.5 * B2;
+    real d = 0.5 * (S2 * B2 - T2);
+    if (d < 0.0) d = 0.0;
+    if (!(a > 0.0)) return false;
+    real x = 1.0 - 27.0 * d / (2.0 * a * a * a);
+    if (x < -1.0) x = -1.0;
+    if (x > 1.0) x = 1.0;
+    real phi = a / 3.0 * (1.0 + 2.0 * cos(acos(x) / 3.0));
+    real w = phi - B2;
+    if (!(w > 0.0)) return false;
+    real v = (S2 * w * w + T2 * (2.0 * w + B2)) / (w * w * phi * phi);
+    if (v < 0.0) v = 0.0;
+    if (v > vsqmax) v = vsqmax;
+    real sq = sqrt(1.0 - v);
+    *W = w;
+    *vsq = v;
+    *pn = gfac * (w * (1.0 - v) - D * sq);
+    return isfinite(*pn);
+}
+
+/* Energy inversion by the Newman & Hamlin fixed point p -> map(p), accelerated
+ * by Aitken's delta-squared extrapolation in Steffensen's form: from p0 two
+ * map evaluations give p1, p2, and the cycle restarts from
+ * p0 - (p1 - p0)^2 / (p2 - 2 p1 + p0) (from p2 when the denominator is 0 or
+ * the extrapolation is not a valid pressure). Pressures are kept >= the
+ * bound of the cubic, max(0, (27 d / 4)^(1/3) - E - B^2/2).
+ * Reading (stopping rule): an Aitken step smaller than 1e-10 W ends the
+ * iteration; one more evaluation at the extrapolated pressure gives (W, v^2)
+ * (the extrapolation error is then of second order in that step, as for
+ * Newton's last step). At most 30 cycles; iterations counted as map
+ * evaluations. Returns 1 when converged. */
+static int aitken_energy(real E, real S2, real T2, real B2, real D, double gfac, double vsqmax, real p0, real* W,
+                         real* vsq, int* evals) {
+    real d = 0.5 * (S2 * B2 - T2);
+    if (d < 0.0) d = 0.0;
+    real pmin = cbrt(6.75 * d) - E - 0.5 * B2;
+    if (pmin < 0.0) pmin = 0.0;
+    real p = p0;
+    if (!(p >= pmin)) p = pmin;
+    int n = 0;
+    for (int cycle = 1; cycle <= C2P_NMAX; cycle++) {
+        real W1, v1, p1, W2, v2, p2;
+        n++;
+        if (!nh_map(E, S2, T2, B2, D, gfac, vsqmax, p, &W1, &v1, &p1)) break;
+        if (p1 < pmin) p1 = pmin;
+        n++;
+        if (!nh_map(E, S2, T2, B2, D, gfac, vsqmax, p1, &W2, &v2, &p2)) break;
+        if (p2 < pmin) p2 = pmin;
+        real den = p2 - 2.0 * p1 + p;
+        real pa = p2;
+        if (den != 0.0) {
+            real e = p - (p1 - p) * (p1 - p) / den;
+            if (e >= pmin && isfinite(e)) pa = e;
+        }
+        real step = fabs(pa - p);
+        p = pa;
+        if (step < C2P_TOL * W2) {
+            n++;
+            real pn;
+            if (!nh_map(E, S2, T2, B2, D, gfac, vsqmax, p, W, vsq, &pn)) break;
+            *evals = n;
+            return 1;
+        }
+    }
+    *evals = n;
+    return 0;
+}
+
 static int con2prim(const ora_desc& d, const real Ucons[NCONS], const real Bc[3], const Geom& G,
                     real* pr, int* iters, int entropy_only = 0) {
     const double gam = d.gam;
@@ -520,36 +601,42 @@ static int con2prim(const ora_desc& d, const real Ucons[NCONS], const real Bc[3]
     real W0 = W;
 
     int ok = 0, it = 0;
-    for (it = 1; it <= (entropy_only ? 0 : C2P_NMAX); it++) {
-        real sq = sqrt(1.0 - vsq);
-        real p = gfac * (W * (1.0 - vsq) - D * sq);
-        real W2 = W * W;
-        real BW = Bsq + W;
-        real f1 = -0.5 * Bsq * (1.0 + vsq) + QdotBsq / (2.0 * W2) - W + p - Qdotn;
-        real f2 = vsq * BW * BW - QdotBsq * (Bsq + 2.0 * W) / W2 - Qtsq;
-        real dpdW = gfac * (1.0 - vsq);
-        real dpdv = gfac * (-W + 0.5 * D / sq);
-        real j11 = -QdotBsq / (W2 * W) - 1.0 + dpdW;
-        real j12 = -0.5 * Bsq + dpdv;
-        real j21 = 2.0 * vsq * BW + 2.0 * QdotBsq * BW / (W2 * W);
-        real j22 = BW * BW;
-        real det = j11 * j22 - j12 * j21;
-        real dW = -(j22 * f1 - j12 * f2) / det;
-        real dv = -(j11 * f2 - j21 * f1) / det;
-        real Wn = W + dW;
-        real vn = vsq + dv;
-        if (vn < 0.0) vn = 0.0;
-        if (vn > vsqmax) vn = vsqmax;
-        if (!(Wn > 0.0)) break;
-        real err = fabs(Wn - W) / Wn + fabs(vn - vsq);
-        W = Wn;
-        vsq = vn;
-        if (err < C2P_TOL) {
-            ok = 1;
-            break;
+    if (d.inversion == ORA_INV_AITKEN) {
+        /* the start: the pressure of the guess primitives */
+        if (!entropy_only)
+            ok = aitken_energy(-Qdotn, Qtsq, QdotBsq, Bsq, D, gfac, vsqmax, (gam - 1.0) * pr[UU], &W, &vsq, &it);
+    } else {
+        for (it = 1; it <= (entropy_only ? 0 : C2P_NMAX); it++) {
+            real sq = sqrt(1.0 - vsq);
+            real p = gfac * (W * (1.0 - vsq) - D * sq);
+            real W2 = W * W;
+            real BW = Bsq + W;
+            real f1 = -0.5 * Bsq * (1.0 + vsq) + QdotBsq / (2.0 * W2) - W + p - Qdotn;
+            real f2 = vsq * BW * BW - QdotBsq * (Bsq + 2.0 * W) / W2 - Qtsq;
+            real dpdW = gfac * (1.0 - vsq);
+            real dpdv = gfac * (-W + 0.5 * D / sq);
+            real j11 = -QdotBsq / (W2 * W) - 1.0 + dpdW;
+            real j12 = -0.5 * Bsq + dpdv;
+            real j21 = 2.0 * vsq * BW + 2.0 * QdotBsq * BW / (W2 * W);
+            real j22 = BW * BW;
+            real det = j11 * j22 - j12 * j21;
+            real dW = -(j22 * f1 - j12 * f2) / det;
+            real dv = -(j11 * f2 - j21 * f1) / det;
+            real Wn = W + dW;
+            real vn = vsq + dv;
+            if (vn < 0.0) vn = 0.0;
+            if (vn > vsqmax) vn = vsqmax;
+            if (!(Wn > 0.0)) break;
+            real err = fabs(Wn - W) / Wn + fabs(vn - vsq);
+            W = Wn;
+            vsq = vn;
+            if (err < C2P_TOL) {
+                ok = 1;
+                break;
+            }
         }
+        if (it > C2P_NMAX) it = C2P_NMAX;
     }
-    if (it > C2P_NMAX) it = C2P_NMAX;
     if (entropy_only) it = 0;
     *iters = it;
     real rho = 0.0, u = 0.0;
@@ -1294,6 +1381,15 @@ void ora_c2p_many(const ora_desc* d, long n, const double* U6, const double* Bc3
         status[s] = st;
         iters[s] = its;
     }
+}
+
+void ora_nh_map(double E, double S2, double T2, double B2, double D, double gam, double p, double* out3) {
+    real W = 0.0, vsq = 0.0, pn = 0.0;
+    const double vsqmax = 1.0 - 1.0 / (GAMMA_MAX * GAMMA_MAX);
+    bool ok = nh_map(E, S2, T2, B2, D, (gam - 1.0) / gam, vsqmax, p, &W, &vsq, &pn);
+    out3[0] = ok ? tod(W) : -1.0;
+    out3[1] = tod(vsq);
+    out3[2] = tod(pn);
 }
 
 void ora_p2u_many(const ora_desc* d, long n, const double* pr8, const double* x1, const double* x2,

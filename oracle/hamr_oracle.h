@@ -24,6 +24,8 @@ enum { ORA_RECON_PPM = 0, ORA_RECON_MC = 1, ORA_RECON_MINMOD = 2 };
 enum { ORA_FLUX_HLL = 0, ORA_FLUX_LLF = 1 };
 enum { ORA_EMF_AVERAGE = 0, ORA_EMF_UPWIND = 1 };
 
+enum { ORA_INV_NEWTON = 0, ORA_INV_AITKEN = 1 };
+
 typedef struct {
     int n1, n2, n3;                 /* interior cells per direction */
     double x1min, x2min, x3min;     /* lower corner in internal coordinates */
@@ -38,6 +40,7 @@ typedef struct {
     int floors;                     /* 1: apply the density/energy floors */
     int emf;                        /* ORA_EMF_*: edge EMFs as the 4-flux average or upwinded */
     int flatten;                    /* 1: PPM shock flattening (Colella & Woodward 1984) */
+    int inversion;                  /* ORA_INV_*: energy inversion by 2-D Newton or Aitken-accelerated fixed point */
 } ora_desc;
 
 /* ---- point-wise pieces (each documented in hamr_oracle.cpp) ---- */
@@ -55,6 +58,9 @@ void ora_source(const ora_desc* d, const double* pr8, double x1, double x2, doub
 void ora_recon_line(int recon, int n, const double* q, double* al, double* ar);
 /* PPM shock flattening: coefficients of a line from u and the velocity
  * primitive along it, and PPM edge values with given coefficients */
+/* Newman-Hamlin pressure map of the Aitken inversion: normal-frame E = -Q.n,
+ * Qt^2, (Q.B)^2, B^2, D and a trial p -> (W, v^2, next p); W = -1 if invalid */
+void ora_nh_map(double E, double S2, double T2, double B2, double D, double gam, double p, double* out3);
 void ora_flatten_line(int n, double gam, const double* u, const double* w, double* f);
 void ora_recon_line_flat(int n, const double* q, const double* f, double* al, double* ar);
 /* con2prim on n independent states: U6 (sqrt(-g) weighted), B3 centre B^i,

@@ -20,6 +20,7 @@
 
 typedef double real;
 static inline double tod(double x) { return x; }
+using std::isfinite;
 
 #else
 
@@ -63,6 +64,9 @@ static inline real exp(const real& a) { ora_flop_ctr[3]++; return real(std::exp(
 static inline real log(const real& a) { ora_flop_ctr[3]++; return real(std::log(a.v)); }
 static inline real pow(const real& a, const real& b) { ora_flop_ctr[3]++; return real(std::pow(a.v, b.v)); }
 static inline real pow(const real& a, double b) { ora_flop_ctr[3]++; return real(std::pow(a.v, b)); }
+static inline real acos(const real& a) { ora_flop_ctr[3]++; return real(std::acos(a.v)); }
+static inline real cos(const real& a) { ora_flop_ctr[3]++; return real(std::cos(a.v)); }
+static inline real cbrt(const real& a) { ora_flop_ctr[3]++; return real(std::cbrt(a.v)); }
 static inline real fmax(const real& a, const real& b) { ora_flop_ctr[4]++; return real(std::fmax(a.v, b.v)); }
 static inline real fmin(const real& a, const real& b) { ora_flop_ctr[4]++; return real(std::fmin(a.v, b.v)); }
 static inline real fmax(const real& a, double b) { ora_flop_ctr[4]++; return real(std::fmax(a.v, b)); }
