@@ -70,6 +70,10 @@ extern "C" {
 #define HAMR_BC_BLOCK 4             /* face shared with other blocks of the grid (ghosts from them) */
 #define HAMR_EMF_AVERAGE 0 /* the 4-flux average of Sec. 2.5 */
 #define HAMR_EMF_UPWIND 1  /* the average plus Gardiner & Stone (2005) upwind corrections (the paper's usual setting) */
+
+/* energy inversion of con2prim (Sec. 2.6); the entropy backup follows either */
+#define HAMR_INV_NEWTON 0 /* 2-D Newton-Raphson on (W, v^2) (Noble et al. 2006) */
+#define HAMR_INV_AITKEN 1 /* Newman & Hamlin (2014) fixed point in the pressure, Aitken-accelerated */
 #define HAMR_PREC_FP64 0  /* every step in FP64 */
 #define HAMR_PREC_MIXED 1 /* FP32 reconstruction, fluxes and EMFs; FP64 metric, inversion, accumulation */
 
@@ -104,6 +108,7 @@ typedef struct {
                             pressure jump above 0.33 of the lower side meets converging flow,
                             the interface values of the cell move toward its value; ignored
                             unless recon is HAMR_RECON_PPM. 0 or 1, else HAMR_EINVAL */
+    int inversion;       /* HAMR_INV_*: energy inversion of every cell update */
 } hamr_grid_desc;
 
 /* Counters of the last step (summed over its two stages and all blocks
@@ -236,6 +241,7 @@ int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, double* bface
 #define HAMR_C2P_ENTROPY_ONLY 1u /* skip the energy inversion (tests of the backup) */
 #define HAMR_C2P_MLP 2u          /* start Newton from the learned guess of `mlp` (fallback: the prim guess) */
 #define HAMR_C2P_MLP_RESCUE 4u   /* start from the prim guess; where that fails, from the learned guess */
+#define HAMR_C2P_AITKEN 8u       /* energy inversion by the Aitken-accelerated pressure iteration, not Newton */
 
 typedef struct hamr_mlp hamr_mlp;
 
@@ -252,8 +258,9 @@ typedef struct {
  * T^t_2, T^t_3, kappa rho u^t); B[3][n] centre B^i; x1[n], x2[n] positions;
  * prim[8][n] in: the guess, out: the result (slots 5..7 set to B);
  * status[n]: 0 energy inversion, 1 entropy backup, 2 both failed (prim keeps
- * the guess); iters[n]: Newton iterations of the energy inversion (may be
- * NULL). Asynchronous on `stream`. */
+ * the guess); iters[n]: Newton iterations of the energy inversion (pressure
+ * map evaluations with HAMR_C2P_AITKEN; may be NULL). Asynchronous on
+ * `stream`. */
 int hamr_con2prim(const hamr_c2p_desc* d, int64_t n, const double* U, const double* B, const double* x1,
                   const double* x2, double* prim, int32_t* status, int32_t* iters, void* stream);
 

@@ -150,6 +150,8 @@ int validate(const hamr_grid_desc* d) {
         return fail(HAMR_EINVAL, "unknown precision %d", d->precision);
     if (d->emf != HAMR_EMF_AVERAGE && d->emf != HAMR_EMF_UPWIND) return fail(HAMR_EINVAL, "unknown emf %d", d->emf);
     if (d->flatten != 0 && d->flatten != 1) return fail(HAMR_EINVAL, "flatten must be 0 or 1, got %d", d->flatten);
+    if (d->inversion != HAMR_INV_NEWTON && d->inversion != HAMR_INV_AITKEN)
+        return fail(HAMR_EINVAL, "unknown inversion %d", d->inversion);
     for (int b = 0; b < d->nblocks; b++) {
         const hamr_block_desc& B = d->blocks[b];
         if (B.n1 < 4 || B.n2 < 4 || B.n3 < 4) return fail(HAMR_EINVAL, "block %d: each n must be >= 4", b);
@@ -353,6 +355,7 @@ int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out) {
     default_launch_shapes(g->ph);
     g->ph.emf = d->emf;
     g->ph.flatten = (d->flatten && d->recon == HAMR_RECON_PPM) ? 1 : 0;
+    g->ph.inversion = d->inversion;
     cudaGetDevice(&g->device);
     for (int b = 0; b < d->nblocks; b++) {
         rc = alloc_block(g, b);
@@ -570,7 +573,7 @@ int hamr_con2prim(const hamr_c2p_desc* d, int64_t n, const double* U, const doub
     if (d->metric != HAMR_METRIC_KS && d->metric != HAMR_METRIC_MINKOWSKI)
         return fail(HAMR_EINVAL, "unknown metric %d", d->metric);
     if (!(d->gam > 1.0 && d->gam <= 2.0)) return fail(HAMR_EINVAL, "gam must be in (1, 2]");
-    if (d->flags & ~(HAMR_C2P_ENTROPY_ONLY | HAMR_C2P_MLP | HAMR_C2P_MLP_RESCUE))
+    if (d->flags & ~(HAMR_C2P_ENTROPY_ONLY | HAMR_C2P_MLP | HAMR_C2P_MLP_RESCUE | HAMR_C2P_AITKEN))
         return fail(HAMR_EINVAL, "unknown flags 0x%x", d->flags);
     if ((d->flags & HAMR_C2P_MLP) && (d->flags & HAMR_C2P_MLP_RESCUE))
         return fail(HAMR_EINVAL, "HAMR_C2P_MLP and HAMR_C2P_MLP_RESCUE exclude each other");

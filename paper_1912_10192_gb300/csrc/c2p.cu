@@ -36,9 +36,9 @@ __global__ void __launch_bounds__(128) k_con2prim(hamr_c2p_desc d, const uint8_t
     const bool entropy_only = (d.flags & HAMR_C2P_ENTROPY_ONLY) != 0;
     const bool rescue = (d.flags & HAMR_C2P_MLP_RESCUE) != 0;
     C2PWork w;
-    if (active) c2p_prepare(u, bc, m, d.gam, pr, w);
+    if (active) c2p_prepare(u, bc, m, d.gam, pr, w, (d.flags & HAMR_C2P_AITKEN) ? HAMR_INV_AITKEN : HAMR_INV_NEWTON);
     if (MLP && !entropy_only) {  // the 128 states of the CTA through the network (mlp.cuh)
-        if (rescue && active) c2p_attempt(w, d.gam, w.W0, w.vsq0);
+        if (rescue && active) c2p_attempt_plain(w, d.gam);
         if (__syncthreads_or(active && !w.ok)) {
             extern __shared__ __align__(16) uint8_t mlp_smem[];
             MlpCta C;
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(128) k_con2prim(hamr_c2p_desc d, const uint8_t
         }
     }
     if (!active) return;
-    if (!entropy_only && !(MLP && rescue)) c2p_attempt(w, d.gam, w.W0, w.vsq0);
+    if (!entropy_only && !(MLP && rescue)) c2p_attempt_plain(w, d.gam);
     const int st = c2p_finish(w, u, m, d.gam, pr);
     const int it = w.its;
 #pragma unroll

@@ -12,6 +12,7 @@
 // accepted iterate at round-off), at most 30 iterations; v^2 is kept
 // in [0, 1 - 1/50^2].
 #pragma once
+#include "../../include/hamr.h"
 #include "grmhd.cuh"
 
 namespace hamr {
@@ -90,6 +91,67 @@ __device__ __forceinline__ bool newton_wv(const C2PScalars& S, double gfac, doub
     return ok;
 }
 
+// Aitken-accelerated inversion (Sec. 2.6 names it beside Newton; Newman &
+// Hamlin 2014). With E = -Q.n, S^2 = Qt^2, T = Q.B the two equations give, for
+// a trial pressure p, a cubic in phi = W + B^2: phi^3 - a phi^2 + d = 0,
+// a = E + p + B^2/2, d = (S^2 B^2 - T^2)/2. Its largest root (closed form
+// (a/3)(1 + 2 cos(acos(1 - 27 d / (2 a^3)) / 3))), v^2 from the momentum
+// equation and the ideal-gas pressure of (W, v^2) map p to the next p.
+// Returns false when W <= 0 or the pressure is not finite.
+__device__ __forceinline__ bool nh_map(const C2PScalars& S, double gfac, double p, double& W, double& vsq,
+                                       double& pn) {
+    const double B2 = S.Bsq;
+    const double a = -S.Qdotn + p + 0.5 * B2;
+    const double d = fmax(0.5 * (S.Qtsq * B2 - S.QB2), 0.0);
+    if (!(a > 0.0)) return false;
+    const double x = fmin(fmax(1.0 - 27.0 * d / (2.0 * a * a * a), -1.0), 1.0);
+    const double phi = a / 3.0 * (1.0 + 2.0 * cos(acos(x) / 3.0));
+    const double w = phi - B2;
+    if (!(w > 0.0)) return false;
+    const double v = fmin(fmax((S.Qtsq * w * w + S.QB2 * (2.0 * w + B2)) / (w * w * phi * phi), 0.0), C2P_VSQMAX);
+    W = w;
+    vsq = v;
+    pn = gfac * (w * (1.0 - v) - S.D * sqrt(1.0 - v));
+    return isfinite(pn);
+}
+
+// Steffensen's form of the Aitken delta-squared acceleration of p -> map(p):
+// two evaluations from p0 give p1, p2, and the next cycle starts from
+// p0 - (p1 - p0)^2 / (p2 - 2 p1 + p0) (from p2 when that is not a valid
+// pressure). Pressures stay >= max(0, (27 d / 4)^(1/3) - E - B^2/2), where
+// the cubic has its root. An extrapolation step below C2P_TOL W ends the
+// iteration, and one more evaluation gives (W, v^2). `it` counts evaluations.
+__device__ __forceinline__ bool aitken_wv(const C2PScalars& S, double gfac, double p, double& W, double& vsq,
+                                          int& it) {
+    const double d = fmax(0.5 * (S.Qtsq * S.Bsq - S.QB2), 0.0);
+    const double pmin = fmax(cbrt(6.75 * d) + S.Qdotn - 0.5 * S.Bsq, 0.0);
+    if (!(p >= pmin)) p = pmin;
+    it = 0;
+    for (int cycle = 1; cycle <= C2P_NMAX; cycle++) {
+        double W1, v1, p1, W2, v2, p2;
+        it++;
+        if (!nh_map(S, gfac, p, W1, v1, p1)) return false;
+        p1 = fmax(p1, pmin);
+        it++;
+        if (!nh_map(S, gfac, p1, W2, v2, p2)) return false;
+        p2 = fmax(p2, pmin);
+        const double den = p2 - 2.0 * p1 + p;
+        double pa = p2;
+        if (den != 0.0) {
+            const double e = p - (p1 - p) * (p1 - p) / den;
+            if (e >= pmin && isfinite(e)) pa = e;
+        }
+        const double step = fabs(pa - p);
+        p = pa;
+        if (step < C2P_TOL * W2) {
+            it++;
+            double pn;
+            return nh_map(S, gfac, p, W, vsq, pn);
+        }
+    }
+    return false;
+}
+
 // rho and u_g of a converged (W, v^2); false unless both are positive
 __device__ __forceinline__ bool energy_result(const C2PScalars& S, double gam, double W, double vsq, double& rho,
                                               double& u) {
@@ -108,14 +170,19 @@ __device__ __forceinline__ bool energy_result(const C2PScalars& S, double gam, d
 struct C2PWork {
     C2PScalars S;
     double W0, vsq0;  // the start from the guess primitives
+    double p0;        // ... and its pressure (the Aitken inversion's start)
+    int method;       // HAMR_INV_NEWTON or HAMR_INV_AITKEN
     double W, vsq, rho, u;
     bool ok;
     int its;          // Newton iterations of every energy attempt
 };
 
 __device__ __forceinline__ void c2p_prepare(const double U[NCONS], const double Bc[3], const Metric<double>& m,
-                                            double gam, const double pr[NPRIM], C2PWork& w) {
+                                            double gam, const double pr[NPRIM], C2PWork& w,
+                                            int method = HAMR_INV_NEWTON) {
     c2p_scalars(U, Bc, m, w.S);
+    w.method = method;
+    w.p0 = (gam - 1.0) * pr[UU];
     const double q1 = pr[U1], q2 = pr[U2], q3 = pr[U3];
     const double qsq = m.g11 * q1 * q1 + m.g22 * q2 * q2 + m.g33 * q3 * q3 + 2.0 * m.g13 * q1 * q3;
     const double gsq = 1.0 + qsq;
@@ -128,18 +195,47 @@ __device__ __forceinline__ void c2p_prepare(const double U[NCONS], const double 
     w.its = 0;
 }
 
-// one energy-equation attempt from (W, v^2); no-op once an attempt succeeded
+// one energy-equation attempt from the pressure p (Aitken inversion)
+__device__ __forceinline__ void c2p_attempt_p(C2PWork& w, double gam, double p) {
+    if (w.ok) return;
+    const double gfac = (gam - 1.0) / gam;
+    int it = 0;
+    double W = 0.0, vsq = 0.0;
+    bool ok = aitken_wv(w.S, gfac, p, W, vsq, it);
+    w.its += it;
+    if (ok) {
+        w.W = W;
+        w.vsq = vsq;
+        ok = energy_result(w.S, gam, W, vsq, w.rho, w.u);
+    }
+    w.ok = ok;
+}
+
+// one energy-equation attempt from (W, v^2); no-op once an attempt succeeded.
+// The Aitken inversion starts from the pressure of (W, v^2).
 __device__ __forceinline__ void c2p_attempt(C2PWork& w, double gam, double W, double vsq) {
     if (w.ok || !(W > 0.0)) return;
     const double gfac = (gam - 1.0) / gam;
-    int it = 0;
     vsq = fmin(fmax(vsq, 0.0), C2P_VSQMAX);
+    if (w.method == HAMR_INV_AITKEN) {
+        c2p_attempt_p(w, gam, gfac * (W * (1.0 - vsq) - w.S.D * sqrt(1.0 - vsq)));
+        return;
+    }
+    int it = 0;
     bool ok = newton_wv(w.S, gfac, W, vsq, it);
     w.its += it;
     w.W = W;
     w.vsq = vsq;
     if (ok) ok = energy_result(w.S, gam, W, vsq, w.rho, w.u);
     w.ok = ok;
+}
+
+// the attempt from the guess primitives: (W, v^2) for Newton, their pressure for Aitken
+__device__ __forceinline__ void c2p_attempt_plain(C2PWork& w, double gam) {
+    if (w.method == HAMR_INV_AITKEN)
+        c2p_attempt_p(w, gam, w.p0);
+    else
+        c2p_attempt(w, gam, w.W0, w.vsq0);
 }
 
 // pr: out the result (slots 0..4) unless INV_FAIL (then untouched)
@@ -214,12 +310,12 @@ __device__ __forceinline__ int c2p_finish(C2PWork& w, const double U[NCONS], con
 // Newton iterations of every start tried.
 __device__ __forceinline__ int invert(const double U[NCONS], const double Bc[3], const Metric<double>& m, double gam,
                                       double pr[NPRIM], int* iters, bool entropy_only,
-                                      const double* guess2 = nullptr) {
+                                      const double* guess2 = nullptr, int method = HAMR_INV_NEWTON) {
     C2PWork w;
-    c2p_prepare(U, Bc, m, gam, pr, w);
+    c2p_prepare(U, Bc, m, gam, pr, w, method);
     if (!entropy_only) {
         if (guess2) c2p_attempt(w, gam, guess2[0], guess2[1]);
-        c2p_attempt(w, gam, w.W0, w.vsq0);
+        c2p_attempt_plain(w, gam);
     }
     if (iters) *iters = w.its;
     return c2p_finish(w, U, m, gam, pr);

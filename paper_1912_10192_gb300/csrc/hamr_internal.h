@@ -55,6 +55,7 @@ struct PhysArgs {
     int bs_recon, bs_flux, bs_update, recon_seg;
     int emf;      // HAMR_EMF_*
     int flatten;  // 1: PPM shock flattening (only set with HAMR_RECON_PPM)
+    int inversion;  // HAMR_INV_*
 };
 
 // threads of one reconstruction launch (FP64): rows along x1 in warps of 32

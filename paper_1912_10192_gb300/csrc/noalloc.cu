@@ -83,6 +83,8 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     if (d->emf != HAMR_EMF_AVERAGE && d->emf != HAMR_EMF_UPWIND) return set_error(HAMR_EINVAL, "unknown emf %d", d->emf);
     if (d->flatten != 0 && d->flatten != 1)
         return set_error(HAMR_EINVAL, "flatten must be 0 or 1, got %d", d->flatten);
+    if (d->inversion != HAMR_INV_NEWTON && d->inversion != HAMR_INV_AITKEN)
+        return set_error(HAMR_EINVAL, "unknown inversion %d", d->inversion);
 
     double* base = nullptr;
     int rc = setup(&base);
@@ -157,6 +159,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     default_launch_shapes(ph);
     ph.emf = d->emf;
     ph.flatten = (d->flatten && d->recon == HAMR_RECON_PPM) ? 1 : 0;
+    ph.inversion = d->inversion;
 
     // the array keeps the previous call's contents: clear what must start at zero
     NA_TRY(cudaMemsetAsync(s.Ph, 0, sizeof(double) * 11 * v.nc, cs));

@@ -748,11 +748,11 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
     }
     // inversion: energy attempts from the start(s), then the entropy backup
     C2PWork w;
-    if (active) c2p_prepare(U, Bc, m, gam, pr, w);
+    if (active) c2p_prepare(U, Bc, m, gam, pr, w, ph.inversion);
     if (MLP) {
         // first: the network's start, then the plain one; rescue: the plain start, then the
         // network's where it failed (the CTA runs the network only if one of its cells failed)
-        if (rescue && active) c2p_attempt(w, gam, w.W0, w.vsq0);
+        if (rescue && active) c2p_attempt_plain(w, gam);
         if (__syncthreads_or(active && !w.ok)) {
             if (rescue) mlp_begin(C, mlp_smem, ph.mlp_img);
             float f[MLP_NIN], y[MLP_NOUT];
@@ -770,7 +770,7 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
         }
     }
     if (active) {
-        if (!rescue) c2p_attempt(w, gam, w.W0, w.vsq0);
+        if (!rescue) c2p_attempt_plain(w, gam);
         its = w.its;
         st = c2p_finish(w, U, m, gam, pr);
         uint8_t sb = (st == INV_ENTROPY) ? ST_ENTROPY : ((st == INV_FAIL) ? ST_FAIL : 0);
@@ -1000,7 +1000,7 @@ __global__ void k_reflux_cells(const DevBlock* tab, int n, const int* cblk, cons
     pr[B2] = Bc[1];
     pr[B3] = Bc[2];
     int its;
-    const int st = invert(U, Bc, m, ph.gam, pr, &its, false);
+    const int st = invert(U, Bc, m, ph.gam, pr, &its, false, nullptr, ph.inversion);
     if (st == INV_FAIL)
 #pragma unroll
         for (int q = 0; q < 5; q++) pr[q] = D.P[q * v.nc + c];
