@@ -18,6 +18,7 @@ RECON_PPM, RECON_MC, RECON_MINMOD = 0, 1, 2
 FLUX_HLL, FLUX_LLF = 0, 1
 EMF_AVERAGE, EMF_UPWIND = 0, 1
 INV_NEWTON, INV_AITKEN = 0, 1
+FLOOR_FLUID, FLOOR_DRIFT = 0, 1
 
 
 class Desc(C.Structure):
@@ -27,7 +28,7 @@ class Desc(C.Structure):
                 ("metric", C.c_int), ("a", C.c_double), ("gam", C.c_double),
                 ("cour", C.c_double), ("recon", C.c_int), ("riemann", C.c_int),
                 ("bc", C.c_int * 6), ("floors", C.c_int), ("emf", C.c_int), ("flatten", C.c_int),
-                ("inversion", C.c_int)]
+                ("inversion", C.c_int), ("floor_frame", C.c_int)]
 
 
 _libs = {}
@@ -49,6 +50,7 @@ def _setup(lib):
         "ora_recon_line": [C.c_int, C.c_int, _D, _D, _D],
         "ora_flatten_line": [C.c_int, C.c_double, _D, _D, _D],
         "ora_nh_map": [C.c_double] * 7 + [_D],
+        "ora_floors_many": [P, C.c_long, _D, _D, _D, _D, _I],
         "ora_recon_line_flat": [C.c_int, _D, _D, _D, _D],
         "ora_c2p_many": [P, C.c_long, _D, _D, _D, _D, _D, _I, _I, C.c_int],
         "ora_p2u_many": [P, C.c_long, _D, _D, _D, _D],
@@ -94,7 +96,7 @@ def _p(a):
 
 def make_desc(n1, n2, n3, x1min, x2min, x3min, dx1, dx2, dx3, metric=METRIC_KS, a=0.0,
               gam=13.0 / 9.0, cour=0.8, recon=RECON_PPM, riemann=FLUX_HLL, bc=(0, 0, 0, 0, 1, 1),
-              floors=1, emf=EMF_AVERAGE, flatten=0, inversion=0):
+              floors=1, emf=EMF_AVERAGE, flatten=0, inversion=0, floor_frame=0):
     d = Desc()
     d.n1, d.n2, d.n3 = n1, n2, n3
     d.x1min, d.x2min, d.x3min = x1min, x2min, x3min
@@ -107,6 +109,7 @@ def make_desc(n1, n2, n3, x1min, x2min, x3min, dx1, dx2, dx3, metric=METRIC_KS, 
     d.emf = emf
     d.flatten = flatten
     d.inversion = inversion
+    d.floor_frame = floor_frame
     return d
 
 
@@ -168,6 +171,17 @@ def recon_line(recon, q):
     ar = np.full_like(q, np.nan)
     lib().ora_recon_line(recon, len(q), _p(q), _p(al), _p(ar))
     return al, ar
+
+
+def floors_many(d, prim, x1, x2, r):
+    """The floors on prim (n, 8) (slots 5..7 centre B) -> (floored prim, hit flags)."""
+    out = np.ascontiguousarray(prim, dtype=np.float64).copy()
+    x1 = np.ascontiguousarray(x1, dtype=np.float64)
+    x2 = np.ascontiguousarray(x2, dtype=np.float64)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    hit = np.zeros(len(x1), dtype=np.int32)
+    lib().ora_floors_many(C.byref(d), len(x1), _p(out), _p(x1), _p(x2), _p(r), hit.ctypes.data_as(_I))
+    return out, hit
 
 
 def nh_map(E, S2, T2, B2, D, gam, p):

@@ -710,9 +710,74 @@ static int con2prim(const ora_desc& d, const real Ucons[NCONS], const real Bc[3]
     return status;
 }
 
-/* Floors (Sec. 2.7): rho >= max(1e-7/r^2, b^2/50), u >= max(1e-9/r^(10/3), b^2/750).
- * Reading / deviation: the paper injects mass and energy in the drift frame;
- * here the floor raises rho and u and keeps utilde^i (fluid-frame injection). */
+/* Floors in the drift frame (Sec. 2.7: the paper injects the floor material
+ * in the drift frame, after Ressler et al. 2017). Reading: the material the
+ * floors add, drho = rho_f - rho and du = u_f - u (each >= 0), moves with the
+ * drift velocity of the field lines, the part of the fluid's normal-frame
+ * velocity across B, v_d = v - (v.Bn / Bn^2) Bn (which is E x B / B^2 for the
+ * ideal-MHD E = -v x B; v_d = v where B = 0). Its stress-energy (no field) is
+ * added to the current state's in conserved form, sqrt(-g)(rho u^t,
+ * T^t_mu + rho u^t), the entropy slot keeps the current kappa, and the sum is
+ * inverted with the same B, starting from the floored rho and u at the drift
+ * velocity (the fluid's own velocity is a poor start where a fast flow along B
+ * is slowed by much). So the
+ * material brings no momentum along B: a flow along the field slows down as
+ * mass is added instead of keeping its Lorentz factor (the runaway of
+ * fluid-frame injection), and the motion across B is the field's. The
+ * fluid-frame floor is applied to the result (mixing changes the Lorentz
+ * factor, so rho and u can land slightly below the floors) and replaces the
+ * whole step where the inversion fails. */
+static bool drift_floor(const ora_desc& d, real* pr, const State& s, const Geom& G, real rf, real uf) {
+    const double gam = d.gam;
+    real drho = rf - pr[RHO], du = uf - pr[UU];
+    if (drho < 0.0) drho = 0.0;
+    if (du < 0.0) du = 0.0;
+    real qsq = 0.0;
+    for (int i = 1; i < 4; i++)
+        for (int j = 1; j < 4; j++) qsq += G.gcov[i][j] * pr[U1 + i - 1] * pr[U1 + j - 1];
+    real gamma = sqrt(1.0 + qsq);
+    real v[4] = {0.0, pr[U1] / gamma, pr[U2] / gamma, pr[U3] / gamma};
+    real Bn[4] = {0.0, G.alpha * pr[B1], G.alpha * pr[B2], G.alpha * pr[B3]};
+    real bn2 = 0.0, vB = 0.0;
+    for (int i = 1; i < 4; i++)
+        for (int j = 1; j < 4; j++) {
+            bn2 += G.gcov[i][j] * Bn[i] * Bn[j];
+            vB += G.gcov[i][j] * v[i] * Bn[j];
+        }
+    real f = (bn2 > 0.0) ? vB / bn2 : real(0.0);
+    real vd[4];
+    for (int i = 1; i < 4; i++) vd[i] = v[i] - f * Bn[i];
+    real vd2 = 0.0;
+    for (int i = 1; i < 4; i++)
+        for (int j = 1; j < 4; j++) vd2 += G.gcov[i][j] * vd[i] * vd[j];
+    real gd = 1.0 / sqrt(1.0 - vd2);
+    real pa[NPR] = {drho, du, gd * vd[1], gd * vd[2], gd * vd[3], 0.0, 0.0, 0.0};
+    State sa;
+    get_state(pa, G, sa);
+    real uo[9], ua[9];
+    prim_to_uf(pr, s, 0, gam, uo);
+    prim_to_uf(pa, sa, 0, gam, ua);
+    real U[NCONS];
+    for (int m = 0; m < 5; m++) U[m] = G.gdet * (uo[m] + ua[m]);
+    U[CENT] = G.gdet * uo[5] / uo[0] * (uo[0] + ua[0]);
+    real q[NPR];
+    for (int m = 0; m < NPR; m++) q[m] = pr[m];
+    if (q[RHO] < rf) q[RHO] = rf;
+    if (q[UU] < uf) q[UU] = uf;
+    for (int i = 0; i < 3; i++) q[U1 + i] = pa[U1 + i]; /* start at the drift velocity */
+    real Bc[3] = {pr[B1], pr[B2], pr[B3]};
+    int its = 0;
+    if (con2prim(d, U, Bc, G, q, &its) == C2P_FAIL) return false;
+    if (q[RHO] < rf) q[RHO] = rf;
+    if (q[UU] < uf) q[UU] = uf;
+    for (int m = 0; m < 5; m++) pr[m] = q[m];
+    return true;
+}
+
+/* Floors (Sec. 2.7): rho >= max(1e-7/r^2, b^2/50), u >= max(1e-9/r^(10/3), b^2/750),
+ * b^2 of the state before the floors. ORA_FLOOR_FLUID raises rho and u and keeps
+ * utilde^i (fluid-frame injection); ORA_FLOOR_DRIFT adds the material in the
+ * drift frame (drift_floor above). */
 static int apply_floors(const ora_desc& d, real* pr, const Geom& G, double r) {
     State s;
     get_state(pr, G, s);
@@ -721,17 +786,11 @@ static int apply_floors(const ora_desc& d, real* pr, const Geom& G, double r) {
     real rb = s.bsq / 50.0, ub = s.bsq / 750.0;
     if (rb > rhoflr) rhoflr = rb;
     if (ub > uflr) uflr = ub;
-    int hit = 0;
-    if (pr[RHO] < rhoflr) {
-        pr[RHO] = rhoflr;
-        hit = 1;
-    }
-    if (pr[UU] < uflr) {
-        pr[UU] = uflr;
-        hit = 1;
-    }
-    (void)d;
-    return hit;
+    if (!(pr[RHO] < rhoflr) && !(pr[UU] < uflr)) return 0;
+    if (d.floor_frame == ORA_FLOOR_DRIFT && drift_floor(d, pr, s, G, rhoflr, uflr)) return 1;
+    if (pr[RHO] < rhoflr) pr[RHO] = rhoflr;
+    if (pr[UU] < uflr) pr[UU] = uflr;
+    return 1;
 }
 
 } /* namespace */
@@ -1390,6 +1449,18 @@ void ora_nh_map(double E, double S2, double T2, double B2, double D, double gam,
     out3[0] = ok ? tod(W) : -1.0;
     out3[1] = tod(vsq);
     out3[2] = tod(pn);
+}
+
+void ora_floors_many(const ora_desc* d, long n, double* pr8, const double* x1, const double* x2, const double* r,
+                     int* hit) {
+    for (long s = 0; s < n; s++) {
+        Geom G;
+        geom_point(*d, x1[s], x2[s], G);
+        real pr[NPR];
+        for (int v = 0; v < NPR; v++) pr[v] = pr8[s * NPR + v];
+        hit[s] = apply_floors(*d, pr, G, r[s]);
+        for (int v = 0; v < NPR; v++) pr8[s * NPR + v] = tod(pr[v]);
+    }
 }
 
 void ora_p2u_many(const ora_desc* d, long n, const double* pr8, const double* x1, const double* x2,

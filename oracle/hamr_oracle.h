@@ -25,6 +25,7 @@ enum { ORA_FLUX_HLL = 0, ORA_FLUX_LLF = 1 };
 enum { ORA_EMF_AVERAGE = 0, ORA_EMF_UPWIND = 1 };
 
 enum { ORA_INV_NEWTON = 0, ORA_INV_AITKEN = 1 };
+enum { ORA_FLOOR_FLUID = 0, ORA_FLOOR_DRIFT = 1 };
 
 typedef struct {
     int n1, n2, n3;                 /* interior cells per direction */
@@ -41,6 +42,7 @@ typedef struct {
     int emf;                        /* ORA_EMF_*: edge EMFs as the 4-flux average or upwinded */
     int flatten;                    /* 1: PPM shock flattening (Colella & Woodward 1984) */
     int inversion;                  /* ORA_INV_*: energy inversion by 2-D Newton or Aitken-accelerated fixed point */
+    int floor_frame;                /* ORA_FLOOR_*: floor material added in the fluid frame or the drift frame */
 } ora_desc;
 
 /* ---- point-wise pieces (each documented in hamr_oracle.cpp) ---- */
@@ -61,6 +63,10 @@ void ora_recon_line(int recon, int n, const double* q, double* al, double* ar);
 /* Newman-Hamlin pressure map of the Aitken inversion: normal-frame E = -Q.n,
  * Qt^2, (Q.B)^2, B^2, D and a trial p -> (W, v^2, next p); W = -1 if invalid */
 void ora_nh_map(double E, double S2, double T2, double B2, double D, double gam, double p, double* out3);
+/* the floors of Sec. 2.7 on n primitive states (slots 5..7: centre B), r[n] the radius of the
+ * floor thresholds; hit[n] = 1 where a floor applied */
+void ora_floors_many(const ora_desc* d, long n, double* pr8, const double* x1, const double* x2, const double* r,
+                     int* hit);
 void ora_flatten_line(int n, double gam, const double* u, const double* w, double* f);
 void ora_recon_line_flat(int n, const double* q, const double* f, double* al, double* ar);
 /* con2prim on n independent states: U6 (sqrt(-g) weighted), B3 centre B^i,
