@@ -74,6 +74,11 @@ extern "C" {
 /* energy inversion of con2prim (Sec. 2.6); the entropy backup follows either */
 #define HAMR_INV_NEWTON 0 /* 2-D Newton-Raphson on (W, v^2) (Noble et al. 2006) */
 #define HAMR_INV_AITKEN 1 /* Newman & Hamlin (2014) fixed point in the pressure, Aitken-accelerated */
+
+/* frame in which the floors of Sec. 2.7 add mass and internal energy */
+#define HAMR_FLOOR_FLUID 0 /* raise rho and u_g, keep utilde (the fluid frame) */
+#define HAMR_FLOOR_DRIFT 1 /* add the material moving with the field lines' drift velocity and re-invert
+                              (the paper's choice, after Ressler et al. 2017) */
 #define HAMR_PREC_FP64 0  /* every step in FP64 */
 #define HAMR_PREC_MIXED 1 /* FP32 reconstruction, fluxes and EMFs; FP64 metric, inversion, accumulation */
 
@@ -109,6 +114,7 @@ typedef struct {
                             the interface values of the cell move toward its value; ignored
                             unless recon is HAMR_RECON_PPM. 0 or 1, else HAMR_EINVAL */
     int inversion;       /* HAMR_INV_*: energy inversion of every cell update */
+    int floor_frame;     /* HAMR_FLOOR_*: where floors apply (floors = 1), the frame of the added material */
 } hamr_grid_desc;
 
 /* Counters of the last step (summed over its two stages and all blocks

@@ -152,6 +152,8 @@ int validate(const hamr_grid_desc* d) {
     if (d->flatten != 0 && d->flatten != 1) return fail(HAMR_EINVAL, "flatten must be 0 or 1, got %d", d->flatten);
     if (d->inversion != HAMR_INV_NEWTON && d->inversion != HAMR_INV_AITKEN)
         return fail(HAMR_EINVAL, "unknown inversion %d", d->inversion);
+    if (d->floor_frame != HAMR_FLOOR_FLUID && d->floor_frame != HAMR_FLOOR_DRIFT)
+        return fail(HAMR_EINVAL, "unknown floor_frame %d", d->floor_frame);
     for (int b = 0; b < d->nblocks; b++) {
         const hamr_block_desc& B = d->blocks[b];
         if (B.n1 < 4 || B.n2 < 4 || B.n3 < 4) return fail(HAMR_EINVAL, "block %d: each n must be >= 4", b);
@@ -356,6 +358,7 @@ int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out) {
     g->ph.emf = d->emf;
     g->ph.flatten = (d->flatten && d->recon == HAMR_RECON_PPM) ? 1 : 0;
     g->ph.inversion = d->inversion;
+    g->ph.floor_frame = d->floor_frame;
     cudaGetDevice(&g->device);
     for (int b = 0; b < d->nblocks; b++) {
         rc = alloc_block(g, b);

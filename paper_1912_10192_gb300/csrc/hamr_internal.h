@@ -56,6 +56,7 @@ struct PhysArgs {
     int emf;      // HAMR_EMF_*
     int flatten;  // 1: PPM shock flattening (only set with HAMR_RECON_PPM)
     int inversion;  // HAMR_INV_*
+    int floor_frame;  // HAMR_FLOOR_*
 };
 
 // threads of one reconstruction launch (FP64): rows along x1 in warps of 32

@@ -671,6 +671,78 @@ __device__ __forceinline__ void source_q(const TT* __restrict__ gc, long n2d, lo
 // tensor cores; Newton starts from it, with the start from Pf as fallback.
 // TS: precision of the connection source and of the CFL rate (float in mixed
 // precision; the conserved accumulation and the inversion are FP64 always).
+// Floors in the drift frame (Sec. 2.7, after Ressler et al. 2017): the floor
+// material, drho = rho_f - rho and du = u_f - u (each >= 0), moves with the
+// drift velocity of the field lines, the part of the normal-frame velocity
+// across B, v_d = v - (v.Bn / Bn^2) Bn (v_d = v where B = 0). Its stress-energy
+// (no field) is added to the cell's in conserved form, the entropy slot keeps
+// the cell's kappa, and the sum is inverted with the same B from rho_f, u_f at
+// the drift velocity. The material brings no momentum along B, so a flow along
+// the field slows as mass is added; the fluid-frame floor is applied to the
+// result. false when the inversion fails (the caller then takes the fluid-frame
+// floor).
+__device__ __forceinline__ bool drift_floor(const Metric<double>& m, const PhysArgs& ph, double pr[NPRIM],
+                                            const Fluid<double>& s, double rf, double uf) {
+    const double gam = ph.gam;
+    const double q1 = pr[U1], q2 = pr[U2], q3 = pr[U3];
+    const double qsq = m.g11 * q1 * q1 + m.g22 * q2 * q2 + m.g33 * q3 * q3 + 2.0 * m.g13 * q1 * q3;
+    const double ig = 1.0 / sqrt(1.0 + qsq);
+    const double v1 = q1 * ig, v2 = q2 * ig, v3 = q3 * ig;
+    const double b1 = m.alpha * pr[B1], b2 = m.alpha * pr[B2], b3 = m.alpha * pr[B3];
+    const double bn2 = m.g11 * b1 * b1 + m.g22 * b2 * b2 + m.g33 * b3 * b3 + 2.0 * m.g13 * b1 * b3;
+    const double vb = m.g11 * v1 * b1 + m.g22 * v2 * b2 + m.g33 * v3 * b3 + m.g13 * (v1 * b3 + v3 * b1);
+    const double f = (bn2 > 0.0) ? vb / bn2 : 0.0;
+    const double d1 = v1 - f * b1, d2 = v2 - f * b2, d3 = v3 - f * b3;
+    const double vd2 = m.g11 * d1 * d1 + m.g22 * d2 * d2 + m.g33 * d3 * d3 + 2.0 * m.g13 * d1 * d3;
+    const double gd = 1.0 / sqrt(1.0 - vd2);
+    double pa[NPRIM] = {fmax(rf - pr[RHO], 0.0), fmax(uf - pr[UU], 0.0), gd * d1, gd * d2, gd * d3, 0.0, 0.0, 0.0};
+    Fluid<double> sa;
+    fluid_state(pa, m, sa);
+    double uo[NFLUX], ua[NFLUX];
+    flux_row(pr, s, 0, 1, gam, entropy_kappa(pr, gam), uo);
+    flux_row(pa, sa, 0, 1, gam, 0.0, ua);
+    double U[NCONS];
+#pragma unroll
+    for (int q = 0; q < 5; q++) U[q] = m.gdet * (uo[q] + ua[q]);
+    U[C_ENT] = m.gdet * uo[5] / uo[0] * (uo[0] + ua[0]);
+    double x[NPRIM];
+#pragma unroll
+    for (int q = 0; q < NPRIM; q++) x[q] = pr[q];
+    x[RHO] = fmax(pr[RHO], rf);
+    x[UU] = fmax(pr[UU], uf);
+    x[U1] = pa[U1];
+    x[U2] = pa[U2];
+    x[U3] = pa[U3];
+    const double Bc[3] = {pr[B1], pr[B2], pr[B3]};
+    int its = 0;
+    if (invert(U, Bc, m, gam, x, &its, false, nullptr, ph.inversion) == INV_FAIL) return false;
+    pr[RHO] = fmax(x[RHO], rf);
+    pr[UU] = fmax(x[UU], uf);
+    pr[U1] = x[U1];
+    pr[U2] = x[U2];
+    pr[U3] = x[U3];
+    return true;
+}
+
+// Floors (Sec. 2.7): rho >= max(1e-7/r^2, b^2/50), u >= max(1e-9/r^(10/3),
+// b^2/750) with b^2 of pr; HAMR_FLOOR_FLUID raises rho and u (utilde kept),
+// HAMR_FLOOR_DRIFT adds the material in the drift frame. s: the fluid state
+// of pr on entry, and again on return (recomputed where the velocity moved).
+// Returns 1 where a floor applied.
+__device__ __forceinline__ int cell_floors(const BlockView& v, long g, const Metric<double>& m, const PhysArgs& ph,
+                                           double pr[NPRIM], Fluid<double>& s) {
+    const double rf = fmax(v.gc[C_RHOFLR * v.n2d + g], s.bsq * (1.0 / 50.0));
+    const double uf = fmax(v.gc[C_UFLR * v.n2d + g], s.bsq * (1.0 / 750.0));
+    if (!(pr[RHO] < rf) && !(pr[UU] < uf)) return 0;
+    if (ph.floor_frame == HAMR_FLOOR_DRIFT && drift_floor(m, ph, pr, s, rf, uf)) {
+        fluid_state(pr, m, s);
+        return 1;
+    }
+    if (pr[RHO] < rf) pr[RHO] = rf;
+    if (pr[UU] < uf) pr[UU] = uf;
+    return 1;
+}
+
 template <bool MLP, typename TS>
 __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int corrector, const double* Pb,
                                                const double* __restrict__ Pf, const double* __restrict__ F1,
@@ -782,17 +854,7 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
         const bool need_fluid = ph.floors || (corrector == 1 && std::is_same<TS, double>::value);
         if (need_fluid) fluid_state(pr, m, s);
         if (ph.floors) {
-            const double bsq = s.bsq;
-            const double rf = fmax(v.gc[C_RHOFLR * v.n2d + g], bsq * (1.0 / 50.0));
-            const double uf = fmax(v.gc[C_UFLR * v.n2d + g], bsq * (1.0 / 750.0));
-            if (pr[RHO] < rf) {
-                pr[RHO] = rf;
-                fl = 1;
-            }
-            if (pr[UU] < uf) {
-                pr[UU] = uf;
-                fl = 1;
-            }
+            fl = cell_floors(v, g, m, ph, pr, s);
             if (fl) sb |= ST_FLOOR;
         }
 #pragma unroll
@@ -1008,16 +1070,7 @@ __global__ void k_reflux_cells(const DevBlock* tab, int n, const int* cblk, cons
     if (ph.floors) {
         Fluid<double> s;
         fluid_state(pr, m, s);
-        const double rf = fmax(v.gc[C_RHOFLR * v.n2d + g], s.bsq * (1.0 / 50.0));
-        const double uf = fmax(v.gc[C_UFLR * v.n2d + g], s.bsq * (1.0 / 750.0));
-        if (pr[RHO] < rf) {
-            pr[RHO] = rf;
-            fl = 1;
-        }
-        if (pr[UU] < uf) {
-            pr[UU] = uf;
-            fl = 1;
-        }
+        fl = cell_floors(v, g, m, ph, pr, s);
     }
 #pragma unroll
     for (int q = 0; q < NPRIM; q++) D.P[q * v.nc + c] = pr[q];

@@ -24,6 +24,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 EMF_AVERAGE, EMF_UPWIND = 0, 1
 C2P_ENTROPY_ONLY, C2P_MLP, C2P_MLP_RESCUE, C2P_AITKEN = 1, 2, 4, 8
 INV_NEWTON, INV_AITKEN = 0, 1
+FLOOR_FLUID, FLOOR_DRIFT = 0, 1
 MLP_FIRST, MLP_RESCUE = 0, 1
 NG = 3
 
@@ -43,7 +44,7 @@ class GridDesc(C.Structure):
     _fields_ = [("metric", C.c_int), ("a", C.c_double), ("gam", C.c_double), ("cour", C.c_double),
                 ("recon", C.c_int), ("riemann", C.c_int), ("floors", C.c_int), ("precision", C.c_int),
                 ("nblocks", C.c_int), ("blocks", C.POINTER(BlockDesc)), ("emf", C.c_int),
-                ("flatten", C.c_int), ("inversion", C.c_int)]
+                ("flatten", C.c_int), ("inversion", C.c_int), ("floor_frame", C.c_int)]
 
 
 class StepStats(C.Structure):
@@ -177,7 +178,8 @@ class Grid:
     """Owner of a hamr_grid handle."""
 
     def __init__(self, blocks, metric=METRIC_KS, a=0.9375, gam=13.0 / 9.0, cour=0.8, recon=RECON_PPM,
-                 riemann=FLUX_HLL, floors=1, precision=PREC_FP64, emf=EMF_AVERAGE, flatten=0, inversion=INV_NEWTON):
+                 riemann=FLUX_HLL, floors=1, precision=PREC_FP64, emf=EMF_AVERAGE, flatten=0, inversion=INV_NEWTON,
+                 floor_frame=FLOOR_FLUID):
         self._blocks = (BlockDesc * len(blocks))(*blocks)
         d = GridDesc()
         d.metric, d.a, d.gam, d.cour = metric, a, gam, cour
@@ -185,6 +187,7 @@ class Grid:
         d.emf = emf
         d.flatten = flatten
         d.inversion = inversion
+        d.floor_frame = floor_frame
         d.nblocks = len(blocks)
         d.blocks = self._blocks
         self.desc = d

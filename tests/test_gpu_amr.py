@@ -26,14 +26,14 @@ def _gpu():
     torch.cuda.set_device(0)
 
 
-def run_pair(blocks, states, phys, periods, emf=0, flatten=0, inversion=0):
+def run_pair(blocks, states, phys, periods, emf=0, flatten=0, inversion=0, floor_frame=0):
     from paper_1912_10192_gb300 import hamr
     ob = [O.make_block(b["n1"], b["n2"], b["n3"], b["x1min"], b["x2min"], b["x3min"], b["dx1"], b["dx2"],
                        b["dx3"], b["bc"], b["lat"]) for b in blocks]
     a = O.AmrGrid(phys, ob)
     g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], metric=phys.metric, a=phys.a, gam=phys.gam,
                   cour=phys.cour, recon=phys.recon, riemann=phys.riemann, floors=phys.floors, emf=emf,
-                  flatten=flatten, inversion=inversion)
+                  flatten=flatten, inversion=inversion, floor_frame=floor_frame)
     for i, (p, bf) in enumerate(states):
         a.set(i, p, bf)
         g.set_state(p, bf, block=i)
