@@ -277,8 +277,80 @@ def mlp_leg(args, hamr, torch, blk, dprim, dbf, cells, stream):
                      "newton_iters_per_inversion": tot["newton_iters"] / max(ninv, 1),
                      "entropy_per_step": tot["c2p_entropy"] / 2, "fail_per_step": tot["c2p_fail"] / 2}
         g.close()
+    out["inversion_variants"] = inversion_variants(hamr, torch, m)
     out["network_error_flag"] = m.error_flag()
     m.close()
+    return out
+
+
+def inversion_variants(hamr, torch, m, n=1_000_000, seed=6):
+    """The energy inversions side by side on n random states (the validation law of the network) from a
+    warm start (the true state perturbed by 5%) and a cold one (rho at rest with u = 1e-3 rho): Newton,
+    the Aitken-accelerated pressure iteration, and Newton from the network's start. Fractions of energy /
+    entropy / failed inversions, iterations per energy inversion (map evaluations for Aitken), and the
+    device time of the call."""
+    from paper_1912_10192_gb300 import workloads as W
+    pr, x1, x2 = W.random_states(n, seed=seed)
+    P = torch.from_numpy(np.ascontiguousarray(pr.T)).cuda()
+    X1, X2 = torch.from_numpy(x1).cuda(), torch.from_numpy(x2).cuda()
+    U = torch.empty((6, n), dtype=torch.float64, device="cuda")
+    hamr.prim2cons(P, X1, X2, U, a=0.9375, gam=13.0 / 9.0)
+    B = P[5:8].contiguous()
+    starts = {"warm": P.clone(), "cold": P.clone()}
+    starts["warm"][0] *= 1.05
+    starts["warm"][1] *= 0.95
+    starts["warm"][2:5] *= 1.02
+    starts["cold"][1] = 1e-3 * starts["cold"][0]
+    starts["cold"][2:5] = 0.0
+    out = {"states": n}
+    for sname, guess in starts.items():
+        for vname, flags, mlp in (("newton", 0, None), ("aitken", hamr.C2P_AITKEN, None), ("network_first", 0, m)):
+            st = torch.zeros(n, dtype=torch.int32, device="cuda")
+            it = torch.zeros(n, dtype=torch.int32, device="cuda")
+            hamr.con2prim(U, B, X1, X2, guess.clone(), st, it, flags=flags, mlp=mlp)  # warm-up
+            work = guess.clone()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            hamr.con2prim(U, B, X1, X2, work, st, it, flags=flags, mlp=mlp)
+            e1.record()
+            torch.cuda.synchronize()
+            ok = st == 0
+            out["%s_%s" % (sname, vname)] = {
+                "energy": float(ok.float().mean()), "entropy": float((st == 1).float().mean()),
+                "failed": float((st == 2).float().mean()),
+                "iters_per_energy_inversion": float(it[ok].float().mean()) if bool(ok.any()) else None,
+                "ms": round(e0.elapsed_time(e1), 3)}
+    return out
+
+
+def options_leg(args, hamr, torch, blk, dprim, dbf, cells, stream):
+    """The benchmark workload with each option of the step switched on alone (FP64): upwinded EMFs, the
+    PPM shock flattener, the Aitken inversion, floors in the drift frame; zone-cycles/s and ms/step."""
+    out = {}
+    for name, kw in (("plain", {}), ("emf_upwind", {"emf": hamr.EMF_UPWIND}), ("flatten", {"flatten": 1}),
+                     ("aitken_inversion", {"inversion": hamr.INV_AITKEN}),
+                     ("drift_floors", {"floor_frame": hamr.FLOOR_DRIFT})):
+        g = hamr.Grid([blk], **kw)
+        g.set_state(dprim, dbf, stream=stream)
+        for _ in range(args.warmup):
+            g.step(stream=stream)
+        torch.cuda.synchronize()
+        steps = min(args.steps, 20)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            g.step(stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        st = g.step(stream=stream, stats=True)
+        out[name] = {"value": cells / (ms * 1e-3), "ms_per_step": round(ms, 3),
+                     "entropy_per_step": st["c2p_entropy"], "floor_hits_per_step": st["floor_hits"],
+                     "iters_per_inversion": st["newton_iters"] / max(st["c2p_ok"] + st["c2p_entropy"] +
+                                                                       st["c2p_fail"], 1)}
+        g.close()
     return out
 
 
@@ -385,6 +457,7 @@ def run_ours(args, rank, world, local):
     extra = {}
     if not args.no_extra and world == 1:
         extra["mlp"] = mlp_leg(args, hamr, torch, blk, dprim, dbf, cells, stream)
+        extra["options"] = options_leg(args, hamr, torch, blk, dprim, dbf, cells, stream)
         extra["amr_lat"] = [amr_leg(hamr, torch, 0), amr_leg(hamr, torch, 1)]
 
     # ---- end to end: host buffers through the C ABI, copies inside the timed region
