@@ -368,6 +368,8 @@ def _amr_setup(L):
     L.ora_amr_period.argtypes = [P, C.c_double]
     L.ora_amr_period.restype = C.c_double
     L.ora_amr_stats.argtypes = [P, C.POINTER(C.c_longlong)]
+    L.ora_amr_regrid.argtypes = [P, C.c_int, C.POINTER(Block)]
+    L.ora_amr_regrid.restype = P
     for n in ("ora_amr_free", "ora_amr_set", "ora_amr_get", "ora_amr_fill", "ora_amr_stats"):
         getattr(L, n).restype = None
     _amr_ready.add(id(L))
@@ -410,6 +412,16 @@ class AmrGrid:
 
     def period(self, dt_fine=-1.0):
         return self.lib.ora_amr_period(self.h, dt_fine)
+
+    def regrid(self, blocks):
+        """A new AmrGrid on `blocks` holding this grid's state (prolongation / restriction / copy)."""
+        new = AmrGrid.__new__(AmrGrid)
+        new.lib = self.lib
+        new.blocks = list(blocks)
+        new._arr = (Block * len(blocks))(*blocks)
+        new.phys = self.phys
+        new.h = self.lib.ora_amr_regrid(self.h, len(blocks), new._arr)
+        return new
 
     def stats(self):
         s = (C.c_longlong * 4)()

@@ -2426,6 +2426,171 @@ void amr_reflux(ora_amr* m, int c) {
             }
 }
 
+/* ------------------------------------------------------------------ */
+/* Regridding (Sec. 3.2: (de)refinement)                                */
+/* ------------------------------------------------------------------ */
+/*
+ * The state of a new tree from the old one at the same time. Cell-centred
+ * primitives are sampled like ghosts (same cell size: copied; old finer:
+ * volume average; old coarser: MINMOD-limited linear prolongation). Reading:
+ * primitives, not conserved variables, are prolonged and restricted (the
+ * paper allows either and calls the primitive form faster and more robust).
+ * Face fields: old face at the same size copied, old finer: area average,
+ * old coarser: the divergence-free prolongation of Balsara (2001), which
+ * fills a coarse cell with a field quadratic in the cell's local coordinates,
+ * exactly divergence-free, that matches every coarse face's mean and
+ * MINMOD-limited tangential slopes (a slope whose stencil leaves the old
+ * block's faces is 0); a fine face takes the polynomial at its centre (its
+ * mean, the polynomial being linear on the face). A face point on a plane
+ * between two old blocks is taken from the finer one.
+ */
+
+/* tangential MINMOD slope of face field a at face (i, j, k) of block N along
+ * direction b, per unit of the local coordinate (half the per-cell slope) */
+double face_slope(const AmrBlk& N, int a, const int ii[4], int b) {
+    const ora_grid* g = N.g;
+    const int nn[4] = {0, g->d.n1, g->d.n2, g->d.n3};
+    if (ii[b] - 1 < 0 || ii[b] + 1 > nn[b] - 1) return 0.0;
+    int im[4] = {0, ii[1], ii[2], ii[3]}, ip[4] = {0, ii[1], ii[2], ii[3]};
+    im[b]--;
+    ip[b]++;
+    const double* B = g->bface.data() + (size_t)(a - 1) * g->ncell;
+    const double q0 = B[cidx(g, ii[1], ii[2], ii[3])];
+    return 0.5 * minmod(q0 - B[cidx(g, im[1], im[2], im[3])], B[cidx(g, ip[1], ip[2], ip[3])] - q0);
+}
+
+/* face field fd at point x from the Balsara reconstruction in the coarse cell
+ * of block N that holds the point probe */
+double balsara_face(const AmrBlk& N, const double x[4], const double probe[4], int fd) {
+    const ora_grid* g = N.g;
+    const int nn[4] = {0, g->d.n1, g->d.n2, g->d.n3};
+    int ic[4];
+    double xi[4];
+    for (int d = 1; d <= 3; d++) {
+        ic[d] = (int)std::floor((probe[d] - N.lo[d]) / N.h[d]);
+        if (ic[d] < 0) ic[d] = 0;
+        if (ic[d] > nn[d] - 1) ic[d] = nn[d] - 1;
+        xi[d] = 2.0 * (x[d] - (N.lo[d] + (ic[d] + 0.5) * N.h[d])) / N.h[d];
+    }
+    /* per face component a: mean values on the lower/upper faces, and the
+     * tangential slopes on both */
+    double Fm[4], Fp[4], Sm[4][4], Sp[4][4];
+    for (int a = 1; a <= 3; a++) {
+        int lo[4] = {0, ic[1], ic[2], ic[3]}, hi[4] = {0, ic[1], ic[2], ic[3]};
+        hi[a]++;
+        const double* B = g->bface.data() + (size_t)(a - 1) * g->ncell;
+        Fm[a] = B[cidx(g, lo[1], lo[2], lo[3])];
+        Fp[a] = B[cidx(g, hi[1], hi[2], hi[3])];
+        for (int b = 1; b <= 3; b++) {
+            Sm[a][b] = Sp[a][b] = 0.0;
+            if (b == a) continue;
+            Sm[a][b] = face_slope(N, a, lo, b);
+            Sp[a][b] = face_slope(N, a, hi, b);
+        }
+    }
+    /* B_a = A0 + A_a xi_a + sum_b (A_b xi_b + A_ab xi_a xi_b) + A_aa xi_a^2 (b != a);
+     * divergence-free: A^a_aa = -(H_a / 2) sum_{b != a} A^b_{ba} / H_b */
+    double Aab[4][4];
+    for (int a = 1; a <= 3; a++)
+        for (int b = 1; b <= 3; b++) Aab[a][b] = (b == a) ? 0.0 : 0.5 * (Sp[a][b] - Sm[a][b]);
+    const int a = fd;
+    double Aaa = 0.0;
+    for (int b = 1; b <= 3; b++)
+        if (b != a) Aaa += Aab[b][a] / N.h[b];
+    Aaa *= -0.5 * N.h[a];
+    double val = 0.5 * (Fp[a] + Fm[a]) - Aaa + 0.5 * (Fp[a] - Fm[a]) * xi[a] + Aaa * xi[a] * xi[a];
+    for (int b = 1; b <= 3; b++) {
+        if (b == a) continue;
+        val += 0.5 * (Sp[a][b] + Sm[a][b]) * xi[b] + Aab[a][b] * xi[a] * xi[b];
+    }
+    return val;
+}
+
+/* x inside the domain's periodic range along the periodic directions */
+void wrap_periodic(const ora_amr* m, double x[4]) {
+    for (int d = 1; d <= 3; d++) {
+        if (!m->per[d]) continue;
+        const double L = m->dhi[d] - m->dlo[d];
+        while (x[d] >= m->dhi[d]) x[d] -= L;
+        while (x[d] < m->dlo[d]) x[d] += L;
+    }
+}
+
+void amr_regrid_fill(ora_amr* old, ora_amr* m) {
+    for (int b = 0; b < (int)m->b.size(); b++) {
+        AmrBlk& R = m->b[b];
+        ora_grid* g = R.g;
+        const ora_desc& d = g->d;
+        const long nc = g->ncell;
+        const int nn[4] = {0, d.n1, d.n2, d.n3};
+        for (int k = 0; k < d.n3; k++)
+            for (int j = 0; j < d.n2; j++)
+                for (int i = 0; i < d.n1; i++) {
+                    double x[4] = {0, R.lo[1] + (i + 0.5) * R.h[1], R.lo[2] + (j + 0.5) * R.h[2],
+                                   R.lo[3] + (k + 0.5) * R.h[3]};
+                    const int n = amr_find(old, x);
+                    if (n < 0) continue;
+                    Src S;
+                    S.Pa = old->b[n].g->prim.data();
+                    S.Ba = old->b[n].g->bface.data();
+                    S.Pb = S.Bb = nullptr;
+                    S.w = 0.0;
+                    double out[NPR];
+                    amr_sample_cell(old, n, S, x, R.h, out);
+                    for (int v = 0; v < 5; v++) g->prim[v * nc + cidx(g, i, j, k)] = out[v];
+                }
+        for (int fd = 1; fd <= 3; fd++)
+            for (int k = 0; k < d.n3 + (fd == 3); k++)
+                for (int j = 0; j < d.n2 + (fd == 2); j++)
+                    for (int i = 0; i < d.n1 + (fd == 1); i++) {
+                        const int ii[4] = {0, i, j, k};
+                        double x[4] = {0, R.lo[1] + (i + 0.5) * R.h[1], R.lo[2] + (j + 0.5) * R.h[2],
+                                       R.lo[3] + (k + 0.5) * R.h[3]};
+                        x[fd] = R.lo[fd] + ii[fd] * R.h[fd];
+                        double pl[4] = {0, x[1], x[2], x[3]}, pr[4] = {0, x[1], x[2], x[3]};
+                        pl[fd] -= 0.25 * R.h[fd];
+                        pr[fd] += 0.25 * R.h[fd];
+                        wrap_periodic(old, pl);
+                        wrap_periodic(old, pr);
+                        const int nl = amr_find(old, pl), nr = amr_find(old, pr);
+                        int n = nr;
+                        const double* probe = pr;
+                        if (n < 0 || (nl >= 0 && old->b[nl].h[1] < old->b[nr].h[1] * (1.0 - 1e-9))) {
+                            n = nl;
+                            probe = pl;
+                        }
+                        if (n < 0) continue;
+                        const AmrBlk& N = old->b[n];
+                        /* the face point in the source block's frame (across a periodic boundary) */
+                        double xs[4] = {0, probe[1], probe[2], probe[3]};
+                        xs[fd] += (probe == pl ? 0.25 : -0.25) * R.h[fd];
+                        double v;
+                        if (N.h[1] > R.h[1] * 1.5) {
+                            v = balsara_face(N, xs, probe, fd);
+                        } else {
+                            Src S;
+                            S.Pa = N.g->prim.data();
+                            S.Ba = N.g->bface.data();
+                            S.Pb = S.Bb = nullptr;
+                            S.w = 0.0;
+                            v = amr_sample_face(old, n, S, xs, R.h, fd);
+                        }
+                        g->bface[(fd - 1) * nc + cidx(g, i, j, k)] = v;
+                    }
+        for (int k = 0; k < d.n3; k++)
+            for (int j = 0; j < d.n2; j++)
+                for (int i = 0; i < d.n1; i++) {
+                    real Bc[3];
+                    centre_b(g, g->bface.data(), i, j, k, Bc);
+                    for (int q = 0; q < 3; q++) g->prim[(B1 + q) * nc + cidx(g, i, j, k)] = tod(Bc[q]);
+                }
+        (void)nn;
+        R.Pold = g->prim;
+        R.Bold = g->bface;
+        R.s0 = 0;
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -2561,6 +2726,14 @@ double ora_amr_period(ora_amr* m, double dtf) {
     }
     m->s = 0;
     return dtf;
+}
+
+ora_amr* ora_amr_regrid(ora_amr* old, int nb, const ora_block* blocks) {
+    ora_amr_fill(old);
+    ora_amr* m = ora_amr_new(&old->phys, nb, blocks);
+    amr_regrid_fill(old, m);
+    ora_amr_fill(m);
+    return m;
 }
 
 void ora_amr_stats(const ora_amr* m, long long* counts4) {

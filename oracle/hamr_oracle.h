@@ -114,6 +114,11 @@ void ora_amr_fill(ora_amr* m);
  * dt_fine <= 0: the CFL fine step min_b dt_b / 2^lat_b; returns dt_fine */
 double ora_amr_period(ora_amr* m, double dt_fine);
 void ora_amr_stats(const ora_amr* m, long long* counts4);
+/* a new tree with the old tree's state (cells: copy / volume average /
+ * MINMOD prolongation of the primitives; faces: copy / area average /
+ * Balsara 2001 divergence-free prolongation); the old tree is unchanged
+ * apart from its ghost zones */
+ora_amr* ora_amr_regrid(ora_amr* old, int nb, const ora_block* blocks);
 
 /* learned inversion guess: the ten inputs of n conserved states (U6 and Bc3
  * as in ora_c2p_many; f10 is n x 10) and the two targets of n primitive
