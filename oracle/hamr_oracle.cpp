@@ -2441,8 +2441,11 @@ void amr_reflux(ora_amr* m, int c) {
  * exactly divergence-free, that matches every coarse face's mean and
  * MINMOD-limited tangential slopes (a slope whose stencil leaves the old
  * block's faces is 0); a fine face takes the polynomial at its centre (its
- * mean, the polynomial being linear on the face). A face point on a plane
- * between two old blocks is taken from the finer one.
+ * mean, the polynomial being linear on the face). Where a coarse cell borders
+ * old finer data, the fine faces on that coarse face are the old ones and the
+ * interior fine faces are corrected (interior_fine_face). A face point on a
+ * plane between two old blocks is taken from the finer one. A regrid changes
+ * a region's cell size by a factor of 2 at most.
  */
 
 /* tangential MINMOD slope of face field a at face (i, j, k) of block N along
@@ -2459,21 +2462,26 @@ double face_slope(const AmrBlk& N, int a, const int ii[4], int b) {
     return 0.5 * minmod(q0 - B[cidx(g, im[1], im[2], im[3])], B[cidx(g, ip[1], ip[2], ip[3])] - q0);
 }
 
-/* face field fd at point x from the Balsara reconstruction in the coarse cell
- * of block N that holds the point probe */
-double balsara_face(const AmrBlk& N, const double x[4], const double probe[4], int fd) {
+/* the coarse cell of N holding point `probe`, and the local coordinates
+ * (-1..1 across the cell) of point x in it */
+void coarse_cell(const AmrBlk& N, const double x[4], const double probe[4], int ic[4], double xi[4]) {
     const ora_grid* g = N.g;
     const int nn[4] = {0, g->d.n1, g->d.n2, g->d.n3};
-    int ic[4];
-    double xi[4];
     for (int d = 1; d <= 3; d++) {
         ic[d] = (int)std::floor((probe[d] - N.lo[d]) / N.h[d]);
         if (ic[d] < 0) ic[d] = 0;
         if (ic[d] > nn[d] - 1) ic[d] = nn[d] - 1;
         xi[d] = 2.0 * (x[d] - (N.lo[d] + (ic[d] + 0.5) * N.h[d])) / N.h[d];
     }
-    /* per face component a: mean values on the lower/upper faces, and the
-     * tangential slopes on both */
+}
+
+/* Balsara's polynomial of face component fd in coarse cell ic of N at local
+ * coordinates xi. B_a = A0 + A_a xi_a + sum_{b != a} (A_b xi_b + A_ab xi_a xi_b)
+ * + A_aa xi_a^2: the means Fm, Fp of the lower and upper faces and their
+ * tangential slopes Sm, Sp give A_a, A_b, A_ab and A0 + A_aa; divergence-free
+ * fixes A^a_aa = -(H_a / 2) sum_{b != a} A^b_ba / H_b. */
+double balsara_poly(const AmrBlk& N, const int ic[4], const double xi[4], int fd) {
+    const ora_grid* g = N.g;
     double Fm[4], Fp[4], Sm[4][4], Sp[4][4];
     for (int a = 1; a <= 3; a++) {
         int lo[4] = {0, ic[1], ic[2], ic[3]}, hi[4] = {0, ic[1], ic[2], ic[3]};
@@ -2488,8 +2496,6 @@ double balsara_face(const AmrBlk& N, const double x[4], const double probe[4], i
             Sp[a][b] = face_slope(N, a, hi, b);
         }
     }
-    /* B_a = A0 + A_a xi_a + sum_b (A_b xi_b + A_ab xi_a xi_b) + A_aa xi_a^2 (b != a);
-     * divergence-free: A^a_aa = -(H_a / 2) sum_{b != a} A^b_{ba} / H_b */
     double Aab[4][4];
     for (int a = 1; a <= 3; a++)
         for (int b = 1; b <= 3; b++) Aab[a][b] = (b == a) ? 0.0 : 0.5 * (Sp[a][b] - Sm[a][b]);
@@ -2504,6 +2510,118 @@ double balsara_face(const AmrBlk& N, const double x[4], const double probe[4], i
         val += 0.5 * (Sp[a][b] + Sm[a][b]) * xi[b] + Aab[a][b] * xi[a] * xi[b];
     }
     return val;
+}
+
+void wrap_periodic(const ora_amr* m, double x[4]);
+
+/* A fine face (cell size hn, half of N's) on the coarse face (a, side) of cell
+ * ic, at tangential halves tb, tc (0: lower, 1: upper) of the other two
+ * directions b < c: the old tree's finer data beyond that coarse face if there
+ * is any (copied or area-averaged), else the polynomial (the coarse face's
+ * linear profile). */
+double fine_face_on_coarse(const ora_amr* old, const AmrBlk& N, const int ic[4], int a, int side, int tb, int tc,
+                           const double hn[4]) {
+    const int b = (a == 1) ? 2 : 1, c = (a == 3) ? 2 : 3;
+    double x[4];
+    x[a] = N.lo[a] + (ic[a] + side) * N.h[a];
+    x[b] = N.lo[b] + (ic[b] + 0.25 + 0.5 * tb) * N.h[b];
+    x[c] = N.lo[c] + (ic[c] + 0.25 + 0.5 * tc) * N.h[c];
+    double probe[4] = {0, x[1], x[2], x[3]};
+    probe[a] += (side ? 0.25 : -0.25) * hn[a];
+    wrap_periodic(old, probe);
+    const int n = amr_find(old, probe);
+    if (n >= 0 && old->b[n].h[1] < N.h[1] * (1.0 - 1e-9)) {
+        double xs[4] = {0, probe[1], probe[2], probe[3]};
+        xs[a] -= (side ? 0.25 : -0.25) * hn[a];
+        Src S;
+        S.Pa = old->b[n].g->prim.data();
+        S.Ba = old->b[n].g->bface.data();
+        S.Pb = S.Bb = nullptr;
+        S.w = 0.0;
+        return amr_sample_face(old, n, S, xs, hn, a);
+    }
+    double xi[4] = {0, 0.0, 0.0, 0.0};
+    xi[a] = side ? 1.0 : -1.0;
+    xi[b] = tb ? 0.5 : -0.5;
+    xi[c] = tc ? 0.5 : -0.5;
+    return balsara_poly(N, ic, xi, a);
+}
+
+/* A fine face interior to coarse cell ic (local plane xi_fd = 0). Reading:
+ * the polynomial's value is a prior; the 24 fine faces on the cell's boundary
+ * (fine_face_on_coarse: old finer data where it exists) and the 12 interior
+ * faces must make each of the 8 fine cells divergence-free, and the interior
+ * faces take the smallest change (least squares) from the prior that does.
+ * With D_c the prior divergence (flux form, face areas A_d) of fine cell c,
+ * the change is A_d (lambda_lo - lambda_hi) across a face of direction d,
+ * where L lambda = -D and L is the 8x8 graph Laplacian of the fine cells
+ * (weights A_d^2 between neighbours along d); solved here with lambda of cell
+ * (0,0,0) fixed at 0 (the change does not depend on that constant). Where the
+ * boundary faces follow the polynomial, D = 0 and the prior stands. */
+double interior_fine_face(const ora_amr* old, const AmrBlk& N, const int ic[4], const double xi[4], int fd,
+                          const double hn[4]) {
+    /* F[a][plane 0..2][t_b][t_c] */
+    double F[4][3][2][2];
+    for (int a = 1; a <= 3; a++) {
+        const int b = (a == 1) ? 2 : 1, c = (a == 3) ? 2 : 3;
+        for (int tb = 0; tb < 2; tb++)
+            for (int tc = 0; tc < 2; tc++) {
+                F[a][0][tb][tc] = fine_face_on_coarse(old, N, ic, a, 0, tb, tc, hn);
+                F[a][2][tb][tc] = fine_face_on_coarse(old, N, ic, a, 1, tb, tc, hn);
+                double x0[4] = {0, 0.0, 0.0, 0.0};
+                x0[b] = tb ? 0.5 : -0.5;
+                x0[c] = tc ? 0.5 : -0.5;
+                F[a][1][tb][tc] = balsara_poly(N, ic, x0, a);
+            }
+    }
+    const double A[4] = {0, hn[2] * hn[3], hn[1] * hn[3], hn[1] * hn[2]};
+    /* fine cells c = i1 + 2 i2 + 4 i3 */
+    double D[8];
+    for (int c = 0; c < 8; c++) {
+        const int ix[4] = {0, c & 1, (c >> 1) & 1, (c >> 2) & 1};
+        double sum = 0.0;
+        for (int a = 1; a <= 3; a++) {
+            const int b = (a == 1) ? 2 : 1, cc = (a == 3) ? 2 : 3;
+            sum += A[a] * (F[a][ix[a] + 1][ix[b]][ix[cc]] - F[a][ix[a]][ix[b]][ix[cc]]);
+        }
+        D[c] = sum;
+    }
+    /* L lambda = -D with lambda_0 = 0: the 7x7 system of cells 1..7 by Gaussian elimination */
+    double M[7][8];
+    for (int r = 0; r < 7; r++)
+        for (int q = 0; q < 8; q++) M[r][q] = 0.0;
+    for (int r = 1; r < 8; r++) {
+        double diag = 0.0;
+        for (int a = 1; a <= 3; a++) {
+            diag += A[a] * A[a];
+            const int nb = r ^ (1 << (a - 1));
+            if (nb != 0) M[r - 1][nb - 1] -= A[a] * A[a];
+        }
+        M[r - 1][r - 1] += diag;
+        M[r - 1][7] = -D[r];
+    }
+    for (int p = 0; p < 7; p++)
+        for (int r = p + 1; r < 7; r++) {
+            const double f = M[r][p] / M[p][p];
+            for (int q = p; q < 8; q++) M[r][q] -= f * M[p][q];
+        }
+    double lam[8];
+    lam[0] = 0.0;
+    for (int p = 6; p >= 0; p--) {
+        double sum = M[p][7];
+        for (int q = p + 1; q < 7; q++) sum -= M[p][q] * lam[q + 1];
+        lam[p + 1] = sum / M[p][p];
+    }
+    const int b = (fd == 1) ? 2 : 1, cc = (fd == 3) ? 2 : 3;
+    const int tb = xi[b] > 0.0, tc = xi[cc] > 0.0;
+    int ix[4] = {0, 0, 0, 0};
+    ix[b] = tb;
+    ix[cc] = tc;
+    ix[fd] = 0;
+    const int clo = ix[1] + 2 * ix[2] + 4 * ix[3];
+    ix[fd] = 1;
+    const int chi = ix[1] + 2 * ix[2] + 4 * ix[3];
+    return F[fd][1][tb][tc] + A[fd] * (lam[clo] - lam[chi]);
 }
 
 /* x inside the domain's periodic range along the periodic directions */
@@ -2566,7 +2684,13 @@ void amr_regrid_fill(ora_amr* old, ora_amr* m) {
                         xs[fd] += (probe == pl ? 0.25 : -0.25) * R.h[fd];
                         double v;
                         if (N.h[1] > R.h[1] * 1.5) {
-                            v = balsara_face(N, xs, probe, fd);
+                            int ic[4];
+                            double xi[4];
+                            coarse_cell(N, xs, probe, ic, xi);
+                            if (std::fabs(xi[fd]) > 0.5)
+                                v = balsara_poly(N, ic, xi, fd);  /* on a coarse face: its linear profile */
+                            else
+                                v = interior_fine_face(old, N, ic, xi, fd, R.h);
                         } else {
                             Src S;
                             S.Pa = N.g->prim.data();

@@ -100,6 +100,30 @@ def test_prolonged_field_is_divergence_free_and_matches_the_coarse_faces():
     assert np.abs(acc - cf).max() <= 1e-14 * bmax
 
 
+def test_refinement_next_to_existing_fine_blocks_stays_divergence_free():
+    """Refining a block whose neighbour is already fine: the new fine faces on the shared plane are the
+    neighbour's faces (copied), and the interior fine faces are corrected so that every fine cell is
+    divergence-free (the coarse face's linear profile alone would leave each fine cell with a
+    divergence of the size of the neighbour's sub-face variation)."""
+    old = W.flat_box_tree(base=(2, 2, 2), n=6, refine=((0, 0, 0),))
+    new = W.flat_box_tree(base=(2, 2, 2), n=6, refine=((0, 0, 0), (1, 0, 0)))
+    a = grid(old, W.flat_box_state(old, bamp=0.3))
+    a.period()  # the fine and coarse faces at the shared plane have been synchronised by a step
+    r = a.regrid(ora_blocks(new))
+    bmax = max(np.abs(r.get(i)[1]).max() for i in range(len(new)))
+    for i, b in enumerate(new):
+        _, bf = r.get(i)
+        assert np.abs(div_b(b, bf)).max() <= 1e-12 * bmax / b["dx1"], i
+    # faces on x = 0.5 of the new fine blocks equal the old fine faces there
+    fine_old = {(b["x2min"], b["x3min"]): i for i, b in enumerate(old) if b["dx1"] < 0.06 and b["x1min"] > 0.2}
+    for i, b in enumerate(new):
+        if b["dx1"] < 0.06 and b["x1min"] == 0.5:
+            j = fine_old[(b["x2min"], b["x3min"])]
+            got = faces(b, r.get(i)[1])[0][:, :, 0]
+            want = faces(old[j], a.get(j)[1])[0][:, :, -1]
+            assert np.array_equal(got, want), i
+
+
 def _linear_states(blocks, c=(0.1, -0.05, 0.02), g=0.3):
     """rho, u linear in x; face field B = (1 + g x, 0.5 - g y, 0.2) (divergence-free, linear)."""
     out = []
