@@ -192,6 +192,49 @@ int hamr_grid_fill_ghosts(hamr_grid* g, void* stream);
 /* Reads the accumulated counters of the last step; synchronises the device. */
 int hamr_grid_stats(const hamr_grid* g, hamr_step_stats* stats);
 
+/* ---- dynamic refinement (Sec. 3.2: (de)refinement, nesting, prolongation
+ * and restriction) ---- */
+
+/* out[b] (host, nblocks doubles) = the maximum of primitive field `field`
+ * (0..7) over the interior cells of block b, the input of a refinement
+ * criterion (the paper's example: the maximum density of a block).
+ * Synchronises `stream`. HAMR_EINVAL for a bad field or a NULL pointer. */
+int hamr_grid_block_max(const hamr_grid* g, int field, double* out, void* stream);
+
+/* Replaces the grid's block tree by `blocks` (nblocks >= 2, the same domain
+ * and physics; every block's state is filled from the old tree at its current
+ * time): cells copied, volume-averaged (restriction) or prolonged with
+ * MINMOD-limited slopes; the face field copied, area-averaged or prolonged
+ * with the divergence-free reconstruction of Balsara (2001) (next to
+ * existing finer blocks, the interior fine faces corrected so that every fine
+ * cell stays divergence-free). Primitives are
+ * what is prolonged and restricted. The grid must be a multi-block grid
+ * (nblocks >= 2 at creation) with every block loaded; the grid keeps its
+ * physics options, launch shapes and learned guess. Runs on `stream` and
+ * synchronises it before the old blocks are freed. The new tree must cover
+ * the old domain and change the cell size of any region by at most a factor
+ * of 2 (HAMR_EINVAL otherwise); on any error the old tree is kept. */
+int hamr_grid_regrid(hamr_grid* g, int nblocks, const hamr_block_desc* blocks, void* stream);
+
+/* Host-only: the octree that the paper's nesting rule gives for per-block
+ * target levels. `cur` (n blocks) is an octree over a base grid of blocks
+ * of extent base_ext[3] from corner dlo[3] (a level-L block has extent
+ * base_ext / 2^L; every block has the same cell counts); target[b] is the
+ * level block b's region should have (e.g. lmax where a criterion holds, 0
+ * elsewhere). Each region moves one level toward its target (the regrid
+ * prolongs and restricts by factors of 2: call again, with the regridded
+ * grid's criterion, until the tree stops changing); then every block whose
+ * face or edge neighbour is two or more levels finer is refined until the
+ * jump is one level (repeated to a fixed point); regions whose targets fell
+ * are derefined where that rule allows. `periodic[3]` marks periodic
+ * directions (neighbours across them count). Output: *nout blocks written to
+ * out (capacity `cap`; HAMR_EINVAL if exceeded, *nout = the count needed),
+ * in base-block order with children in z-order; interior faces get
+ * HAMR_BC_BLOCK, domain faces the bc of the input blocks on that side;
+ * lat = (finest level - level). Levels above 10 are refused. */
+int hamr_tree_adapt(const hamr_block_desc* cur, int n, const int* target, const double dlo[3],
+                    const double base_ext[3], const int periodic[3], hamr_block_desc* out, int cap, int* nout);
+
 /* ---- measurement ---- */
 /* Per-kernel device time of the grid's launches. */
 typedef struct {

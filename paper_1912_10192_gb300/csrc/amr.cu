@@ -265,6 +265,280 @@ __global__ void k_ghost_faces(AmrDomain A, const int* list, int sigma, int s) {
     out[(fd - 1) * v.nc + t] = (neg && fd == 2) ? -val : val;
 }
 
+// ------------------------------------------------------------------ regridding
+// The state of a new tree from the old one (Sec. 3.2: prolongation and
+// restriction on (de)refinement). Cell-centred primitives are sampled like
+// ghosts from the old block holding the cell centre (copy, volume average or
+// MINMOD-limited prolongation; primitives, the paper's faster and more
+// robust choice). Face fields: copy, area average, or from an old coarser
+// block the divergence-free reconstruction of Balsara (2001): a field
+// quadratic in the coarse cell's local coordinates that is exactly
+// divergence-free and matches each coarse face's mean and MINMOD-limited
+// tangential slopes (0 where the stencil leaves the old block's faces); a
+// fine face takes it at its centre. Where a coarse cell borders old finer
+// data, the fine faces on that coarse face are the old fine faces and the
+// cell's interior fine faces are corrected (least change) so that each fine
+// cell stays divergence-free. A face on a plane between two old blocks is
+// taken from the finer one.
+
+__device__ inline void wrap_domain(const AmrDomain& A, double x[4]) {
+    for (int d = 1; d <= 3; d++) {
+        if (!A.per[d]) continue;
+        const double L = A.dhi[d] - A.dlo[d];
+        while (x[d] >= A.dhi[d]) x[d] -= L;
+        while (x[d] < A.dlo[d]) x[d] += L;
+    }
+}
+
+__global__ void k_regrid_cells(AmrDomain A, const DevBlock* ntab) {
+    const DevBlock& R = ntab[blockIdx.y];
+    const BlockView& v = R.v;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)v.n1 * v.n2 * v.n3) return;
+    const int i = (int)(t % v.n1), j = (int)((t / v.n1) % v.n2), k = (int)(t / ((long)v.n1 * v.n2));
+    double x[4] = {0.0, R.lo[1] + (i + 0.5) * R.h[1], R.lo[2] + (j + 0.5) * R.h[2], R.lo[3] + (k + 0.5) * R.h[3]};
+    const int n = find_block(A, A.tab, x);
+    if (n < 0) return;
+    const DevBlock& N = A.tab[n];
+    int i0[4], cnt[4];
+    double dl[4];
+    footprint(N, x, R.h, i0, cnt, dl);
+    const int nn[4] = {0, N.v.n1, N.v.n2, N.v.n3};
+    const double inv = 1.0 / (double)(cnt[1] * cnt[2] * cnt[3]);
+    const long c = pidx(v, i, j, k);
+    for (int q = 0; q < 5; q++) {
+        double sum = 0.0;
+        for (int c3 = 0; c3 < cnt[3]; c3++)
+            for (int c2 = 0; c2 < cnt[2]; c2++)
+                for (int c1 = 0; c1 < cnt[1]; c1++) {
+                    const int ii[4] = {0, i0[1] + c1, i0[2] + c2, i0[3] + c3};
+                    const long cs = pidx(N.v, ii[1], ii[2], ii[3]);
+                    const double q0 = N.P[q * N.v.nc + cs];
+                    double val = q0;
+                    for (int d = 1; d <= 3; d++) {
+                        if (dl[d] == 0.0) continue;
+                        if (ii[d] - 1 < 0 || ii[d] + 1 >= nn[d]) continue;
+                        const long st = (d == 1) ? 1 : ((d == 2) ? (long)N.v.n1p : (long)N.v.n1p * N.v.n2p);
+                        val += dl[d] * minmod_(q0 - N.P[q * N.v.nc + cs - st], N.P[q * N.v.nc + cs + st] - q0);
+                    }
+                    sum += val;
+                }
+        R.P[q * v.nc + c] = sum * inv;
+    }
+}
+
+// tangential MINMOD slope of face field a of block N at face ii along b, per unit local coordinate
+__device__ inline double face_slope(const DevBlock& N, int a, const int ii[4], int b) {
+    const int nn[4] = {0, N.v.n1, N.v.n2, N.v.n3};
+    if (ii[b] - 1 < 0 || ii[b] + 1 > nn[b] - 1) return 0.0;
+    const long st = (b == 1) ? 1 : ((b == 2) ? (long)N.v.n1p : (long)N.v.n1p * N.v.n2p);
+    const double* B = N.B + (long)(a - 1) * N.v.nc;
+    const long c = pidx(N.v, ii[1], ii[2], ii[3]);
+    const double q0 = B[c];
+    return 0.5 * minmod_(q0 - B[c - st], B[c + st] - q0);
+}
+
+// the coarse cell of N holding `probe` and the local coordinates (-1..1) of x in it
+__device__ inline void coarse_cell(const DevBlock& N, const double x[4], const double probe[4], int ic[4],
+                                   double xi[4]) {
+    const int nn[4] = {0, N.v.n1, N.v.n2, N.v.n3};
+    for (int d = 1; d <= 3; d++) {
+        ic[d] = (int)floor((probe[d] - N.lo[d]) / N.h[d]);
+        ic[d] = min(max(ic[d], 0), nn[d] - 1);
+        xi[d] = 2.0 * (x[d] - (N.lo[d] + (ic[d] + 0.5) * N.h[d])) / N.h[d];
+    }
+}
+
+// Balsara's divergence-free polynomial of face component fd in coarse cell ic of N at local coordinates xi
+__device__ inline double balsara_poly(const DevBlock& N, const int ic[4], const double xi[4], int fd) {
+    double Fm[4], Fp[4], Sm[4][4], Sp[4][4];
+    for (int a = 1; a <= 3; a++) {
+        int lo[4] = {0, ic[1], ic[2], ic[3]}, hi[4] = {0, ic[1], ic[2], ic[3]};
+        hi[a]++;
+        const double* B = N.B + (long)(a - 1) * N.v.nc;
+        Fm[a] = B[pidx(N.v, lo[1], lo[2], lo[3])];
+        Fp[a] = B[pidx(N.v, hi[1], hi[2], hi[3])];
+        for (int b = 1; b <= 3; b++) {
+            Sm[a][b] = Sp[a][b] = 0.0;
+            if (b == a) continue;
+            Sm[a][b] = face_slope(N, a, lo, b);
+            Sp[a][b] = face_slope(N, a, hi, b);
+        }
+    }
+    const int a = fd;
+    double Aaa = 0.0;
+    for (int b = 1; b <= 3; b++)
+        if (b != a) Aaa += 0.5 * (Sp[b][a] - Sm[b][a]) / N.h[b];
+    Aaa *= -0.5 * N.h[a];
+    double val = 0.5 * (Fp[a] + Fm[a]) - Aaa + 0.5 * (Fp[a] - Fm[a]) * xi[a] + Aaa * xi[a] * xi[a];
+    for (int b = 1; b <= 3; b++) {
+        if (b == a) continue;
+        val += 0.5 * (Sp[a][b] + Sm[a][b]) * xi[b] + 0.5 * (Sp[a][b] - Sm[a][b]) * xi[a] * xi[b];
+    }
+    return val;
+}
+
+__device__ inline double sample_face_plain(const DevBlock& N, const double x[4], const double ht[4], int fd);
+
+// a fine face (cell size hn, half of N's) on coarse face (a, side) of cell ic at tangential halves
+// tb, tc of the other two directions: the old tree's finer data beyond it, else the face's linear profile
+__device__ inline double fine_face_on_coarse(const AmrDomain& A, const DevBlock& N, const int ic[4], int a,
+                                             int side, int tb, int tc, const double hn[4]) {
+    const int b = (a == 1) ? 2 : 1, c = (a == 3) ? 2 : 3;
+    double x[4];
+    x[0] = 0.0;
+    x[a] = N.lo[a] + (ic[a] + side) * N.h[a];
+    x[b] = N.lo[b] + (ic[b] + 0.25 + 0.5 * tb) * N.h[b];
+    x[c] = N.lo[c] + (ic[c] + 0.25 + 0.5 * tc) * N.h[c];
+    double probe[4] = {0.0, x[1], x[2], x[3]};
+    probe[a] += (side ? 0.25 : -0.25) * hn[a];
+    wrap_domain(A, probe);
+    const int n = find_block(A, A.tab, probe);
+    if (n >= 0 && A.tab[n].h[1] < N.h[1] * (1.0 - 1e-9)) {
+        double xs[4] = {0.0, probe[1], probe[2], probe[3]};
+        xs[a] -= (side ? 0.25 : -0.25) * hn[a];
+        return sample_face_plain(A.tab[n], xs, hn, a);
+    }
+    double xi[4] = {0.0, 0.0, 0.0, 0.0};
+    xi[a] = side ? 1.0 : -1.0;
+    xi[b] = tb ? 0.5 : -0.5;
+    xi[c] = tc ? 0.5 : -0.5;
+    return balsara_poly(N, ic, xi, a);
+}
+
+// a fine face interior to coarse cell ic (local plane xi_fd = 0): the polynomial's value corrected
+// by the least change of the 12 interior faces that makes the 8 fine cells divergence-free, given
+// the 24 fine faces on the cell's boundary. The fine cells' graph Laplacian L (weights A_d^2, A_d
+// the fine face areas) has the parity vectors chi_s(c) = (-1)^(s.c) as eigenvectors with
+// eigenvalues 2 sum_d s_d A_d^2, so L lambda = -D is solved in closed form; the change across an
+// interior face of direction d is A_d (lambda_lo - lambda_hi).
+__device__ inline double interior_fine_face(const AmrDomain& A, const DevBlock& N, const int ic[4],
+                                            const double xi[4], int fd, const double hn[4]) {
+    double F[4][3][2][2];
+    for (int a = 1; a <= 3; a++) {
+        const int b = (a == 1) ? 2 : 1, c = (a == 3) ? 2 : 3;
+        for (int tb = 0; tb < 2; tb++)
+            for (int tc = 0; tc < 2; tc++) {
+                F[a][0][tb][tc] = fine_face_on_coarse(A, N, ic, a, 0, tb, tc, hn);
+                F[a][2][tb][tc] = fine_face_on_coarse(A, N, ic, a, 1, tb, tc, hn);
+                double x0[4] = {0.0, 0.0, 0.0, 0.0};
+                x0[b] = tb ? 0.5 : -0.5;
+                x0[c] = tc ? 0.5 : -0.5;
+                F[a][1][tb][tc] = balsara_poly(N, ic, x0, a);
+            }
+    }
+    const double Ar[4] = {0.0, hn[2] * hn[3], hn[1] * hn[3], hn[1] * hn[2]};
+    double D[8];
+    for (int c = 0; c < 8; c++) {
+        const int ix[4] = {0, c & 1, (c >> 1) & 1, (c >> 2) & 1};
+        double sum = 0.0;
+        for (int a = 1; a <= 3; a++) {
+            const int b = (a == 1) ? 2 : 1, cc = (a == 3) ? 2 : 3;
+            sum += Ar[a] * (F[a][ix[a] + 1][ix[b]][ix[cc]] - F[a][ix[a]][ix[b]][ix[cc]]);
+        }
+        D[c] = sum;
+    }
+    // lambda = sum_{s != 0} (rho_s / mu_s) chi_s, rho_s = (1/8) sum_c chi_s(c) (-D_c)
+    double lam[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int sm = 1; sm < 8; sm++) {
+        double rho = 0.0;
+        for (int c = 0; c < 8; c++) rho -= (__popc(sm & c) & 1) ? -D[c] : D[c];
+        rho *= 0.125;
+        double mu = 0.0;
+        for (int a = 1; a <= 3; a++)
+            if (sm & (1 << (a - 1))) mu += 2.0 * Ar[a] * Ar[a];
+        const double coef = rho / mu;
+        for (int c = 0; c < 8; c++) lam[c] += (__popc(sm & c) & 1) ? -coef : coef;
+    }
+    const int b = (fd == 1) ? 2 : 1, cc = (fd == 3) ? 2 : 3;
+    const int tb = xi[b] > 0.0, tc = xi[cc] > 0.0;
+    int ix[4] = {0, 0, 0, 0};
+    ix[b] = tb;
+    ix[cc] = tc;
+    ix[fd] = 0;
+    const int clo = ix[1] + 2 * ix[2] + 4 * ix[3];
+    ix[fd] = 1;
+    const int chi = ix[1] + 2 * ix[2] + 4 * ix[3];
+    return F[fd][1][tb][tc] + Ar[fd] * (lam[clo] - lam[chi]);
+}
+
+// face field fd of a target face (cell size ht) at x from a source of the same or finer size
+__device__ inline double sample_face_plain(const DevBlock& N, const double x[4], const double ht[4], int fd) {
+    int i0[4], cnt[4];
+    double dl[4];
+    double xc[4] = {0.0, x[1], x[2], x[3]};
+    xc[fd] += 0.5 * ht[fd];
+    footprint(N, xc, ht, i0, cnt, dl);
+    const double pos = (x[fd] - N.lo[fd]) / N.h[fd];
+    int p0 = (int)floor(pos + 1e-9);
+    double fr = nearbyint(8.0 * (pos - p0)) / 8.0;
+    if (fr >= 1.0) {
+        p0 += 1;
+        fr = 0.0;
+    }
+    cnt[fd] = 1;
+    const double inv = 1.0 / (double)(cnt[1] * cnt[2] * cnt[3]);
+    const long st = (fd == 1) ? 1 : ((fd == 2) ? (long)N.v.n1p : (long)N.v.n1p * N.v.n2p);
+    const double* B = N.B + (long)(fd - 1) * N.v.nc;
+    double sum = 0.0;
+    for (int c3 = 0; c3 < cnt[3]; c3++)
+        for (int c2 = 0; c2 < cnt[2]; c2++)
+            for (int c1 = 0; c1 < cnt[1]; c1++) {
+                int jj[4] = {0, i0[1] + c1, i0[2] + c2, i0[3] + c3};
+                jj[fd] = p0;
+                const long c = pidx(N.v, jj[1], jj[2], jj[3]);
+                double q = B[c];
+                if (fr != 0.0) q = q + fr * (B[c + st] - q);
+                sum += q;
+            }
+    return sum * inv;
+}
+
+__global__ void k_regrid_faces(AmrDomain A, const DevBlock* ntab) {
+    const DevBlock& R = ntab[blockIdx.y];
+    const BlockView& v = R.v;
+    const long nf = (long)(v.n1 + 1) * (v.n2 + 1) * (v.n3 + 1);
+    const long tt = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tt >= 3 * nf) return;
+    const int fd = 1 + (int)(tt / nf);
+    const long t = tt % nf;
+    const int i = (int)(t % (v.n1 + 1)), j = (int)((t / (v.n1 + 1)) % (v.n2 + 1)),
+              k = (int)(t / ((long)(v.n1 + 1) * (v.n2 + 1)));
+    const int ii[4] = {0, i, j, k};
+    const int nn[4] = {0, v.n1, v.n2, v.n3};
+    for (int e = 1; e <= 3; e++)
+        if (e != fd && ii[e] >= nn[e]) return;  // only the block's own faces
+    double x[4] = {0.0, R.lo[1] + (i + 0.5) * R.h[1], R.lo[2] + (j + 0.5) * R.h[2], R.lo[3] + (k + 0.5) * R.h[3]};
+    x[fd] = R.lo[fd] + ii[fd] * R.h[fd];
+    double pl[4] = {0.0, x[1], x[2], x[3]}, pr[4] = {0.0, x[1], x[2], x[3]};
+    pl[fd] -= 0.25 * R.h[fd];
+    pr[fd] += 0.25 * R.h[fd];
+    wrap_domain(A, pl);
+    wrap_domain(A, pr);
+    const int nl = find_block(A, A.tab, pl), nr = find_block(A, A.tab, pr);
+    int n = nr;
+    bool left = false;
+    if (n < 0 || (nl >= 0 && A.tab[nl].h[1] < A.tab[nr].h[1] * (1.0 - 1e-9))) {
+        n = nl;
+        left = true;
+    }
+    if (n < 0) return;
+    const DevBlock& N = A.tab[n];
+    const double* probe = left ? pl : pr;
+    double xs[4] = {0.0, probe[1], probe[2], probe[3]};
+    xs[fd] += (left ? 0.25 : -0.25) * R.h[fd];
+    double val;
+    if (N.h[1] > R.h[1] * 1.5) {
+        int ic[4];
+        double xi[4];
+        coarse_cell(N, xs, probe, ic, xi);
+        val = (fabs(xi[fd]) > 0.5) ? balsara_poly(N, ic, xi, fd) : interior_fine_face(A, N, ic, xi, fd, R.h);
+    } else {
+        val = sample_face_plain(N, xs, R.h, fd);
+    }
+    R.B[(long)(fd - 1) * v.nc + pidx(v, i, j, k)] = val;
+}
+
 // ------------------------------------------------------------------ synchronisation
 struct SyncDev {  // SoA: dst block, field/face direction, dst index, source block, n <= 4 source indices
     const int *dst, *dir, *src, *n;
@@ -1263,6 +1537,25 @@ int amr_fill(AmrImpl* M, cudaStream_t s) {
     }
     AM_TRY(cudaGetLastError());
     return HAMR_OK;
+}
+
+int amr_regrid_fill(const AmrImpl* old, AmrImpl* M, cudaStream_t s) {
+    long maxc = 1, maxf = 1;
+    for (int b = 0; b < M->nb; b++) {
+        const BlockView& v = M->H.b[b].v;
+        maxc = std::max(maxc, (long)v.n1 * v.n2 * v.n3);
+        maxf = std::max(maxf, (long)(v.n1 + 1) * (v.n2 + 1) * (v.n3 + 1));
+    }
+    k_regrid_cells<<<dim3(nb_(maxc), M->nb), BSA, 0, s>>>(old->H.A, M->dtab);
+    k_regrid_faces<<<dim3(nb_(3 * maxf), M->nb), BSA, 0, s>>>(old->H.A, M->dtab);
+    AM_TRY(cudaGetLastError());
+    for (int b = 0; b < M->nb; b++) {
+        const DevBlock& D = M->H.b[b];
+        AM_TRY(launch_centre_b(D.v, D.P, D.B, s));
+        int rc = amr_after_load(M, b, s);
+        if (rc) return rc;
+    }
+    return amr_fill(M, s);
 }
 
 int amr_info(const AmrImpl* M, int* lmax, double* dtf_host) {

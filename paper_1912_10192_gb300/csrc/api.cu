@@ -534,6 +534,126 @@ int hamr_measure_fp64_peak(void* stream, double* gflops) {
     return HAMR_OK;
 }
 
+int hamr_grid_block_max(const hamr_grid* g, int field, double* out, void* stream) {
+    if (!g) return fail(HAMR_EINVAL, "grid is NULL");
+    if (!out) return fail(HAMR_EINVAL, "out is NULL");
+    if (field < 0 || field >= NPRIM) return fail(HAMR_EINVAL, "field %d out of range 0..7", field);
+    const int nb = (int)g->st.size();
+    unsigned long long* d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, sizeof(unsigned long long) * nb));
+    cudaStream_t cs = S(stream);
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long) * nb, cs);
+    for (int b = 0; b < nb && e == cudaSuccess; b++) e = launch_block_max(g->view[b], g->st[b].P, field, d + b, cs);
+    std::vector<unsigned long long> h(nb, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(HAMR_ECUDA, "block maximum failed: %s", cudaGetErrorString(e));
+    for (int b = 0; b < nb; b++) out[b] = ordered_to_double(h[b]);
+    return HAMR_OK;
+}
+
+int hamr_grid_regrid(hamr_grid* g, int nblocks, const hamr_block_desc* blocks, void* stream) {
+    if (!g) return fail(HAMR_EINVAL, "grid is NULL");
+    if (!g->amr) return fail(HAMR_EINVAL, "regridding needs a multi-block grid (nblocks >= 2 at creation)");
+    if (nblocks < 2 || !blocks) return fail(HAMR_EINVAL, "the new tree needs nblocks >= 2 and a block array");
+    for (size_t b = 0; b < g->loaded.size(); b++)
+        if (!g->loaded[b]) return fail(HAMR_ESTATE, "block %zu has no state", b);
+    hamr_grid_desc d = g->desc;
+    d.nblocks = nblocks;
+    d.blocks = blocks;
+    int rc = validate(&d);
+    if (rc) return rc;
+    // the same domain: the bounding boxes of the two trees agree
+    double lo0[3], hi0[3], lo1[3], hi1[3];
+    auto box = [](const hamr_block_desc* B, int n, double* lo, double* hi) {
+        for (int e = 0; e < 3; e++) {
+            lo[e] = 1e300;
+            hi[e] = -1e300;
+        }
+        for (int b = 0; b < n; b++) {
+            const double x0[3] = {B[b].x1min, B[b].x2min, B[b].x3min};
+            const double ext[3] = {B[b].n1 * B[b].dx1, B[b].n2 * B[b].dx2, B[b].n3 * B[b].dx3};
+            for (int e = 0; e < 3; e++) {
+                lo[e] = std::min(lo[e], x0[e]);
+                hi[e] = std::max(hi[e], x0[e] + ext[e]);
+            }
+        }
+    };
+    box(g->blocks.data(), (int)g->blocks.size(), lo0, hi0);
+    box(blocks, nblocks, lo1, hi1);
+    for (int e = 0; e < 3; e++) {
+        const double tol = 1e-9 * (hi0[e] - lo0[e]);
+        if (std::fabs(lo0[e] - lo1[e]) > tol || std::fabs(hi0[e] - hi1[e]) > tol)
+            return fail(HAMR_EINVAL, "the new tree covers another domain along x%d", e + 1);
+    }
+    // a region's cell size changes by at most a factor of 2 (the regrid's operators)
+    for (int nbk = 0; nbk < nblocks; nbk++) {
+        const hamr_block_desc& B = blocks[nbk];
+        const double bl[3] = {B.x1min, B.x2min, B.x3min};
+        const double bh[3] = {B.x1min + B.n1 * B.dx1, B.x2min + B.n2 * B.dx2, B.x3min + B.n3 * B.dx3};
+        for (const hamr_block_desc& Q : g->blocks) {
+            const double ql[3] = {Q.x1min, Q.x2min, Q.x3min};
+            const double qh[3] = {Q.x1min + Q.n1 * Q.dx1, Q.x2min + Q.n2 * Q.dx2, Q.x3min + Q.n3 * Q.dx3};
+            bool over = true;
+            for (int e = 0; e < 3 && over; e++) {
+                const double tol = 1e-9 * (hi0[e] - lo0[e]);
+                over = (bl[e] < qh[e] - tol) && (ql[e] < bh[e] - tol);
+            }
+            if (!over) continue;
+            const double r = Q.dx1 / B.dx1;
+            if (r > 2.0 * (1.0 + 1e-9) || r < 0.5 * (1.0 - 1e-9))
+                return fail(HAMR_EINVAL, "new block %d changes the cell size by more than 2x (use hamr_tree_adapt "
+                                         "steps of one level)", nbk);
+        }
+    }
+    hamr_grid* ng = new hamr_grid;
+    ng->desc = d;
+    ng->blocks.assign(blocks, blocks + nblocks);
+    ng->desc.blocks = ng->blocks.data();
+    ng->ph = g->ph;
+    ng->device = g->device;
+    for (int b = 0; b < nblocks; b++) {
+        rc = alloc_block(ng, b);
+        if (rc) {
+            free_grid(ng);
+            return rc;
+        }
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_grid(ng);
+        return fail(HAMR_ECUDA, "geometry build failed: %s", cudaGetErrorString(e));
+    }
+    rc = amr_create(&ng->amr, ng->desc, ng->view, ng->st, ng->ph);
+    if (rc) {
+        free_grid(ng);
+        return rc;
+    }
+    cudaStream_t cs = S(stream);
+    rc = amr_regrid_fill(g->amr, ng->amr, cs);
+    if (rc == HAMR_OK) {
+        e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) rc = fail(HAMR_ECUDA, "regridding failed: %s", cudaGetErrorString(e));
+    }
+    if (rc) {
+        free_grid(ng);
+        return rc;
+    }
+    ng->loaded.assign(nblocks, 1);
+    // the new tree takes the grid's place; the old one is freed with the temporary
+    std::swap(g->amr, ng->amr);
+    std::swap(g->blocks, ng->blocks);
+    std::swap(g->st, ng->st);
+    std::swap(g->view, ng->view);
+    std::swap(g->arena, ng->arena);
+    std::swap(g->loaded, ng->loaded);
+    g->desc.nblocks = nblocks;
+    g->desc.blocks = g->blocks.data();
+    free_grid(ng);
+    return HAMR_OK;
+}
+
 int hamr_grid_stats(const hamr_grid* g, hamr_step_stats* stats) {
     if (!g || !stats) return fail(HAMR_EINVAL, "grid and stats must not be NULL");
     CUDA_TRY(cudaDeviceSynchronize());

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "../../include/hamr.h"
@@ -71,6 +72,19 @@ __host__ __device__ inline long recon_threads(const BlockView& v, int dir, int f
     if (dir == 2) return n1 * n3 * ((n2 + seg - 1) / seg) * 7;
     return n1 * n2 * ((n3 + seg - 1) / seg) * 7;
 }
+// monotone map of (non-NaN) doubles to unsigned integers and back: maxima by atomicMax
+__host__ __device__ inline unsigned long long ordered_bits(double x) {
+    unsigned long long u;
+    memcpy(&u, &x, sizeof(u));
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__host__ __device__ inline double ordered_to_double(unsigned long long o) {
+    const unsigned long long u = (o >> 63) ? (o & 0x7fffffffffffffffull) : ~o;
+    double x;
+    memcpy(&x, &u, sizeof(x));
+    return x;
+}
+
 // the launch-shape defaults (what hamr_grid_autotune starts from)
 inline void default_launch_shapes(PhysArgs& ph) {
     ph.bs_recon = 128;
@@ -133,6 +147,8 @@ int set_error(int code, const char* fmt, ...);
 
 // step.cu
 cudaError_t launch_centre_b(const BlockView& v, double* P, const double* B, cudaStream_t s);
+// atomicMax of ordered_bits(P[q]) over the interior cells into *out (initialise to 0)
+cudaError_t launch_block_max(const BlockView& v, const double* P, int q, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_bc(const BlockView& v, double* P, double* B, cudaStream_t s);
 cudaError_t launch_recon(const BlockView& v, const PhysArgs& ph, int dir, const double* P, const float* P32,
                          double* QL, double* QR, cudaStream_t s);
@@ -214,6 +230,8 @@ int amr_period(AmrImpl* M, cudaStream_t s, int nperiods, bool use_graph);
 int amr_info(const AmrImpl* M, int* lmax, double* dtf_host);
 int amr_links(const AmrImpl* M, int* counts5);
 int amr_fill(AmrImpl* M, cudaStream_t s);
+// fills every block of M from the old tree at its current state (regridding)
+int amr_regrid_fill(const AmrImpl* old, AmrImpl* M, cudaStream_t s);
 int amr_set_phys(AmrImpl* M, const PhysArgs& ph);
 int amr_time_group(AmrImpl* M, const PhysArgs& ph, int which, cudaStream_t cs, float* ms);
 const uint8_t* mlp_image(const hamr_mlp* m);

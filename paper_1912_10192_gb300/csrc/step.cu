@@ -1078,7 +1078,28 @@ __global__ void k_reflux_cells(const DevBlock* tab, int n, const int* cblk, cons
     if (fl) atomicAdd(&D.dcnt[3], 1ull);
 }
 
+// maximum of field q over the interior cells, as ordered bits (ordered_bits)
+__global__ void k_block_max(BlockView v, const double* __restrict__ P, int q, unsigned long long* out) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long n = (long)v.n1 * v.n2 * v.n3;
+    unsigned long long m = 0ull;
+    if (t < n) {
+        const int i = (int)(t % v.n1), j = (int)((t / v.n1) % v.n2), k = (int)(t / ((long)v.n1 * v.n2));
+        m = ordered_bits(P[q * v.nc + cidx(v, i, j, k)]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long x = __shfl_down_sync(0xffffffffu, m, o);
+        m = x > m ? x : m;
+    }
+    if ((threadIdx.x & 31u) == 0 && m) atomicMax(out, m);
+}
+
 }  // namespace
+
+cudaError_t launch_block_max(const BlockView& v, const double* P, int q, unsigned long long* out, cudaStream_t s) {
+    k_block_max<<<nblk((long)v.n1 * v.n2 * v.n3), BS, 0, s>>>(v, P, q, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_centre_b(const BlockView& v, double* P, const double* B, cudaStream_t s) {
     k_centre_b<<<nblk((long)v.n1 * v.n2 * v.n3), BS, 0, s>>>(v, P, B);

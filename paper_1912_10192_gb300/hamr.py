@@ -108,6 +108,10 @@ def lib():
         L.hamr_con2prim.argtypes = [C.POINTER(C2PDesc), C.c_int64, P, P, P, P, P, P, P, P]
         L.hamr_grid_set_timing.argtypes = [P, C.c_int]
         L.hamr_grid_fill_ghosts.argtypes = [P, P]
+        L.hamr_grid_block_max.argtypes = [P, C.c_int, D, P]
+        L.hamr_grid_regrid.argtypes = [P, C.c_int, C.POINTER(BlockDesc), P]
+        L.hamr_tree_adapt.argtypes = [C.POINTER(BlockDesc), C.c_int, C.POINTER(C.c_int), D, D,
+                                      C.POINTER(C.c_int), C.POINTER(BlockDesc), C.c_int, C.POINTER(C.c_int)]
         L.hamr_grid_timing.argtypes = [P, C.POINTER(KernelTime), C.c_int, C.POINTER(C.c_int)]
         L.hamr_measure_fp64_peak.argtypes = [P, C.POINTER(C.c_double)]
         L.hamr_block_step_noalloc.argtypes = [C.POINTER(GridDesc), P, P, C.c_double, P]
@@ -166,6 +170,24 @@ def block(n1, n2, n3, x1min, x2min, x3min, dx1, dx2, dx3, bc, lat=0):
         b.bc[m] = bc[m]
     b.lat = lat
     return b
+
+
+def tree_adapt(blocks, target, dlo, base_ext, periodic=(1, 1, 1)):
+    """hamr_tree_adapt: the nested octree for per-block target levels -> list of BlockDesc."""
+    n = len(blocks)
+    arr = (BlockDesc * n)(*blocks)
+    tg = (C.c_int * n)(*[int(t) for t in target])
+    lo = (C.c_double * 3)(*dlo)
+    ext = (C.c_double * 3)(*base_ext)
+    per = (C.c_int * 3)(*[int(p) for p in periodic])
+    nout = C.c_int()
+    rc = lib().hamr_tree_adapt(arr, n, tg, lo, ext, per, None, 0, C.byref(nout))
+    cap = nout.value
+    if rc != 0 and cap <= 0:
+        check(rc)
+    out = (BlockDesc * cap)()
+    check(lib().hamr_tree_adapt(arr, n, tg, lo, ext, per, out, cap, C.byref(nout)))
+    return [out[i] for i in range(nout.value)]
 
 
 def block_from_dict(b):
@@ -237,6 +259,20 @@ class Grid:
 
     def fill_ghosts(self, stream=None):
         check(lib().hamr_grid_fill_ghosts(self.h, _stream(stream)))
+
+    def block_max(self, field=0, stream=None):
+        """Maximum of primitive `field` over each block's interior cells (numpy array, one per block)."""
+        out = np.zeros(len(self.blocks))
+        check(lib().hamr_grid_block_max(self.h, int(field), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                        _stream(stream)))
+        return out
+
+    def regrid(self, blocks, stream=None):
+        """Replaces the block tree by `blocks` (BlockDesc list), the state carried over."""
+        arr = (BlockDesc * len(blocks))(*blocks)
+        check(lib().hamr_grid_regrid(self.h, len(blocks), arr, _stream(stream)))
+        self._blocks = arr
+        self.blocks = list(blocks)
 
     def set_timing(self, enable):
         check(lib().hamr_grid_set_timing(self.h, int(bool(enable))))
