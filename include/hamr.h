@@ -192,6 +192,14 @@ int hamr_grid_fill_ghosts(hamr_grid* g, void* stream);
 /* Reads the accumulated counters of the last step; synchronises the device. */
 int hamr_grid_stats(const hamr_grid* g, hamr_step_stats* stats);
 
+/* Multi-block grids: the fine time step dt_fine (> 0) of every following
+ * hamr_batch_step period (a block of LAT level L steps with 2^L dt_fine), or
+ * the CFL step of each period (dt_fine <= 0, the default). Kept across
+ * hamr_grid_regrid. For runs that must end at a given time (the convergence
+ * tests); the caller keeps dt_fine within the CFL limit. Synchronises the
+ * device. HAMR_EINVAL on a single-block grid (it takes dt per step). */
+int hamr_grid_set_fine_dt(hamr_grid* g, double dt_fine);
+
 /* ---- dynamic refinement (Sec. 3.2: (de)refinement, nesting, prolongation
  * and restriction) ---- */
 

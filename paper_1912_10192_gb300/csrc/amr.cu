@@ -677,12 +677,17 @@ __global__ void k_period_begin(const DevBlock* tab, int nb) {
     for (int q = 0; q < 5; q++) tab[b].dcnt[q] = 0ull;
 }
 
+// dtf_out[1] > 0: the caller's fine dt (hamr_grid_set_fine_dt), else the CFL dt of the blocks' rates
 __global__ void k_period_dt(const DevBlock* tab, int nb, double cour, double* dtf_out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double dtf = 1e300;
-    for (int b = 0; b < nb; b++) {
-        const double rate = __longlong_as_double((long long)tab[b].dmax[0]);
-        dtf = fmin(dtf, cour / rate / (double)(1 << tab[b].lat));
+    if (dtf_out[1] > 0.0) {
+        dtf = dtf_out[1];
+    } else {
+        for (int b = 0; b < nb; b++) {
+            const double rate = __longlong_as_double((long long)tab[b].dmax[0]);
+            dtf = fmin(dtf, cour / rate / (double)(1 << tab[b].lat));
+        }
     }
     for (int b = 0; b < nb; b++) tab[b].dscal[0] = dtf * (double)(1 << tab[b].lat);
     dtf_out[0] = dtf;
@@ -1556,6 +1561,12 @@ int amr_regrid_fill(const AmrImpl* old, AmrImpl* M, cudaStream_t s) {
         if (rc) return rc;
     }
     return amr_fill(M, s);
+}
+
+int amr_set_fine_dt(AmrImpl* M, double dt) {
+    const double v = dt > 0.0 ? dt : 0.0;
+    AM_TRY(cudaMemcpy(M->dtf + 1, &v, sizeof(double), cudaMemcpyHostToDevice));
+    return HAMR_OK;
 }
 
 int amr_info(const AmrImpl* M, int* lmax, double* dtf_host) {

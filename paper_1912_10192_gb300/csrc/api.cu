@@ -132,6 +132,7 @@ struct hamr_grid {
     std::vector<int> loaded;
     PhysArgs ph;
     int device;
+    double fine_dt = 0.0;  // hamr_grid_set_fine_dt (<= 0: CFL)
 };
 
 namespace {
@@ -534,6 +535,17 @@ int hamr_measure_fp64_peak(void* stream, double* gflops) {
     return HAMR_OK;
 }
 
+int hamr_grid_set_fine_dt(hamr_grid* g, double dt_fine) {
+    if (!g) return fail(HAMR_EINVAL, "grid is NULL");
+    if (!g->amr) return fail(HAMR_EINVAL, "a single-block grid takes dt in each hamr_block_step call");
+    if (!std::isfinite(dt_fine)) return fail(HAMR_EINVAL, "dt_fine must be finite");
+    CUDA_TRY(cudaDeviceSynchronize());
+    int rc = amr_set_fine_dt(g->amr, dt_fine);
+    if (rc) return rc;
+    g->fine_dt = dt_fine > 0.0 ? dt_fine : 0.0;
+    return HAMR_OK;
+}
+
 int hamr_grid_block_max(const hamr_grid* g, int field, double* out, void* stream) {
     if (!g) return fail(HAMR_EINVAL, "grid is NULL");
     if (!out) return fail(HAMR_EINVAL, "out is NULL");
@@ -640,6 +652,14 @@ int hamr_grid_regrid(hamr_grid* g, int nblocks, const hamr_block_desc* blocks, v
         free_grid(ng);
         return rc;
     }
+    if (g->fine_dt > 0.0) {
+        rc = amr_set_fine_dt(ng->amr, g->fine_dt);
+        if (rc) {
+            free_grid(ng);
+            return rc;
+        }
+    }
+    ng->fine_dt = g->fine_dt;
     ng->loaded.assign(nblocks, 1);
     // the new tree takes the grid's place; the old one is freed with the temporary
     std::swap(g->amr, ng->amr);

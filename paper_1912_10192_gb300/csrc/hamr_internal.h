@@ -232,6 +232,8 @@ int amr_links(const AmrImpl* M, int* counts5);
 int amr_fill(AmrImpl* M, cudaStream_t s);
 // fills every block of M from the old tree at its current state (regridding)
 int amr_regrid_fill(const AmrImpl* old, AmrImpl* M, cudaStream_t s);
+// fine dt of every following period (<= 0: the CFL dt); read on the device, no graph rebuild
+int amr_set_fine_dt(AmrImpl* M, double dt);
 int amr_set_phys(AmrImpl* M, const PhysArgs& ph);
 int amr_time_group(AmrImpl* M, const PhysArgs& ph, int which, cudaStream_t cs, float* ms);
 const uint8_t* mlp_image(const hamr_mlp* m);

@@ -109,6 +109,7 @@ def lib():
         L.hamr_grid_set_timing.argtypes = [P, C.c_int]
         L.hamr_grid_fill_ghosts.argtypes = [P, P]
         L.hamr_grid_block_max.argtypes = [P, C.c_int, D, P]
+        L.hamr_grid_set_fine_dt.argtypes = [P, C.c_double]
         L.hamr_grid_regrid.argtypes = [P, C.c_int, C.POINTER(BlockDesc), P]
         L.hamr_tree_adapt.argtypes = [C.POINTER(BlockDesc), C.c_int, C.POINTER(C.c_int), D, D,
                                       C.POINTER(C.c_int), C.POINTER(BlockDesc), C.c_int, C.POINTER(C.c_int)]
@@ -259,6 +260,10 @@ class Grid:
 
     def fill_ghosts(self, stream=None):
         check(lib().hamr_grid_fill_ghosts(self.h, _stream(stream)))
+
+    def set_fine_dt(self, dt_fine):
+        """Fixed fine dt of the batched periods (<= 0: the CFL dt)."""
+        check(lib().hamr_grid_set_fine_dt(self.h, float(dt_fine)))
 
     def block_max(self, field=0, stream=None):
         """Maximum of primitive `field` over each block's interior cells (numpy array, one per block)."""

@@ -879,3 +879,74 @@ def riemann_block(n1, left, right, n2=4, n3=4, x0=0.5, gam=5.0 / 3.0):
                                 (left[2] / math.sqrt(1.0 - left[2] ** 2), right[2] / math.sqrt(1.0 - right[2] ** 2))]):
         prim[q][...] = np.where(on_left, a, b)[None, None, :]
     return prim, np.zeros((3,) + shp)
+
+
+def _edge_integral(c, k, h, phase):
+    """Integral over s in [0, h] of c cos(phase + k s)."""
+    if abs(k * h) < 1e-12:
+        return c * h * np.cos(phase)
+    return c * (np.sin(phase + k * h) - np.sin(phase)) / k
+
+
+def linear_wave_states(blocks, rho0, p0, B0, kvec, R, r, amp, gam=5.0 / 3.0):
+    """A plane linear wave on flat-space blocks: background rho0, p0 at rest with uniform field B0
+    (3-vector), perturbation amp * r * sin(k.x) where r is a given eigenvector in the wave's frame,
+    r = (drho, dp, dv_par, dv_perp1, dv_perp2, dB_perp1, dB_perp2), and R the rotation whose
+    columns are the wave frame's axes (R[:, 0] = k / |k|) in grid coordinates. Face B is B0 plus the
+    face average of the curl of the vector potential (k x b) / |k|^2 cos(k.x), b = amp R (0, dB1, dB2),
+    taken from exact edge integrals (divergence-free, and a coarse face's flux is the sum of its fine
+    faces'). Returns [(prim, bface)] per block (padded; ghosts left for the library)."""
+    kvec = np.asarray(kvec, dtype=float)
+    k2 = kvec @ kvec
+    b = amp * (R @ np.array([0.0, r[5], r[6]]))
+    cvec = np.cross(kvec, b) / k2
+    dv = amp * (R @ np.array([r[2], r[3], r[4]]))
+    out = []
+    for blk in blocks:
+        n1, n2, n3 = blk["n1"], blk["n2"], blk["n3"]
+        h = (blk["dx1"], blk["dx2"], blk["dx3"])
+        lo = (blk["x1min"], blk["x2min"], blk["x3min"])
+        shp = (n3 + 2 * NG, n2 + 2 * NG, n1 + 2 * NG)
+        prim = np.zeros((8,) + shp)
+        bf = np.zeros((3,) + shp)
+        x = _centres(lo[0], h[0], n1)
+        y = _centres(lo[1], h[1], n2)
+        z = _centres(lo[2], h[2], n3)
+        Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+        sn = np.sin(kvec[0] * X + kvec[1] * Y + kvec[2] * Z)
+        s = (slice(NG, NG + n3), slice(NG, NG + n2), slice(NG, NG + n1))
+        prim[0][s] = rho0 + amp * r[0] * sn
+        prim[1][s] = (p0 + amp * r[1] * sn) / (gam - 1.0)
+        v = [dv[d] * sn for d in range(3)]
+        lor = 1.0 / np.sqrt(1.0 - (v[0] ** 2 + v[1] ** 2 + v[2] ** 2))
+        for d in range(3):
+            prim[2 + d][s] = lor * v[d]
+        xe = _edges(lo[0], h[0], n1)
+        ye = _edges(lo[1], h[1], n2)
+        ze = _edges(lo[2], h[2], n3)
+        # x1 faces: circulation of A around (y0..y0+hy) x (z0..z0+hz) at x = xe
+        Zc, Yc, Xe = np.meshgrid(ze[:-1], ye[:-1], xe, indexing="ij")
+        ph = kvec[0] * Xe + kvec[1] * Yc + kvec[2] * Zc
+        Iy0 = _edge_integral(cvec[1], kvec[1], h[1], ph)
+        Iy1 = _edge_integral(cvec[1], kvec[1], h[1], ph + kvec[2] * h[2])
+        Iz0 = _edge_integral(cvec[2], kvec[2], h[2], ph)
+        Iz1 = _edge_integral(cvec[2], kvec[2], h[2], ph + kvec[1] * h[1])
+        bf[0][NG:NG + n3, NG:NG + n2, NG:NG + n1 + 1] = B0[0] + ((Iy0 - Iy1) + (Iz1 - Iz0)) / (h[1] * h[2])
+        # x2 faces: (z, x) circulation at y = ye: B2 = dA1/dz - dA3/dx
+        Zc, Ye, Xc = np.meshgrid(ze[:-1], ye, xe[:-1], indexing="ij")
+        ph = kvec[0] * Xc + kvec[1] * Ye + kvec[2] * Zc
+        Iz0 = _edge_integral(cvec[2], kvec[2], h[2], ph)
+        Iz1 = _edge_integral(cvec[2], kvec[2], h[2], ph + kvec[0] * h[0])
+        Ix0 = _edge_integral(cvec[0], kvec[0], h[0], ph)
+        Ix1 = _edge_integral(cvec[0], kvec[0], h[0], ph + kvec[2] * h[2])
+        bf[1][NG:NG + n3, NG:NG + n2 + 1, NG:NG + n1] = B0[1] + ((Iz0 - Iz1) + (Ix1 - Ix0)) / (h[2] * h[0])
+        # x3 faces: (x, y) circulation at z = ze: B3 = dA2/dx - dA1/dy
+        Ze, Yc, Xc = np.meshgrid(ze, ye[:-1], xe[:-1], indexing="ij")
+        ph = kvec[0] * Xc + kvec[1] * Yc + kvec[2] * Ze
+        Ix0 = _edge_integral(cvec[0], kvec[0], h[0], ph)
+        Ix1 = _edge_integral(cvec[0], kvec[0], h[0], ph + kvec[1] * h[1])
+        Iy0 = _edge_integral(cvec[1], kvec[1], h[1], ph)
+        Iy1 = _edge_integral(cvec[1], kvec[1], h[1], ph + kvec[0] * h[0])
+        bf[2][NG:NG + n3 + 1, NG:NG + n2, NG:NG + n1] = B0[2] + ((Ix0 - Ix1) + (Iy1 - Iy0)) / (h[0] * h[1])
+        out.append((prim, bf))
+    return out
