@@ -15,6 +15,7 @@ NG = 3
 BC_OUTFLOW, BC_PERIODIC, BC_POLAR, BC_OUTFLOW_NOINFLOW = 0, 1, 2, 3
 METRIC_KS, METRIC_MINKOWSKI = 0, 1
 RECON_PPM, RECON_MC, RECON_MINMOD = 0, 1, 2
+METRIC_SPHERICAL = 2  # flat space in log-r spherical coordinates
 FLUX_HLL, FLUX_LLF = 0, 1
 EMF_AVERAGE, EMF_UPWIND = 0, 1
 INV_NEWTON, INV_AITKEN = 0, 1

@@ -105,14 +105,16 @@ static void metric_point(const ora_desc& d, double x1, double x2, double gcov[4]
         *gdet = 1.0;
         return;
     }
-    const double a = d.a;
+    /* flat spherical coordinates: the same form with mass 0 and no spin */
+    const double mass = (d.metric == ORA_METRIC_SPHERICAL) ? 0.0 : 1.0;
+    const double a = (d.metric == ORA_METRIC_SPHERICAL) ? 0.0 : d.a;
     const double r = std::exp(x1);
     const double th = mirror_theta(x2);
     const double sth = std::sin(th), cth = std::cos(th);
     const double s2 = sth * sth;
     const double sig = r * r + a * a * cth * cth;
-    const double del = r * r - 2.0 * r + a * a;
-    const double z = 2.0 * r / sig;
+    const double del = r * r - 2.0 * mass * r + a * a;
+    const double z = 2.0 * mass * r / sig;
     /* covariant KS: g_tt, g_tr, g_tphi, g_rr, g_rphi, g_thth, g_phph */
     gcov[0][0] = -(1.0 - z);
     gcov[0][1] = gcov[1][0] = z * r;
@@ -841,7 +843,7 @@ void build_geometry(ora_grid* g) {
             double cn[4][4][4];
             conn_point(d, x1c, x2c, cn);
             std::memcpy(&g->conn[q * 64], cn, sizeof(cn));
-            g->rc[q] = (d.metric == ORA_METRIC_KS) ? std::exp(x1c) : 1.0;
+            g->rc[q] = (d.metric != ORA_METRIC_MINKOWSKI) ? std::exp(x1c) : 1.0;
         }
 }
 

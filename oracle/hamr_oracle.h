@@ -19,7 +19,9 @@ extern "C" {
 #endif
 
 enum { ORA_BC_OUTFLOW = 0, ORA_BC_PERIODIC = 1, ORA_BC_POLAR = 2, ORA_BC_OUTFLOW_NOINFLOW = 3, ORA_BC_BLOCK = 4 };
-enum { ORA_METRIC_KS = 0, ORA_METRIC_MINKOWSKI = 1 };
+/* ORA_METRIC_SPHERICAL: flat space in the same log-r spherical coordinates
+ * (the Kerr-Schild form with the mass set to 0 and a = 0) */
+enum { ORA_METRIC_KS = 0, ORA_METRIC_MINKOWSKI = 1, ORA_METRIC_SPHERICAL = 2 };
 enum { ORA_RECON_PPM = 0, ORA_RECON_MC = 1, ORA_RECON_MINMOD = 2 };
 enum { ORA_FLUX_HLL = 0, ORA_FLUX_LLF = 1 };
 enum { ORA_EMF_AVERAGE = 0, ORA_EMF_UPWIND = 1 };
