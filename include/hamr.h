@@ -58,6 +58,7 @@ extern "C" {
 /* ---- option enums ---- */
 #define HAMR_METRIC_KS 0        /* Kerr metric, Kerr-Schild, log-r spherical (Sec. 2.2) */
 #define HAMR_METRIC_MINKOWSKI 1 /* flat space, Cartesian (validation problems) */
+#define HAMR_METRIC_SPHERICAL 2 /* flat space in the log-r spherical coordinates of HAMR_METRIC_KS (a ignored) */
 #define HAMR_RECON_PPM 0        /* piecewise parabolic (Sec. 2.1) */
 #define HAMR_RECON_MC 1         /* monotonised-central linear */
 #define HAMR_RECON_MINMOD 2     /* minmod linear */

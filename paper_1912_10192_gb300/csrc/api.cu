@@ -140,7 +140,7 @@ namespace {
 int validate(const hamr_grid_desc* d) {
     if (!d) return fail(HAMR_EINVAL, "descriptor is NULL");
     if (d->nblocks < 1 || !d->blocks) return fail(HAMR_EINVAL, "nblocks must be >= 1 with a block array");
-    if (d->metric != HAMR_METRIC_KS && d->metric != HAMR_METRIC_MINKOWSKI)
+    if (d->metric != HAMR_METRIC_KS && d->metric != HAMR_METRIC_MINKOWSKI && d->metric != HAMR_METRIC_SPHERICAL)
         return fail(HAMR_EINVAL, "unknown metric %d", d->metric);
     if (d->metric == HAMR_METRIC_KS && !(std::fabs(d->a) < 1.0)) return fail(HAMR_EINVAL, "spin must satisfy |a| < 1");
     if (!(d->gam > 1.0 && d->gam <= 2.0)) return fail(HAMR_EINVAL, "gam must be in (1, 2]");
@@ -170,8 +170,8 @@ int validate(const hamr_grid_desc* d) {
             if (bc == HAMR_BC_OUTFLOW_NOINFLOW && (f / 2) != 0)
                 return fail(HAMR_EINVAL, "block %d: noinflow bc only on x1", b);
             if (bc == HAMR_BC_POLAR && (B.n3 % 2) != 0) return fail(HAMR_EINVAL, "block %d: polar bc needs even n3", b);
-            if (bc == HAMR_BC_POLAR && d->metric != HAMR_METRIC_KS)
-                return fail(HAMR_EINVAL, "block %d: polar bc needs the KS metric", b);
+            if (bc == HAMR_BC_POLAR && d->metric == HAMR_METRIC_MINKOWSKI)
+                return fail(HAMR_EINVAL, "block %d: polar bc needs spherical coordinates (KS or SPHERICAL)", b);
         }
         if (!multi && ((B.bc[0] == HAMR_BC_PERIODIC) != (B.bc[1] == HAMR_BC_PERIODIC) ||
                        (B.bc[2] == HAMR_BC_PERIODIC) != (B.bc[3] == HAMR_BC_PERIODIC) ||
@@ -713,7 +713,7 @@ int hamr_con2prim(const hamr_c2p_desc* d, int64_t n, const double* U, const doub
     if (n < 0) return fail(HAMR_EINVAL, "n must be >= 0");
     if (n == 0) return HAMR_OK;
     if (!U || !B || !x1 || !x2 || !prim || !status) return fail(HAMR_EINVAL, "array argument is NULL");
-    if (d->metric != HAMR_METRIC_KS && d->metric != HAMR_METRIC_MINKOWSKI)
+    if (d->metric != HAMR_METRIC_KS && d->metric != HAMR_METRIC_MINKOWSKI && d->metric != HAMR_METRIC_SPHERICAL)
         return fail(HAMR_EINVAL, "unknown metric %d", d->metric);
     if (!(d->gam > 1.0 && d->gam <= 2.0)) return fail(HAMR_EINVAL, "gam must be in (1, 2]");
     if (d->flags & ~(HAMR_C2P_ENTROPY_ONLY | HAMR_C2P_MLP | HAMR_C2P_MLP_RESCUE | HAMR_C2P_AITKEN))

@@ -51,7 +51,7 @@ __global__ void k_geometry(GeomArgs A) {
     double dg[3][4][4];  // d/dx1, d/dx2 (index 1, 2); index 0 unused
     for (int m = 0; m < 4; m++)
         for (int n = 0; n < 4; n++) dg[0][m][n] = dg[1][m][n] = dg[2][m][n] = 0.0;
-    if (A.metric == 0) {
+    if (A.metric != HAMR_METRIC_MINKOWSKI) {
         for (int s = 1; s <= 2; s++) {
             const double e1 = (s == 1) ? CONN_H : 0.0, e2 = (s == 2) ? CONN_H : 0.0;
             FullMetric p2, p1, m1, m2;
@@ -77,7 +77,7 @@ __global__ void k_geometry(GeomArgs A) {
                 }
                 A.centre[(C_CONN + l * 10 + sym(m, n)) * n2d + q] = 0.5 * s;
             }
-    const double r = (A.metric == 0) ? exp(x1c) : 1.0;
+    const double r = (A.metric != HAMR_METRIC_MINKOWSKI) ? exp(x1c) : 1.0;
     A.centre[C_RHOFLR * n2d + q] = 1.0e-7 / (r * r);
     A.centre[C_UFLR * n2d + q] = 1.0e-9 * pow(r, -10.0 / 3.0);
 

@@ -1,6 +1,7 @@
 // metric.cuh -- the Kerr metric in Kerr-Schild coordinates carried to the
 // internal coordinates x1 = log r, x2 = theta, x3 = phi (Liska et al. 2019,
-// Sec. 2.2), evaluated analytically on the device; flat space as option 1.
+// Sec. 2.2), evaluated analytically on the device; flat space in Cartesian
+// coordinates as option 1, in the same spherical coordinates as option 2.
 #pragma once
 #include "grmhd.cuh"
 
@@ -28,6 +29,9 @@ __device__ inline void metric_at(int metric, double a, double x1, double x2, Ful
         M.gdet = 1.0;
         return;
     }
+    // metric 2: flat space in the same coordinates (mass 0, no spin)
+    const double mass = (metric == 2) ? 0.0 : 1.0;
+    if (metric == 2) a = 0.0;
     const double r = exp(x1);
     const double th = mirror_theta(x2);
     double sth, cth;
@@ -35,7 +39,7 @@ __device__ inline void metric_at(int metric, double a, double x1, double x2, Ful
     const double s2 = sth * sth;
     const double r2 = r * r;
     const double sig = r2 + a * a * cth * cth;
-    const double z = 2.0 * r / sig;  // 2r / Sigma
+    const double z = 2.0 * mass * r / sig;  // 2Mr / Sigma
     M.g[0][0] = z - 1.0;
     M.g[0][1] = M.g[1][0] = z * r;
     M.g[0][3] = M.g[3][0] = -z * a * s2;
@@ -45,7 +49,7 @@ __device__ inline void metric_at(int metric, double a, double x1, double x2, Ful
     M.g[3][3] = s2 * (sig + (1.0 + z) * a * a * s2);
     M.gi[0][0] = -(1.0 + z);
     M.gi[0][1] = M.gi[1][0] = z / r;
-    M.gi[1][1] = (r2 - 2.0 * r + a * a) / (sig * r2);
+    M.gi[1][1] = (r2 - 2.0 * mass * r + a * a) / (sig * r2);
     M.gi[1][3] = M.gi[3][1] = a / (sig * r);
     M.gi[2][2] = 1.0 / sig;
     M.gi[3][3] = 1.0 / (sig * s2);

@@ -77,7 +77,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
                          B.n1, B.n2, B.n3, NA_CELLS, NA_PLANE);
     for (int f = 0; f < 6; f++)
         if (B.bc[f] < 0 || B.bc[f] > 3) return set_error(HAMR_EINVAL, "unknown bc %d", B.bc[f]);
-    if ((B.bc[2] == HAMR_BC_POLAR || B.bc[3] == HAMR_BC_POLAR) && (B.n3 % 2 != 0 || d->metric != HAMR_METRIC_KS))
+    if ((B.bc[2] == HAMR_BC_POLAR || B.bc[3] == HAMR_BC_POLAR) && (B.n3 % 2 != 0 || d->metric == HAMR_METRIC_MINKOWSKI))
         return set_error(HAMR_EINVAL, "polar bc needs even n3 and the KS metric");
     if (d->precision != HAMR_PREC_FP64) return set_error(HAMR_EINVAL, "the no-allocation step is FP64 only");
     if (d->emf != HAMR_EMF_AVERAGE && d->emf != HAMR_EMF_UPWIND) return set_error(HAMR_EINVAL, "unknown emf %d", d->emf);

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libhamr.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "hamr.h")
 
 OK, EINVAL, ECUDA, ENOMEM, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
-METRIC_KS, METRIC_MINKOWSKI = 0, 1
+METRIC_KS, METRIC_MINKOWSKI, METRIC_SPHERICAL = 0, 1, 2
 RECON_PPM, RECON_MC, RECON_MINMOD = 0, 1, 2
 FLUX_HLL, FLUX_LLF = 0, 1
 BC_OUTFLOW, BC_PERIODIC, BC_POLAR, BC_OUTFLOW_NOINFLOW, BC_BLOCK = 0, 1, 2, 3, 4
