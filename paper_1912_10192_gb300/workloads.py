@@ -536,17 +536,14 @@ def assign_lat_levels(blocks, lmax=3, period3=2.0 * math.pi):
     return blocks
 
 
-def amr_torus_tree(rin=1.2, rout=50.0, n=32):
-    """512 blocks over r in [rin, rout] (log), theta in [0, pi], phi in [0, 2 pi):
-    a base of 8 x 4 x 4 blocks, n^3 cells near the equator and n x n x n/2 within
-    45 degrees of the poles (phi derefined, external SMR, Sec. 3.3.1); base
-    blocks at r index 2..5 are refined: equatorial ones into 8 octants of n^3
-    cells, polar ones 6-way (Sec. 3.3.1: 4 octants refined in every direction
-    and the 2 children on the axis refined in r and theta only), all n x n x n/2.
-    13,107,200 cells; effective finest grid 512 x 256 x 256. LAT levels from
-    assign_lat_levels."""
+def polar_smr_tree(rin, rout, nb=(8, 4, 4), n=32, refine_ib=range(2, 6), lmax=3):
+    """Blocks over r in [rin, rout] (log), theta in [0, pi], phi in [0, 2 pi): a base of
+    nb blocks, n^3 cells near the equator and n x n x n/2 within pi/nb[1] of the poles (phi
+    derefined, external SMR, Sec. 3.3.1); base blocks at the radial indices refine_ib are refined:
+    equatorial ones into 8 octants of n^3 cells, polar ones 6-way (Sec. 3.3.1: 4 octants refined in
+    every direction and the 2 children on the axis refined in r and theta only), all n x n x n/2.
+    LAT levels from assign_lat_levels (at most lmax)."""
     x1a, x1b = math.log(rin), math.log(rout)
-    nb = (8, 4, 4)
     hb = ((x1b - x1a) / nb[0], math.pi / nb[1], 2.0 * math.pi / nb[2])
     blocks = []
 
@@ -561,7 +558,7 @@ def amr_torus_tree(rin=1.2, rout=50.0, n=32):
                 lo = (x1a + ib * hb[0], jb * hb[1], kb * hb[2])
                 polar = jb in (0, nb[1] - 1)
                 cells = (n, n, n // 2) if polar else (n, n, n)
-                if not (2 <= ib <= 5):
+                if ib not in refine_ib:
                     add(lo, hb, cells)
                     continue
                 half = (hb[0] / 2, hb[1] / 2, hb[2] / 2)
@@ -575,7 +572,83 @@ def amr_torus_tree(rin=1.2, rout=50.0, n=32):
                             for kc in range(2):
                                 add((clo[0], clo[1], lo[2] + kc * half[2]), half, cells)
     _mark_block_faces(blocks, periodic=(False, False, True))
-    return assign_lat_levels(blocks)
+    return assign_lat_levels(blocks, lmax=lmax)
+
+
+def amr_torus_tree(rin=1.2, rout=50.0, n=32):
+    """512 blocks: polar_smr_tree with a base of 8 x 4 x 4 blocks and the base blocks at r index
+    2..5 refined. 13,107,200 cells; effective finest grid 512 x 256 x 256."""
+    return polar_smr_tree(rin, rout, (8, 4, 4), n, range(2, 6))
+
+
+def _softplus(x):
+    return np.where(x > 30.0, x, np.log1p(np.exp(np.minimum(x, 30.0))))
+
+
+def explosion_blocks(blocks, centre=(3.0, 0.0, 10.0), rs=2.0, rho=1e-4, p_in=3e-5, p_out=3e-8, width=0.1,
+                     beta_max=None, gam=5.0 / 3.0, nquad=16):
+    """An off-centre explosion in flat space on log-r spherical blocks (Sec. 6): density rho
+    everywhere, pressure p_in inside the sphere of radius rs about the Cartesian point `centre` and
+    p_out outside, joined by p_out + (p_in - p_out) / (1 + exp((d - rs) / (width rs))) (the smoothed
+    edge; the ambient pressure is not given, p_out is this stand-in's choice), at rest. With
+    beta_max, a field from the vector potential A_phi = c w rs ln(1 + exp((rs - d) / (w rs))) (the
+    (rs - d) profile inside, 0 outside, with a smooth edge), its face fluxes from Gauss-Legendre
+    integrals of A_phi along the phi-edges (divergence-free; a coarse edge integral is the sum of its
+    fine ones to rounding), c set so that max p_gas / max p_mag = beta_max over the cells (flat
+    space at rest: b^2 = r^2 (B^1)^2 + r^2 (B^2)^2, B^i = Bbar^i / (r^3 sin theta)). Returns padded
+    (prim, bface) per block."""
+    x0 = np.asarray(centre, dtype=float)
+    gl_x, gl_w = np.polynomial.legendre.leggauss(nquad)
+
+    def dist(r, th, ph):
+        return np.sqrt((r * np.sin(th) * np.cos(ph) - x0[0]) ** 2 + (r * np.sin(th) * np.sin(ph) - x0[1]) ** 2
+                       + (r * np.cos(th) - x0[2]) ** 2)
+
+    out = []
+    for b in blocks:
+        n1, n2, n3 = b["n1"], b["n2"], b["n3"]
+        shp = (n3 + 2 * NG, n2 + 2 * NG, n1 + 2 * NG)
+        prim = np.zeros((8,) + shp)
+        bf = np.zeros((3,) + shp)
+        x1 = _centres(b["x1min"], b["dx1"], n1)
+        x2 = _centres(b["x2min"], b["dx2"], n2)
+        x3 = _centres(b["x3min"], b["dx3"], n3)
+        P3, T2, R1 = np.meshgrid(x3, x2, np.exp(x1), indexing="ij")
+        d = dist(R1, T2, P3)
+        s = (slice(NG, NG + n3), slice(NG, NG + n2), slice(NG, NG + n1))
+        prim[0][s] = rho
+        prim[1][s] = (p_out + (p_in - p_out) / (1.0 + np.exp(np.minimum((d - rs) / (width * rs), 50.0)))) / (gam - 1.0)
+        if beta_max is not None:
+            # integrals of A_phi (unit c) along the phi-edges at the (x1, x2) corners
+            xe1 = _edges(b["x1min"], b["dx1"], n1)
+            xe2 = _edges(b["x2min"], b["dx2"], n2)
+            I = np.zeros((n3, n2 + 1, n1 + 1))
+            for k in range(n3):
+                ph = b["x3min"] + (k + 0.5 + 0.5 * gl_x) * b["dx3"]
+                E2, E1, PH = np.meshgrid(xe2, np.exp(xe1), ph, indexing="ij")
+                dd = dist(E1, E2, PH)
+                A = width * rs * _softplus((rs - dd) / (width * rs))
+                I[k] = (A * (0.5 * b["dx3"] * gl_w)).sum(axis=2)
+            bf[0][NG:NG + n3, NG:NG + n2, NG:NG + n1 + 1] = (I[:, 1:, :] - I[:, :-1, :]) / (b["dx2"] * b["dx3"])
+            bf[1][NG:NG + n3, NG:NG + n2 + 1, NG:NG + n1] = -(I[:, :, 1:] - I[:, :, :-1]) / (b["dx1"] * b["dx3"])
+        out.append((prim, bf))
+    if beta_max is not None:
+        pg, pb = 0.0, 0.0
+        for b, (prim, bf) in zip(blocks, out):
+            n1, n2, n3 = b["n1"], b["n2"], b["n3"]
+            x1 = _centres(b["x1min"], b["dx1"], n1)
+            x2 = _centres(b["x2min"], b["dx2"], n2)
+            T2, R1 = np.meshgrid(x2, np.exp(x1), indexing="ij")
+            gdet = R1 ** 3 * np.abs(np.sin(T2))
+            b1 = 0.5 * (bf[0][NG:NG + n3, NG:NG + n2, NG:NG + n1] + bf[0][NG:NG + n3, NG:NG + n2, NG + 1:NG + n1 + 1])
+            b2 = 0.5 * (bf[1][NG:NG + n3, NG:NG + n2, NG:NG + n1] + bf[1][NG:NG + n3, NG + 1:NG + n2 + 1, NG:NG + n1])
+            bsq = R1 ** 2 * ((b1 / gdet) ** 2 + (b2 / gdet) ** 2)
+            pb = max(pb, 0.5 * float(bsq.max()))
+            pg = max(pg, float((gam - 1.0) * prim[1][NG:NG + n3, NG:NG + n2, NG:NG + n1].max()))
+        c = math.sqrt(pg / (beta_max * pb)) if pb > 0 else 0.0
+        for prim, bf in out:
+            bf *= c
+    return out
 
 
 # --- tilted thin disk --------------------------------------------------------
