@@ -29,7 +29,7 @@ class Desc(C.Structure):
                 ("metric", C.c_int), ("a", C.c_double), ("gam", C.c_double),
                 ("cour", C.c_double), ("recon", C.c_int), ("riemann", C.c_int),
                 ("bc", C.c_int * 6), ("floors", C.c_int), ("emf", C.c_int), ("flatten", C.c_int),
-                ("inversion", C.c_int), ("floor_frame", C.c_int)]
+                ("inversion", C.c_int), ("floor_frame", C.c_int), ("smr", C.c_int)]
 
 
 _libs = {}
@@ -97,7 +97,7 @@ def _p(a):
 
 def make_desc(n1, n2, n3, x1min, x2min, x3min, dx1, dx2, dx3, metric=METRIC_KS, a=0.0,
               gam=13.0 / 9.0, cour=0.8, recon=RECON_PPM, riemann=FLUX_HLL, bc=(0, 0, 0, 0, 1, 1),
-              floors=1, emf=EMF_AVERAGE, flatten=0, inversion=0, floor_frame=0):
+              floors=1, emf=EMF_AVERAGE, flatten=0, inversion=0, floor_frame=0, smr=0):
     d = Desc()
     d.n1, d.n2, d.n3 = n1, n2, n3
     d.x1min, d.x2min, d.x3min = x1min, x2min, x3min
@@ -111,6 +111,7 @@ def make_desc(n1, n2, n3, x1min, x2min, x3min, dx1, dx2, dx3, metric=METRIC_KS, 
     d.flatten = flatten
     d.inversion = inversion
     d.floor_frame = floor_frame
+    d.smr = smr
     return d
 
 

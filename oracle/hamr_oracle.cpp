@@ -1194,12 +1194,62 @@ void stage_ct(ora_grid* g, const std::vector<double>& E, const double* Bfb, doub
 }
 
 /* cell update, inversion, floors */
+/* Internal SMR (Sec. 3.3.2: phi-averaging within polar blocks). Reading:
+ * with n_max levels, a row of cells at distance jp (in cells) from a polar
+ * face is grouped into cells 2^n wide in phi, n the largest level in
+ * 1..n_max with jp < 2^(n_max - n) (rows farther out: no grouping). A
+ * group acts as one cell: after the face update its x1-faces and its x2-face
+ * on the far side from the pole take their group mean (the near side belongs
+ * to the row closer to the pole, whose groups are at least as wide) and the
+ * x3-faces inside it are interpolated linearly between its two outer ones,
+ * which keeps every cell divergence-free; after the cell update the group's
+ * conserved variables are averaged and inverted once (start: the mean of
+ * the cells' primitives, field: the mean of their centre fields), every cell
+ * of the group takes the result (its own centre field kept), and the CFL rate
+ * uses the group's width in x3. Returns the group width of row j (1: none). */
+int smr_width(const ora_desc& d, int j) {
+    if (d.smr <= 0) return 1;
+    int jp = 1 << 30;
+    if (d.bc[2] == ORA_BC_POLAR) jp = j;
+    if (d.bc[3] == ORA_BC_POLAR) jp = std::min(jp, d.n2 - 1 - j);
+    for (int n = d.smr; n >= 1; n--)
+        if (jp < (1 << (d.smr - n))) return 1 << n;
+    return 1;
+}
+
+void smr_faces(ora_grid* g, double* Bf) {
+    const ora_desc& d = g->d;
+    const long nc = g->ncell;
+    for (int j = 0; j < d.n2; j++) {
+        const int w = smr_width(d, j);
+        if (w == 1) continue;
+        /* the x2-face on the side away from the pole */
+        const bool lower_pole = (d.bc[2] == ORA_BC_POLAR) && (j < d.n2 / 2);
+        const int jf = lower_pole ? j + 1 : j;
+        for (int k0 = 0; k0 < d.n3; k0 += w) {
+            for (int i = 0; i <= d.n1; i++) {
+                double s1 = 0.0;
+                for (int m = 0; m < w; m++) s1 += Bf[0 * nc + cidx(g, i, j, k0 + m)];
+                for (int m = 0; m < w; m++) Bf[0 * nc + cidx(g, i, j, k0 + m)] = s1 / w;
+            }
+            for (int i = 0; i < d.n1; i++) {
+                double s2 = 0.0;
+                for (int m = 0; m < w; m++) s2 += Bf[1 * nc + cidx(g, i, jf, k0 + m)];
+                for (int m = 0; m < w; m++) Bf[1 * nc + cidx(g, i, jf, k0 + m)] = s2 / w;
+                const double b0 = Bf[2 * nc + cidx(g, i, j, k0)], bw = Bf[2 * nc + cidx(g, i, j, k0 + w)];
+                for (int m = 1; m < w; m++) Bf[2 * nc + cidx(g, i, j, k0 + m)] = b0 + (bw - b0) * m / w;
+            }
+        }
+    }
+}
+
 void stage_update(ora_grid* g, const Fluxes& F, const double* Pb, const double* Pf, const double* Bfout, double dts,
                   double* Pout) {
     const ora_desc& d = g->d;
     const long nc = g->ncell;
     const int n1 = d.n1, n2 = d.n2, n3 = d.n3;
     const double dx[4] = {0.0, d.dx1, d.dx2, d.dx3};
+    std::vector<double> Usmr(d.smr > 0 ? (size_t)NCONS * nc : 0);
     phase_begin();
     for (int k = 0; k < n3; k++)
         for (int j = 0; j < n2; j++)
@@ -1227,6 +1277,10 @@ void stage_update(ora_grid* g, const Fluxes& F, const double* Pb, const double* 
                                (real(F[3][(size_t)m * nc + c3]) - real(F[3][(size_t)m * nc + c])) / dx[3];
                     U[m] = u9[m] * G.gdet + dts * (Q[m] - div);
                 }
+                if (smr_width(d, j) > 1) { /* inverted with its group below */
+                    for (int m = 0; m < NCONS; m++) Usmr[(size_t)m * nc + c] = tod(U[m]);
+                    continue;
+                }
                 real Bc[3];
                 centre_b(g, Bfout, i, j, k, Bc);
                 real pr[NPR];
@@ -1247,6 +1301,53 @@ void stage_update(ora_grid* g, const Fluxes& F, const double* Pb, const double* 
                 }
                 for (int v = 0; v < NPR; v++) Pout[v * nc + c] = tod(pr[v]);
             }
+    /* internal SMR groups: one inversion of the group's mean state */
+    for (int j = 0; j < n2; j++) {
+        const int w = smr_width(d, j);
+        if (w == 1) continue;
+        for (int k0 = 0; k0 < n3; k0 += w)
+            for (int i = 0; i < n1; i++) {
+                const long q2 = gidx(g, i, j);
+                const Geom& G = g->gc[q2];
+                real U[NCONS], Bc[3] = {0.0, 0.0, 0.0}, pr[NPR];
+                for (int m = 0; m < NCONS; m++) U[m] = 0.0;
+                for (int v = 0; v < NPR; v++) pr[v] = 0.0;
+                for (int q = 0; q < w; q++) {
+                    const long c = cidx(g, i, j, k0 + q);
+                    for (int m = 0; m < NCONS; m++) U[m] += Usmr[(size_t)m * nc + c];
+                    real b[3];
+                    centre_b(g, Bfout, i, j, k0 + q, b);
+                    for (int e = 0; e < 3; e++) Bc[e] += b[e];
+                    for (int v = 0; v < 5; v++) pr[v] += Pf[v * nc + c];
+                }
+                for (int m = 0; m < NCONS; m++) U[m] /= w;
+                for (int e = 0; e < 3; e++) Bc[e] /= w;
+                for (int v = 0; v < 5; v++) pr[v] /= w;
+                real pf[5];
+                for (int v = 0; v < 5; v++) pf[v] = pr[v];
+                pr[B1] = Bc[0];
+                pr[B2] = Bc[1];
+                pr[B3] = Bc[2];
+                int its = 0;
+                int st = con2prim(d, U, Bc, G, pr, &its);
+                if (st == C2P_FAIL)
+                    for (int v = 0; v < 5; v++) pr[v] = pf[v];
+                int fl = (d.floors && apply_floors(d, pr, G, g->rc[q2])) ? 1 : 0;
+                for (int q = 0; q < w; q++) {
+                    const long c = cidx(g, i, j, k0 + q);
+                    g->stats[st == C2P_OK ? 0 : (st == C2P_ENTROPY ? 1 : 2)]++;
+                    g->status[c] |= st;
+                    if (fl) {
+                        g->stats[3]++;
+                        g->status[c] |= C2P_FLOOR;
+                    }
+                    real b[3];
+                    centre_b(g, Bfout, i, j, k0 + q, b);
+                    for (int v = 0; v < 5; v++) Pout[v * nc + c] = tod(pr[v]);
+                    for (int e = 0; e < 3; e++) Pout[(B1 + e) * nc + c] = tod(b[e]);
+                }
+            }
+    }
     phase_end(4);
 }
 
@@ -1257,6 +1358,7 @@ void stage(ora_grid* g, const double* Pf, const double* Bff, const double* Pb, c
     stage_fluxes(g, Pf, Bff, F);
     stage_emf(g, F, Pf, E);
     stage_ct(g, E, Bfb, dts, Bfout);
+    if (g->d.smr > 0) smr_faces(g, Bfout);
     stage_update(g, F, Pb, Pf, Bfout, dts, Pout);
 }
 
@@ -1281,7 +1383,7 @@ double grid_dt(ora_grid* g) {
                     real vp, vm;
                     vchar(pr, s, G, dir, d.gam, &vp, &vm);
                     real vf = fmax(fabs(vp), fabs(vm));
-                    inv += vf / dx[dir];
+                    inv += vf / (dir == 3 ? dx[3] * smr_width(d, j) : dx[dir]);
                 }
                 if (inv > invmax) invmax = inv;
             }

@@ -45,6 +45,7 @@ typedef struct {
     int flatten;                    /* 1: PPM shock flattening (Colella & Woodward 1984) */
     int inversion;                  /* ORA_INV_*: energy inversion by 2-D Newton or Aitken-accelerated fixed point */
     int floor_frame;                /* ORA_FLOOR_*: floor material added in the fluid frame or the drift frame */
+    int smr;                        /* internal SMR levels n_max next to polar faces (0: off; single grids) */
 } ora_desc;
 
 /* ---- point-wise pieces (each documented in hamr_oracle.cpp) ---- */
