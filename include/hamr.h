@@ -116,6 +116,12 @@ typedef struct {
                             unless recon is HAMR_RECON_PPM. 0 or 1, else HAMR_EINVAL */
     int inversion;       /* HAMR_INV_*: energy inversion of every cell update */
     int floor_frame;     /* HAMR_FLOOR_*: where floors apply (floors = 1), the frame of the added material */
+    int smr;             /* internal SMR levels n_max (Sec. 3.3.2; 0: off, at most 4): the row at
+                            distance jp (cells) from a polar x2 face acts as cells 2^n wide in x3, n the
+                            largest level with jp < 2^(n_max - n) (faces averaged, inner x3-faces
+                            interpolated, one inversion per group, CFL over the group width). Single-
+                            block grids with a polar x2 bc, n3 a multiple of 2^(n_max + 1),
+                            n2 >= 2^n_max; the no-allocation step refuses it */
 } hamr_grid_desc;
 
 /* Counters of the last step (summed over its two stages and all blocks

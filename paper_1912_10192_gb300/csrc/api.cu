@@ -155,6 +155,15 @@ int validate(const hamr_grid_desc* d) {
         return fail(HAMR_EINVAL, "unknown inversion %d", d->inversion);
     if (d->floor_frame != HAMR_FLOOR_FLUID && d->floor_frame != HAMR_FLOOR_DRIFT)
         return fail(HAMR_EINVAL, "unknown floor_frame %d", d->floor_frame);
+    if (d->smr < 0 || d->smr > 4) return fail(HAMR_EINVAL, "smr must be in 0..4, got %d", d->smr);
+    if (d->smr > 0) {
+        if (d->nblocks != 1) return fail(HAMR_EINVAL, "internal SMR is for single-block grids");
+        const hamr_block_desc& B = d->blocks[0];
+        if (B.bc[2] != HAMR_BC_POLAR && B.bc[3] != HAMR_BC_POLAR)
+            return fail(HAMR_EINVAL, "internal SMR needs a polar x2 boundary");
+        if (B.n3 % (2 << d->smr) != 0) return fail(HAMR_EINVAL, "internal SMR needs n3 a multiple of %d", 2 << d->smr);
+        if (B.n2 < (1 << d->smr)) return fail(HAMR_EINVAL, "internal SMR needs n2 >= %d", 1 << d->smr);
+    }
     for (int b = 0; b < d->nblocks; b++) {
         const hamr_block_desc& B = d->blocks[b];
         if (B.n1 < 4 || B.n2 < 4 || B.n3 < 4) return fail(HAMR_EINVAL, "block %d: each n must be >= 4", b);
@@ -360,6 +369,8 @@ int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out) {
     g->ph.flatten = (d->flatten && d->recon == HAMR_RECON_PPM) ? 1 : 0;
     g->ph.inversion = d->inversion;
     g->ph.floor_frame = d->floor_frame;
+    g->ph.smr = d->smr;
+    g->ph.smr_u = nullptr;
     cudaGetDevice(&g->device);
     for (int b = 0; b < d->nblocks; b++) {
         rc = alloc_block(g, b);
@@ -373,6 +384,7 @@ int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out) {
         free_grid(g);
         return fail(HAMR_ECUDA, "geometry build failed: %s", cudaGetErrorString(e));
     }
+    if (d->smr > 0) g->ph.smr_u = g->st[0].QR;  // free once the fluxes are formed
     if (d->nblocks > 1) {
         rc = amr_create(&g->amr, g->desc, g->view, g->st, g->ph);
         if (rc) {
@@ -455,8 +467,11 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
     }
     LAUNCH(g, K_EMF, ph.emf ? 2 : 1, cs, launch_emf(v, s.F, s.E, ph.mixed, s.P, ph.emf ? s.QL : nullptr, cs));
     LAUNCH(g, K_CT, 1, cs, launch_ct(v, s.E, s.B, s.Bh, s.dscal, 0.5, cs));
+    if (ph.smr) LAUNCH(g, K_CT, 1, cs, launch_smr_faces(v, ph, s.Bh, cs));
     LAUNCH(g, K_UPDATE, 1, cs,
            launch_update(v, ph, 0, s.P, s.P, s.F, s.Bh, s.Un, s.Ph, s.status, s.dscal, 0.5, s.dmax, s.dcnt, cs));
+    if (ph.smr)
+        LAUNCH(g, K_UPDATE, 1, cs, launch_smr_cells(v, ph, 0, s.P, s.Bh, s.Ph, s.status, s.dmax, s.dcnt, cs));
     // corrector: U^n and the fluxes of P^{n+1/2} -> P^{n+1}, B^{n+1} (in place)
     LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.Ph, s.Bh, cs));
     if (ph.mixed) LAUNCH(g, K_BC, 1, cs, launch_to_f32(v, s.Ph, s.P32, cs));
@@ -467,8 +482,11 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
     }
     LAUNCH(g, K_EMF, ph.emf ? 2 : 1, cs, launch_emf(v, s.F, s.E, ph.mixed, s.Ph, ph.emf ? s.QL : nullptr, cs));
     LAUNCH(g, K_CT, 1, cs, launch_ct(v, s.E, s.B, s.B, s.dscal, 1.0, cs));
+    if (ph.smr) LAUNCH(g, K_CT, 1, cs, launch_smr_faces(v, ph, s.B, cs));
     LAUNCH(g, K_UPDATE, 1, cs,
            launch_update(v, ph, 1, s.P, s.Ph, s.F, s.B, s.Un, s.P, s.status, s.dscal, 1.0, s.dmax, s.dcnt, cs));
+    if (ph.smr)
+        LAUNCH(g, K_UPDATE, 1, cs, launch_smr_cells(v, ph, 1, s.Ph, s.B, s.P, s.status, s.dmax, s.dcnt, cs));
     LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.P, s.B, cs));
     if (stats) {
         CUDA_TRY(cudaStreamSynchronize(cs));

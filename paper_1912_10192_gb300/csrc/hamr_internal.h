@@ -58,7 +58,20 @@ struct PhysArgs {
     int flatten;  // 1: PPM shock flattening (only set with HAMR_RECON_PPM)
     int inversion;  // HAMR_INV_*
     int floor_frame;  // HAMR_FLOOR_*
+    int smr;          // internal SMR levels next to polar faces (single-block grids; 0: off)
+    double* smr_u;    // scratch of the deferred conserved states (6 fields, stride nc) when smr > 0
 };
+
+// group width in x3 of row j under internal SMR (1: not grouped); see cell_floors' neighbour in step.cu
+__host__ __device__ inline int smr_width(const BlockView& v, const PhysArgs& ph, int j) {
+    if (ph.smr <= 0) return 1;
+    int jp = 1 << 30;
+    if (v.bc[2] == HAMR_BC_POLAR) jp = j;
+    if (v.bc[3] == HAMR_BC_POLAR) jp = (v.n2 - 1 - j < jp) ? v.n2 - 1 - j : jp;
+    for (int n = ph.smr; n >= 1; n--)
+        if (jp < (1 << (ph.smr - n))) return 1 << n;
+    return 1;
+}
 
 // threads of one reconstruction launch (FP64): rows along x1 in warps of 32
 // lanes that produce RECON_TILE cells each; pencils along x2 or x3 of
@@ -163,6 +176,12 @@ cudaError_t launch_emf(const BlockView& v, double* const F[3], double* E, int mi
                        cudaStream_t s);
 cudaError_t launch_ct(const BlockView& v, const double* E, const double* Bbase, double* Bout, const double* dscal,
                       double dt_factor, cudaStream_t s);
+// internal SMR (single-block grids): group means of the radial and far-side theta faces and
+// interpolated inner phi faces after CT; one inversion per group after the cell update
+cudaError_t launch_smr_faces(const BlockView& v, const PhysArgs& ph, double* B, cudaStream_t s);
+cudaError_t launch_smr_cells(const BlockView& v, const PhysArgs& ph, int corrector, const double* Pf, const double* Bn,
+                             double* Po, uint8_t* status, unsigned long long* dmax, unsigned long long* dcnt,
+                             cudaStream_t s);
 cudaError_t launch_update(const BlockView& v, const PhysArgs& ph, int corrector, const double* Pbase,
                           const double* Pflux, double* const F[3], const double* Bnew, double* Un, double* Pout,
                           uint8_t* status, const double* dscal, double dt_factor, unsigned long long* dmax,

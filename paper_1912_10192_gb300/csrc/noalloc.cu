@@ -87,6 +87,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
         return set_error(HAMR_EINVAL, "unknown inversion %d", d->inversion);
     if (d->floor_frame != HAMR_FLOOR_FLUID && d->floor_frame != HAMR_FLOOR_DRIFT)
         return set_error(HAMR_EINVAL, "unknown floor_frame %d", d->floor_frame);
+    if (d->smr != 0) return set_error(HAMR_EINVAL, "the no-allocation step does not do internal SMR");
 
     double* base = nullptr;
     int rc = setup(&base);
@@ -163,6 +164,8 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     ph.flatten = (d->flatten && d->recon == HAMR_RECON_PPM) ? 1 : 0;
     ph.inversion = d->inversion;
     ph.floor_frame = d->floor_frame;
+    ph.smr = 0;
+    ph.smr_u = nullptr;
 
     // the array keeps the previous call's contents: clear what must start at zero
     NA_TRY(cudaMemsetAsync(s.Ph, 0, sizeof(double) * 11 * v.nc, cs));

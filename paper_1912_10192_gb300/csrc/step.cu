@@ -751,7 +751,7 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
                                                uint8_t* __restrict__ status, const double* __restrict__ dscal,
                                                double fac, unsigned long long* dmax, unsigned long long* dcnt, long t) {
     const long n = (long)v.n1 * v.n2 * v.n3;
-    const bool active = t < n;
+    bool active = t < n;  // false again for a cell whose inversion its internal-SMR group does
     double inv = 0.0;
     int st = -1, fl = 0, its = 0;
     const double gam = ph.gam;
@@ -817,6 +817,11 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
         pr[B1] = Bc[0];
         pr[B2] = Bc[1];
         pr[B3] = Bc[2];
+        if (ph.smr > 0 && smr_width(v, ph, j) > 1) {  // inverted with its group (k_smr_cells)
+#pragma unroll
+            for (int q = 0; q < NCONS; q++) ph.smr_u[q * nc + c] = U[q];
+            active = false;
+        }
     }
     // inversion: energy attempts from the start(s), then the entropy backup
     C2PWork w;
@@ -908,7 +913,14 @@ __device__ __forceinline__ void b_dt_reduce(const BlockView& v, PhysArgs ph, con
         double pr[NPRIM];
 #pragma unroll
         for (int q = 0; q < NPRIM; q++) pr[q] = P[q * v.nc + c];
-        inv = inv_dt_cell(v, pr, m, ph.gam);
+        const int w = smr_width(v, ph, j);
+        if (w > 1) {  // an internal-SMR group: its width in x3
+            BlockView vw = v;
+            vw.idx3 = v.idx3 / w;
+            inv = inv_dt_cell(vw, pr, m, ph.gam);
+        } else {
+            inv = inv_dt_cell(v, pr, m, ph.gam);
+        }
     }
     const double wmax = warp_max(inv);
     if ((threadIdx.x & 31u) == 0 && wmax > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(wmax));
@@ -1078,6 +1090,119 @@ __global__ void k_reflux_cells(const DevBlock* tab, int n, const int* cblk, cons
     if (fl) atomicAdd(&D.dcnt[3], 1ull);
 }
 
+// ---------------------------------------------------------------- internal SMR
+// Rows next to a polar face grouped into cells smr_width wide in x3 (Sec. 3.3.2):
+// after CT, a group's x1-faces and its x2-face away from the pole take their
+// group mean and its inner x3-faces are interpolated linearly between its two
+// outer ones (every cell stays divergence-free); after the cell update (which
+// leaves the group's conserved states in ph.smr_u) the group's mean state is
+// inverted once with the mean centre field, from the mean primitives, and every
+// cell takes the result (its own centre field kept); the CFL rate uses the
+// group's width. Threads: rows j in [0, nr) and [n2 - nr, n2), nr = 2^(smr-1).
+__device__ __forceinline__ int smr_row(const BlockView& v, const PhysArgs& ph, int r) {
+    const int nr = 1 << (ph.smr - 1);
+    return (r < nr) ? r : v.n2 - 2 * nr + r;
+}
+
+__global__ void k_smr_faces(BlockView v, PhysArgs ph, double* __restrict__ B) {
+    const int nr = 1 << (ph.smr - 1);
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ng = v.n3 / 2;
+    if (t >= (long)(v.n1 + 1) * 2 * nr * ng) return;
+    const int i = (int)(t % (v.n1 + 1));
+    const int r = (int)((t / (v.n1 + 1)) % (2 * nr));
+    const int gi = (int)(t / ((long)(v.n1 + 1) * 2 * nr));
+    const int j = smr_row(v, ph, r);
+    const int w = smr_width(v, ph, j);
+    if (w == 1 || gi >= v.n3 / w) return;
+    const int k0 = gi * w;
+    double s1 = 0.0;
+    for (int m = 0; m < w; m++) s1 += B[cidx(v, i, j, k0 + m)];
+    for (int m = 0; m < w; m++) B[cidx(v, i, j, k0 + m)] = s1 / w;
+    if (i == v.n1) return;
+    const bool lower_pole = (v.bc[2] == HAMR_BC_POLAR) && (j < v.n2 / 2);
+    const int jf = lower_pole ? j + 1 : j;
+    double* B2 = B + v.nc;
+    double s2 = 0.0;
+    for (int m = 0; m < w; m++) s2 += B2[cidx(v, i, jf, k0 + m)];
+    for (int m = 0; m < w; m++) B2[cidx(v, i, jf, k0 + m)] = s2 / w;
+    double* B3 = B + 2 * v.nc;
+    const double b0 = B3[cidx(v, i, j, k0)], bw = B3[cidx(v, i, j, k0 + w)];
+    for (int m = 1; m < w; m++) B3[cidx(v, i, j, k0 + m)] = b0 + (bw - b0) * m / w;
+}
+
+__global__ void k_smr_cells(BlockView v, PhysArgs ph, int corrector, const double* __restrict__ Pf,
+                            const double* __restrict__ Bn, double* Po, uint8_t* __restrict__ status,
+                            unsigned long long* dmax, unsigned long long* dcnt) {
+    const int nr = 1 << (ph.smr - 1);
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ng = v.n3 / 2;
+    if (t >= (long)v.n1 * 2 * nr * ng) return;
+    const int i = (int)(t % v.n1);
+    const int r = (int)((t / v.n1) % (2 * nr));
+    const int gi = (int)(t / ((long)v.n1 * 2 * nr));
+    const int j = smr_row(v, ph, r);
+    const int w = smr_width(v, ph, j);
+    if (w == 1 || gi >= v.n3 / w) return;
+    const int k0 = gi * w;
+    const long g = gidx(v, i, j);
+    Metric<double> m;
+    load_metric(v.gc, v.n2d, g, m);
+    double U[NCONS], Bc[3] = {0.0, 0.0, 0.0}, pr[NPRIM];
+#pragma unroll
+    for (int q = 0; q < NCONS; q++) U[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < NPRIM; q++) pr[q] = 0.0;
+    for (int a = 0; a < w; a++) {
+        const long c = cidx(v, i, j, k0 + a);
+#pragma unroll
+        for (int q = 0; q < NCONS; q++) U[q] += ph.smr_u[q * v.nc + c];
+        double b[3];
+        centre_field(v, Bn, i, j, k0 + a, m.gdet, b);
+        for (int e = 0; e < 3; e++) Bc[e] += b[e];
+#pragma unroll
+        for (int q = 0; q < 5; q++) pr[q] += Pf[q * v.nc + c];
+    }
+#pragma unroll
+    for (int q = 0; q < NCONS; q++) U[q] /= w;
+    for (int e = 0; e < 3; e++) Bc[e] /= w;
+#pragma unroll
+    for (int q = 0; q < 5; q++) pr[q] /= w;
+    double pf[5];
+#pragma unroll
+    for (int q = 0; q < 5; q++) pf[q] = pr[q];
+    pr[B1] = Bc[0];
+    pr[B2] = Bc[1];
+    pr[B3] = Bc[2];
+    int its = 0;
+    const int st = invert(U, Bc, m, ph.gam, pr, &its, false, nullptr, ph.inversion);
+    if (st == INV_FAIL)
+#pragma unroll
+        for (int q = 0; q < 5; q++) pr[q] = pf[q];
+    Fluid<double> s;
+    fluid_state(pr, m, s);
+    const int fl = ph.floors ? cell_floors(v, g, m, ph, pr, s) : 0;
+    const uint8_t sb = ((st == INV_ENTROPY) ? ST_ENTROPY : ((st == INV_FAIL) ? ST_FAIL : 0)) | (fl ? ST_FLOOR : 0);
+    for (int a = 0; a < w; a++) {
+        const long c = cidx(v, i, j, k0 + a);
+        double b[3];
+        centre_field(v, Bn, i, j, k0 + a, m.gdet, b);
+#pragma unroll
+        for (int q = 0; q < 5; q++) Po[q * v.nc + c] = pr[q];
+        for (int e = 0; e < 3; e++) Po[(B1 + e) * v.nc + c] = b[e];
+        status[c] |= sb;
+    }
+    atomicAdd(&dcnt[st == INV_OK ? 0 : (st == INV_ENTROPY ? 1 : 2)], (unsigned long long)w);
+    if (fl) atomicAdd(&dcnt[3], (unsigned long long)w);
+    atomicAdd(&dcnt[4], (unsigned long long)(w * its));
+    if (corrector == 1) {
+        BlockView vw = v;
+        vw.idx3 = v.idx3 / w;
+        const double inv = inv_dt_fluid(vw, pr, s, m, ph.gam);
+        if (inv > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(inv));
+    }
+}
+
 // maximum of field q over the interior cells, as ordered bits (ordered_bits)
 __global__ void k_block_max(BlockView v, const double* __restrict__ P, int q, unsigned long long* out) {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1095,6 +1220,20 @@ __global__ void k_block_max(BlockView v, const double* __restrict__ P, int q, un
 }
 
 }  // namespace
+
+cudaError_t launch_smr_faces(const BlockView& v, const PhysArgs& ph, double* B, cudaStream_t s) {
+    const long n = (long)(v.n1 + 1) * 2 * (1 << (ph.smr - 1)) * (v.n3 / 2);
+    k_smr_faces<<<nblk(n), BS, 0, s>>>(v, ph, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_smr_cells(const BlockView& v, const PhysArgs& ph, int corrector, const double* Pf, const double* Bn,
+                             double* Po, uint8_t* status, unsigned long long* dmax, unsigned long long* dcnt,
+                             cudaStream_t s) {
+    const long n = (long)v.n1 * 2 * (1 << (ph.smr - 1)) * (v.n3 / 2);
+    k_smr_cells<<<nblk(n), BS, 0, s>>>(v, ph, corrector, Pf, Bn, Po, status, dmax, dcnt);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_block_max(const BlockView& v, const double* P, int q, unsigned long long* out, cudaStream_t s) {
     k_block_max<<<nblk((long)v.n1 * v.n2 * v.n3), BS, 0, s>>>(v, P, q, out);

@@ -44,7 +44,7 @@ class GridDesc(C.Structure):
     _fields_ = [("metric", C.c_int), ("a", C.c_double), ("gam", C.c_double), ("cour", C.c_double),
                 ("recon", C.c_int), ("riemann", C.c_int), ("floors", C.c_int), ("precision", C.c_int),
                 ("nblocks", C.c_int), ("blocks", C.POINTER(BlockDesc)), ("emf", C.c_int),
-                ("flatten", C.c_int), ("inversion", C.c_int), ("floor_frame", C.c_int)]
+                ("flatten", C.c_int), ("inversion", C.c_int), ("floor_frame", C.c_int), ("smr", C.c_int)]
 
 
 class StepStats(C.Structure):
@@ -202,7 +202,7 @@ class Grid:
 
     def __init__(self, blocks, metric=METRIC_KS, a=0.9375, gam=13.0 / 9.0, cour=0.8, recon=RECON_PPM,
                  riemann=FLUX_HLL, floors=1, precision=PREC_FP64, emf=EMF_AVERAGE, flatten=0, inversion=INV_NEWTON,
-                 floor_frame=FLOOR_FLUID):
+                 floor_frame=FLOOR_FLUID, smr=0):
         self._blocks = (BlockDesc * len(blocks))(*blocks)
         d = GridDesc()
         d.metric, d.a, d.gam, d.cour = metric, a, gam, cour
@@ -211,6 +211,7 @@ class Grid:
         d.flatten = flatten
         d.inversion = inversion
         d.floor_frame = floor_frame
+        d.smr = smr
         d.nblocks = len(blocks)
         d.blocks = self._blocks
         self.desc = d

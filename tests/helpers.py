@@ -23,7 +23,7 @@ def gpu_grid(d):
     b = hamr.block(d.n1, d.n2, d.n3, d.x1min, d.x2min, d.x3min, d.dx1, d.dx2, d.dx3, tuple(d.bc))
     return hamr.Grid([b], metric=d.metric, a=d.a, gam=d.gam, cour=d.cour, recon=d.recon, riemann=d.riemann,
                      floors=d.floors, emf=d.emf, flatten=d.flatten,
-                     inversion=d.inversion, floor_frame=d.floor_frame)
+                     inversion=d.inversion, floor_frame=d.floor_frame, smr=d.smr)
 
 
 def interior(a, d):
