@@ -47,3 +47,49 @@ def test_invalid_descriptors_rejected_without_gpu_work(libpath):
     d2.metric, d2.a, d2.gam, d2.flags = 0, 0.5, 13 / 9, 0x10
     assert L.hamr_con2prim(ctypes.byref(d2), 5, 1, 1, 1, 1, 1, 1, None, None) == hamr.EINVAL
     assert L.hamr_con2prim(ctypes.byref(d2), 0, None, None, None, None, None, None, None, None) == hamr.OK
+
+
+def _desc(blocks, **kw):
+    arr = (hamr.BlockDesc * len(blocks))(*blocks)
+    d = hamr.GridDesc()
+    d.metric, d.a, d.gam, d.cour = kw.pop("metric", 0), 0.5, 13 / 9, 0.8
+    d.nblocks = len(blocks)
+    d.blocks = arr
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d, arr
+
+
+def test_option_fields_are_validated_before_any_device_call(libpath):
+    """Each option of the step refuses an unknown value with HAMR_EINVAL and a message, on CPU."""
+    L = hamr.lib()
+    h = ctypes.c_void_p()
+    polar = hamr.block(16, 16, 16, 0.0, 0.0, 0.0, 0.1, 0.1, 0.1, (3, 3, 2, 2, 1, 1))
+    for field, bad, msg in (("emf", 2, b"unknown emf"), ("flatten", 3, b"flatten must be 0 or 1"),
+                            ("inversion", 5, b"unknown inversion"), ("floor_frame", 2, b"unknown floor_frame"),
+                            ("smr", 5, b"smr must be in 0..4"), ("metric", 3, b"unknown metric")):
+        d, arr = _desc([polar], **{field: bad})
+        assert L.hamr_grid_create(ctypes.byref(d), ctypes.byref(h)) == hamr.EINVAL, field
+        assert msg in L.hamr_last_error(), (field, L.hamr_last_error())
+    # internal SMR: single blocks with a polar face and n3 divisible by 2^(smr+1)
+    flat = hamr.block(16, 16, 16, 0.0, 0.0, 0.0, 0.1, 0.1, 0.1, (1, 1, 1, 1, 1, 1))
+    d, arr = _desc([flat], smr=1)
+    assert L.hamr_grid_create(ctypes.byref(d), ctypes.byref(h)) == hamr.EINVAL
+    assert b"polar" in L.hamr_last_error()
+    odd = hamr.block(16, 16, 12, 0.0, 0.0, 0.0, 0.1, 0.1, 0.1, (3, 3, 2, 2, 1, 1))
+    d, arr = _desc([odd], smr=3)
+    assert L.hamr_grid_create(ctypes.byref(d), ctypes.byref(h)) == hamr.EINVAL
+    assert b"multiple of 16" in L.hamr_last_error()
+    # polar boundaries need spherical coordinates: refused in flat Cartesian space
+    d, arr = _desc([polar], metric=1)
+    assert L.hamr_grid_create(ctypes.byref(d), ctypes.byref(h)) == hamr.EINVAL
+    assert b"spherical" in L.hamr_last_error()
+
+
+def test_tree_and_regrid_arguments_checked_on_cpu(libpath):
+    L = hamr.lib()
+    assert L.hamr_grid_regrid(None, 2, None, None) == hamr.EINVAL
+    assert L.hamr_grid_block_max(None, 0, None, None) == hamr.EINVAL
+    assert L.hamr_grid_set_fine_dt(None, 0.1) == hamr.EINVAL
+    n = ctypes.c_int()
+    assert L.hamr_tree_adapt(None, 0, None, None, None, None, None, 0, ctypes.byref(n)) == hamr.EINVAL
