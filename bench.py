@@ -326,11 +326,14 @@ def inversion_variants(hamr, torch, m, n=1_000_000, seed=6):
 
 def options_leg(args, hamr, torch, blk, dprim, dbf, cells, stream):
     """The benchmark workload with each option of the step switched on alone (FP64): upwinded EMFs, the
-    PPM shock flattener, the Aitken inversion, floors in the drift frame; zone-cycles/s and ms/step."""
+    PPM shock flattener, the Aitken inversion, floors in the drift frame, two levels of internal SMR;
+    zone-cycles/s, ms/step and the CFL step after the timed steps (internal SMR buys time step, not
+    zone-cycles)."""
     out = {}
     for name, kw in (("plain", {}), ("emf_upwind", {"emf": hamr.EMF_UPWIND}), ("flatten", {"flatten": 1}),
                      ("aitken_inversion", {"inversion": hamr.INV_AITKEN}),
-                     ("drift_floors", {"floor_frame": hamr.FLOOR_DRIFT})):
+                     ("drift_floors", {"floor_frame": hamr.FLOOR_DRIFT}),
+                     ("internal_smr_2", {"smr": 2})):
         g = hamr.Grid([blk], **kw)
         g.set_state(dprim, dbf, stream=stream)
         for _ in range(args.warmup):
@@ -346,7 +349,7 @@ def options_leg(args, hamr, torch, blk, dprim, dbf, cells, stream):
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1) / steps
         st = g.step(stream=stream, stats=True)
-        out[name] = {"value": cells / (ms * 1e-3), "ms_per_step": round(ms, 3),
+        out[name] = {"value": cells / (ms * 1e-3), "ms_per_step": round(ms, 3), "dt_next": st["dt_next"],
                      "entropy_per_step": st["c2p_entropy"], "floor_hits_per_step": st["floor_hits"],
                      "iters_per_inversion": st["newton_iters"] / max(st["c2p_ok"] + st["c2p_entropy"] +
                                                                        st["c2p_fail"], 1)}
@@ -379,6 +382,10 @@ def amr_leg(hamr, torch, precision=0):
     ms_default = time_periods()
     tune = g.autotune()
     ms = time_periods()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.regrid([hamr.block_from_dict(b) for b in blocks])  # onto the same tree: allocation + device fill
+    regrid_ms = (time.perf_counter() - t0) * 1e3
     real = sum(b["n1"] * b["n2"] * b["n3"] * 2 ** (lmax - b["lat"]) for b in blocks)
     eff = sum(b["n1"] * b["n2"] * b["n3"] for b in blocks) * per
     hist = {str(L): sum(1 for b in blocks if b["lat"] == L) for L in range(lmax + 1)}
@@ -389,7 +396,7 @@ def amr_leg(hamr, torch, precision=0):
             "ms_per_period_default_shapes": ms_default,
             "launch_shapes": {k: tune[k] for k in ("recon_seg", "bs_recon", "bs_flux", "bs_update")},
             "autotune_ms": {k: [round(x, 3) for x in tune[k]] for k in ("ms_seg", "ms_recon", "ms_flux", "ms_update")},
-            "fine_substeps_per_period": per,
+            "fine_substeps_per_period": per, "regrid_same_tree_ms": round(regrid_ms, 1),
             "real_zone_cycles_per_s": real / (ms * 1e-3), "lat_effective_zone_cycles_per_s": eff / (ms * 1e-3),
             "lat_levels": hist}
 
