@@ -58,6 +58,21 @@ def env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """The slowest rank's value of x (the job's time): an all-reduce MAX over the ranks of the process
+    group (x itself on one rank). Every rank gets the result."""
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds_max):
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -196,16 +211,13 @@ def mixed_leg(args, hamr, torch, blk, dprim, dbf, g64, stream, cells, world, dis
     ms = ev0.elapsed_time(ev1)
     timing = gm.timing()
     gm.set_timing(False)
-    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist)
     pm, bm = gm.get_state()
     p64, b64 = g64.get_state()
     gm.close()
     return {"form": "mixed: FP32 reconstruction, face fluxes and edge EMFs; FP64 metric, U^n, update, "
                     "connection source, CT curl and inversion",
-            "value": cells * args.steps * world / (ms_max * 1e-3), "unit": "zone-cycles/s",
+            "value": job_rate(cells * args.steps, world, ms_max * 1e-3), "unit": "zone-cycles/s",
             "ms_per_step": ms_max / args.steps, "dtype": "f32+f64",
             "l1_vs_fp64": dict(field_l1(pm, bm, p64, b64), steps=args.warmup + args.steps),
             "kernel_ms": {k: round(v[1], 3) for k, v in timing.items()},
@@ -448,12 +460,9 @@ def run_ours(args, rank, world, local):
         dist.barrier()
     timing = g.timing()
     g.set_timing(False)
-    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist)
     stats = g.stats()
-    value = cells * args.steps * world / (ms_max * 1e-3)
+    value = job_rate(cells * args.steps, world, ms_max * 1e-3)
 
     # ---- chosen form: the same workload with FP32 reconstruction, fluxes and EMFs
     chosen = None
@@ -486,10 +495,7 @@ def run_ours(args, rank, world, local):
         g2.get_state(prim=op, bface=ob)
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
-    te_t = torch.tensor([te], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
-    e2e = {"value": cells * e2e_steps * world / float(te_t.item()), "unit": "zone-cycles/s",
+    e2e = {"value": job_rate(cells * e2e_steps, world, max_over_ranks(te, dist)), "unit": "zone-cycles/s",
            "h2d_bytes_per_step": int(hp.nbytes + hb.nbytes), "d2h_bytes_per_step": int(op.nbytes + ob.nbytes),
            "steps": e2e_steps,
            "path": "hamr_grid_set_state(host, pinned) + hamr_block_step + hamr_grid_get_state(host) per step"}
