@@ -406,8 +406,9 @@ def amr_leg(hamr, torch, precision=0):
                         sum(b["n1"] * b["n2"] * b["n3"] for b in blocks),
             "precision": "mixed" if precision else "fp64", "ms_per_period": ms,
             "ms_per_period_default_shapes": ms_default,
-            "launch_shapes": {k: tune[k] for k in ("recon_seg", "bs_recon", "bs_flux", "bs_update")},
-            "autotune_ms": {k: [round(x, 3) for x in tune[k]] for k in ("ms_seg", "ms_recon", "ms_flux", "ms_update")},
+            "launch_shapes": {k: tune[k] for k in ("recon_seg", "recon_x1_sweep", "bs_recon", "bs_flux", "bs_update")},
+            "autotune_ms": {k: [round(x, 3) for x in tune[k]] for k in ("ms_seg", "ms_x1", "ms_recon", "ms_flux",
+                                                                       "ms_update")},
             "fine_substeps_per_period": per, "regrid_same_tree_ms": round(regrid_ms, 1),
             "real_zone_cycles_per_s": real / (ms * 1e-3), "lat_effective_zone_cycles_per_s": eff / (ms * 1e-3),
             "lat_levels": hist}

@@ -408,8 +408,9 @@ int hamr_grid_set_mlp(hamr_grid* g, const hamr_mlp* m, int mode);
 /* ---- launch-shape autotuner (no paper counterpart) ----
  * Times the grid's reconstruction, face-flux and cell-update kernels on its
  * current state for each candidate launch shape and keeps the fastest:
- * cells per thread of the x2/x3 reconstruction sweeps (8, 16, 32; FP64),
- * then threads per CTA of the reconstruction and flux kernels (64, 128, 256)
+ * cells per thread of the reconstruction sweeps (8, 16, 32; FP64), the form
+ * of the x1 edge values (pencil sweeps or warp rows; FP64), then threads per
+ * CTA of the reconstruction and flux kernels (64, 128, 256)
  * and of the cell update (64, 128; 128 while a network is attached). Shapes
  * change no result bit. The timed launches write only scratch (edge values,
  * fluxes, the midpoint state); call it after a first step or period so the
@@ -421,12 +422,19 @@ typedef struct {
     float ms_recon[3];  /* reconstruction, 64, 128, 256 threads per CTA (chosen sweep) */
     float ms_flux[3];   /* face fluxes, 64, 128, 256 threads per CTA */
     float ms_update[2]; /* cell update (predictor), 64, 128 threads per CTA */
+    int recon_x1_sweep;  /* chosen x1 form: 1 pencil sweeps (the default), 0 warp rows */
+    float ms_x1[2];      /* reconstruction with x1 by warp rows, by sweeps (chosen sweep length) */
 } hamr_tune_report;
 
 int hamr_grid_autotune(hamr_grid* g, void* stream, hamr_tune_report* report);
 /* The grid's current launch shapes (defaults 16, 128, 128, 128) into report
  * (timings zero). */
 int hamr_grid_launch_shapes(const hamr_grid* g, hamr_tune_report* report);
+/* Sets the launch shapes of report (recon_seg 8/16/32, recon_x1_sweep 0/1,
+ * bs_recon and bs_flux 64/128/256, bs_update 64/128; timings ignored), e.g.
+ * those a previous hamr_grid_autotune chose. HAMR_EINVAL for other values.
+ * Synchronises; results do not change. */
+int hamr_grid_set_launch_shapes(hamr_grid* g, const hamr_tune_report* report);
 
 /* Message of the last error in the calling thread ("" if none). */
 const char* hamr_last_error(void);

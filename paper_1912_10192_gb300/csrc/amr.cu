@@ -1294,7 +1294,8 @@ int amr_create(AmrImpl** out, const hamr_grid_desc& d, const std::vector<BlockVi
         const long cel = (long)v.n1 * v.n2 * v.n3;
         M->lmw_pad[L] = std::max(M->lmw_pad[L], pad);
         for (int dir = 1; dir <= 3; dir++)
-            M->lmw_recon[L][dir] = std::max(M->lmw_recon[L][dir], recon_threads(v, dir, ph.mixed, ph.recon_seg));
+            M->lmw_recon[L][dir] =
+                std::max(M->lmw_recon[L][dir], recon_threads(v, dir, ph.mixed, ph.recon_seg, ph.recon_x1_sweep));
         M->lmw_edge[L] = std::max(M->lmw_edge[L], edg);
         M->lmw_cell[L] = std::max(M->lmw_cell[L], cel);
         M->lmw_ext[L] = std::max(M->lmw_ext[L], (long)(v.n1 + 2) * (v.n2 + 2) * (v.n3 + 2));
@@ -1460,7 +1461,8 @@ int amr_set_phys(AmrImpl* M, const PhysArgs& ph) {
     for (int L = 0; L <= M->Lmax; L++)
         for (int dir = 1; dir <= 3; dir++) {
             long mw = 0;
-            for (int b : M->lev[L]) mw = std::max(mw, recon_threads(M->H.b[b].v, dir, ph.mixed, ph.recon_seg));
+            for (int b : M->lev[L])
+                mw = std::max(mw, recon_threads(M->H.b[b].v, dir, ph.mixed, ph.recon_seg, ph.recon_x1_sweep));
             M->lmw_recon[L][dir] = mw;
         }
     if (M->exec) cudaGraphExecDestroy(M->exec);
@@ -1488,8 +1490,9 @@ int amr_time_group(AmrImpl* M, const PhysArgs& ph, int which, cudaStream_t cs, f
         long mwr[4];
         for (int dir = 1; dir <= 3; dir++) {
             mwr[dir] = 0;
-            for (int bb : M->lev[L]) mwr[dir] = std::max(mwr[dir], recon_threads(M->H.b[bb].v, dir, ph.mixed,
-                                                                                 ph.recon_seg));
+            for (int bb : M->lev[L])
+                mwr[dir] = std::max(mwr[dir], recon_threads(M->H.b[bb].v, dir, ph.mixed, ph.recon_seg,
+                                                            ph.recon_x1_sweep));
         }
         auto timed = [&](auto launch) {
             cudaEventRecord(a, cs);

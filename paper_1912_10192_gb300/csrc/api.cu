@@ -817,6 +817,11 @@ int hamr_grid_autotune(hamr_grid* g, void* stream, hamr_tune_report* rep) {
         if ((rc = time_group(g, ph, 0, cs, &rep->ms_seg[c]))) return rc;
     }
     ph.recon_seg = segs[std::min_element(rep->ms_seg, rep->ms_seg + 3) - rep->ms_seg];
+    for (int c = 0; c < 2; c++) {
+        ph.recon_x1_sweep = c;
+        if ((rc = time_group(g, ph, 0, cs, &rep->ms_x1[c]))) return rc;
+    }
+    ph.recon_x1_sweep = (rep->ms_x1[0] < rep->ms_x1[1]) ? 0 : 1;
     for (int c = 0; c < 3; c++) {
         ph.bs_recon = bss[c];
         if ((rc = time_group(g, ph, 0, cs, &rep->ms_recon[c]))) return rc;
@@ -836,7 +841,29 @@ int hamr_grid_autotune(hamr_grid* g, void* stream, hamr_tune_report* rep) {
     rep->bs_recon = ph.bs_recon;
     rep->bs_flux = ph.bs_flux;
     rep->bs_update = ph.bs_update;
+    rep->recon_x1_sweep = ph.recon_x1_sweep;
     g->ph = ph;
+    if (g->amr) return amr_set_phys(g->amr, g->ph);
+    return HAMR_OK;
+}
+
+int hamr_grid_set_launch_shapes(hamr_grid* g, const hamr_tune_report* rep) {
+    if (!g || !rep) return fail(HAMR_EINVAL, "grid and report must not be NULL");
+    auto in = [](int x, std::initializer_list<int> ok) {
+        for (int v : ok)
+            if (x == v) return true;
+        return false;
+    };
+    if (!in(rep->recon_seg, {8, 16, 32}) || !in(rep->recon_x1_sweep, {0, 1}) || !in(rep->bs_recon, {64, 128, 256}) ||
+        !in(rep->bs_flux, {64, 128, 256}) || !in(rep->bs_update, {64, 128}))
+        return fail(HAMR_EINVAL, "launch shapes out of the supported sets");
+    if (g->ph.mlp_img && rep->bs_update != 128) return fail(HAMR_EINVAL, "a grid with a network keeps bs_update 128");
+    CUDA_TRY(cudaDeviceSynchronize());
+    g->ph.recon_seg = rep->recon_seg;
+    g->ph.recon_x1_sweep = rep->recon_x1_sweep;
+    g->ph.bs_recon = rep->bs_recon;
+    g->ph.bs_flux = rep->bs_flux;
+    g->ph.bs_update = rep->bs_update;
     if (g->amr) return amr_set_phys(g->amr, g->ph);
     return HAMR_OK;
 }
@@ -848,6 +875,7 @@ int hamr_grid_launch_shapes(const hamr_grid* g, hamr_tune_report* rep) {
     rep->bs_recon = g->ph.bs_recon;
     rep->bs_flux = g->ph.bs_flux;
     rep->bs_update = g->ph.bs_update;
+    rep->recon_x1_sweep = g->ph.recon_x1_sweep;
     return HAMR_OK;
 }
 

@@ -54,6 +54,7 @@ struct PhysArgs {
     // launch shapes (hamr_grid_autotune): threads per CTA of the reconstruction,
     // flux and cell-update kernels, cells per thread of the x2/x3 sweeps
     int bs_recon, bs_flux, bs_update, recon_seg;
+    int recon_x1_sweep;  // 1: x1 edge values by pencil sweeps (like x2/x3), 0: by warp rows
     int emf;      // HAMR_EMF_*
     int flatten;  // 1: PPM shock flattening (only set with HAMR_RECON_PPM)
     int inversion;  // HAMR_INV_*
@@ -78,10 +79,12 @@ __host__ __device__ inline int smr_width(const BlockView& v, const PhysArgs& ph,
 // RECON_SEG cells per thread; 7 variables each. FP32: one thread per cell.
 constexpr int RECON_TILE = 28;
 constexpr int RECON_SEG = 16;  // default sweep length
-__host__ __device__ inline long recon_threads(const BlockView& v, int dir, int fp32, int seg) {
+constexpr int RECON_X1_SWEEP = 1;  // default form of the x1 edge values
+__host__ __device__ inline long recon_threads(const BlockView& v, int dir, int fp32, int seg, int x1_sweep = 0) {
     const long n1 = v.n1 + 2, n2 = v.n2 + 2, n3 = v.n3 + 2;
     if (fp32) return n1 * n2 * n3;  // one thread per cell
-    if (dir == 1) return ((n1 + RECON_TILE - 1) / RECON_TILE) * 32 * n2 * n3 * 7;
+    if (dir == 1 && !x1_sweep) return ((n1 + RECON_TILE - 1) / RECON_TILE) * 32 * n2 * n3 * 7;
+    if (dir == 1) return n2 * n3 * ((n1 + seg - 1) / seg) * 7;
     if (dir == 2) return n1 * n3 * ((n2 + seg - 1) / seg) * 7;
     return n1 * n2 * ((n3 + seg - 1) / seg) * 7;
 }
@@ -104,6 +107,7 @@ inline void default_launch_shapes(PhysArgs& ph) {
     ph.bs_flux = 128;
     ph.bs_update = 128;
     ph.recon_seg = RECON_SEG;
+    ph.recon_x1_sweep = RECON_X1_SWEEP;
 }
 
 // device scratch/state of one block

@@ -247,10 +247,12 @@ __device__ __forceinline__ void b_recon_row(const BlockView& v, PhysArgs ph, con
 template <int DIR, typename T>
 __device__ __forceinline__ void b_recon_sweep(const BlockView& v, PhysArgs ph, const T* __restrict__ P,
                                               T* __restrict__ QL, T* __restrict__ QR, long t) {
-    const int na = (DIR == 2 ? v.n2 : v.n3) + 2;  // cells along the sweep: -1..n_dir
+    // cells along the sweep: -1..n_dir; across: the two other directions, the faster one first
+    // (x1 for the x2 and x3 sweeps, so that loads and stores coalesce; x2 for the x1 sweep)
+    const int na = (DIR == 1 ? v.n1 : (DIR == 2 ? v.n2 : v.n3)) + 2;
     const int seglen = ph.recon_seg;
     const int nseg = (na + seglen - 1) / seglen;
-    const int n1 = v.n1 + 2, no = (DIR == 2 ? v.n3 : v.n2) + 2;
+    const int n1 = (DIR == 1 ? v.n2 : v.n1) + 2, no = (DIR == 3 ? v.n2 : v.n3) + 2;
     if (t >= (long)n1 * no * nseg * 7) return;
     const int i = (int)(t % n1) - 1;
     long rest = t / n1;
@@ -258,10 +260,10 @@ __device__ __forceinline__ void b_recon_sweep(const BlockView& v, PhysArgs ph, c
     rest /= no;
     const int seg = (int)(rest % nseg);
     const int q = recon_var<DIR>((int)(rest / nseg));
-    const long st = (DIR == 2) ? (long)v.n1p : (long)v.n1p * v.n2p;
+    const long st = (DIR == 1) ? 1L : ((DIR == 2) ? (long)v.n1p : (long)v.n1p * v.n2p);
     const int a0 = seg * seglen - 1;
     const int ncell = min(seglen, na - 1 - a0);           // cells a0 .. a0 + ncell - 1 (<= n_dir)
-    const long c0 = q * v.nc + ((DIR == 2) ? cidx(v, i, a0, o) : cidx(v, i, o, a0));
+    const long c0 = q * v.nc + ((DIR == 1) ? cidx(v, a0, i, o) : ((DIR == 2) ? cidx(v, i, a0, o) : cidx(v, i, o, a0)));
     const T* p = P + c0;
     if (ph.recon == HAMR_RECON_PPM) {
         T qm = p[-st], qc = p[0], qp = p[st];
@@ -334,10 +336,14 @@ __device__ __forceinline__ void b_recon(const BlockView& v, PhysArgs ph, const T
                                         T* __restrict__ QR, long t) {
     if constexpr (!std::is_same<T, double>::value)
         b_recon_cell<DIR>(v, ph, P, QL, QR, t);
-    else if constexpr (DIR == 1)
-        b_recon_row(v, ph, P, QL, QR, t);
-    else
+    else if constexpr (DIR == 1) {
+        if (ph.recon_x1_sweep)
+            b_recon_sweep<1>(v, ph, P, QL, QR, t);
+        else
+            b_recon_row(v, ph, P, QL, QR, t);
+    } else {
         b_recon_sweep<DIR>(v, ph, P, QL, QR, t);
+    }
 }
 
 template <int DIR, typename T>
@@ -1275,7 +1281,7 @@ cudaError_t launch_flatten(const BlockView& v, const PhysArgs& ph, int dir, cons
 
 cudaError_t launch_recon(const BlockView& v, const PhysArgs& ph, int dir, const double* P, const float* P32,
                          double* QL, double* QR, cudaStream_t s) {
-    const long n = recon_threads(v, dir, ph.mixed, ph.recon_seg);
+    const long n = recon_threads(v, dir, ph.mixed, ph.recon_seg, ph.recon_x1_sweep);
     const unsigned nb = nblk(n, ph.bs_recon);
     const int bs = ph.bs_recon;
     if (ph.mixed) {

@@ -68,12 +68,13 @@ class C2PDesc(C.Structure):
 class TuneReport(C.Structure):
     _fields_ = [("recon_seg", C.c_int), ("bs_recon", C.c_int), ("bs_flux", C.c_int), ("bs_update", C.c_int),
                 ("ms_seg", C.c_float * 3), ("ms_recon", C.c_float * 3), ("ms_flux", C.c_float * 3),
-                ("ms_update", C.c_float * 2)]
+                ("ms_update", C.c_float * 2), ("recon_x1_sweep", C.c_int), ("ms_x1", C.c_float * 2)]
 
     def as_dict(self):
         return {"recon_seg": self.recon_seg, "bs_recon": self.bs_recon, "bs_flux": self.bs_flux,
                 "bs_update": self.bs_update, "ms_seg": list(self.ms_seg), "ms_recon": list(self.ms_recon),
-                "ms_flux": list(self.ms_flux), "ms_update": list(self.ms_update)}
+                "ms_flux": list(self.ms_flux), "ms_update": list(self.ms_update),
+                "recon_x1_sweep": self.recon_x1_sweep, "ms_x1": list(self.ms_x1)}
 
 
 class MlpTrainArgs(C.Structure):
@@ -109,6 +110,7 @@ def lib():
         L.hamr_grid_set_timing.argtypes = [P, C.c_int]
         L.hamr_grid_fill_ghosts.argtypes = [P, P]
         L.hamr_grid_block_max.argtypes = [P, C.c_int, D, P]
+        L.hamr_grid_set_launch_shapes.argtypes = [P, C.POINTER(TuneReport)]
         L.hamr_grid_set_fine_dt.argtypes = [P, C.c_double]
         L.hamr_grid_regrid.argtypes = [P, C.c_int, C.POINTER(BlockDesc), P]
         L.hamr_tree_adapt.argtypes = [C.POINTER(BlockDesc), C.c_int, C.POINTER(C.c_int), D, D,
@@ -305,6 +307,14 @@ class Grid:
         r = TuneReport()
         check(lib().hamr_grid_launch_shapes(self.h, C.byref(r)))
         return r.as_dict()
+
+    def set_launch_shapes(self, **shapes):
+        """Sets launch shapes (recon_seg, recon_x1_sweep, bs_recon, bs_flux, bs_update); others kept."""
+        r = TuneReport()
+        check(lib().hamr_grid_launch_shapes(self.h, C.byref(r)))
+        for k, v in shapes.items():
+            setattr(r, k, int(v))
+        check(lib().hamr_grid_set_launch_shapes(self.h, C.byref(r)))
 
     def set_mlp(self, mlp, mode=0):
         """Attach `mlp` to the grid's inversions (None detaches): mode MLP_FIRST (0) starts Newton from

@@ -23,7 +23,8 @@ def _gpu():
 
 
 def _check_report(r):
-    assert r["recon_seg"] in (8, 16, 32)
+    assert r["recon_seg"] in (8, 16, 32) and r["recon_x1_sweep"] in (0, 1)
+    assert all(t > 0.0 for t in r["ms_x1"])
     assert r["bs_recon"] in (64, 128, 256) and r["bs_flux"] in (64, 128, 256) and r["bs_update"] in (64, 128)
     for k in ("ms_seg", "ms_recon", "ms_flux", "ms_update"):
         assert all(t > 0.0 for t in r[k]), (k, r)
@@ -76,3 +77,24 @@ def test_tuned_multiblock_grid_is_bitwise_the_default():
         g.close()
     for (pa, ba), (pb, bb) in zip(*res):
         assert np.array_equal(pa, pb) and np.array_equal(ba, bb)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_every_launch_shape_gives_the_same_bits(precision):
+    """The x1 edge values by warp rows or pencil sweeps, every sweep length and CTA size: the same
+    state bit for bit (the shapes only reorder independent work)."""
+    from paper_1912_10192_gb300 import hamr
+    _, d, prim, bf = torus_case(64, 32, 16, seed=1912)
+    out = []
+    for shapes in (dict(), dict(recon_x1_sweep=0), dict(recon_x1_sweep=1, recon_seg=8, bs_recon=64),
+                   dict(recon_x1_sweep=0, recon_seg=32, bs_recon=256, bs_flux=64, bs_update=64)):
+        b = hamr.block(d.n1, d.n2, d.n3, d.x1min, d.x2min, d.x3min, d.dx1, d.dx2, d.dx3, tuple(d.bc))
+        g = hamr.Grid([b], precision=precision)
+        g.set_launch_shapes(**shapes)
+        g.set_state(torch.from_numpy(prim).cuda(), torch.from_numpy(bf).cuda())
+        for _ in range(3):
+            g.step()
+        out.append(g.get_state())
+        g.close()
+    for p, bb in out[1:]:
+        assert np.array_equal(p, out[0][0]) and np.array_equal(bb, out[0][1])
