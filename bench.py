@@ -40,10 +40,10 @@ WORKLOAD = "FM torus block 256x128x64, Kerr-Schild a=0.9375, r 1.2-50, loop fiel
 # Algorithmic FP64 operations per unit of work, from the flop-counting CPU
 # oracle on the 64x32x16 torus (tests/golden/make_flop_counts.py writes them;
 # tests/test_bench_constants.py checks these copies against it).
-FLOPS_PER_FACE = 325.9           # one HLL face flux from given edge states
-FLOPS_PER_RECON_CELL = 90.16     # one cell's edge values, one direction
+FLOPS_PER_FACE = 318.09          # one HLL face flux from given edge states
+FLOPS_PER_RECON_CELL = 105.18    # one cell's edge values (and a third of its kappa), one direction
 FLOPS_PER_UPDATE_CELL = 694.5    # one cell: U, div F, source, inversion, floors (per stage)
-FLOPS_PER_ZONE_CYCLE = 4549.7    # one cell, one full step
+FLOPS_PER_ZONE_CYCLE = 4605.0    # one cell, one full step
 # Peaks. FP64: nominal GB300 rate (the profiling recipe's 1.25 TFLOP/s); the
 # FMA rate measured by hamr_measure_fp64_peak is reported beside it.
 FP64_NOMINAL_TFLOPS = 1.25

@@ -66,6 +66,7 @@ def _setup(lib):
         "ora_grid_step": [C.c_void_p, C.c_double],
         "ora_grid_stats": [C.c_void_p, C.POINTER(C.c_longlong)],
         "ora_grid_divb": [C.c_void_p, _D],
+        "ora_grid_fluxes": [C.c_void_p, _D],
         "ora_grid_status": [C.c_void_p, _I],
         "ora_flops_reset": [],
         "ora_flops_get": [C.POINTER(C.c_ulonglong)],
@@ -305,6 +306,13 @@ class Grid:
         out = np.zeros(d.n1 * d.n2 * d.n3, dtype=np.int32)
         self.lib.ora_grid_status(self.h, out.ctypes.data_as(_I))
         return out.reshape(d.n3, d.n2, d.n1)
+
+    def fluxes(self):
+        """Face fluxes of the current state, shape (3, 8, n3p, n2p, n1p) (slot 0 mass,
+        5 entropy tracer); the dir-face of cell (i, j, k) lies on its lower side."""
+        out = np.zeros((3, 8, *self.shape))
+        self.lib.ora_grid_fluxes(self.h, _p(out))
+        return out
 
     def divb(self):
         d = self.d

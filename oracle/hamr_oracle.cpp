@@ -240,13 +240,15 @@ static real tmunu(const real* pr, const State& s, int mu, int nu, double gam) {
  * Reading: the flux of B^i in direction j is F*^{ij} = b^i u^j - b^j u^i, the
  * sign that makes U_B = B^i = F*^{it} obey div F* = 0; the printed
  * "b^j u^i - b^i u^j" has the opposite sign. (For dir = 0 this gives B^i.) */
-static void prim_to_uf(const real* pr, const State& s, int dir, double gam, real out[9]) {
+/* kap: the entropy tracer kappa to use (the face value reconstructed from the
+ * cells' kappa, see stage_fluxes); NULL: kappa = p / rho^gam of pr */
+static void prim_to_uf(const real* pr, const State& s, int dir, double gam, real out[9], const real* kap = nullptr) {
     real mass = pr[RHO] * s.ucon[dir];
     out[0] = mass;
     out[1] = tmunu(pr, s, dir, 0, gam) + mass;
     for (int i = 1; i < 4; i++) out[1 + i] = tmunu(pr, s, dir, i, gam);
     real p = (gam - 1.0) * pr[UU];
-    real kappa = p / pow(pr[RHO], gam);
+    real kappa = kap ? *kap : p / pow(pr[RHO], gam);
     out[5] = kappa * mass;
     for (int i = 1; i < 4; i++) out[5 + i] = s.bcon[i] * s.ucon[dir] - s.bcon[dir] * s.ucon[i];
 }
@@ -391,8 +393,9 @@ static int bslot(int dir, int i) { /* flux slot 6/7 of B^i for a dir-face, i != 
  *   cmax = max(0, v+_L, v+_R), cmin = max(0, -v-_L, -v-_R).
  * Reading: when cmax + cmin = 0, F = (F_L + F_R)/2.
  * LLF: c = max(cmax, cmin), F = (F_L + F_R - c (U_R - U_L))/2. */
+/* kap (optional): the entropy tracer kappa on the left and right of the face */
 static void face_flux(const ora_desc& d, const real* pl, const real* pr, const Geom& G, int dir,
-                      real F[NFX]) {
+                      real F[NFX], const real* kap = nullptr) {
     if (G.pole) {
         for (int m = 0; m < NFX; m++) F[m] = 0.0;
         return;
@@ -401,10 +404,10 @@ static void face_flux(const ora_desc& d, const real* pl, const real* pr, const G
     get_state(pl, G, sl);
     get_state(pr, G, sr);
     real Ul[9], Ur[9], Fl[9], Fr[9];
-    prim_to_uf(pl, sl, 0, d.gam, Ul);
-    prim_to_uf(pl, sl, dir, d.gam, Fl);
-    prim_to_uf(pr, sr, 0, d.gam, Ur);
-    prim_to_uf(pr, sr, dir, d.gam, Fr);
+    prim_to_uf(pl, sl, 0, d.gam, Ul, kap);
+    prim_to_uf(pl, sl, dir, d.gam, Fl, kap);
+    prim_to_uf(pr, sr, 0, d.gam, Ur, kap ? kap + 1 : nullptr);
+    prim_to_uf(pr, sr, dir, d.gam, Fr, kap ? kap + 1 : nullptr);
     real vpl, vml, vpr, vmr;
     vchar(pl, sl, G, dir, d.gam, &vpl, &vml);
     vchar(pr, sr, G, dir, d.gam, &vpr, &vmr);
@@ -956,6 +959,15 @@ void stage_fluxes(ora_grid* g, const double* Pf, const double* Bff, Fluxes& F) {
     const int nn[4] = {0, d.n1, d.n2, d.n3};
     for (int dir = 1; dir <= 3; dir++) F[dir].assign((size_t)NFX * nc, 0.0);
 
+    /* the entropy tracer kappa = p / rho^gam of every cell, ghosts included: the
+     * face fluxes take reconstructed values of it, like the primitives (reading:
+     * the paper leaves the face value of kappa open; this takes one power per
+     * cell, not one per face side) */
+    phase_begin();
+    std::vector<real> kcell((size_t)nc);
+    for (long c = 0; c < nc; c++) kcell[c] = (d.gam - 1.0) * real(Pf[UU * nc + c]) / pow(real(Pf[RHO * nc + c]), d.gam);
+    phase_end(0);
+
     /* fluxes: dir-faces over the interior faces, one transverse ghost layer */
     for (int dir = 1; dir <= 3; dir++) {
         int lo[4], hi[4]; /* inclusive face/cell ranges */
@@ -965,7 +977,7 @@ void stage_fluxes(ora_grid* g, const double* Pf, const double* Bff, Fluxes& F) {
         }
         int L = nn[dir] + 2 * NG;
         std::vector<real> q(L), al(L), ar(L);
-        std::vector<real> PL((size_t)NPR * L), PR((size_t)NPR * L);
+        std::vector<real> PL((size_t)NPR * L), PR((size_t)NPR * L), KL(L), KR(L);
         /* loop over lines along dir */
         int ta = (dir == 1) ? 2 : 1, tb = (dir == 3) ? 2 : 3;
         std::vector<real> flat(L, real(0.0));
@@ -1001,6 +1013,15 @@ void stage_fluxes(ora_grid* g, const double* Pf, const double* Bff, Fluxes& F) {
                         PR[(size_t)v * L + c] = ar[c];
                     }
                 }
+                for (int c = 0; c < L; c++) {  /* the cells' kappa along the line */
+                    int ii[4];
+                    ii[dir] = c - NG;
+                    ii[ta] = a;
+                    ii[tb] = b;
+                    q[c] = kcell[cidx(g, ii[1], ii[2], ii[3])];
+                }
+                recon_line_impl(d.recon, L, q.data(), KL.data(), KR.data(),
+                                (d.flatten && d.recon == ORA_RECON_PPM) ? flat.data() : nullptr);
                 phase_end(0);
                 phase_begin();
                 for (int f = lo[dir]; f <= hi[dir]; f++) {
@@ -1026,7 +1047,8 @@ void stage_fluxes(ora_grid* g, const double* Pf, const double* Bff, Fluxes& F) {
                         real bn = real(Bff[(dir - 1) * nc + fi]) / G.gdet;
                         pl[B1 + dir - 1] = bn;
                         pr[B1 + dir - 1] = bn;
-                        face_flux(d, pl, pr, G, dir, fx);
+                        const real kap[2] = {KR[cl], KL[cr]};
+                        face_flux(d, pl, pr, G, dir, fx, kap);
                     }
                     for (int m = 0; m < NFX; m++) F[dir][(size_t)m * nc + fi] = tod(fx[m]);
                 }
@@ -1741,6 +1763,14 @@ void ora_grid_status(const ora_grid* g, int* out) {
     for (int k = 0; k < d.n3; k++)
         for (int j = 0; j < d.n2; j++)
             for (int i = 0; i < d.n1; i++) out[o++] = g->status[cidx(g, i, j, k)];
+}
+
+void ora_grid_fluxes(ora_grid* g, double* out) {
+    apply_bc(g, g->prim.data(), g->bface.data());
+    Fluxes F;
+    stage_fluxes(g, g->prim.data(), g->bface.data(), F);
+    const size_t n = (size_t)NFX * g->ncell;
+    for (int dir = 1; dir <= 3; dir++) std::copy(F[dir].begin(), F[dir].end(), out + (dir - 1) * n);
 }
 
 /* discrete div B per interior cell: sum_d (Bbar^d_hi - Bbar^d_lo)/dx^d */

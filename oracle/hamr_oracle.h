@@ -93,6 +93,12 @@ double ora_grid_step(ora_grid* g, double dt);
 void ora_grid_stats(const ora_grid* g, long long* counts4);
 void ora_grid_divb(const ora_grid* g, double* divb_cells);
 void ora_grid_status(const ora_grid* g, int* status_cells);
+/* face fluxes of the current state (ghosts filled first) as a stage computes
+ * them: out[d][m][cell] for face direction d = 0..2 and slot m = 0..7 (0..5
+ * the conserved variables, 5 the entropy tracer), padded-block layout; a
+ * dir-face at cell index (i, j, k) is the face at i - 1/2 (dir 1) etc.;
+ * faces outside the computed range are 0 */
+void ora_grid_fluxes(ora_grid* g, double* out);
 
 /* ---- multi-block grid: static refinement + local adaptive time steps ----
  * Blocks tile the domain; a face with bc ORA_BC_BLOCK takes its ghosts from
