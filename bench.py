@@ -50,7 +50,7 @@ FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes per launch of the dominant kernel group, from one ncu capture
 # of this build's x1-face flux kernel (the x2 and x3 kernels move the same
 # field sizes).
-NCU_TRAFFIC_PER_LAUNCH = 392.2e6
+NCU_TRAFFIC_PER_LAUNCH = 429.3e6
 
 
 def env_rank():

@@ -1352,6 +1352,7 @@ int group_step(AmrImpl& M, int L, int s, cudaStream_t cs) {
         k_ghost_faces<<<dim3(nb_(3 * M.lmw_pad[L]), nl), BSA, 0, cs>>>(M.H.A, list, sigma, s);
         AM_TRY(cudaGetLastError());
         if (ph.mixed) AM_TRY(launch_to_f32_batch(tab, list, nl, M.lmw_pad[L], sigma, cs));
+        AM_TRY(launch_kappa_batch(tab, list, nl, M.lmw_pad[L], ph, sigma, cs));
         for (int dir = 1; dir <= 3; dir++) {
             if (ph.flatten) AM_TRY(launch_flatten_batch(tab, list, nl, M.lmw_ext[L], ph, dir, sigma, cs));
             AM_TRY(launch_recon_batch(tab, list, nl, M.lmw_recon[L][dir], ph, dir, sigma, cs));
@@ -1509,6 +1510,15 @@ int amr_time_group(AmrImpl* M, const PhysArgs& ph, int which, cudaStream_t cs, f
         if (ph.mixed) {
             cudaError_t e = launch_to_f32_batch(tab, list, nl, M->lmw_pad[L], 0, cs);
             if (e != cudaSuccess) rc = set_error(HAMR_ECUDA, "launch failed: %s", cudaGetErrorString(e));
+        }
+        if (rc == HAMR_OK) {
+            auto kap = [&]() { return launch_kappa_batch(tab, list, nl, M->lmw_pad[L], ph, 0, cs); };
+            if (which == 0) {
+                rc = timed(kap);
+            } else {
+                cudaError_t e = kap();
+                if (e != cudaSuccess) rc = set_error(HAMR_ECUDA, "launch failed: %s", cudaGetErrorString(e));
+            }
         }
         for (int dir = 1; dir <= 3 && rc == HAMR_OK; dir++) {
             auto rec = [&]() {

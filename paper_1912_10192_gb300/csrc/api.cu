@@ -460,9 +460,10 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
     // predictor: P^n, B^n -> P^{n+1/2}, B^{n+1/2}
     LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.P, s.B, cs));
     if (ph.mixed) LAUNCH(g, K_BC, 1, cs, launch_to_f32(v, s.P, s.P32, cs));
+    LAUNCH(g, K_RECON, 1, cs, launch_kappa(v, ph, s.P, s.P32, s.E, cs));
     for (int dir = 1; dir <= 3; dir++) {
-        if (ph.flatten) LAUNCH(g, K_RECON, 1, cs, launch_flatten(v, ph, dir, s.P, s.P32, s.QL, cs));
-        LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.P, s.P32, s.QL, s.QR, cs));
+        if (ph.flatten) LAUNCH(g, K_RECON, 1, cs, launch_flatten(v, ph, dir, s.P, s.P32, s.F[dir - 1], cs));
+        LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.P, s.P32, s.E, s.F[dir - 1], s.QL, s.QR, cs));
         LAUNCH(g, K_FLUX, 1, cs, launch_flux(v, ph, dir, s.QL, s.QR, s.B, s.F[dir - 1], cs));
     }
     LAUNCH(g, K_EMF, ph.emf ? 2 : 1, cs, launch_emf(v, s.F, s.E, ph.mixed, s.P, ph.emf ? s.QL : nullptr, cs));
@@ -475,9 +476,10 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
     // corrector: U^n and the fluxes of P^{n+1/2} -> P^{n+1}, B^{n+1} (in place)
     LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.Ph, s.Bh, cs));
     if (ph.mixed) LAUNCH(g, K_BC, 1, cs, launch_to_f32(v, s.Ph, s.P32, cs));
+    LAUNCH(g, K_RECON, 1, cs, launch_kappa(v, ph, s.Ph, s.P32, s.E, cs));
     for (int dir = 1; dir <= 3; dir++) {
-        if (ph.flatten) LAUNCH(g, K_RECON, 1, cs, launch_flatten(v, ph, dir, s.Ph, s.P32, s.QL, cs));
-        LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.Ph, s.P32, s.QL, s.QR, cs));
+        if (ph.flatten) LAUNCH(g, K_RECON, 1, cs, launch_flatten(v, ph, dir, s.Ph, s.P32, s.F[dir - 1], cs));
+        LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.Ph, s.P32, s.E, s.F[dir - 1], s.QL, s.QR, cs));
         LAUNCH(g, K_FLUX, 1, cs, launch_flux(v, ph, dir, s.QL, s.QR, s.Bh, s.F[dir - 1], cs));
     }
     LAUNCH(g, K_EMF, ph.emf ? 2 : 1, cs, launch_emf(v, s.F, s.E, ph.mixed, s.Ph, ph.emf ? s.QL : nullptr, cs));
@@ -755,10 +757,19 @@ int time_group_block(hamr_grid* g, const PhysArgs& ph, int which, cudaStream_t c
         BlockState& s = g->st[k];
         const BlockView& v = g->view[k];
         if (ph.mixed) CUDA_TRY(launch_to_f32(v, s.P, s.P32, cs));
+        if (which == 0) CUDA_TRY(cudaEventRecord(a, cs));
+        CUDA_TRY(launch_kappa(v, ph, s.P, s.P32, s.E, cs));
+        if (which == 0) {
+            float t = 0.0f;
+            CUDA_TRY(cudaEventRecord(b, cs));
+            CUDA_TRY(cudaEventSynchronize(b));
+            CUDA_TRY(cudaEventElapsedTime(&t, a, b));
+            total += t;
+        }
         for (int dir = 1; dir <= 3; dir++) {
             if (which == 0) CUDA_TRY(cudaEventRecord(a, cs));
-            if (ph.flatten) CUDA_TRY(launch_flatten(v, ph, dir, s.P, s.P32, s.QL, cs));
-            CUDA_TRY(launch_recon(v, ph, dir, s.P, s.P32, s.QL, s.QR, cs));
+            if (ph.flatten) CUDA_TRY(launch_flatten(v, ph, dir, s.P, s.P32, s.F[dir - 1], cs));
+            CUDA_TRY(launch_recon(v, ph, dir, s.P, s.P32, s.E, s.F[dir - 1], s.QL, s.QR, cs));
             if (which == 1) CUDA_TRY(cudaEventRecord(a, cs));
             if (which != 0) CUDA_TRY(launch_flux(v, ph, dir, s.QL, s.QR, s.B, s.F[dir - 1], cs));
             if (which <= 1) {

@@ -83,10 +83,11 @@ constexpr int RECON_X1_SWEEP = 1;  // default form of the x1 edge values
 __host__ __device__ inline long recon_threads(const BlockView& v, int dir, int fp32, int seg, int x1_sweep = 0) {
     const long n1 = v.n1 + 2, n2 = v.n2 + 2, n3 = v.n3 + 2;
     if (fp32) return n1 * n2 * n3;  // one thread per cell
-    if (dir == 1 && !x1_sweep) return ((n1 + RECON_TILE - 1) / RECON_TILE) * 32 * n2 * n3 * 7;
-    if (dir == 1) return n2 * n3 * ((n1 + seg - 1) / seg) * 7;
-    if (dir == 2) return n1 * n3 * ((n2 + seg - 1) / seg) * 7;
-    return n1 * n2 * ((n3 + seg - 1) / seg) * 7;
+    // 8 variables: the 7 primitives other than B^dir and the entropy tracer
+    if (dir == 1 && !x1_sweep) return ((n1 + RECON_TILE - 1) / RECON_TILE) * 32 * n2 * n3 * 8;
+    if (dir == 1) return n2 * n3 * ((n1 + seg - 1) / seg) * 8;
+    if (dir == 2) return n1 * n3 * ((n2 + seg - 1) / seg) * 8;
+    return n1 * n2 * ((n3 + seg - 1) / seg) * 8;
 }
 // monotone map of (non-NaN) doubles to unsigned integers and back: maxima by atomicMax
 __host__ __device__ inline unsigned long long ordered_bits(double x) {
@@ -167,12 +168,18 @@ cudaError_t launch_centre_b(const BlockView& v, double* P, const double* B, cuda
 // atomicMax of ordered_bits(P[q]) over the interior cells into *out (initialise to 0)
 cudaError_t launch_block_max(const BlockView& v, const double* P, int q, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_bc(const BlockView& v, double* P, double* B, cudaStream_t s);
+// entropy tracer kappa = p / rho^gam of every padded cell into K (FP32 view of K when mixed)
+cudaError_t launch_kappa(const BlockView& v, const PhysArgs& ph, const double* P, const float* P32, double* K,
+                         cudaStream_t s);
+// edge values of direction dir: the 7 primitives other than B^dir into their fields of QL / QR,
+// kappa (from K) into the B^dir fields; Fl: the flattening coefficients (when ph.flatten)
 cudaError_t launch_recon(const BlockView& v, const PhysArgs& ph, int dir, const double* P, const float* P32,
-                         double* QL, double* QR, cudaStream_t s);
+                         const double* K, const double* Fl, double* QL, double* QR, cudaStream_t s);
 cudaError_t launch_to_f32(const BlockView& v, const double* P, float* P32, cudaStream_t s);
-// PPM shock-flattening coefficients of direction dir into the B^dir field of QL (before launch_recon)
+// PPM shock-flattening coefficients of direction dir into Fl (field 0 of the dir-flux array,
+// which launch_flux overwrites after launch_recon has read it)
 cudaError_t launch_flatten(const BlockView& v, const PhysArgs& ph, int dir, const double* P, const float* P32,
-                           double* QL, cudaStream_t s);
+                           double* Fl, cudaStream_t s);
 cudaError_t launch_flux(const BlockView& v, const PhysArgs& ph, int dir, const double* QL, const double* QR,
                         const double* Bf, double* F, cudaStream_t s);
 // upwinded EMFs when Ec (3 fields of scratch, stride nc) is given: the cell EMFs of P go there first
@@ -201,6 +208,9 @@ cudaError_t measure_fp64_peak(cudaStream_t s, double* gflops);
 // step.cu, batched over the blocks list[0..nlist) of a table (sigma: 0 predictor, 1 corrector)
 cudaError_t launch_to_f32_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, int sigma,
                                 cudaStream_t s);
+// kappa of each listed block into field 0 of its EMF array (maxwork: largest padded cell count)
+cudaError_t launch_kappa_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
+                               int sigma, cudaStream_t s);
 cudaError_t launch_recon_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
                                int dir, int sigma, cudaStream_t s);
 // maxcells: largest (n1 + 2)(n2 + 2)(n3 + 2) of the listed blocks

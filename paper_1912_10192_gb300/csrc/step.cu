@@ -133,7 +133,9 @@ __global__ void k_bc_axis(BlockView v, double* __restrict__ B) {
 
 // ---------------------------------------------------------------- reconstruction
 // Edge values of every cell that borders a flux face of direction dir: cells
-// -1..n_dir along dir, -1..n_e across, for the 7 primitives other than B^dir.
+// -1..n_dir along dir, -1..n_e across, for the 7 primitives other than B^dir
+// and the entropy tracer kappa of the cells (an eighth variable, read from K,
+// whose edge values go to the B^dir fields of QL and QR).
 // Every slope and every PPM interface value is formed once and shared by the
 // two cells that use it: along x1 a warp holds 32 consecutive cells (28 of
 // them produced) and passes values between lanes by shuffles; along x2 and
@@ -149,9 +151,10 @@ __global__ void k_bc_axis(BlockView v, double* __restrict__ B) {
 // magnitude: at a narrow pressure peak dp2 is zero up to rounding, and a
 // signed ratio would follow the rounding noise). The coefficient stays with its cell
 // (no max with the upwind neighbour: its stencil would pass three ghost
-// layers). It is written to the B^dir field of QL, which the reconstruction
-// of dir leaves unused; the reconstruction blends both interface values of
-// the cell toward its value, f q + (1 - f) a, before the parabola constraints.
+// layers). It is written to field 0 of the dir-flux array, which the flux
+// kernel of dir fills only afterwards; the reconstruction blends both
+// interface values of the cell toward its value, f q + (1 - f) a, before the
+// parabola constraints.
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 
@@ -195,6 +198,21 @@ __device__ __forceinline__ void flatten_edges(T f, T qc, T& l, T& r) {
     r = f * qc + (T(1) - f) * r;
 }
 
+// entropy tracer kappa = p / rho^gam of every padded cell into K: one power per
+// cell; the reconstruction carries kappa to the faces like a primitive
+template <typename T>
+__device__ __forceinline__ void b_kappa(const BlockView& v, T gam, const T* __restrict__ P, T* __restrict__ K,
+                                        long t) {
+    const long n = (long)v.n1p * v.n2p * v.n3p;
+    if (t >= n) return;
+    K[t] = (gam - T(1)) * P[UU * v.nc + t] * pow_pos(P[RHO * v.nc + t], -gam);
+}
+
+template <typename T>
+__global__ void k_kappa(BlockView v, T gam, const T* __restrict__ P, T* __restrict__ K) {
+    b_kappa<T>(v, gam, P, K, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 template <int DIR>
 __device__ __forceinline__ int recon_var(int n) {  // the n-th of the 7 reconstructed primitives
     return n + (n >= B1 + DIR - 1 ? 1 : 0);
@@ -205,24 +223,36 @@ __device__ __forceinline__ T limited_slope(int recon, T qm, T q0, T qp) {
     return (recon == HAMR_RECON_MC) ? mc_slope_i(qm, q0, qp) : minmod_slope_i(qm, q0, qp);
 }
 
+// the n-th reconstructed variable's source field and its edge-value field
+template <int DIR, typename T>
+__device__ __forceinline__ const T* recon_src(const BlockView& v, int n, const T* P, const T* K) {
+    return (n < 7) ? P + (long)recon_var<DIR>(n) * v.nc : K;
+}
+template <int DIR>
+__device__ __forceinline__ int recon_dst(int n) {
+    return (n < 7) ? recon_var<DIR>(n) : B1 + DIR - 1;
+}
+
 template <typename T>
 __device__ __forceinline__ void b_recon_row(const BlockView& v, PhysArgs ph, const T* __restrict__ P,
+                                            const T* __restrict__ K, const T* __restrict__ Fl,
                                             T* __restrict__ QL, T* __restrict__ QR, long t) {
     const int n2 = v.n2 + 2, n3 = v.n3 + 2;
     const int ntile = (v.n1 + 2 + RECON_TILE - 1) / RECON_TILE;
     const long w = t >> 5;  // whole warps leave or stay together
-    if (w >= (long)ntile * n2 * n3 * 7) return;
+    if (w >= (long)ntile * n2 * n3 * 8) return;
     const int lane = (int)(t & 31);
     const int tile = (int)(w % ntile);
     long rest = w / ntile;
     const int j = (int)(rest % n2) - 1;
     rest /= n2;
     const int k = (int)(rest % n3) - 1;
-    const int q = recon_var<1>((int)(rest / n3));
+    const int nv = (int)(rest / n3);
+    const int q = recon_dst<1>(nv);
     const int i = RECON_TILE * tile - 3 + lane;               // lanes 2..29 produce cells tile*28-1 .. +27
     const int ic = min(max(i, -NG), v.n1 + NG - 1);           // loads stay inside the padded row
     const long c = cidx(v, 0, j, k);
-    const T qc = P[q * v.nc + c + ic];
+    const T qc = recon_src<1>(v, nv, P, K)[c + ic];
     const T qm = __shfl_up_sync(0xffffffffu, qc, 1);
     const T qp = __shfl_down_sync(0xffffffffu, qc, 1);
     T l, r;
@@ -231,7 +261,7 @@ __device__ __forceinline__ void b_recon_row(const BlockView& v, PhysArgs ph, con
         const T sp = __shfl_down_sync(0xffffffffu, sc, 1);
         r = ppm_face(qc, qp, sc, sp);                         // interface i+1/2, valid on lanes 1..29
         l = __shfl_up_sync(0xffffffffu, r, 1);                // interface i-1/2, valid on lanes 2..30
-        if (ph.flatten) flatten_edges(QL[(B1 + 0) * v.nc + c + ic], qc, l, r);
+        if (ph.flatten) flatten_edges(Fl[c + ic], qc, l, r);
         ppm_limit(qc, l, r);
     } else {
         const T dq = limited_slope(ph.recon, qm, qc, qp);
@@ -246,6 +276,7 @@ __device__ __forceinline__ void b_recon_row(const BlockView& v, PhysArgs ph, con
 
 template <int DIR, typename T>
 __device__ __forceinline__ void b_recon_sweep(const BlockView& v, PhysArgs ph, const T* __restrict__ P,
+                                              const T* __restrict__ K, const T* __restrict__ Fl,
                                               T* __restrict__ QL, T* __restrict__ QR, long t) {
     // cells along the sweep: -1..n_dir; across: the two other directions, the faster one first
     // (x1 for the x2 and x3 sweeps, so that loads and stores coalesce; x2 for the x1 sweep)
@@ -253,18 +284,19 @@ __device__ __forceinline__ void b_recon_sweep(const BlockView& v, PhysArgs ph, c
     const int seglen = ph.recon_seg;
     const int nseg = (na + seglen - 1) / seglen;
     const int n1 = (DIR == 1 ? v.n2 : v.n1) + 2, no = (DIR == 3 ? v.n2 : v.n3) + 2;
-    if (t >= (long)n1 * no * nseg * 7) return;
+    if (t >= (long)n1 * no * nseg * 8) return;
     const int i = (int)(t % n1) - 1;
     long rest = t / n1;
     const int o = (int)(rest % no) - 1;
     rest /= no;
     const int seg = (int)(rest % nseg);
-    const int q = recon_var<DIR>((int)(rest / nseg));
+    const int nv = (int)(rest / nseg);
     const long st = (DIR == 1) ? 1L : ((DIR == 2) ? (long)v.n1p : (long)v.n1p * v.n2p);
     const int a0 = seg * seglen - 1;
     const int ncell = min(seglen, na - 1 - a0);           // cells a0 .. a0 + ncell - 1 (<= n_dir)
-    const long c0 = q * v.nc + ((DIR == 1) ? cidx(v, a0, i, o) : ((DIR == 2) ? cidx(v, i, a0, o) : cidx(v, i, o, a0)));
-    const T* p = P + c0;
+    const long co = (DIR == 1) ? cidx(v, a0, i, o) : ((DIR == 2) ? cidx(v, i, a0, o) : cidx(v, i, o, a0));
+    const long c0 = (long)recon_dst<DIR>(nv) * v.nc + co;
+    const T* p = recon_src<DIR>(v, nv, P, K) + co;
     if (ph.recon == HAMR_RECON_PPM) {
         T qm = p[-st], qc = p[0], qp = p[st];
         T sm = mc_slope_i(p[-2 * st], qm, qc);
@@ -275,7 +307,7 @@ __device__ __forceinline__ void b_recon_sweep(const BlockView& v, PhysArgs ph, c
             const T sp = mc_slope_i(qc, qp, qpp);
             const T fr = ppm_face(qc, qp, sc, sp);  // interface a + 1/2
             T l = fl, r = fr;
-            if (ph.flatten) flatten_edges(QL[(B1 + DIR - 1) * v.nc + c0 - q * v.nc + m * st], qc, l, r);
+            if (ph.flatten) flatten_edges(Fl[co + m * st], qc, l, r);
             ppm_limit(qc, l, r);
             QL[c0 + m * st] = l;
             QR[c0 + m * st] = r;
@@ -301,6 +333,7 @@ __device__ __forceinline__ void b_recon_sweep(const BlockView& v, PhysArgs ph, c
 // the loads, and a thread per cell keeps more loads in flight than a sweep)
 template <int DIR, typename T>
 __device__ __forceinline__ void b_recon_cell(const BlockView& v, PhysArgs ph, const T* __restrict__ P,
+                                             const T* __restrict__ K, const T* __restrict__ Fl,
                                              T* __restrict__ QL, T* __restrict__ QR, long t) {
     const int e1 = v.n1 + 2, e2 = v.n2 + 2, e3 = v.n3 + 2;
     if (t >= (long)e1 * e2 * e3) return;
@@ -308,9 +341,9 @@ __device__ __forceinline__ void b_recon_cell(const BlockView& v, PhysArgs ph, co
     const long c = cidx(v, i, j, k);
     const long st = (DIR == 1) ? 1 : ((DIR == 2) ? (long)v.n1p : (long)v.n1p * v.n2p);
 #pragma unroll
-    for (int n = 0; n < 7; n++) {
-        const int q = recon_var<DIR>(n);
-        const T* p = P + q * v.nc + c;
+    for (int n = 0; n < 8; n++) {
+        const int q = recon_dst<DIR>(n);
+        const T* p = recon_src<DIR>(v, n, P, K) + c;
         T l, r;
         if (ph.recon == HAMR_RECON_PPM) {
             const T qm = p[-st], qc = p[0], qp = p[st];
@@ -318,7 +351,7 @@ __device__ __forceinline__ void b_recon_cell(const BlockView& v, PhysArgs ph, co
                     sp = mc_slope_i(qc, qp, p[2 * st]);
             l = ppm_face(qm, qc, sm, sc);
             r = ppm_face(qc, qp, sc, sp);
-            if (ph.flatten) flatten_edges(QL[(B1 + DIR - 1) * v.nc + c], qc, l, r);
+            if (ph.flatten) flatten_edges(Fl[c], qc, l, r);
             ppm_limit(qc, l, r);
         } else {
             const T dq = limited_slope(ph.recon, p[-st], p[0], p[st]);
@@ -332,23 +365,25 @@ __device__ __forceinline__ void b_recon_cell(const BlockView& v, PhysArgs ph, co
 
 // FP64: the non-redundant row and pencil forms; FP32: one thread per cell
 template <int DIR, typename T>
-__device__ __forceinline__ void b_recon(const BlockView& v, PhysArgs ph, const T* __restrict__ P, T* __restrict__ QL,
+__device__ __forceinline__ void b_recon(const BlockView& v, PhysArgs ph, const T* __restrict__ P,
+                                        const T* __restrict__ K, const T* __restrict__ Fl, T* __restrict__ QL,
                                         T* __restrict__ QR, long t) {
     if constexpr (!std::is_same<T, double>::value)
-        b_recon_cell<DIR>(v, ph, P, QL, QR, t);
+        b_recon_cell<DIR>(v, ph, P, K, Fl, QL, QR, t);
     else if constexpr (DIR == 1) {
         if (ph.recon_x1_sweep)
-            b_recon_sweep<1>(v, ph, P, QL, QR, t);
+            b_recon_sweep<1>(v, ph, P, K, Fl, QL, QR, t);
         else
-            b_recon_row(v, ph, P, QL, QR, t);
+            b_recon_row(v, ph, P, K, Fl, QL, QR, t);
     } else {
-        b_recon_sweep<DIR>(v, ph, P, QL, QR, t);
+        b_recon_sweep<DIR>(v, ph, P, K, Fl, QL, QR, t);
     }
 }
 
 template <int DIR, typename T>
-__global__ void k_recon(BlockView v, PhysArgs ph, const T* __restrict__ P, T* __restrict__ QL, T* __restrict__ QR) {
-    b_recon<DIR, T>(v, ph, P, QL, QR, (long)blockIdx.x * blockDim.x + threadIdx.x);
+__global__ void k_recon(BlockView v, PhysArgs ph, const T* __restrict__ P, const T* __restrict__ K,
+                        const T* __restrict__ Fl, T* __restrict__ QL, T* __restrict__ QR) {
+    b_recon<DIR, T>(v, ph, P, K, Fl, QL, QR, (long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // FP32 copy of the 8 primitive fields over the whole padded block (mixed precision)
@@ -407,23 +442,23 @@ __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const T*
     const T bn = (T)Bf[(DIR - 1) * v.nc + c] / m.gdet;
     pl[B1 + DIR - 1] = bn;
     pr[B1 + DIR - 1] = bn;
+    // the entropy tracer's edge values sit in the B^dir fields
+    const T kapl = QR[(B1 + DIR - 1) * v.nc + c - st], kapr = QL[(B1 + DIR - 1) * v.nc + c];
     const T gam = (T)ph.gam;
     T UL[NFLUX], FL[NFLUX], UR[NFLUX], FR[NFLUX];
     T vpl, vml, vpr, vmr;
     {
         Fluid<T> s;
         fluid_state(pl, m, s);
-        const T kap = entropy_kappa(pl, gam);
-        flux_row(pl, s, 0, DIR, gam, kap, UL);
-        flux_row(pl, s, DIR, DIR, gam, kap, FL);
+        flux_row(pl, s, 0, DIR, gam, kapl, UL);
+        flux_row(pl, s, DIR, DIR, gam, kapl, FL);
         wave_speeds(pl, s, m, DIR, gam, vpl, vml);
     }
     {
         Fluid<T> s;
         fluid_state(pr, m, s);
-        const T kap = entropy_kappa(pr, gam);
-        flux_row(pr, s, 0, DIR, gam, kap, UR);
-        flux_row(pr, s, DIR, DIR, gam, kap, FR);
+        flux_row(pr, s, 0, DIR, gam, kapr, UR);
+        flux_row(pr, s, DIR, DIR, gam, kapr, FR);
         wave_speeds(pr, s, m, DIR, gam, vpr, vmr);
     }
     // U's B slots: B^i for the transverse i (flux_row with d = 0 gives b^i u^t - b^t u^i = B^i)
@@ -953,22 +988,36 @@ __global__ void k_dt_select(double cour, double user_dt, double* dscal, unsigned
 // threadIdx.x index the work inside it exactly as in the single-block kernels.
 __device__ __forceinline__ long tidx() { return (long)blockIdx.x * blockDim.x + threadIdx.x; }
 
+// kappa goes to field 0 of the EMF array (free until the EMFs), the flattening
+// coefficients of dir to field 0 of the dir-flux array
 template <int DIR, typename T>
 __global__ void kb_recon(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
     const DevBlock& D = tab[list[blockIdx.y]];
+    const double* Fl = (DIR == 1) ? D.F1 : ((DIR == 2) ? D.F2 : D.F3);
     if constexpr (std::is_same<T, double>::value)
-        b_recon<DIR, T>(D.v, ph, sigma ? D.Ph : D.P, D.QL, D.QR, tidx());
+        b_recon<DIR, T>(D.v, ph, sigma ? D.Ph : D.P, D.E, Fl, D.QL, D.QR, tidx());
     else  // the FP32 copy holds the stage's state
-        b_recon<DIR, T>(D.v, ph, D.P32, reinterpret_cast<float*>(D.QL), reinterpret_cast<float*>(D.QR), tidx());
+        b_recon<DIR, T>(D.v, ph, D.P32, reinterpret_cast<const float*>(D.E), reinterpret_cast<const float*>(Fl),
+                        reinterpret_cast<float*>(D.QL), reinterpret_cast<float*>(D.QR), tidx());
 }
 
 template <int DIR, typename T>
 __global__ void kb_flatten(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
     const DevBlock& D = tab[list[blockIdx.y]];
+    double* Fl = (DIR == 1) ? D.F1 : ((DIR == 2) ? D.F2 : D.F3);
     if constexpr (std::is_same<T, double>::value)
-        b_flatten<DIR, T>(D.v, ph, sigma ? D.Ph : D.P, D.QL + (long)(B1 + DIR - 1) * D.v.nc, tidx());
+        b_flatten<DIR, T>(D.v, ph, sigma ? D.Ph : D.P, Fl, tidx());
     else
-        b_flatten<DIR, T>(D.v, ph, D.P32, reinterpret_cast<float*>(D.QL) + (long)(B1 + DIR - 1) * D.v.nc, tidx());
+        b_flatten<DIR, T>(D.v, ph, D.P32, reinterpret_cast<float*>(Fl), tidx());
+}
+
+template <typename T>
+__global__ void kb_kappa(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
+    const DevBlock& D = tab[list[blockIdx.y]];
+    if constexpr (std::is_same<T, double>::value)
+        b_kappa<T>(D.v, ph.gam, sigma ? D.Ph : D.P, D.E, tidx());
+    else
+        b_kappa<T>(D.v, (float)ph.gam, D.P32, reinterpret_cast<float*>(D.E), tidx());
 }
 
 __global__ void kb_to_f32(const DevBlock* tab, const int* list, int sigma) {
@@ -1263,37 +1312,48 @@ cudaError_t launch_bc(const BlockView& v, double* P, double* B, cudaStream_t s) 
 }
 
 cudaError_t launch_flatten(const BlockView& v, const PhysArgs& ph, int dir, const double* P, const float* P32,
-                           double* QL, cudaStream_t s) {
+                           double* Fl, cudaStream_t s) {
     const long n = (long)(v.n1 + 2) * (v.n2 + 2) * (v.n3 + 2);
-    const long off = (long)(B1 + dir - 1) * v.nc;
     if (ph.mixed) {
-        float* F = reinterpret_cast<float*>(QL) + off;
+        float* F = reinterpret_cast<float*>(Fl);
         if (dir == 1) k_flatten<1, float><<<nblk(n), BS, 0, s>>>(v, ph, P32, F);
         if (dir == 2) k_flatten<2, float><<<nblk(n), BS, 0, s>>>(v, ph, P32, F);
         if (dir == 3) k_flatten<3, float><<<nblk(n), BS, 0, s>>>(v, ph, P32, F);
     } else {
-        if (dir == 1) k_flatten<1, double><<<nblk(n), BS, 0, s>>>(v, ph, P, QL + off);
-        if (dir == 2) k_flatten<2, double><<<nblk(n), BS, 0, s>>>(v, ph, P, QL + off);
-        if (dir == 3) k_flatten<3, double><<<nblk(n), BS, 0, s>>>(v, ph, P, QL + off);
+        if (dir == 1) k_flatten<1, double><<<nblk(n), BS, 0, s>>>(v, ph, P, Fl);
+        if (dir == 2) k_flatten<2, double><<<nblk(n), BS, 0, s>>>(v, ph, P, Fl);
+        if (dir == 3) k_flatten<3, double><<<nblk(n), BS, 0, s>>>(v, ph, P, Fl);
     }
     return cudaGetLastError();
 }
 
+cudaError_t launch_kappa(const BlockView& v, const PhysArgs& ph, const double* P, const float* P32, double* K,
+                         cudaStream_t s) {
+    const long n = (long)v.n1p * v.n2p * v.n3p;
+    if (ph.mixed)
+        k_kappa<float><<<nblk(n), BS, 0, s>>>(v, (float)ph.gam, P32, reinterpret_cast<float*>(K));
+    else
+        k_kappa<double><<<nblk(n), BS, 0, s>>>(v, ph.gam, P, K);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_recon(const BlockView& v, const PhysArgs& ph, int dir, const double* P, const float* P32,
-                         double* QL, double* QR, cudaStream_t s) {
+                         const double* K, const double* Fl, double* QL, double* QR, cudaStream_t s) {
     const long n = recon_threads(v, dir, ph.mixed, ph.recon_seg, ph.recon_x1_sweep);
     const unsigned nb = nblk(n, ph.bs_recon);
     const int bs = ph.bs_recon;
     if (ph.mixed) {
+        const float* K32 = reinterpret_cast<const float*>(K);
+        const float* F32 = reinterpret_cast<const float*>(Fl);
         float* L = reinterpret_cast<float*>(QL);
         float* R = reinterpret_cast<float*>(QR);
-        if (dir == 1) k_recon<1, float><<<nb, bs, 0, s>>>(v, ph, P32, L, R);
-        if (dir == 2) k_recon<2, float><<<nb, bs, 0, s>>>(v, ph, P32, L, R);
-        if (dir == 3) k_recon<3, float><<<nb, bs, 0, s>>>(v, ph, P32, L, R);
+        if (dir == 1) k_recon<1, float><<<nb, bs, 0, s>>>(v, ph, P32, K32, F32, L, R);
+        if (dir == 2) k_recon<2, float><<<nb, bs, 0, s>>>(v, ph, P32, K32, F32, L, R);
+        if (dir == 3) k_recon<3, float><<<nb, bs, 0, s>>>(v, ph, P32, K32, F32, L, R);
     } else {
-        if (dir == 1) k_recon<1, double><<<nb, bs, 0, s>>>(v, ph, P, QL, QR);
-        if (dir == 2) k_recon<2, double><<<nb, bs, 0, s>>>(v, ph, P, QL, QR);
-        if (dir == 3) k_recon<3, double><<<nb, bs, 0, s>>>(v, ph, P, QL, QR);
+        if (dir == 1) k_recon<1, double><<<nb, bs, 0, s>>>(v, ph, P, K, Fl, QL, QR);
+        if (dir == 2) k_recon<2, double><<<nb, bs, 0, s>>>(v, ph, P, K, Fl, QL, QR);
+        if (dir == 3) k_recon<3, double><<<nb, bs, 0, s>>>(v, ph, P, K, Fl, QL, QR);
     }
     return cudaGetLastError();
 }
@@ -1411,6 +1471,16 @@ cudaError_t launch_flatten_batch(const DevBlock* tab, const int* list, int nlist
         if (dir == 2) kb_flatten<2, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
         if (dir == 3) kb_flatten<3, double><<<g, BS, 0, s>>>(tab, list, ph, sigma);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kappa_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
+                               int sigma, cudaStream_t s) {
+    if (nlist <= 0) return cudaSuccess;
+    if (ph.mixed)
+        kb_kappa<float><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
+    else
+        kb_kappa<double><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, ph, sigma);
     return cudaGetLastError();
 }
 
