@@ -207,21 +207,33 @@ __device__ __forceinline__ T entropy_kappa(const T pr[NPRIM], T gam) {
 }
 
 // fastest magnetosonic characteristic speeds along dir (Sec. 2.1): roots of
-// A v^2 - 2 B v + C = 0 with c^2 = vA^2 + cs^2 (1 - vA^2).
+// A v^2 - 2 B v + C = 0 with c^2 = vA^2 + cs^2 (1 - vA^2), vA^2 = b^2/(b^2 + w),
+// cs^2 = gam p / w, i.e. c^2 = (b^2 + gam p)/(b^2 + w). The quadratic is taken
+// times b^2 + w (same roots, no division for c^2): with num = b^2 + gam p and
+// (b^2 + w)(1 - c^2) = w - gam p,
+//   A = u^t u^t (w - gam p) - num g^{tt}, B = u^t u^d (w - gam p) - num g^{td},
+//   C = u^d u^d (w - gam p) - num g^{dd}; v = (B +- sd)/A, sd = sqrt(max(0, B^2 - A C)).
+template <typename T>
+__device__ __forceinline__ void wave_quadratic(const T pr[NPRIM], const Fluid<T>& s, const Metric<T>& m, int dir,
+                                               T gam, T& A, T& B, T& sd) {
+    const T p = (gam - T(1)) * pr[UU];
+    const T gp = gam * p;
+    const T num = s.bsq + gp;
+    const T dn = pr[RHO] + pr[UU] + p - gp;
+    const T ut = s.ucon[0], ud = s.ucon[dir];
+    A = ut * ut * dn - num * m.c00;
+    B = ut * ud * dn - num * gcon0(m, dir);
+    const T C = ud * ud * dn - num * gcondd(m, dir);
+    T disc = B * B - A * C;
+    disc = disc > T(0) ? disc : T(0);
+    sd = sqrt(disc);
+}
+
 template <typename T>
 __device__ __forceinline__ void wave_speeds(const T pr[NPRIM], const Fluid<T>& s, const Metric<T>& m, int dir, T gam,
                                             T& vp, T& vm) {
-    const T p = (gam - T(1)) * pr[UU];
-    const T w = pr[RHO] + pr[UU] + p;
-    // c^2 = vA^2 + cs^2 (1 - vA^2) with vA^2 = b^2/(b^2 + w), cs^2 = gam p / w, over one denominator
-    const T c2 = (s.bsq + gam * p) / (s.bsq + w);
-    const T ut = s.ucon[0], ud = s.ucon[dir];
-    const T A = ut * ut - c2 * (ut * ut + m.c00);
-    const T B = ut * ud - c2 * (ut * ud + gcon0(m, dir));
-    const T C = ud * ud - c2 * (ud * ud + gcondd(m, dir));
-    T disc = B * B - A * C;
-    disc = disc > T(0) ? disc : T(0);
-    const T sd = sqrt(disc);
+    T A, B, sd;
+    wave_quadratic(pr, s, m, dir, gam, A, B, sd);
     const T iA = T(1) / A;
     vp = (B + sd) * iA;
     vm = (B - sd) * iA;
@@ -276,17 +288,22 @@ __device__ __forceinline__ bool nonpos_product(T a, T b) {
     return ((ia ^ ib) < 0) || (ia & B::MAG) == 0 || (ib & B::MAG) == 0;
 }
 
+// from the differences dl = q0 - qm, dr = qp - q0 and dlr = qp - qm
 template <typename T>
-__device__ __forceinline__ T mc_slope_i(T qm, T q0, T qp) {
+__device__ __forceinline__ T mc_slope_d(T dl, T dr, T dlr) {
     using B = FBits<T>;
     using I = typename B::I;
-    const T dl = q0 - qm, dr = qp - q0;
     if (nonpos_product(dl, dr)) return T(0);
-    const T dc = T(0.5) * (qp - qm);
+    const T dc = T(0.5) * dlr;
     const I al = B::of(dl) & B::MAG, ar = B::of(dr) & B::MAG;
     const T lim = T(2) * B::from(al < ar ? al : ar);  // 2 min(|dl|, |dr|)
     const I ac = B::of(dc) & B::MAG, alim = B::of(lim);
     return B::from((ac < alim ? ac : alim) | (B::of(dc) & ~B::MAG));  // min(|dc|, lim) with the sign of dc
+}
+
+template <typename T>
+__device__ __forceinline__ T mc_slope_i(T qm, T q0, T qp) {
+    return mc_slope_d(q0 - qm, qp - q0, qp - qm);
 }
 
 template <typename T>
@@ -302,19 +319,44 @@ template <typename T>
 __device__ __forceinline__ T ppm_face(T qa, T qb, T sa, T sb) {
     return T(0.5) * (qa + qb) - (sb - sa) * T(1.0 / 6.0);
 }
+// the same with d = qb - qa given: qa + d/2 - (sb - sa)/6
+template <typename T>
+__device__ __forceinline__ T ppm_face_d(T qa, T d, T sa, T sb) {
+    return fma(T(0.5), d, qa) - (sb - sa) * T(1.0 / 6.0);
+}
 
-// the two parabola constraints of a cell with value c and edge values l, r
+// a non-NaN value as a signed integer of the same order (+0 and -0 both 0)
+template <typename T>
+__device__ __forceinline__ typename FBits<T>::I ordered_int(typename FBits<T>::I b) {
+    const typename FBits<T>::I m = b & FBits<T>::MAG;
+    return (b < 0) ? -m : m;
+}
+
+// the two parabola constraints of a cell with value c and edge values l, r.
+// Every decision is a comparison of values, taken on the integer pipe:
+// (r - c)(c - l) <= 0 is "c not strictly between l and r" (a rounded difference
+// has the exact sign; as with nonpos_product, products that underflow aside);
+// with da = r - l != 0 and s its sign, da a6 > da^2 is s a6 > |da| and
+// -da^2 > da a6 is s a6 < -|da|. Near a tie the product form may take the
+// other branch, which there gives the same edge value (the constraints are
+// continuous across their switching surfaces).
 template <typename T>
 __device__ __forceinline__ void ppm_limit(T c, T& l, T& r) {
-    if (nonpos_product(r - c, c - l)) {
+    using B = FBits<T>;
+    using I = typename B::I;
+    const I oc = ordered_int<T>(B::of(c)), ol = ordered_int<T>(B::of(l)), orr = ordered_int<T>(B::of(r));
+    if (!((orr > oc && oc > ol) || (orr < oc && oc < ol))) {
         l = c;
         r = c;
     } else {
         const T da = r - l;
         const T a6 = T(6) * (c - T(0.5) * (l + r));
-        if (da * a6 > da * da)
+        const I bda = B::of(da);
+        const I mda = bda & B::MAG;                                   // |da| (ordered, > 0)
+        const I sa6 = ordered_int<T>(B::of(a6) ^ (bda & ~B::MAG));   // s a6 (ordered)
+        if (sa6 > mda)
             l = T(3) * c - T(2) * r;
-        else if (-(da * da) > da * a6)
+        else if (sa6 < -mda)
             r = T(3) * c - T(2) * l;
     }
 }

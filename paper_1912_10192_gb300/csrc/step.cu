@@ -257,9 +257,12 @@ __device__ __forceinline__ void b_recon_row(const BlockView& v, PhysArgs ph, con
     const T qp = __shfl_down_sync(0xffffffffu, qc, 1);
     T l, r;
     if (ph.recon == HAMR_RECON_PPM) {
-        const T sc = mc_slope_i(qm, qc, qp);                  // valid on lanes 1..30
+        // the same differences and formulas as the pencil sweep (identical edge values)
+        const T dr = qp - qc;
+        const T dl = __shfl_up_sync(0xffffffffu, dr, 1);
+        const T sc = mc_slope_d(dl, dr, qp - qm);             // valid on lanes 1..30
         const T sp = __shfl_down_sync(0xffffffffu, sc, 1);
-        r = ppm_face(qc, qp, sc, sp);                         // interface i+1/2, valid on lanes 1..29
+        r = ppm_face_d(qc, dr, sc, sp);                       // interface i+1/2, valid on lanes 1..29
         l = __shfl_up_sync(0xffffffffu, r, 1);                // interface i-1/2, valid on lanes 2..30
         if (ph.flatten) flatten_edges(Fl[c + ic], qc, l, r);
         ppm_limit(qc, l, r);
@@ -298,14 +301,19 @@ __device__ __forceinline__ void b_recon_sweep(const BlockView& v, PhysArgs ph, c
     const long c0 = (long)recon_dst<DIR>(nv) * v.nc + co;
     const T* p = recon_src<DIR>(v, nv, P, K) + co;
     if (ph.recon == HAMR_RECON_PPM) {
-        T qm = p[-st], qc = p[0], qp = p[st];
-        T sm = mc_slope_i(p[-2 * st], qm, qc);
-        T sc = mc_slope_i(qm, qc, qp);
-        T fl = ppm_face(qm, qc, sm, sc);  // interface a0 - 1/2
+        // each difference of neighbours is formed once and serves two slopes and a face
+        const T qmm = p[-2 * st], qm = p[-st];
+        T qc = p[0], qp = p[st];
+        const T dmm = qm - qmm, dm = qc - qm;
+        T dc = qp - qc;
+        const T sm = mc_slope_d(dmm, dm, qc - qmm);
+        T sc = mc_slope_d(dm, dc, qp - qm);
+        T fl = ppm_face_d(qm, dm, sm, sc);  // interface a0 - 1/2
         for (int m = 0; m < ncell; m++) {
             const T qpp = p[(m + 2) * st];
-            const T sp = mc_slope_i(qc, qp, qpp);
-            const T fr = ppm_face(qc, qp, sc, sp);  // interface a + 1/2
+            const T dp = qpp - qp;
+            const T sp = mc_slope_d(dc, dp, qpp - qc);
+            const T fr = ppm_face_d(qc, dc, sc, sp);  // interface a + 1/2
             T l = fl, r = fr;
             if (ph.flatten) flatten_edges(Fl[co + m * st], qc, l, r);
             ppm_limit(qc, l, r);
@@ -313,6 +321,7 @@ __device__ __forceinline__ void b_recon_sweep(const BlockView& v, PhysArgs ph, c
             QR[c0 + m * st] = r;
             qc = qp;
             qp = qpp;
+            dc = dp;
             sc = sp;
             fl = fr;
         }
@@ -346,11 +355,12 @@ __device__ __forceinline__ void b_recon_cell(const BlockView& v, PhysArgs ph, co
         const T* p = recon_src<DIR>(v, n, P, K) + c;
         T l, r;
         if (ph.recon == HAMR_RECON_PPM) {
-            const T qm = p[-st], qc = p[0], qp = p[st];
-            const T sm = mc_slope_i(p[-2 * st], qm, qc), sc = mc_slope_i(qm, qc, qp),
-                    sp = mc_slope_i(qc, qp, p[2 * st]);
-            l = ppm_face(qm, qc, sm, sc);
-            r = ppm_face(qc, qp, sc, sp);
+            const T qmm = p[-2 * st], qm = p[-st], qc = p[0], qp = p[st], qpp = p[2 * st];
+            const T dmm = qm - qmm, dm = qc - qm, dp = qp - qc, dpp = qpp - qp;
+            const T sm = mc_slope_d(dmm, dm, qc - qmm), sc = mc_slope_d(dm, dp, qp - qm),
+                    sp = mc_slope_d(dp, dpp, qpp - qc);
+            l = ppm_face_d(qm, dm, sm, sc);
+            r = ppm_face_d(qc, dp, sc, sp);
             if (ph.flatten) flatten_edges(Fl[c], qc, l, r);
             ppm_limit(qc, l, r);
         } else {
@@ -446,22 +456,34 @@ __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const T*
     const T kapl = QR[(B1 + DIR - 1) * v.nc + c - st], kapr = QL[(B1 + DIR - 1) * v.nc + c];
     const T gam = (T)ph.gam;
     T UL[NFLUX], FL[NFLUX], UR[NFLUX], FR[NFLUX];
-    T vpl, vml, vpr, vmr;
+    T Al, Bl, sdl, Ar, Br, sdr;
     {
         Fluid<T> s;
         fluid_state(pl, m, s);
         flux_row(pl, s, 0, DIR, gam, kapl, UL);
         flux_row(pl, s, DIR, DIR, gam, kapl, FL);
-        wave_speeds(pl, s, m, DIR, gam, vpl, vml);
+        wave_quadratic(pl, s, m, DIR, gam, Al, Bl, sdl);
     }
     {
         Fluid<T> s;
         fluid_state(pr, m, s);
         flux_row(pr, s, 0, DIR, gam, kapr, UR);
         flux_row(pr, s, DIR, DIR, gam, kapr, FR);
-        wave_speeds(pr, s, m, DIR, gam, vpr, vmr);
+        wave_quadratic(pr, s, m, DIR, gam, Ar, Br, sdr);
     }
-    // U's B slots: B^i for the transverse i (flux_row with d = 0 gives b^i u^t - b^t u^i = B^i)
+    // U's B slots are B^i of the transverse i (b^i u^t - b^t u^i = B^i): the edge values themselves
+    {
+        constexpr int i1 = (DIR == 1) ? B2 : B1, i2 = (DIR == 3) ? B2 : B3;
+        UL[6] = pl[i1];
+        UL[7] = pl[i2];
+        UR[6] = pr[i1];
+        UR[7] = pr[i2];
+    }
+    // the two sides' 1/A from one division
+    const T iAA = T(1) / (Al * Ar);
+    const T iAl = Ar * iAA, iAr = Al * iAA;
+    const T vpl = (Bl + sdl) * iAl, vml = (Bl - sdl) * iAl;
+    const T vpr = (Br + sdr) * iAr, vmr = (Br - sdr) * iAr;
     const T cmax = fmax(T(0), fmax(vpl, vpr));
     const T cmin = fmax(T(0), fmax(-vml, -vmr));
     if (ph.riemann == HAMR_FLUX_LLF) {
@@ -470,11 +492,12 @@ __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const T*
         for (int q = 0; q < NFLUX; q++)
             F[q * v.nc + c] = (double)(T(0.5) * (FL[q] + FR[q] - cm * (UR[q] - UL[q])) * m.gdet);
     } else if (cmax + cmin > T(0)) {
+        // (cmin F_R + cmax F_L - cmax cmin (U_R - U_L)) sqrt(-g) / (cmax + cmin), weights formed once
         const T w = m.gdet / (cmax + cmin);
-        const T cc = cmax * cmin;
+        const T wl = cmax * w, wr = cmin * w, wc = cmax * wr;
 #pragma unroll
         for (int q = 0; q < NFLUX; q++)
-            F[q * v.nc + c] = (double)((cmin * FR[q] + cmax * FL[q] - cc * (UR[q] - UL[q])) * w);
+            F[q * v.nc + c] = (double)(wr * FR[q] + wl * FL[q] - wc * (UR[q] - UL[q]));
     } else {
 #pragma unroll
         for (int q = 0; q < NFLUX; q++) F[q * v.nc + c] = (double)(T(0.5) * (FL[q] + FR[q]) * m.gdet);
@@ -637,17 +660,19 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
 }
 
 // sum_i v_f^i / dx^i at a cell centre (Sec. 2.1 CFL condition), given the fluid state
+// (max(|v+|, |v-|) = (|B| + sd)/|A| per direction; the three terms over one denominator)
 template <typename T>
 __device__ __forceinline__ double inv_dt_fluid(const BlockView& v, const T pr[NPRIM], const Fluid<T>& s,
                                                const Metric<T>& m, T gam) {
-    T vp, vm, inv = T(0);
-    wave_speeds(pr, s, m, 1, gam, vp, vm);
-    inv += fmax(fabs(vp), fabs(vm)) * (T)v.idx1;
-    wave_speeds(pr, s, m, 2, gam, vp, vm);
-    inv += fmax(fabs(vp), fabs(vm)) * (T)v.idx2;
-    wave_speeds(pr, s, m, 3, gam, vp, vm);
-    inv += fmax(fabs(vp), fabs(vm)) * (T)v.idx3;
-    return (double)inv;
+    T A1, Bq1, sd1, A2, Bq2, sd2, A3, Bq3, sd3;
+    wave_quadratic(pr, s, m, 1, gam, A1, Bq1, sd1);
+    wave_quadratic(pr, s, m, 2, gam, A2, Bq2, sd2);
+    wave_quadratic(pr, s, m, 3, gam, A3, Bq3, sd3);
+    const T a1 = fabs(A1), a2 = fabs(A2), a3 = fabs(A3);
+    const T n1 = (fabs(Bq1) + sd1) * (T)v.idx1, n2 = (fabs(Bq2) + sd2) * (T)v.idx2,
+            n3 = (fabs(Bq3) + sd3) * (T)v.idx3;
+    const T a23 = a2 * a3;
+    return (double)((n1 * a23 + (n2 * a3 + n3 * a2) * a1) / (a1 * a23));
 }
 
 template <typename T>
