@@ -91,6 +91,94 @@ __device__ __forceinline__ bool newton_wv(const C2PScalars& S, double gfac, doub
     return ok;
 }
 
+// Mixed precision (the FP32-flux form only): FP32 Newton iterations first, on
+// the two equations scaled by k ~ 1/W of the start (every term then O(1):
+// f1 ~ W, f2 ~ W^2, so D, B^2, Q.n scale by k, Qt^2 by k^2, (Q.B)^2 by k^3),
+// until a step is below 1e-5 W (at most 8); then FP64 iterations from there,
+// which stop at the usual rule or, right after that FP32 stage, at a step below
+// 1e-5 W: in the quadratic regime a step d leaves an error of order d^2 / W,
+// at or below the usual 1e-10 W. When the FP32 stage does not get there the
+// FP64 iteration runs from the original start alone. `it` counts the
+// iterations of both precisions.
+__device__ __forceinline__ bool newton_wv_mixed(const C2PScalars& S, double gfac, double& W, double& vsq, int& it) {
+    const float k = 1.0f / (float)W;
+    const double kd = (double)k;
+    const float D = (float)(S.D * kd), Bsq = (float)(S.Bsq * kd), Qdotn = (float)(S.Qdotn * kd);
+    const float Qtsq = (float)(S.Qtsq * (kd * kd)), QB2 = (float)(S.QB2 * (kd * kd * kd));
+    const float gf = (float)gfac, vmax = (float)C2P_VSQMAX;
+    float w = (float)(W * kd), v = (float)vsq;
+    bool ok32 = false;
+    int it32 = 0;
+    for (it32 = 1; it32 <= 8; it32++) {
+        const float omv = 1.0f - v;
+        const float rs = rsqrtf(omv);
+        const float sq = omv * rs;
+        const float iw = 1.0f / w;
+        const float iw2 = iw * iw;
+        const float bw = Bsq + w;
+        const float p = gf * (w * omv - D * sq);
+        const float f1 = -0.5f * Bsq * (1.0f + v) + 0.5f * QB2 * iw2 - w + p - Qdotn;
+        const float f2 = v * bw * bw - QB2 * (Bsq + 2.0f * w) * iw2 - Qtsq;
+        const float j11 = -QB2 * iw2 * iw - 1.0f + gf * omv;
+        const float j12 = -0.5f * Bsq + gf * (0.5f * D * rs - w);
+        const float j21 = 2.0f * bw * (v + QB2 * iw2 * iw);
+        const float j22 = bw * bw;
+        const float idet = 1.0f / (j11 * j22 - j12 * j21);
+        const float wn = w + (j12 * f2 - j22 * f1) * idet;
+        const float vn = fminf(fmaxf(v + (j21 * f1 - j11 * f2) * idet, 0.0f), vmax);
+        if (!(wn > 0.0f) || !(wn < 1e30f)) break;
+        const float err = fabsf(wn - w) + fabsf(vn - v) * wn;
+        w = wn;
+        v = vn;
+        if (err < 1e-5f * wn) {
+            ok32 = true;
+            break;
+        }
+    }
+    if (it32 > 8) it32 = 8;
+    if (!ok32) {  // the FP64 iteration from the original start
+        const bool ok = newton_wv(S, gfac, W, vsq, it);
+        it += it32;
+        return ok;
+    }
+    // FP64 iterations from the FP32 root (w / k, taken as w W: the start may be off by the rounding of k)
+    double Wd = (double)w * W, vd = (double)v;
+    const double D64 = S.D, Bsq64 = S.Bsq, QB264 = S.QB2, Qdotn64 = S.Qdotn, Qtsq64 = S.Qtsq;
+    bool ok = false;
+    int it64;
+    for (it64 = 1; it64 <= C2P_NMAX; it64++) {
+        const double omv = 1.0 - vd;
+        const double rs = rsqrt(omv);
+        const double sq = omv * rs;
+        const double iW = 1.0 / Wd;
+        const double iW2 = iW * iW;
+        const double BW = Bsq64 + Wd;
+        const double p = gfac * (Wd * omv - D64 * sq);
+        const double f1 = -0.5 * Bsq64 * (1.0 + vd) + 0.5 * QB264 * iW2 - Wd + p - Qdotn64;
+        const double f2 = vd * BW * BW - QB264 * (Bsq64 + 2.0 * Wd) * iW2 - Qtsq64;
+        const double j11 = -QB264 * iW2 * iW - 1.0 + gfac * omv;
+        const double j12 = -0.5 * Bsq64 + gfac * (0.5 * D64 * rs - Wd);
+        const double j21 = 2.0 * BW * (vd + QB264 * iW2 * iW);
+        const double j22 = BW * BW;
+        const double idet = 1.0 / (j11 * j22 - j12 * j21);
+        const double Wn = Wd + (j12 * f2 - j22 * f1) * idet;
+        const double vn = fmin(fmax(vd + (j21 * f1 - j11 * f2) * idet, 0.0), C2P_VSQMAX);
+        if (!(Wn > 0.0)) break;
+        const double err = fabs(Wn - Wd) + fabs(vn - vd) * Wn;
+        Wd = Wn;
+        vd = vn;
+        if (err < C2P_TOL * Wn || (it64 == 1 && err < 1e-5 * Wn)) {
+            ok = true;
+            break;
+        }
+    }
+    if (it64 > C2P_NMAX) it64 = C2P_NMAX;
+    it = it32 + it64;
+    W = Wd;
+    vsq = vd;
+    return ok;
+}
+
 // Aitken-accelerated inversion (Sec. 2.6 names it beside Newton; Newman &
 // Hamlin 2014). With E = -Q.n, S^2 = Qt^2, T = Q.B the two equations give, for
 // a trial pressure p, a cubic in phi = W + B^2: phi^3 - a phi^2 + d = 0,
@@ -172,6 +260,7 @@ struct C2PWork {
     double W0, vsq0;  // the start from the guess primitives
     double p0;        // ... and its pressure (the Aitken inversion's start)
     int method;       // HAMR_INV_NEWTON or HAMR_INV_AITKEN
+    int mixed;        // Newton: FP32 iterations first (newton_wv_mixed)
     double W, vsq, rho, u;
     bool ok;
     int its;          // Newton iterations of every energy attempt
@@ -179,9 +268,10 @@ struct C2PWork {
 
 __device__ __forceinline__ void c2p_prepare(const double U[NCONS], const double Bc[3], const Metric<double>& m,
                                             double gam, const double pr[NPRIM], C2PWork& w,
-                                            int method = HAMR_INV_NEWTON) {
+                                            int method = HAMR_INV_NEWTON, int mixed = 0) {
     c2p_scalars(U, Bc, m, w.S);
     w.method = method;
+    w.mixed = mixed;
     w.p0 = (gam - 1.0) * pr[UU];
     const double q1 = pr[U1], q2 = pr[U2], q3 = pr[U3];
     const double qsq = m.g11 * q1 * q1 + m.g22 * q2 * q2 + m.g33 * q3 * q3 + 2.0 * m.g13 * q1 * q3;
@@ -222,7 +312,7 @@ __device__ __forceinline__ void c2p_attempt(C2PWork& w, double gam, double W, do
         return;
     }
     int it = 0;
-    bool ok = newton_wv(w.S, gfac, W, vsq, it);
+    bool ok = w.mixed ? newton_wv_mixed(w.S, gfac, W, vsq, it) : newton_wv(w.S, gfac, W, vsq, it);
     w.its += it;
     w.W = W;
     w.vsq = vsq;

@@ -891,7 +891,7 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
     }
     // inversion: energy attempts from the start(s), then the entropy backup
     C2PWork w;
-    if (active) c2p_prepare(U, Bc, m, gam, pr, w, ph.inversion);
+    if (active) c2p_prepare(U, Bc, m, gam, pr, w, ph.inversion, std::is_same<TS, float>::value ? 1 : 0);
     if (MLP) {
         // first: the network's start, then the plain one; rescue: the plain start, then the
         // network's where it failed (the CTA runs the network only if one of its cells failed)
