@@ -33,7 +33,7 @@ struct C2PScalars {
 __device__ __forceinline__ void c2p_scalars(const double U[NCONS], const double Bc[3], const Metric<double>& m,
                                             C2PScalars& S) {
     const double al = m.alpha;
-    const double ig = 1.0 / m.gdet;
+    const double ig = m.igdet;
     S.D = U[C_RHO] * al * ig;
     // Q_mu = alpha T^t_mu, raised with the sparse inverse metric
     const double Q0 = al * (U[C_EN] - U[C_RHO]) * ig;

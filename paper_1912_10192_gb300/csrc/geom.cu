@@ -34,6 +34,7 @@ __device__ void store_metric(double* __restrict__ tab, long stride, long q, cons
     tab[G_DET * stride + q] = pole ? 0.0 : M.gdet;
     tab[G_ALPHA * stride + q] = 1.0 / sqrt(-M.gi[0][0]);
     tab[G_IALPHA * stride + q] = sqrt(-M.gi[0][0]);
+    tab[G_IGDET * stride + q] = pole ? 0.0 : 1.0 / M.gdet;
 }
 
 __global__ void k_geometry(GeomArgs A) {

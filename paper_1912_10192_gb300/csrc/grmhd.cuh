@@ -24,7 +24,7 @@ constexpr int NFLUX = 8;  // 6 cell-conserved slots + the two B^i with i != dir
 enum {
     G_00 = 0, G_01, G_03, G_11, G_13, G_22, G_33,  // covariant
     GI_00, GI_01, GI_11, GI_13, GI_22, GI_33,      // contravariant
-    G_DET, G_ALPHA, G_IALPHA, NGEOM  // G_IALPHA: 1 / alpha
+    G_DET, G_ALPHA, G_IALPHA, G_IGDET, NGEOM  // G_IALPHA: 1 / alpha; G_IGDET: 1 / sqrt(-g) (0 on the axis)
 };
 // centre tables append: Christoffel symbols (40 = 4 upper x 10 symmetric lower)
 // and the r-dependent floor values
@@ -45,7 +45,7 @@ template <typename T>
 struct Metric {
     T g00, g01, g03, g11, g13, g22, g33;
     T c00, c01, c11, c13, c22, c33;
-    T gdet, alpha, ialpha;
+    T gdet, alpha, ialpha, igdet;
 };
 
 template <typename T, typename TT>
@@ -66,6 +66,7 @@ __device__ __forceinline__ void load_metric(const TT* __restrict__ tab, long str
     m.gdet = (T)tab[G_DET * stride + q];
     m.alpha = (T)tab[G_ALPHA * stride + q];
     m.ialpha = (T)tab[G_IALPHA * stride + q];
+    m.igdet = (T)tab[G_IGDET * stride + q];
 }
 
 template <typename T>
@@ -206,6 +207,38 @@ __device__ __forceinline__ T entropy_kappa(const T pr[NPRIM], T gam) {
     return (gam - T(1)) * pr[UU] * pow_pos(pr[RHO], -gam);
 }
 
+// Bit patterns of FP64/FP32 values: sign tests, magnitude comparisons and
+// maxima on the integer pipe (FP64 comparisons take the FP64 pipe).
+template <typename T>
+struct FBits;
+template <>
+struct FBits<double> {
+    using I = long long;
+    static constexpr I MAG = 0x7FFFFFFFFFFFFFFFll;
+    static __device__ __forceinline__ I of(double x) { return __double_as_longlong(x); }
+    static __device__ __forceinline__ double from(I i) { return __longlong_as_double(i); }
+};
+template <>
+struct FBits<float> {
+    using I = int;
+    static constexpr I MAG = 0x7FFFFFFF;
+    static __device__ __forceinline__ I of(float x) { return __float_as_int(x); }
+    static __device__ __forceinline__ float from(I i) { return __int_as_float(i); }
+};
+
+// a non-NaN value as a signed integer of the same order (+0 and -0 both 0)
+template <typename T>
+__device__ __forceinline__ typename FBits<T>::I ordered_int(typename FBits<T>::I b) {
+    const typename FBits<T>::I m = b & FBits<T>::MAG;
+    return (b < 0) ? -m : m;
+}
+
+// max(a, b) of non-NaN values by their ordered bit patterns (ties give a)
+template <typename T>
+__device__ __forceinline__ T max_i(T a, T b) {
+    return ordered_int<T>(FBits<T>::of(a)) >= ordered_int<T>(FBits<T>::of(b)) ? a : b;
+}
+
 // fastest magnetosonic characteristic speeds along dir (Sec. 2.1): roots of
 // A v^2 - 2 B v + C = 0 with c^2 = vA^2 + cs^2 (1 - vA^2), vA^2 = b^2/(b^2 + w),
 // cs^2 = gam p / w, i.e. c^2 = (b^2 + gam p)/(b^2 + w). The quadratic is taken
@@ -225,7 +258,7 @@ __device__ __forceinline__ void wave_quadratic(const T pr[NPRIM], const Fluid<T>
     B = ut * ud * dn - num * gcon0(m, dir);
     const T C = ud * ud * dn - num * gcondd(m, dir);
     T disc = B * B - A * C;
-    disc = disc > T(0) ? disc : T(0);
+    disc = FBits<T>::of(disc) > 0 ? disc : T(0);  // max(disc, 0) on the integer pipe (-0 -> 0)
     sd = sqrt(disc);
 }
 
@@ -260,25 +293,8 @@ __device__ __forceinline__ T minmod_slope(T qm, T q0, T qp) {
 }
 
 // The same limiters with their sign tests and magnitude comparisons done on the
-// bit patterns (integer pipe; FP64 comparisons take the FP64 pipe). dl dr <= 0
-// becomes "opposite signs or a zero"; they differ from the products only where
-// dl dr underflows.
-template <typename T>
-struct FBits;
-template <>
-struct FBits<double> {
-    using I = long long;
-    static constexpr I MAG = 0x7FFFFFFFFFFFFFFFll;
-    static __device__ __forceinline__ I of(double x) { return __double_as_longlong(x); }
-    static __device__ __forceinline__ double from(I i) { return __longlong_as_double(i); }
-};
-template <>
-struct FBits<float> {
-    using I = int;
-    static constexpr I MAG = 0x7FFFFFFF;
-    static __device__ __forceinline__ I of(float x) { return __float_as_int(x); }
-    static __device__ __forceinline__ float from(I i) { return __int_as_float(i); }
-};
+// bit patterns (FBits above). dl dr <= 0 becomes "opposite signs or a zero";
+// they differ from the products only where dl dr underflows.
 
 // a b <= 0 (opposite signs or a zero)
 template <typename T>
@@ -323,13 +339,6 @@ __device__ __forceinline__ T ppm_face(T qa, T qb, T sa, T sb) {
 template <typename T>
 __device__ __forceinline__ T ppm_face_d(T qa, T d, T sa, T sb) {
     return fma(T(0.5), d, qa) - (sb - sa) * T(1.0 / 6.0);
-}
-
-// a non-NaN value as a signed integer of the same order (+0 and -0 both 0)
-template <typename T>
-__device__ __forceinline__ typename FBits<T>::I ordered_int(typename FBits<T>::I b) {
-    const typename FBits<T>::I m = b & FBits<T>::MAG;
-    return (b < 0) ? -m : m;
 }
 
 // the two parabola constraints of a cell with value c and edge values l, r.

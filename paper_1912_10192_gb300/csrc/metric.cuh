@@ -75,6 +75,7 @@ __device__ inline void to_sparse(const FullMetric& M, Metric<double>& m) {
     m.gdet = M.gdet;
     m.alpha = 1.0 / sqrt(-M.gi[0][0]);
     m.ialpha = sqrt(-M.gi[0][0]);
+    m.igdet = (M.gdet != 0.0) ? 1.0 / M.gdet : 0.0;
 }
 
 }  // namespace hamr

@@ -30,9 +30,8 @@ inline unsigned nblk(long n, int bs = BS) { return (unsigned)((n + bs - 1) / bs)
 // ---------------------------------------------------------------- centre B
 // B^i = (Bbar^i_lo + Bbar^i_hi) / 2 / sqrt(-g)_centre (Sec. 2.5)
 __device__ __forceinline__ void centre_field(const BlockView& v, const double* __restrict__ B, int i, int j, int k,
-                                             double gdet, double Bc[3]) {
+                                             double ig, double Bc[3]) {  // ig = 1 / sqrt(-g)
     const long c = cidx(v, i, j, k);
-    const double ig = 1.0 / gdet;
     Bc[0] = 0.5 * (B[c] + B[c + 1]) * ig;
     Bc[1] = 0.5 * (B[v.nc + c] + B[v.nc + c + v.n1p]) * ig;
     Bc[2] = 0.5 * (B[2 * v.nc + c] + B[2 * v.nc + c + (long)v.n1p * v.n2p]) * ig;
@@ -43,7 +42,7 @@ __device__ __forceinline__ void b_centre_b(const BlockView& v, double* __restric
     if (t >= n) return;
     const int i = (int)(t % v.n1), j = (int)((t / v.n1) % v.n2), k = (int)(t / ((long)v.n1 * v.n2));
     double Bc[3];
-    centre_field(v, B, i, j, k, v.gc[G_DET * v.n2d + gidx(v, i, j)], Bc);
+    centre_field(v, B, i, j, k, v.gc[G_IGDET * v.n2d + gidx(v, i, j)], Bc);
     const long c = cidx(v, i, j, k);
     P[B1 * v.nc + c] = Bc[0];
     P[B2 * v.nc + c] = Bc[1];
@@ -449,7 +448,7 @@ __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const T*
         pl[q] = QR[q * v.nc + c - st];
         pr[q] = QL[q * v.nc + c];
     }
-    const T bn = (T)Bf[(DIR - 1) * v.nc + c] / m.gdet;
+    const T bn = (T)Bf[(DIR - 1) * v.nc + c] * m.igdet;
     pl[B1 + DIR - 1] = bn;
     pr[B1 + DIR - 1] = bn;
     // the entropy tracer's edge values sit in the B^dir fields
@@ -484,10 +483,11 @@ __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const T*
     const T iAl = Ar * iAA, iAr = Al * iAA;
     const T vpl = (Bl + sdl) * iAl, vml = (Bl - sdl) * iAl;
     const T vpr = (Br + sdr) * iAr, vmr = (Br - sdr) * iAr;
-    const T cmax = fmax(T(0), fmax(vpl, vpr));
-    const T cmin = fmax(T(0), fmax(-vml, -vmr));
+    // maxima on the integer pipe
+    const T cmax = max_i(T(0), max_i(vpl, vpr));
+    const T cmin = max_i(T(0), max_i(-vml, -vmr));
     if (ph.riemann == HAMR_FLUX_LLF) {
-        const T cm = fmax(cmax, cmin);
+        const T cm = max_i(cmax, cmin);
 #pragma unroll
         for (int q = 0; q < NFLUX; q++)
             F[q * v.nc + c] = (double)(T(0.5) * (FL[q] + FR[q] - cm * (UR[q] - UL[q])) * m.gdet);
@@ -701,14 +701,8 @@ __device__ __forceinline__ double inv_dt_at(const BlockView& v, const double pr[
 // source sqrt(-g) T^k_l Gamma^l_{nu k} at a cell centre in precision T
 // (tables gc: metric and connection planes of that precision)
 template <typename T, typename TT>
-__device__ __forceinline__ void source_q(const TT* __restrict__ gc, long n2d, long g, const Metric<T>& m,
-                                        const double pfd[NPRIM], double gam_d, double Q[4]) {
-    T pf[NPRIM];
-#pragma unroll
-    for (int q = 0; q < NPRIM; q++) pf[q] = (T)pfd[q];
-    const T gam = (T)gam_d;
-    Fluid<T> s;
-    fluid_state(pf, m, s);
+__device__ __forceinline__ void source_q_state(const TT* __restrict__ gc, long n2d, long g, const Metric<T>& m,
+                                              const T pf[NPRIM], const Fluid<T>& s, T gam, double Q[4]) {
     const T p = (gam - T(1)) * pf[UU];
     const T eta = pf[RHO] + pf[UU] + p + s.bsq;
     const T ptot = p + T(0.5) * s.bsq;
@@ -728,6 +722,17 @@ __device__ __forceinline__ void source_q(const TT* __restrict__ gc, long n2d, lo
             for (int kk = 0; kk < 4; kk++) acc += Tm[kk][l] * (T)cn[(l * 10 + sym(nu, kk)) * n2d];
         Q[nu] = (double)(acc * m.gdet);
     }
+}
+
+template <typename T, typename TT>
+__device__ __forceinline__ void source_q(const TT* __restrict__ gc, long n2d, long g, const Metric<T>& m,
+                                        const double pfd[NPRIM], double gam_d, double Q[4]) {
+    T pf[NPRIM];
+#pragma unroll
+    for (int q = 0; q < NPRIM; q++) pf[q] = (T)pfd[q];
+    Fluid<T> s;
+    fluid_state(pf, m, s);
+    source_q_state(gc, n2d, g, m, pf, s, (T)gam_d, Q);
 }
 
 // ---------------------------------------------------------------- cell update
@@ -837,15 +842,27 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
         g = gidx(v, i, j);
         const long nc = v.nc;
         load_metric(v.gc, v.n2d, g, m);
+        double pf[NPRIM];
+#pragma unroll
+        for (int q = 0; q < NPRIM; q++) pf[q] = Pf[q * nc + c];
+        // in the predictor the base state is the stage state (Pb == Pf): with an FP64
+        // source one fluid state serves U^n and the source
+        const bool share = std::is_same<TS, double>::value && !corrector && Pb == Pf;
+        Fluid<double> sf;
+        if (share) fluid_state(pf, m, sf);
         // U^n
         if (!corrector) {
-            double pb[NPRIM];
-#pragma unroll
-            for (int q = 0; q < NPRIM; q++) pb[q] = Pb[q * nc + c];
-            Fluid<double> s;
-            fluid_state(pb, m, s);
             double row[NFLUX];
-            flux_row(pb, s, 0, 1, gam, entropy_kappa(pb, gam), row);
+            if (share) {
+                flux_row(pf, sf, 0, 1, gam, entropy_kappa(pf, gam), row);
+            } else {
+                double pb[NPRIM];
+#pragma unroll
+                for (int q = 0; q < NPRIM; q++) pb[q] = Pb[q * nc + c];
+                Fluid<double> s;
+                fluid_state(pb, m, s);
+                flux_row(pb, s, 0, 1, gam, entropy_kappa(pb, gam), row);
+            }
 #pragma unroll
             for (int q = 0; q < NCONS; q++) {
                 U[q] = row[q] * m.gdet;
@@ -855,13 +872,13 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
 #pragma unroll
             for (int q = 0; q < NCONS; q++) U[q] = Un[q * nc + c];
         }
-        double pf[NPRIM];
-#pragma unroll
-        for (int q = 0; q < NPRIM; q++) pf[q] = Pf[q * nc + c];
         // source sqrt(-g) T^k_l Gamma^l_{nu k} at the centre, from Pf
         double Q[4];
         if constexpr (std::is_same<TS, double>::value) {
-            source_q(v.gc, v.n2d, g, m, pf, gam, Q);
+            if (share)
+                source_q_state(v.gc, v.n2d, g, m, pf, sf, gam, Q);
+            else
+                source_q(v.gc, v.n2d, g, m, pf, gam, Q);
         } else {
             Metric<float> mf;
             load_metric(v.gc32, v.n2d, g, mf);
@@ -877,7 +894,7 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
             const double src = (q >= C_EN && q <= C_S3) ? Q[q - C_EN] : 0.0;
             U[q] = U[q] + dts * (src - div);
         }
-        centre_field(v, Bn, i, j, k, m.gdet, Bc);
+        centre_field(v, Bn, i, j, k, m.igdet, Bc);
 #pragma unroll
         for (int q = 0; q < NPRIM; q++) pr[q] = pf[q];
         pr[B1] = Bc[0];
@@ -1146,7 +1163,7 @@ __global__ void k_reflux_cells(const DevBlock* tab, int n, const int* cblk, cons
     double U[NCONS];
     for (int q = 0; q < NCONS; q++) U[q] = Ucorr[(long)q * n + i];
     double Bc[3];
-    centre_field(v, D.B, ii, jj, kk, m.gdet, Bc);
+    centre_field(v, D.B, ii, jj, kk, m.igdet, Bc);
     double pr[NPRIM];
 #pragma unroll
     for (int q = 0; q < NPRIM; q++) pr[q] = D.P[q * v.nc + c];
@@ -1238,7 +1255,7 @@ __global__ void k_smr_cells(BlockView v, PhysArgs ph, int corrector, const doubl
 #pragma unroll
         for (int q = 0; q < NCONS; q++) U[q] += ph.smr_u[q * v.nc + c];
         double b[3];
-        centre_field(v, Bn, i, j, k0 + a, m.gdet, b);
+        centre_field(v, Bn, i, j, k0 + a, m.igdet, b);
         for (int e = 0; e < 3; e++) Bc[e] += b[e];
 #pragma unroll
         for (int q = 0; q < 5; q++) pr[q] += Pf[q * v.nc + c];
@@ -1266,7 +1283,7 @@ __global__ void k_smr_cells(BlockView v, PhysArgs ph, int corrector, const doubl
     for (int a = 0; a < w; a++) {
         const long c = cidx(v, i, j, k0 + a);
         double b[3];
-        centre_field(v, Bn, i, j, k0 + a, m.gdet, b);
+        centre_field(v, Bn, i, j, k0 + a, m.igdet, b);
 #pragma unroll
         for (int q = 0; q < 5; q++) Po[q * v.nc + c] = pr[q];
         for (int e = 0; e < 3; e++) Po[(B1 + e) * v.nc + c] = b[e];
