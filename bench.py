@@ -369,8 +369,9 @@ def options_leg(args, hamr, torch, blk, dprim, dbf, cells, stream):
     return out
 
 
-def amr_leg(hamr, torch, precision=0):
-    """512-block AMR/LAT torus tree (levels 0..3), whole LAT periods replayed from one CUDA graph."""
+def amr_leg(hamr, torch, precision=0, tune=True, nper=2):
+    """512-block AMR/LAT torus tree (levels 0..3), whole LAT periods replayed from one CUDA graph.
+    tune=False keeps the default launch shapes and skips the regrid timing."""
     from paper_1912_10192_gb300 import workloads as W
     blocks = W.amr_torus_tree(n=32)
     states = W.torus_blocks(blocks, seed=3)
@@ -379,7 +380,6 @@ def amr_leg(hamr, torch, precision=0):
         g.set_state(p, bf, block=i)
     lmax = max(b["lat"] for b in blocks)
     per = 2 ** lmax
-    nper = 2
 
     def time_periods():
         g.batch_step(per)  # capture (after any change of launch shapes) + one period
@@ -392,6 +392,9 @@ def amr_leg(hamr, torch, precision=0):
         torch.cuda.synchronize()
         return ev0.elapsed_time(ev1) / nper
     ms_default = time_periods()
+    if not tune:
+        g.close()
+        return {"precision": "mixed" if precision else "fp64", "ms_per_period_default_shapes": ms_default}
     tune = g.autotune()
     ms = time_periods()
     torch.cuda.synchronize()
@@ -557,10 +560,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--no-extra", action="store_true", help="skip the network and AMR/LAT legs")
+    ap.add_argument("--amr-periods", type=int, default=0, metavar="P",
+                    help="only time P LAT periods of the 512-block FP64 tree at the default launch shapes "
+                         "(for launch lists) and print them")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank, world, local = env_rank()
+    if args.amr_periods > 0:
+        import torch
+        from paper_1912_10192_gb300 import _build, hamr
+        _build.build()
+        print(json.dumps(amr_leg(hamr, torch, 0, tune=False, nper=args.amr_periods)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

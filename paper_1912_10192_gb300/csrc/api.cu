@@ -460,7 +460,7 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
     // predictor: P^n, B^n -> P^{n+1/2}, B^{n+1/2}
     LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.P, s.B, cs));
     if (ph.mixed) LAUNCH(g, K_BC, 1, cs, launch_to_f32(v, s.P, s.P32, cs));
-    LAUNCH(g, K_RECON, 1, cs, launch_kappa(v, ph, s.P, s.P32, s.E, cs));
+    LAUNCH(g, K_RECON, 1, cs, launch_kappa(v, ph, s.P, s.P32, s.E, s.Un, cs));
     for (int dir = 1; dir <= 3; dir++) {
         if (ph.flatten) LAUNCH(g, K_RECON, 1, cs, launch_flatten(v, ph, dir, s.P, s.P32, s.F[dir - 1], cs));
         LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.P, s.P32, s.E, s.F[dir - 1], s.QL, s.QR, cs));
@@ -476,7 +476,7 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
     // corrector: U^n and the fluxes of P^{n+1/2} -> P^{n+1}, B^{n+1} (in place)
     LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.Ph, s.Bh, cs));
     if (ph.mixed) LAUNCH(g, K_BC, 1, cs, launch_to_f32(v, s.Ph, s.P32, cs));
-    LAUNCH(g, K_RECON, 1, cs, launch_kappa(v, ph, s.Ph, s.P32, s.E, cs));
+    LAUNCH(g, K_RECON, 1, cs, launch_kappa(v, ph, s.Ph, s.P32, s.E, nullptr, cs));
     for (int dir = 1; dir <= 3; dir++) {
         if (ph.flatten) LAUNCH(g, K_RECON, 1, cs, launch_flatten(v, ph, dir, s.Ph, s.P32, s.F[dir - 1], cs));
         LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.Ph, s.P32, s.E, s.F[dir - 1], s.QL, s.QR, cs));
@@ -758,7 +758,7 @@ int time_group_block(hamr_grid* g, const PhysArgs& ph, int which, cudaStream_t c
         const BlockView& v = g->view[k];
         if (ph.mixed) CUDA_TRY(launch_to_f32(v, s.P, s.P32, cs));
         if (which == 0) CUDA_TRY(cudaEventRecord(a, cs));
-        CUDA_TRY(launch_kappa(v, ph, s.P, s.P32, s.E, cs));
+        CUDA_TRY(launch_kappa(v, ph, s.P, s.P32, s.E, s.Un, cs));
         if (which == 0) {
             float t = 0.0f;
             CUDA_TRY(cudaEventRecord(b, cs));

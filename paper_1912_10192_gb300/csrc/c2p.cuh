@@ -63,19 +63,21 @@ __device__ __forceinline__ bool newton_wv(const C2PScalars& S, double gfac, doub
         const double omv = 1.0 - vsq;
         const double rs = rsqrt(omv);
         const double sq = omv * rs;
-        const double iW = 1.0 / W;
-        const double iW2 = iW * iW;
+        const double W2 = W * W, W3 = W2 * W;
         const double BW = Bsq + W;
         const double p = gfac * (W * omv - D * sq);
-        const double f1 = -0.5 * Bsq * (1.0 + vsq) + 0.5 * QB2 * iW2 - W + p - Qdotn;
-        const double f2 = vsq * BW * BW - QB2 * (Bsq + 2.0 * W) * iW2 - Qtsq;
-        const double j11 = -QB2 * iW2 * iW - 1.0 + gfac * omv;
+        // the residuals f1, f2 times W^2 and the Jacobian's first column (d/dW) times W^3, so that no
+        // 1/W is formed: with det' = det W^3 the Newton step is dW = W (j12 f2' - j22 f1') / det',
+        // dv = (j21' f1' - j11' f2') / (W^2 det'), both from the one reciprocal of W^2 det'
+        const double f1 = (-0.5 * Bsq * (1.0 + vsq) - W + p - Qdotn) * W2 + 0.5 * QB2;
+        const double f2 = (vsq * BW * BW - Qtsq) * W2 - QB2 * (Bsq + 2.0 * W);
+        const double j11 = (gfac * omv - 1.0) * W3 - QB2;
         const double j12 = -0.5 * Bsq + gfac * (0.5 * D * rs - W);
-        const double j21 = 2.0 * BW * (vsq + QB2 * iW2 * iW);
+        const double j21 = 2.0 * BW * (vsq * W3 + QB2);
         const double j22 = BW * BW;
-        const double idet = 1.0 / (j11 * j22 - j12 * j21);
-        const double dW = (j12 * f2 - j22 * f1) * idet;
-        const double dv = (j21 * f1 - j11 * f2) * idet;
+        const double r = 1.0 / ((j11 * j22 - j12 * j21) * W2);
+        const double dW = (j12 * f2 - j22 * f1) * W3 * r;
+        const double dv = (j21 * f1 - j11 * f2) * r;
         const double Wn = W + dW;
         const double vn = fmin(fmax(vsq + dv, 0.0), C2P_VSQMAX);
         if (!(Wn > 0.0)) break;
@@ -150,19 +152,19 @@ __device__ __forceinline__ bool newton_wv_mixed(const C2PScalars& S, double gfac
         const double omv = 1.0 - vd;
         const double rs = rsqrt(omv);
         const double sq = omv * rs;
-        const double iW = 1.0 / Wd;
-        const double iW2 = iW * iW;
+        const double W2 = Wd * Wd, W3 = W2 * Wd;
         const double BW = Bsq64 + Wd;
         const double p = gfac * (Wd * omv - D64 * sq);
-        const double f1 = -0.5 * Bsq64 * (1.0 + vd) + 0.5 * QB264 * iW2 - Wd + p - Qdotn64;
-        const double f2 = vd * BW * BW - QB264 * (Bsq64 + 2.0 * Wd) * iW2 - Qtsq64;
-        const double j11 = -QB264 * iW2 * iW - 1.0 + gfac * omv;
+        // scaled as in newton_wv: one reciprocal per iteration
+        const double f1 = (-0.5 * Bsq64 * (1.0 + vd) - Wd + p - Qdotn64) * W2 + 0.5 * QB264;
+        const double f2 = (vd * BW * BW - Qtsq64) * W2 - QB264 * (Bsq64 + 2.0 * Wd);
+        const double j11 = (gfac * omv - 1.0) * W3 - QB264;
         const double j12 = -0.5 * Bsq64 + gfac * (0.5 * D64 * rs - Wd);
-        const double j21 = 2.0 * BW * (vd + QB264 * iW2 * iW);
+        const double j21 = 2.0 * BW * (vd * W3 + QB264);
         const double j22 = BW * BW;
-        const double idet = 1.0 / (j11 * j22 - j12 * j21);
-        const double Wn = Wd + (j12 * f2 - j22 * f1) * idet;
-        const double vn = fmin(fmax(vd + (j21 * f1 - j11 * f2) * idet, 0.0), C2P_VSQMAX);
+        const double r = 1.0 / ((j11 * j22 - j12 * j21) * W2);
+        const double Wn = Wd + (j12 * f2 - j22 * f1) * W3 * r;
+        const double vn = fmin(fmax(vd + (j21 * f1 - j11 * f2) * r, 0.0), C2P_VSQMAX);
         if (!(Wn > 0.0)) break;
         const double err = fabs(Wn - Wd) + fabs(vn - vd) * Wn;
         Wd = Wn;

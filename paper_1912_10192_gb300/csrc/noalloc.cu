@@ -197,7 +197,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     NA_TRY(launch_dt_select(ph, dt, s.dscal, s.dmax, s.dcnt, s.status, v.nc, cs));
     // predictor
     NA_TRY(launch_bc(v, s.P, s.B, cs));
-    NA_TRY(launch_kappa(v, ph, s.P, nullptr, s.E, cs));
+    NA_TRY(launch_kappa(v, ph, s.P, nullptr, s.E, s.Un, cs));
     for (int dir = 1; dir <= 3; dir++) {
         if (ph.flatten) NA_TRY(launch_flatten(v, ph, dir, s.P, nullptr, s.F[dir - 1], cs));
         NA_TRY(launch_recon(v, ph, dir, s.P, nullptr, s.E, s.F[dir - 1], s.QL, s.QR, cs));
@@ -208,7 +208,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     NA_TRY(launch_update(v, ph, 0, s.P, s.P, s.F, s.Bh, s.Un, s.Ph, s.status, s.dscal, 0.5, s.dmax, s.dcnt, cs));
     // corrector
     NA_TRY(launch_bc(v, s.Ph, s.Bh, cs));
-    NA_TRY(launch_kappa(v, ph, s.Ph, nullptr, s.E, cs));
+    NA_TRY(launch_kappa(v, ph, s.Ph, nullptr, s.E, nullptr, cs));
     for (int dir = 1; dir <= 3; dir++) {
         if (ph.flatten) NA_TRY(launch_flatten(v, ph, dir, s.Ph, nullptr, s.F[dir - 1], cs));
         NA_TRY(launch_recon(v, ph, dir, s.Ph, nullptr, s.E, s.F[dir - 1], s.QL, s.QR, cs));

@@ -199,17 +199,22 @@ __device__ __forceinline__ void flatten_edges(T f, T qc, T& l, T& r) {
 
 // entropy tracer kappa = p / rho^gam of every padded cell into K: one power per
 // cell; the reconstruction carries kappa to the faces like a primitive
+// (FP64 predictor: also into Kn, the entropy slot of the U^n cache, where the
+// cell update takes it for U^n instead of forming the power again)
 template <typename T>
 __device__ __forceinline__ void b_kappa(const BlockView& v, T gam, const T* __restrict__ P, T* __restrict__ K,
-                                        long t) {
+                                        long t, double* __restrict__ Kn = nullptr) {
     const long n = (long)v.n1p * v.n2p * v.n3p;
     if (t >= n) return;
-    K[t] = (gam - T(1)) * P[UU * v.nc + t] * pow_pos(P[RHO * v.nc + t], -gam);
+    const T kap = (gam - T(1)) * P[UU * v.nc + t] * pow_pos(P[RHO * v.nc + t], -gam);
+    K[t] = kap;
+    if constexpr (std::is_same<T, double>::value)
+        if (Kn) Kn[t] = kap;
 }
 
 template <typename T>
-__global__ void k_kappa(BlockView v, T gam, const T* __restrict__ P, T* __restrict__ K) {
-    b_kappa<T>(v, gam, P, K, (long)blockIdx.x * blockDim.x + threadIdx.x);
+__global__ void k_kappa(BlockView v, T gam, const T* __restrict__ P, T* __restrict__ K, double* __restrict__ Kn) {
+    b_kappa<T>(v, gam, P, K, (long)blockIdx.x * blockDim.x + threadIdx.x, Kn);
 }
 
 template <int DIR>
@@ -478,8 +483,35 @@ __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const T*
         UR[6] = pr[i1];
         UR[7] = pr[i2];
     }
-    // the two sides' 1/A from one division
-    const T iAA = T(1) / (Al * Ar);
+    // FP64 HLL with both sides' A > 0 (always for admissible states: A = u^t u^t (w - gam p) - (b^2 + gam p) g^{tt}
+    // with g^{tt} < 0 and w - gam p > 0 for gam < 2): the speeds are numerators over AA = A_L A_R, so the
+    // maxima compare numerators and the weights
+    //   wl = Nmax sqrt(-g) / (Nmax + Nmin), wr = Nmin sqrt(-g) / (Nmax + Nmin), wc = wl Nmin / AA
+    // come from one division. AA (Nmax + Nmin) ~ A^4 leaves FP32's range in the floored atmosphere (A ~ rho),
+    // so FP32 keeps the form below (its divisions do not take the FP64 pipe).
+    const T AA = Al * Ar;
+    if (std::is_same<T, double>::value && ph.riemann != HAMR_FLUX_LLF && FBits<T>::of(Al) > 0 &&
+        FBits<T>::of(Ar) > 0) {  // sign tests on the integer pipe
+        const T npl = (Bl + sdl) * Ar, nml = (Bl - sdl) * Ar;
+        const T npr = (Br + sdr) * Al, nmr = (Br - sdr) * Al;
+        const T nmax = max_i(T(0), max_i(npl, npr));
+        const T nmin = max_i(T(0), max_i(-nml, -nmr));
+        const T ns = nmax + nmin;
+        if (FBits<T>::of(ns) > 0) {  // ns >= 0
+            const T r = m.gdet / (AA * ns);
+            const T ra = r * AA;
+            const T wl = nmax * ra, wr = nmin * ra, wc = nmax * nmin * r;
+#pragma unroll
+            for (int q = 0; q < NFLUX; q++)
+                F[q * v.nc + c] = (double)(wr * FR[q] + wl * FL[q] - wc * (UR[q] - UL[q]));
+        } else {
+#pragma unroll
+            for (int q = 0; q < NFLUX; q++) F[q * v.nc + c] = (double)(T(0.5) * (FL[q] + FR[q]) * m.gdet);
+        }
+        return;
+    }
+    // general form: the two sides' 1/A from one division
+    const T iAA = T(1) / AA;
     const T iAl = Ar * iAA, iAr = Al * iAA;
     const T vpl = (Bl + sdl) * iAl, vml = (Bl - sdl) * iAl;
     const T vpr = (Br + sdr) * iAr, vmr = (Br - sdr) * iAr;
@@ -814,6 +846,23 @@ __device__ __forceinline__ int cell_floors(const BlockView& v, long g, const Met
     return 1;
 }
 
+// The same floors with b^2 given (the mixed-precision update takes it from its FP32 fluid
+// state); the drift frame forms the FP64 fluid state of pr where a floor applies.
+__device__ __forceinline__ int cell_floors_b2(const BlockView& v, long g, const Metric<double>& m, const PhysArgs& ph,
+                                              double pr[NPRIM], double bsq) {
+    const double rf = fmax(v.gc[C_RHOFLR * v.n2d + g], bsq * (1.0 / 50.0));
+    const double uf = fmax(v.gc[C_UFLR * v.n2d + g], bsq * (1.0 / 750.0));
+    if (!(pr[RHO] < rf) && !(pr[UU] < uf)) return 0;
+    if (ph.floor_frame == HAMR_FLOOR_DRIFT) {
+        Fluid<double> s;
+        fluid_state(pr, m, s);
+        if (drift_floor(m, ph, pr, s, rf, uf)) return 1;
+    }
+    if (pr[RHO] < rf) pr[RHO] = rf;
+    if (pr[UU] < uf) pr[UU] = uf;
+    return 1;
+}
+
 template <bool MLP, typename TS>
 __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int corrector, const double* Pb,
                                                const double* __restrict__ Pf, const double* __restrict__ F1,
@@ -853,8 +902,8 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
         // U^n
         if (!corrector) {
             double row[NFLUX];
-            if (share) {
-                flux_row(pf, sf, 0, 1, gam, entropy_kappa(pf, gam), row);
+            if (share) {  // kappa of P^n from the predictor's entropy-tracer pass
+                flux_row(pf, sf, 0, 1, gam, Un[C_ENT * nc + c], row);
             } else {
                 double pb[NPRIM];
 #pragma unroll
@@ -938,22 +987,42 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
         // b^mu and b^2 do not depend on rho and u_g, which are all the floors change). The floors take
         // b^2 of these primitives, not of the inversion's own (W, v^2), which differ from them by the
         // Newton tolerance (more where v^2 was clamped), and the floor rho = b^2/50 would carry that.
-        Fluid<double> s;
-        const bool need_fluid = ph.floors || (corrector == 1 && std::is_same<TS, double>::value);
-        if (need_fluid) fluid_state(pr, m, s);
-        if (ph.floors) {
-            fl = cell_floors(v, g, m, ph, pr, s);
-            if (fl) sb |= ST_FLOOR;
-        }
+        if constexpr (std::is_same<TS, double>::value) {
+            Fluid<double> s;
+            const bool need_fluid = ph.floors || corrector == 1;
+            if (need_fluid) fluid_state(pr, m, s);
+            if (ph.floors) {
+                fl = cell_floors(v, g, m, ph, pr, s);
+                if (fl) sb |= ST_FLOOR;
+            }
 #pragma unroll
-        for (int q = 0; q < NPRIM; q++) Po[q * v.nc + c] = pr[q];
-        status[c] |= sb;
-        if (corrector == 1) {
-            if constexpr (std::is_same<TS, double>::value)
-                inv = inv_dt_fluid(v, pr, s, m, gam);
-            else
-                inv = inv_dt_at<TS>(v, pr, m, g, gam);
+            for (int q = 0; q < NPRIM; q++) Po[q * v.nc + c] = pr[q];
+            if (corrector == 1) inv = inv_dt_fluid(v, pr, s, m, gam);
+        } else {
+            // mixed precision: one FP32 fluid state of the returned primitives gives the floors'
+            // b^2 (the thresholds b^2/50 and b^2/750 to FP32 accuracy, like the fluxes) and the
+            // FP32 CFL rate; drift-frame floors form the FP64 state they need themselves
+            Metric<TS> mf;
+            load_metric(v.gc32, v.n2d, g, mf);
+            TS pf32[NPRIM];
+#pragma unroll
+            for (int q = 0; q < NPRIM; q++) pf32[q] = (TS)pr[q];
+            Fluid<TS> s32;
+            fluid_state(pf32, mf, s32);
+            if (ph.floors) {
+                fl = cell_floors_b2(v, g, m, ph, pr, (double)s32.bsq);
+                if (fl) {
+                    sb |= ST_FLOOR;
+#pragma unroll
+                    for (int q = 0; q < NPRIM; q++) pf32[q] = (TS)pr[q];
+                    if (ph.floor_frame == HAMR_FLOOR_DRIFT && corrector == 1) fluid_state(pf32, mf, s32);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NPRIM; q++) Po[q * v.nc + c] = pr[q];
+            if (corrector == 1) inv = inv_dt_fluid(v, pf32, s32, mf, (TS)gam);
         }
+        status[c] |= sb;
     }
     // warp-aggregated counters and CFL max
     const unsigned lane = threadIdx.x & 31u;
@@ -1057,7 +1126,7 @@ template <typename T>
 __global__ void kb_kappa(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
     const DevBlock& D = tab[list[blockIdx.y]];
     if constexpr (std::is_same<T, double>::value)
-        b_kappa<T>(D.v, ph.gam, sigma ? D.Ph : D.P, D.E, tidx());
+        b_kappa<T>(D.v, ph.gam, sigma ? D.Ph : D.P, D.E, tidx(), sigma ? nullptr : D.Un + (long)C_ENT * D.v.nc);
     else
         b_kappa<T>(D.v, (float)ph.gam, D.P32, reinterpret_cast<float*>(D.E), tidx());
 }
@@ -1370,12 +1439,12 @@ cudaError_t launch_flatten(const BlockView& v, const PhysArgs& ph, int dir, cons
 }
 
 cudaError_t launch_kappa(const BlockView& v, const PhysArgs& ph, const double* P, const float* P32, double* K,
-                         cudaStream_t s) {
+                         double* Un, cudaStream_t s) {
     const long n = (long)v.n1p * v.n2p * v.n3p;
     if (ph.mixed)
-        k_kappa<float><<<nblk(n), BS, 0, s>>>(v, (float)ph.gam, P32, reinterpret_cast<float*>(K));
+        k_kappa<float><<<nblk(n), BS, 0, s>>>(v, (float)ph.gam, P32, reinterpret_cast<float*>(K), nullptr);
     else
-        k_kappa<double><<<nblk(n), BS, 0, s>>>(v, ph.gam, P, K);
+        k_kappa<double><<<nblk(n), BS, 0, s>>>(v, ph.gam, P, K, Un ? Un + (long)C_ENT * v.nc : nullptr);
     return cudaGetLastError();
 }
 
