@@ -207,6 +207,19 @@ int hamr_grid_stats(const hamr_grid* g, hamr_step_stats* stats);
  * device. HAMR_EINVAL on a single-block grid (it takes dt per step). */
 int hamr_grid_set_fine_dt(hamr_grid* g, double dt_fine);
 
+/* Multi-block grids: how the batched step fills ghost cells and faces from
+ * the neighbouring blocks (Sec. 3.2: copies, restriction and MINMOD
+ * prolongation with linear interpolation in time under LAT). Where a ghost's
+ * source lies depends only on the tree, so by default the grid finds it once,
+ * when the grid is created or regridded, and every stage only applies it
+ * (on = 1); on = 0 finds it again on every stage. Both give the same bits.
+ * `was` (may be NULL) receives the previous setting. Synchronises the
+ * device; the next hamr_batch_step captures its period again. HAMR_EINVAL on
+ * a single-block grid, for on not 0 or 1, or for on = 1 where a ghost's
+ * footprint does not fit the stored form (more than 15 source cells along
+ * a direction; such grids keep on = 0). */
+int hamr_grid_set_ghost_maps(hamr_grid* g, int on, int* was);
+
 /* ---- dynamic refinement (Sec. 3.2: (de)refinement, nesting, prolongation
  * and restriction) ---- */
 

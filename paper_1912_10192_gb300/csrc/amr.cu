@@ -154,88 +154,150 @@ __device__ inline double minmod_(double a, double b) {
 }
 
 // ------------------------------------------------------------------ ghost kernels
-__global__ void k_ghost_cells(AmrDomain A, const int* list, int sigma, int s) {
-    const DevBlock& R = A.tab[list[blockIdx.y]];
-    const BlockView& v = R.v;
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long)v.n1p * v.n2p * v.n3p) return;
-    const int i = (int)(t % v.n1p) - NG, j = (int)((t / v.n1p) % v.n2p) - NG, k = (int)(t / ((long)v.n1p * v.n2p)) - NG;
-    if (i >= 0 && i < v.n1 && j >= 0 && j < v.n2 && k >= 0 && k < v.n3) return;
+// A ghost cell or face first locates its source (the block holding the mapped
+// point, the footprint there, the prolongation offsets and the sign flips of
+// the polar map), then forms its value from the source's state at the stage's
+// time. The location depends only on the tree, so the grid stores it once per
+// ghost (GhostLoc, built by k_ghost_*_locate with the same device code) and
+// the stage launches only apply it; the direct kernels (locate and apply in
+// one) remain for trees whose footprints do not fit the packed form.
+
+// packed location of one ghost: receiving padded index t, source block n (-1: none),
+// base padded index c0 of the footprint in n, and in pk: footprint counts (4 bits each,
+// bits 0..11), offsets in eighths of a source cell (signed 4 bits each, bits 12..23:
+// the prolongation offsets dl of a cell, the face fraction fr in the face's normal
+// slot), the polar sign flip (bit 24), the radial no-inflow clamp of u^1 (bits 25..26:
+// 1 keeps it >= 0, 2 keeps it <= 0) and the face direction (bits 28..29)
+struct GhostLoc {
+    int t, n, c0;
+    unsigned pk;
+};
+
+struct GhostGeo {  // an unpacked location
+    int n, cnt[4], e8[4], neg, clamp, fd;
+    long c0;
+};
+
+__device__ inline bool pack_loc(const GhostGeo& G, int t, GhostLoc& L) {
+    L.t = t;
+    L.n = G.n;
+    L.c0 = (int)G.c0;
+    unsigned pk = 0;
+    bool ok = G.c0 >= 0 && G.c0 < 0x7FFFFFFF;
+    for (int d = 1; d <= 3; d++) {
+        ok = ok && G.cnt[d] >= 1 && G.cnt[d] <= 15 && G.e8[d] >= -7 && G.e8[d] <= 7;
+        pk |= (unsigned)(G.cnt[d] & 15) << (4 * (d - 1));
+        pk |= (unsigned)(G.e8[d] & 15) << (12 + 4 * (d - 1));
+    }
+    pk |= (unsigned)(G.neg & 1) << 24;
+    pk |= (unsigned)(G.clamp > 0 ? 1 : (G.clamp < 0 ? 2 : 0)) << 25;
+    pk |= (unsigned)(G.fd & 3) << 28;
+    L.pk = pk;
+    return ok || G.n < 0;
+}
+
+__device__ inline void unpack_loc(const GhostLoc& L, GhostGeo& G) {
+    G.n = L.n;
+    G.c0 = L.c0;
+    for (int d = 1; d <= 3; d++) {
+        G.cnt[d] = (int)((L.pk >> (4 * (d - 1))) & 15u);
+        const int e = (int)((L.pk >> (12 + 4 * (d - 1))) & 15u);
+        G.e8[d] = (e & 8) ? e - 16 : e;
+    }
+    G.neg = (int)((L.pk >> 24) & 1u);
+    const unsigned c = (L.pk >> 25) & 3u;
+    G.clamp = (c == 1u) ? 1 : ((c == 2u) ? -1 : 0);
+    G.fd = (int)((L.pk >> 28) & 3u);
+}
+
+// the source of ghost cell (i, j, k) of R; G.n = -1 where no block holds the mapped point.
+// e8[d]: the MINMOD prolongation offset in eighths, 0 where the slope stencil leaves the
+// source block's interior (the value then takes no slope in d)
+__device__ inline void ghost_cell_locate(const AmrDomain& A, const DevBlock& R, int i, int j, int k, GhostGeo& G) {
     double x[4] = {0.0, R.lo[1] + (i + 0.5) * R.h[1], R.lo[2] + (j + 0.5) * R.h[2], R.lo[3] + (k + 0.5) * R.h[3]};
     int neg, clamp;
     map_point(A, R, x, 0, &neg, &clamp);
-    const int n = find_block(A, A.tab, x);
-    if (n < 0) return;
-    const DevBlock& N = A.tab[n];
-    const SrcView S = source_view(R, N, sigma, s);
-    int i0[4], cnt[4];
+    G.n = find_block(A, A.tab, x);
+    G.neg = neg;
+    G.clamp = clamp;
+    G.fd = 0;
+    if (G.n < 0) {
+        G.c0 = 0;
+        for (int d = 1; d <= 3; d++) G.cnt[d] = 1, G.e8[d] = 0;
+        return;
+    }
+    const DevBlock& N = A.tab[G.n];
+    int i0[4];
     double dl[4];
-    footprint(N, x, R.h, i0, cnt, dl);
+    footprint(N, x, R.h, i0, G.cnt, dl);
     const int nn[4] = {0, N.v.n1, N.v.n2, N.v.n3};
-    const double inv = 1.0 / (double)(cnt[1] * cnt[2] * cnt[3]);
+    for (int d = 1; d <= 3; d++) {
+        G.e8[d] = (int)(8.0 * dl[d]);  // dl is a multiple of 1/8
+        if (i0[d] - 1 < 0 || i0[d] + 1 >= nn[d]) G.e8[d] = 0;
+    }
+    G.c0 = pidx(N.v, i0[1], i0[2], i0[3]);
+}
+
+// the value of a located ghost cell at stage sigma of substep s into P (or Ph) of R at t
+__device__ inline void ghost_cell_apply(const AmrDomain& A, const DevBlock& R, const GhostGeo& G, long t, int sigma,
+                                        int s) {
+    if (G.n < 0) return;
+    const DevBlock& N = A.tab[G.n];
+    const SrcView S = source_view(R, N, sigma, s);
+    const long sj = N.v.n1p, sk = (long)N.v.n1p * N.v.n2p;
+    const long st[4] = {0, 1, sj, sk};
+    const double inv = 1.0 / (double)(G.cnt[1] * G.cnt[2] * G.cnt[3]);
     double* out = sigma ? R.Ph : R.P;
     for (int q = 0; q < NPRIM; q++) {
         double sum = 0.0;
-        for (int c3 = 0; c3 < cnt[3]; c3++)
-            for (int c2 = 0; c2 < cnt[2]; c2++)
-                for (int c1 = 0; c1 < cnt[1]; c1++) {
-                    const int ii[4] = {0, i0[1] + c1, i0[2] + c2, i0[3] + c3};
-                    const long c = pidx(N.v, ii[1], ii[2], ii[3]);
+        for (int c3 = 0; c3 < G.cnt[3]; c3++)
+            for (int c2 = 0; c2 < G.cnt[2]; c2++)
+                for (int c1 = 0; c1 < G.cnt[1]; c1++) {
+                    const long c = G.c0 + c1 + c2 * sj + c3 * sk;
                     const double q0 = S.P(q * N.v.nc + c);
                     double val = q0;
                     for (int d = 1; d <= 3; d++) {
-                        if (dl[d] == 0.0) continue;
-                        if (ii[d] - 1 < 0 || ii[d] + 1 >= nn[d]) continue;
-                        const long st = (d == 1) ? 1 : ((d == 2) ? (long)N.v.n1p : (long)N.v.n1p * N.v.n2p);
-                        const double qm = S.P(q * N.v.nc + c - st);
-                        const double qp = S.P(q * N.v.nc + c + st);
-                        val += dl[d] * minmod_(q0 - qm, qp - q0);
+                        if (G.e8[d] == 0) continue;
+                        const double qm = S.P(q * N.v.nc + c - st[d]);
+                        const double qp = S.P(q * N.v.nc + c + st[d]);
+                        val += (G.e8[d] * 0.125) * minmod_(q0 - qm, qp - q0);
                     }
                     sum += val;
                 }
         double o = sum * inv;
-        if (neg && (q == U2 || q == B2)) o = -o;
+        if (G.neg && (q == U2 || q == B2)) o = -o;
         if (q == U1) {
-            if (clamp > 0 && o < 0.0) o = 0.0;
-            if (clamp < 0 && o > 0.0) o = 0.0;
+            if (G.clamp > 0 && o < 0.0) o = 0.0;
+            if (G.clamp < 0 && o > 0.0) o = 0.0;
         }
-        out[q * v.nc + t] = o;
+        out[q * R.v.nc + t] = o;
     }
 }
 
-__global__ void k_ghost_faces(AmrDomain A, const int* list, int sigma, int s) {
-    const DevBlock& R = A.tab[list[blockIdx.y]];
-    const BlockView& v = R.v;
-    const long np = (long)v.n1p * v.n2p * v.n3p;
-    const long tt = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tt >= 3 * np) return;
-    const int fd = 1 + (int)(tt / np);
-    const long t = tt % np;
-    const int i = (int)(t % v.n1p) - NG, j = (int)((t / v.n1p) % v.n2p) - NG, k = (int)(t / ((long)v.n1p * v.n2p)) - NG;
+// the source of ghost face (i, j, k) of direction fd of R: the face fraction fr (eighths of a
+// source face spacing toward the next face) in e8[fd]
+__device__ inline void ghost_face_locate(const AmrDomain& A, const DevBlock& R, int fd, int i, int j, int k,
+                                         GhostGeo& G) {
     const int ii[4] = {0, i, j, k};
-    const int nn[4] = {0, v.n1, v.n2, v.n3};
-    bool owned = true;
-    for (int e = 1; e <= 3; e++) {
-        if (e == fd) {
-            if (ii[e] < 0 || ii[e] > nn[e]) owned = false;
-        } else if (ii[e] < 0 || ii[e] >= nn[e]) {
-            owned = false;
-        }
-    }
-    if (owned) return;
     double x[4] = {0.0, R.lo[1] + (i + 0.5) * R.h[1], R.lo[2] + (j + 0.5) * R.h[2], R.lo[3] + (k + 0.5) * R.h[3]};
     x[fd] = R.lo[fd] + ii[fd] * R.h[fd];
     int neg, clamp;
     map_point(A, R, x, fd, &neg, &clamp);
-    const int n = find_block(A, A.tab, x);
-    if (n < 0) return;
-    const DevBlock& N = A.tab[n];
-    const SrcView S = source_view(R, N, sigma, s);
-    int i0[4], cnt[4];
+    G.n = find_block(A, A.tab, x);
+    G.neg = neg;
+    G.clamp = 0;
+    G.fd = fd;
+    if (G.n < 0) {
+        G.c0 = 0;
+        for (int d = 1; d <= 3; d++) G.cnt[d] = 1, G.e8[d] = 0;
+        return;
+    }
+    const DevBlock& N = A.tab[G.n];
+    int i0[4];
     double dl[4];
     double xc[4] = {0.0, x[1], x[2], x[3]};
     xc[fd] += 0.5 * R.h[fd];
-    footprint(N, xc, R.h, i0, cnt, dl);
+    footprint(N, xc, R.h, i0, G.cnt, dl);
     const double pos = (x[fd] - N.lo[fd]) / N.h[fd];
     int p0 = (int)floor(pos + 1e-9);
     double fr = nearbyint(8.0 * (pos - p0)) / 8.0;
@@ -243,16 +305,28 @@ __global__ void k_ghost_faces(AmrDomain A, const int* list, int sigma, int s) {
         p0 += 1;
         fr = 0.0;
     }
-    cnt[fd] = 1;
-    const double inv = 1.0 / (double)(cnt[1] * cnt[2] * cnt[3]);
-    const long st = (fd == 1) ? 1 : ((fd == 2) ? (long)N.v.n1p : (long)N.v.n1p * N.v.n2p);
+    G.cnt[fd] = 1;
+    i0[fd] = p0;
+    for (int d = 1; d <= 3; d++) G.e8[d] = 0;
+    G.e8[fd] = (int)(8.0 * fr);
+    G.c0 = pidx(N.v, i0[1], i0[2], i0[3]);
+}
+
+__device__ inline void ghost_face_apply(const AmrDomain& A, const DevBlock& R, const GhostGeo& G, long t, int sigma,
+                                        int s) {
+    if (G.n < 0) return;
+    const DevBlock& N = A.tab[G.n];
+    const SrcView S = source_view(R, N, sigma, s);
+    const int fd = G.fd;
+    const long sj = N.v.n1p, sk = (long)N.v.n1p * N.v.n2p;
+    const long st = (fd == 1) ? 1 : ((fd == 2) ? sj : sk);
+    const double fr = G.e8[fd] * 0.125;
+    const double inv = 1.0 / (double)(G.cnt[1] * G.cnt[2] * G.cnt[3]);
     double sum = 0.0;
-    for (int c3 = 0; c3 < cnt[3]; c3++)
-        for (int c2 = 0; c2 < cnt[2]; c2++)
-            for (int c1 = 0; c1 < cnt[1]; c1++) {
-                int jj[4] = {0, i0[1] + c1, i0[2] + c2, i0[3] + c3};
-                jj[fd] = p0;
-                const long c = pidx(N.v, jj[1], jj[2], jj[3]);
+    for (int c3 = 0; c3 < G.cnt[3]; c3++)
+        for (int c2 = 0; c2 < G.cnt[2]; c2++)
+            for (int c1 = 0; c1 < G.cnt[1]; c1++) {
+                const long c = G.c0 + c1 + c2 * sj + c3 * sk;
                 double q = S.B((fd - 1) * N.v.nc + c);
                 if (fr != 0.0) {
                     const double q1 = S.B((fd - 1) * N.v.nc + c + st);
@@ -262,7 +336,106 @@ __global__ void k_ghost_faces(AmrDomain A, const int* list, int sigma, int s) {
             }
     const double val = sum * inv;
     double* out = sigma ? R.Bh : R.B;
-    out[(fd - 1) * v.nc + t] = (neg && fd == 2) ? -val : val;
+    out[(fd - 1) * R.v.nc + t] = (G.neg && fd == 2) ? -val : val;
+}
+
+// padded cell t of R as (i, j, k); false for an interior cell
+__device__ inline bool ghost_cell_at(const BlockView& v, long t, int& i, int& j, int& k) {
+    i = (int)(t % v.n1p) - NG;
+    j = (int)((t / v.n1p) % v.n2p) - NG;
+    k = (int)(t / ((long)v.n1p * v.n2p)) - NG;
+    return !(i >= 0 && i < v.n1 && j >= 0 && j < v.n2 && k >= 0 && k < v.n3);
+}
+
+// padded face t of direction fd of R as (i, j, k); false for a face the block owns
+__device__ inline bool ghost_face_at(const BlockView& v, int fd, long t, int& i, int& j, int& k) {
+    i = (int)(t % v.n1p) - NG;
+    j = (int)((t / v.n1p) % v.n2p) - NG;
+    k = (int)(t / ((long)v.n1p * v.n2p)) - NG;
+    const int ii[4] = {0, i, j, k};
+    const int nn[4] = {0, v.n1, v.n2, v.n3};
+    for (int e = 1; e <= 3; e++) {
+        if (e == fd) {
+            if (ii[e] < 0 || ii[e] > nn[e]) return true;
+        } else if (ii[e] < 0 || ii[e] >= nn[e]) {
+            return true;
+        }
+    }
+    return false;
+}
+
+// direct forms: locate and apply per launch
+__global__ void k_ghost_cells(AmrDomain A, const int* list, int sigma, int s) {
+    const DevBlock& R = A.tab[list[blockIdx.y]];
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)R.v.n1p * R.v.n2p * R.v.n3p) return;
+    int i, j, k;
+    if (!ghost_cell_at(R.v, t, i, j, k)) return;
+    GhostGeo G;
+    ghost_cell_locate(A, R, i, j, k, G);
+    ghost_cell_apply(A, R, G, t, sigma, s);
+}
+
+__global__ void k_ghost_faces(AmrDomain A, const int* list, int sigma, int s) {
+    const DevBlock& R = A.tab[list[blockIdx.y]];
+    const long np = (long)R.v.n1p * R.v.n2p * R.v.n3p;
+    const long tt = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tt >= 3 * np) return;
+    const int fd = 1 + (int)(tt / np);
+    const long t = tt % np;
+    int i, j, k;
+    if (!ghost_face_at(R.v, fd, t, i, j, k)) return;
+    GhostGeo G;
+    ghost_face_locate(A, R, fd, i, j, k, G);
+    ghost_face_apply(A, R, G, t, sigma, s);
+}
+
+// stored locations: the builders take entry (t, receiving block) and fill the rest;
+// *bad counts entries whose footprint does not fit the packed form
+__global__ void k_ghost_cells_locate(AmrDomain A, GhostLoc* loc, long n, int* bad) {
+    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const DevBlock& R = A.tab[loc[q].n];
+    const long t = loc[q].t;
+    int i, j, k;
+    ghost_cell_at(R.v, t, i, j, k);
+    GhostGeo G;
+    ghost_cell_locate(A, R, i, j, k, G);
+    if (!pack_loc(G, (int)t, loc[q])) atomicAdd(bad, 1);
+}
+
+__global__ void k_ghost_faces_locate(AmrDomain A, GhostLoc* loc, long n, int* bad) {
+    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const DevBlock& R = A.tab[loc[q].n];
+    const int fd = (int)(loc[q].pk >> 28) & 3;
+    const long t = loc[q].t;
+    int i, j, k;
+    ghost_face_at(R.v, fd, t, i, j, k);
+    GhostGeo G;
+    ghost_face_locate(A, R, fd, i, j, k, G);
+    if (!pack_loc(G, (int)t, loc[q])) atomicAdd(bad, 1);
+}
+
+// the stage launches: ghost g of block list[blockIdx.y] (gofs / gcnt: the block's entries)
+__global__ void k_ghost_cells_mapped(AmrDomain A, const int* list, int sigma, int s, const GhostLoc* loc) {
+    const DevBlock& R = A.tab[list[blockIdx.y]];
+    const long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= R.ng_cell) return;
+    const GhostLoc L = loc[R.gofs_cell + g];
+    GhostGeo G;
+    unpack_loc(L, G);
+    ghost_cell_apply(A, R, G, L.t, sigma, s);
+}
+
+__global__ void k_ghost_faces_mapped(AmrDomain A, const int* list, int sigma, int s, const GhostLoc* loc) {
+    const DevBlock& R = A.tab[list[blockIdx.y]];
+    const long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= R.ng_face) return;
+    const GhostLoc L = loc[R.gofs_face + g];
+    GhostGeo G;
+    unpack_loc(L, G);
+    ghost_face_apply(A, R, G, L.t, sigma, s);
 }
 
 // ------------------------------------------------------------------ regridding
@@ -845,6 +1018,11 @@ struct AmrImpl {
     std::vector<std::vector<int>> lev_edgefix;  // blocks of each level with edge corrections
     std::vector<int*> dlev_edgefix;
     double* dtf = nullptr;
+    // stored ghost locations (use_maps false: the direct kernels locate on every launch)
+    GhostLoc *gloc_cell = nullptr, *gloc_face = nullptr;
+    long n_gc = 0, n_gf = 0;
+    bool use_maps = false, maps_ok = false;
+    std::vector<long> lmw_gc, lmw_gf;  // most ghost cells / faces of a block of each level
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     cudaStream_t cap = nullptr;
@@ -1270,6 +1448,51 @@ int amr_create(AmrImpl** out, const hamr_grid_desc& d, const std::vector<BlockVi
         cudaMemcpy(H.b[b].dscal + 1, &one, sizeof(double), cudaMemcpyHostToDevice);
         (void)v;
     }
+    // ghost lists in padded order: (t, receiving block) now, the locations on the device below
+    std::vector<GhostLoc> gcell, gface;
+    for (int b = 0; b < M->nb; b++) {
+        DevBlock& D = H.b[b];
+        const BlockView& v = D.v;
+        const int nn[4] = {0, v.n1, v.n2, v.n3};
+        D.gofs_cell = (long)gcell.size();
+        for (int k = 0; k < v.n3p; k++)
+            for (int j = 0; j < v.n2p; j++)
+                for (int i = 0; i < v.n1p; i++) {
+                    const int ii[4] = {0, i - NG, j - NG, k - NG};
+                    bool ghost = false;
+                    for (int e = 1; e <= 3; e++) ghost = ghost || ii[e] < 0 || ii[e] >= nn[e];
+                    if (ghost) gcell.push_back({(int)(((long)k * v.n2p + j) * v.n1p + i), b, 0, 0u});
+                }
+        D.ng_cell = (int)((long)gcell.size() - D.gofs_cell);
+        D.gofs_face = (long)gface.size();
+        for (int fd = 1; fd <= 3; fd++)
+            for (int k = 0; k < v.n3p; k++)
+                for (int j = 0; j < v.n2p; j++)
+                    for (int i = 0; i < v.n1p; i++) {
+                        const int ii[4] = {0, i - NG, j - NG, k - NG};
+                        bool ghost = false;
+                        for (int e = 1; e <= 3; e++)
+                            ghost = ghost || ii[e] < 0 || ii[e] > nn[e] || (e != fd && ii[e] == nn[e]);
+                        if (ghost)
+                            gface.push_back({(int)(((long)k * v.n2p + j) * v.n1p + i), b, 0, (unsigned)fd << 28});
+                    }
+        D.ng_face = (int)((long)gface.size() - D.gofs_face);
+    }
+    M->n_gc = (long)gcell.size();
+    M->n_gf = (long)gface.size();
+    M->gloc_cell = M->dev(gcell);
+    M->gloc_face = M->dev(gface);
+    if (!M->gloc_cell || !M->gloc_face) {
+        cudaGetLastError();
+        delete M;
+        return set_error(HAMR_ENOMEM, "allocation of the ghost locations failed");
+    }
+    M->lmw_gc.assign(M->Lmax + 1, 0);
+    M->lmw_gf.assign(M->Lmax + 1, 0);
+    for (int b = 0; b < M->nb; b++) {
+        M->lmw_gc[H.b[b].lat] = std::max(M->lmw_gc[H.b[b].lat], (long)H.b[b].ng_cell);
+        M->lmw_gf[H.b[b].lat] = std::max(M->lmw_gf[H.b[b].lat], (long)H.b[b].ng_face);
+    }
     M->dtab = M->dev(H.b);
     M->dbucket = M->dev(H.bucket);
     M->lev.assign(M->Lmax + 1, {});
@@ -1308,6 +1531,14 @@ int amr_create(AmrImpl** out, const hamr_grid_desc& d, const std::vector<BlockVi
     M->dtf = M->dev(std::vector<double>(4, 0.0));
     H.A.tab = M->dtab;
     H.A.bucket = M->dbucket;
+    {
+        int* bad = M->dev(std::vector<int>(1, 0));
+        if (M->n_gc) k_ghost_cells_locate<<<nb_(M->n_gc), BSA>>>(H.A, M->gloc_cell, M->n_gc, bad);
+        if (M->n_gf) k_ghost_faces_locate<<<nb_(M->n_gf), BSA>>>(H.A, M->gloc_face, M->n_gf, bad);
+        int hbad = 1;
+        if (cudaGetLastError() == cudaSuccess && cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess)
+            M->maps_ok = M->use_maps = (hbad == 0);
+    }
     if (cudaStreamCreateWithFlags(&M->cap, cudaStreamNonBlocking) != cudaSuccess) {
         delete M;
         return set_error(HAMR_ECUDA, "stream creation failed");
@@ -1348,8 +1579,15 @@ int group_step(AmrImpl& M, int L, int s, cudaStream_t cs) {
     const PhysArgs& ph = M.ph;
     AM_TRY(launch_save_old_batch(tab, list, nl, M.lmw_pad[L], cs));
     for (int sigma = 0; sigma < 2; sigma++) {
-        k_ghost_cells<<<dim3(nb_(M.lmw_pad[L]), nl), BSA, 0, cs>>>(M.H.A, list, sigma, s);
-        k_ghost_faces<<<dim3(nb_(3 * M.lmw_pad[L]), nl), BSA, 0, cs>>>(M.H.A, list, sigma, s);
+        if (M.use_maps) {
+            if (M.lmw_gc[L])
+                k_ghost_cells_mapped<<<dim3(nb_(M.lmw_gc[L]), nl), BSA, 0, cs>>>(M.H.A, list, sigma, s, M.gloc_cell);
+            if (M.lmw_gf[L])
+                k_ghost_faces_mapped<<<dim3(nb_(M.lmw_gf[L]), nl), BSA, 0, cs>>>(M.H.A, list, sigma, s, M.gloc_face);
+        } else {
+            k_ghost_cells<<<dim3(nb_(M.lmw_pad[L]), nl), BSA, 0, cs>>>(M.H.A, list, sigma, s);
+            k_ghost_faces<<<dim3(nb_(3 * M.lmw_pad[L]), nl), BSA, 0, cs>>>(M.H.A, list, sigma, s);
+        }
         AM_TRY(cudaGetLastError());
         if (ph.mixed) AM_TRY(launch_to_f32_batch(tab, list, nl, M.lmw_pad[L], sigma, cs));
         AM_TRY(launch_kappa_batch(tab, list, nl, M.lmw_pad[L], ph, sigma, cs));
@@ -1550,8 +1788,15 @@ int amr_fill(AmrImpl* M, cudaStream_t s) {
     for (int L = 0; L <= M->Lmax; L++) {
         const int nl = (int)M->lev[L].size();
         if (!nl) continue;
-        k_ghost_cells<<<dim3(nb_(M->lmw_pad[L]), nl), BSA, 0, s>>>(M->H.A, M->dlev[L], 0, 0);
-        k_ghost_faces<<<dim3(nb_(3 * M->lmw_pad[L]), nl), BSA, 0, s>>>(M->H.A, M->dlev[L], 0, 0);
+        if (M->use_maps) {
+            if (M->lmw_gc[L])
+                k_ghost_cells_mapped<<<dim3(nb_(M->lmw_gc[L]), nl), BSA, 0, s>>>(M->H.A, M->dlev[L], 0, 0, M->gloc_cell);
+            if (M->lmw_gf[L])
+                k_ghost_faces_mapped<<<dim3(nb_(M->lmw_gf[L]), nl), BSA, 0, s>>>(M->H.A, M->dlev[L], 0, 0, M->gloc_face);
+        } else {
+            k_ghost_cells<<<dim3(nb_(M->lmw_pad[L]), nl), BSA, 0, s>>>(M->H.A, M->dlev[L], 0, 0);
+            k_ghost_faces<<<dim3(nb_(3 * M->lmw_pad[L]), nl), BSA, 0, s>>>(M->H.A, M->dlev[L], 0, 0);
+        }
     }
     AM_TRY(cudaGetLastError());
     return HAMR_OK;
@@ -1574,6 +1819,20 @@ int amr_regrid_fill(const AmrImpl* old, AmrImpl* M, cudaStream_t s) {
         if (rc) return rc;
     }
     return amr_fill(M, s);
+}
+
+int amr_set_ghost_maps(AmrImpl* M, int on, int* was) {
+    if (was) *was = M->use_maps ? 1 : 0;
+    if (on && !M->maps_ok) return set_error(HAMR_EINVAL, "this tree's ghost footprints do not fit the stored form");
+    const bool u = on != 0;
+    if (u != M->use_maps) {  // the captured period holds the other kernels: capture again
+        M->use_maps = u;
+        if (M->exec) cudaGraphExecDestroy(M->exec);
+        if (M->graph) cudaGraphDestroy(M->graph);
+        M->exec = nullptr;
+        M->graph = nullptr;
+    }
+    return HAMR_OK;
 }
 
 int amr_set_fine_dt(AmrImpl* M, double dt) {

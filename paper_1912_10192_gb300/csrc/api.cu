@@ -566,6 +566,14 @@ int hamr_grid_set_fine_dt(hamr_grid* g, double dt_fine) {
     return HAMR_OK;
 }
 
+int hamr_grid_set_ghost_maps(hamr_grid* g, int on, int* was) {
+    if (!g) return fail(HAMR_EINVAL, "grid is NULL");
+    if (!g->amr) return fail(HAMR_EINVAL, "a single-block grid has no ghost locations");
+    if (on != 0 && on != 1) return fail(HAMR_EINVAL, "on must be 0 or 1");
+    CUDA_TRY(cudaDeviceSynchronize());
+    return amr_set_ghost_maps(g->amr, on, was);
+}
+
 int hamr_grid_block_max(const hamr_grid* g, int field, double* out, void* stream) {
     if (!g) return fail(HAMR_EINVAL, "grid is NULL");
     if (!out) return fail(HAMR_EINVAL, "out is NULL");

@@ -144,6 +144,8 @@ struct DevBlock {
     uint8_t* status;
     double* dscal;  // [0] dt of the block's step, [1] = 1.0
     unsigned long long *dmax, *dcnt;
+    long gofs_cell, gofs_face;  // first stored ghost-cell / ghost-face location of the block
+    int ng_cell, ng_face;       // the block's ghost cells / ghost faces (all three directions)
 };
 
 // domain and block lookup for the ghost kernels
@@ -268,6 +270,8 @@ int amr_fill(AmrImpl* M, cudaStream_t s);
 int amr_regrid_fill(const AmrImpl* old, AmrImpl* M, cudaStream_t s);
 // fine dt of every following period (<= 0: the CFL dt); read on the device, no graph rebuild
 int amr_set_fine_dt(AmrImpl* M, double dt);
+// ghost fill from the stored locations (on != 0, the default where they fit) or by locating on every launch
+int amr_set_ghost_maps(AmrImpl* M, int on, int* was);
 int amr_set_phys(AmrImpl* M, const PhysArgs& ph);
 int amr_time_group(AmrImpl* M, const PhysArgs& ph, int which, cudaStream_t cs, float* ms);
 const uint8_t* mlp_image(const hamr_mlp* m);

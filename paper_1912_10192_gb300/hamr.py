@@ -112,6 +112,7 @@ def lib():
         L.hamr_grid_block_max.argtypes = [P, C.c_int, D, P]
         L.hamr_grid_set_launch_shapes.argtypes = [P, C.POINTER(TuneReport)]
         L.hamr_grid_set_fine_dt.argtypes = [P, C.c_double]
+        L.hamr_grid_set_ghost_maps.argtypes = [P, C.c_int, C.POINTER(C.c_int)]
         L.hamr_grid_regrid.argtypes = [P, C.c_int, C.POINTER(BlockDesc), P]
         L.hamr_tree_adapt.argtypes = [C.POINTER(BlockDesc), C.c_int, C.POINTER(C.c_int), D, D,
                                       C.POINTER(C.c_int), C.POINTER(BlockDesc), C.c_int, C.POINTER(C.c_int)]
@@ -267,6 +268,13 @@ class Grid:
     def set_fine_dt(self, dt_fine):
         """Fixed fine dt of the batched periods (<= 0: the CFL dt)."""
         check(lib().hamr_grid_set_fine_dt(self.h, float(dt_fine)))
+
+    def set_ghost_maps(self, on):
+        """Ghost fill from the locations stored at creation (True) or located on every stage (False);
+        returns the previous setting."""
+        was = C.c_int(0)
+        check(lib().hamr_grid_set_ghost_maps(self.h, 1 if on else 0, C.byref(was)))
+        return bool(was.value)
 
     def block_max(self, field=0, stream=None):
         """Maximum of primitive `field` over each block's interior cells (numpy array, one per block)."""

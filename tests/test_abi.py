@@ -91,5 +91,6 @@ def test_tree_and_regrid_arguments_checked_on_cpu(libpath):
     assert L.hamr_grid_regrid(None, 2, None, None) == hamr.EINVAL
     assert L.hamr_grid_block_max(None, 0, None, None) == hamr.EINVAL
     assert L.hamr_grid_set_fine_dt(None, 0.1) == hamr.EINVAL
+    assert L.hamr_grid_set_ghost_maps(None, 1, None) == hamr.EINVAL
     n = ctypes.c_int()
     assert L.hamr_tree_adapt(None, 0, None, None, None, None, None, 0, ctypes.byref(n)) == hamr.EINVAL

@@ -209,6 +209,28 @@ def test_512_block_tree_at_8_cubed_matches_oracle():
         assert e <= 1e-10, (k, e, errs)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_stored_ghost_locations_give_the_same_bits(precision):
+    """The ghost fill from the locations stored at creation and the fill that
+    locates every ghost on every stage give bit-identical states after one LAT
+    period of the 512-block tree (8^3-class blocks: every kind of neighbour,
+    the polar map, prolongation, restriction and time interpolation)."""
+    from paper_1912_10192_gb300 import hamr
+    blocks = W.amr_torus_tree(n=8)
+    states = W.torus_blocks(blocks, seed=3)
+    res = []
+    for maps in (True, False):
+        g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], precision=precision)
+        for i, (p, bf) in enumerate(states):
+            g.set_state(p, bf, block=i)
+        assert g.set_ghost_maps(maps) is True  # stored locations are the default for this tree
+        g.batch_step(8)
+        res.append([g.get_state(block=i) for i in range(len(blocks))])
+        g.close()
+    for (pa, ba), (pb, bb) in zip(*res):
+        assert np.array_equal(pa, pb, equal_nan=True) and np.array_equal(ba, bb, equal_nan=True)
+
+
 def test_512_block_tree_full_size_properties():
     """Full size (13.1 M cells): after one LAT period every block keeps div B at
     round-off and every face shared by two blocks has one value (the coarse
