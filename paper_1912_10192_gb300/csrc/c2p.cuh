@@ -242,14 +242,15 @@ __device__ __forceinline__ bool aitken_wv(const C2PScalars& S, double gfac, doub
     return false;
 }
 
-// rho and u_g of a converged (W, v^2); false unless both are positive
-__device__ __forceinline__ bool energy_result(const C2PScalars& S, double gam, double W, double vsq, double& rho,
-                                              double& u) {
-    const double gfac = (gam - 1.0) / gam;
+// rho and u_g of a converged (W, v^2) (u_g = p / (gam - 1) = (W (1 - v^2) - D sqrt(1 - v^2)) / gam);
+// false unless both are positive. rs: 1/sqrt(1 - v^2), the Lorentz factor, for the velocity.
+__device__ __forceinline__ bool energy_result(const C2PScalars& S, double igam, double W, double vsq, double& rho,
+                                              double& u, double& rs) {
     const double omv = 1.0 - vsq;
-    const double sq = sqrt(omv);
+    rs = rsqrt(omv);
+    const double sq = omv * rs;
     rho = S.D * sq;
-    u = gfac * (W * omv - S.D * sq) / (gam - 1.0);
+    u = (W * omv - S.D * sq) * igam;
     return (rho > 0.0) && (u > 0.0);
 }
 
@@ -263,7 +264,9 @@ struct C2PWork {
     double p0;        // ... and its pressure (the Aitken inversion's start)
     int method;       // HAMR_INV_NEWTON or HAMR_INV_AITKEN
     int mixed;        // Newton: FP32 iterations first (newton_wv_mixed)
+    double igam, gfac;  // 1/gam and (gam - 1)/gam, from one division per inversion
     double W, vsq, rho, u;
+    double rs;        // 1/sqrt(1 - v^2) of an energy result
     bool ok;
     int its;          // Newton iterations of every energy attempt
 };
@@ -272,6 +275,8 @@ __device__ __forceinline__ void c2p_prepare(const double U[NCONS], const double 
                                             double gam, const double pr[NPRIM], C2PWork& w,
                                             int method = HAMR_INV_NEWTON, int mixed = 0) {
     c2p_scalars(U, Bc, m, w.S);
+    w.igam = 1.0 / gam;
+    w.gfac = (gam - 1.0) * w.igam;
     w.method = method;
     w.mixed = mixed;
     w.p0 = (gam - 1.0) * pr[UU];
@@ -290,15 +295,15 @@ __device__ __forceinline__ void c2p_prepare(const double U[NCONS], const double 
 // one energy-equation attempt from the pressure p (Aitken inversion)
 __device__ __forceinline__ void c2p_attempt_p(C2PWork& w, double gam, double p) {
     if (w.ok) return;
-    const double gfac = (gam - 1.0) / gam;
+    (void)gam;
     int it = 0;
     double W = 0.0, vsq = 0.0;
-    bool ok = aitken_wv(w.S, gfac, p, W, vsq, it);
+    bool ok = aitken_wv(w.S, w.gfac, p, W, vsq, it);
     w.its += it;
     if (ok) {
         w.W = W;
         w.vsq = vsq;
-        ok = energy_result(w.S, gam, W, vsq, w.rho, w.u);
+        ok = energy_result(w.S, w.igam, W, vsq, w.rho, w.u, w.rs);
     }
     w.ok = ok;
 }
@@ -307,7 +312,7 @@ __device__ __forceinline__ void c2p_attempt_p(C2PWork& w, double gam, double p) 
 // The Aitken inversion starts from the pressure of (W, v^2).
 __device__ __forceinline__ void c2p_attempt(C2PWork& w, double gam, double W, double vsq) {
     if (w.ok || !(W > 0.0)) return;
-    const double gfac = (gam - 1.0) / gam;
+    const double gfac = w.gfac;
     vsq = fmin(fmax(vsq, 0.0), C2P_VSQMAX);
     if (w.method == HAMR_INV_AITKEN) {
         c2p_attempt_p(w, gam, gfac * (W * (1.0 - vsq) - w.S.D * sqrt(1.0 - vsq)));
@@ -318,7 +323,7 @@ __device__ __forceinline__ void c2p_attempt(C2PWork& w, double gam, double W, do
     w.its += it;
     w.W = W;
     w.vsq = vsq;
-    if (ok) ok = energy_result(w.S, gam, W, vsq, w.rho, w.u);
+    if (ok) ok = energy_result(w.S, w.igam, W, vsq, w.rho, w.u, w.rs);
     w.ok = ok;
 }
 
@@ -382,10 +387,13 @@ __device__ __forceinline__ int c2p_finish(C2PWork& w, const double U[NCONS], con
         if (!eok) return INV_FAIL;
         status = INV_ENTROPY;
     }
-    // utilde^i = Gamma/(W + B^2) (Qt^i + (Q.B) Bn^i / W), Qt^i = Q^i - alpha g^{ti} (Q.n)
-    const double gamma = rsqrt(1.0 - vsq);
-    const double pre = gamma / (W + Bsq);
-    const double qbw = S.QdotB / W;
+    // utilde^i = Gamma/(W + B^2) (Qt^i + (Q.B) Bn^i / W), Qt^i = Q^i - alpha g^{ti} (Q.n);
+    // 1/(W + B^2) and 1/W from one reciprocal of W (W + B^2)
+    const double gamma = (status == INV_OK) ? w.rs : rsqrt(1.0 - vsq);
+    const double WB = W + Bsq;
+    const double r = 1.0 / (W * WB);
+    const double pre = gamma * W * r;
+    const double qbw = S.QdotB * WB * r;
     pr[U1] = pre * (S.Qc1 - m.alpha * m.c01 * S.Qdotn + qbw * S.Bn1);
     pr[U2] = pre * (S.Qc2 + qbw * S.Bn2);
     pr[U3] = pre * (S.Qc3 + qbw * S.Bn3);

@@ -4,7 +4,8 @@
 // carried to the internal coordinates x1 = log r, x2 = theta, x3 = phi with
 // the exact Jacobian dr/dx1 = r. Christoffel symbols are finite differences
 // of the internal-coordinate metric: 4th-order central differences with
-// step h = 1e-3 in x1 and x2 (the metric does not depend on t or phi).
+// step h = 1e-3 in x1 and x2 (the metric does not depend on t or phi); the
+// same derivatives are also stored themselves for the FP64 source term.
 // Tables are 2-D over the padded (i, j) plane because the metric is
 // stationary and axisymmetric; each component is one contiguous plane.
 #include "grmhd.cuh"
@@ -78,6 +79,12 @@ __global__ void k_geometry(GeomArgs A) {
                 }
                 A.centre[(C_CONN + l * 10 + sym(m, n)) * n2d + q] = 0.5 * s;
             }
+    {
+        const int pm[7] = {0, 0, 0, 1, 1, 2, 3}, pn[7] = {0, 1, 3, 1, 3, 2, 3};
+        for (int s = 1; s <= 2; s++)
+            for (int p = 0; p < 7; p++)
+                A.centre[(C_DG + (s - 1) * 7 + p) * n2d + q] = (pm[p] == pn[p] ? 0.5 : 1.0) * dg[s][pm[p]][pn[p]];
+    }
     const double r = (A.metric != HAMR_METRIC_MINKOWSKI) ? exp(x1c) : 1.0;
     A.centre[C_RHOFLR * n2d + q] = 1.0e-7 / (r * r);
     A.centre[C_UFLR * n2d + q] = 1.0e-9 * pow(r, -10.0 / 3.0);

@@ -26,12 +26,16 @@ enum {
     GI_00, GI_01, GI_11, GI_13, GI_22, GI_33,      // contravariant
     G_DET, G_ALPHA, G_IALPHA, G_IGDET, NGEOM  // G_IALPHA: 1 / alpha; G_IGDET: 1 / sqrt(-g) (0 on the axis)
 };
-// centre tables append: Christoffel symbols (40 = 4 upper x 10 symmetric lower)
-// and the r-dependent floor values
+// centre tables append: Christoffel symbols (40 = 4 upper x 10 symmetric lower),
+// the r-dependent floor values and the metric derivatives d_s g_{mn} (s = 1, 2; the
+// 7 structurally non-zero (m, n) in the order of the covariant entries above), each
+// times 1/2 on the diagonal and 1 off it: the weights of the symmetric contraction
+// (1/2) T^{mn} d_s g_{mn} over m <= n
 constexpr int C_CONN = NGEOM;
 constexpr int C_RHOFLR = NGEOM + 40;
 constexpr int C_UFLR = NGEOM + 41;
-constexpr int NGEOM_C = NGEOM + 42;
+constexpr int C_DG = NGEOM + 42;
+constexpr int NGEOM_C = NGEOM + 56;
 
 // status bits of a cell (OR over the two stages of a step)
 enum : uint8_t { ST_ENTROPY = 1, ST_FAIL = 2, ST_FLOOR = 4 };

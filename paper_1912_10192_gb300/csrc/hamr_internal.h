@@ -171,7 +171,7 @@ cudaError_t launch_centre_b(const BlockView& v, double* P, const double* B, cuda
 cudaError_t launch_block_max(const BlockView& v, const double* P, int q, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_bc(const BlockView& v, double* P, double* B, cudaStream_t s);
 // entropy tracer kappa = p / rho^gam of every padded cell into K (FP32 view of K when mixed)
-// Un: the U^n cache (predictor) or nullptr (corrector); the FP64 predictor stores kappa in its entropy slot
+// Un: the U^n cache (predictor) or nullptr (corrector); the predictor stores kappa in its entropy slot
 cudaError_t launch_kappa(const BlockView& v, const PhysArgs& ph, const double* P, const float* P32, double* K,
                          double* Un, cudaStream_t s);
 // edge values of direction dir: the 7 primitives other than B^dir into their fields of QL / QR,

@@ -199,8 +199,9 @@ __device__ __forceinline__ void flatten_edges(T f, T qc, T& l, T& r) {
 
 // entropy tracer kappa = p / rho^gam of every padded cell into K: one power per
 // cell; the reconstruction carries kappa to the faces like a primitive
-// (FP64 predictor: also into Kn, the entropy slot of the U^n cache, where the
-// cell update takes it for U^n instead of forming the power again)
+// (predictor: also into Kn, the entropy slot of the U^n cache, where the cell
+// update takes it for U^n instead of forming the power again; in mixed
+// precision this kappa is the FP32 one, like the entropy fluxes)
 template <typename T>
 __device__ __forceinline__ void b_kappa(const BlockView& v, T gam, const T* __restrict__ P, T* __restrict__ K,
                                         long t, double* __restrict__ Kn = nullptr) {
@@ -208,8 +209,7 @@ __device__ __forceinline__ void b_kappa(const BlockView& v, T gam, const T* __re
     if (t >= n) return;
     const T kap = (gam - T(1)) * P[UU * v.nc + t] * pow_pos(P[RHO * v.nc + t], -gam);
     K[t] = kap;
-    if constexpr (std::is_same<T, double>::value)
-        if (Kn) Kn[t] = kap;
+    if (Kn) Kn[t] = (double)kap;
 }
 
 template <typename T>
@@ -756,6 +756,37 @@ __device__ __forceinline__ void source_q_state(const TT* __restrict__ gc, long n
     }
 }
 
+// The same source in FP64 from the stored metric derivatives: with the Christoffel
+// symbols formed from the derivatives d_s g of the metric whose inverse raises T,
+// T^k_l Gamma^l_{nu k} = (1/2) T^{kl} d_nu g_{kl} (the terms with d_k g_{l nu} - d_l g_{nu k}
+// cancel against the symmetric T^{kl}), so Q_t = Q_phi = 0 (stationary, axisymmetric
+// metric) and Q_1, Q_2 contract the 7 non-zero d_s g_{mn}; the same number up to
+// rounding order, with a third of the operations.
+__device__ __forceinline__ void source_q_dg(const double* __restrict__ gc, long n2d, long g, const Metric<double>& m,
+                                            const double pf[NPRIM], const Fluid<double>& s, double gam, double Q[4]) {
+    const double p = (gam - 1.0) * pf[UU];
+    const double eta = pf[RHO] + pf[UU] + p + s.bsq;
+    const double ptot = p + 0.5 * s.bsq;
+    const double* u = s.ucon;
+    const double* b = s.bcon;
+    const double e0 = eta * u[0], e1 = eta * u[1], e3 = eta * u[3];
+    const double T[7] = {e0 * u[0] - b[0] * b[0] + ptot * m.c00, e0 * u[1] - b[0] * b[1] + ptot * m.c01,
+                         e0 * u[3] - b[0] * b[3],                e1 * u[1] - b[1] * b[1] + ptot * m.c11,
+                         e1 * u[3] - b[1] * b[3] + ptot * m.c13, eta * u[2] * u[2] - b[2] * b[2] + ptot * m.c22,
+                         e3 * u[3] - b[3] * b[3] + ptot * m.c33};
+    const double* d = gc + (long)C_DG * n2d + g;
+    double q1 = 0.0, q2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 7; k++) {
+        q1 += T[k] * d[k * n2d];
+        q2 += T[k] * d[(7 + k) * n2d];
+    }
+    Q[0] = 0.0;
+    Q[1] = q1 * m.gdet;
+    Q[2] = q2 * m.gdet;
+    Q[3] = 0.0;
+}
+
 template <typename T, typename TT>
 __device__ __forceinline__ void source_q(const TT* __restrict__ gc, long n2d, long g, const Metric<T>& m,
                                         const double pfd[NPRIM], double gam_d, double Q[4]) {
@@ -910,7 +941,7 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
                 for (int q = 0; q < NPRIM; q++) pb[q] = Pb[q * nc + c];
                 Fluid<double> s;
                 fluid_state(pb, m, s);
-                flux_row(pb, s, 0, 1, gam, entropy_kappa(pb, gam), row);
+                flux_row(pb, s, 0, 1, gam, Un[C_ENT * nc + c], row);  // kappa from the tracer pass
             }
 #pragma unroll
             for (int q = 0; q < NCONS; q++) {
@@ -924,10 +955,13 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
         // source sqrt(-g) T^k_l Gamma^l_{nu k} at the centre, from Pf
         double Q[4];
         if constexpr (std::is_same<TS, double>::value) {
-            if (share)
-                source_q_state(v.gc, v.n2d, g, m, pf, sf, gam, Q);
-            else
-                source_q(v.gc, v.n2d, g, m, pf, gam, Q);
+            if (share) {
+                source_q_dg(v.gc, v.n2d, g, m, pf, sf, gam, Q);
+            } else {
+                Fluid<double> s;
+                fluid_state(pf, m, s);
+                source_q_dg(v.gc, v.n2d, g, m, pf, s, gam, Q);
+            }
         } else {
             Metric<float> mf;
             load_metric(v.gc32, v.n2d, g, mf);
@@ -1128,7 +1162,8 @@ __global__ void kb_kappa(const DevBlock* tab, const int* list, PhysArgs ph, int 
     if constexpr (std::is_same<T, double>::value)
         b_kappa<T>(D.v, ph.gam, sigma ? D.Ph : D.P, D.E, tidx(), sigma ? nullptr : D.Un + (long)C_ENT * D.v.nc);
     else
-        b_kappa<T>(D.v, (float)ph.gam, D.P32, reinterpret_cast<float*>(D.E), tidx());
+        b_kappa<T>(D.v, (float)ph.gam, D.P32, reinterpret_cast<float*>(D.E), tidx(),
+                   sigma ? nullptr : D.Un + (long)C_ENT * D.v.nc);
 }
 
 __global__ void kb_to_f32(const DevBlock* tab, const int* list, int sigma) {
@@ -1442,7 +1477,8 @@ cudaError_t launch_kappa(const BlockView& v, const PhysArgs& ph, const double* P
                          double* Un, cudaStream_t s) {
     const long n = (long)v.n1p * v.n2p * v.n3p;
     if (ph.mixed)
-        k_kappa<float><<<nblk(n), BS, 0, s>>>(v, (float)ph.gam, P32, reinterpret_cast<float*>(K), nullptr);
+        k_kappa<float><<<nblk(n), BS, 0, s>>>(v, (float)ph.gam, P32, reinterpret_cast<float*>(K),
+                                              Un ? Un + (long)C_ENT * v.nc : nullptr);
     else
         k_kappa<double><<<nblk(n), BS, 0, s>>>(v, ph.gam, P, K, Un ? Un + (long)C_ENT * v.nc : nullptr);
     return cudaGetLastError();

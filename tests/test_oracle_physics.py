@@ -197,6 +197,40 @@ def _backward_error(d, prim, out, x1, x2):
     return np.abs(U1[:, :5] - U0[:, :5]).sum(axis=1) / scale
 
 
+@pytest.mark.parametrize("a", [0.0, 0.9375])
+def test_source_is_half_T_contracted_with_metric_derivatives(a):
+    """Eq. for the source: with Gamma formed from the metric derivatives d_s g and the
+    inverse metric, sqrt(-g) T^k_l Gamma^l_{nu k} = sqrt(-g) (1/2) T^{kl} d_nu g_{kl}
+    (the form the FP64 cell update evaluates). Checked against the oracle's
+    Christoffel contraction on random magnetised states, with d_s g by the same
+    4th-order differences (h = 1e-3); the energy and phi-momentum sources vanish
+    (stationary, axisymmetric metric)."""
+    d = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, metric=O.METRIC_KS, a=a, gam=13.0 / 9.0)
+    rng = np.random.default_rng(7)
+    h = 1.0e-3
+    for x1, x2 in [(math.log(1.6), 0.3), (math.log(7.0), 1.4), (math.log(30.0), 2.8)]:
+        dg = np.zeros((4, 4, 4))
+        for s_ in (1, 2):
+            e = np.array([0.0, h if s_ == 1 else 0.0, h if s_ == 2 else 0.0])
+            g = [O.geom(d, x1 + k * e[1], x2 + k * e[2])[0] for k in (2, 1, -1, -2)]
+            dg[s_] = (-g[0] + 8.0 * g[1] - 8.0 * g[2] + g[3]) / (12.0 * h)
+        gcov, gcon, gdet, _ = O.geom(d, x1, x2)
+        for _ in range(20):
+            pr = np.array([10 ** rng.uniform(-4, 0), 10 ** rng.uniform(-5, -1), *rng.normal(0, 0.5, 3),
+                           *rng.normal(0, 0.05, 3)])
+            ucon, ucov, bcon, bcov, bsq = O.state(d, pr, x1, x2)
+            p = (13.0 / 9.0 - 1.0) * pr[1]
+            eta = pr[0] + pr[1] + p + bsq
+            T = eta * np.outer(ucon, ucon) + (p + 0.5 * bsq) * gcon - np.outer(bcon, bcon)
+            q = O.source(d, pr, x1, x2)  # conserved slots: mass, energy, momentum 1..3, entropy
+            scale = gdet * np.abs(T).max() * np.abs(dg).max()
+            want = [0.5 * gdet * np.sum(T * dg[nu]) for nu in range(4)]
+            for nu in range(4):
+                assert abs(q[1 + nu] - want[nu]) <= 1e-12 * scale, (nu, q[1 + nu], want[nu])
+            assert abs(q[1]) <= 1e-12 * scale and abs(q[4]) <= 1e-12 * scale
+            assert q[0] == 0.0 and q[5] == 0.0
+
+
 def test_con2prim_round_trip_random_states():
     """prim -> U -> prim with a 10% wrong guess over the whole range
     (rho 1e-6..1, u/rho 1e-4..1e2, Lorentz 1..50, sigma 0..100).
