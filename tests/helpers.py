@@ -42,3 +42,35 @@ def rel_l1(x, ref):
     den = np.abs(ref).sum()
     num = np.abs(x - ref).sum()
     return num / den if den > 0 else num
+
+
+def inversion_bar(d, U, B, x1, x2, p_ref, p_exact, safety=32.0):
+    """Per state and primitive: how far a correct energy inversion of the conserved state U may lie
+    from the reference result p_ref, given the conditioning of the inversion.
+
+    With J = dU/dP (the FP64 prim -> cons map over the five hydro primitives at fixed B, by central
+    differences of the oracle's map at p_ref), two inversions whose residuals U(p) - U are both at the
+    rounding level s of evaluating that map differ by at most sum_m |J^-1|_im 2 s_m to first order.
+    s_m is estimated from two points where the map's value is known to be U up to its own rounding:
+    the reference result and the primitives U was formed from (p_exact), floored at the unit
+    round-off of U_m. A candidate with a larger residual (a wrong root, a dropped term) is not
+    covered by the bar. Returns (n, 5) absolute bars."""
+    import oracle as O
+    n = U.shape[0]
+    J = np.zeros((n, 5, 5))
+    vscale = np.maximum(np.abs(p_ref[:, 2:5]).max(axis=1), 1e-300)
+    for v in range(5):
+        h = 1e-6 * (np.maximum(np.abs(p_ref[:, v]), 1e-300) if v < 2 else vscale)
+        pp, pm = p_ref.copy(), p_ref.copy()
+        pp[:, v] += h
+        pm[:, v] -= h
+        J[:, :, v] = (O.p2u_many(d, pp, x1, x2)[:, :5] - O.p2u_many(d, pm, x1, x2)[:, :5]) / (2 * h)[:, None]
+    Ji = np.abs(np.linalg.inv(J))
+    eps = np.finfo(np.float64).eps
+    pr, pe = p_ref.copy(), p_exact.copy()
+    pr[:, 5:8] = B
+    pe[:, 5:8] = B
+    s = np.maximum(np.abs(O.p2u_many(d, pr, x1, x2)[:, :5] - U[:, :5]),
+                   np.abs(O.p2u_many(d, pe, x1, x2)[:, :5] - U[:, :5]))
+    s = np.maximum(s, eps * np.abs(U[:, :5]))
+    return safety * np.einsum("nim,nm->ni", Ji, 2.0 * s)

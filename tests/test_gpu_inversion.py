@@ -10,7 +10,7 @@ import pytest
 import oracle as O
 from paper_1912_10192_gb300 import workloads as W
 
-from helpers import face_interior, interior, rel_l1, torus_case
+from helpers import face_interior, interior, inversion_bar, rel_l1, torus_case
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -72,9 +72,12 @@ def test_aitken_parity_random_states(start):
     assert np.array_equal(sg, so)
     ok = so == 0
     assert ok.mean() > 0.999
+    # per state within the conditioning bar of the inversion, in distribution within the spread of
+    # two correct inversions (tests/test_inversion_bar.py)
+    bar = inversion_bar(d, U[ok], prim[ok, 5:8], x1[ok], x2[ok], po[ok], prim[ok])
+    assert np.all(np.abs(pg[ok, :5] - po[ok, :5]) <= bar)
     rel = np.abs(pg[ok, :5] - po[ok, :5]) / np.abs(po[ok, :5]).max(axis=1, keepdims=True)
-    assert np.median(rel) < 1e-14 and np.quantile(rel, 0.99) < 1e-11 and rel.max() < 1e-8, \
-        (np.median(rel), np.quantile(rel, 0.99), rel.max())
+    assert np.median(rel) < 1e-14 and np.quantile(rel, 0.99) < 1e-11, (np.median(rel), np.quantile(rel, 0.99))
     # the same iteration: map evaluations agree (a cycle more or less where the stopping test is at rounding)
     assert (ig == io).mean() > 0.99 and np.abs(ig - io).max() <= 3
 

@@ -17,7 +17,7 @@ import pytest
 import oracle as O
 from paper_1912_10192_gb300 import workloads as W
 
-from helpers import NG, face_interior, gpu_grid, interior, rel_l1, torus_case
+from helpers import NG, face_interior, gpu_grid, interior, inversion_bar, rel_l1, torus_case
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -92,13 +92,16 @@ def test_c2p_parity_random_states():
     # the outcome of every inversion (energy / entropy / failed) is identical
     assert np.array_equal(sg, so)
     ok = so == 0
-    # the two results agree to the conditioning of the inversion: the backward
-    # error of the GPU result (U of its primitives against the input U) is as
-    # small as the oracle's own, and forward differences are at round-off for
-    # all but the sigma ~ 100, Lorentz ~ 50 corner
+    # the two results agree to the conditioning of the inversion, state by state
+    # (helpers.inversion_bar: |J^-1| of the prim -> cons map times the rounding
+    # of evaluating it), and in distribution within the oracle's own spread
+    # between two starting points (median 1.8e-15, 99th percentile 7.8e-13,
+    # tests/test_inversion_bar.py) with room for a third rounding path
+    bar = inversion_bar(d, U[ok], prim[ok, 5:8], x1[ok], x2[ok], po[ok], prim[ok])
+    assert np.all(np.abs(pg[ok, :5] - po[ok, :5]) <= bar)
     scale = np.abs(po[ok, :5]).max(axis=1, keepdims=True)
     rel = np.abs(pg[ok, :5] - po[ok, :5]) / scale
-    assert np.median(rel) < 1e-14 and np.quantile(rel, 0.99) < 1e-11 and rel.max() < 1e-8
+    assert np.median(rel) < 1e-14 and np.quantile(rel, 0.99) < 1e-11
     sub = np.nonzero(ok)[0][:20000]
     Ug = O.p2u_many(d, pg[sub], x1[sub], x2[sub])
     Uo = O.p2u_many(d, po[sub], x1[sub], x2[sub])
