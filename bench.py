@@ -156,6 +156,56 @@ def cpu_oracle_rate(n1, n2, n3, steps, warmup, seed=SEED):
     return n1 * n2 * n3 * steps / t, t
 
 
+def _oracle_worker(n, steps, barrier, out, idx):
+    """One process of the all-cores CPU baseline: its own copy of an n[0] x n[1] x n[2] torus block."""
+    sys.path.insert(0, ROOT)
+    import oracle as O
+    geo, prim, bf = torus_inputs(*n)
+    d = O.make_desc(n[0], n[1], n[2], geo.x1min, geo.x2min, geo.x3min, geo.dx1, geo.dx2, geo.dx3,
+                    metric=O.METRIC_KS, a=0.9375, gam=13.0 / 9.0, cour=0.8, bc=TORUS_BC)
+    g = O.Grid(d)
+    g.set(prim, bf)
+    barrier.wait()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        g.step()
+    out[idx] = time.perf_counter() - t0
+
+
+def host_cpu():
+    """nproc and the lscpu lines that name the host's cores."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        txt = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in txt.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Architecture", "Model name", "CPU(s)", "Thread(s) per core", "Core(s) per socket",
+                             "Socket(s)", "CPU max MHz"):
+                info[k.strip()] = v.strip()
+    except (OSError, subprocess.SubprocessError):
+        info["lscpu"] = "unavailable"
+    return info
+
+
+def cpu_oracle_all_cores(n=(128, 64, 32), steps=2, procs=None):
+    """Whole-host oracle rate: one single-threaded oracle process per core, each stepping its own copy of
+    a torus block (independent blocks, the way the paper's CPU code spreads blocks over cores), started
+    together; zone-cycles of all processes / the slowest process's time. Processes are spawned (fresh
+    interpreters, no CUDA state inherited)."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(procs)
+    out = ctx.Array("d", procs)
+    ps = [ctx.Process(target=_oracle_worker, args=(n, steps, barrier, out, i)) for i in range(procs)]
+    for q in ps:
+        q.start()
+    for q in ps:
+        q.join()
+    t = max(out[:])
+    return procs * n[0] * n[1] * n[2] * steps / t, t, procs
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -188,11 +238,12 @@ def field_l1(pa, ba, pr, br):
             "Bface": float(sum(np.abs(x - y).sum() for x, y in zip(fa, fr)) / sum(np.abs(y).sum() for y in fr))}
 
 
-def mixed_leg(args, hamr, torch, blk, dprim, dbf, g64, stream, cells, world, dist):
-    """Times the mixed-precision form on the benchmark workload (same protocol as
+def mixed_leg(args, hamr, torch, blk, dprim, dbf, g64, stream, cells, world, dist, precision=None):
+    """Times a mixed-precision form on the benchmark workload (same protocol as
     the FP64 leg) and states its relative L1 error per field against the FP64
     state after the same number of steps from the same initial state."""
-    gm = hamr.Grid([blk], precision=hamr.PREC_MIXED)
+    precision = hamr.PREC_MIXED if precision is None else precision
+    gm = hamr.Grid([blk], precision=precision)
     gm.set_state(dprim, dbf, stream=stream)
     for _ in range(args.warmup):
         gm.step(stream=stream)
@@ -215,8 +266,12 @@ def mixed_leg(args, hamr, torch, blk, dprim, dbf, g64, stream, cells, world, dis
     pm, bm = gm.get_state()
     p64, b64 = g64.get_state()
     gm.close()
-    return {"form": "mixed: FP32 reconstruction, face fluxes and edge EMFs; FP64 metric, U^n, update, "
-                    "connection source, CT curl and inversion",
+    form = ("mixed: FP32 reconstruction, face fluxes, edge EMFs and connection source; FP64 metric, U^n, "
+            "update and CT curl; Newton iterates in FP32 until a step is below 1e-5 W, then in FP64"
+            if precision == hamr.PREC_MIXED else
+            "mixed, FP64 inversion: FP32 reconstruction, face fluxes and edge EMFs; FP64 metric, U^n, update, "
+            "connection source, CT curl and every Newton iteration")
+    return {"form": form, "precision": int(precision),
             "value": job_rate(cells * args.steps, world, ms_max * 1e-3), "unit": "zone-cycles/s",
             "ms_per_step": ms_max / args.steps, "dtype": "f32+f64",
             "l1_vs_fp64": dict(field_l1(pm, bm, p64, b64), steps=args.warmup + args.steps),
@@ -369,19 +424,30 @@ def options_leg(args, hamr, torch, blk, dprim, dbf, cells, stream):
     return out
 
 
-def amr_leg(hamr, torch, precision=0, tune=True, nper=2):
-    """512-block AMR/LAT torus tree (levels 0..3), whole LAT periods replayed from one CUDA graph.
-    tune=False keeps the default launch shapes and skips the regrid timing."""
+SHAPE_KEYS = ("recon_seg", "recon_x1_sweep", "bs_recon", "bs_flux", "bs_update")
+
+
+def amr_leg(hamr, torch, precision=0, tune=True, nper=3, reps=2):
+    """The 512-block C3 torus tree (two refinement levels, 6-way polar children, LAT levels 0..3),
+    whole LAT periods replayed from one CUDA graph. Every timing starts from the same initial state
+    (restored), runs one untimed period (graph capture) and times nper periods. With tune: the
+    autotuner runs on a representative state, then the default and the tuned launch shapes are timed
+    alternately, reps times each, from the same initial state; the tuned shapes are used only if their
+    median beats the default's by more than the spread of the repetitions. tune=False times the
+    default shapes only."""
     from paper_1912_10192_gb300 import workloads as W
-    blocks = W.amr_torus_tree(n=32)
+    blocks = W.c3_tree(n=32)
     states = W.torus_blocks(blocks, seed=3)
     g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], precision=precision)
-    for i, (p, bf) in enumerate(states):
-        g.set_state(p, bf, block=i)
     lmax = max(b["lat"] for b in blocks)
     per = 2 ** lmax
 
+    def restore():
+        for i, (p, bf) in enumerate(states):
+            g.set_state(p, bf, block=i)
+
     def time_periods():
+        restore()
         g.batch_step(per)  # capture (after any change of launch shapes) + one period
         torch.cuda.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -391,30 +457,48 @@ def amr_leg(hamr, torch, precision=0, tune=True, nper=2):
         ev1.record()
         torch.cuda.synchronize()
         return ev0.elapsed_time(ev1) / nper
-    ms_default = time_periods()
+    summary = W.tree_summary(blocks)
+    real = sum(b["n1"] * b["n2"] * b["n3"] * 2 ** (lmax - b["lat"]) for b in blocks)
+    eff = summary["cells"] * per
+    base = {"workload": "C3: 512-block torus tree (8x4x4 base of 32^3, 16 disk blocks to level 1, 16 of those "
+                        "to level 2, 32 polar blocks split 6-way, polar rows derefined in phi), %d cells, "
+                        "1024x512x512 effective, seed 3" % summary["cells"],
+            "precision": "mixed" if precision else "fp64", "tree": summary,
+            "fine_substeps_per_period": per, "real_zone_cycles_per_period": real}
+    default = g.launch_shapes()
+    default = {k: default[k] for k in SHAPE_KEYS}
     if not tune:
+        ms = time_periods()
         g.close()
-        return {"precision": "mixed" if precision else "fp64", "ms_per_period_default_shapes": ms_default}
-    tune = g.autotune()
-    ms = time_periods()
+        return dict(base, ms_per_period_default_shapes=ms, real_zone_cycles_per_s=real / (ms * 1e-3),
+                    lat_effective_zone_cycles_per_s=eff / (ms * 1e-3))
+    restore()
+    g.batch_step(per)
+    rep = g.autotune()
+    tuned = {k: rep[k] for k in SHAPE_KEYS}
+    found = dict(tuned)
+    times = {"default": [], "tuned": []}
+    for r in range(reps):
+        for name in (("default", "tuned") if r % 2 == 0 else ("tuned", "default")):
+            g.set_launch_shapes(**(default if name == "default" else tuned))
+            times[name].append(time_periods())
+    md, mt = statistics.median(times["default"]), statistics.median(times["tuned"])
+    spread = max(max(v) - min(v) for v in times.values())
+    use_tuned = mt < md - spread
+    ms = mt if use_tuned else md
+    g.set_launch_shapes(**(tuned if use_tuned else default))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g.regrid([hamr.block_from_dict(b) for b in blocks])  # onto the same tree: allocation + device fill
     regrid_ms = (time.perf_counter() - t0) * 1e3
-    real = sum(b["n1"] * b["n2"] * b["n3"] * 2 ** (lmax - b["lat"]) for b in blocks)
-    eff = sum(b["n1"] * b["n2"] * b["n3"] for b in blocks) * per
-    hist = {str(L): sum(1 for b in blocks if b["lat"] == L) for L in range(lmax + 1)}
     g.close()
-    return {"workload": "512-block AMR/LAT torus tree, 32^3 and 32x32x16 blocks, %d cells, seed 3" %
-                        sum(b["n1"] * b["n2"] * b["n3"] for b in blocks),
-            "precision": "mixed" if precision else "fp64", "ms_per_period": ms,
-            "ms_per_period_default_shapes": ms_default,
-            "launch_shapes": {k: tune[k] for k in ("recon_seg", "recon_x1_sweep", "bs_recon", "bs_flux", "bs_update")},
-            "autotune_ms": {k: [round(x, 3) for x in tune[k]] for k in ("ms_seg", "ms_x1", "ms_recon", "ms_flux",
-                                                                       "ms_update")},
-            "fine_substeps_per_period": per, "regrid_same_tree_ms": round(regrid_ms, 1),
-            "real_zone_cycles_per_s": real / (ms * 1e-3), "lat_effective_zone_cycles_per_s": eff / (ms * 1e-3),
-            "lat_levels": hist}
+    return dict(base, ms_per_period=ms, ms_per_period_default_shapes=md, ms_per_period_tuned_shapes=mt,
+                ms_repetitions=times, ms_noise=spread, shapes_used="tuned" if use_tuned else "default",
+                launch_shapes_tuned=found, autotuner_kept_tuned=rep["kept_tuned"],
+                autotuner_groups_ms={"default": round(rep["ms_default"], 3), "tuned": round(rep["ms_tuned"], 3),
+                                     "spread": round(rep["ms_spread"], 3)},
+                regrid_same_tree_ms=round(regrid_ms, 1),
+                real_zone_cycles_per_s=real / (ms * 1e-3), lat_effective_zone_cycles_per_s=eff / (ms * 1e-3))
 
 
 def run_ours(args, rank, world, local):
@@ -471,7 +555,15 @@ def run_ours(args, rank, world, local):
     # ---- chosen form: the same workload with FP32 reconstruction, fluxes and EMFs
     chosen = None
     if not args.fp64_only:
-        chosen = mixed_leg(args, hamr, torch, blk, dprim, dbf, g, stream, cells, world, dist)
+        forms = [mixed_leg(args, hamr, torch, blk, dprim, dbf, g, stream, cells, world, dist, precision=pr)
+                 for pr in (hamr.PREC_MIXED, hamr.PREC_MIXED_FP64INV)]
+        ok = [f for f in forms if f["l1_vs_fp64"]["rho"] <= 1e-6]
+        best = max(ok or forms, key=lambda f: f["value"])
+        chosen = {"value": best["value"], "unit": "zone-cycles/s", "ms_per_step": best["ms_per_step"],
+                  "form": best["form"], "l1_vs_fp64": best["l1_vs_fp64"], "fp64_value": value,
+                  "speedup_vs_fp64": best["value"] / value, "rho_l1_target": 1e-6,
+                  "variants": [{k: f[k] for k in ("precision", "value", "ms_per_step", "l1_vs_fp64", "kernel_ms")}
+                               for f in forms]}
 
     # ---- the learned inversion guess and the batched AMR/LAT tree (single GPU, rank 0 only)
     extra = {}
@@ -537,12 +629,19 @@ def run_ours(args, rank, world, local):
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches_total), "roofline": roofline,
             "step_fp64_tflops": whole, "step_fp64_frac_nominal": whole / FP64_NOMINAL_TFLOPS,
             "kernel_ms": {k: round(v[1], 3) for k, v in timing.items()},
-            "c2p": {k: stats[k] for k in ("c2p_ok", "c2p_entropy", "c2p_fail", "floor_hits")},
-            "chosen_form": chosen, **extra}
+            "c2p": {k: stats[k] for k in ("c2p_ok", "c2p_entropy", "c2p_fail", "floor_hits")}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, t = cpu_oracle_rate(N1, N2, N3, 1, 0)
         line["cpu_baseline"] = {"value": rate, "unit": "zone-cycles/s", "cores": 1, "kind": "oracle",
                                 "sample": "one oracle step of the full 256x128x64 torus block (%.1f s)" % t}
+        arate, at, nproc = cpu_oracle_all_cores()
+        line["cpu_baseline"]["all_cores"] = {
+            "value": arate, "unit": "zone-cycles/s", "cores": nproc, "kind": "oracle",
+            "sample": "%d single-threaded oracle processes, one per core, each 2 steps of its own 128x64x32 "
+                      "torus block, started together (%.1f s)" % (nproc, at),
+            "host": host_cpu()}
+    line.update(extra)
+    line["chosen_form"] = chosen   # last: a truncated tail of the line still shows it
     if rank == 0:
         print(json.dumps(line), flush=True)
     g.close()

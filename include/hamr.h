@@ -82,6 +82,10 @@ extern "C" {
                               (the paper's choice, after Ressler et al. 2017) */
 #define HAMR_PREC_FP64 0  /* every step in FP64 */
 #define HAMR_PREC_MIXED 1 /* FP32 reconstruction, fluxes and EMFs; FP64 metric, inversion, accumulation */
+/* As HAMR_PREC_MIXED, with the connection source and every Newton iteration of
+ * the inversion in FP64 (HAMR_PREC_MIXED iterates in FP32 until the step is
+ * below 1e-5 W and finishes in FP64, and takes the source in FP32). */
+#define HAMR_PREC_MIXED_FP64INV 2
 
 /* One block: a box of cells uniform in the internal coordinates. In a grid
  * of several blocks (Sec. 3.2), blocks tile the domain with cell sizes that
@@ -427,16 +431,25 @@ int hamr_grid_set_mlp(hamr_grid* g, const hamr_mlp* m, int mode);
  * and of the cell update (64, 128; 128 while a network is attached). Shapes
  * change no result bit. The timed launches write only scratch (edge values,
  * fluxes, the midpoint state); call it after a first step or period so the
- * state and dt are representative. Synchronises; a multi-block grid
- * captures its period graph again on the next hamr_batch_step. */
+ * state and dt are representative. After the search the three groups
+ * together are timed with the shapes found and with the default shapes on
+ * the same state, five alternating repetitions each; the found shapes are
+ * kept only if their median is below the defaults' by more than the larger
+ * spread of the repetitions, else the defaults are kept (kept_tuned = 0).
+ * Synchronises; a multi-block grid captures its period graph again on the
+ * next hamr_batch_step. */
 typedef struct {
-    int recon_seg, bs_recon, bs_flux, bs_update; /* the chosen shapes */
+    int recon_seg, bs_recon, bs_flux, bs_update; /* the shapes set on the grid */
     float ms_seg[3];    /* reconstruction, sweeps of 8, 16, 32 cells (128 threads per CTA) */
     float ms_recon[3];  /* reconstruction, 64, 128, 256 threads per CTA (chosen sweep) */
     float ms_flux[3];   /* face fluxes, 64, 128, 256 threads per CTA */
     float ms_update[2]; /* cell update (predictor), 64, 128 threads per CTA */
     int recon_x1_sweep;  /* chosen x1 form: 1 pencil sweeps (the default), 0 warp rows */
     float ms_x1[2];      /* reconstruction with x1 by warp rows, by sweeps (chosen sweep length) */
+    float ms_default;    /* the three groups with the default shapes: median of 5 */
+    float ms_tuned;      /* the same with the shapes the search found: median of 5 */
+    float ms_spread;     /* the larger (max - min) of the two sets of repetitions */
+    int kept_tuned;      /* 1 the found shapes are set, 0 the defaults are */
 } hamr_tune_report;
 
 int hamr_grid_autotune(hamr_grid* g, void* stream, hamr_tune_report* report);

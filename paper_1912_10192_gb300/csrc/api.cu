@@ -135,9 +135,8 @@ struct hamr_grid {
     double fine_dt = 0.0;  // hamr_grid_set_fine_dt (<= 0: CFL)
 };
 
-namespace {
-
-int validate(const hamr_grid_desc* d) {
+// The descriptor checks of hamr_grid_create, also run by hamr_block_step_noalloc.
+int hamr::validate_desc(const hamr_grid_desc* d) {
     if (!d) return fail(HAMR_EINVAL, "descriptor is NULL");
     if (d->nblocks < 1 || !d->blocks) return fail(HAMR_EINVAL, "nblocks must be >= 1 with a block array");
     if (d->metric != HAMR_METRIC_KS && d->metric != HAMR_METRIC_MINKOWSKI && d->metric != HAMR_METRIC_SPHERICAL)
@@ -147,7 +146,7 @@ int validate(const hamr_grid_desc* d) {
     if (!(d->cour > 0.0 && d->cour <= 1.0)) return fail(HAMR_EINVAL, "cour must be in (0, 1]");
     if (d->recon < 0 || d->recon > 2) return fail(HAMR_EINVAL, "unknown recon %d", d->recon);
     if (d->riemann < 0 || d->riemann > 1) return fail(HAMR_EINVAL, "unknown riemann %d", d->riemann);
-    if (d->precision != HAMR_PREC_FP64 && d->precision != HAMR_PREC_MIXED)
+    if (d->precision != HAMR_PREC_FP64 && d->precision != HAMR_PREC_MIXED && d->precision != HAMR_PREC_MIXED_FP64INV)
         return fail(HAMR_EINVAL, "unknown precision %d", d->precision);
     if (d->emf != HAMR_EMF_AVERAGE && d->emf != HAMR_EMF_UPWIND) return fail(HAMR_EINVAL, "unknown emf %d", d->emf);
     if (d->flatten != 0 && d->flatten != 1) return fail(HAMR_EINVAL, "flatten must be 0 or 1, got %d", d->flatten);
@@ -195,6 +194,10 @@ int validate(const hamr_grid_desc* d) {
     return HAMR_OK;
 }
 
+namespace {
+
+int validate(const hamr_grid_desc* d) { return validate_desc(d); }
+
 void free_grid(hamr_grid* g) {
     if (g->amr) amr_destroy(g->amr);
     for (void* p : g->arena)
@@ -231,7 +234,7 @@ int alloc_block(hamr_grid* g, int b) {
     const int nfields = 8 + 3 + 8 + 3 + 8 + 8 + 24 + 3 + 6;
     const size_t stbytes = align256((size_t)v.nc);
     // mixed precision: the FP32 copy of the primitives and FP32 metric/connection tables
-    const bool mixed = (g->desc.precision == HAMR_PREC_MIXED);
+    const bool mixed = (g->desc.precision != HAMR_PREC_FP64);
     const size_t fld32 = align256(sizeof(float) * (size_t)v.nc * NPRIM);
     const size_t tab32 = align256(sizeof(float) * (size_t)v.n2d);
     const int nc32 = NGEOM + 40;  // centre planes the FP32 path reads: metric and connection
@@ -360,7 +363,8 @@ int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out) {
     g->ph.recon = d->recon;
     g->ph.riemann = d->riemann;
     g->ph.floors = d->floors;
-    g->ph.mixed = (d->precision == HAMR_PREC_MIXED);
+    g->ph.mixed = (d->precision != HAMR_PREC_FP64);
+    g->ph.fp64_inv = (d->precision == HAMR_PREC_MIXED_FP64INV);
     g->ph.mlp_img = nullptr;
     g->ph.mlp_err = nullptr;
     g->ph.mlp_mode = HAMR_MLP_FIRST;
@@ -856,6 +860,29 @@ int hamr_grid_autotune(hamr_grid* g, void* stream, hamr_tune_report* rep) {
         if ((rc = time_group(g, ph, 2, cs, &rep->ms_update[c]))) return rc;
     }
     ph.bs_update = ph.mlp_img ? 128 : bsu[std::min_element(rep->ms_update, rep->ms_update + 2) - rep->ms_update];
+    // the found shapes against the defaults on the same state (the timed launches write only
+    // scratch), alternating, five repetitions each of the three groups together
+    PhysArgs ph0 = ph;
+    default_launch_shapes(ph0);
+    float t_def[5], t_tun[5];
+    for (int r = 0; r < 5; r++)
+        for (int o = 0; o < 2; o++) {
+            const bool def = ((r + o) % 2) == 0;
+            float sum = 0.0f;
+            for (int which = 0; which < 3; which++) {
+                float t = 0.0f;
+                if ((rc = time_group(g, def ? ph0 : ph, which, cs, &t))) return rc;
+                sum += t;
+            }
+            (def ? t_def : t_tun)[r] = sum;
+        }
+    std::sort(t_def, t_def + 5);
+    std::sort(t_tun, t_tun + 5);
+    rep->ms_default = t_def[2];
+    rep->ms_tuned = t_tun[2];
+    rep->ms_spread = std::max(t_def[4] - t_def[0], t_tun[4] - t_tun[0]);
+    rep->kept_tuned = (t_tun[2] < t_def[2] - rep->ms_spread) ? 1 : 0;
+    if (!rep->kept_tuned) ph = ph0;
     rep->recon_seg = ph.recon_seg;
     rep->bs_recon = ph.bs_recon;
     rep->bs_flux = ph.bs_flux;

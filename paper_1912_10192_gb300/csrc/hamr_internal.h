@@ -47,7 +47,8 @@ struct PhysArgs {
     int recon;
     int riemann;
     int floors;
-    int mixed;  // 1: reconstruction and face fluxes in FP32 (HAMR_PREC_MIXED)
+    int mixed;  // 1: reconstruction and face fluxes in FP32 (HAMR_PREC_MIXED, HAMR_PREC_MIXED_FP64INV)
+    int fp64_inv;  // 1 (with mixed): connection source and every Newton iteration in FP64
     const uint8_t* mlp_img;  // inference image of the learned inversion guess (nullptr: not used)
     int* mlp_err;            // set to 1 by a CTA whose network waits gave up
     int mlp_mode;            // HAMR_MLP_FIRST or HAMR_MLP_RESCUE
@@ -164,6 +165,8 @@ cudaError_t launch_table_f32(const double* src, float* dst, int nplanes, long st
 
 // api.cu: records the calling thread's last-error message and returns `code`
 int set_error(int code, const char* fmt, ...);
+// api.cu: the descriptor checks of hamr_grid_create (HAMR_OK or HAMR_EINVAL with a message)
+int validate_desc(const hamr_grid_desc* d);
 
 // step.cu
 cudaError_t launch_centre_b(const BlockView& v, double* P, const double* B, cudaStream_t s);

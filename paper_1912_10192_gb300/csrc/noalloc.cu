@@ -64,29 +64,21 @@ using namespace hamr;
 
 extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, double* bface, double dt,
                                        void* stream) {
-    if (!d || !d->blocks || d->nblocks != 1) return set_error(HAMR_EINVAL, "need a descriptor with one block");
+    // every check hamr_grid_create makes (metric, spin, gam, cour, options, cell widths, boundary
+    // placement), then the limits of this entry point
+    int vrc = validate_desc(d);
+    if (vrc) return vrc;
+    if (d->nblocks != 1) return set_error(HAMR_EINVAL, "need a descriptor with one block");
     if (!prim || !bface) return set_error(HAMR_EINVAL, "prim and bface must not be NULL");
     if (!std::isfinite(dt)) return set_error(HAMR_EINVAL, "dt must be finite");
     const hamr_block_desc& B = d->blocks[0];
-    if (B.n1 < 4 || B.n2 < 4 || B.n3 < 4) return set_error(HAMR_EINVAL, "each n must be >= 4");
     const long n1p = B.n1 + 2 * NG, n2p = B.n2 + 2 * NG, n3p = B.n3 + 2 * NG;
     if (n1p * n2p * n3p > NA_CELLS || n1p * n2p > NA_PLANE)
         return set_error(HAMR_EINVAL,
                          "block %dx%dx%d too large for the no-allocation step: (n1+6)(n2+6)(n3+6) must be <= %ld "
                          "and (n1+6)(n2+6) <= %ld",
                          B.n1, B.n2, B.n3, NA_CELLS, NA_PLANE);
-    for (int f = 0; f < 6; f++)
-        if (B.bc[f] < 0 || B.bc[f] > 3) return set_error(HAMR_EINVAL, "unknown bc %d", B.bc[f]);
-    if ((B.bc[2] == HAMR_BC_POLAR || B.bc[3] == HAMR_BC_POLAR) && (B.n3 % 2 != 0 || d->metric == HAMR_METRIC_MINKOWSKI))
-        return set_error(HAMR_EINVAL, "polar bc needs even n3 and the KS metric");
     if (d->precision != HAMR_PREC_FP64) return set_error(HAMR_EINVAL, "the no-allocation step is FP64 only");
-    if (d->emf != HAMR_EMF_AVERAGE && d->emf != HAMR_EMF_UPWIND) return set_error(HAMR_EINVAL, "unknown emf %d", d->emf);
-    if (d->flatten != 0 && d->flatten != 1)
-        return set_error(HAMR_EINVAL, "flatten must be 0 or 1, got %d", d->flatten);
-    if (d->inversion != HAMR_INV_NEWTON && d->inversion != HAMR_INV_AITKEN)
-        return set_error(HAMR_EINVAL, "unknown inversion %d", d->inversion);
-    if (d->floor_frame != HAMR_FLOOR_FLUID && d->floor_frame != HAMR_FLOOR_DRIFT)
-        return set_error(HAMR_EINVAL, "unknown floor_frame %d", d->floor_frame);
     if (d->smr != 0) return set_error(HAMR_EINVAL, "the no-allocation step does not do internal SMR");
 
     double* base = nullptr;
@@ -156,6 +148,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     ph.riemann = d->riemann;
     ph.floors = d->floors;
     ph.mixed = 0;
+    ph.fp64_inv = 0;
     ph.mlp_img = nullptr;
     ph.mlp_err = nullptr;
     ph.mlp_mode = HAMR_MLP_FIRST;

@@ -804,7 +804,9 @@ __device__ __forceinline__ void source_q(const TT* __restrict__ gc, long n2d, lo
 // MLP: the CTA's 128 cells first run the learned guess (mlp.cuh) on the
 // tensor cores; Newton starts from it, with the start from Pf as fallback.
 // TS: precision of the connection source and of the CFL rate (float in mixed
-// precision; the conserved accumulation and the inversion are FP64 always).
+// precision; the conserved accumulation and the inversion are FP64 always). With
+// ph.fp64_inv the mixed form takes the FP64 source and iterates Newton in FP64
+// only (without it, its Newton iteration starts in FP32, c2p.cuh).
 // Floors in the drift frame (Sec. 2.7, after Ressler et al. 2017): the floor
 // material, drho = rho_f - rho and du = u_f - u (each >= 0), moves with the
 // drift velocity of the field lines, the part of the normal-frame velocity
@@ -962,6 +964,10 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
                 fluid_state(pf, m, s);
                 source_q_dg(v.gc, v.n2d, g, m, pf, s, gam, Q);
             }
+        } else if (ph.fp64_inv) {  // mixed form with the FP64 source of the FP64 path
+            Fluid<double> s;
+            fluid_state(pf, m, s);
+            source_q_dg(v.gc, v.n2d, g, m, pf, s, gam, Q);
         } else {
             Metric<float> mf;
             load_metric(v.gc32, v.n2d, g, mf);
@@ -991,7 +997,8 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
     }
     // inversion: energy attempts from the start(s), then the entropy backup
     C2PWork w;
-    if (active) c2p_prepare(U, Bc, m, gam, pr, w, ph.inversion, std::is_same<TS, float>::value ? 1 : 0);
+    if (active)
+        c2p_prepare(U, Bc, m, gam, pr, w, ph.inversion, (std::is_same<TS, float>::value && !ph.fp64_inv) ? 1 : 0);
     if (MLP) {
         // first: the network's start, then the plain one; rescue: the plain start, then the
         // network's where it failed (the CTA runs the network only if one of its cells failed)

@@ -20,7 +20,7 @@ METRIC_KS, METRIC_MINKOWSKI, METRIC_SPHERICAL = 0, 1, 2
 RECON_PPM, RECON_MC, RECON_MINMOD = 0, 1, 2
 FLUX_HLL, FLUX_LLF = 0, 1
 BC_OUTFLOW, BC_PERIODIC, BC_POLAR, BC_OUTFLOW_NOINFLOW, BC_BLOCK = 0, 1, 2, 3, 4
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_MIXED_FP64INV = 0, 1, 2
 EMF_AVERAGE, EMF_UPWIND = 0, 1
 C2P_ENTROPY_ONLY, C2P_MLP, C2P_MLP_RESCUE, C2P_AITKEN = 1, 2, 4, 8
 INV_NEWTON, INV_AITKEN = 0, 1
@@ -68,13 +68,17 @@ class C2PDesc(C.Structure):
 class TuneReport(C.Structure):
     _fields_ = [("recon_seg", C.c_int), ("bs_recon", C.c_int), ("bs_flux", C.c_int), ("bs_update", C.c_int),
                 ("ms_seg", C.c_float * 3), ("ms_recon", C.c_float * 3), ("ms_flux", C.c_float * 3),
-                ("ms_update", C.c_float * 2), ("recon_x1_sweep", C.c_int), ("ms_x1", C.c_float * 2)]
+                ("ms_update", C.c_float * 2), ("recon_x1_sweep", C.c_int), ("ms_x1", C.c_float * 2),
+                ("ms_default", C.c_float), ("ms_tuned", C.c_float), ("ms_spread", C.c_float),
+                ("kept_tuned", C.c_int)]
 
     def as_dict(self):
         return {"recon_seg": self.recon_seg, "bs_recon": self.bs_recon, "bs_flux": self.bs_flux,
                 "bs_update": self.bs_update, "ms_seg": list(self.ms_seg), "ms_recon": list(self.ms_recon),
                 "ms_flux": list(self.ms_flux), "ms_update": list(self.ms_update),
-                "recon_x1_sweep": self.recon_x1_sweep, "ms_x1": list(self.ms_x1)}
+                "recon_x1_sweep": self.recon_x1_sweep, "ms_x1": list(self.ms_x1),
+                "ms_default": self.ms_default, "ms_tuned": self.ms_tuned, "ms_spread": self.ms_spread,
+                "kept_tuned": self.kept_tuned}
 
 
 class MlpTrainArgs(C.Structure):

@@ -575,10 +575,139 @@ def polar_smr_tree(rin, rout, nb=(8, 4, 4), n=32, refine_ib=range(2, 6), lmax=3)
     return assign_lat_levels(blocks, lmax=lmax)
 
 
-def amr_torus_tree(rin=1.2, rout=50.0, n=32):
-    """512 blocks: polar_smr_tree with a base of 8 x 4 x 4 blocks and the base blocks at r index
-    2..5 refined. 13,107,200 cells; effective finest grid 512 x 256 x 256."""
-    return polar_smr_tree(rin, rout, (8, 4, 4), n, range(2, 6))
+def c3_blocks(nb=(8, 4, 4), n=32, rin=1.2, rout=50.0, disk=None, level2=None, polar_split=range(2, 6),
+              polar_cells=None, axis_cells=None, far_cells=None):
+    """Blocks of a two-level refined torus grid over r in [rin, rout] (log), theta in [0, pi],
+    phi in [0, 2 pi): a base of nb blocks of n^3 cells; base rows next to the poles (theta index 0
+    and nb[1] - 1) derefined in phi (external SMR, Sec. 3.3.1: polar_cells, default n x n x n/2);
+    the base blocks (ib, jb) of `disk` (all phi) split into 8 octants of n^3 cells (level 1); the
+    level-1 blocks (i1, j1) of `level2` (global level-1 indices, all phi) split again (level 2);
+    the polar base blocks at the radial indices `polar_split` split 6-way (Sec. 3.3.1: the two
+    children on the axis keep the parent's phi resolution and halve r and theta, the four others
+    halve all three; default cell counts: both n x n x n/2, i.e. axis_cells and far_cells).
+    Each block carries "level" (spatial refinement level) and "group" (for the histogram)."""
+    if disk is None:
+        disk = {(ib, jb) for ib in (3, 4) for jb in (1, 2)}
+    if level2 is None:
+        level2 = {(8, j1) for j1 in (3, 4)}
+    polar_cells = polar_cells or (n, n, n // 2)
+    axis_cells = axis_cells or (n, n, n // 2)
+    far_cells = far_cells or (n, n, n // 2)
+    x1a, x1b = math.log(rin), math.log(rout)
+    hb = ((x1b - x1a) / nb[0], math.pi / nb[1], 2.0 * math.pi / nb[2])
+    blocks = []
+
+    def add(lo, ext, cells, level, group):
+        blocks.append(dict(n1=cells[0], n2=cells[1], n3=cells[2], x1min=lo[0], x2min=lo[1], x3min=lo[2],
+                           dx1=ext[0] / cells[0], dx2=ext[1] / cells[1], dx3=ext[2] / cells[2],
+                           bc=[3, 3, 2, 2, 1, 1], lat=0, level=level, group=group))
+
+    for kb in range(nb[2]):
+        for jb in range(nb[1]):
+            for ib in range(nb[0]):
+                lo = (x1a + ib * hb[0], jb * hb[1], kb * hb[2])
+                polar = jb in (0, nb[1] - 1)
+                half = (hb[0] / 2, hb[1] / 2, hb[2] / 2)
+                if polar and ib in polar_split:
+                    for jc in range(2):
+                        for ic in range(2):
+                            clo = (lo[0] + ic * half[0], lo[1] + jc * half[1])
+                            if (jb == 0 and jc == 0) or (jb == nb[1] - 1 and jc == 1):
+                                add((clo[0], clo[1], lo[2]), (half[0], half[1], hb[2]), axis_cells, 1,
+                                    "polar child on the axis")
+                            else:
+                                for kc in range(2):
+                                    add((clo[0], clo[1], lo[2] + kc * half[2]), half, far_cells, 1,
+                                        "polar child off the axis")
+                elif polar:
+                    add(lo, hb, polar_cells, 0, "polar base")
+                elif (ib, jb) in disk:
+                    q = (hb[0] / 4, hb[1] / 4, hb[2] / 4)
+                    for kc in range(2):
+                        for jc in range(2):
+                            for ic in range(2):
+                                i1, j1, k1 = 2 * ib + ic, 2 * jb + jc, 2 * kb + kc
+                                clo = (x1a + i1 * half[0], j1 * half[1], k1 * half[2])
+                                if (i1, j1) in level2:
+                                    for kf in range(2):
+                                        for jf in range(2):
+                                            for i_f in range(2):
+                                                add((clo[0] + i_f * q[0], clo[1] + jf * q[1], clo[2] + kf * q[2]),
+                                                    q, (n, n, n), 2, "level 2")
+                                else:
+                                    add(clo, half, (n, n, n), 1, "level 1")
+                else:
+                    add(lo, hb, (n, n, n), 0, "base")
+    _mark_block_faces(blocks, periodic=(False, False, True))
+    return blocks
+
+
+def nesting_violations(blocks, period3=2.0 * math.pi):
+    """Pairs of blocks that share a face or an edge (Sec. 3.2 names faces and edges; corners are not
+    constrained) whose cell widths differ by more than a factor 2 in some direction:
+    [(a, b, direction, ratio)]."""
+    boxes = [_box(b) for b in blocks]
+    h = [(b["dx1"], b["dx2"], b["dx3"]) for b in blocks]
+    out = []
+    for a in range(len(blocks)):
+        la, ha = boxes[a]
+        for c in range(a + 1, len(blocks)):
+            lc, hc = boxes[c]
+            overlap = 0
+            touch = 0
+            for d in range(3):
+                tol = 1e-9 * max(ha[d] - la[d], hc[d] - lc[d])
+                shifts = (-period3, 0.0, period3) if d == 2 else (0.0,)
+                best = None
+                for sft in shifts:
+                    lo_, hi_ = max(la[d], lc[d] + sft), min(ha[d], hc[d] + sft)
+                    if hi_ > lo_ + tol:
+                        best = "overlap"
+                        break
+                    if abs(hi_ - lo_) <= tol:
+                        best = "touch"
+                if best is None:
+                    break
+                overlap += best == "overlap"
+                touch += best == "touch"
+            else:
+                if touch >= 1 and overlap >= 1:          # a shared face (2 overlaps) or edge (1 overlap)
+                    for d in range(3):
+                        r = max(h[a][d], h[c][d]) / min(h[a][d], h[c][d])
+                        if r > 2.0 + 1e-9:
+                            out.append((a, c, d + 1, r))
+    return out
+
+
+def c3_tree(rin=1.2, rout=50.0, n=32):
+    """The 512-block torus tree of the batched AMR/LAT configuration (C3): a base of 8 x 4 x 4 blocks;
+    the 16 disk blocks (r index 3-4, theta index 1-2) refined to level 1, the 16 level-1 blocks at
+    global r index 8, theta index 3-4 refined to level 2 (the finest level: a 1024 x 512 x 512
+    effective grid at n = 32); the 32 polar base blocks at r index 2-5 split 6-way; the polar base
+    rows derefined in phi. Cell counts: base and levels 1-2 n^3, polar blocks n x n x n/2
+    (13,107,200 cells at n = 32). Checked: no face or edge neighbours more than a factor 2 apart
+    in any direction; LAT levels from assign_lat_levels."""
+    blocks = c3_blocks(n=n, rin=rin, rout=rout)
+    bad = nesting_violations(blocks)
+    if bad:
+        raise ValueError("C3 tree violates the nesting rule: %s" % bad[:4])
+    return assign_lat_levels(blocks)
+
+
+def tree_summary(blocks):
+    """Counts per group and shape, cells, LAT-level and refinement-level histograms."""
+    groups = {}
+    for b in blocks:
+        key = "%s %dx%dx%d" % (b.get("group", "block"), b["n1"], b["n2"], b["n3"])
+        groups[key] = groups.get(key, 0) + 1
+    lat = {}
+    lev = {}
+    for b in blocks:
+        lat[b["lat"]] = lat.get(b["lat"], 0) + 1
+        lev[b.get("level", 0)] = lev.get(b.get("level", 0), 0) + 1
+    return dict(blocks=len(blocks), cells=int(sum(b["n1"] * b["n2"] * b["n3"] for b in blocks)), groups=groups,
+                lat_levels={str(k): v for k, v in sorted(lat.items())},
+                refinement_levels={str(k): v for k, v in sorted(lev.items())})
 
 
 def _softplus(x):

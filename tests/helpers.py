@@ -44,7 +44,7 @@ def rel_l1(x, ref):
     return num / den if den > 0 else num
 
 
-def inversion_bar(d, U, B, x1, x2, p_ref, p_exact, safety=32.0):
+def inversion_bar(d, U, B, x1, x2, p_ref, p_exact, safety=32.0, p_other=None):
     """Per state and primitive: how far a correct energy inversion of the conserved state U may lie
     from the reference result p_ref, given the conditioning of the inversion.
 
@@ -54,7 +54,9 @@ def inversion_bar(d, U, B, x1, x2, p_ref, p_exact, safety=32.0):
     s_m is estimated from two points where the map's value is known to be U up to its own rounding:
     the reference result and the primitives U was formed from (p_exact), floored at the unit
     round-off of U_m. A candidate with a larger residual (a wrong root, a dropped term) is not
-    covered by the bar. Returns (n, 5) absolute bars."""
+    covered by the bar. For an iteration that stops at a tolerance rather than at round-off (the
+    Aitken pressure iteration), pass the candidate as p_other: its own residual then enters s, and
+    the caller bounds that residual (its backward error) separately. Returns (n, 5) absolute bars."""
     import oracle as O
     n = U.shape[0]
     J = np.zeros((n, 5, 5))
@@ -72,5 +74,57 @@ def inversion_bar(d, U, B, x1, x2, p_ref, p_exact, safety=32.0):
     pe[:, 5:8] = B
     s = np.maximum(np.abs(O.p2u_many(d, pr, x1, x2)[:, :5] - U[:, :5]),
                    np.abs(O.p2u_many(d, pe, x1, x2)[:, :5] - U[:, :5]))
+    if p_other is not None:
+        po = p_other.copy()
+        po[:, 5:8] = B
+        s = np.maximum(s, np.abs(O.p2u_many(d, po, x1, x2)[:, :5] - U[:, :5]))
     s = np.maximum(s, eps * np.abs(U[:, :5]))
     return safety * np.einsum("nim,nm->ni", Ji, 2.0 * s)
+
+
+U32 = 2.0 ** -24
+
+
+def mixed_rounding_per_step(d, prim, bf):
+    """A-priori size of one step's FP32 rounding in the mixed form, per field, relative L1.
+
+    Each face flux computed from FP32 edge values carries a relative error of order the FP32 unit
+    round-off u: a cell's conserved state then moves by up to u sum over its 6 faces of
+    dt/dx |F_m| per component m (the oracle's own first-stage fluxes of the state, at the CFL dt),
+    which the inversion maps to the primitives through |J^-1| (J = dU/dP of the FP64 prim -> cons
+    map); the face field moves by u dt/dx times its EMFs (the B rows of the fluxes). Returns
+    {rho, u, utilde, Bface}: sum over cells of the moved amount / sum |field|."""
+    import oracle as O
+    g = O.Grid(d)
+    g.set(prim, bf)
+    dt = g.dt()
+    P, B = g.get()
+    F = g.fluxes()
+    n1, n2, n3 = d.n1, d.n2, d.n3
+    s = (slice(NG, NG + n3), slice(NG, NG + n2), slice(NG, NG + n1))
+    dx = (d.dx1, d.dx2, d.dx3)
+    dU = np.zeros((5, n3, n2, n1))
+    dB = np.zeros((n3, n2, n1))
+    for dd in range(3):
+        hi = [slice(NG, NG + n3), slice(NG, NG + n2), slice(NG, NG + n1)]
+        hi[2 - dd] = slice(NG + 1, NG + 1 + (n1, n2, n3)[dd])
+        for m in range(5):
+            dU[m] += dt / dx[dd] * (np.abs(F[dd, m][s]) + np.abs(F[dd, m][tuple(hi)]))
+        for m in (6, 7):
+            dB += dt / dx[dd] * 2.0 * np.abs(F[dd, m][s])
+    k, j, i = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+    pr = np.stack([P[v][s].ravel() for v in range(8)], axis=1)
+    x1 = d.x1min + (i.ravel() + 0.5) * d.dx1
+    x2 = d.x2min + (j.ravel() + 0.5) * d.dx2
+    J = np.zeros((len(x1), 5, 5))
+    vs = np.maximum(np.abs(pr[:, 2:5]).max(axis=1), 1e-6)
+    for v in range(5):
+        h = 1e-6 * (np.maximum(np.abs(pr[:, v]), 1e-300) if v < 2 else vs)
+        pp, pm = pr.copy(), pr.copy()
+        pp[:, v] += h
+        pm[:, v] -= h
+        J[:, :, v] = (O.p2u_many(d, pp, x1, x2)[:, :5] - O.p2u_many(d, pm, x1, x2)[:, :5]) / (2 * h)[:, None]
+    dP = np.einsum("nfm,nm->nf", np.abs(np.linalg.inv(J)), U32 * dU.reshape(5, -1).T)
+    return {"rho": dP[:, 0].sum() / np.abs(pr[:, 0]).sum(), "u": dP[:, 1].sum() / np.abs(pr[:, 1]).sum(),
+            "utilde": dP[:, 2:5].sum() / np.abs(pr[:, 2:5]).sum(),
+            "Bface": U32 * dB.sum() / sum(np.abs(B[m][s]).sum() for m in range(3))}

@@ -94,3 +94,31 @@ def test_tree_and_regrid_arguments_checked_on_cpu(libpath):
     assert L.hamr_grid_set_ghost_maps(None, 1, None) == hamr.EINVAL
     n = ctypes.c_int()
     assert L.hamr_tree_adapt(None, 0, None, None, None, None, None, 0, ctypes.byref(n)) == hamr.EINVAL
+
+
+def test_noalloc_step_validates_like_grid_create(libpath):
+    """hamr_block_step_noalloc refuses every descriptor hamr_grid_create refuses, before touching the
+    device or the (here never dereferenced) state pointers, plus its own limits."""
+    L = hamr.lib()
+    ok_block = hamr.block(8, 8, 8, 0.0, 0.0, 0.0, 0.1, 0.1, 0.1, (0, 0, 1, 1, 1, 1))
+    fake = ctypes.c_void_p(256)
+    cases = []
+    cases.append((*_desc([ok_block], a=1.5), b"spin"))
+    bad_dx = hamr.block(8, 8, 8, 0.0, 0.0, 0.0, 0.0, 0.1, 0.1, (0, 0, 1, 1, 1, 1))
+    cases.append((*_desc([bad_dx]), b"dx must be > 0"))
+    polar_x1 = hamr.block(8, 8, 8, 0.0, 0.0, 0.0, 0.1, 0.1, 0.1, (2, 2, 1, 1, 1, 1))
+    cases.append((*_desc([polar_x1]), b"polar bc only on x2"))
+    half_periodic = hamr.block(8, 8, 8, 0.0, 0.0, 0.0, 0.1, 0.1, 0.1, (0, 0, 1, 0, 1, 1))
+    cases.append((*_desc([half_periodic]), b"periodic bc must be on both sides"))
+    cases.append((*_desc([ok_block], gam=3.0), b"gam"))
+    cases.append((*_desc([ok_block], cour=0.0), b"cour"))
+    cases.append((*_desc([ok_block], recon=7), b"unknown recon"))
+    cases.append((*_desc([ok_block], riemann=4), b"unknown riemann"))
+    cases.append((*_desc([ok_block], precision=1), b"FP64 only"))
+    cases.append((*_desc([ok_block], smr=1), b"polar"))
+    big = hamr.block(20, 20, 20, 0.0, 0.0, 0.0, 0.1, 0.1, 0.1, (0, 0, 1, 1, 1, 1))
+    cases.append((*_desc([big]), b"too large for the no-allocation step"))
+    cases.append((*_desc([ok_block, ok_block]), b"one block"))
+    for d, arr, msg in cases:
+        assert L.hamr_block_step_noalloc(ctypes.byref(d), fake, fake, -1.0, None) == hamr.EINVAL, msg
+        assert msg in L.hamr_last_error(), (msg, L.hamr_last_error())

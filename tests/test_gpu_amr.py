@@ -195,10 +195,10 @@ def test_ghost_exchange_matches_oracle(tree):
 
 
 def test_512_block_tree_at_8_cubed_matches_oracle():
-    """The 512-block torus tree of the batched benchmark (external SMR, octree
-    and 6-way polar refinement, four LAT levels) with 8^3-class blocks, one
-    LAT period."""
-    blocks = W.amr_torus_tree(n=8)
+    """The 512-block C3 torus tree of the batched benchmark (external SMR, two
+    octree levels and 6-way polar refinement, four LAT levels) with 8^3-class
+    blocks, one LAT period."""
+    blocks = W.c3_tree(n=8)
     states = W.torus_blocks(blocks, seed=3)
     phys = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, **KS)
     out, dts = run_pair(blocks, states, phys, 1)
@@ -216,7 +216,7 @@ def test_stored_ghost_locations_give_the_same_bits(precision):
     period of the 512-block tree (8^3-class blocks: every kind of neighbour,
     the polar map, prolongation, restriction and time interpolation)."""
     from paper_1912_10192_gb300 import hamr
-    blocks = W.amr_torus_tree(n=8)
+    blocks = W.c3_tree(n=8)
     states = W.torus_blocks(blocks, seed=3)
     res = []
     for maps in (True, False):
@@ -231,12 +231,52 @@ def test_stored_ghost_locations_give_the_same_bits(precision):
         assert np.array_equal(pa, pb, equal_nan=True) and np.array_equal(ba, bb, equal_nan=True)
 
 
+def test_32_cubed_tree_two_levels_matches_oracle():
+    """A tree built like the benchmark's C3 tree at its full block size, so that the kernels and launch
+    shapes the benchmark times are compared cell by cell: 3 x 4 x 1 base blocks of 32^3 (polar rows
+    derefined in phi), the disk blocks at the outer radial index refined to level 1 and one level-1
+    ring refined again to level 2, the polar blocks at radial index 1-2 split 6-way; 60 blocks, 1.54M
+    cells, LAT levels 0 and 1, no nesting violation. One LAT period with the default launch shapes and
+    one with a non-default set (x1 edge values by warp rows, 32-cell sweeps, 64/256-thread CTAs)."""
+    from paper_1912_10192_gb300 import hamr
+    blocks = W.c3_blocks(nb=(3, 4, 1), n=32, disk={(2, 1), (2, 2)}, level2={(5, 3)}, polar_split=[1, 2])
+    assert not W.nesting_violations(blocks)
+    blocks = W.assign_lat_levels(blocks)
+    assert {b["level"] for b in blocks} == {0, 1, 2} and max(b["lat"] for b in blocks) >= 1
+    states = W.torus_blocks(blocks, seed=3)
+    phys = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, **KS)
+    ob = [O.make_block(b["n1"], b["n2"], b["n3"], b["x1min"], b["x2min"], b["x3min"], b["dx1"], b["dx2"],
+                       b["dx3"], b["bc"], b["lat"]) for b in blocks]
+    a = O.AmrGrid(phys, ob)
+    for i, (p, bf) in enumerate(states):
+        a.set(i, p, bf)
+    dto = a.period()
+    ora = [a.get(i) for i in range(len(blocks))]
+    del a
+    lmax = max(b["lat"] for b in blocks)
+    for shapes in ({}, dict(recon_x1_sweep=0, recon_seg=32, bs_recon=64, bs_flux=256, bs_update=64)):
+        g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], metric=phys.metric, a=phys.a, gam=phys.gam,
+                      cour=phys.cour, recon=phys.recon, riemann=phys.riemann, floors=phys.floors)
+        if shapes:
+            g.set_launch_shapes(**shapes)
+        for i, (p, bf) in enumerate(states):
+            g.set_state(p, bf, block=i)
+        st = g.batch_step(2 ** lmax, stats=True)
+        assert abs(st["dt_used"] - dto) <= 1e-13 * dto, (st["dt_used"], dto)
+        out = [(*g.get_state(block=i), *ora[i]) for i in range(len(blocks))]
+        g.close()
+        errs = field_errors(blocks, out)
+        print("32^3 tree vs oracle", shapes, errs)
+        for k, e in errs.items():
+            assert e <= 1e-10, (k, e, errs, shapes)   # the bar of the 512-block tree at 8^3
+
+
 def test_512_block_tree_full_size_properties():
-    """Full size (13.1 M cells): after one LAT period every block keeps div B at
+    """Full size (the C3 tree, 13.1 M cells): after one LAT period every block keeps div B at
     round-off and every face shared by two blocks has one value (the coarse
     face equals the average of the finer faces covering it)."""
     from paper_1912_10192_gb300 import hamr
-    blocks = W.amr_torus_tree(n=32)
+    blocks = W.c3_tree(n=32)
     states = W.torus_blocks(blocks, seed=3)
     g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], metric=0, a=0.9375, gam=13.0 / 9.0, cour=0.8,
                   floors=1)

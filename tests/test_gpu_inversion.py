@@ -72,9 +72,16 @@ def test_aitken_parity_random_states(start):
     assert np.array_equal(sg, so)
     ok = so == 0
     assert ok.mean() > 0.999
-    # per state within the conditioning bar of the inversion, in distribution within the spread of
-    # two correct inversions (tests/test_inversion_bar.py)
-    bar = inversion_bar(d, U[ok], prim[ok, 5:8], x1[ok], x2[ok], po[ok], prim[ok])
+    # the pressure iteration stops at a tolerance (an extrapolation step below 1e-10 W), not at
+    # round-off: its backward error (the relative residual U(p) - U) is bounded like the oracle's
+    # (measured over this law: median 2e-14, 99th percentile 3e-11, max 3e-10 on the CPU), and the
+    # two results differ by at most the conditioning of the inversion times both residuals
+    # (helpers.inversion_bar with the GPU result as p_other)
+    pg8 = pg[ok].copy()
+    pg8[:, 5:8] = prim[ok, 5:8]
+    be = np.abs(O.p2u_many(d, pg8, x1[ok], x2[ok])[:, :5] - U[ok, :5]).sum(axis=1) / np.abs(U[ok, :5]).sum(axis=1)
+    assert be.max() < 1e-8 and np.quantile(be, 0.99) < 1e-10, (be.max(), np.quantile(be, 0.99))
+    bar = inversion_bar(d, U[ok], prim[ok, 5:8], x1[ok], x2[ok], po[ok], prim[ok], p_other=pg[ok])
     assert np.all(np.abs(pg[ok, :5] - po[ok, :5]) <= bar)
     rel = np.abs(pg[ok, :5] - po[ok, :5]) / np.abs(po[ok, :5]).max(axis=1, keepdims=True)
     assert np.median(rel) < 1e-14 and np.quantile(rel, 0.99) < 1e-11, (np.median(rel), np.quantile(rel, 0.99))

@@ -12,25 +12,30 @@ interior cells (the utilde and face-B vectors as one field each).
 * div B stays at FP64 roundoff: each edge EMF is stored once and shared by
   every face that takes its curl.
 
-Bars. FP32 unit roundoff is u = 2^-24 = 6.0e-8. The edge values carry
-O(u |dq|) error (they are formed relative to the cell value), a face flux
-O(u |F|); a step changes a cell by dt/dx sum(F), so the density gains
-O(u) relative error per step, of random sign from step to step. Two fields
-amplify it: the velocity where the field dominates the inertia (the
-momentum-flux error is O(u b^2) against a momentum O(rho); sigma = b^2/rho
-reaches the floor cap of 50, and 99% of the utilde error sits in cells with
-rho < 1e-6), and u_g where it is a small remainder of the total energy (a
-cold, rotating flow: in the thin disk the kinetic energy is ~ (h/r)^-2 ~ 1e3
-times the thermal one). The bars are about 10x the errors measured on GB300
-(FP64 against the same oracle: <= 1e-13):
+Bars. The density, the internal energy and the face field are held to an
+a-priori rounding model (tests/helpers.py mixed_rounding_per_step): a face
+flux formed from FP32 edge values is off by about u = 2^-24 of itself, so
+one step moves a cell's conserved state by up to u sum_faces dt/dx |F_m|,
+which the inversion maps to the primitives through |dP/dU|; the face field
+moves by u dt/dx times its EMFs. The per-step amount is evaluated on the
+initial state with the oracle's own fluxes and accumulated as a random walk
+(sqrt of the number of steps, the signs of the rounding vary from step to
+step): bar = 32 sqrt(N) x per-step. Measured on GB300 against this model:
+density 0.07-2.4, internal energy 0.3-3.3, face field 0.5-11 times
+sqrt(N) x per-step. The full 448x192x384 disk takes the per-step amount of
+the 56x24x48 disk (the same state at 8x the cell width; dt/dx |F| / |U|
+is a Courant number, independent of the resolution), and its density bar
+is also the 1e-6 target. The model gives no useful bound for the velocity:
+near-static cells dominated by the field map a momentum error of order
+u b^2 dt/dx into a large relative velocity error, while the L1 norm is set
+by the moving gas; the velocity bars stay at ~10x the errors measured on
+GB300 (in FP64 against the same oracle: <= 1e-13):
 
-  torus 64x32x16, 1 step     rho 1.0e-9  u_g 6.1e-8  utilde 1.1e-6  Bbar 2.1e-9
-  torus 64x32x16, 10 steps   rho 5.4e-9  u_g 2.0e-7  utilde 1.9e-6  Bbar 8.3e-9
-  disk 56x24x48, 10 steps    rho 4.7e-8  u_g 2.0e-5  utilde 4.3e-6  Bbar 1.1e-8
-  disk 448x192x384, 100 steps against FP64:
-                             rho 6.3e-8  u_g 1.7e-4  utilde 4.5e-6  Bbar 8.4e-9
+  torus 64x32x16, 1 step     utilde 1.1e-6      disk 56x24x48, 10 steps  utilde 4.3e-6
+  torus 64x32x16, 10 steps   utilde 1.9e-6      disk 448x192x384, 100 steps against FP64: utilde 4.5e-6
 
-and for the full disk the density bar is the 1e-6 target itself.
+The variant with the connection source and every Newton iteration in FP64
+(HAMR_PREC_MIXED_FP64INV) is held to the same bars.
 """
 import numpy as np
 import pytest
@@ -38,15 +43,31 @@ import pytest
 import oracle as O
 from paper_1912_10192_gb300 import workloads as W
 
-from helpers import NG, TORUS_BC, face_interior, interior, rel_l1, torus_case
+from helpers import NG, TORUS_BC, face_interior, interior, mixed_rounding_per_step, rel_l1, torus_case
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-BAR_TORUS_1 = {"rho": 1e-8, "u": 1e-6, "utilde": 1e-5, "Bface": 2e-8}
-BAR_TORUS_10 = {"rho": 5e-8, "u": 2e-6, "utilde": 2e-5, "Bface": 1e-7}
-BAR_DISK_10 = {"rho": 5e-7, "u": 2e-4, "utilde": 5e-5, "Bface": 1e-7}
-BAR_DISK_100 = {"rho": 1e-6, "u": 2e-3, "utilde": 5e-5, "Bface": 1e-7}
+UTILDE_BAR = {"torus1": 1e-5, "torus10": 2e-5, "disk10": 5e-5, "disk100": 5e-5}
+K_MODEL = 32.0
+MIXED_FORMS = [1, 2]  # HAMR_PREC_MIXED, HAMR_PREC_MIXED_FP64INV
+
+
+def model_bars(per_step, nsteps, utilde):
+    bars = {k: K_MODEL * np.sqrt(nsteps) * per_step[k] for k in ("rho", "u", "Bface")}
+    bars["utilde"] = utilde
+    return bars
+
+
+_TORUS_STEP = {}
+
+
+def torus_bars(nsteps):
+    """The bars of the 64x32x16 torus after 1 or 10 steps (the rounding model on its initial state)."""
+    if not _TORUS_STEP:
+        _, d, prim, bf = torus_case(64, 32, 16, seed=1912)
+        _TORUS_STEP.update(mixed_rounding_per_step(d, prim, bf))
+    return model_bars(_TORUS_STEP, nsteps, UTILDE_BAR["torus%d" % nsteps])
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -105,17 +126,19 @@ def div_b(d, b):
     return np.abs(div).max() / scale
 
 
-@pytest.mark.parametrize("nsteps,bar", [(1, BAR_TORUS_1), (10, BAR_TORUS_10)])
-def test_mixed_vs_oracle_torus(nsteps, bar):
+@pytest.mark.parametrize("precision", MIXED_FORMS)
+@pytest.mark.parametrize("nsteps", [1, 10])
+def test_mixed_vs_oracle_torus(nsteps, precision):
     _, d, prim, bf = torus_case(64, 32, 16, seed=1912)
-    p, b, used = run_gpu(d, prim, bf, nsteps, precision=1)
+    bar = torus_bars(nsteps)
+    p, b, used = run_gpu(d, prim, bf, nsteps, precision=precision)
     og = O.Grid(d)
     og.set(prim, bf)
     for n in range(nsteps):
         og.step(used[n])  # the oracle takes the mixed run's dt: the comparison is of the update alone
     po, bo = og.get()
     e = errors(d, p, b, po, bo)
-    print("mixed vs oracle, torus 64x32x16, %d steps:" % nsteps, e)
+    print("mixed (%d) vs oracle, torus 64x32x16, %d steps:" % (precision, nsteps), e, "bars", bar)
     for k, v in e.items():
         assert v <= bar[k], (k, v, e)
 
@@ -146,32 +169,40 @@ def test_disk_fp64_parity_with_oracle():
         assert v <= (1e-11 if k == "u" else 1e-12), (k, v, e)
 
 
-def test_mixed_vs_oracle_disk_small():
+@pytest.mark.parametrize("precision", MIXED_FORMS)
+def test_mixed_vs_oracle_disk_small(precision):
     _, d, prim, bf = disk_case(56, 24, 48)
-    p, b, used = run_gpu(d, prim, bf, 10, precision=1)
+    bar = model_bars(mixed_rounding_per_step(d, prim, bf), 10, UTILDE_BAR["disk10"])
+    p, b, used = run_gpu(d, prim, bf, 10, precision=precision)
     og = O.Grid(d)
     og.set(prim, bf)
     for n in range(10):
         og.step(used[n])
     po, bo = og.get()
     e = errors(d, p, b, po, bo)
-    print("mixed vs oracle, tilted disk 56x24x48, 10 steps:", e)
+    print("mixed (%d) vs oracle, tilted disk 56x24x48, 10 steps:" % precision, e, "bars", bar)
     for k, v in e.items():
-        assert v <= BAR_DISK_10[k], (k, v, e)
+        assert v <= bar[k], (k, v, e)
 
 
 def test_mixed_vs_fp64_disk_100_steps():
     """Tilted thin disk 448x192x384 (h/r 0.03, tilt 65 deg, toroidal field beta 10, a 0.9375, r 1.2-200,
     seed 4), 100 steps each at its own CFL dt: relative L1 of the mixed form against the FP64 path."""
+    _, ds, sprim, sbf = disk_case(56, 24, 48)
+    bar = model_bars(mixed_rounding_per_step(ds, sprim, sbf), 100, UTILDE_BAR["disk100"])
+    bar["rho"] = min(bar["rho"], 1e-6)
+    del sprim, sbf
     _, d, prim, bf = disk_case(448, 192, 384)
     p64, b64, dt64 = run_gpu(d, prim, bf, 100, precision=0)
-    pm, bm, dtm = run_gpu(d, prim, bf, 100, precision=1)
-    e = errors(d, pm, bm, p64, b64)
-    print("mixed vs FP64, tilted disk 448x192x384, 100 steps:", e,
-          "relative difference of the elapsed time:", abs(sum(dtm) - sum(dt64)) / sum(dt64))
-    for k, v in e.items():
-        assert v <= BAR_DISK_100[k], (k, v, e)
-    assert div_b(d, bm) <= max(4.0 * div_b(d, b64), 1e-14)
+    for precision in MIXED_FORMS:
+        pm, bm, dtm = run_gpu(d, prim, bf, 100, precision=precision)
+        e = errors(d, pm, bm, p64, b64)
+        print("mixed (%d) vs FP64, tilted disk 448x192x384, 100 steps:" % precision, e, "bars", bar,
+              "relative difference of the elapsed time:", abs(sum(dtm) - sum(dt64)) / sum(dt64))
+        for k, v in e.items():
+            assert v <= bar[k], (precision, k, v, e)
+        assert div_b(d, bm) <= max(4.0 * div_b(d, b64), 1e-14)
+        del pm, bm
 
 
 def test_mixed_tree_periods_vs_oracle():
@@ -197,5 +228,6 @@ def test_mixed_tree_periods_vs_oracle():
     g.close()
     errs = A.field_errors(blocks, out)
     print("mixed tree vs oracle, 2 periods:", errs)
+    bar = torus_bars(10)
     for k, v in errs.items():
-        assert v <= BAR_TORUS_10[k], (k, v, errs)
+        assert v <= bar[k], (k, v, errs)

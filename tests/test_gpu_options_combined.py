@@ -15,7 +15,7 @@ import pytest
 import oracle as O
 
 from helpers import face_interior, gpu_grid, interior, rel_l1, torus_case
-from test_gpu_mixed import BAR_TORUS_1, BAR_TORUS_10, div_b, errors
+from test_gpu_mixed import div_b, errors, torus_bars
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -59,7 +59,7 @@ def test_all_options_against_oracle(precision, nsteps):
     if precision == 0:
         bar = {k: (1e-12 if nsteps == 1 else 1e-9) for k in e}
     else:
-        bar = dict(BAR_TORUS_1 if nsteps == 1 else BAR_TORUS_10)
+        bar = torus_bars(nsteps)
         bar["utilde"] = max(bar["utilde"], 5e-4)
     for k, v in e.items():
         assert v <= bar[k], (k, v, e)
