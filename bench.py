@@ -370,6 +370,25 @@ def inversion_variants(hamr, torch, m, n=1_000_000, seed=6):
     starts["cold"][1] = 1e-3 * starts["cold"][0]
     starts["cold"][2:5] = 0.0
     out = {"states": n}
+    # the start's distance from the answer at which the network's start begins to pay: the true state
+    # perturbed by a relative eps (rho up, u_g down, velocity up), Newton from it against Newton from the
+    # network (which does not see the start)
+    sweep = {}
+    for eps in (1e-4, 1e-3, 1e-2, 5e-2, 2e-1):
+        guess = P.clone()
+        guess[0] *= 1.0 + eps
+        guess[1] *= 1.0 - eps
+        guess[2:5] *= 1.0 + 0.4 * eps
+        row = {}
+        for vname, mlp in (("newton", None), ("network_first", m)):
+            st = torch.zeros(n, dtype=torch.int32, device="cuda")
+            it = torch.zeros(n, dtype=torch.int32, device="cuda")
+            hamr.con2prim(U, B, X1, X2, guess.clone(), st, it, mlp=mlp)
+            ok = st == 0
+            row[vname] = {"iters_per_energy_inversion": float(it[ok].float().mean()) if bool(ok.any()) else None,
+                          "not_energy": float((st != 0).float().mean())}
+        sweep["%g" % eps] = row
+    out["start_distance_sweep"] = sweep
     for sname, guess in starts.items():
         for vname, flags, mlp in (("newton", 0, None), ("aitken", hamr.C2P_AITKEN, None), ("network_first", 0, m)):
             st = torch.zeros(n, dtype=torch.int32, device="cuda")

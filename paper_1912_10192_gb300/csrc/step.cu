@@ -424,6 +424,36 @@ __device__ __forceinline__ const T* face_table(const BlockView& v) {
 
 
 // ---------------------------------------------------------------- fluxes
+// One side's share of an HLL face flux: cF F + cU U of that side's state, where F is its flux row
+// along DIR and U its conserved row (both without sqrt(-g), which the weights carry), accumulated
+// into acc (FIRST: acc is set). Uses that the two rows differ only in the contravariant index:
+//   cF F_q + cU U_q = eta (cF u^D + cU u^t) u_q - (cF b^D + cU b^t) b_q + (cF delta^D_q + cU delta^t_q) ptot,
+// the mass row rho (cF u^D + cU u^t), the energy row adding it, the entropy row kappa times it, and
+// the transverse B slots cF (b^i u^D - b^D u^i) + cU B^i (U's B^i slot is the edge value itself).
+template <int DIR, bool FIRST, typename T>
+__device__ __forceinline__ void hll_side(const T pr[NPRIM], const Fluid<T>& s, T gam, T kappa, T cF, T cU,
+                                         T acc[NFLUX]) {
+    const T p = (gam - T(1)) * pr[UU];
+    const T eta = pr[RHO] + pr[UU] + p + s.bsq;
+    const T ptot = p + T(0.5) * s.bsq;
+    const T tu = cF * s.ucon[DIR] + cU * s.ucon[0];
+    const T tb = cF * s.bcon[DIR] + cU * s.bcon[0];
+    const T a = eta * tu;
+    const T mass = pr[RHO] * tu;
+    T c[NFLUX];
+    c[0] = mass;
+    c[1] = a * s.ucov[0] - tb * s.bcov[0] + cU * ptot + mass;
+    c[2] = a * s.ucov[1] - tb * s.bcov[1] + ((DIR == 1) ? cF * ptot : T(0));
+    c[3] = a * s.ucov[2] - tb * s.bcov[2] + ((DIR == 2) ? cF * ptot : T(0));
+    c[4] = a * s.ucov[3] - tb * s.bcov[3] + ((DIR == 3) ? cF * ptot : T(0));
+    c[5] = kappa * mass;
+    constexpr int i1 = (DIR == 1) ? 2 : 1, i2 = (DIR == 3) ? 2 : 3;
+    c[6] = cF * (s.bcon[i1] * s.ucon[DIR] - s.bcon[DIR] * s.ucon[i1]) + cU * pr[B1 + i1 - 1];
+    c[7] = cF * (s.bcon[i2] * s.ucon[DIR] - s.bcon[DIR] * s.ucon[i2]) + cU * pr[B1 + i2 - 1];
+#pragma unroll
+    for (int q = 0; q < NFLUX; q++) acc[q] = FIRST ? c[q] : acc[q] + c[q];
+}
+
 // HLLE (or LLF) flux through every dir-face: faces 0..n_dir, -1..n_e across.
 template <int DIR, typename T>
 __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const T* __restrict__ QL,
@@ -459,30 +489,17 @@ __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const T*
     // the entropy tracer's edge values sit in the B^dir fields
     const T kapl = QR[(B1 + DIR - 1) * v.nc + c - st], kapr = QL[(B1 + DIR - 1) * v.nc + c];
     const T gam = (T)ph.gam;
-    T UL[NFLUX], FL[NFLUX], UR[NFLUX], FR[NFLUX];
+    Fluid<T> sl, sr;
     T Al, Bl, sdl, Ar, Br, sdr;
-    {
-        Fluid<T> s;
-        fluid_state(pl, m, s);
-        flux_row(pl, s, 0, DIR, gam, kapl, UL);
-        flux_row(pl, s, DIR, DIR, gam, kapl, FL);
-        wave_quadratic(pl, s, m, DIR, gam, Al, Bl, sdl);
-    }
-    {
-        Fluid<T> s;
-        fluid_state(pr, m, s);
-        flux_row(pr, s, 0, DIR, gam, kapr, UR);
-        flux_row(pr, s, DIR, DIR, gam, kapr, FR);
-        wave_quadratic(pr, s, m, DIR, gam, Ar, Br, sdr);
-    }
-    // U's B slots are B^i of the transverse i (b^i u^t - b^t u^i = B^i): the edge values themselves
-    {
-        constexpr int i1 = (DIR == 1) ? B2 : B1, i2 = (DIR == 3) ? B2 : B3;
-        UL[6] = pl[i1];
-        UL[7] = pl[i2];
-        UR[6] = pr[i1];
-        UR[7] = pr[i2];
-    }
+    fluid_state(pl, m, sl);
+    wave_quadratic(pl, sl, m, DIR, gam, Al, Bl, sdl);
+    fluid_state(pr, m, sr);
+    wave_quadratic(pr, sr, m, DIR, gam, Ar, Br, sdr);
+    // F sqrt(-g) = wl F_L + wr F_R - wc (U_R - U_L): the weights first, then each side's
+    // wl F_L + wc U_L (wr F_R - wc U_R) from its fluid state in one pass (hll_side), which forms no
+    // U or F row on its own
+    T wl, wr, wc;
+    const T half = T(0.5) * m.gdet;
     // FP64 HLL with both sides' A > 0 (always for admissible states: A = u^t u^t (w - gam p) - (b^2 + gam p) g^{tt}
     // with g^{tt} < 0 and w - gam p > 0 for gam < 2): the speeds are numerators over AA = A_L A_R, so the
     // maxima compare numerators and the weights
@@ -500,40 +517,41 @@ __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const T*
         if (FBits<T>::of(ns) > 0) {  // ns >= 0
             const T r = m.gdet / (AA * ns);
             const T ra = r * AA;
-            const T wl = nmax * ra, wr = nmin * ra, wc = nmax * nmin * r;
-#pragma unroll
-            for (int q = 0; q < NFLUX; q++)
-                F[q * v.nc + c] = (double)(wr * FR[q] + wl * FL[q] - wc * (UR[q] - UL[q]));
+            wl = nmax * ra;
+            wr = nmin * ra;
+            wc = nmax * nmin * r;
         } else {
-#pragma unroll
-            for (int q = 0; q < NFLUX; q++) F[q * v.nc + c] = (double)(T(0.5) * (FL[q] + FR[q]) * m.gdet);
+            wl = wr = half;
+            wc = T(0);
         }
-        return;
-    }
-    // general form: the two sides' 1/A from one division
-    const T iAA = T(1) / AA;
-    const T iAl = Ar * iAA, iAr = Al * iAA;
-    const T vpl = (Bl + sdl) * iAl, vml = (Bl - sdl) * iAl;
-    const T vpr = (Br + sdr) * iAr, vmr = (Br - sdr) * iAr;
-    // maxima on the integer pipe
-    const T cmax = max_i(T(0), max_i(vpl, vpr));
-    const T cmin = max_i(T(0), max_i(-vml, -vmr));
-    if (ph.riemann == HAMR_FLUX_LLF) {
-        const T cm = max_i(cmax, cmin);
-#pragma unroll
-        for (int q = 0; q < NFLUX; q++)
-            F[q * v.nc + c] = (double)(T(0.5) * (FL[q] + FR[q] - cm * (UR[q] - UL[q])) * m.gdet);
-    } else if (cmax + cmin > T(0)) {
-        // (cmin F_R + cmax F_L - cmax cmin (U_R - U_L)) sqrt(-g) / (cmax + cmin), weights formed once
-        const T w = m.gdet / (cmax + cmin);
-        const T wl = cmax * w, wr = cmin * w, wc = cmax * wr;
-#pragma unroll
-        for (int q = 0; q < NFLUX; q++)
-            F[q * v.nc + c] = (double)(wr * FR[q] + wl * FL[q] - wc * (UR[q] - UL[q]));
     } else {
-#pragma unroll
-        for (int q = 0; q < NFLUX; q++) F[q * v.nc + c] = (double)(T(0.5) * (FL[q] + FR[q]) * m.gdet);
+        // general form: the two sides' 1/A from one division
+        const T iAA = T(1) / AA;
+        const T iAl = Ar * iAA, iAr = Al * iAA;
+        const T vpl = (Bl + sdl) * iAl, vml = (Bl - sdl) * iAl;
+        const T vpr = (Br + sdr) * iAr, vmr = (Br - sdr) * iAr;
+        // maxima on the integer pipe
+        const T cmax = max_i(T(0), max_i(vpl, vpr));
+        const T cmin = max_i(T(0), max_i(-vml, -vmr));
+        if (ph.riemann == HAMR_FLUX_LLF) {
+            wl = wr = half;
+            wc = half * max_i(cmax, cmin);
+        } else if (cmax + cmin > T(0)) {
+            // (cmin F_R + cmax F_L - cmax cmin (U_R - U_L)) sqrt(-g) / (cmax + cmin)
+            const T w = m.gdet / (cmax + cmin);
+            wl = cmax * w;
+            wr = cmin * w;
+            wc = cmax * wr;
+        } else {
+            wl = wr = half;
+            wc = T(0);
+        }
     }
+    T acc[NFLUX];
+    hll_side<DIR, true>(pl, sl, gam, kapl, wl, wc, acc);
+    hll_side<DIR, false>(pr, sr, gam, kapr, wr, -wc, acc);
+#pragma unroll
+    for (int q = 0; q < NFLUX; q++) F[q * v.nc + c] = (double)acc[q];
 }
 
 template <int DIR, typename T>
