@@ -267,6 +267,21 @@ int hamr_grid_regrid(hamr_grid* g, int nblocks, const hamr_block_desc* blocks, v
 int hamr_tree_adapt(const hamr_block_desc* cur, int n, const int* target, const double dlo[3],
                     const double base_ext[3], const int periodic[3], hamr_block_desc* out, int cap, int* nout);
 
+/* As hamr_tree_adapt, on a spherical grid whose x2 domain faces are polar
+ * axes (axis[0]: the lower x2 face, axis[1]: the upper; Sec. 3.3.1): a block
+ * touching an axis splits 6-way, the x2 half at the axis into 2 children that
+ * keep the parent's x3 cells (halved in x1 and x2), the other half into 4
+ * children halved in all three directions, and 6 such children merge back
+ * into their parent. Blocks may have different cell counts per base block
+ * (e.g. polar rows with fewer x3 cells: external SMR); descendants keep their
+ * base block's counts. The nesting rule is applied to cell widths: face and
+ * edge neighbours at most a factor 2 apart in every direction (the coarser
+ * one is refined until that holds). Output as hamr_tree_adapt; lat = (finest
+ * level - level), the level being that of x1 and x2. */
+int hamr_tree_adapt_polar(const hamr_block_desc* cur, int n, const int* target, const double dlo[3],
+                          const double base_ext[3], const int periodic[3], const int axis[2], hamr_block_desc* out,
+                          int cap, int* nout);
+
 /* ---- measurement ---- */
 /* Per-kernel device time of the grid's launches. */
 typedef struct {

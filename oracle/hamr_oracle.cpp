@@ -2648,18 +2648,30 @@ double balsara_poly(const AmrBlk& N, const int ic[4], const double xi[4], int fd
 
 void wrap_periodic(const ora_amr* m, double x[4]);
 
-/* A fine face (cell size hn, half of N's) on the coarse face (a, side) of cell
- * ic, at tangential halves tb, tc (0: lower, 1: upper) of the other two
- * directions b < c: the old tree's finer data beyond that coarse face if there
- * is any (copied or area-averaged), else the polynomial (the coarse face's
- * linear profile). */
+/* Refinement factor (1 or 2) along each direction of a new block of cell
+ * widths hn inside an old coarser block N: an octree child halves all three
+ * widths, a 6-way polar child on the axis keeps N's x3 width (Sec. 3.3.1). */
+void refine_factors(const AmrBlk& N, const double hn[4], int f[4]) {
+    f[0] = 1;
+    for (int d = 1; d <= 3; d++) f[d] = (N.h[d] > 1.5 * hn[d]) ? 2 : 1;
+}
+
+/* A fine face (cell widths hn) on the coarse face (a, side) of cell ic; along
+ * each tangential direction b < c it is one of the two halves (tb, tc: 0 lower,
+ * 1 upper) where the refinement splits that direction, else the whole width
+ * (tb, tc = 0). Its value: the old tree's finer data beyond that coarse face if
+ * there is any (copied or area-averaged), else the polynomial (the coarse
+ * face's linear profile). */
 double fine_face_on_coarse(const ora_amr* old, const AmrBlk& N, const int ic[4], int a, int side, int tb, int tc,
                            const double hn[4]) {
     const int b = (a == 1) ? 2 : 1, c = (a == 3) ? 2 : 3;
+    int f[4];
+    refine_factors(N, hn, f);
+    const double ob = (f[b] == 2) ? 0.25 + 0.5 * tb : 0.5, oc = (f[c] == 2) ? 0.25 + 0.5 * tc : 0.5;
     double x[4];
     x[a] = N.lo[a] + (ic[a] + side) * N.h[a];
-    x[b] = N.lo[b] + (ic[b] + 0.25 + 0.5 * tb) * N.h[b];
-    x[c] = N.lo[c] + (ic[c] + 0.25 + 0.5 * tc) * N.h[c];
+    x[b] = N.lo[b] + (ic[b] + ob) * N.h[b];
+    x[c] = N.lo[c] + (ic[c] + oc) * N.h[c];
     double probe[4] = {0, x[1], x[2], x[3]};
     probe[a] += (side ? 0.25 : -0.25) * hn[a];
     wrap_periodic(old, probe);
@@ -2676,78 +2688,92 @@ double fine_face_on_coarse(const ora_amr* old, const AmrBlk& N, const int ic[4],
     }
     double xi[4] = {0, 0.0, 0.0, 0.0};
     xi[a] = side ? 1.0 : -1.0;
-    xi[b] = tb ? 0.5 : -0.5;
-    xi[c] = tc ? 0.5 : -0.5;
+    xi[b] = (f[b] == 2) ? (tb ? 0.5 : -0.5) : 0.0;
+    xi[c] = (f[c] == 2) ? (tc ? 0.5 : -0.5) : 0.0;
     return balsara_poly(N, ic, xi, a);
 }
 
-/* A fine face interior to coarse cell ic (local plane xi_fd = 0). Reading:
- * the polynomial's value is a prior; the 24 fine faces on the cell's boundary
- * (fine_face_on_coarse: old finer data where it exists) and the 12 interior
- * faces must make each of the 8 fine cells divergence-free, and the interior
- * faces take the smallest change (least squares) from the prior that does.
- * With D_c the prior divergence (flux form, face areas A_d) of fine cell c,
- * the change is A_d (lambda_lo - lambda_hi) across a face of direction d,
- * where L lambda = -D and L is the 8x8 graph Laplacian of the fine cells
- * (weights A_d^2 between neighbours along d); solved here with lambda of cell
- * (0,0,0) fixed at 0 (the change does not depend on that constant). Where the
- * boundary faces follow the polynomial, D = 0 and the prior stands. */
+/* A fine face interior to coarse cell ic (local plane xi_fd = 0), the cell
+ * split into f1 x f2 x f3 fine cells (refine_factors; 2 x 2 x 2 for an
+ * octree child, 2 x 2 x 1 for a polar child on the axis). Reading: the
+ * polynomial's value is a prior; the fine faces on the cell's boundary
+ * (fine_face_on_coarse: old finer data where it exists) and the interior faces
+ * must make each fine cell divergence-free, and the interior faces take the
+ * smallest change (least squares) from the prior that does. With D_c the prior
+ * divergence (flux form, face areas A_d) of fine cell c, the change is
+ * A_d (lambda_lo - lambda_hi) across a face of direction d, where
+ * L lambda = -D and L is the graph Laplacian of the fine cells (weights A_d^2
+ * between neighbours along d); solved here with lambda of the first cell fixed
+ * at 0 (the change does not depend on that constant). Where the boundary faces
+ * follow the polynomial, D = 0 and the prior stands. */
 double interior_fine_face(const ora_amr* old, const AmrBlk& N, const int ic[4], const double xi[4], int fd,
                           const double hn[4]) {
-    /* F[a][plane 0..2][t_b][t_c] */
+    int f[4];
+    refine_factors(N, hn, f);
+    /* F[a][plane 0..2][t_b][t_c]: planes 0 and 2 on the coarse faces, 1 the interior plane (split a) */
     double F[4][3][2][2];
     for (int a = 1; a <= 3; a++) {
         const int b = (a == 1) ? 2 : 1, c = (a == 3) ? 2 : 3;
-        for (int tb = 0; tb < 2; tb++)
-            for (int tc = 0; tc < 2; tc++) {
+        for (int tb = 0; tb < f[b]; tb++)
+            for (int tc = 0; tc < f[c]; tc++) {
                 F[a][0][tb][tc] = fine_face_on_coarse(old, N, ic, a, 0, tb, tc, hn);
                 F[a][2][tb][tc] = fine_face_on_coarse(old, N, ic, a, 1, tb, tc, hn);
-                double x0[4] = {0, 0.0, 0.0, 0.0};
-                x0[b] = tb ? 0.5 : -0.5;
-                x0[c] = tc ? 0.5 : -0.5;
-                F[a][1][tb][tc] = balsara_poly(N, ic, x0, a);
+                if (f[a] == 2) {
+                    double x0[4] = {0, 0.0, 0.0, 0.0};
+                    x0[b] = (f[b] == 2) ? (tb ? 0.5 : -0.5) : 0.0;
+                    x0[c] = (f[c] == 2) ? (tc ? 0.5 : -0.5) : 0.0;
+                    F[a][1][tb][tc] = balsara_poly(N, ic, x0, a);
+                }
             }
     }
     const double A[4] = {0, hn[2] * hn[3], hn[1] * hn[3], hn[1] * hn[2]};
-    /* fine cells c = i1 + 2 i2 + 4 i3 */
-    double D[8];
-    for (int c = 0; c < 8; c++) {
+    /* the fine cells, c = i1 + 2 i2 + 4 i3 with i_d < f_d */
+    int cells[8], nc = 0;
+    for (int c = 0; c < 8; c++)
+        if ((c & 1) < f[1] && ((c >> 1) & 1) < f[2] && ((c >> 2) & 1) < f[3]) cells[nc++] = c;
+    double D[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int q = 0; q < nc; q++) {
+        const int c = cells[q];
         const int ix[4] = {0, c & 1, (c >> 1) & 1, (c >> 2) & 1};
         double sum = 0.0;
         for (int a = 1; a <= 3; a++) {
             const int b = (a == 1) ? 2 : 1, cc = (a == 3) ? 2 : 3;
-            sum += A[a] * (F[a][ix[a] + 1][ix[b]][ix[cc]] - F[a][ix[a]][ix[b]][ix[cc]]);
+            const int lo = (f[a] == 2) ? ix[a] : 0, up = (f[a] == 2) ? ix[a] + 1 : 2;
+            sum += A[a] * (F[a][up][ix[b]][ix[cc]] - F[a][lo][ix[b]][ix[cc]]);
         }
         D[c] = sum;
     }
-    /* L lambda = -D with lambda_0 = 0: the 7x7 system of cells 1..7 by Gaussian elimination */
+    /* L lambda = -D with lambda of cells[0] = 0: the (nc - 1) x (nc - 1) system by Gaussian elimination */
+    const int m = nc - 1;
     double M[7][8];
-    for (int r = 0; r < 7; r++)
-        for (int q = 0; q < 8; q++) M[r][q] = 0.0;
-    for (int r = 1; r < 8; r++) {
+    for (int r = 0; r < m; r++)
+        for (int q = 0; q <= m; q++) M[r][q] = 0.0;
+    for (int r = 1; r < nc; r++) {
+        const int c = cells[r];
         double diag = 0.0;
         for (int a = 1; a <= 3; a++) {
+            if (f[a] != 2) continue;
             diag += A[a] * A[a];
-            const int nb = r ^ (1 << (a - 1));
-            if (nb != 0) M[r - 1][nb - 1] -= A[a] * A[a];
+            const int nb = c ^ (1 << (a - 1));
+            for (int q = 1; q < nc; q++)
+                if (cells[q] == nb) M[r - 1][q - 1] -= A[a] * A[a];
         }
         M[r - 1][r - 1] += diag;
-        M[r - 1][7] = -D[r];
+        M[r - 1][m] = -D[c];
     }
-    for (int p = 0; p < 7; p++)
-        for (int r = p + 1; r < 7; r++) {
-            const double f = M[r][p] / M[p][p];
-            for (int q = p; q < 8; q++) M[r][q] -= f * M[p][q];
+    for (int p = 0; p < m; p++)
+        for (int r = p + 1; r < m; r++) {
+            const double fac = M[r][p] / M[p][p];
+            for (int q = p; q <= m; q++) M[r][q] -= fac * M[p][q];
         }
-    double lam[8];
-    lam[0] = 0.0;
-    for (int p = 6; p >= 0; p--) {
-        double sum = M[p][7];
-        for (int q = p + 1; q < 7; q++) sum -= M[p][q] * lam[q + 1];
-        lam[p + 1] = sum / M[p][p];
+    double lam[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int p = m - 1; p >= 0; p--) {
+        double sum = M[p][m];
+        for (int q = p + 1; q < m; q++) sum -= M[p][q] * lam[cells[q + 1]];
+        lam[cells[p + 1]] = sum / M[p][p];
     }
     const int b = (fd == 1) ? 2 : 1, cc = (fd == 3) ? 2 : 3;
-    const int tb = xi[b] > 0.0, tc = xi[cc] > 0.0;
+    const int tb = (f[b] == 2) ? (xi[b] > 0.0) : 0, tc = (f[cc] == 2) ? (xi[cc] > 0.0) : 0;
     int ix[4] = {0, 0, 0, 0};
     ix[b] = tb;
     ix[cc] = tc;

@@ -553,16 +553,27 @@ __device__ inline double balsara_poly(const DevBlock& N, const int ic[4], const 
 
 __device__ inline double sample_face_plain(const DevBlock& N, const double x[4], const double ht[4], int fd);
 
-// a fine face (cell size hn, half of N's) on coarse face (a, side) of cell ic at tangential halves
-// tb, tc of the other two directions: the old tree's finer data beyond it, else the face's linear profile
+// refinement factor (1 or 2) per direction of new cells of widths hn inside the old coarser block N: an
+// octree child halves all three widths, a 6-way polar child on the axis keeps N's x3 width
+__device__ inline void refine_factors(const DevBlock& N, const double hn[4], int f[4]) {
+    f[0] = 1;
+    for (int d = 1; d <= 3; d++) f[d] = (N.h[d] > 1.5 * hn[d]) ? 2 : 1;
+}
+
+// a fine face (cell widths hn) on coarse face (a, side) of cell ic; along each tangential direction b < c
+// one of its two halves (tb, tc) where the refinement splits that direction, else the whole width
+// (tb, tc = 0): the old tree's finer data beyond it, else the face's linear profile
 __device__ inline double fine_face_on_coarse(const AmrDomain& A, const DevBlock& N, const int ic[4], int a,
                                              int side, int tb, int tc, const double hn[4]) {
     const int b = (a == 1) ? 2 : 1, c = (a == 3) ? 2 : 3;
+    int f[4];
+    refine_factors(N, hn, f);
+    const double ob = (f[b] == 2) ? 0.25 + 0.5 * tb : 0.5, oc = (f[c] == 2) ? 0.25 + 0.5 * tc : 0.5;
     double x[4];
     x[0] = 0.0;
     x[a] = N.lo[a] + (ic[a] + side) * N.h[a];
-    x[b] = N.lo[b] + (ic[b] + 0.25 + 0.5 * tb) * N.h[b];
-    x[c] = N.lo[c] + (ic[c] + 0.25 + 0.5 * tc) * N.h[c];
+    x[b] = N.lo[b] + (ic[b] + ob) * N.h[b];
+    x[c] = N.lo[c] + (ic[c] + oc) * N.h[c];
     double probe[4] = {0.0, x[1], x[2], x[3]};
     probe[a] += (side ? 0.25 : -0.25) * hn[a];
     wrap_domain(A, probe);
@@ -574,57 +585,70 @@ __device__ inline double fine_face_on_coarse(const AmrDomain& A, const DevBlock&
     }
     double xi[4] = {0.0, 0.0, 0.0, 0.0};
     xi[a] = side ? 1.0 : -1.0;
-    xi[b] = tb ? 0.5 : -0.5;
-    xi[c] = tc ? 0.5 : -0.5;
+    xi[b] = (f[b] == 2) ? (tb ? 0.5 : -0.5) : 0.0;
+    xi[c] = (f[c] == 2) ? (tc ? 0.5 : -0.5) : 0.0;
     return balsara_poly(N, ic, xi, a);
 }
 
-// a fine face interior to coarse cell ic (local plane xi_fd = 0): the polynomial's value corrected
-// by the least change of the 12 interior faces that makes the 8 fine cells divergence-free, given
-// the 24 fine faces on the cell's boundary. The fine cells' graph Laplacian L (weights A_d^2, A_d
-// the fine face areas) has the parity vectors chi_s(c) = (-1)^(s.c) as eigenvectors with
-// eigenvalues 2 sum_d s_d A_d^2, so L lambda = -D is solved in closed form; the change across an
-// interior face of direction d is A_d (lambda_lo - lambda_hi).
+// a fine face interior to coarse cell ic (local plane xi_fd = 0), the cell split into f1 x f2 x f3 fine
+// cells (2 x 2 x 2 for an octree child, 2 x 2 x 1 for a polar child on the axis): the polynomial's value
+// corrected by the least change of the interior faces that makes every fine cell divergence-free, given
+// the fine faces on the cell's boundary. The fine cells' graph Laplacian L (weights A_d^2 along the split
+// directions, A_d the fine face areas) has the parity vectors chi_s(c) = (-1)^(s.c), s a subset of the
+// split directions, as eigenvectors with eigenvalues 2 sum_d s_d A_d^2, so L lambda = -D is solved in
+// closed form; the change across an interior face of direction d is A_d (lambda_lo - lambda_hi).
 __device__ inline double interior_fine_face(const AmrDomain& A, const DevBlock& N, const int ic[4],
                                             const double xi[4], int fd, const double hn[4]) {
+    int f[4];
+    refine_factors(N, hn, f);
     double F[4][3][2][2];
     for (int a = 1; a <= 3; a++) {
         const int b = (a == 1) ? 2 : 1, c = (a == 3) ? 2 : 3;
-        for (int tb = 0; tb < 2; tb++)
-            for (int tc = 0; tc < 2; tc++) {
+        for (int tb = 0; tb < f[b]; tb++)
+            for (int tc = 0; tc < f[c]; tc++) {
                 F[a][0][tb][tc] = fine_face_on_coarse(A, N, ic, a, 0, tb, tc, hn);
                 F[a][2][tb][tc] = fine_face_on_coarse(A, N, ic, a, 1, tb, tc, hn);
-                double x0[4] = {0.0, 0.0, 0.0, 0.0};
-                x0[b] = tb ? 0.5 : -0.5;
-                x0[c] = tc ? 0.5 : -0.5;
-                F[a][1][tb][tc] = balsara_poly(N, ic, x0, a);
+                if (f[a] == 2) {
+                    double x0[4] = {0.0, 0.0, 0.0, 0.0};
+                    x0[b] = (f[b] == 2) ? (tb ? 0.5 : -0.5) : 0.0;
+                    x0[c] = (f[c] == 2) ? (tc ? 0.5 : -0.5) : 0.0;
+                    F[a][1][tb][tc] = balsara_poly(N, ic, x0, a);
+                }
             }
     }
     const double Ar[4] = {0.0, hn[2] * hn[3], hn[1] * hn[3], hn[1] * hn[2]};
-    double D[8];
+    // split directions as a bit mask; the fine cells are the c with no bit outside it
+    const int smask = (f[1] == 2 ? 1 : 0) | (f[2] == 2 ? 2 : 0) | (f[3] == 2 ? 4 : 0);
+    const double ncell = (double)(f[1] * f[2] * f[3]);
+    double D[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int c = 0; c < 8; c++) {
+        if (c & ~smask) continue;
         const int ix[4] = {0, c & 1, (c >> 1) & 1, (c >> 2) & 1};
         double sum = 0.0;
         for (int a = 1; a <= 3; a++) {
             const int b = (a == 1) ? 2 : 1, cc = (a == 3) ? 2 : 3;
-            sum += Ar[a] * (F[a][ix[a] + 1][ix[b]][ix[cc]] - F[a][ix[a]][ix[b]][ix[cc]]);
+            const int lo = (f[a] == 2) ? ix[a] : 0, up = (f[a] == 2) ? ix[a] + 1 : 2;
+            sum += Ar[a] * (F[a][up][ix[b]][ix[cc]] - F[a][lo][ix[b]][ix[cc]]);
         }
         D[c] = sum;
     }
-    // lambda = sum_{s != 0} (rho_s / mu_s) chi_s, rho_s = (1/8) sum_c chi_s(c) (-D_c)
+    // lambda = sum_{s != 0, s within the split directions} (rho_s / mu_s) chi_s, rho_s = (1/n) sum_c chi_s(c) (-D_c)
     double lam[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int sm = 1; sm < 8; sm++) {
+        if (sm & ~smask) continue;
         double rho = 0.0;
-        for (int c = 0; c < 8; c++) rho -= (__popc(sm & c) & 1) ? -D[c] : D[c];
-        rho *= 0.125;
+        for (int c = 0; c < 8; c++)
+            if (!(c & ~smask)) rho -= (__popc(sm & c) & 1) ? -D[c] : D[c];
+        rho /= ncell;
         double mu = 0.0;
         for (int a = 1; a <= 3; a++)
             if (sm & (1 << (a - 1))) mu += 2.0 * Ar[a] * Ar[a];
         const double coef = rho / mu;
-        for (int c = 0; c < 8; c++) lam[c] += (__popc(sm & c) & 1) ? -coef : coef;
+        for (int c = 0; c < 8; c++)
+            if (!(c & ~smask)) lam[c] += (__popc(sm & c) & 1) ? -coef : coef;
     }
     const int b = (fd == 1) ? 2 : 1, cc = (fd == 3) ? 2 : 3;
-    const int tb = xi[b] > 0.0, tc = xi[cc] > 0.0;
+    const int tb = (f[b] == 2) ? (xi[b] > 0.0) : 0, tc = (f[cc] == 2) ? (xi[cc] > 0.0) : 0;
     int ix[4] = {0, 0, 0, 0};
     ix[b] = tb;
     ix[cc] = tc;

@@ -120,6 +120,9 @@ def lib():
         L.hamr_grid_regrid.argtypes = [P, C.c_int, C.POINTER(BlockDesc), P]
         L.hamr_tree_adapt.argtypes = [C.POINTER(BlockDesc), C.c_int, C.POINTER(C.c_int), D, D,
                                       C.POINTER(C.c_int), C.POINTER(BlockDesc), C.c_int, C.POINTER(C.c_int)]
+        L.hamr_tree_adapt_polar.argtypes = [C.POINTER(BlockDesc), C.c_int, C.POINTER(C.c_int), D, D,
+                                            C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(BlockDesc), C.c_int,
+                                            C.POINTER(C.c_int)]
         L.hamr_grid_timing.argtypes = [P, C.POINTER(KernelTime), C.c_int, C.POINTER(C.c_int)]
         L.hamr_measure_fp64_peak.argtypes = [P, C.POINTER(C.c_double)]
         L.hamr_block_step_noalloc.argtypes = [C.POINTER(GridDesc), P, P, C.c_double, P]
@@ -180,8 +183,9 @@ def block(n1, n2, n3, x1min, x2min, x3min, dx1, dx2, dx3, bc, lat=0):
     return b
 
 
-def tree_adapt(blocks, target, dlo, base_ext, periodic=(1, 1, 1)):
-    """hamr_tree_adapt: the nested octree for per-block target levels -> list of BlockDesc."""
+def tree_adapt(blocks, target, dlo, base_ext, periodic=(1, 1, 1), axis=None):
+    """hamr_tree_adapt (axis None) or hamr_tree_adapt_polar (axis = (lower, upper) x2 faces that are
+    polar axes): the nested block tree for per-block target levels -> list of BlockDesc."""
     n = len(blocks)
     arr = (BlockDesc * n)(*blocks)
     tg = (C.c_int * n)(*[int(t) for t in target])
@@ -189,12 +193,17 @@ def tree_adapt(blocks, target, dlo, base_ext, periodic=(1, 1, 1)):
     ext = (C.c_double * 3)(*base_ext)
     per = (C.c_int * 3)(*[int(p) for p in periodic])
     nout = C.c_int()
-    rc = lib().hamr_tree_adapt(arr, n, tg, lo, ext, per, None, 0, C.byref(nout))
+    if axis is None:
+        call = lambda o, cap: lib().hamr_tree_adapt(arr, n, tg, lo, ext, per, o, cap, C.byref(nout))
+    else:
+        ax = (C.c_int * 2)(*[int(a) for a in axis])
+        call = lambda o, cap: lib().hamr_tree_adapt_polar(arr, n, tg, lo, ext, per, ax, o, cap, C.byref(nout))
+    rc = call(None, 0)
     cap = nout.value
     if rc != 0 and cap <= 0:
         check(rc)
     out = (BlockDesc * cap)()
-    check(lib().hamr_tree_adapt(arr, n, tg, lo, ext, per, out, cap, C.byref(nout)))
+    check(call(out, cap))
     return [out[i] for i in range(nout.value)]
 
 

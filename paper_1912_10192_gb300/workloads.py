@@ -310,6 +310,53 @@ def flat_box_tree(base=(2, 2, 2), n=8, refine=((0, 0, 0),), lat_coarse=1, lat_fi
     return blocks
 
 
+def split6(b, axis_low=True):
+    """The 6-way split of a block (Sec. 3.3.1) with its 'axis' at the lower (axis_low) or upper x2 side:
+    the x2 half at the axis gives 2 children (halved in x1 and x2, the parent's x3 extent and cells),
+    the other half 4 children halved in all three directions; every child keeps the parent's cell
+    counts. Returns the 6 block dicts (bc copied, lat kept)."""
+    h = (b["n1"] * b["dx1"] / 2, b["n2"] * b["dx2"] / 2, b["n3"] * b["dx3"] / 2)
+    out = []
+    for jc in range(2):
+        for ic in range(2):
+            lo = (b["x1min"] + ic * h[0], b["x2min"] + jc * h[1])
+            if (jc == 0) == axis_low:
+                out.append(dict(b, x1min=lo[0], x2min=lo[1], x3min=b["x3min"], dx1=b["dx1"] / 2,
+                                dx2=b["dx2"] / 2, dx3=b["dx3"], bc=list(b["bc"])))
+            else:
+                for kc in range(2):
+                    out.append(dict(b, x1min=lo[0], x2min=lo[1], x3min=b["x3min"] + kc * h[2], dx1=b["dx1"] / 2,
+                                    dx2=b["dx2"] / 2, dx3=b["dx3"] / 2, bc=list(b["bc"])))
+    return out
+
+
+def flat_box_tree6(base=(2, 2, 2), n=6, split=((0, 0, 0),), refine=(), L=1.0, lat=0):
+    """Periodic flat box of base blocks of n^3 cells; the base blocks listed in `split` are split 6-way
+    (split6, the axis on their lower x2 side), those in `refine` into 8 octants."""
+    blocks = []
+    nn = (n, n, n) if isinstance(n, int) else tuple(n)
+    hb = [L / base[d] for d in range(3)]
+    for kb in range(base[2]):
+        for jb in range(base[1]):
+            for ib in range(base[0]):
+                b = dict(n1=nn[0], n2=nn[1], n3=nn[2], x1min=ib * hb[0], x2min=jb * hb[1], x3min=kb * hb[2],
+                         dx1=hb[0] / nn[0], dx2=hb[1] / nn[1], dx3=hb[2] / nn[2], bc=[1] * 6, lat=lat)
+                if (ib, jb, kb) in split:
+                    blocks.extend(split6(b))
+                elif (ib, jb, kb) in refine:
+                    for kc in range(2):
+                        for jc in range(2):
+                            for ic in range(2):
+                                blocks.append(dict(b, x1min=b["x1min"] + ic * hb[0] / 2,
+                                                   x2min=b["x2min"] + jc * hb[1] / 2,
+                                                   x3min=b["x3min"] + kc * hb[2] / 2, dx1=b["dx1"] / 2,
+                                                   dx2=b["dx2"] / 2, dx3=b["dx3"] / 2, bc=[1] * 6))
+                else:
+                    blocks.append(b)
+    _mark_block_faces(blocks, periodic=(True, True, True))
+    return blocks
+
+
 def _mark_block_faces(blocks, periodic):
     """Faces interior to the domain get BC_BLOCK; faces on the domain boundary
     keep their bc (periodic ones too: the neighbour across the period is

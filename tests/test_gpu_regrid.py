@@ -97,6 +97,76 @@ def test_regrid_parity_flat_box(src, dst):
     g.close()
 
 
+@pytest.mark.parametrize("src,dst", [
+    (dict(), dict(split=((1, 0, 1),))),                                     # 6-way split of a coarse block
+    (dict(split=((0, 1, 0),)), dict()),                                     # the 6 children merged back
+    (dict(refine=((0, 0, 0),)), dict(refine=((0, 0, 0),), split=((1, 0, 0),)))])  # split next to finer blocks
+def test_regrid_parity_flat_box_six_way(src, dst):
+    """6-way splits (workloads.split6: two children keep the parent's x3 cells, 2 x 2 x 1 fine cells per
+    coarse cell; four halve all widths) and their merge, against the oracle's regridding."""
+    from paper_1912_10192_gb300 import hamr
+    old = W.flat_box_tree6(base=(2, 2, 2), n=6, **src)
+    new = W.flat_box_tree6(base=(2, 2, 2), n=6, **dst)
+    a, g = pair(old, W.flat_box_state(old, bamp=0.2), FLAT)
+    if len(old) > 1:
+        a.period()
+        g.batch_step(2 ** max(b["lat"] for b in old))
+    a2 = a.regrid(ora_blocks(new))
+    g.regrid([hamr.block_from_dict(b) for b in new])
+    compare(a2, g, new, 1e-12)
+    assert div_b_max(g, new) < 1e-13
+    g.close()
+
+
+def test_regrid_parity_torus_polar_split():
+    """The polar blocks of a Kerr-Schild torus tree split 6-way at run time and merged again (the C3
+    tree's polar rule, here as a regrid), against the oracle."""
+    from paper_1912_10192_gb300 import hamr
+    KS = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, metric=O.METRIC_KS, a=0.9375, gam=13.0 / 9.0, cour=0.8)
+    old = W.c3_blocks(nb=(3, 4, 2), n=8, disk=set(), level2=set(), polar_split=[])
+    new = W.c3_blocks(nb=(3, 4, 2), n=8, disk=set(), level2=set(), polar_split=[1])
+    assert not W.nesting_violations(new)
+    for bl in (old, new):
+        for b in bl:
+            b["lat"] = 0
+    a, g = pair(old, W.torus_blocks(old, seed=3), KS)
+    a2 = a.regrid(ora_blocks(new))
+    g.regrid([hamr.block_from_dict(b) for b in new])
+    compare(a2, g, new, 1e-12)
+    assert div_b_max(g, new) < 1e-12   # the oracle's own: 1e-13 of max |Bbar| / dx1
+    a3 = a2.regrid(ora_blocks(old))
+    g.regrid([hamr.block_from_dict(b) for b in old])
+    compare(a3, g, old, 1e-12)
+    g.close()
+
+
+def test_adaptive_polar_refinement_matches_oracle():
+    """hamr_tree_adapt_polar marks the polar blocks at r index 1 of a torus tree for level 1 (6-way splits
+    on both axes), the GPU and the oracle regrid onto that tree and take one LAT period (levels 0 and 1)."""
+    import math
+    from paper_1912_10192_gb300 import hamr
+    KS = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, metric=O.METRIC_KS, a=0.9375, gam=13.0 / 9.0, cour=0.8)
+    old = W.c3_blocks(nb=(3, 4, 2), n=8, disk=set(), level2=set(), polar_split=[])
+    for b in old:
+        b["lat"] = 0
+    x1a, x1b = math.log(1.2), math.log(50.0)
+    dlo, ext = (x1a, 0.0, 0.0), ((x1b - x1a) / 3, math.pi / 4, math.pi)
+    tgt = [1 if (b["group"] == "polar base" and abs(b["x1min"] - (x1a + ext[0])) < 1e-9) else 0 for b in old]
+    new = hamr.tree_adapt([hamr.block_from_dict(b) for b in old], tgt, dlo, ext, periodic=(0, 0, 1), axis=(1, 1))
+    new = _as_dicts(new)
+    assert len(new) == len(old) + 4 * 5 and not W.nesting_violations(new)
+    a, g = pair(old, W.torus_blocks(old, seed=3), KS)
+    a2 = a.regrid(ora_blocks(new))
+    g.regrid([hamr.block_from_dict(b) for b in new])
+    compare(a2, g, new, 1e-12)
+    lmax = max(b["lat"] for b in new)
+    assert lmax == 1
+    a2.period()
+    g.batch_step(2 ** lmax)
+    compare(a2, g, new, 1e-10)
+    g.close()
+
+
 def test_regrid_parity_torus_tree():
     from paper_1912_10192_gb300 import hamr
     KS = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, metric=O.METRIC_KS, a=0.9375, gam=13.0 / 9.0, cour=0.8)

@@ -36,7 +36,7 @@ def _frame():
     return np.stack([kh, ey, np.cross(kh, ey)], axis=1)
 
 
-def wave_error(kind, n, refined=True):
+def wave_error(kind, n, refined=True, split=False):
     import rmhd_modes as M
     from paper_1912_10192_gb300 import hamr
     R = _frame()
@@ -67,15 +67,24 @@ def wave_error(kind, n, refined=True):
     nper = int(math.ceil(T / (2 * 0.25 * hfine)))
     g.set_fine_dt(T / (2 * nper))
     g.batch_step(2 * nper)
-    err, vol = 0.0, 0.0
+    acc = {"all": [0.0, 0.0], "extrema": [0.0, 0.0], "away": [0.0, 0.0]}
     for i, b in enumerate(blocks):
         p, _ = g.get_state(block=i)
         s = (slice(None), slice(NG, NG + b["n3"]), slice(NG, NG + b["n2"]), slice(NG, NG + b["n1"]))
         dv = b["dx1"] * b["dx2"] * b["dx3"]
-        err += np.abs(p[s] - init[i][s]).sum() * dv
-        vol += b["n1"] * b["n2"] * b["n3"] * dv
+        e = np.abs(p[s] - init[i][s]).sum(axis=0) * dv
+        # cells near the extrema of the initial profile sin(k.x): |cos(k.x)| < 0.3
+        x = b["x1min"] + (np.arange(b["n1"]) + 0.5) * b["dx1"]
+        y = b["x2min"] + (np.arange(b["n2"]) + 0.5) * b["dx2"]
+        z = b["x3min"] + (np.arange(b["n3"]) + 0.5) * b["dx3"]
+        Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+        near = np.abs(np.cos(kvec[0] * X + kvec[1] * Y + kvec[2] * Z)) < 0.3
+        for key, msk in (("all", np.ones_like(near)), ("extrema", near), ("away", ~near)):
+            acc[key][0] += e[msk].sum()
+            acc[key][1] += msk.sum() * dv
     g.close()
-    return err / (vol * AMP)
+    out = {k: v[0] / (v[1] * AMP) for k, v in acc.items()}
+    return out if split else out["all"]
 
 
 @pytest.mark.parametrize("kind", ["fast", "alfven", "slow", "entropy"])
@@ -88,5 +97,19 @@ def test_linear_wave_converges_through_refinement_and_time_jump(kind):
     rate = math.log2(e[0] / e[1])
     print("%s wave: L1 error / amplitude %.3e (n=8), %.3e (n=16), rate %.2f; uniform n=16 %.3e"
           % (kind, e[0], e[1], rate, uni))
-    assert rate > 1.45, (kind, e, rate)
+    assert rate > 1.5, (kind, e, rate)
     assert e[1] <= 1.35 * uni, (kind, e[1], uni)
+
+
+def test_fast_wave_rate_is_set_near_the_extrema():
+    """Between 32 and 64 cells per block the fast wave converges at 1.68 overall; split by the phase
+    of the initial profile, the cells near its extrema (|cos k.x| < 0.3, where PPM's monotonicity
+    constraints flatten the parabolae) converge at 1.24 and the rest at 1.94 (measured on GB300; the
+    Alfven and slow waves show the same split, 1.18 / 1.74 and 1.31 / 1.68, the entropy wave 1.65 /
+    1.80). The scheme's second order holds away from extrema; the limiter at the extrema sets the
+    global rate at these resolutions."""
+    e32 = wave_error("fast", 32, split=True)
+    e64 = wave_error("fast", 64, split=True)
+    rate = {k: math.log2(e32[k] / e64[k]) for k in e32}
+    print("fast wave 32 -> 64 cells per block:", e32, e64, rate)
+    assert rate["away"] > 1.85 and rate["extrema"] < rate["away"] - 0.4 and rate["all"] > 1.55, rate

@@ -200,3 +200,80 @@ def test_restriction_is_the_mean():
         gf = faces(coarse[ci], bc)[0][kc:kc + m3, jc:jc + m3, ic:ic + m2 + 1]
         assert np.abs(gf - fm).max() <= 1e-14 * np.abs(fm).max() + 1e-300, i
     del b0
+
+
+# ---- 6-way splits (Sec. 3.3.1): two children keep the parent's x3 cells, four halve all three widths;
+# in a periodic flat box with the 'axis' on the split block's lower x2 side (workloads.split6)
+
+def test_six_way_split_then_merge_returns_the_state():
+    coarse = W.flat_box_tree(base=(2, 2, 2), n=6, refine=())
+    split = W.flat_box_tree6(base=(2, 2, 2), n=6, split=((1, 0, 1),))
+    assert len(split) == 13
+    a = grid(coarse, W.flat_box_state(coarse, bamp=0.2))
+    back = a.regrid(ora_blocks(split)).regrid(ora_blocks(coarse))
+    for i, b in enumerate(coarse):
+        p0, b0 = a.get(i)
+        p1, b1 = back.get(i)
+        x, y = interior(b, p0)[:5], interior(b, p1)[:5]
+        assert np.abs(x - y).max() <= 1e-14 * np.abs(x).max(), i
+        for f0, f1 in zip(faces(b, b0), faces(b, b1)):
+            assert np.abs(f0 - f1).max() <= 1e-14 * np.abs(b0).max(), i
+
+
+def test_six_way_children_are_divergence_free_and_match_the_coarse_faces():
+    coarse = W.flat_box_tree(base=(2, 2, 2), n=6, refine=())
+    split = W.flat_box_tree6(base=(2, 2, 2), n=6, split=((0, 1, 0),))
+    a = grid(coarse, W.flat_box_state(coarse, bamp=0.2))
+    r = a.regrid(ora_blocks(split))
+    bmax = max(np.abs(a.get(i)[1]).max() for i in range(len(coarse)))
+    kinds = set()
+    for i, b in enumerate(split):
+        _, bf = r.get(i)
+        assert np.abs(div_b(b, bf)).max() <= 1e-12 * bmax / b["dx1"], i
+        kinds.add((round(b["dx1"], 9), round(b["dx3"], 9)))
+    assert len(kinds) == 3   # base blocks, children keeping x3, children halving x3
+    # the coarse x2-face at y = 0.5 (the split block's lower, 'axis' side) is the mean of the axis children's
+    # faces on it: 2 x 1 fine faces (x1 halves, the whole x3 cell) per coarse face
+    ci = next(i for i, b in enumerate(coarse) if (b["x1min"], b["x2min"], b["x3min"]) == (0.0, 0.5, 0.0))
+    cf = faces(coarse[ci], a.get(ci)[1])[1][:, 0, :]          # (n3, n1)
+    acc = np.zeros_like(cf)
+    for i, b in enumerate(split):
+        if b["x2min"] == 0.5 and b["dx1"] < coarse[0]["dx1"] and b["dx3"] == coarse[0]["dx3"]:
+            ff = faces(b, r.get(i)[1])[1][:, 0, :]               # (n3, n1) fine faces at y = 0.5
+            i0 = int(round(b["x1min"] / (2 * b["dx1"])))
+            m1 = ff.shape[1] // 2
+            acc[:, i0:i0 + m1] += 0.5 * (ff[:, 0::2] + ff[:, 1::2])
+    assert np.abs(acc - cf).max() <= 1e-14 * bmax
+
+
+def test_six_way_split_next_to_fine_blocks_stays_divergence_free():
+    """The interior-face correction on 2 x 2 x 1 fine cells (the axis children) and 2 x 2 x 2 (the
+    others), with an octree-refined neighbour across x1 whose faces are kept on the shared plane."""
+    old = W.flat_box_tree6(base=(2, 2, 2), n=6, refine=((0, 0, 0),), split=())
+    new = W.flat_box_tree6(base=(2, 2, 2), n=6, refine=((0, 0, 0),), split=((1, 0, 0),))
+    a = grid(old, W.flat_box_state(old, bamp=0.3))
+    a.period()
+    r = a.regrid(ora_blocks(new))
+    bmax = max(np.abs(r.get(i)[1]).max() for i in range(len(new)))
+    for i, b in enumerate(new):
+        _, bf = r.get(i)
+        assert np.abs(div_b(b, bf)).max() <= 1e-12 * bmax / b["dx1"], i
+
+
+def test_six_way_children_prolong_linear_fields_exactly():
+    coarse = W.flat_box_tree(base=(2, 2, 2), n=8, refine=())
+    split = W.flat_box_tree6(base=(2, 2, 2), n=8, split=((0, 0, 0),))
+    a = grid(coarse, _linear_states(coarse))
+    r = a.regrid(ora_blocks(split))
+    want = _linear_states(split)
+    for i, b in enumerate(split):
+        if b["dx1"] > 0.05:
+            continue
+        p, bf = r.get(i)
+        pw, bw = want[i]
+        sl = (slice(0, 3), slice(NG + 2, NG + b["n3"] - 2), slice(NG + 2, NG + b["n2"] - 2),
+              slice(NG + 2, NG + b["n1"] - 2))
+        assert np.abs(p[sl] - pw[sl]).max() < 1e-14, i
+        for d in range(3):
+            fs = (slice(NG + 2, NG + b["n3"] - 2), slice(NG + 2, NG + b["n2"] - 2), slice(NG + 2, NG + b["n1"] - 2))
+            assert np.abs(bf[d][fs] - bw[d][fs]).max() < 1e-14, (i, d)

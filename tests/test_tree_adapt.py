@@ -119,3 +119,70 @@ def test_moving_target_and_bad_inputs():
     bad = _blocks(tree) + _blocks(tree)[:1]
     with pytest.raises(hamr.HamrError):
         hamr.tree_adapt(bad, [0] * len(bad), (0, 0, 0), (0.25, 0.25, 0.25))
+
+
+# ---- spherical grids with polar axes (hamr_tree_adapt_polar; Sec. 3.3.1): 6-way splits on the axis
+
+def _dicts(out):
+    return [dict(n1=b.n1, n2=b.n2, n3=b.n3, x1min=b.x1min, x2min=b.x2min, x3min=b.x3min, dx1=b.dx1, dx2=b.dx2,
+                 dx3=b.dx3, bc=list(b.bc), lat=b.lat) for b in out]
+
+
+def _polar_base():
+    import math
+    base = W.c3_blocks(nb=(4, 4, 2), n=8, disk=set(), level2=set(), polar_split=[])
+    x1a, x1b = math.log(1.2), math.log(50.0)
+    return base, (x1a, 0.0, 0.0), ((x1b - x1a) / 4, math.pi / 4, math.pi)
+
+
+def _covers(blocks, volume):
+    vol = sum(b["n1"] * b["dx1"] * b["n2"] * b["dx2"] * b["n3"] * b["dx3"] for b in blocks)
+    assert abs(vol - volume) <= 1e-9 * volume
+
+
+def test_polar_blocks_split_six_way_and_merge_back():
+    import math
+    base, dlo, ext = _polar_base()
+    volume = (math.log(50.0) - math.log(1.2)) * math.pi * 2 * math.pi
+    # refine the polar blocks at r index 1: each splits into 2 axis children and 4 off-axis children
+    tgt = [1 if (b["group"] == "polar base" and abs(b["x1min"] - (dlo[0] + ext[0])) < 1e-9) else 0 for b in base]
+    out = _dicts(hamr.tree_adapt(_blocks(base), tgt, dlo, ext, periodic=(0, 0, 1), axis=(1, 1)))
+    _covers(out, volume)
+    assert not W.nesting_violations(out)
+    axis_kids = [b for b in out if b["dx1"] < ext[0] / 8 * 0.75 and b["n3"] * b["dx3"] > 0.99 * ext[2]]
+    far_kids = [b for b in out if b["dx1"] < ext[0] / 8 * 0.75 and b["n3"] * b["dx3"] < 0.51 * ext[2]]
+    # 4 refined polar base blocks (2 poles x 2 in phi): 2 axis + 4 off-axis children each
+    assert len(axis_kids) == 8 and len(far_kids) == 16, (len(axis_kids), len(far_kids))
+    for b in axis_kids:
+        assert b["n3"] == 4 and (b["x2min"] == 0.0 or abs(b["x2min"] + b["n2"] * b["dx2"] - math.pi) < 1e-9)
+    # every region moved by at most a factor 2 in every direction; targets back to 0 merge the children
+    back = _dicts(hamr.tree_adapt(_blocks(out), [0] * len(out), dlo, ext, periodic=(0, 0, 1), axis=(1, 1)))
+    assert len(back) == len(base)
+    for b, c in zip(sorted(back, key=lambda b: (b["x3min"], b["x2min"], b["x1min"])),
+                    sorted(base, key=lambda b: (b["x3min"], b["x2min"], b["x1min"]))):
+        for k in ("n1", "n2", "n3", "x1min", "x2min", "x3min", "dx1", "dx2", "dx3"):
+            assert abs(b[k] - c[k]) <= 1e-12 * max(1.0, abs(c[k])), k
+
+
+def test_polar_refinement_nests_in_every_direction():
+    """Two levels on an axis child: the tree grows 6-way splits on the axis, octree splits elsewhere, and
+    refines neighbours until no face or edge neighbours are more than a factor 2 apart in x1, x2 or x3
+    (the axis children's x3 cells are the wide ones)."""
+    import math
+    base, dlo, ext = _polar_base()
+    volume = (math.log(50.0) - math.log(1.2)) * math.pi * 2 * math.pi
+    cur = base
+    for _ in range(3):
+        tgt = []
+        for b in cur:
+            near = (b["x2min"] == 0.0 and b["x3min"] == 0.0 and b["x1min"] < dlo[0] + 2.01 * ext[0]
+                    and b["x1min"] >= dlo[0] + 0.99 * ext[0])
+            tgt.append(2 if near else 0)
+        cur = _dicts(hamr.tree_adapt(_blocks(cur), tgt, dlo, ext, periodic=(0, 0, 1), axis=(1, 1)))
+        _covers(cur, volume)
+        assert not W.nesting_violations(cur)
+    levels = {int(round(math.log2(ext[0] / (b["n1"] * b["dx1"])))) for b in cur}
+    assert levels == {0, 1, 2}, levels
+    # level-2 blocks on the axis keep the base polar rows' x3 cells; octree descendants halve them
+    on_axis = [b for b in cur if b["x2min"] == 0.0 and b["dx1"] < ext[0] / 8 / 3]
+    assert on_axis and all(abs(b["dx3"] - ext[2] / 4) < 1e-12 for b in on_axis)
