@@ -2648,6 +2648,12 @@ double balsara_poly(const AmrBlk& N, const int ic[4], const double xi[4], int fd
 
 void wrap_periodic(const ora_amr* m, double x[4]);
 
+/* cell widths a narrower than b in some direction (a block finer than b along it) */
+bool finer_cells(const double a[4], const double b[4]) {
+    return a[1] < b[1] * (1.0 - 1e-9) || a[2] < b[2] * (1.0 - 1e-9) || a[3] < b[3] * (1.0 - 1e-9);
+}
+double cell_volume(const double h[4]) { return h[1] * h[2] * h[3]; }
+
 /* Refinement factor (1 or 2) along each direction of a new block of cell
  * widths hn inside an old coarser block N: an octree child halves all three
  * widths, a 6-way polar child on the axis keeps N's x3 width (Sec. 3.3.1). */
@@ -2676,12 +2682,22 @@ double fine_face_on_coarse(const ora_amr* old, const AmrBlk& N, const int ic[4],
     probe[a] += (side ? 0.25 : -0.25) * hn[a];
     wrap_periodic(old, probe);
     const int n = amr_find(old, probe);
-    if (n >= 0 && old->b[n].h[1] < N.h[1] * (1.0 - 1e-9)) {
+    if (n >= 0 && finer_cells(old->b[n].h, N.h)) {
         double xs[4] = {0, probe[1], probe[2], probe[3]};
         xs[a] -= (side ? 0.25 : -0.25) * hn[a];
+        const AmrBlk& B = old->b[n];
+        if (B.h[b] > 1.5 * hn[b] || B.h[c] > 1.5 * hn[c]) {
+            /* that block's cells are wider than the new face along the plane (an axis child next to
+             * octants): its polynomial's linear profile on its face, the value the new block on the
+             * other side of the plane takes for this face */
+            int icb[4];
+            double xib[4];
+            coarse_cell(B, xs, probe, icb, xib);
+            return balsara_poly(B, icb, xib, a);
+        }
         Src S;
-        S.Pa = old->b[n].g->prim.data();
-        S.Ba = old->b[n].g->bface.data();
+        S.Pa = B.g->prim.data();
+        S.Ba = B.g->bface.data();
         S.Pb = S.Bb = nullptr;
         S.w = 0.0;
         return amr_sample_face(old, n, S, xs, hn, a);
@@ -2833,7 +2849,7 @@ void amr_regrid_fill(ora_amr* old, ora_amr* m) {
                         const int nl = amr_find(old, pl), nr = amr_find(old, pr);
                         int n = nr;
                         const double* probe = pr;
-                        if (n < 0 || (nl >= 0 && old->b[nl].h[1] < old->b[nr].h[1] * (1.0 - 1e-9))) {
+                        if (n < 0 || (nl >= 0 && cell_volume(old->b[nl].h) < cell_volume(old->b[nr].h) * (1.0 - 1e-9))) {
                             n = nl;
                             probe = pl;
                         }
@@ -2843,7 +2859,7 @@ void amr_regrid_fill(ora_amr* old, ora_amr* m) {
                         double xs[4] = {0, probe[1], probe[2], probe[3]};
                         xs[fd] += (probe == pl ? 0.25 : -0.25) * R.h[fd];
                         double v;
-                        if (N.h[1] > R.h[1] * 1.5) {
+                        if (N.h[1] > R.h[1] * 1.5 || N.h[2] > R.h[2] * 1.5 || N.h[3] > R.h[3] * 1.5) {
                             int ic[4];
                             double xi[4];
                             coarse_cell(N, xs, probe, ic, xi);

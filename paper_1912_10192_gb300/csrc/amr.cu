@@ -553,6 +553,12 @@ __device__ inline double balsara_poly(const DevBlock& N, const int ic[4], const 
 
 __device__ inline double sample_face_plain(const DevBlock& N, const double x[4], const double ht[4], int fd);
 
+// cell widths a narrower than b in some direction (a block finer than b along it)
+__device__ inline bool finer_cells(const double a[4], const double b[4]) {
+    return a[1] < b[1] * (1.0 - 1e-9) || a[2] < b[2] * (1.0 - 1e-9) || a[3] < b[3] * (1.0 - 1e-9);
+}
+__device__ inline double cell_volume(const double h[4]) { return h[1] * h[2] * h[3]; }
+
 // refinement factor (1 or 2) per direction of new cells of widths hn inside the old coarser block N: an
 // octree child halves all three widths, a 6-way polar child on the axis keeps N's x3 width
 __device__ inline void refine_factors(const DevBlock& N, const double hn[4], int f[4]) {
@@ -578,10 +584,19 @@ __device__ inline double fine_face_on_coarse(const AmrDomain& A, const DevBlock&
     probe[a] += (side ? 0.25 : -0.25) * hn[a];
     wrap_domain(A, probe);
     const int n = find_block(A, A.tab, probe);
-    if (n >= 0 && A.tab[n].h[1] < N.h[1] * (1.0 - 1e-9)) {
+    if (n >= 0 && finer_cells(A.tab[n].h, N.h)) {
         double xs[4] = {0.0, probe[1], probe[2], probe[3]};
         xs[a] -= (side ? 0.25 : -0.25) * hn[a];
-        return sample_face_plain(A.tab[n], xs, hn, a);
+        const DevBlock& B = A.tab[n];
+        if (B.h[b] > 1.5 * hn[b] || B.h[c] > 1.5 * hn[c]) {
+            // its cells wider than the new face along the plane: its polynomial's linear profile on its
+            // face, the value the new block on the other side of the plane takes for this face
+            int icb[4];
+            double xib[4];
+            coarse_cell(B, xs, probe, icb, xib);
+            return balsara_poly(B, icb, xib, a);
+        }
+        return sample_face_plain(B, xs, hn, a);
     }
     double xi[4] = {0.0, 0.0, 0.0, 0.0};
     xi[a] = side ? 1.0 : -1.0;
@@ -715,7 +730,7 @@ __global__ void k_regrid_faces(AmrDomain A, const DevBlock* ntab) {
     const int nl = find_block(A, A.tab, pl), nr = find_block(A, A.tab, pr);
     int n = nr;
     bool left = false;
-    if (n < 0 || (nl >= 0 && A.tab[nl].h[1] < A.tab[nr].h[1] * (1.0 - 1e-9))) {
+    if (n < 0 || (nl >= 0 && cell_volume(A.tab[nl].h) < cell_volume(A.tab[nr].h) * (1.0 - 1e-9))) {
         n = nl;
         left = true;
     }
@@ -725,7 +740,7 @@ __global__ void k_regrid_faces(AmrDomain A, const DevBlock* ntab) {
     double xs[4] = {0.0, probe[1], probe[2], probe[3]};
     xs[fd] += (left ? 0.25 : -0.25) * R.h[fd];
     double val;
-    if (N.h[1] > R.h[1] * 1.5) {
+    if (N.h[1] > R.h[1] * 1.5 || N.h[2] > R.h[2] * 1.5 || N.h[3] > R.h[3] * 1.5) {
         int ic[4];
         double xi[4];
         coarse_cell(N, xs, probe, ic, xi);

@@ -104,10 +104,16 @@ struct Fluid {
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 
+// The spatial covariant components need no lowering of u^mu: with u^mu = Gamma n^mu + (0, utilde^i)
+// and n_i = 0, u_i = g_ij utilde^j; then g_ij utilde^i utilde^j = utilde^i u_i, and
+// u_t = Gamma n_t + g_tj utilde^j = -alpha Gamma + g_t1 utilde^1 + g_t3 utilde^3.
 template <typename T>
 __device__ __forceinline__ void fluid_state(const T pr[NPRIM], const Metric<T>& m, Fluid<T>& s) {
     const T q1 = pr[U1], q2 = pr[U2], q3 = pr[U3];
-    T qsq = m.g11 * q1 * q1 + m.g22 * q2 * q2 + m.g33 * q3 * q3 + T(2) * m.g13 * q1 * q3;
+    s.ucov[1] = m.g11 * q1 + m.g13 * q3;
+    s.ucov[2] = m.g22 * q2;
+    s.ucov[3] = m.g13 * q1 + m.g33 * q3;
+    const T qsq = q1 * s.ucov[1] + q2 * s.ucov[2] + q3 * s.ucov[3];
     const T g2 = T(1) + qsq;
     const T ig = rsq(g2);  // 1 / Gamma
     const T gamma = g2 * ig;
@@ -115,7 +121,7 @@ __device__ __forceinline__ void fluid_state(const T pr[NPRIM], const Metric<T>& 
     s.ucon[1] = q1 - gamma * m.alpha * m.c01;
     s.ucon[2] = q2;
     s.ucon[3] = q3;
-    lower4(m, s.ucon, s.ucov);
+    s.ucov[0] = m.g01 * q1 + m.g03 * q3 - m.alpha * gamma;
     T bt = pr[B1] * s.ucov[1] + pr[B2] * s.ucov[2] + pr[B3] * s.ucov[3];
     T iut = m.alpha * ig;
     s.bcon[0] = bt;

@@ -440,18 +440,33 @@ __device__ __forceinline__ void hll_side(const T pr[NPRIM], const Fluid<T>& s, T
     const T tb = cF * s.bcon[DIR] + cU * s.bcon[0];
     const T a = eta * tu;
     const T mass = pr[RHO] * tu;
-    T c[NFLUX];
-    c[0] = mass;
-    c[1] = a * s.ucov[0] - tb * s.bcov[0] + cU * ptot + mass;
-    c[2] = a * s.ucov[1] - tb * s.bcov[1] + ((DIR == 1) ? cF * ptot : T(0));
-    c[3] = a * s.ucov[2] - tb * s.bcov[2] + ((DIR == 2) ? cF * ptot : T(0));
-    c[4] = a * s.ucov[3] - tb * s.bcov[3] + ((DIR == 3) ? cF * ptot : T(0));
-    c[5] = kappa * mass;
+    const T cfp = cF * ptot;
     constexpr int i1 = (DIR == 1) ? 2 : 1, i2 = (DIR == 3) ? 2 : 3;
-    c[6] = cF * (s.bcon[i1] * s.ucon[DIR] - s.bcon[DIR] * s.ucon[i1]) + cU * pr[B1 + i1 - 1];
-    c[7] = cF * (s.bcon[i2] * s.ucon[DIR] - s.bcon[DIR] * s.ucon[i2]) + cU * pr[B1 + i2 - 1];
+    const T fu = cF * s.ucon[DIR], fb = cF * s.bcon[DIR];
+    // the second side's terms are summed into the running total innermost, so its products fuse
+    // with the accumulation (no separate addition per component)
+    T r[NFLUX];
 #pragma unroll
-    for (int q = 0; q < NFLUX; q++) acc[q] = FIRST ? c[q] : acc[q] + c[q];
+    for (int q = 0; q < NFLUX; q++) r[q] = acc[q];
+    if constexpr (FIRST) {
+        acc[0] = mass;
+        acc[1] = a * s.ucov[0] + (-tb * s.bcov[0] + (cU * ptot + mass));
+        acc[2] = (DIR == 1) ? a * s.ucov[1] + (-tb * s.bcov[1] + cfp) : a * s.ucov[1] - tb * s.bcov[1];
+        acc[3] = (DIR == 2) ? a * s.ucov[2] + (-tb * s.bcov[2] + cfp) : a * s.ucov[2] - tb * s.bcov[2];
+        acc[4] = (DIR == 3) ? a * s.ucov[3] + (-tb * s.bcov[3] + cfp) : a * s.ucov[3] - tb * s.bcov[3];
+        acc[5] = kappa * mass;
+        acc[6] = s.bcon[i1] * fu + (-fb * s.ucon[i1] + cU * pr[B1 + i1 - 1]);
+        acc[7] = s.bcon[i2] * fu + (-fb * s.ucon[i2] + cU * pr[B1 + i2 - 1]);
+    } else {
+        acc[0] = r[0] + mass;
+        acc[1] = a * s.ucov[0] + (-tb * s.bcov[0] + (cU * ptot + (mass + r[1])));
+        acc[2] = a * s.ucov[1] + (-tb * s.bcov[1] + ((DIR == 1) ? cfp + r[2] : r[2]));
+        acc[3] = a * s.ucov[2] + (-tb * s.bcov[2] + ((DIR == 2) ? cfp + r[3] : r[3]));
+        acc[4] = a * s.ucov[3] + (-tb * s.bcov[3] + ((DIR == 3) ? cfp + r[4] : r[4]));
+        acc[5] = kappa * mass + r[5];
+        acc[6] = s.bcon[i1] * fu + (-fb * s.ucon[i1] + (cU * pr[B1 + i1 - 1] + r[6]));
+        acc[7] = s.bcon[i2] * fu + (-fb * s.ucon[i2] + (cU * pr[B1 + i2 - 1] + r[7]));
+    }
 }
 
 // HLLE (or LLF) flux through every dir-face: faces 0..n_dir, -1..n_e across.
@@ -555,7 +570,7 @@ __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const T*
 }
 
 template <int DIR, typename T>
-__global__ void __launch_bounds__(256) k_flux(BlockView v, PhysArgs ph, const T* __restrict__ QL,
+__global__ void __launch_bounds__(256, 2) k_flux(BlockView v, PhysArgs ph, const T* __restrict__ QL,
                                              const T* __restrict__ QR, const double* __restrict__ Bf,
                                              double* __restrict__ F) {
     b_flux<DIR, T>(v, ph, QL, QR, Bf, F, (long)blockIdx.x * blockDim.x + threadIdx.x);
@@ -1206,7 +1221,7 @@ __global__ void kb_to_f32(const DevBlock* tab, const int* list, int sigma) {
 }
 
 template <int DIR, typename T>
-__global__ void __launch_bounds__(256) kb_flux(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
+__global__ void __launch_bounds__(256, 2) kb_flux(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
     const DevBlock& D = tab[list[blockIdx.y]];
     double* F = (DIR == 1) ? D.F1 : ((DIR == 2) ? D.F2 : D.F3);
     b_flux<DIR, T>(D.v, ph, reinterpret_cast<const T*>(D.QL), reinterpret_cast<const T*>(D.QR), sigma ? D.Bh : D.B, F,

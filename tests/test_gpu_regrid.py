@@ -99,8 +99,11 @@ def test_regrid_parity_flat_box(src, dst):
 
 @pytest.mark.parametrize("src,dst", [
     (dict(), dict(split=((1, 0, 1),))),                                     # 6-way split of a coarse block
-    (dict(split=((0, 1, 0),)), dict()),                                     # the 6 children merged back
-    (dict(refine=((0, 0, 0),)), dict(refine=((0, 0, 0),), split=((1, 0, 0),)))])  # split next to finer blocks
+    (dict(split=((0, 1, 0),)), dict(split=())),                             # the 6 children merged back
+    (dict(refine=((0, 0, 0),), split=()), dict(refine=((0, 0, 0),), split=((1, 0, 0),))),  # next to finer blocks
+    (dict(split=((0, 0, 0),)), dict(refine=((0, 0, 0),), split=())),      # axis children refined in x3 only
+    (dict(refine=((0, 0, 0),), split=()), dict(split=((0, 0, 0),))),      # octants merged in x3 only
+    (dict(split=((0, 1, 0),)), dict(split=((0, 0, 0),)))])                 # a split next to a merge
 def test_regrid_parity_flat_box_six_way(src, dst):
     """6-way splits (workloads.split6: two children keep the parent's x3 cells, 2 x 2 x 1 fine cells per
     coarse cell; four halve all widths) and their merge, against the oracle's regridding."""

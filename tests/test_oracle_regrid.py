@@ -277,3 +277,25 @@ def test_six_way_children_prolong_linear_fields_exactly():
         for d in range(3):
             fs = (slice(NG + 2, NG + b["n3"] - 2), slice(NG + 2, NG + b["n2"] - 2), slice(NG + 2, NG + b["n1"] - 2))
             assert np.abs(bf[d][fs] - bw[d][fs]).max() < 1e-14, (i, d)
+
+
+@pytest.mark.parametrize("src,dst", [(dict(split=((0, 0, 0),)), dict(refine=((0, 0, 0),), split=())),
+                                     (dict(refine=((0, 0, 0),), split=()), dict(split=((0, 0, 0),))),
+                                     (dict(split=((0, 1, 0),)), dict(split=((0, 0, 0),))),
+                                     (dict(split=((0, 0, 0), (1, 1, 0))), dict(split=((1, 0, 0), (0, 1, 1))))])
+def test_x3_only_refinement_and_merge_stay_divergence_free(src, dst):
+    """A region whose cells change along x3 alone (the axis children of a 6-way split becoming octants,
+    and back), and splits next to merges: the refinement takes Balsara's polynomial on 1 x 1 x 2 fine
+    cells, the merge the area means; every cell stays divergence-free. Two versions failed these:
+    piecewise-constant copies of the x1 and x2 faces along x3 (the x3 faces change across the cell),
+    and octants whose faces on a plane shared with an axis child were copied piecewise-constant along
+    x3 while the axis child's side of the plane took its polynomial's linear profile."""
+    old = W.flat_box_tree6(base=(2, 2, 2), n=6, **src)
+    new = W.flat_box_tree6(base=(2, 2, 2), n=6, **dst)
+    a = grid(old, W.flat_box_state(old, bamp=0.2))
+    a.period()
+    r = a.regrid(ora_blocks(new))
+    bmax = max(np.abs(r.get(i)[1]).max() for i in range(len(new)))
+    for i, b in enumerate(new):
+        _, bf = r.get(i)
+        assert np.abs(div_b(b, bf)).max() <= 1e-12 * bmax / b["dx1"], i
