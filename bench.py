@@ -49,8 +49,8 @@ FLOPS_PER_ZONE_CYCLE = 4605.0    # one cell, one full step
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes per launch of the dominant kernel group, from one ncu capture
 # of this build's x1-face flux kernel (the x2 and x3 kernels move the same
-# field sizes).
-NCU_TRAFFIC_PER_LAUNCH = 429.3e6
+# field sizes): 312.5 MB read + 115.4 MB written.
+NCU_TRAFFIC_PER_LAUNCH = 427.9e6
 
 
 def env_rank():

@@ -280,11 +280,21 @@ __device__ __forceinline__ void c2p_prepare(const double U[NCONS], const double 
     w.method = method;
     w.mixed = mixed;
     w.p0 = (gam - 1.0) * pr[UU];
-    const double q1 = pr[U1], q2 = pr[U2], q3 = pr[U3];
-    const double qsq = m.g11 * q1 * q1 + m.g22 * q2 * q2 + m.g33 * q3 * q3 + 2.0 * m.g13 * q1 * q3;
-    const double gsq = 1.0 + qsq;
-    w.W0 = (pr[RHO] + gam * pr[UU]) * gsq;
-    w.vsq0 = fmin(qsq / gsq, C2P_VSQMAX);
+    if (mixed) {
+        // the start only seeds the FP32 iterations (and, where they fail, the FP64 ones): in FP32
+        const float q1 = (float)pr[U1], q2 = (float)pr[U2], q3 = (float)pr[U3];
+        const float qsq = (float)m.g11 * q1 * q1 + (float)m.g22 * q2 * q2 + (float)m.g33 * q3 * q3 +
+                          2.0f * (float)m.g13 * q1 * q3;
+        const float gsq = 1.0f + qsq;
+        w.W0 = (double)(((float)pr[RHO] + (float)gam * (float)pr[UU]) * gsq);
+        w.vsq0 = (double)fminf(qsq / gsq, (float)C2P_VSQMAX);
+    } else {
+        const double q1 = pr[U1], q2 = pr[U2], q3 = pr[U3];
+        const double qsq = m.g11 * q1 * q1 + m.g22 * q2 * q2 + m.g33 * q3 * q3 + 2.0 * m.g13 * q1 * q3;
+        const double gsq = 1.0 + qsq;
+        w.W0 = (pr[RHO] + gam * pr[UU]) * gsq;
+        w.vsq0 = fmin(qsq * (1.0 / gsq), C2P_VSQMAX);
+    }
     w.W = w.W0;
     w.vsq = 0.0;
     w.rho = w.u = 0.0;
