@@ -284,6 +284,7 @@ int alloc_block(hamr_grid* g, int b) {
     v.gc32 = g32c;
     v.gf1_32 = g32f1;
     v.gf2_32 = g32f2;
+    v.P32 = s.P32;
     CUDA_TRY(cudaMemset(base, 0, bytes));
     GeomArgs A;
     A.metric = g->desc.metric;

@@ -103,12 +103,15 @@ __device__ __forceinline__ bool newton_wv(const C2PScalars& S, double gfac, doub
 // FP64 iteration runs from the original start alone. `it` counts the
 // iterations of both precisions.
 __device__ __forceinline__ bool newton_wv_mixed(const C2PScalars& S, double gfac, double& W, double& vsq, int& it) {
-    const float k = 1.0f / (float)W;
-    const double kd = (double)k;
-    const float D = (float)(S.D * kd), Bsq = (float)(S.Bsq * kd), Qdotn = (float)(S.Qdotn * kd);
-    const float Qtsq = (float)(S.Qtsq * (kd * kd)), QB2 = (float)(S.QB2 * (kd * kd * kd));
+    // the scalars rounded to FP32 first and scaled there (their magnitudes stay far inside FP32's
+    // range for admissible states; an overflow makes the FP32 stage fail, and the FP64 iteration runs)
+    const float Wf = (float)W;
+    const float k = 1.0f / Wf;
+    const float k2 = k * k;
+    const float D = (float)S.D * k, Bsq = (float)S.Bsq * k, Qdotn = (float)S.Qdotn * k;
+    const float Qtsq = (float)S.Qtsq * k2, QB2 = (float)S.QB2 * (k2 * k);
     const float gf = (float)gfac, vmax = (float)C2P_VSQMAX;
-    float w = (float)(W * kd), v = (float)vsq;
+    float w = Wf * k, v = (float)vsq;
     bool ok32 = false;
     int it32 = 0;
     for (it32 = 1; it32 <= 8; it32++) {
@@ -144,7 +147,7 @@ __device__ __forceinline__ bool newton_wv_mixed(const C2PScalars& S, double gfac
         return ok;
     }
     // FP64 iterations from the FP32 root (w / k, taken as w W: the start may be off by the rounding of k)
-    double Wd = (double)w * W, vd = (double)v;
+    double Wd = (double)(w * Wf), vd = (double)v;
     const double D64 = S.D, Bsq64 = S.Bsq, QB264 = S.QB2, Qdotn64 = S.Qdotn, Qtsq64 = S.Qtsq;
     bool ok = false;
     int it64;

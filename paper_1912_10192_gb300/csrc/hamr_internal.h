@@ -39,6 +39,9 @@ struct BlockView {
     const float* gc32;
     const float* gf1_32;
     const float* gf2_32;
+    // FP32 copy of the stage's primitives (mixed precision, written at the start of each stage),
+    // else null
+    const float* P32;
 };
 
 struct PhysArgs {

@@ -1011,9 +1011,15 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
             fluid_state(pf, m, s);
             source_q_dg(v.gc, v.n2d, g, m, pf, s, gam, Q);
         } else {
+            // the FP32 source of the stage state: its FP32 copy, the values (float)pf exactly
             Metric<float> mf;
             load_metric(v.gc32, v.n2d, g, mf);
-            source_q(v.gc32, v.n2d, g, mf, pf, gam, Q);
+            float p32[NPRIM];
+#pragma unroll
+            for (int q = 0; q < NPRIM; q++) p32[q] = v.P32[q * nc + c];
+            Fluid<float> s32;
+            fluid_state(p32, mf, s32);
+            source_q_state(v.gc32, v.n2d, g, mf, p32, s32, (float)gam, Q);
         }
         const double dts = dscal[0] * fac;
         const long sj = v.n1p, sk = (long)v.n1p * v.n2p;
