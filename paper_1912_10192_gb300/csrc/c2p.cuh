@@ -274,16 +274,21 @@ struct C2PWork {
     int its;          // Newton iterations of every energy attempt
 };
 
+// start32 (mixed form, optional): the start (W, v^2) already formed in FP32 from the guess primitives
 __device__ __forceinline__ void c2p_prepare(const double U[NCONS], const double Bc[3], const Metric<double>& m,
                                             double gam, const double pr[NPRIM], C2PWork& w,
-                                            int method = HAMR_INV_NEWTON, int mixed = 0) {
+                                            int method = HAMR_INV_NEWTON, int mixed = 0,
+                                            const float* start32 = nullptr) {
     c2p_scalars(U, Bc, m, w.S);
     w.igam = 1.0 / gam;
     w.gfac = (gam - 1.0) * w.igam;
     w.method = method;
     w.mixed = mixed;
     w.p0 = (gam - 1.0) * pr[UU];
-    if (mixed) {
+    if (mixed && start32) {
+        w.W0 = (double)start32[0];
+        w.vsq0 = (double)fminf(start32[1], (float)C2P_VSQMAX);
+    } else if (mixed) {
         // the start only seeds the FP32 iterations (and, where they fail, the FP64 ones): in FP32
         const float q1 = (float)pr[U1], q2 = (float)pr[U2], q3 = (float)pr[U3];
         const float qsq = (float)m.g11 * q1 * q1 + (float)m.g22 * q2 * q2 + (float)m.g33 * q3 * q3 +

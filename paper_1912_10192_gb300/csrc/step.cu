@@ -955,6 +955,8 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
     long c = 0, g = 0;
     int i = 0, j = 0;
     MlpCta C;
+    float start32[2] = {0.0f, 0.0f};  // mixed form: the inversion's start in FP32 (see the source)
+    bool have32 = false;
     const bool rescue = MLP && ph.mlp_mode == HAMR_MLP_RESCUE;
     extern __shared__ __align__(16) uint8_t mlp_smem[];
     if (MLP && !rescue) mlp_begin(C, mlp_smem, ph.mlp_img);  // the weight image streams in while U is formed
@@ -1020,6 +1022,12 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
             Fluid<float> s32;
             fluid_state(p32, mf, s32);
             source_q_state(v.gc32, v.n2d, g, mf, p32, s32, (float)gam, Q);
+            // the inversion's start from the same state (it only seeds the FP32 iterations)
+            const float qsq = p32[U1] * s32.ucov[1] + p32[U2] * s32.ucov[2] + p32[U3] * s32.ucov[3];
+            const float gsq = 1.0f + qsq;
+            start32[0] = (p32[RHO] + (float)gam * p32[UU]) * gsq;
+            start32[1] = qsq / gsq;
+            have32 = true;
         }
         const double dts = dscal[0] * fac;
         const long sj = v.n1p, sk = (long)v.n1p * v.n2p;
@@ -1046,7 +1054,8 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
     // inversion: energy attempts from the start(s), then the entropy backup
     C2PWork w;
     if (active)
-        c2p_prepare(U, Bc, m, gam, pr, w, ph.inversion, (std::is_same<TS, float>::value && !ph.fp64_inv) ? 1 : 0);
+        c2p_prepare(U, Bc, m, gam, pr, w, ph.inversion, (std::is_same<TS, float>::value && !ph.fp64_inv) ? 1 : 0,
+                    have32 ? start32 : nullptr);
     if (MLP) {
         // first: the network's start, then the plain one; rescue: the plain start, then the
         // network's where it failed (the CTA runs the network only if one of its cells failed)
