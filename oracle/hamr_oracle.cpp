@@ -24,6 +24,7 @@
 #include "ora_real.h"
 #include "hamr_oracle.h"
 
+#include <cmath>
 #include <cstdlib>
 #include <algorithm>
 #include <cstring>
@@ -814,6 +815,8 @@ struct ora_grid {
     std::vector<double> rc;         /* r at centres */
     std::vector<int> status;        /* per cell: OR of the inversion/floor bits of the last step */
     long long stats[4];
+    int smr_l2, smr_l3;             /* internal SMR in a block tree: log2 of the coarsest polar block's
+                                       x2 and x3 cell widths over this block's (0 on a single block) */
 };
 
 namespace {
@@ -1216,52 +1219,92 @@ void stage_ct(ora_grid* g, const std::vector<double>& E, const double* Bfb, doub
 }
 
 /* cell update, inversion, floors */
-/* Internal SMR (Sec. 3.3.2: phi-averaging within polar blocks). Reading:
- * with n_max levels, a row of cells at distance jp (in cells) from a polar
- * face is grouped into cells 2^n wide in phi, n the largest level in
- * 1..n_max with jp < 2^(n_max - n) (rows farther out: no grouping). A
- * group acts as one cell: after the face update its x1-faces and its x2-face
- * on the far side from the pole take their group mean (the near side belongs
- * to the row closer to the pole, whose groups are at least as wide) and the
- * x3-faces inside it are interpolated linearly between its two outer ones,
- * which keeps every cell divergence-free; after the cell update the group's
- * conserved variables are averaged and inverted once (start: the mean of
- * the cells' primitives, field: the mean of their centre fields), every cell
- * of the group takes the result (its own centre field kept), and the CFL rate
- * uses the group's width in x3. Returns the group width of row j (1: none). */
-int smr_width(const ora_desc& d, int j) {
+/* Internal SMR (Sec. 3.3.2: phi-averaging within polar blocks; the paper
+ * averages "the fluxes and conserved quantities"). Reading: with n_max
+ * levels, a row of cells at distance jp (in cells) from a polar face is
+ * grouped into cells 2^n wide in phi, n the largest level in 1..n_max with
+ * jp < 2^(n_max - n) (rows farther out: no grouping). A group acts as one
+ * cell. Its field changes as a wide cell's: the EMFs (the fluxes of the
+ * induction equation) are averaged before the face update (smr_emf), so
+ * the change of every x1- and x2-face of a group is its group mean and the
+ * change of its inner x3-faces is linear between its outer ones, and div B
+ * stays at round-off under CT. Its fluid state: after the cell update the
+ * group's conserved variables are averaged and inverted once (start: the
+ * mean of the cells' primitives, field: the mean of their centre fields),
+ * and every cell of the group takes the result (its own centre field
+ * kept). The CFL rate uses the group's width in x3. Returns the group width
+ * of row j (1: none).
+ *
+ * In a block tree the rows and widths are those of the coarsest polar
+ * blocks (reading: the paper counts cells from the pole without saying at
+ * which resolution). A polar block whose x2 cells are 2^l2 times finer and x3
+ * cells 2^l3 times finer than theirs groups its row j as their row
+ * j / 2^l2, with 2^l3 times as many of its own cells, so the groups of blocks
+ * that meet at a face cover the same phi ranges and the EMFs that blocks
+ * exchange (edge synchronisation, refluxing) are averaged alike on both
+ * sides. */
+int smr_width(const ora_grid* g, int j) {
+    const ora_desc& d = g->d;
     if (d.smr <= 0) return 1;
     int jp = 1 << 30;
     if (d.bc[2] == ORA_BC_POLAR) jp = j;
     if (d.bc[3] == ORA_BC_POLAR) jp = std::min(jp, d.n2 - 1 - j);
+    const int jb = jp >> g->smr_l2;
     for (int n = d.smr; n >= 1; n--)
-        if (jp < (1 << (d.smr - n))) return 1 << n;
+        if (jb < (1 << (d.smr - n))) return (1 << n) << g->smr_l3;
     return 1;
 }
 
-void smr_faces(ora_grid* g, double* Bf) {
+/* sum of w = 2^n values as a balanced binary tree: w equal values sum to
+ * exactly w times the value, so a group mean of equal values is that value */
+double pair_sum(const double* a, int w) { return (w == 1) ? a[0] : pair_sum(a, w / 2) + pair_sum(a + w / 2, w / 2); }
+
+/* group width of the EMF line at x2-edge je: that of the adjacent row
+ * closer to the pole (the wider one) */
+int smr_line_width(const ora_grid* g, int je) {
+    int w = 1;
+    if (je >= 1) w = std::max(w, smr_width(g, je - 1));
+    if (je < g->d.n2) w = std::max(w, smr_width(g, je));
+    return w;
+}
+
+/* the EMFs of grouped rows as a wide cell's (smr_width): along each x2-line
+ * of edges with group width W, the x3-edge EMFs E3 take their group mean
+ * and the x1-edge EMFs E1 inside a group are linear between the group's two
+ * outer ones; inside each grouped row the x2-edge EMFs E2 are linear
+ * between the group's outer ones. Then the CT changes of a group's x1- and
+ * x2-faces are uniform and those of its inner x3-faces linear. */
+void smr_emf(ora_grid* g, std::vector<double>& E) {
     const ora_desc& d = g->d;
     const long nc = g->ncell;
-    for (int j = 0; j < d.n2; j++) {
-        const int w = smr_width(d, j);
-        if (w == 1) continue;
-        /* the x2-face on the side away from the pole */
-        const bool lower_pole = (d.bc[2] == ORA_BC_POLAR) && (j < d.n2 / 2);
-        const int jf = lower_pole ? j + 1 : j;
-        for (int k0 = 0; k0 < d.n3; k0 += w) {
+    double* E1 = E.data();
+    double* E2 = E.data() + nc;
+    double* E3 = E.data() + 2 * nc;
+    std::vector<double> a;
+    for (int je = 0; je <= d.n2; je++) {
+        const int W = smr_line_width(g, je);
+        if (W == 1) continue;
+        a.resize(W);
+        for (int k0 = 0; k0 < d.n3; k0 += W) {
             for (int i = 0; i <= d.n1; i++) {
-                double s1 = 0.0;
-                for (int m = 0; m < w; m++) s1 += Bf[0 * nc + cidx(g, i, j, k0 + m)];
-                for (int m = 0; m < w; m++) Bf[0 * nc + cidx(g, i, j, k0 + m)] = s1 / w;
+                for (int m = 0; m < W; m++) a[m] = E3[cidx(g, i, je, k0 + m)];
+                const double s3 = pair_sum(a.data(), W);
+                for (int m = 0; m < W; m++) E3[cidx(g, i, je, k0 + m)] = s3 / W;
             }
             for (int i = 0; i < d.n1; i++) {
-                double s2 = 0.0;
-                for (int m = 0; m < w; m++) s2 += Bf[1 * nc + cidx(g, i, jf, k0 + m)];
-                for (int m = 0; m < w; m++) Bf[1 * nc + cidx(g, i, jf, k0 + m)] = s2 / w;
-                const double b0 = Bf[2 * nc + cidx(g, i, j, k0)], bw = Bf[2 * nc + cidx(g, i, j, k0 + w)];
-                for (int m = 1; m < w; m++) Bf[2 * nc + cidx(g, i, j, k0 + m)] = b0 + (bw - b0) * m / w;
+                const double e0 = E1[cidx(g, i, je, k0)], ew = E1[cidx(g, i, je, k0 + W)];
+                for (int m = 1; m < W; m++) E1[cidx(g, i, je, k0 + m)] = e0 + (ew - e0) * m / W;
             }
         }
+    }
+    for (int j = 0; j < d.n2; j++) {
+        const int w = smr_width(g, j);
+        if (w == 1) continue;
+        for (int k0 = 0; k0 < d.n3; k0 += w)
+            for (int i = 0; i <= d.n1; i++) {
+                const double e0 = E2[cidx(g, i, j, k0)], ew = E2[cidx(g, i, j, k0 + w)];
+                for (int m = 1; m < w; m++) E2[cidx(g, i, j, k0 + m)] = e0 + (ew - e0) * m / w;
+            }
     }
 }
 
@@ -1299,7 +1342,7 @@ void stage_update(ora_grid* g, const Fluxes& F, const double* Pb, const double* 
                                (real(F[3][(size_t)m * nc + c3]) - real(F[3][(size_t)m * nc + c])) / dx[3];
                     U[m] = u9[m] * G.gdet + dts * (Q[m] - div);
                 }
-                if (smr_width(d, j) > 1) { /* inverted with its group below */
+                if (smr_width(g, j) > 1) { /* inverted with its group below */
                     for (int m = 0; m < NCONS; m++) Usmr[(size_t)m * nc + c] = tod(U[m]);
                     continue;
                 }
@@ -1325,7 +1368,7 @@ void stage_update(ora_grid* g, const Fluxes& F, const double* Pb, const double* 
             }
     /* internal SMR groups: one inversion of the group's mean state */
     for (int j = 0; j < n2; j++) {
-        const int w = smr_width(d, j);
+        const int w = smr_width(g, j);
         if (w == 1) continue;
         for (int k0 = 0; k0 < n3; k0 += w)
             for (int i = 0; i < n1; i++) {
@@ -1379,8 +1422,8 @@ void stage(ora_grid* g, const double* Pf, const double* Bff, const double* Pb, c
     std::vector<double> E;
     stage_fluxes(g, Pf, Bff, F);
     stage_emf(g, F, Pf, E);
+    if (g->d.smr > 0) smr_emf(g, E);
     stage_ct(g, E, Bfb, dts, Bfout);
-    if (g->d.smr > 0) smr_faces(g, Bfout);
     stage_update(g, F, Pb, Pf, Bfout, dts, Pout);
 }
 
@@ -1405,7 +1448,7 @@ double grid_dt(ora_grid* g) {
                     real vp, vm;
                     vchar(pr, s, G, dir, d.gam, &vp, &vm);
                     real vf = fmax(fabs(vp), fabs(vm));
-                    inv += vf / (dir == 3 ? dx[3] * smr_width(d, j) : dx[dir]);
+                    inv += vf / (dir == 3 ? dx[3] * smr_width(g, j) : dx[dir]);
                 }
                 if (inv > invmax) invmax = inv;
             }
@@ -1700,6 +1743,7 @@ ora_grid* ora_grid_new(const ora_desc* d) {
     g->bface.assign((size_t)3 * g->ncell, 0.0);
     g->status.assign(g->ncell, 0);
     for (int m = 0; m < 4; m++) g->stats[m] = 0;
+    g->smr_l2 = g->smr_l3 = 0;
     build_geometry(g);
     return g;
 }
@@ -2408,6 +2452,10 @@ void amr_fluxes_group(ora_amr* m, const std::vector<int>& grp, int sigma) {
         AmrBlk& D = m->b[r.dst];
         D.E[(size_t)(r.d - 1) * D.g->ncell + r.di] = vals[q];
     }
+    /* internal SMR: each block's EMFs as its groups' after the exchange (groups that meet at a shared
+       edge cover the same phi range, so both sides average the same values) */
+    for (int b : grp)
+        if (m->b[b].g->d.smr > 0) smr_emf(m->b[b].g, m->b[b].E);
 }
 
 /* one midpoint step of every block of a same-level group (Sec. 2.1) */
@@ -2469,10 +2517,30 @@ void amr_step_group(ora_amr* m, const std::vector<int>& grp, double dtf) {
     }
 }
 
+/* internal SMR at a reflux: a group is inverted as one cell, so every cell of
+ * a group with a marked cell is marked */
+void smr_mark(const ora_grid* g, std::vector<char>& mark) {
+    const ora_desc& d = g->d;
+    for (int j = 0; j < d.n2; j++) {
+        const int w = smr_width(g, j);
+        if (w == 1) continue;
+        for (int k0 = 0; k0 < d.n3; k0 += w)
+            for (int i = 0; i < d.n1; i++) {
+                bool any = false;
+                for (int q = 0; q < w; q++) any = any || mark[cidx(g, i, j, k0 + q)];
+                if (any)
+                    for (int q = 0; q < w; q++) mark[cidx(g, i, j, k0 + q)] = 1;
+            }
+    }
+}
+
 /* end of a coarse step (Sec. 3.2 refluxing, Sec. 3.4 flux correction): the
  * coarse block's face fluxes and edge EMFs are replaced by the time
  * integrals of the finer level's; the cells next to changed faces are
- * inverted again from U(P) + the flux correction. */
+ * inverted again from U(P) + the flux correction. With internal SMR the
+ * replaced EMFs are the finer side's averaged ones (the same phi ranges,
+ * so the correction keeps the group structure of the field's change) and
+ * grouped cells are inverted as groups (smr_mark). */
 void amr_reflux(ora_amr* m, int c) {
     AmrBlk& C = m->b[c];
     ora_grid* g = C.g;
@@ -2517,6 +2585,7 @@ void amr_reflux(ora_amr* m, int c) {
                 }
         }
     }
+    if (d.smr > 0) smr_mark(g, mark);
     /* U of the marked cells with the field before the correction */
     std::vector<double> U0((size_t)NCONS * nc, 0.0);
     for (int k = 0; k < d.n3; k++)
@@ -2538,7 +2607,7 @@ void amr_reflux(ora_amr* m, int c) {
         for (int j = 0; j < d.n2; j++)
             for (int i = 0; i < d.n1; i++) {
                 long cc = cidx(g, i, j, k);
-                if (!mark[cc]) continue;
+                if (!mark[cc] || smr_width(g, j) > 1) continue;
                 const Geom& G = g->gc[gidx(g, i, j)];
                 real U[NCONS];
                 for (int q = 0; q < NCONS; q++) U[q] = U0[(size_t)q * nc + cc] + dU[(size_t)q * nc + cc];
@@ -2558,6 +2627,52 @@ void amr_reflux(ora_amr* m, int c) {
                 if (d.floors && apply_floors(d, pr, G, g->rc[gidx(g, i, j)])) m->stats[3]++;
                 for (int v = 0; v < NPR; v++) g->prim[v * nc + cc] = tod(pr[v]);
             }
+    /* marked internal-SMR groups: the mean of the cells' corrected states inverted once (start: the
+       mean of their primitives, field: the mean of their new centre fields), as in stage_update */
+    for (int j = 0; j < d.n2 && d.smr > 0; j++) {
+        const int w = smr_width(g, j);
+        if (w == 1) continue;
+        for (int k0 = 0; k0 < d.n3; k0 += w)
+            for (int i = 0; i < d.n1; i++) {
+                if (!mark[cidx(g, i, j, k0)]) continue;
+                const long q2 = gidx(g, i, j);
+                const Geom& G = g->gc[q2];
+                real U[NCONS], Bc[3] = {0.0, 0.0, 0.0}, pr[NPR];
+                for (int q = 0; q < NCONS; q++) U[q] = 0.0;
+                for (int v = 0; v < NPR; v++) pr[v] = 0.0;
+                for (int a = 0; a < w; a++) {
+                    const long cc = cidx(g, i, j, k0 + a);
+                    for (int q = 0; q < NCONS; q++)
+                        U[q] += real(U0[(size_t)q * nc + cc] + dU[(size_t)q * nc + cc]);
+                    real b[3];
+                    centre_b(g, g->bface.data(), i, j, k0 + a, b);
+                    for (int e = 0; e < 3; e++) Bc[e] += b[e];
+                    for (int v = 0; v < 5; v++) pr[v] += g->prim[v * nc + cc];
+                }
+                for (int q = 0; q < NCONS; q++) U[q] /= w;
+                for (int e = 0; e < 3; e++) Bc[e] /= w;
+                for (int v = 0; v < 5; v++) pr[v] /= w;
+                real p0[5];
+                for (int v = 0; v < 5; v++) p0[v] = pr[v];
+                pr[B1] = Bc[0];
+                pr[B2] = Bc[1];
+                pr[B3] = Bc[2];
+                int its = 0;
+                int st = con2prim(d, U, Bc, G, pr, &its);
+                if (st == C2P_FAIL)
+                    for (int v = 0; v < 5; v++) pr[v] = p0[v];
+                const bool fl = d.floors && apply_floors(d, pr, G, g->rc[q2]);
+                for (int a = 0; a < w; a++) {
+                    const long cc = cidx(g, i, j, k0 + a);
+                    m->stats[st == C2P_OK ? 0 : (st == C2P_ENTROPY ? 1 : 2)]++;
+                    if (fl) m->stats[3]++;
+                    real b[3];
+                    centre_b(g, g->bface.data(), i, j, k0 + a, b);
+                    for (int v = 0; v < 5; v++) g->prim[v * nc + cc] = tod(pr[v]);
+                    for (int e = 0; e < 3; e++) g->prim[(B1 + e) * nc + cc] = tod(b[e]);
+                }
+            }
+    }
 }
 
 /* ------------------------------------------------------------------ */
@@ -2942,6 +3057,20 @@ ora_amr* ora_amr_new(const ora_desc* phys, int nb, const ora_block* blocks) {
         m->b.push_back(B);
     }
     const int nbk = (int)m->b.size();
+    /* internal SMR: each polar block's widths against the coarsest polar block's (smr_width) */
+    if (phys->smr > 0) {
+        double h2b = 0.0, h3b = 0.0;
+        for (const AmrBlk& B : m->b)
+            if (B.g->d.bc[2] == ORA_BC_POLAR || B.g->d.bc[3] == ORA_BC_POLAR) {
+                h2b = std::max(h2b, B.h[2]);
+                h3b = std::max(h3b, B.h[3]);
+            }
+        for (AmrBlk& B : m->b)
+            if (B.g->d.bc[2] == ORA_BC_POLAR || B.g->d.bc[3] == ORA_BC_POLAR) {
+                B.g->smr_l2 = (int)std::lround(std::log2(h2b / B.h[2]));
+                B.g->smr_l3 = (int)std::lround(std::log2(h3b / B.h[3]));
+            }
+    }
     m->touch.assign(nbk, {});
     for (int a = 0; a < nbk; a++)
         for (int c = 0; c < nbk; c++) {
