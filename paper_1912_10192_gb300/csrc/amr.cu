@@ -1047,7 +1047,11 @@ struct AmrImpl {
     FaceRecDev fr{};
     EdgeRecDev er{};
     int n_fr = 0, n_er = 0;
-    std::vector<int> rc_beg, rc_end;  // refluxed cells per level
+    std::vector<int> rc_beg, rc_end;  // refluxed cells per level: single cells first, then whole SMR groups
+    std::vector<int> rc_sgl;          // end of each level's single cells
+    std::vector<int> rg_beg, rg_end;  // refluxed SMR groups per level
+    int* rg_first = nullptr;          // first list position of each group, relative to its level's rc_beg
+    int* rg_w = nullptr;              // its cells
     int* rc_blk = nullptr;
     long* rc_idx = nullptr;
     int* rc_nrec = nullptr;
@@ -1056,6 +1060,9 @@ struct AmrImpl {
     int n_rc = 0;
     std::vector<std::vector<int>> lev_edgefix;  // blocks of each level with edge corrections
     std::vector<int*> dlev_edgefix;
+    std::vector<std::vector<int>> lev_smr;  // blocks of each level with internal-SMR rows
+    std::vector<int*> dlev_smr;
+    std::vector<long> lmw_smr_emf, lmw_smr_cell;
     double* dtf = nullptr;
     // stored ghost locations (use_maps false: the direct kernels locate on every launch)
     GhostLoc *gloc_cell = nullptr, *gloc_face = nullptr;
@@ -1207,6 +1214,10 @@ int amr_create(AmrImpl** out, const hamr_grid_desc& d, const std::vector<BlockVi
         }
         D.lat = o.lat;
         M->Lmax = std::max(M->Lmax, o.lat);
+        if (ph.smr > 0 && smr_polar(o) && !smr_factors(d, o, &D.v.smr_l2, &D.v.smr_l3)) {
+            delete M;
+            return set_error(HAMR_EINVAL, "block %d: internal SMR needs cell widths a power of 2 finer", b);
+        }
         const BlockState& s = st[b];
         D.P = s.P;
         D.B = s.B;
@@ -1443,10 +1454,39 @@ int amr_create(AmrImpl** out, const hamr_grid_desc& d, const std::vector<BlockVi
                 }
             }
         }
-        std::vector<int> blk, nrec, recs;
+        // internal SMR: a group is inverted as one cell, so every cell of a group with a refluxed cell is
+        // refluxed
+        auto cell_of = [](const BlockView& v, long c, int* i, int* j, int* k) {
+            *i = (int)(c % v.n1p) - NG;
+            *j = (int)((c / v.n1p) % v.n2p) - NG;
+            *k = (int)(c / ((long)v.n1p * v.n2p)) - NG;
+        };
+        if (ph.smr > 0)
+            for (int b = 0; b < M->nb; b++) {
+                const BlockView& v = H.b[b].v;
+                const size_t n0 = per_block[b].size();
+                for (size_t q = 0; q < n0; q++) {
+                    int i, j, k;
+                    cell_of(v, per_block[b][q].idx, &i, &j, &k);
+                    const int w = smr_width(v, ph, j);
+                    for (int m = 0; w > 1 && m < w; m++) add_cell(b, i, j, k - k % w + m, -1);
+                }
+            }
+        std::vector<int> blk, nrec, recs, gfirst, gw;
         std::vector<long> idx;
+        auto push = [&](const RC& x) {
+            blk.push_back(x.blk);
+            idx.push_back(x.idx);
+            nrec.push_back((int)x.recs.size());
+            std::vector<int> rs = x.recs;
+            std::sort(rs.begin(), rs.end());
+            for (int m = 0; m < 3; m++) recs.push_back(m < (int)rs.size() ? rs[m] : 0);
+        };
         M->rc_beg.assign(M->Lmax + 1, 0);
         M->rc_end.assign(M->Lmax + 1, 0);
+        M->rc_sgl.assign(M->Lmax + 1, 0);
+        M->rg_beg.assign(M->Lmax + 1, 0);
+        M->rg_end.assign(M->Lmax + 1, 0);
         for (int L = 0; L <= M->Lmax; L++) {
             M->rc_beg[L] = (int)blk.size();
             for (int b = 0; b < M->nb; b++) {
@@ -1458,16 +1498,35 @@ int amr_create(AmrImpl** out, const hamr_grid_desc& d, const std::vector<BlockVi
                         delete M;
                         return set_error(HAMR_EINVAL, "a refluxed cell with more than 3 corrected faces");
                     }
-                    blk.push_back(x.blk);
-                    idx.push_back(x.idx);
-                    nrec.push_back((int)x.recs.size());
-                    std::vector<int> rs = x.recs;
-                    std::sort(rs.begin(), rs.end());
-                    for (int m = 0; m < 3; m++) recs.push_back(m < (int)rs.size() ? rs[m] : 0);
+                    int i, j, k;
+                    cell_of(H.b[b].v, x.idx, &i, &j, &k);
+                    if (smr_width(H.b[b].v, ph, j) == 1) push(x);
                 }
             }
+            M->rc_sgl[L] = (int)blk.size();
+            M->rg_beg[L] = (int)gfirst.size();
+            for (int b = 0; b < M->nb; b++) {
+                if (H.b[b].lat != L) continue;
+                const BlockView& bv = H.b[b].v;
+                for (const RC& x : per_block[b]) {  // sorted by cell: a group's first cell comes first
+                    int i, j, k;
+                    cell_of(bv, x.idx, &i, &j, &k);
+                    const int w = smr_width(bv, ph, j);
+                    if (w == 1 || k % w != 0) continue;
+                    gfirst.push_back((int)blk.size() - M->rc_beg[L]);
+                    gw.push_back(w);
+                    for (int m = 0; m < w; m++) {
+                        const long c = pidx(bv, i, j, k + m);
+                        for (const RC& y : per_block[b])
+                            if (y.idx == c) push(y);
+                    }
+                }
+            }
+            M->rg_end[L] = (int)gfirst.size();
             M->rc_end[L] = (int)blk.size();
         }
+        M->rg_first = M->dev(gfirst);
+        M->rg_w = M->dev(gw);
         M->n_rc = (int)blk.size();
         M->rc_blk = M->dev(blk);
         M->rc_idx = M->dev(idx);
@@ -1542,6 +1601,18 @@ int amr_create(AmrImpl** out, const hamr_grid_desc& d, const std::vector<BlockVi
     }
     for (int L = 0; L <= M->Lmax; L++) M->dlev.push_back(M->dev(M->lev[L]));
     M->dall = M->dev(all);
+    M->lev_smr.assign(M->Lmax + 1, {});
+    M->lmw_smr_emf.assign(M->Lmax + 1, 0);
+    M->lmw_smr_cell.assign(M->Lmax + 1, 0);
+    for (int b = 0; b < M->nb; b++) {
+        const long nf = smr_emf_threads(H.b[b].v, ph), ncl = smr_cell_threads(H.b[b].v, ph);
+        if (!smr_polar(d.blocks[b]) || nf == 0) continue;
+        const int L = H.b[b].lat;
+        M->lev_smr[L].push_back(b);
+        M->lmw_smr_emf[L] = std::max(M->lmw_smr_emf[L], nf);
+        M->lmw_smr_cell[L] = std::max(M->lmw_smr_cell[L], ncl);
+    }
+    for (int L = 0; L <= M->Lmax; L++) M->dlev_smr.push_back(M->dev(M->lev_smr[L]));
     M->lmw_pad.assign(M->Lmax + 1, 0);
     M->lmw_recon.assign(M->Lmax + 1, std::vector<long>(4, 0));
     M->lmw_edge.assign(M->Lmax + 1, 0);
@@ -1644,6 +1715,9 @@ int group_step(AmrImpl& M, int L, int s, cudaStream_t cs) {
             k_edge_scatter<<<nb_(ee - eb), BSA, 0, cs>>>(tab, M.es, eb, ee, M.es_tmp);
         }
         AM_TRY(cudaGetLastError());
+        // internal SMR: each block's EMFs as its groups' after the exchange
+        const int ns = (int)M.lev_smr[L].size();
+        if (ns) AM_TRY(launch_smr_emf_batch(tab, M.dlev_smr[L], ns, M.lmw_smr_emf[L], ph, cs));
         if (sigma == 1) {
             if (M.n_fr) {
                 k_face_own<<<nb_(M.n_fr), BSA, 0, cs>>>(tab, M.fr, M.n_fr, L);
@@ -1657,6 +1731,7 @@ int group_step(AmrImpl& M, int L, int s, cudaStream_t cs) {
         }
         AM_TRY(launch_ct_batch(tab, list, nl, M.lmw_edge[L], sigma, cs));
         AM_TRY(launch_update_batch(tab, list, nl, M.lmw_cell[L], ph, sigma, cs));
+        if (ns) AM_TRY(launch_smr_cells_batch(tab, M.dlev_smr[L], ns, M.lmw_smr_cell[L], ph, sigma, cs));
     }
     return HAMR_OK;
 }
@@ -1681,7 +1756,11 @@ int reflux_level(AmrImpl& M, int L, cudaStream_t cs) {
         }
         AM_TRY(launch_ct_batch(tab, M.dlev_edgefix[L], ne, mw, 2, cs));
     }
-    AM_TRY(launch_reflux_cells(tab, ce - cb, M.rc_blk + cb, M.rc_idx + cb, M.rc_U, M.ph, cs));
+    const int cg = M.rc_sgl[L];
+    AM_TRY(launch_reflux_cells(tab, cg - cb, M.rc_blk + cb, M.rc_idx + cb, M.rc_U, ce - cb, M.ph, cs));
+    const int gb = M.rg_beg[L], ge = M.rg_end[L];
+    AM_TRY(launch_reflux_groups(tab, ge - gb, M.rg_first + gb, M.rg_w + gb, M.rc_blk + cb, M.rc_idx + cb, M.rc_U,
+                                ce - cb, M.ph, cs));
     return HAMR_OK;
 }
 

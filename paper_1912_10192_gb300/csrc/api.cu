@@ -136,6 +136,29 @@ struct hamr_grid {
 };
 
 // The descriptor checks of hamr_grid_create, also run by hamr_block_step_noalloc.
+bool hamr::smr_polar(const hamr_block_desc& B) { return B.bc[2] == HAMR_BC_POLAR || B.bc[3] == HAMR_BC_POLAR; }
+
+// log2 of the coarsest polar block's x2 and x3 cell widths over B's; false unless both are powers of 2
+// (within 1e-9) between 2^0 and 2^6
+bool hamr::smr_factors(const hamr_grid_desc& d, const hamr_block_desc& B, int* l2, int* l3) {
+    double h2 = 0.0, h3 = 0.0;
+    for (int b = 0; b < d.nblocks; b++)
+        if (smr_polar(d.blocks[b])) {
+            h2 = std::max(h2, d.blocks[b].dx2);
+            h3 = std::max(h3, d.blocks[b].dx3);
+        }
+    const double r[2] = {h2 / B.dx2, h3 / B.dx3};
+    int l[2] = {0, 0};
+    for (int q = 0; q < 2; q++) {
+        if (!(r[q] >= 1.0 - 1e-9 && r[q] <= 64.0 * (1.0 + 1e-9))) return false;
+        l[q] = (int)std::lround(std::log2(r[q]));
+        if (std::fabs(r[q] - std::ldexp(1.0, l[q])) > 1e-9 * r[q]) return false;
+    }
+    *l2 = l[0];
+    *l3 = l[1];
+    return true;
+}
+
 int hamr::validate_desc(const hamr_grid_desc* d) {
     if (!d) return fail(HAMR_EINVAL, "descriptor is NULL");
     if (d->nblocks < 1 || !d->blocks) return fail(HAMR_EINVAL, "nblocks must be >= 1 with a block array");
@@ -156,12 +179,23 @@ int hamr::validate_desc(const hamr_grid_desc* d) {
         return fail(HAMR_EINVAL, "unknown floor_frame %d", d->floor_frame);
     if (d->smr < 0 || d->smr > 4) return fail(HAMR_EINVAL, "smr must be in 0..4, got %d", d->smr);
     if (d->smr > 0) {
-        if (d->nblocks != 1) return fail(HAMR_EINVAL, "internal SMR is for single-block grids");
-        const hamr_block_desc& B = d->blocks[0];
-        if (B.bc[2] != HAMR_BC_POLAR && B.bc[3] != HAMR_BC_POLAR)
-            return fail(HAMR_EINVAL, "internal SMR needs a polar x2 boundary");
-        if (B.n3 % (2 << d->smr) != 0) return fail(HAMR_EINVAL, "internal SMR needs n3 a multiple of %d", 2 << d->smr);
-        if (B.n2 < (1 << d->smr)) return fail(HAMR_EINVAL, "internal SMR needs n2 >= %d", 1 << d->smr);
+        // every polar block groups its rows like the coarsest polar blocks (smr_width): its cell widths
+        // a power of 2 finer, n3 a multiple of twice its widest group, its grouped rows within half of n2
+        bool polar = false;
+        for (int b = 0; b < d->nblocks; b++) polar = polar || smr_polar(d->blocks[b]);
+        if (!polar) return fail(HAMR_EINVAL, "internal SMR needs a polar x2 boundary");
+        for (int b = 0; b < d->nblocks; b++) {
+            const hamr_block_desc& B = d->blocks[b];
+            if (!smr_polar(B)) continue;
+            int l2 = 0, l3 = 0;
+            if (!smr_factors(*d, B, &l2, &l3))
+                return fail(HAMR_EINVAL, "block %d: internal SMR needs x2 and x3 cell widths a power of 2 finer than "
+                            "the coarsest polar block's", b);
+            const int rows = (1 << (d->smr - 1)) << l2, wmax = (1 << d->smr) << l3;
+            if (B.n3 % (2 * wmax) != 0)
+                return fail(HAMR_EINVAL, "block %d: internal SMR needs n3 a multiple of %d", b, 2 * wmax);
+            if (B.n2 < 2 * rows) return fail(HAMR_EINVAL, "block %d: internal SMR needs n2 >= %d", b, 2 * rows);
+        }
     }
     for (int b = 0; b < d->nblocks; b++) {
         const hamr_block_desc& B = d->blocks[b];
@@ -472,8 +506,8 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
         LAUNCH(g, K_FLUX, 1, cs, launch_flux(v, ph, dir, s.QL, s.QR, s.B, s.F[dir - 1], cs));
     }
     LAUNCH(g, K_EMF, ph.emf ? 2 : 1, cs, launch_emf(v, s.F, s.E, ph.mixed, s.P, ph.emf ? s.QL : nullptr, cs));
+    if (ph.smr) LAUNCH(g, K_EMF, 1, cs, launch_smr_emf(v, ph, s.E, cs));
     LAUNCH(g, K_CT, 1, cs, launch_ct(v, s.E, s.B, s.Bh, s.dscal, 0.5, cs));
-    if (ph.smr) LAUNCH(g, K_CT, 1, cs, launch_smr_faces(v, ph, s.Bh, cs));
     LAUNCH(g, K_UPDATE, 1, cs,
            launch_update(v, ph, 0, s.P, s.P, s.F, s.Bh, s.Un, s.Ph, s.status, s.dscal, 0.5, s.dmax, s.dcnt, cs));
     if (ph.smr)
@@ -488,8 +522,8 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
         LAUNCH(g, K_FLUX, 1, cs, launch_flux(v, ph, dir, s.QL, s.QR, s.Bh, s.F[dir - 1], cs));
     }
     LAUNCH(g, K_EMF, ph.emf ? 2 : 1, cs, launch_emf(v, s.F, s.E, ph.mixed, s.Ph, ph.emf ? s.QL : nullptr, cs));
+    if (ph.smr) LAUNCH(g, K_EMF, 1, cs, launch_smr_emf(v, ph, s.E, cs));
     LAUNCH(g, K_CT, 1, cs, launch_ct(v, s.E, s.B, s.B, s.dscal, 1.0, cs));
-    if (ph.smr) LAUNCH(g, K_CT, 1, cs, launch_smr_faces(v, ph, s.B, cs));
     LAUNCH(g, K_UPDATE, 1, cs,
            launch_update(v, ph, 1, s.P, s.Ph, s.F, s.B, s.Un, s.P, s.status, s.dscal, 1.0, s.dmax, s.dcnt, cs));
     if (ph.smr)

@@ -42,6 +42,9 @@ struct BlockView {
     // FP32 copy of the stage's primitives (mixed precision, written at the start of each stage),
     // else null
     const float* P32;
+    // internal SMR in a block tree: log2 of the coarsest polar block's x2 and x3 cell widths over
+    // this block's (0 on a single block; smr_width)
+    int smr_l2, smr_l3;
 };
 
 struct PhysArgs {
@@ -63,19 +66,28 @@ struct PhysArgs {
     int flatten;  // 1: PPM shock flattening (only set with HAMR_RECON_PPM)
     int inversion;  // HAMR_INV_*
     int floor_frame;  // HAMR_FLOOR_*
-    int smr;          // internal SMR levels next to polar faces (single-block grids; 0: off)
+    int smr;          // internal SMR levels next to polar faces (0: off)
     double* smr_u;    // scratch of the deferred conserved states (6 fields, stride nc) when smr > 0
 };
 
-// group width in x3 of row j under internal SMR (1: not grouped); see cell_floors' neighbour in step.cu
+// group width in x3 of row j under internal SMR (1: not grouped): row jp from a polar face of the
+// coarsest polar blocks is grouped 2^n wide, n the largest level with jp < 2^(smr - n); a polar block
+// with 2^smr_l2 times finer x2 cells and 2^smr_l3 times finer x3 cells groups its row j as their row
+// j >> smr_l2, over 2^smr_l3 times as many of its own cells (the same phi range)
 __host__ __device__ inline int smr_width(const BlockView& v, const PhysArgs& ph, int j) {
     if (ph.smr <= 0) return 1;
     int jp = 1 << 30;
     if (v.bc[2] == HAMR_BC_POLAR) jp = j;
     if (v.bc[3] == HAMR_BC_POLAR) jp = (v.n2 - 1 - j < jp) ? v.n2 - 1 - j : jp;
+    const int jb = jp >> v.smr_l2;
     for (int n = ph.smr; n >= 1; n--)
-        if (jp < (1 << (ph.smr - n))) return 1 << n;
+        if (jb < (1 << (ph.smr - n))) return (1 << n) << v.smr_l3;
     return 1;
+}
+
+// grouped rows next to each polar face under internal SMR
+__host__ __device__ inline int smr_rows(const BlockView& v, const PhysArgs& ph) {
+    return (ph.smr > 0) ? ((1 << (ph.smr - 1)) << v.smr_l2) : 0;
 }
 
 // threads of one reconstruction launch (FP64): rows along x1 in warps of 32
@@ -170,6 +182,10 @@ cudaError_t launch_table_f32(const double* src, float* dst, int nplanes, long st
 int set_error(int code, const char* fmt, ...);
 // api.cu: the descriptor checks of hamr_grid_create (HAMR_OK or HAMR_EINVAL with a message)
 int validate_desc(const hamr_grid_desc* d);
+// api.cu: internal SMR in a block tree: whether B touches a polar face, and log2 of the coarsest
+// polar block's x2 and x3 cell widths over B's (false unless both are powers of 2)
+bool smr_polar(const hamr_block_desc& B);
+bool smr_factors(const hamr_grid_desc& d, const hamr_block_desc& B, int* l2, int* l3);
 
 // step.cu
 cudaError_t launch_centre_b(const BlockView& v, double* P, const double* B, cudaStream_t s);
@@ -198,10 +214,19 @@ cudaError_t launch_ct(const BlockView& v, const double* E, const double* Bbase, 
                       double dt_factor, cudaStream_t s);
 // internal SMR (single-block grids): group means of the radial and far-side theta faces and
 // interpolated inner phi faces after CT; one inversion per group after the cell update
-cudaError_t launch_smr_faces(const BlockView& v, const PhysArgs& ph, double* B, cudaStream_t s);
+cudaError_t launch_smr_emf(const BlockView& v, const PhysArgs& ph, double* E, cudaStream_t s);
 cudaError_t launch_smr_cells(const BlockView& v, const PhysArgs& ph, int corrector, const double* Pf, const double* Bn,
                              double* Po, uint8_t* status, unsigned long long* dmax, unsigned long long* dcnt,
                              cudaStream_t s);
+// threads of one block's SMR EMF and cell kernels (0 where the block groups no row)
+long smr_emf_threads(const BlockView& v, const PhysArgs& ph);
+long smr_cell_threads(const BlockView& v, const PhysArgs& ph);
+// batched over list[0..nlist): the stage's EMFs; the cells of the predictor (sigma 0) or the corrector
+// (1); maxwork: the largest smr_*_threads of the listed blocks
+cudaError_t launch_smr_emf_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
+                                 cudaStream_t s);
+cudaError_t launch_smr_cells_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
+                                   int sigma, cudaStream_t s);
 cudaError_t launch_update(const BlockView& v, const PhysArgs& ph, int corrector, const double* Pbase,
                           const double* Pflux, double* const F[3], const double* Bnew, double* Un, double* Pout,
                           uint8_t* status, const double* dscal, double dt_factor, unsigned long long* dmax,
@@ -241,7 +266,12 @@ cudaError_t launch_reflux_u0(const DevBlock* tab, int n, const int* cblk, const 
                              const int* recs, const double* rec_dU, int nrec_tot, double* Ucorr, const PhysArgs& ph,
                              cudaStream_t s);
 cudaError_t launch_reflux_cells(const DevBlock* tab, int n, const int* cblk, const long* cidx, const double* Ucorr,
-                                const PhysArgs& ph, cudaStream_t s);
+                                long stride, const PhysArgs& ph, cudaStream_t s);
+// refluxed internal-SMR groups: group g's w[g] cells at list positions first[g].. (relative to cblk,
+// cidx and Ucorr); inverted as one cell
+cudaError_t launch_reflux_groups(const DevBlock* tab, int ngrp, const int* first, const int* w, const int* cblk,
+                                 const long* cidx, const double* Ucorr, long stride, const PhysArgs& ph,
+                                 cudaStream_t s);
 
 // amr.cu
 struct AmrImpl;

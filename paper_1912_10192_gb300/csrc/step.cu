@@ -1269,7 +1269,9 @@ template <bool MLP, typename TS>
 __global__ void __launch_bounds__(BS, 3) kb_update(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
     const DevBlock& D = tab[list[blockIdx.y]];
     const bool c = sigma != 0;  // predictor (0) or corrector (2, no CFL rate here) of the block's step
-    b_update<MLP, TS>(D.v, ph, c ? 2 : 0, D.P, c ? D.Ph : D.P, D.F1, D.F2, D.F3, c ? D.B : D.Bh, D.Un, c ? D.P : D.Ph,
+    PhysArgs pb = ph;
+    pb.smr_u = D.QR;  // internal SMR: the grouped cells' conserved states (free once the fluxes exist)
+    b_update<MLP, TS>(D.v, pb, c ? 2 : 0, D.P, c ? D.Ph : D.P, D.F1, D.F2, D.F3, c ? D.B : D.Bh, D.Un, c ? D.P : D.Ph,
                       D.status, D.dscal, c ? 1.0 : 0.5, D.dmax, D.dcnt, tidx());
 }
 
@@ -1316,9 +1318,9 @@ __global__ void k_reflux_u0(const DevBlock* tab, int n, const int* cblk, const l
     }
 }
 
-// inversion of the refluxed cells with the corrected field; floors
+// inversion of the refluxed cells with the corrected field; floors. Ucorr: stride `stride` per field
 __global__ void k_reflux_cells(const DevBlock* tab, int n, const int* cblk, const long* cix, const double* Ucorr,
-                               PhysArgs ph) {
+                               long stride, PhysArgs ph) {
     const long i = tidx();
     if (i >= n) return;
     const DevBlock& D = tab[cblk[i]];
@@ -1329,7 +1331,7 @@ __global__ void k_reflux_cells(const DevBlock* tab, int n, const int* cblk, cons
     Metric<double> m;
     load_metric(v.gc, v.n2d, g, m);
     double U[NCONS];
-    for (int q = 0; q < NCONS; q++) U[q] = Ucorr[(long)q * n + i];
+    for (int q = 0; q < NCONS; q++) U[q] = Ucorr[(long)q * stride + i];
     double Bc[3];
     centre_field(v, D.B, ii, jj, kk, m.igdet, Bc);
     double pr[NPRIM];
@@ -1355,54 +1357,159 @@ __global__ void k_reflux_cells(const DevBlock* tab, int n, const int* cblk, cons
     if (fl) atomicAdd(&D.dcnt[3], 1ull);
 }
 
+// refluxed internal-SMR groups (its w cells consecutive in the list from position first[g]): the mean
+// of the cells' corrected states inverted once with the mean corrected centre field, from the mean
+// primitives; every cell takes the result and keeps its own centre field; floors
+__global__ void k_reflux_groups(const DevBlock* tab, int ngrp, const int* first, const int* gw, const int* cblk,
+                                const long* cix, const double* Ucorr, long stride, PhysArgs ph) {
+    const long t = tidx();
+    if (t >= ngrp) return;
+    const int f = first[t], w = gw[t];
+    const DevBlock& D = tab[cblk[f]];
+    const BlockView& v = D.v;
+    const long c0 = cix[f];
+    const int ii = (int)(c0 % v.n1p) - NG, jj = (int)((c0 / v.n1p) % v.n2p) - NG;
+    const int k0 = (int)(c0 / ((long)v.n1p * v.n2p)) - NG;
+    const long g = gidx(v, ii, jj);
+    Metric<double> m;
+    load_metric(v.gc, v.n2d, g, m);
+    double U[NCONS], Bc[3] = {0.0, 0.0, 0.0}, pr[NPRIM];
+#pragma unroll
+    for (int q = 0; q < NCONS; q++) U[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < NPRIM; q++) pr[q] = 0.0;
+    for (int a = 0; a < w; a++) {
+        const long c = cix[f + a];
+#pragma unroll
+        for (int q = 0; q < NCONS; q++) U[q] += Ucorr[(long)q * stride + f + a];
+        double b[3];
+        centre_field(v, D.B, ii, jj, k0 + a, m.igdet, b);
+        for (int e = 0; e < 3; e++) Bc[e] += b[e];
+#pragma unroll
+        for (int q = 0; q < 5; q++) pr[q] += D.P[q * v.nc + c];
+    }
+#pragma unroll
+    for (int q = 0; q < NCONS; q++) U[q] /= w;
+    for (int e = 0; e < 3; e++) Bc[e] /= w;
+#pragma unroll
+    for (int q = 0; q < 5; q++) pr[q] /= w;
+    double p0[5];
+#pragma unroll
+    for (int q = 0; q < 5; q++) p0[q] = pr[q];
+    pr[B1] = Bc[0];
+    pr[B2] = Bc[1];
+    pr[B3] = Bc[2];
+    int its;
+    const int st = invert(U, Bc, m, ph.gam, pr, &its, false, nullptr, ph.inversion);
+    if (st == INV_FAIL)
+#pragma unroll
+        for (int q = 0; q < 5; q++) pr[q] = p0[q];
+    int fl = 0;
+    if (ph.floors) {
+        Fluid<double> s;
+        fluid_state(pr, m, s);
+        fl = cell_floors(v, g, m, ph, pr, s);
+    }
+    for (int a = 0; a < w; a++) {
+        const long c = cix[f + a];
+        double b[3];
+        centre_field(v, D.B, ii, jj, k0 + a, m.igdet, b);
+#pragma unroll
+        for (int q = 0; q < 5; q++) D.P[q * v.nc + c] = pr[q];
+        for (int e = 0; e < 3; e++) D.P[(B1 + e) * v.nc + c] = b[e];
+    }
+    atomicAdd(&D.dcnt[st == INV_OK ? 0 : (st == INV_ENTROPY ? 1 : 2)], (unsigned long long)w);
+    if (fl) atomicAdd(&D.dcnt[3], (unsigned long long)w);
+}
+
 // ---------------------------------------------------------------- internal SMR
-// Rows next to a polar face grouped into cells smr_width wide in x3 (Sec. 3.3.2):
-// after CT, a group's x1-faces and its x2-face away from the pole take their
-// group mean and its inner x3-faces are interpolated linearly between its two
-// outer ones (every cell stays divergence-free); after the cell update (which
-// leaves the group's conserved states in ph.smr_u) the group's mean state is
-// inverted once with the mean centre field, from the mean primitives, and every
-// cell takes the result (its own centre field kept); the CFL rate uses the
-// group's width. Threads: rows j in [0, nr) and [n2 - nr, n2), nr = 2^(smr-1).
+// Rows next to a polar face grouped into cells smr_width wide in x3 (Sec. 3.3.2:
+// a group's fluxes and conserved state are averaged). The field: before CT, along
+// each x2-line of edges with group width W (that of the adjacent row closer to the
+// pole) the E3 of a group take their mean and the inner E1 are linear between the
+// group's outer ones; inside each grouped row the inner E2 are linear between the
+// group's outer ones. The changes of a group's x1- and x2-faces are then uniform
+// and those of its inner x3-faces linear (a wide cell's), and CT keeps div B. The
+// cells: after the cell update (which leaves the group's conserved states in the
+// scratch U) the group's mean state is inverted once with the mean centre field,
+// from the mean primitives, and every cell takes the result (its own centre field
+// kept); the CFL rate uses the group's width.
+__device__ __forceinline__ int smr_line_width(const BlockView& v, const PhysArgs& ph, int je) {
+    int w = 1;
+    if (je >= 1) w = max(w, smr_width(v, ph, je - 1));
+    if (je < v.n2) w = max(w, smr_width(v, ph, je));
+    return w;
+}
+
+// sum of w = 2^n values as a balanced binary tree (w equal values sum to exactly w times the
+// value): element m closes the subtrees its trailing one bits end
+__device__ __forceinline__ double pair_sum_strided(const double* __restrict__ a, long stride, int w) {
+    double st[12];
+    for (int m = 0; m < w; m++) {
+        double t = a[m * stride];
+        int l = 0;
+        while ((m >> l) & 1) {
+            t = st[l] + t;
+            l++;
+        }
+        st[l] = t;
+    }
+    return st[__ffs(w) - 1];
+}
+
+// Threads: i in [0, n1], q over the nr + 1 edge lines and nr rows next to each polar face
+// (lines je = 0..nr and n2 - nr..n2, a line counted once when n2 = 2 nr), gi over the groups.
+__device__ __forceinline__ void b_smr_emf(const BlockView& v, const PhysArgs& ph, double* __restrict__ E, long t) {
+    const int nr = smr_rows(v, ph);
+    const int ng = v.n3 / 2;
+    const int nq = 2 * (nr + 1);
+    if (nr == 0 || t >= (long)(v.n1 + 1) * nq * ng) return;
+    const int i = (int)(t % (v.n1 + 1));
+    const int q = (int)((t / (v.n1 + 1)) % nq);
+    const int gi = (int)(t / ((long)(v.n1 + 1) * nq));
+    const long sk = (long)v.n1p * v.n2p;
+    double* E1 = E;
+    double* E2 = E + v.nc;
+    double* E3 = E + 2 * v.nc;
+    // the edge line: lower side je = q, upper side je = n2 - 2 nr - 1 + q
+    const bool upper = q > nr;
+    const int je = upper ? v.n2 - 2 * nr - 1 + q : q;
+    const int W = (upper && je <= nr) ? 1 : smr_line_width(v, ph, je);
+    if (W > 1 && gi < v.n3 / W) {
+        const int k0 = gi * W;
+        const long c0 = cidx(v, i, je, k0);
+        const double s3 = pair_sum_strided(E3 + c0, sk, W);
+        for (int m = 0; m < W; m++) E3[c0 + m * sk] = s3 / W;
+        if (i < v.n1) {
+            const double e0 = E1[c0], ew = E1[c0 + W * sk];
+            for (int m = 1; m < W; m++) E1[c0 + m * sk] = e0 + (ew - e0) * m / W;
+        }
+    }
+    // the row: lower side j = q (q < nr), upper side j = n2 - 2 nr - 1 + q (nr < q <= 2 nr)
+    const int j = (q < nr) ? q : ((q > nr && q <= 2 * nr) ? v.n2 - 2 * nr - 1 + q : -1);
+    if (j < 0) return;
+    const int w = smr_width(v, ph, j);
+    if (w > 1 && gi < v.n3 / w) {
+        const int k0 = gi * w;
+        const long c0 = cidx(v, i, j, k0);
+        const double e0 = E2[c0], ew = E2[c0 + w * sk];
+        for (int m = 1; m < w; m++) E2[c0 + m * sk] = e0 + (ew - e0) * m / w;
+    }
+}
+
+// the grouped row of cell-thread row r: rows [0, nr) and [n2 - nr, n2), nr = smr_rows
 __device__ __forceinline__ int smr_row(const BlockView& v, const PhysArgs& ph, int r) {
-    const int nr = 1 << (ph.smr - 1);
+    const int nr = smr_rows(v, ph);
     return (r < nr) ? r : v.n2 - 2 * nr + r;
 }
 
-__global__ void k_smr_faces(BlockView v, PhysArgs ph, double* __restrict__ B) {
-    const int nr = 1 << (ph.smr - 1);
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_smr_cells(const BlockView& v, const PhysArgs& ph, int corrector,
+                                            const double* __restrict__ Pf, const double* __restrict__ Bn,
+                                            const double* __restrict__ Us, double* Po, uint8_t* __restrict__ status,
+                                            unsigned long long* dmax, unsigned long long* dcnt, long t) {
+    const int nr = smr_rows(v, ph);
     const int ng = v.n3 / 2;
-    if (t >= (long)(v.n1 + 1) * 2 * nr * ng) return;
-    const int i = (int)(t % (v.n1 + 1));
-    const int r = (int)((t / (v.n1 + 1)) % (2 * nr));
-    const int gi = (int)(t / ((long)(v.n1 + 1) * 2 * nr));
-    const int j = smr_row(v, ph, r);
-    const int w = smr_width(v, ph, j);
-    if (w == 1 || gi >= v.n3 / w) return;
-    const int k0 = gi * w;
-    double s1 = 0.0;
-    for (int m = 0; m < w; m++) s1 += B[cidx(v, i, j, k0 + m)];
-    for (int m = 0; m < w; m++) B[cidx(v, i, j, k0 + m)] = s1 / w;
-    if (i == v.n1) return;
-    const bool lower_pole = (v.bc[2] == HAMR_BC_POLAR) && (j < v.n2 / 2);
-    const int jf = lower_pole ? j + 1 : j;
-    double* B2 = B + v.nc;
-    double s2 = 0.0;
-    for (int m = 0; m < w; m++) s2 += B2[cidx(v, i, jf, k0 + m)];
-    for (int m = 0; m < w; m++) B2[cidx(v, i, jf, k0 + m)] = s2 / w;
-    double* B3 = B + 2 * v.nc;
-    const double b0 = B3[cidx(v, i, j, k0)], bw = B3[cidx(v, i, j, k0 + w)];
-    for (int m = 1; m < w; m++) B3[cidx(v, i, j, k0 + m)] = b0 + (bw - b0) * m / w;
-}
-
-__global__ void k_smr_cells(BlockView v, PhysArgs ph, int corrector, const double* __restrict__ Pf,
-                            const double* __restrict__ Bn, double* Po, uint8_t* __restrict__ status,
-                            unsigned long long* dmax, unsigned long long* dcnt) {
-    const int nr = 1 << (ph.smr - 1);
-    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int ng = v.n3 / 2;
-    if (t >= (long)v.n1 * 2 * nr * ng) return;
+    if (nr == 0 || t >= (long)v.n1 * 2 * nr * ng) return;
     const int i = (int)(t % v.n1);
     const int r = (int)((t / v.n1) % (2 * nr));
     const int gi = (int)(t / ((long)v.n1 * 2 * nr));
@@ -1421,7 +1528,7 @@ __global__ void k_smr_cells(BlockView v, PhysArgs ph, int corrector, const doubl
     for (int a = 0; a < w; a++) {
         const long c = cidx(v, i, j, k0 + a);
 #pragma unroll
-        for (int q = 0; q < NCONS; q++) U[q] += ph.smr_u[q * v.nc + c];
+        for (int q = 0; q < NCONS; q++) U[q] += Us[q * v.nc + c];
         double b[3];
         centre_field(v, Bn, i, j, k0 + a, m.igdet, b);
         for (int e = 0; e < 3; e++) Bc[e] += b[e];
@@ -1460,12 +1567,45 @@ __global__ void k_smr_cells(BlockView v, PhysArgs ph, int corrector, const doubl
     atomicAdd(&dcnt[st == INV_OK ? 0 : (st == INV_ENTROPY ? 1 : 2)], (unsigned long long)w);
     if (fl) atomicAdd(&dcnt[3], (unsigned long long)w);
     atomicAdd(&dcnt[4], (unsigned long long)(w * its));
-    if (corrector == 1) {
+    if (corrector == 1) {  // the CFL rate over the group's width, of each cell with its own centre field
         BlockView vw = v;
         vw.idx3 = v.idx3 / w;
-        const double inv = inv_dt_fluid(vw, pr, s, m, ph.gam);
+        double inv = 0.0;
+        for (int a = 0; a < w; a++) {
+            double pa[NPRIM];
+#pragma unroll
+            for (int q = 0; q < NPRIM; q++) pa[q] = Po[q * v.nc + cidx(v, i, j, k0 + a)];
+            Fluid<double> sa;
+            fluid_state(pa, m, sa);
+            inv = fmax(inv, inv_dt_fluid(vw, pa, sa, m, ph.gam));
+        }
         if (inv > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(inv));
     }
+}
+
+__global__ void k_smr_emf(BlockView v, PhysArgs ph, double* __restrict__ E) {
+    b_smr_emf(v, ph, E, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void k_smr_cells(BlockView v, PhysArgs ph, int corrector, const double* __restrict__ Pf,
+                            const double* __restrict__ Bn, double* Po, uint8_t* __restrict__ status,
+                            unsigned long long* dmax, unsigned long long* dcnt) {
+    b_smr_cells(v, ph, corrector, Pf, Bn, ph.smr_u, Po, status, dmax, dcnt, (long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// batched: the EMFs of the stage (after the edge synchronisation) and the cells of the block's
+// predictor (sigma 0) or corrector (1, no CFL rate: the period sets dt); scratch: the block's right
+// edge values, free once the fluxes are formed
+__global__ void kb_smr_emf(const DevBlock* tab, const int* list, PhysArgs ph) {
+    const DevBlock& D = tab[list[blockIdx.y]];
+    b_smr_emf(D.v, ph, D.E, tidx());
+}
+
+__global__ void kb_smr_cells(const DevBlock* tab, const int* list, PhysArgs ph, int sigma) {
+    const DevBlock& D = tab[list[blockIdx.y]];
+    const bool c = sigma != 0;
+    b_smr_cells(D.v, ph, c ? 2 : 0, c ? D.Ph : D.P, c ? D.B : D.Bh, D.QR, c ? D.P : D.Ph, D.status, D.dmax, D.dcnt,
+                tidx());
 }
 
 // maximum of field q over the interior cells, as ordered bits (ordered_bits)
@@ -1486,17 +1626,38 @@ __global__ void k_block_max(BlockView v, const double* __restrict__ P, int q, un
 
 }  // namespace
 
-cudaError_t launch_smr_faces(const BlockView& v, const PhysArgs& ph, double* B, cudaStream_t s) {
-    const long n = (long)(v.n1 + 1) * 2 * (1 << (ph.smr - 1)) * (v.n3 / 2);
-    k_smr_faces<<<nblk(n), BS, 0, s>>>(v, ph, B);
+cudaError_t launch_smr_emf(const BlockView& v, const PhysArgs& ph, double* E, cudaStream_t s) {
+    const long n = smr_emf_threads(v, ph);
+    if (n > 0) k_smr_emf<<<nblk(n), BS, 0, s>>>(v, ph, E);
     return cudaGetLastError();
 }
 
 cudaError_t launch_smr_cells(const BlockView& v, const PhysArgs& ph, int corrector, const double* Pf, const double* Bn,
                              double* Po, uint8_t* status, unsigned long long* dmax, unsigned long long* dcnt,
                              cudaStream_t s) {
-    const long n = (long)v.n1 * 2 * (1 << (ph.smr - 1)) * (v.n3 / 2);
-    k_smr_cells<<<nblk(n), BS, 0, s>>>(v, ph, corrector, Pf, Bn, Po, status, dmax, dcnt);
+    const long n = smr_cell_threads(v, ph);
+    if (n > 0) k_smr_cells<<<nblk(n), BS, 0, s>>>(v, ph, corrector, Pf, Bn, Po, status, dmax, dcnt);
+    return cudaGetLastError();
+}
+
+long smr_emf_threads(const BlockView& v, const PhysArgs& ph) {
+    const int nr = smr_rows(v, ph);
+    return nr ? (long)(v.n1 + 1) * 2 * (nr + 1) * (v.n3 / 2) : 0;
+}
+
+long smr_cell_threads(const BlockView& v, const PhysArgs& ph) { return (long)v.n1 * 2 * smr_rows(v, ph) * (v.n3 / 2); }
+
+cudaError_t launch_smr_emf_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
+                                 cudaStream_t s) {
+    if (nlist == 0 || maxwork == 0) return cudaSuccess;
+    kb_smr_emf<<<dim3(nblk(maxwork), nlist), BS, 0, s>>>(tab, list, ph);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_smr_cells_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, const PhysArgs& ph,
+                                   int sigma, cudaStream_t s) {
+    if (nlist == 0 || maxwork == 0) return cudaSuccess;
+    kb_smr_cells<<<dim3(nblk(maxwork), nlist), BS, 0, s>>>(tab, list, ph, sigma);
     return cudaGetLastError();
 }
 
@@ -1775,9 +1936,17 @@ cudaError_t launch_reflux_u0(const DevBlock* tab, int n, const int* cblk, const 
 }
 
 cudaError_t launch_reflux_cells(const DevBlock* tab, int n, const int* cblk, const long* cidx_, const double* Ucorr,
-                                const PhysArgs& ph, cudaStream_t s) {
+                                long stride, const PhysArgs& ph, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_reflux_cells<<<nblk(n), BS, 0, s>>>(tab, n, cblk, cidx_, Ucorr, ph);
+    k_reflux_cells<<<nblk(n), BS, 0, s>>>(tab, n, cblk, cidx_, Ucorr, stride, ph);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reflux_groups(const DevBlock* tab, int ngrp, const int* first, const int* w, const int* cblk,
+                                 const long* cidx_, const double* Ucorr, long stride, const PhysArgs& ph,
+                                 cudaStream_t s) {
+    if (ngrp <= 0) return cudaSuccess;
+    k_reflux_groups<<<nblk(ngrp), BS, 0, s>>>(tab, ngrp, first, w, cblk, cidx_, Ucorr, stride, ph);
     return cudaGetLastError();
 }
 

@@ -128,3 +128,69 @@ def mixed_rounding_per_step(d, prim, bf):
     return {"rho": dP[:, 0].sum() / np.abs(pr[:, 0]).sum(), "u": dP[:, 1].sum() / np.abs(pr[:, 1]).sum(),
             "utilde": dP[:, 2:5].sum() / np.abs(pr[:, 2:5]).sum(),
             "Bface": U32 * dB.sum() / sum(np.abs(B[m][s]).sum() for m in range(3))}
+
+
+def polar_field(bf, x1min, x2min, x3min, dx1, dx2, dx3, n, B0=1e-3, m3=0.3):
+    """adds a divergence-free field threading the poles to the face fluxes bf (padded, in place): the
+    vector potential A_3 = (B0 / 2) r^2 sin^2(theta) (1 + m3 cos phi) (r = exp(x1), theta = x2,
+    phi = x3) at the cells' x3-edges (a vertical field, modulated in phi), whose discrete curl gives
+    the x1- and x2-face fluxes of each phi cell"""
+    n1, n2, n3 = n
+    r = np.exp(x1min + np.arange(n1 + 1) * dx1)
+    th = x2min + np.arange(n2 + 1) * dx2
+    ph = x3min + (np.arange(n3) + 0.5) * dx3
+    A = 0.5 * B0 * (r[None, None, :] * np.sin(th)[None, :, None]) ** 2 * (1.0 + m3 * np.cos(ph))[:, None, None]
+    bf[0][NG:NG + n3, NG:NG + n2, NG:NG + n1 + 1] += (A[:, 1:, :] - A[:, :-1, :]) / dx2
+    bf[1][NG:NG + n3, NG:NG + n2 + 1, NG:NG + n1] += -(A[:, :, 1:] - A[:, :, :-1]) / dx1
+
+
+def polar_field_desc(bf, d, B0=1e-3, m3=0.3):
+    """polar_field on the single block of descriptor d"""
+    polar_field(bf, d.x1min, d.x2min, d.x3min, d.dx1, d.dx2, d.dx3, (d.n1, d.n2, d.n3), B0=B0, m3=m3)
+
+
+def refined_polar_tree(n=8, nb=(4, 2, 2), centre=(1.0, 0.0, 18.0), B0=1e-8, gam=5.0 / 3.0):
+    """flat log-r spherical blocks over r in [2, 40], the radial block column at index 2 refined
+    (octants, 6-way next to the axis), LAT levels; an explosion over the axis across the face where
+    the refined blocks meet a coarser block on a slower LAT level (refluxed cells in grouped rows),
+    into a cold ambient (p = 1e-14, so the discrete imbalance of a gas at rest in spherical
+    coordinates moves no measurable mass through the radial boundaries), plus a weak axisymmetric
+    vertical field through the poles. Returns (blocks, states)."""
+    blocks = W.polar_smr_tree(2.0, 40.0, nb, n, range(2, 3))
+    states = W.explosion_blocks(blocks, centre=centre, gam=gam, p_out=1e-14)
+    for b, (p, bf) in zip(blocks, states):
+        polar_field(bf, b["x1min"], b["x2min"], b["x3min"], b["dx1"], b["dx2"], b["dx3"],
+                    (b["n1"], b["n2"], b["n3"]), B0=B0, m3=0.0)
+    return blocks, states
+
+
+def ora_tree(phys, blocks, states):
+    """the oracle's multi-block grid of block dicts with their padded states"""
+    a = O.AmrGrid(phys, [O.make_block(b["n1"], b["n2"], b["n3"], b["x1min"], b["x2min"], b["x3min"], b["dx1"],
+                                      b["dx2"], b["dx3"], b["bc"], b["lat"]) for b in blocks])
+    for i, (p, bf) in enumerate(states):
+        a.set(i, p, bf)
+    return a
+
+
+def tree_errors(g, a, blocks):
+    """relative L1 differences (rho, u, utilde, face fluxes) between the GPU grid g and the oracle's a
+    over the interiors of all blocks"""
+    num = {k: 0.0 for k in ("rho", "u", "utilde", "Bface")}
+    den = dict(num)
+    for i, b in enumerate(blocks):
+        pg, bg = g.get_state(block=i)
+        po, bo = a.get(i)
+        n1, n2, n3 = b["n1"], b["n2"], b["n3"]
+        s = (slice(NG, NG + n3), slice(NG, NG + n2), slice(NG, NG + n1))
+        for k, vs in (("rho", (0,)), ("u", (1,)), ("utilde", (2, 3, 4))):
+            for v in vs:
+                num[k] += np.abs(pg[v][s] - po[v][s]).sum()
+                den[k] += np.abs(po[v][s]).sum()
+        fs = [(slice(NG, NG + n3), slice(NG, NG + n2), slice(NG, NG + n1 + 1)),
+              (slice(NG, NG + n3), slice(NG, NG + n2 + 1), slice(NG, NG + n1)),
+              (slice(NG, NG + n3 + 1), slice(NG, NG + n2), slice(NG, NG + n1))]
+        for m in range(3):
+            num["Bface"] += np.abs(bg[m][fs[m]] - bo[m][fs[m]]).sum()
+            den["Bface"] += np.abs(bo[m][fs[m]]).sum()
+    return {k: num[k] / max(den[k], 1e-300) for k in num}

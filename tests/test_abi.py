@@ -80,6 +80,12 @@ def test_option_fields_are_validated_before_any_device_call(libpath):
     d, arr = _desc([odd], smr=3)
     assert L.hamr_grid_create(ctypes.byref(d), ctypes.byref(h)) == hamr.EINVAL
     assert b"multiple of 16" in L.hamr_last_error()
+    # in a block tree every polar block's widths are a power of 2 finer than the coarsest polar block's
+    base = hamr.block(16, 16, 16, 0.0, 0.0, 0.0, 0.1, 0.1, 0.1, (3, 4, 2, 2, 1, 1))
+    third = hamr.block(16, 16, 16, 1.6, 0.0, 0.0, 0.1, 0.1, 0.1 / 3.0, (4, 3, 2, 2, 1, 1))
+    d, arr = _desc([base, third], smr=1)
+    assert L.hamr_grid_create(ctypes.byref(d), ctypes.byref(h)) == hamr.EINVAL
+    assert b"block 1: internal SMR needs" in L.hamr_last_error(), L.hamr_last_error()
     # polar boundaries need spherical coordinates: refused in flat Cartesian space
     d, arr = _desc([polar], metric=1)
     assert L.hamr_grid_create(ctypes.byref(d), ctypes.byref(h)) == hamr.EINVAL

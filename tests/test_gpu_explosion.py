@@ -1,11 +1,11 @@
 """The paper's off-centre explosion through the pole on the GPU path (Sec. 6):
 flat space in log-r spherical coordinates, a base of 8 x 4 x 4 blocks with
 phi-derefined polar blocks (external SMR), the blocks around the explosion
-refined (octants, 6-way next to the axis), four LAT levels; a sphere of
-radius 2 at (3, 0, 10) at high pressure. Checks: a LAT period of the
-magnetised explosion equals the oracle's; after the hydrodynamic blast has
-crossed the polar axis its front is as far from the centre toward and
-through the axis as across, and no inversion fails."""
+refined (octants, 6-way next to the axis), four LAT levels, without and with
+internal SMR; a sphere of radius 2 at (3, 0, 10) at high pressure. Checks: a
+LAT period of the magnetised explosion equals the oracle's; after the
+hydrodynamic blast has crossed the polar axis its front is as far from the
+centre toward and through the axis as across, and no inversion fails."""
 import math
 
 import numpy as np
@@ -30,20 +30,21 @@ def _gpu():
     torch.cuda.set_device(0)
 
 
-def _grid(blocks, states):
+def _grid(blocks, states, smr=0):
     from paper_1912_10192_gb300 import hamr
     g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], metric=hamr.METRIC_SPHERICAL, gam=GAM, cour=0.8,
-                  floors=0)
+                  floors=0, smr=smr)
     for i, (p, bf) in enumerate(states):
         g.set_state(p, bf, block=i)
     return g
 
 
-def test_magnetised_explosion_period_matches_oracle():
+@pytest.mark.parametrize("smr", [0, 1])
+def test_magnetised_explosion_period_matches_oracle(smr):
     blocks = W.polar_smr_tree(2.0, 40.0, (8, 4, 4), 8, range(3, 6))
     states = W.explosion_blocks(blocks, beta_max=10.0)
-    g = _grid(blocks, states)
-    phys = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, metric=O.METRIC_SPHERICAL, gam=GAM, cour=0.8, floors=0)
+    g = _grid(blocks, states, smr)
+    phys = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, metric=O.METRIC_SPHERICAL, gam=GAM, cour=0.8, floors=0, smr=smr)
     a = O.AmrGrid(phys, [O.make_block(b["n1"], b["n2"], b["n3"], b["x1min"], b["x2min"], b["x3min"], b["dx1"],
                                       b["dx2"], b["dx3"], b["bc"], b["lat"]) for b in blocks])
     for i, (p, bf) in enumerate(states):
@@ -74,10 +75,13 @@ def test_magnetised_explosion_period_matches_oracle():
         assert e <= 1e-10, (k, e, errs)
 
 
-def test_blast_front_keeps_its_shape_through_the_pole():
+@pytest.mark.parametrize("smr", [0, 2])
+def test_blast_front_keeps_its_shape_through_the_pole(smr):
+    """with two internal SMR levels too (the paper's set-up: one external and two internal SMR
+    layers, four LAT levels)"""
     blocks = W.polar_smr_tree(2.0, 40.0, (8, 4, 4), 16, range(3, 6))
     states = W.explosion_blocks(blocks)
-    g = _grid(blocks, states)
+    g = _grid(blocks, states, smr)
     lmax = max(b["lat"] for b in blocks)
     t, fails = 0.0, 0
     while t < 5.0:
@@ -109,8 +113,8 @@ def test_blast_front_keeps_its_shape_through_the_pole():
         return dist[sel].max()
     toward_axis = front(np.array([-1.0, 0.0, 0.0]))       # through the pole
     across = [front(np.array([0.0, 1.0, 0.0])), front(np.array([0.0, -1.0, 0.0]))]  # same height, away
-    print("blast at t=%.2f: front toward/through the axis %.3f, across %.3f %.3f, inversion failures %d"
-          % (t, toward_axis, across[0], across[1], fails))
+    print("smr %d, blast at t=%.2f: front toward/through the axis %.3f, across %.3f %.3f, inversion failures %d"
+          % (smr, t, toward_axis, across[0], across[1], fails))
     assert toward_axis > 3.5  # the front has passed the axis (3 from the centre)
     for r in across:
         assert abs(toward_axis - r) < 0.08 * r, (toward_axis, across)

@@ -1,12 +1,17 @@
 """Internal SMR on the GPU (Sec. 3.3.2, the phi-averaging of polar rows)
-against the oracle: the torus block at the FP64 bars (1 and 10 steps), groups
-identical cell by cell, and the larger CFL step where the pole limits it."""
+against the oracle: the torus block with a field threading the poles at the
+FP64 bars (1 and 10 steps), groups identical cell by cell, the larger CFL step
+where the pole limits it; inside the batched block tree: the torus cut into
+same-level blocks and a refined polar block on a faster LAT level (edge
+synchronisation and refluxing through grouped rows), one period each against
+the oracle."""
 import numpy as np
 import pytest
 
 import oracle as O
 
-from helpers import NG, face_interior, gpu_grid, interior, rel_l1, torus_case
+from helpers import (NG, face_interior, gpu_grid, interior, ora_tree, polar_field, polar_field_desc,
+                     refined_polar_tree, rel_l1, torus_case, tree_errors)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -29,6 +34,7 @@ def _cu(a):
 def test_smr_torus_parity(nsteps, bar):
     geo, d, prim, bf = torus_case(64, 32, 16, seed=1912)
     d.smr = 2
+    polar_field_desc(bf, d, B0=1e-4)  # the grouped rows' EMFs are then not zero
     g = gpu_grid(d)
     g.set_state(_cu(prim), _cu(bf))
     og = O.Grid(d)
@@ -65,3 +71,67 @@ def test_smr_time_step_gain():
         g.close()
     print("CFL step without / with internal SMR (2 levels): %.4g / %.4g" % tuple(dts))
     assert dts[1] > 1.3 * dts[0], dts  # measured 1.43 (the rate also has the x1 and x2 terms)
+
+
+def _tree_grid(blocks, states, **kw):
+    from paper_1912_10192_gb300 import hamr
+    g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], **kw)
+    for i, (p, bf) in enumerate(states):
+        g.set_state(p, bf, block=i)
+    return g
+
+
+def test_smr_split_torus_tree_parity():
+    """The torus with a field through the poles cut into 2 x 2 x 2 same-level blocks, two SMR levels:
+    two periods of the batched path against the oracle's block tree."""
+    geo, d, prim, bf = torus_case(32, 32, 16, seed=3)
+    polar_field_desc(bf, d, B0=1e-4)
+    n = (16, 16, 8)
+    blocks, states = [], []
+    for kb in range(2):
+        for jb in range(2):
+            for ib in range(2):
+                bc = [4] * 6
+                bc[ib] = O.BC_OUTFLOW_NOINFLOW
+                bc[2 + jb] = O.BC_POLAR
+                bc[4 + kb] = O.BC_PERIODIC
+                i0, j0, k0 = ib * n[0], jb * n[1], kb * n[2]
+                blocks.append(dict(n1=n[0], n2=n[1], n3=n[2], x1min=d.x1min + i0 * d.dx1,
+                                   x2min=d.x2min + j0 * d.dx2, x3min=d.x3min + k0 * d.dx3, dx1=d.dx1, dx2=d.dx2,
+                                   dx3=d.dx3, bc=bc, lat=0))
+                pb = np.zeros((8, n[2] + 6, n[1] + 6, n[0] + 6))
+                bb = np.zeros((3, n[2] + 6, n[1] + 6, n[0] + 6))
+                pb[:, 3:3 + n[2], 3:3 + n[1], 3:3 + n[0]] = prim[:, 3 + k0:3 + k0 + n[2], 3 + j0:3 + j0 + n[1],
+                                                                  3 + i0:3 + i0 + n[0]]
+                bb[:, 3:4 + n[2], 3:4 + n[1], 3:4 + n[0]] = bf[:, 3 + k0:4 + k0 + n[2], 3 + j0:4 + j0 + n[1],
+                                                                3 + i0:4 + i0 + n[0]]
+                states.append((pb, bb))
+    d.smr = 2
+    a = ora_tree(d, blocks, states)
+    g = _tree_grid(blocks, states, metric=d.metric, a=d.a, gam=d.gam, cour=d.cour, floors=d.floors, smr=2)
+    for _ in range(2):
+        a.period()
+        g.batch_step(1)
+    errs = tree_errors(g, a, blocks)
+    g.close()
+    for k, e in errs.items():
+        assert e <= 1e-10, (k, e, errs)
+
+
+def test_smr_refined_polar_tree_parity():
+    """A polar block split 6-way next to coarser polar blocks on a slower LAT level, an explosion over
+    the axis across the refluxed face, one SMR level: three periods of the batched path (grouped EMFs
+    after the edge synchronisation, grouped refluxed cells) against the oracle."""
+    blocks, states = refined_polar_tree()
+    phys = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, metric=O.METRIC_SPHERICAL, gam=5.0 / 3.0, cour=0.8, floors=0,
+                       smr=1)
+    a = ora_tree(phys, blocks, states)
+    g = _tree_grid(blocks, states, metric=O.METRIC_SPHERICAL, gam=5.0 / 3.0, cour=0.8, floors=0, smr=1)
+    lmax = max(b["lat"] for b in blocks)
+    for _ in range(3):
+        a.period()
+        g.batch_step(2 ** lmax)
+    errs = tree_errors(g, a, blocks)
+    g.close()
+    for k, e in errs.items():
+        assert e <= 1e-10, (k, e, errs)

@@ -13,6 +13,8 @@ import numpy as np
 import oracle as O
 from paper_1912_10192_gb300 import workloads as W
 
+from helpers import polar_field_desc
+
 NG = O.NG
 
 
@@ -31,24 +33,12 @@ def _div(d, bf):
     return np.diff(f1, axis=2) / d.dx1 + np.diff(f2, axis=1) / d.dx2 + np.diff(f3, axis=0) / d.dx3
 
 
-def polar_field(bf, d, B0=1e-3, m3=0.3):
-    """adds a divergence-free field threading the poles to the face fluxes bf (padded, in place): the
-    vector potential A_3 = (B0 / 2) r^2 sin^2(theta) (1 + m3 cos phi) at the cells' x3-edges, whose
-    discrete curl gives the x1- and x2-face fluxes of each phi cell"""
-    r = np.exp(d.x1min + np.arange(d.n1 + 1) * d.dx1)
-    th = d.x2min + np.arange(d.n2 + 1) * d.dx2
-    ph = d.x3min + (np.arange(d.n3) + 0.5) * d.dx3
-    A = 0.5 * B0 * (r[None, None, :] * np.sin(th)[None, :, None]) ** 2 * (1.0 + m3 * np.cos(ph))[:, None, None]
-    bf[0][NG:NG + d.n3, NG:NG + d.n2, NG:NG + d.n1 + 1] += (A[:, 1:, :] - A[:, :-1, :]) / d.dx2
-    bf[1][NG:NG + d.n3, NG:NG + d.n2 + 1, NG:NG + d.n1] += -(A[:, :, 1:] - A[:, :, :-1]) / d.dx1
-
-
 def test_groups_act_as_single_cells_and_div_b_stays_zero():
     """The torus with a field through the poles that varies in phi: after each step the grouped cells
     hold identical primitives, each group's x1- and x2-faces changed by one amount and its inner
     x3-faces by amounts linear between its outer ones, div B at round-off."""
     d, prim, bf = torus(2)
-    polar_field(bf, d)
+    polar_field_desc(bf, d)
     g = O.Grid(d)
     g.set(prim, bf)
     scale = np.abs(bf).max() / min(d.dx1, d.dx2, d.dx3)
@@ -87,7 +77,7 @@ def test_phi_mirror_symmetric_state_stays_symmetric():
                     metric=O.METRIC_SPHERICAL, gam=5.0 / 3.0, cour=0.8, bc=(3, 3, 2, 2, 1, 1), floors=0, smr=2)
     blk = dict(n1=n1, n2=n2, n3=n3, x1min=d.x1min, x2min=d.x2min, x3min=d.x3min, dx1=d.dx1, dx2=d.dx2, dx3=d.dx3)
     (prim, bf), = W.explosion_blocks([blk], centre=(1.5, 0.0, 8.0), gam=5.0 / 3.0)
-    polar_field(bf, d, B0=1e-4)
+    polar_field_desc(bf, d, B0=1e-4)
     g = O.Grid(d)
     g.set(prim, bf)
     for _ in range(4):

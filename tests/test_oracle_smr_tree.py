@@ -11,22 +11,9 @@ import pytest
 import oracle as O
 from paper_1912_10192_gb300 import workloads as W
 
-from helpers import NG, face_interior, torus_case
+from helpers import NG, ora_tree, polar_field, refined_polar_tree, torus_case
 
 GAM = 5.0 / 3.0
-
-
-def polar_field(bf, x1min, x2min, x3min, dx1, dx2, dx3, n, B0=1e-3, m3=0.3):
-    """adds a divergence-free field threading the poles to the face fluxes bf (padded, in place): the
-    vector potential A_3 = (B0 / 2) r^2 sin^2(theta) (1 + m3 cos phi) at the cells' x3-edges (a vertical
-    field, modulated in phi), whose discrete curl gives the x1- and x2-face fluxes of each phi cell"""
-    n1, n2, n3 = n
-    r = np.exp(x1min + np.arange(n1 + 1) * dx1)
-    th = x2min + np.arange(n2 + 1) * dx2
-    ph = x3min + (np.arange(n3) + 0.5) * dx3
-    A = 0.5 * B0 * (r[None, None, :] * np.sin(th)[None, :, None]) ** 2 * (1.0 + m3 * np.cos(ph))[:, None, None]
-    bf[0][NG:NG + n3, NG:NG + n2, NG:NG + n1 + 1] += (A[:, 1:, :] - A[:, :-1, :]) / dx2
-    bf[1][NG:NG + n3, NG:NG + n2 + 1, NG:NG + n1] += -(A[:, :, 1:] - A[:, :, :-1]) / dx1
 
 
 def _split(prim, bf, d, nb=(2, 2, 2)):
@@ -115,23 +102,10 @@ def smr_width(b, j, smr, h2b, h3b):
     return 1
 
 
-def _refined_polar_case(smr, nb=(4, 2, 2), n=8):
-    """flat log-r spherical blocks, the radial column of the explosion refined (6-way next to the
-    axis), LAT levels; an explosion over the axis, across the face where the refined blocks meet a
-    coarser block on a slower LAT level (so refluxed cells fall in grouped rows), into a cold ambient
-    (whose discrete imbalance in spherical coordinates then moves no measurable mass through the
-    radial boundaries), plus a weak axisymmetric vertical field through the poles"""
-    blocks = W.polar_smr_tree(2.0, 40.0, nb, n, range(2, 3))
-    states = W.explosion_blocks(blocks, centre=(1.0, 0.0, 18.0), gam=GAM, p_out=1e-14)
-    for b, (p, bf) in zip(blocks, states):
-        polar_field(bf, b["x1min"], b["x2min"], b["x3min"], b["dx1"], b["dx2"], b["dx3"], (b["n1"], b["n2"], b["n3"]),
-                    B0=1e-8, m3=0.0)
+def _refined_polar_case(smr):
+    blocks, states = refined_polar_tree()
     phys = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, metric=O.METRIC_SPHERICAL, gam=GAM, cour=0.8, floors=0, smr=smr)
-    a = O.AmrGrid(phys, [O.make_block(b["n1"], b["n2"], b["n3"], b["x1min"], b["x2min"], b["x3min"], b["dx1"],
-                                      b["dx2"], b["dx3"], b["bc"], b["lat"]) for b in blocks])
-    for i, (p, bf) in enumerate(states):
-        a.set(i, p, bf)
-    return blocks, phys, a
+    return blocks, phys, ora_tree(phys, blocks, states)
 
 
 def _mass_and_div(a, blocks, phys):
@@ -182,10 +156,9 @@ def _shared_x1_faces(a, blocks):
 
 def test_groups_coincide_across_a_refined_polar_block():
     """A polar block split 6-way next to coarser polar blocks, on a lower LAT level: after each period
-    every shared x1-face has one value (the coarse group means equal the finer side's, because the
-    finer blocks group their rows by the coarse rows and the refluxed coarse faces are averaged over
-    their groups again), every group's cells hold identical primitives, mass is conserved and div B
-    stays at round-off."""
+    every shared x1-face has one value (the finer blocks group their rows by the coarse rows, so the
+    EMFs the two sides exchange are averaged over the same phi ranges), every group's cells hold
+    identical primitives, mass is conserved and div B stays at round-off."""
     smr = 1
     blocks, phys, a = _refined_polar_case(smr)
     assert len({b["lat"] for b in blocks}) > 1
