@@ -306,6 +306,18 @@ int hamr_grid_timing(hamr_grid* g, hamr_kernel_time* out, int max, int* n);
  * roofline that bounds the FP64 update on this hardware. */
 int hamr_measure_fp64_peak(void* stream, double* gflops);
 
+/* Self-check of the binary32 <-> binary64 conversions the mixed-precision
+ * kernels do on the integer pipe instead of the FP64 pipe (IEEE 754 formats;
+ * narrowing rounds to nearest, ties to even): widening of every binary32
+ * value, and narrowing of every binary32 value's binary64 image, its binary64
+ * neighbours, the midpoint to the next binary32 value and that midpoint's
+ * neighbours, plus `nrandom` pseudo-random binary64 bit patterns (splitmix64
+ * from `seed`), each compared bit for bit with the hardware conversion. No
+ * counterpart in the paper. out4 (host): {widening mismatches, the first
+ * mismatching binary32 pattern or -1, narrowing mismatches, the first
+ * mismatching binary64 pattern or -1}. Synchronises the device; about 0.1 s. */
+int hamr_check_conversions(long long nrandom, unsigned long long seed, long long out4[4]);
+
 /* ---- stepping without allocation ---- */
 /* Largest block hamr_block_step_noalloc accepts: padded cells
  * (n1+6)(n2+6)(n3+6) and padded (i, j) points (n1+6)(n2+6). */
@@ -338,6 +350,7 @@ int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, double* bface
 #define HAMR_C2P_MLP 2u          /* start Newton from the learned guess of `mlp` (fallback: the prim guess) */
 #define HAMR_C2P_MLP_RESCUE 4u   /* start from the prim guess; where that fails, from the learned guess */
 #define HAMR_C2P_AITKEN 8u       /* energy inversion by the Aitken-accelerated pressure iteration, not Newton */
+#define HAMR_C2P_MIXED 16u       /* Newton in FP32 first, then one FP64 refinement step (the mixed-precision update's) */
 
 typedef struct hamr_mlp hamr_mlp;
 

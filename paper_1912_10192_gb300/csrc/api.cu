@@ -394,6 +394,8 @@ int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out) {
     g->blocks.assign(d->blocks, d->blocks + d->nblocks);
     g->desc.blocks = g->blocks.data();
     g->ph.gam = d->gam;
+    g->ph.igam = 1.0 / d->gam;
+    g->ph.gfac = (d->gam - 1.0) * g->ph.igam;
     g->ph.cour = d->cour;
     g->ph.recon = d->recon;
     g->ph.riemann = d->riemann;
@@ -594,6 +596,15 @@ int hamr_measure_fp64_peak(void* stream, double* gflops) {
     return HAMR_OK;
 }
 
+int hamr_check_conversions(long long nrandom, unsigned long long seed, long long out4[4]) {
+    if (!out4) return fail(HAMR_EINVAL, "out4 is NULL");
+    if (nrandom < 0) return fail(HAMR_EINVAL, "nrandom must be >= 0");
+    unsigned long long r[4];
+    CUDA_TRY(check_conversions((unsigned long long)nrandom, seed, r));
+    for (int q = 0; q < 4; q++) out4[q] = (long long)r[q];
+    return HAMR_OK;
+}
+
 int hamr_grid_set_fine_dt(hamr_grid* g, double dt_fine) {
     if (!g) return fail(HAMR_EINVAL, "grid is NULL");
     if (!g->amr) return fail(HAMR_EINVAL, "a single-block grid takes dt in each hamr_block_step call");
@@ -783,7 +794,7 @@ int hamr_con2prim(const hamr_c2p_desc* d, int64_t n, const double* U, const doub
     if (d->metric != HAMR_METRIC_KS && d->metric != HAMR_METRIC_MINKOWSKI && d->metric != HAMR_METRIC_SPHERICAL)
         return fail(HAMR_EINVAL, "unknown metric %d", d->metric);
     if (!(d->gam > 1.0 && d->gam <= 2.0)) return fail(HAMR_EINVAL, "gam must be in (1, 2]");
-    if (d->flags & ~(HAMR_C2P_ENTROPY_ONLY | HAMR_C2P_MLP | HAMR_C2P_MLP_RESCUE | HAMR_C2P_AITKEN))
+    if (d->flags & ~(HAMR_C2P_ENTROPY_ONLY | HAMR_C2P_MLP | HAMR_C2P_MLP_RESCUE | HAMR_C2P_AITKEN | HAMR_C2P_MIXED))
         return fail(HAMR_EINVAL, "unknown flags 0x%x", d->flags);
     if ((d->flags & HAMR_C2P_MLP) && (d->flags & HAMR_C2P_MLP_RESCUE))
         return fail(HAMR_EINVAL, "HAMR_C2P_MLP and HAMR_C2P_MLP_RESCUE exclude each other");

@@ -36,7 +36,9 @@ __global__ void __launch_bounds__(128) k_con2prim(hamr_c2p_desc d, const uint8_t
     const bool entropy_only = (d.flags & HAMR_C2P_ENTROPY_ONLY) != 0;
     const bool rescue = (d.flags & HAMR_C2P_MLP_RESCUE) != 0;
     C2PWork w;
-    if (active) c2p_prepare(u, bc, m, d.gam, pr, w, (d.flags & HAMR_C2P_AITKEN) ? HAMR_INV_AITKEN : HAMR_INV_NEWTON);
+    if (active)
+        c2p_prepare(u, bc, m, d.gam, pr, w, (d.flags & HAMR_C2P_AITKEN) ? HAMR_INV_AITKEN : HAMR_INV_NEWTON,
+                    (d.flags & HAMR_C2P_MIXED) ? 1 : 0);
     if (MLP && !entropy_only) {  // the 128 states of the CTA through the network (mlp.cuh)
         if (rescue && active) c2p_attempt_plain(w, d.gam);
         if (__syncthreads_or(active && !w.ok)) {

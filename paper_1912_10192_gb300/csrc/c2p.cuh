@@ -33,13 +33,13 @@ struct C2PScalars {
 __device__ __forceinline__ void c2p_scalars(const double U[NCONS], const double Bc[3], const Metric<double>& m,
                                             C2PScalars& S) {
     const double al = m.alpha;
-    const double ig = m.igdet;
-    S.D = U[C_RHO] * al * ig;
+    const double aig = al * m.igdet;  // alpha / sqrt(-g), formed once
+    S.D = U[C_RHO] * aig;
     // Q_mu = alpha T^t_mu, raised with the sparse inverse metric
-    const double Q0 = al * (U[C_EN] - U[C_RHO]) * ig;
-    const double Q1 = al * U[C_S1] * ig;
-    const double Q2 = al * U[C_S2] * ig;
-    const double Q3 = al * U[C_S3] * ig;
+    const double Q0 = (U[C_EN] - U[C_RHO]) * aig;
+    const double Q1 = U[C_S1] * aig;
+    const double Q2 = U[C_S2] * aig;
+    const double Q3 = U[C_S3] * aig;
     const double Qc0 = m.c00 * Q0 + m.c01 * Q1;
     S.Qc1 = m.c01 * Q0 + m.c11 * Q1 + m.c13 * Q3;
     S.Qc2 = m.c22 * Q2;
@@ -94,24 +94,34 @@ __device__ __forceinline__ bool newton_wv(const C2PScalars& S, double gfac, doub
 }
 
 // Mixed precision (the FP32-flux form only): FP32 Newton iterations first, on
-// the two equations scaled by k ~ 1/W of the start (every term then O(1):
-// f1 ~ W, f2 ~ W^2, so D, B^2, Q.n scale by k, Qt^2 by k^2, (Q.B)^2 by k^3),
-// until a step is below 1e-5 W (at most 8); then FP64 iterations from there,
-// which stop at the usual rule or, right after that FP32 stage, at a step below
-// 1e-5 W: in the quadratic regime a step d leaves an error of order d^2 / W,
-// at or below the usual 1e-10 W. When the FP32 stage does not get there the
-// FP64 iteration runs from the original start alone. `it` counts the
-// iterations of both precisions.
+// the two equations scaled by k = 2^-e, e the binary exponent of the start's W
+// (an exact scaling; every term then O(1): f1 ~ W, f2 ~ W^2, so D, B^2, Q.n
+// scale by k, Qt^2 by k^2, (Q.B)^2 by k^3), until a step is below 1e-5 W (at
+// most 8). Then one refinement step in the manner of mixed-precision iterative
+// refinement: the FP64 residuals at the FP32 root, solved with the FP32
+// Jacobian there; it shrinks the root's error (~1e-7 W) by the Jacobian's
+// relative error times its condition, to the FP64 level. It is accepted when
+// the step is below 1e-5 W and that bound times the Jacobian's cancellation
+// (|j11 j22| + |j12 j21|) / |det| stays below 1e-3 W (the remaining error of
+// order 1e-10 W, the FP64 rule's); otherwise FP64 Newton iterations run from
+// the refined point, stopping at the usual rule. When the FP32 stage does not
+// converge the FP64 iteration runs from the original start alone. `it` counts
+// the iterations of both precisions (the refinement as one).
 __device__ __forceinline__ bool newton_wv_mixed(const C2PScalars& S, double gfac, double& W, double& vsq, int& it) {
     // the scalars rounded to FP32 first and scaled there (their magnitudes stay far inside FP32's
-    // range for admissible states; an overflow makes the FP32 stage fail, and the FP64 iteration runs)
-    const float Wf = (float)W;
-    const float k = 1.0f / Wf;
+    // range for admissible states; a start outside the normal FP32 range takes the FP64 iteration)
+    const float Wf = narrow(W);
+    const unsigned eb = (__float_as_uint(Wf) >> 23) & 0xffu;  // biased exponent of the start
+    if (!(Wf > 0.0f) || eb == 0u || eb >= 254u) {
+        const bool ok = newton_wv(S, gfac, W, vsq, it);
+        return ok;
+    }
+    const float k = __uint_as_float((254u - eb) << 23);  // 2^(127 - eb): w = W k in [1, 2)
     const float k2 = k * k;
-    const float D = (float)S.D * k, Bsq = (float)S.Bsq * k, Qdotn = (float)S.Qdotn * k;
-    const float Qtsq = (float)S.Qtsq * k2, QB2 = (float)S.QB2 * (k2 * k);
-    const float gf = (float)gfac, vmax = (float)C2P_VSQMAX;
-    float w = Wf * k, v = (float)vsq;
+    const float D = narrow(S.D) * k, Bsq = narrow(S.Bsq) * k, Qdotn = narrow(S.Qdotn) * k;
+    const float Qtsq = narrow(S.Qtsq) * k2, QB2 = narrow(S.QB2) * (k2 * k);
+    const float gf = narrow(gfac), vmax = (float)C2P_VSQMAX;
+    float w = Wf * k, v = narrow(vsq);
     bool ok32 = false;
     int it32 = 0;
     for (it32 = 1; it32 <= 8; it32++) {
@@ -146,11 +156,52 @@ __device__ __forceinline__ bool newton_wv_mixed(const C2PScalars& S, double gfac
         it += it32;
         return ok;
     }
-    // FP64 iterations from the FP32 root (w / k, taken as w W: the start may be off by the rounding of k)
-    double Wd = (double)(w * Wf), vd = (double)v;
     const double D64 = S.D, Bsq64 = S.Bsq, QB264 = S.QB2, Qdotn64 = S.Qdotn, Qtsq64 = S.Qtsq;
+    // the FP32 root in FP64 (W = w / k exactly) and the exact powers 1/k, k^3, k^4 in FP64
+    const int ed = (int)eb - 127;  // 1/k = 2^ed
+    const double ik = __hiloint2double((1023 + ed) << 20, 0);
+    const double k3 = __hiloint2double((1023 - 3 * ed) << 20, 0), k4 = __hiloint2double((1023 - 4 * ed) << 20, 0);
+    double Wd = widen(w) * ik, vd = widen(v);
+    int it64 = 0;
+    {
+        // FP64 residuals of newton_wv's form (times W^2) at the root
+        const double omv = 1.0 - vd;
+        const double sq = omv * rsqrt(omv);
+        const double W2 = Wd * Wd;
+        const double BW = Bsq64 + Wd;
+        const double p = gfac * (Wd * omv - D64 * sq);
+        const double f1 = (-0.5 * Bsq64 * (1.0 + vd) - Wd + p - Qdotn64) * W2 + 0.5 * QB264;
+        const double f2 = (vd * BW * BW - Qtsq64) * W2 - QB264 * (Bsq64 + 2.0 * Wd);
+        // in the FP32 stage's scaled form: k f1 / W^2 = k^3 f1 / w^2, k^2 f2 / W^2 = k^4 f2 / w^2
+        const float iw = 1.0f / w, iw2 = iw * iw;
+        const float r1 = narrow(f1 * k3) * iw2, r2 = narrow(f2 * k4) * iw2;
+        // the FP32 Jacobian at the root
+        const float om = 1.0f - v;
+        const float rs = rsqrtf(om);
+        const float bw = Bsq + w;
+        const float j11 = -QB2 * iw2 * iw - 1.0f + gf * om;
+        const float j12 = -0.5f * Bsq + gf * (0.5f * D * rs - w);
+        const float j21 = 2.0f * bw * (v + QB2 * iw2 * iw);
+        const float j22 = bw * bw;
+        const float det = j11 * j22 - j12 * j21;
+        const float idet = 1.0f / det;
+        const float dw = (j12 * r2 - j22 * r1) * idet, dv = (j21 * r1 - j11 * r2) * idet;
+        const float step = fabsf(dw) + fabsf(dv) * w;
+        const float cancel = (fabsf(j11 * j22) + fabsf(j12 * j21)) * fabsf(idet);
+        const double Wn = Wd + widen(dw) * ik;
+        const double vn = fmin(fmax(vd + widen(dv), 0.0), C2P_VSQMAX);
+        if (Wn > 0.0 && step < 1e-5f * w && step * cancel < 1e-3f * w) {
+            it = it32 + 1;
+            W = Wn;
+            vsq = vn;
+            return true;
+        }
+        if (Wn > 0.0) {
+            Wd = Wn;
+            vd = vn;
+        }
+    }
     bool ok = false;
-    int it64;
     for (it64 = 1; it64 <= C2P_NMAX; it64++) {
         const double omv = 1.0 - vd;
         const double rs = rsqrt(omv);
@@ -172,13 +223,13 @@ __device__ __forceinline__ bool newton_wv_mixed(const C2PScalars& S, double gfac
         const double err = fabs(Wn - Wd) + fabs(vn - vd) * Wn;
         Wd = Wn;
         vd = vn;
-        if (err < C2P_TOL * Wn || (it64 == 1 && err < 1e-5 * Wn)) {
+        if (err < C2P_TOL * Wn) {
             ok = true;
             break;
         }
     }
     if (it64 > C2P_NMAX) it64 = C2P_NMAX;
-    it = it32 + it64;
+    it = it32 + 1 + it64;
     W = Wd;
     vsq = vd;
     return ok;
@@ -274,28 +325,34 @@ struct C2PWork {
     int its;          // Newton iterations of every energy attempt
 };
 
-// start32 (mixed form, optional): the start (W, v^2) already formed in FP32 from the guess primitives
+// start32 (mixed form, optional): the start (W, v^2) already formed in FP32 from the guess primitives;
+// igam, gfac (optional, > 0): 1/gam and (gam - 1)/gam formed once by the caller (else here, per state)
 __device__ __forceinline__ void c2p_prepare(const double U[NCONS], const double Bc[3], const Metric<double>& m,
                                             double gam, const double pr[NPRIM], C2PWork& w,
                                             int method = HAMR_INV_NEWTON, int mixed = 0,
-                                            const float* start32 = nullptr) {
+                                            const float* start32 = nullptr, double igam = 0.0, double gfac = 0.0) {
     c2p_scalars(U, Bc, m, w.S);
-    w.igam = 1.0 / gam;
-    w.gfac = (gam - 1.0) * w.igam;
+    if (igam > 0.0) {
+        w.igam = igam;
+        w.gfac = gfac;
+    } else {
+        w.igam = 1.0 / gam;
+        w.gfac = (gam - 1.0) * w.igam;
+    }
     w.method = method;
     w.mixed = mixed;
-    w.p0 = (gam - 1.0) * pr[UU];
+    w.p0 = (method == HAMR_INV_AITKEN) ? (gam - 1.0) * pr[UU] : 0.0;
     if (mixed && start32) {
-        w.W0 = (double)start32[0];
-        w.vsq0 = (double)fminf(start32[1], (float)C2P_VSQMAX);
+        w.W0 = widen(start32[0]);
+        w.vsq0 = widen(fminf(start32[1], (float)C2P_VSQMAX));
     } else if (mixed) {
         // the start only seeds the FP32 iterations (and, where they fail, the FP64 ones): in FP32
-        const float q1 = (float)pr[U1], q2 = (float)pr[U2], q3 = (float)pr[U3];
-        const float qsq = (float)m.g11 * q1 * q1 + (float)m.g22 * q2 * q2 + (float)m.g33 * q3 * q3 +
-                          2.0f * (float)m.g13 * q1 * q3;
+        const float q1 = narrow(pr[U1]), q2 = narrow(pr[U2]), q3 = narrow(pr[U3]);
+        const float qsq = narrow(m.g11) * q1 * q1 + narrow(m.g22) * q2 * q2 + narrow(m.g33) * q3 * q3 +
+                          2.0f * narrow(m.g13) * q1 * q3;
         const float gsq = 1.0f + qsq;
-        w.W0 = (double)(((float)pr[RHO] + (float)gam * (float)pr[UU]) * gsq);
-        w.vsq0 = (double)fminf(qsq / gsq, (float)C2P_VSQMAX);
+        w.W0 = widen((narrow(pr[RHO]) + narrow(gam) * narrow(pr[UU])) * gsq);
+        w.vsq0 = widen(fminf(qsq / gsq, (float)C2P_VSQMAX));
     } else {
         const double q1 = pr[U1], q2 = pr[U2], q3 = pr[U3];
         const double qsq = m.g11 * q1 * q1 + m.g22 * q2 * q2 + m.g33 * q3 * q3 + 2.0 * m.g13 * q1 * q3;

@@ -15,6 +15,8 @@
 
 #include <type_traits>
 
+#include "cvt.cuh"
+
 namespace hamr {
 
 constexpr int NG = 3;

@@ -49,6 +49,7 @@ struct BlockView {
 
 struct PhysArgs {
     double gam;
+    double igam, gfac;  // 1/gam and (gam - 1)/gam, formed once on the host
     double cour;
     int recon;
     int riemann;
@@ -238,6 +239,9 @@ cudaError_t launch_dt_select(const PhysArgs& ph, double user_dt, double* dscal, 
 
 // probe.cu
 cudaError_t measure_fp64_peak(cudaStream_t s, double* gflops);
+// probe.cu: the integer-pipe conversions (cvt.cuh) against the hardware ones: out = {widening
+// mismatches, first mismatching binary32 pattern or ~0, narrowing mismatches, first binary64 pattern or ~0}
+cudaError_t check_conversions(unsigned long long nrand, unsigned long long seed, unsigned long long out[4]);
 
 // step.cu, batched over the blocks list[0..nlist) of a table (sigma: 0 predictor, 1 corrector)
 cudaError_t launch_to_f32_batch(const DevBlock* tab, const int* list, int nlist, long maxwork, int sigma,

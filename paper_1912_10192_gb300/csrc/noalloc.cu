@@ -143,6 +143,8 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
 
     PhysArgs ph;
     ph.gam = d->gam;
+    ph.igam = 1.0 / d->gam;
+    ph.gfac = (d->gam - 1.0) * ph.igam;
     ph.cour = d->cour;
     ph.recon = d->recon;
     ph.riemann = d->riemann;

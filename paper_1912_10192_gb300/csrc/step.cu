@@ -737,7 +737,7 @@ __device__ __forceinline__ double inv_dt_fluid(const BlockView& v, const T pr[NP
     const T dn = pr[RHO] + pr[UU] + p - gp;
     const T ut = s.ucon[0];
     const T A = ut * ut * dn - num * m.c00;
-    const T idx[3] = {(T)v.idx1, (T)v.idx2, (T)v.idx3};
+    const T idx[3] = {to_t<T>(v.idx1), to_t<T>(v.idx2), to_t<T>(v.idx3)};
     T nsum = T(0);
 #pragma unroll
     for (int d = 1; d <= 3; d++) {
@@ -746,7 +746,7 @@ __device__ __forceinline__ double inv_dt_fluid(const BlockView& v, const T pr[NP
         const T C = ud * ud * dn - num * gcondd(m, d);
         nsum += (fabs(B) + root_pos(B * B - A * C)) * idx[d - 1];
     }
-    return (double)(nsum / fabs(A));
+    return to_d(nsum / fabs(A));
 }
 
 template <typename T>
@@ -757,21 +757,6 @@ __device__ __forceinline__ double inv_dt_cell(const BlockView& v, const T pr[NPR
 }
 
 // the rate of a cell in precision T from its (FP64) primitives
-template <typename T>
-__device__ __forceinline__ double inv_dt_at(const BlockView& v, const double pr[NPRIM], const Metric<double>& m,
-                                            long g, double gam) {
-    if constexpr (std::is_same<T, double>::value) {
-        return inv_dt_cell(v, pr, m, gam);
-    } else {
-        Metric<float> mf;
-        load_metric(v.gc32, v.n2d, g, mf);
-        float pf[NPRIM];
-#pragma unroll
-        for (int q = 0; q < NPRIM; q++) pf[q] = (float)pr[q];
-        return inv_dt_cell(v, pf, mf, (float)gam);
-    }
-}
-
 // source sqrt(-g) T^k_l Gamma^l_{nu k} at a cell centre in precision T
 // (tables gc: metric and connection planes of that precision)
 template <typename T, typename TT>
@@ -794,7 +779,7 @@ __device__ __forceinline__ void source_q_state(const TT* __restrict__ gc, long n
         for (int l = 0; l < 4; l++)
 #pragma unroll
             for (int kk = 0; kk < 4; kk++) acc += Tm[kk][l] * (T)cn[(l * 10 + sym(nu, kk)) * n2d];
-        Q[nu] = (double)(acc * m.gdet);
+        Q[nu] = to_d(acc * m.gdet);
     }
 }
 
@@ -834,10 +819,10 @@ __device__ __forceinline__ void source_q(const TT* __restrict__ gc, long n2d, lo
                                         const double pfd[NPRIM], double gam_d, double Q[4]) {
     T pf[NPRIM];
 #pragma unroll
-    for (int q = 0; q < NPRIM; q++) pf[q] = (T)pfd[q];
+    for (int q = 0; q < NPRIM; q++) pf[q] = to_t<T>(pfd[q]);
     Fluid<T> s;
     fluid_state(pf, m, s);
-    source_q_state(gc, n2d, g, m, pf, s, (T)gam_d, Q);
+    source_q_state(gc, n2d, g, m, pf, s, to_t<T>(gam_d), Q);
 }
 
 // ---------------------------------------------------------------- cell update
@@ -1021,11 +1006,11 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
             for (int q = 0; q < NPRIM; q++) p32[q] = v.P32[q * nc + c];
             Fluid<float> s32;
             fluid_state(p32, mf, s32);
-            source_q_state(v.gc32, v.n2d, g, mf, p32, s32, (float)gam, Q);
+            source_q_state(v.gc32, v.n2d, g, mf, p32, s32, narrow(gam), Q);
             // the inversion's start from the same state (it only seeds the FP32 iterations)
             const float qsq = p32[U1] * s32.ucov[1] + p32[U2] * s32.ucov[2] + p32[U3] * s32.ucov[3];
             const float gsq = 1.0f + qsq;
-            start32[0] = (p32[RHO] + (float)gam * p32[UU]) * gsq;
+            start32[0] = (p32[RHO] + narrow(gam) * p32[UU]) * gsq;
             start32[1] = qsq / gsq;
             have32 = true;
         }
@@ -1055,7 +1040,7 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
     C2PWork w;
     if (active)
         c2p_prepare(U, Bc, m, gam, pr, w, ph.inversion, (std::is_same<TS, float>::value && !ph.fp64_inv) ? 1 : 0,
-                    have32 ? start32 : nullptr);
+                    have32 ? start32 : nullptr, ph.igam, ph.gfac);
     if (MLP) {
         // first: the network's start, then the plain one; rescue: the plain start, then the
         // network's where it failed (the CTA runs the network only if one of its cells failed)
@@ -1104,21 +1089,21 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
             load_metric(v.gc32, v.n2d, g, mf);
             TS pf32[NPRIM];
 #pragma unroll
-            for (int q = 0; q < NPRIM; q++) pf32[q] = (TS)pr[q];
+            for (int q = 0; q < NPRIM; q++) pf32[q] = to_t<TS>(pr[q]);
             Fluid<TS> s32;
             fluid_state(pf32, mf, s32);
             if (ph.floors) {
-                fl = cell_floors_b2(v, g, m, ph, pr, (double)s32.bsq);
+                fl = cell_floors_b2(v, g, m, ph, pr, to_d(s32.bsq));
                 if (fl) {
                     sb |= ST_FLOOR;
 #pragma unroll
-                    for (int q = 0; q < NPRIM; q++) pf32[q] = (TS)pr[q];
+                    for (int q = 0; q < NPRIM; q++) pf32[q] = to_t<TS>(pr[q]);
                     if (ph.floor_frame == HAMR_FLOOR_DRIFT && corrector == 1) fluid_state(pf32, mf, s32);
                 }
             }
 #pragma unroll
             for (int q = 0; q < NPRIM; q++) Po[q * v.nc + c] = pr[q];
-            if (corrector == 1) inv = inv_dt_fluid(v, pf32, s32, mf, (TS)gam);
+            if (corrector == 1) inv = inv_dt_fluid(v, pf32, s32, mf, to_t<TS>(gam));
         }
         status[c] |= sb;
     }

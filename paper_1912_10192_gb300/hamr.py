@@ -22,7 +22,7 @@ FLUX_HLL, FLUX_LLF = 0, 1
 BC_OUTFLOW, BC_PERIODIC, BC_POLAR, BC_OUTFLOW_NOINFLOW, BC_BLOCK = 0, 1, 2, 3, 4
 PREC_FP64, PREC_MIXED, PREC_MIXED_FP64INV = 0, 1, 2
 EMF_AVERAGE, EMF_UPWIND = 0, 1
-C2P_ENTROPY_ONLY, C2P_MLP, C2P_MLP_RESCUE, C2P_AITKEN = 1, 2, 4, 8
+C2P_ENTROPY_ONLY, C2P_MLP, C2P_MLP_RESCUE, C2P_AITKEN, C2P_MIXED = 1, 2, 4, 8, 16
 INV_NEWTON, INV_AITKEN = 0, 1
 FLOOR_FLUID, FLOOR_DRIFT = 0, 1
 MLP_FIRST, MLP_RESCUE = 0, 1
@@ -125,6 +125,7 @@ def lib():
                                             C.POINTER(C.c_int)]
         L.hamr_grid_timing.argtypes = [P, C.POINTER(KernelTime), C.c_int, C.POINTER(C.c_int)]
         L.hamr_measure_fp64_peak.argtypes = [P, C.POINTER(C.c_double)]
+        L.hamr_check_conversions.argtypes = [C.c_longlong, C.c_ulonglong, C.POINTER(C.c_longlong)]
         L.hamr_block_step_noalloc.argtypes = [C.POINTER(GridDesc), P, P, C.c_double, P]
         L.hamr_prim2cons.argtypes = [C.POINTER(C2PDesc), C.c_int64, P, P, P, P, P]
         L.hamr_mlp_create.argtypes = [C.POINTER(C.c_void_p), C.c_uint64]
@@ -443,6 +444,14 @@ def measure_fp64_peak(stream=None):
     g = C.c_double()
     check(lib().hamr_measure_fp64_peak(_stream(stream), C.byref(g)))
     return g.value
+
+
+def check_conversions(nrandom=1 << 24, seed=10192):
+    """The integer-pipe binary32 <-> binary64 conversions against the hardware's:
+    (widening mismatches, first bad binary32 pattern, narrowing mismatches, first bad binary64 pattern)."""
+    out = (C.c_longlong * 4)()
+    check(lib().hamr_check_conversions(int(nrandom), int(seed), out))
+    return tuple(out)
 
 
 def block_step_noalloc(grid, prim, bface, dt=-1.0, stream=None):

@@ -3,7 +3,8 @@ alternative to the 2-D Newton, after Newman & Hamlin 2014) against the
 oracle: standalone inversions of random states from a warm and a cold start,
 the torus block and a refined tree at the FP64 bars; and the comparison the
 variant exists for (failures and iterations against Newton from the same
-starts)."""
+starts). Also the mixed-precision form of Newton (FP32 iterations, one FP64
+refinement step) against the oracle's FP64 Newton on random states."""
 import numpy as np
 import pytest
 
@@ -87,6 +88,49 @@ def test_aitken_parity_random_states(start):
     assert np.median(rel) < 1e-14 and np.quantile(rel, 0.99) < 1e-11, (np.median(rel), np.quantile(rel, 0.99))
     # the same iteration: map evaluations agree (a cycle more or less where the stopping test is at rounding)
     assert (ig == io).mean() > 0.99 and np.abs(ig - io).max() <= 3
+
+
+def test_mixed_newton_random_states():
+    """The inversion of the mixed-precision cell update (Newton in FP32, then one refinement step with
+    the FP64 residuals and the FP32 Jacobian, FP64 Newton where that step is not accepted) on 1M
+    states of the wide law from a 5% start: the same outcomes as the oracle's FP64 Newton, results
+    within the conditioning bar of both residuals, and a backward error at the FP64 Newton
+    tolerance's level (the refinement stops an error of ~1e-7 W at ~1e-14 W for a well-conditioned
+    Jacobian; an ill-conditioned one is sent on to FP64 Newton)."""
+    from paper_1912_10192_gb300 import hamr
+    d = O.make_desc(1, 1, 1, 0, 0, 0, 1, 1, 1, metric=O.METRIC_KS, a=0.9375, gam=GAM)
+    n = 1_000_000
+    prim, x1, x2 = W.random_states(n, seed=31)
+    U = O.p2u_many(d, prim, x1, x2)
+    guess = prim.copy()
+    guess[:, 0] *= 1.05
+    guess[:, 1] *= 0.95
+    guess[:, 2:5] *= 1.02
+    po, so, io = O.c2p_many(d, U, prim[:, 5:8], x1, x2, guess)
+    pg, sg, ig, ms = gpu_invert(U, prim[:, 5:8], x1, x2, guess, hamr.C2P_MIXED, timed=True)
+    pn, sn, inn, msn = gpu_invert(U, prim[:, 5:8], x1, x2, guess, 0, timed=True)
+    print("mixed Newton: %.2f ms per 1M (FP64 Newton %.2f), iterations %.2f (FP64 %.2f)"
+          % (ms, msn, ig[sg == 0].mean(), inn[sn == 0].mean()))
+    assert (sg == so).mean() > 0.9999
+    ok = (so == 0) & (sg == 0) & (sn == 0)
+    assert ok.mean() > 0.999
+
+    def backward(p):  # relative residual |U(p) - U| of each accepted state
+        p8 = p[ok].copy()
+        p8[:, 5:8] = prim[ok, 5:8]
+        return np.abs(O.p2u_many(d, p8, x1[ok], x2[ok])[:, :5] - U[ok, :5]).sum(axis=1) / np.abs(U[ok, :5]).sum(axis=1)
+
+    be, ben = backward(pg), backward(pn)
+    print("backward error: mixed median %.1e p99 %.1e max %.1e; FP64 Newton median %.1e p99 %.1e max %.1e"
+          % (np.median(be), np.quantile(be, 0.99), be.max(), np.median(ben), np.quantile(ben, 0.99), ben.max()))
+    # the tail at the FP64 iteration's level (its tolerance on W, 1e-10, sets both; measured p99 3.4e-11,
+    # max 4e-10 for both); the bulk at the refinement's level: the FP32 root's error (~1e-7) times the
+    # FP32 Jacobian's relative error and its cancellation (measured median 1.7e-13 against 2.4e-14
+    # after the FP64 Newton's last quadratic step)
+    assert np.median(be) <= 1e-12
+    assert np.quantile(be, 0.99) <= 2.0 * np.quantile(ben, 0.99) + 1e-15 and be.max() <= 2.0 * ben.max() + 1e-15
+    bar = inversion_bar(d, U[ok], prim[ok, 5:8], x1[ok], x2[ok], po[ok], prim[ok], p_other=pg[ok])
+    assert np.all(np.abs(pg[ok, :5] - po[ok, :5]) <= bar)
 
 
 def test_aitken_against_newton_from_the_same_starts():
