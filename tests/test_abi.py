@@ -44,7 +44,7 @@ def test_invalid_descriptors_rejected_without_gpu_work(libpath):
     arr[0].n3 = 7
     assert L.hamr_grid_create(ctypes.byref(d), ctypes.byref(h)) == hamr.EINVAL
     d2 = hamr.C2PDesc()
-    d2.metric, d2.a, d2.gam, d2.flags = 0, 0.5, 13 / 9, 0x10
+    d2.metric, d2.a, d2.gam, d2.flags = 0, 0.5, 13 / 9, 0x20
     assert L.hamr_con2prim(ctypes.byref(d2), 5, 1, 1, 1, 1, 1, 1, None, None) == hamr.EINVAL
     assert L.hamr_con2prim(ctypes.byref(d2), 0, None, None, None, None, None, None, None, None) == hamr.OK
 
