@@ -133,6 +133,8 @@ struct hamr_grid {
     PhysArgs ph;
     int device;
     double fine_dt = 0.0;  // hamr_grid_set_fine_dt (<= 0: CFL)
+    bool stage32_valid = false;  // ph.stage32: the FP32 copy, its kappa and the U^n kappa are the state's
+    bool ghosts_valid = false;   // single block: the ghost cells and faces of P, B are the boundary conditions'
 };
 
 // The descriptor checks of hamr_grid_create, also run by hamr_block_step_noalloc.
@@ -426,6 +428,16 @@ int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out) {
         return fail(HAMR_ECUDA, "geometry build failed: %s", cudaGetErrorString(e));
     }
     if (d->smr > 0) g->ph.smr_u = g->st[0].QR;  // free once the fluxes are formed
+    g->ph.stage32 = 0;
+    g->ph.p32w = nullptr;
+    g->ph.k32 = nullptr;
+    g->ph.un = nullptr;
+    if (d->nblocks == 1 && g->ph.mixed) {  // the update and the boundary kernels keep the FP32 stage copy
+        g->ph.stage32 = 1;
+        g->ph.p32w = g->st[0].P32;
+        g->ph.k32 = reinterpret_cast<float*>(g->st[0].E);
+        g->ph.un = g->st[0].Un;
+    }
     if (d->nblocks > 1) {
         rc = amr_create(&g->amr, g->desc, g->view, g->st, g->ph);
         if (rc) {
@@ -460,6 +472,8 @@ int hamr_grid_set_state(hamr_grid* g, int block, const double* prim, const doubl
     cudaStream_t cs = S(stream);
     CUDA_TRY(cudaMemsetAsync(s.dmax, 0, sizeof(unsigned long long), cs));
     LAUNCH(g, K_LOAD, g->amr ? 2 : 6, cs, load_kernels(v, g->ph, s, g->amr == nullptr, cs));
+    g->stage32_valid = false;
+    g->ghosts_valid = (g->amr == nullptr);  // the load applied the boundary conditions
     if (g->amr) {
         rc = amr_after_load(g->amr, block, cs);
         if (rc) return rc;
@@ -498,10 +512,18 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
     const PhysArgs& ph = g->ph;
     cudaStream_t cs = S(stream);
     LAUNCH(g, K_DT, 1, cs, launch_dt_select(ph, dt, s.dscal, s.dmax, s.dcnt, s.status, v.nc, cs));
-    // predictor: P^n, B^n -> P^{n+1/2}, B^{n+1/2}
-    LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.P, s.B, cs));
-    if (ph.mixed) LAUNCH(g, K_BC, 1, cs, launch_to_f32(v, s.P, s.P32, cs));
-    LAUNCH(g, K_RECON, 1, cs, launch_kappa(v, ph, s.P, s.P32, s.E, s.Un, cs));
+    // mixed precision: the boundary kernels copy the ghosts of the FP32 stage copy and its kappa, whose
+    // interior the cell update wrote; a separate pass forms them where no update did (after loading)
+    float* P32g = ph.stage32 ? s.P32 : nullptr;
+    float* K32g = ph.stage32 ? reinterpret_cast<float*>(s.E) : nullptr;
+    const bool fused = ph.stage32 && g->stage32_valid;
+    // predictor: P^n, B^n -> P^{n+1/2}, B^{n+1/2} (the ghosts of P^n are current after a load or a step,
+    // which end with the boundary conditions)
+    if (!g->ghosts_valid) LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.P, s.B, cs, P32g, K32g));
+    g->ghosts_valid = false;  // until this step has ended (an error on the way leaves them unknown)
+    g->stage32_valid = false;
+    if (ph.mixed && !fused) LAUNCH(g, K_BC, 1, cs, launch_to_f32(v, s.P, s.P32, cs));
+    if (!fused) LAUNCH(g, K_RECON, 1, cs, launch_kappa(v, ph, s.P, s.P32, s.E, s.Un, cs));
     for (int dir = 1; dir <= 3; dir++) {
         if (ph.flatten) LAUNCH(g, K_RECON, 1, cs, launch_flatten(v, ph, dir, s.P, s.P32, s.F[dir - 1], cs));
         LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.P, s.P32, s.E, s.F[dir - 1], s.QL, s.QR, cs));
@@ -515,9 +537,9 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
     if (ph.smr)
         LAUNCH(g, K_UPDATE, 1, cs, launch_smr_cells(v, ph, 0, s.P, s.Bh, s.Ph, s.status, s.dmax, s.dcnt, cs));
     // corrector: U^n and the fluxes of P^{n+1/2} -> P^{n+1}, B^{n+1} (in place)
-    LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.Ph, s.Bh, cs));
-    if (ph.mixed) LAUNCH(g, K_BC, 1, cs, launch_to_f32(v, s.Ph, s.P32, cs));
-    LAUNCH(g, K_RECON, 1, cs, launch_kappa(v, ph, s.Ph, s.P32, s.E, nullptr, cs));
+    LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.Ph, s.Bh, cs, P32g, K32g));
+    if (ph.mixed && !ph.stage32) LAUNCH(g, K_BC, 1, cs, launch_to_f32(v, s.Ph, s.P32, cs));
+    if (!ph.stage32) LAUNCH(g, K_RECON, 1, cs, launch_kappa(v, ph, s.Ph, s.P32, s.E, nullptr, cs));
     for (int dir = 1; dir <= 3; dir++) {
         if (ph.flatten) LAUNCH(g, K_RECON, 1, cs, launch_flatten(v, ph, dir, s.Ph, s.P32, s.F[dir - 1], cs));
         LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.Ph, s.P32, s.E, s.F[dir - 1], s.QL, s.QR, cs));
@@ -530,7 +552,9 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
            launch_update(v, ph, 1, s.P, s.Ph, s.F, s.B, s.Un, s.P, s.status, s.dscal, 1.0, s.dmax, s.dcnt, cs));
     if (ph.smr)
         LAUNCH(g, K_UPDATE, 1, cs, launch_smr_cells(v, ph, 1, s.Ph, s.B, s.P, s.status, s.dmax, s.dcnt, cs));
-    LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.P, s.B, cs));
+    LAUNCH(g, K_BC, 4, cs, launch_bc(v, s.P, s.B, cs, P32g, K32g));
+    g->stage32_valid = ph.stage32 != 0;
+    g->ghosts_valid = true;
     if (stats) {
         CUDA_TRY(cudaStreamSynchronize(cs));
         return hamr_grid_stats(g, stats);
@@ -858,6 +882,7 @@ int time_group_block(hamr_grid* g, const PhysArgs& ph, int which, cudaStream_t c
 // best of three timed repetitions after one warm-up
 int time_group(hamr_grid* g, const PhysArgs& ph, int which, cudaStream_t cs, float* best) {
     *best = 1e30f;
+    g->stage32_valid = false;  // the timed kernels overwrite the FP32 stage copy and the U^n cache
     for (int r = 0; r < 4; r++) {
         float t = 0.0f;
         int rc = g->amr ? amr_time_group(g->amr, ph, which, cs, &t) : time_group_block(g, ph, which, cs, &t);

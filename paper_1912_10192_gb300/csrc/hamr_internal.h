@@ -67,6 +67,14 @@ struct PhysArgs {
     int flatten;  // 1: PPM shock flattening (only set with HAMR_RECON_PPM)
     int inversion;  // HAMR_INV_*
     int floor_frame;  // HAMR_FLOOR_*
+    // mixed precision on a single block: the cell update and the boundary kernels keep the next
+    // stage's FP32 copy of the primitives (p32w), its entropy tracer kappa (k32, in the EMF array's
+    // first field, free from the face update to the next EMFs) and, in the corrector, the next step's
+    // U^n kappa, so that no separate pass forms them (0: the separate passes)
+    int stage32;
+    float* p32w;
+    float* k32;
+    double* un;       // the U^n cache (its entropy slot takes the next step's kappa)
     int smr;          // internal SMR levels next to polar faces (0: off)
     double* smr_u;    // scratch of the deferred conserved states (6 fields, stride nc) when smr > 0
 };
@@ -192,7 +200,8 @@ bool smr_factors(const hamr_grid_desc& d, const hamr_block_desc& B, int* l2, int
 cudaError_t launch_centre_b(const BlockView& v, double* P, const double* B, cudaStream_t s);
 // atomicMax of ordered_bits(P[q]) over the interior cells into *out (initialise to 0)
 cudaError_t launch_block_max(const BlockView& v, const double* P, int q, unsigned long long* out, cudaStream_t s);
-cudaError_t launch_bc(const BlockView& v, double* P, double* B, cudaStream_t s);
+cudaError_t launch_bc(const BlockView& v, double* P, double* B, cudaStream_t s, float* P32 = nullptr,
+                      float* K32 = nullptr);
 // entropy tracer kappa = p / rho^gam of every padded cell into K (FP32 view of K when mixed)
 // Un: the U^n cache (predictor) or nullptr (corrector); the predictor stores kappa in its entropy slot
 cudaError_t launch_kappa(const BlockView& v, const PhysArgs& ph, const double* P, const float* P32, double* K,

@@ -71,7 +71,10 @@ __device__ __forceinline__ int face_src(int bc, int n, int g) {
     return g < 0 ? 0 : n;
 }
 
-__global__ void k_bc_pass(BlockView v, double* __restrict__ P, double* __restrict__ B, int e) {
+// P32, K32 (mixed precision on a single block, else null): the ghost cells of the FP32 copy of the
+// primitives and of its entropy tracer kappa, from the same sources
+__global__ void k_bc_pass(BlockView v, double* __restrict__ P, double* __restrict__ B, int e, float* __restrict__ P32,
+                          float* __restrict__ K32) {
     const int nn[4] = {0, v.n1, v.n2, v.n3};
     const int ta = (e == 1) ? 2 : 1, tb = (e == 3) ? 2 : 3;
     const int na = nn[ta] + 2 * NG, nb = nn[tb] + 2 * NG;
@@ -103,7 +106,9 @@ __global__ void k_bc_pass(BlockView v, double* __restrict__ P, double* __restric
             if (side == 0 && x > 0.0) x = 0.0;
         }
         P[q * v.nc + dst] = x;
+        if (P32) P32[q * v.nc + dst] = (float)x;
     }
+    if (K32) K32[dst] = K32[src];  // kappa depends on rho and u only, which the map keeps
 #pragma unroll
     for (int f = 1; f <= 3; f++)
         if (f != e) B[(f - 1) * v.nc + dst] = B[(f - 1) * v.nc + src];
@@ -923,6 +928,19 @@ __device__ __forceinline__ int cell_floors_b2(const BlockView& v, long g, const 
     return 1;
 }
 
+// the next stage's FP32 copy of cell c (p: the returned primitives rounded to FP32) and its entropy
+// tracer kappa = (gam - 1) u / rho^gam formed as the kappa pass forms it; in the corrector also the
+// next step's U^n kappa (the entropy slot of the U^n cache, which the predictor reads)
+__device__ __forceinline__ void store_stage32(const BlockView& v, const PhysArgs& ph, int corrector, long c,
+                                              const float p[NPRIM]) {
+#pragma unroll
+    for (int q = 0; q < NPRIM; q++) ph.p32w[q * v.nc + c] = p[q];
+    const float g32 = narrow(ph.gam);
+    const float kap = (g32 - 1.0f) * p[UU] * pow_pos(p[RHO], -g32);
+    ph.k32[c] = kap;
+    if (corrector == 1) ph.un[(long)C_ENT * v.nc + c] = widen(kap);
+}
+
 template <bool MLP, typename TS>
 __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int corrector, const double* Pb,
                                                const double* __restrict__ Pf, const double* __restrict__ F1,
@@ -1104,6 +1122,7 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
 #pragma unroll
             for (int q = 0; q < NPRIM; q++) Po[q * v.nc + c] = pr[q];
             if (corrector == 1) inv = inv_dt_fluid(v, pf32, s32, mf, to_t<TS>(gam));
+            if (ph.stage32) store_stage32(v, ph, corrector, c, pf32);
         }
         status[c] |= sb;
     }
@@ -1548,6 +1567,13 @@ __device__ __forceinline__ void b_smr_cells(const BlockView& v, const PhysArgs& 
         for (int q = 0; q < 5; q++) Po[q * v.nc + c] = pr[q];
         for (int e = 0; e < 3; e++) Po[(B1 + e) * v.nc + c] = b[e];
         status[c] |= sb;
+        if (ph.stage32) {
+            float p8[NPRIM];
+#pragma unroll
+            for (int q = 0; q < 5; q++) p8[q] = narrow(pr[q]);
+            for (int e = 0; e < 3; e++) p8[B1 + e] = narrow(b[e]);
+            store_stage32(v, ph, corrector, c, p8);
+        }
     }
     atomicAdd(&dcnt[st == INV_OK ? 0 : (st == INV_ENTROPY ? 1 : 2)], (unsigned long long)w);
     if (fl) atomicAdd(&dcnt[3], (unsigned long long)w);
@@ -1656,12 +1682,12 @@ cudaError_t launch_centre_b(const BlockView& v, double* P, const double* B, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_bc(const BlockView& v, double* P, double* B, cudaStream_t s) {
+cudaError_t launch_bc(const BlockView& v, double* P, double* B, cudaStream_t s, float* P32, float* K32) {
     const int nn[4] = {0, v.n1, v.n2, v.n3};
     for (int e = 3; e >= 1; e--) {
         const int ta = (e == 1) ? 2 : 1, tb = (e == 3) ? 2 : 3;
         const long total = 2L * NG * (nn[ta] + 2 * NG) * (nn[tb] + 2 * NG);
-        k_bc_pass<<<nblk(total), BS, 0, s>>>(v, P, B, e);
+        k_bc_pass<<<nblk(total), BS, 0, s>>>(v, P, B, e, P32, K32);
         if (e == 2) k_bc_axis<<<nblk(2L * (v.n1 + 2 * NG) * (v.n3 + 2 * NG)), BS, 0, s>>>(v, B);
     }
     return cudaGetLastError();
