@@ -312,7 +312,8 @@ int hamr_measure_fp64_peak(void* stream, double* gflops);
  * value, and narrowing of every binary32 value's binary64 image, its binary64
  * neighbours, the midpoint to the next binary32 value and that midpoint's
  * neighbours, plus `nrandom` pseudo-random binary64 bit patterns (splitmix64
- * from `seed`), each compared bit for bit with the hardware conversion. No
+ * from `seed`), each compared bit for bit with the hardware conversion (a
+ * NaN only as a NaN: payloads are the implementation's). No
  * counterpart in the paper. out4 (host): {widening mismatches, the first
  * mismatching binary32 pattern or -1, narrowing mismatches, the first
  * mismatching binary64 pattern or -1}. Synchronises the device; about 0.1 s. */

@@ -267,7 +267,7 @@ int alloc_block(hamr_grid* g, int b) {
     const size_t tab = align256(sizeof(double) * (size_t)v.n2d);
     v.nc = (long)(fld / sizeof(double));   // stride between two fields
     v.n2d = (long)(tab / sizeof(double));  // stride between two table components
-    const int nfields = 8 + 3 + 8 + 3 + 8 + 8 + 24 + 3 + 6;
+    const int nfields = 8 + 3 + 8 + 3 + 8 + 8 + 27 + 3 + 6;
     const size_t stbytes = align256((size_t)v.nc);
     // mixed precision: the FP32 copy of the primitives and FP32 metric/connection tables
     const bool mixed = (g->desc.precision != HAMR_PREC_FP64);
@@ -296,7 +296,7 @@ int alloc_block(hamr_grid* g, int b) {
     s.Bh = (double*)take(3 * fld);
     s.QL = (double*)take(8 * fld);
     s.QR = (double*)take(8 * fld);
-    for (int d = 0; d < 3; d++) s.F[d] = (double*)take(8 * fld);
+    for (int d = 0; d < 3; d++) s.F[d] = (double*)take(9 * fld);  // 8 FP64 fields, 2 FP32 (mixed, one block)
     s.E = (double*)take(3 * fld);
     s.Un = (double*)take(6 * fld);
     s.status = (uint8_t*)take(stbytes);
@@ -429,11 +429,13 @@ int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out) {
     }
     if (d->smr > 0) g->ph.smr_u = g->st[0].QR;  // free once the fluxes are formed
     g->ph.stage32 = 0;
+    g->ph.flux32 = 0;
     g->ph.p32w = nullptr;
     g->ph.k32 = nullptr;
     g->ph.un = nullptr;
     if (d->nblocks == 1 && g->ph.mixed) {  // the update and the boundary kernels keep the FP32 stage copy
         g->ph.stage32 = 1;
+        g->ph.flux32 = 1;
         g->ph.p32w = g->st[0].P32;
         g->ph.k32 = reinterpret_cast<float*>(g->st[0].E);
         g->ph.un = g->st[0].Un;
@@ -529,7 +531,7 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
         LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.P, s.P32, s.E, s.F[dir - 1], s.QL, s.QR, cs));
         LAUNCH(g, K_FLUX, 1, cs, launch_flux(v, ph, dir, s.QL, s.QR, s.B, s.F[dir - 1], cs));
     }
-    LAUNCH(g, K_EMF, ph.emf ? 2 : 1, cs, launch_emf(v, s.F, s.E, ph.mixed, s.P, ph.emf ? s.QL : nullptr, cs));
+    LAUNCH(g, K_EMF, ph.emf ? 2 : 1, cs, launch_emf(v, s.F, s.E, ph.mixed ? ((ph.flux32 && !ph.emf) ? 2 : 1) : 0, s.P, ph.emf ? s.QL : nullptr, cs));
     if (ph.smr) LAUNCH(g, K_EMF, 1, cs, launch_smr_emf(v, ph, s.E, cs));
     LAUNCH(g, K_CT, 1, cs, launch_ct(v, s.E, s.B, s.Bh, s.dscal, 0.5, cs));
     LAUNCH(g, K_UPDATE, 1, cs,
@@ -545,7 +547,7 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
         LAUNCH(g, K_RECON, 1, cs, launch_recon(v, ph, dir, s.Ph, s.P32, s.E, s.F[dir - 1], s.QL, s.QR, cs));
         LAUNCH(g, K_FLUX, 1, cs, launch_flux(v, ph, dir, s.QL, s.QR, s.Bh, s.F[dir - 1], cs));
     }
-    LAUNCH(g, K_EMF, ph.emf ? 2 : 1, cs, launch_emf(v, s.F, s.E, ph.mixed, s.Ph, ph.emf ? s.QL : nullptr, cs));
+    LAUNCH(g, K_EMF, ph.emf ? 2 : 1, cs, launch_emf(v, s.F, s.E, ph.mixed ? ((ph.flux32 && !ph.emf) ? 2 : 1) : 0, s.Ph, ph.emf ? s.QL : nullptr, cs));
     if (ph.smr) LAUNCH(g, K_EMF, 1, cs, launch_smr_emf(v, ph, s.E, cs));
     LAUNCH(g, K_CT, 1, cs, launch_ct(v, s.E, s.B, s.B, s.dscal, 1.0, cs));
     LAUNCH(g, K_UPDATE, 1, cs,

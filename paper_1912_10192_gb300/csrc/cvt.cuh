@@ -10,9 +10,9 @@
 // widening, and narrowing that rounds to nearest with ties to even (IEEE 754
 // roundTiesToEven), both equal bit for bit to the hardware conversions
 // (checked over every binary32 value and the rounding neighbourhoods by
-// hamr_check_conversions). Values whose result is not a normal binary32
-// number (zero excepted), and infinities and NaNs, take the hardware
-// conversion, out of line. They cost about ten
+// hamr_check_conversions; NaNs stay NaNs). The narrowing of values whose
+// result is not a normal binary32 number (zero excepted), and of infinities
+// and NaNs, takes the hardware conversion, out of line. They cost about ten
 // integer instructions each, so kernels that are bound by issue or memory
 // rather than by the FP64 pipe (face fluxes, EMFs, the FP32 copy of the state)
 // keep the hardware conversions (measured: those kernels got slower, the cell
@@ -21,20 +21,36 @@
 
 namespace hamr {
 
-// the hardware conversions of the rare cases, kept out of line: a call is a real branch, where an
+// the hardware narrowing of the rare cases, kept out of line: a call is a real branch, where an
 // inlined conversion would be predicated and still issue to the FP64 pipe in every warp
-static __device__ __noinline__ double widen_hw(float x) { return (double)x; }
 static __device__ __noinline__ float narrow_hw(double x) { return __double2float_rn(x); }
 
-// binary32 -> binary64, exact: the exponent rebiased by 1023 - 127 = 896, the
-// 23 fraction bits moved to the top of the 52
+// binary32 -> binary64, exact, without branches or calls (the selects below are all integer): a
+// normal value's exponent rebiased by 1023 - 127 = 896 and its 23 fraction bits moved to the top of
+// the 52; a subnormal one normalised by its leading zeros (value a 2^-149 with the leading one at bit
+// 31 - lz: exponent 905 - lz); zero; infinity and NaN (all-ones exponent, the fraction kept, a NaN
+// made quiet)
 __device__ __forceinline__ double widen(float x) {
     const unsigned b = __float_as_uint(x);
     const unsigned a = b & 0x7fffffffu;
-    if (a - 0x00800000u < 0x7f000000u)  // normal: biased exponent 1..254
-        return __hiloint2double((int)((b & 0x80000000u) | ((a >> 3) + 0x38000000u)), (int)(b << 29));
-    if (a == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
-    return widen_hw(x);
+    const unsigned lz = __clz(a);
+    const unsigned ms = (a << ((lz - 8u) & 31u)) & 0x007fffffu;
+    unsigned hi, lo;
+    if (a - 0x00800000u < 0x7f000000u) {  // normal: biased exponent 1..254
+        hi = (a >> 3) + 0x38000000u;
+        lo = b << 29;
+    } else if (a == 0u) {
+        hi = 0u;
+        lo = 0u;
+    } else if (a < 0x00800000u) {  // subnormal
+        hi = ((905u - lz) << 20) | (ms >> 3);
+        lo = ms << 29;
+    } else {  // infinity, NaN
+        const unsigned f = a & 0x007fffffu;
+        hi = 0x7ff00000u | (f >> 3) | (f ? 0x00080000u : 0u);
+        lo = f << 29;
+    }
+    return __hiloint2double((int)((b & 0x80000000u) | hi), (int)lo);
 }
 
 // binary64 -> binary32, round to nearest, ties to even: the top 23 of the 52

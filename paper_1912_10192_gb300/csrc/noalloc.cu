@@ -142,6 +142,7 @@ extern "C" int hamr_block_step_noalloc(const hamr_grid_desc* d, double* prim, do
     v.gf2 = s.geom_f2;
 
     PhysArgs ph;
+    std::memset(&ph, 0, sizeof(ph));  // FP64 only: no FP32 stage copy, no FP32 fluxes
     ph.gam = d->gam;
     ph.igam = 1.0 / d->gam;
     ph.gfac = (d->gam - 1.0) * ph.igam;

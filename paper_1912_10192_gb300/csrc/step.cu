@@ -491,9 +491,12 @@ __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const T*
     const long st = (DIR == 1) ? 1 : ((DIR == 2) ? (long)v.n1p : (long)v.n1p * v.n2p);
     Metric<T> m;
     load_metric(face_table<DIR, T>(v), v.n2d, gidx(v, i, j), m);
+    // single-block mixed precision: the two field slots (6, 7) also in FP32, after the FP64 fields
+    float* F32 = (std::is_same<T, float>::value && ph.flux32) ? reinterpret_cast<float*>(F + NFLUX * v.nc) : nullptr;
     if (m.gdet == T(0)) {  // face on the polar axis: no area
 #pragma unroll
         for (int q = 0; q < NFLUX; q++) F[q * v.nc + c] = 0.0;
+        if (F32) F32[c] = F32[v.nc + c] = 0.0f;
         return;
     }
     T pl[NPRIM], pr[NPRIM];
@@ -572,6 +575,10 @@ __device__ __forceinline__ void b_flux(const BlockView& v, PhysArgs ph, const T*
     hll_side<DIR, false>(pr, sr, gam, kapr, wr, -wc, acc);
 #pragma unroll
     for (int q = 0; q < NFLUX; q++) F[q * v.nc + c] = (double)acc[q];
+    if (F32) {
+        F32[c] = (float)acc[6];
+        F32[v.nc + c] = (float)acc[7];
+    }
 }
 
 template <int DIR, typename T>
@@ -629,6 +636,18 @@ __device__ __forceinline__ T upwind_pick(T mass_flux, T lower, T upper) {
 // edge's cell c: sp, sq the index strides of p and q; Fp / Fq the flux arrays of the p / q
 // faces, slp / slq their B-flux slots with signs gp / gq (the EMF a face carries is g F[sl]);
 // ec the cell-EMF field of the component
+// field slot `slot` (6 or 7) of a face flux at cell offset i as T: the FP64 field converted, or (F32)
+// the FP32 copy of slots 6 and 7 kept after the FP64 fields
+template <typename T, bool F32>
+__device__ __forceinline__ T ld_bflux(const double* __restrict__ F, int slot, long nc, long i) {
+    if constexpr (F32) {
+        static_assert(std::is_same<T, float>::value, "the FP32 slot copy serves the FP32 EMFs");
+        return reinterpret_cast<const float*>(F + NFLUX * nc)[(slot - 6) * nc + i];
+    } else {
+        return (T)F[slot * nc + i];
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T gs_correction(long c, long sp, long sq, long nc, const double* __restrict__ Fp,
                                            const double* __restrict__ Fq, int slp, int slq, T gp, T gq,
@@ -645,7 +664,7 @@ __device__ __forceinline__ T gs_correction(long c, long sp, long sq, long nc, co
     return T(0.25) * (dq_lo - dq_hi) + T(0.25) * (dp_lo - dp_hi);
 }
 
-template <typename T>
+template <typename T, bool F32 = false>
 __device__ __forceinline__ void b_emf(const BlockView& v, const double* __restrict__ F1, const double* __restrict__ F2,
                       const double* __restrict__ F3, double* __restrict__ E, const double* __restrict__ Ec, long t) {
     const int e1 = v.n1 + 1, e2 = v.n2 + 1, e3 = v.n3 + 1;
@@ -657,29 +676,32 @@ __device__ __forceinline__ void b_emf(const BlockView& v, const double* __restri
     const T q = T(0.25);
     // flux slots: F1 -> (B2: 6, B3: 7), F2 -> (B1: 6, B3: 7), F3 -> (B1: 6, B2: 7)
     if (i < v.n1) {
-        T x = q * ((T)F3[7 * nc + c] + (T)F3[7 * nc + c - sj] - (T)F2[7 * nc + c - sk] - (T)F2[7 * nc + c]);
+        T x = q * (ld_bflux<T, F32>(F3, 7, nc, c) + ld_bflux<T, F32>(F3, 7, nc, c - sj) -
+                   ld_bflux<T, F32>(F2, 7, nc, c - sk) - ld_bflux<T, F32>(F2, 7, nc, c));
         // p = x2 faces (value -F2(B3)), q = x3 faces (value F3(B2))
         if (Ec) x += gs_correction<T>(c, sj, sk, nc, F2, F3, 7, 7, T(-1), T(1), Ec);
         E[c] = axis ? 0.0 : (double)x;
     }
     if (j < v.n2) {
-        T x = q * ((T)F1[7 * nc + c - sk] + (T)F1[7 * nc + c] - (T)F3[6 * nc + c] - (T)F3[6 * nc + c - si]);
+        T x = q * (ld_bflux<T, F32>(F1, 7, nc, c - sk) + ld_bflux<T, F32>(F1, 7, nc, c) -
+                   ld_bflux<T, F32>(F3, 6, nc, c) - ld_bflux<T, F32>(F3, 6, nc, c - si));
         // p = x1 faces (value F1(B3)), q = x3 faces (value -F3(B1))
         if (Ec) x += gs_correction<T>(c, si, sk, nc, F1, F3, 7, 6, T(1), T(-1), Ec + nc);
         E[nc + c] = (double)x;
     }
     if (k < v.n3) {
-        T x = q * ((T)F2[6 * nc + c - si] + (T)F2[6 * nc + c] - (T)F1[6 * nc + c] - (T)F1[6 * nc + c - sj]);
+        T x = q * (ld_bflux<T, F32>(F2, 6, nc, c - si) + ld_bflux<T, F32>(F2, 6, nc, c) -
+                   ld_bflux<T, F32>(F1, 6, nc, c) - ld_bflux<T, F32>(F1, 6, nc, c - sj));
         // p = x1 faces (value -F1(B2)), q = x2 faces (value F2(B1))
         if (Ec) x += gs_correction<T>(c, si, sj, nc, F1, F2, 6, 6, T(-1), T(1), Ec + 2 * nc);
         E[2 * nc + c] = axis ? 0.0 : (double)x;
     }
 }
 
-template <typename T>
+template <typename T, bool F32 = false>
 __global__ void k_emf(BlockView v, const double* __restrict__ F1, const double* __restrict__ F2,
                       const double* __restrict__ F3, double* __restrict__ E, const double* __restrict__ Ec) {
-    b_emf<T>(v, F1, F2, F3, E, Ec, (long)blockIdx.x * blockDim.x + threadIdx.x);
+    b_emf<T, F32>(v, F1, F2, F3, E, Ec, (long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 
@@ -1772,7 +1794,9 @@ cudaError_t launch_emf(const BlockView& v, double* const F[3], double* E, int mi
     if (Ec) {  // upwinded EMFs: the cell EMFs of the stage state P first
         k_cell_emf<<<nblk((long)(v.n1 + 2) * (v.n2 + 2) * (v.n3 + 2)), BS, 0, s>>>(v, P, Ec);
     }
-    if (mixed)
+    if (mixed == 2)  // FP32 EMFs of fluxes stored in FP32
+        k_emf<float, true><<<nblk(n), BS, 0, s>>>(v, F[0], F[1], F[2], E, Ec);
+    else if (mixed)
         k_emf<float><<<nblk(n), BS, 0, s>>>(v, F[0], F[1], F[2], E, Ec);
     else
         k_emf<double><<<nblk(n), BS, 0, s>>>(v, F[0], F[1], F[2], E, Ec);
