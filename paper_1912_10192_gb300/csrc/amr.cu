@@ -757,7 +757,9 @@ struct SyncDev {  // SoA: dst block, field/face direction, dst index, source blo
     const long *di, *si;
 };
 
-__global__ void k_flux_sync(const DevBlock* tab, SyncDev S, int beg, int end) {
+// flux32: the destination's FP32 copies of the field slots 6 and 7 (kept after its FP64 fields for
+// the FP32 EMFs) follow the synchronised values
+__global__ void k_flux_sync(const DevBlock* tab, SyncDev S, int beg, int end, int flux32) {
     const int e = beg + (int)((long)blockIdx.x * blockDim.x + threadIdx.x);
     if (e >= end) return;
     const DevBlock& D = tab[S.dst[e]];
@@ -771,6 +773,8 @@ __global__ void k_flux_sync(const DevBlock* tab, SyncDev S, int beg, int end) {
         double sum = 0.0;
         for (int m = 0; m < n; m++) sum += Fs[q * F.v.nc + S.si[4 * e + m]];
         Fd[q * D.v.nc + S.di[e]] = sum * inv;
+        if (flux32 && q >= 6)
+            reinterpret_cast<float*>(Fd + NFLUX * D.v.nc)[(q - 6) * D.v.nc + S.di[e]] = (float)(sum * inv);
     }
 }
 
@@ -1707,8 +1711,9 @@ int group_step(AmrImpl& M, int L, int s, cudaStream_t cs) {
             AM_TRY(launch_flux_batch(tab, list, nl, M.lmw_flux[L][dir], ph, dir, sigma, cs));
         }
         const int fb = M.fs_beg[L], fe = M.fs_end[L];
-        if (fe > fb) k_flux_sync<<<nb_(fe - fb), BSA, 0, cs>>>(tab, M.fs, fb, fe);
-        AM_TRY(launch_emf_batch(tab, list, nl, M.lmw_edge[L], ph.mixed, ph.emf, M.lmw_ext[L], sigma, cs));
+        if (fe > fb) k_flux_sync<<<nb_(fe - fb), BSA, 0, cs>>>(tab, M.fs, fb, fe, ph.flux32);
+        AM_TRY(launch_emf_batch(tab, list, nl, M.lmw_edge[L], ph.mixed ? (ph.flux32 ? 2 : 1) : 0, ph.emf,
+                                M.lmw_ext[L], sigma, cs));
         const int eb = M.es_beg[L], ee = M.es_end[L];
         if (ee > eb) {
             k_edge_gather<<<nb_(ee - eb), BSA, 0, cs>>>(tab, M.es, eb, ee, M.es_tmp);

@@ -429,13 +429,12 @@ int hamr_grid_create(const hamr_grid_desc* d, hamr_grid** out) {
     }
     if (d->smr > 0) g->ph.smr_u = g->st[0].QR;  // free once the fluxes are formed
     g->ph.stage32 = 0;
-    g->ph.flux32 = 0;
+    g->ph.flux32 = g->ph.mixed;  // FP32 copies of the flux field slots for the FP32 EMFs
     g->ph.p32w = nullptr;
     g->ph.k32 = nullptr;
     g->ph.un = nullptr;
     if (d->nblocks == 1 && g->ph.mixed) {  // the update and the boundary kernels keep the FP32 stage copy
         g->ph.stage32 = 1;
-        g->ph.flux32 = 1;
         g->ph.p32w = g->st[0].P32;
         g->ph.k32 = reinterpret_cast<float*>(g->st[0].E);
         g->ph.un = g->st[0].Un;

@@ -334,34 +334,27 @@ __device__ __forceinline__ bool nonpos_product(T a, T b) {
 // from the differences dl = q0 - qm, dr = qp - q0 and dlr = qp - qm
 template <typename T>
 __device__ __forceinline__ T mc_slope_d(T dl, T dr, T dlr) {
-    using B = FBits<T>;
-    using I = typename B::I;
     if constexpr (std::is_same<T, float>::value) {
         // FP32: the FP32 pipes take the comparisons and products in one instruction each (the
         // bit-pattern forms pay off only where they replace FP64-pipe work)
         const float mag = fminf(fabsf(0.5f * dlr), 2.0f * fminf(fabsf(dl), fabsf(dr)));
         return (dl * dr > 0.0f) ? copysignf(mag, dlr) : 0.0f;
     } else {
-    if (nonpos_product(dl, dr)) return T(0);
-    const I al = B::of(dl) & B::MAG, ar = B::of(dr) & B::MAG;
-    if constexpr (std::is_same<T, double>::value) {
-        // FP64: the halving and the doubling on the integer pipe as well, bit-identical to the
-        // FP64 products for finite values: |x|/2 is one exponent step down, or for |x| < 2^-1021
-        // (the magnitude bits below 2^53, subnormal result) the bits shifted right with the
-        // dropped bit rounded to even; 2|x| is one exponent step up, or for a subnormal x
-        // (bits below 2^52) the bits shifted left
+        // FP64: the sign test, the magnitude comparisons, the halving and the doubling on the
+        // integer pipe, bit-identical to the FP64 products for finite values: |x|/2 is one exponent
+        // step down, or for |x| < 2^-1021 (the magnitude bits below 2^53, subnormal result) the bits
+        // shifted right with the dropped bit rounded to even; 2|x| is one exponent step up, or for a
+        // subnormal x (bits below 2^52) the bits shifted left
+        using B = FBits<T>;
+        using I = typename B::I;
+        if (nonpos_product(dl, dr)) return T(0);
+        const I al = B::of(dl) & B::MAG, ar = B::of(dr) & B::MAG;
         const I bl = B::of(dlr);
         const I ml = bl & B::MAG;
         const I ac = (ml >= (I(1) << 53)) ? ml - (I(1) << 52) : (ml >> 1) + (ml & (ml >> 1) & 1);  // |dlr|/2
         const I mn = al < ar ? al : ar;
         const I alim = (mn < (I(1) << 52)) ? (mn << 1) : mn + (I(1) << 52);                       // 2 min
         return B::from((ac < alim ? ac : alim) | (bl & ~B::MAG));
-    } else {
-        const T dc = T(0.5) * dlr;
-        const T lim = T(2) * B::from(al < ar ? al : ar);  // 2 min(|dl|, |dr|)
-        const I ac = B::of(dc) & B::MAG, alim = B::of(lim);
-        return B::from((ac < alim ? ac : alim) | (B::of(dc) & ~B::MAG));  // min(|dc|, lim) with the sign of dc
-    }
     }
 }
 

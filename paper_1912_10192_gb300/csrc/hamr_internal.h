@@ -75,8 +75,8 @@ struct PhysArgs {
     float* p32w;
     float* k32;
     double* un;       // the U^n cache (its entropy slot takes the next step's kappa)
-    int flux32;       // mixed precision on a single block: the face fluxes' field slots (6, 7) also in
-                      // FP32, after the FP64 fields, for the FP32 EMFs
+    int flux32;       // mixed precision: the face fluxes' field slots (6, 7) also in FP32, after the FP64
+                      // fields, for the FP32 EMFs
     int smr;          // internal SMR levels next to polar faces (0: off)
     double* smr_u;    // scratch of the deferred conserved states (6 fields, stride nc) when smr > 0
 };

@@ -32,9 +32,10 @@ inline unsigned nblk(long n, int bs = BS) { return (unsigned)((n + bs - 1) / bs)
 __device__ __forceinline__ void centre_field(const BlockView& v, const double* __restrict__ B, int i, int j, int k,
                                              double ig, double Bc[3]) {  // ig = 1 / sqrt(-g)
     const long c = cidx(v, i, j, k);
-    Bc[0] = 0.5 * (B[c] + B[c + 1]) * ig;
-    Bc[1] = 0.5 * (B[v.nc + c] + B[v.nc + c + v.n1p]) * ig;
-    Bc[2] = 0.5 * (B[2 * v.nc + c] + B[2 * v.nc + c + (long)v.n1p * v.n2p]) * ig;
+    const double hig = 0.5 * ig;
+    Bc[0] = (B[c] + B[c + 1]) * hig;
+    Bc[1] = (B[v.nc + c] + B[v.nc + c + v.n1p]) * hig;
+    Bc[2] = (B[2 * v.nc + c] + B[2 * v.nc + c + (long)v.n1p * v.n2p]) * hig;
 }
 
 __device__ __forceinline__ void b_centre_b(const BlockView& v, double* __restrict__ P, const double* __restrict__ B, long t) {
@@ -963,6 +964,33 @@ __device__ __forceinline__ void store_stage32(const BlockView& v, const PhysArgs
     if (corrector == 1) ph.un[(long)C_ENT * v.nc + c] = widen(kap);
 }
 
+// The floors of the mixed form in FP32: b^2 of the FP32 fluid state (like the fluxes), thresholds,
+// comparisons and floor values in FP32 (pf: the returned primitives rounded to FP32, updated with
+// pr); drift-frame floors take the FP64 path of cell_floors_b2
+__device__ __forceinline__ int cell_floors_f32(const BlockView& v, long g, const Metric<double>& m, const PhysArgs& ph,
+                                               double pr[NPRIM], float pf[NPRIM], float bsq) {
+    if (ph.floor_frame == HAMR_FLOOR_DRIFT) {
+        const int fl = cell_floors_b2(v, g, m, ph, pr, widen(bsq));
+        if (fl)
+#pragma unroll
+            for (int q = 0; q < NPRIM; q++) pf[q] = narrow(pr[q]);
+        return fl;
+    }
+    const float rf = fmaxf(narrow(v.gc[C_RHOFLR * v.n2d + g]), bsq * (1.0f / 50.0f));
+    const float uf = fmaxf(narrow(v.gc[C_UFLR * v.n2d + g]), bsq * (1.0f / 750.0f));
+    const bool lr = pf[RHO] < rf, lu = pf[UU] < uf;
+    if (!lr && !lu) return 0;
+    if (lr) {
+        pf[RHO] = rf;
+        pr[RHO] = widen(rf);
+    }
+    if (lu) {
+        pf[UU] = uf;
+        pr[UU] = widen(uf);
+    }
+    return 1;
+}
+
 template <bool MLP, typename TS>
 __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int corrector, const double* Pb,
                                                const double* __restrict__ Pf, const double* __restrict__ F1,
@@ -1055,14 +1083,15 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
             have32 = true;
         }
         const double dts = dscal[0] * fac;
+        const double a1 = dts * v.idx1, a2 = dts * v.idx2, a3 = dts * v.idx3;  // dt / dx^i
         const long sj = v.n1p, sk = (long)v.n1p * v.n2p;
 #pragma unroll
         for (int q = 0; q < NCONS; q++) {
-            const double div = (F1[q * nc + c + 1] - F1[q * nc + c]) * v.idx1 +
-                               (F2[q * nc + c + sj] - F2[q * nc + c]) * v.idx2 +
-                               (F3[q * nc + c + sk] - F3[q * nc + c]) * v.idx3;
-            const double src = (q >= C_EN && q <= C_S3) ? Q[q - C_EN] : 0.0;
-            U[q] = U[q] + dts * (src - div);
+            // U + dt (Q - div F): the flux differences times dt/dx^i taken off one by one
+            double u = (q >= C_EN && q <= C_S3) ? fma(dts, Q[q - C_EN], U[q]) : U[q];
+            u = fma(-a1, F1[q * nc + c + 1] - F1[q * nc + c], u);
+            u = fma(-a2, F2[q * nc + c + sj] - F2[q * nc + c], u);
+            U[q] = fma(-a3, F3[q * nc + c + sk] - F3[q * nc + c], u);
         }
         centre_field(v, Bn, i, j, k, m.igdet, Bc);
 #pragma unroll
@@ -1133,11 +1162,9 @@ __device__ __forceinline__ void b_update(const BlockView& v, PhysArgs ph, int co
             Fluid<TS> s32;
             fluid_state(pf32, mf, s32);
             if (ph.floors) {
-                fl = cell_floors_b2(v, g, m, ph, pr, to_d(s32.bsq));
+                fl = cell_floors_f32(v, g, m, ph, pr, pf32, s32.bsq);
                 if (fl) {
                     sb |= ST_FLOOR;
-#pragma unroll
-                    for (int q = 0; q < NPRIM; q++) pf32[q] = to_t<TS>(pr[q]);
                     if (ph.floor_frame == HAMR_FLOOR_DRIFT && corrector == 1) fluid_state(pf32, mf, s32);
                 }
             }
@@ -1269,10 +1296,10 @@ __global__ void __launch_bounds__(256, 2) kb_flux(const DevBlock* tab, const int
                    tidx());
 }
 
-template <typename T>
+template <typename T, bool F32 = false>
 __global__ void kb_emf(const DevBlock* tab, const int* list, int upwind) {
     const DevBlock& D = tab[list[blockIdx.y]];
-    b_emf<T>(D.v, D.F1, D.F2, D.F3, D.E, upwind ? D.QL : nullptr, tidx());
+    b_emf<T, F32>(D.v, D.F1, D.F2, D.F3, D.E, upwind ? D.QL : nullptr, tidx());
 }
 
 // cell EMFs of the stage state into the edge-value scratch (free once the fluxes exist)
@@ -1919,7 +1946,9 @@ cudaError_t launch_emf_batch(const DevBlock* tab, const int* list, int nlist, lo
                              long maxcells, int sigma, cudaStream_t s) {
     if (nlist <= 0) return cudaSuccess;
     if (upwind) kb_cell_emf<<<bgrid(maxcells, nlist), BS, 0, s>>>(tab, list, sigma);
-    if (mixed)
+    if (mixed == 2 && !upwind)  // FP32 EMFs of the FP32 copies of the flux field slots
+        kb_emf<float, true><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, upwind);
+    else if (mixed)
         kb_emf<float><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, upwind);
     else
         kb_emf<double><<<bgrid(maxwork, nlist), BS, 0, s>>>(tab, list, upwind);
