@@ -183,8 +183,8 @@ int hamr_block_step(hamr_grid* g, int block, double dt, void* stream, hamr_step_
  * s mod 2^L = 0; levels run coarsest first; every kernel of a stage runs as
  * one batched launch over all due blocks of the level. Ghost zones come from
  * the neighbouring blocks (restriction, MINMOD prolongation, linear time
- * interpolation of a coarser-level neighbour, linear extrapolation of a
- * finer-level one at the coarse midpoint; Sec. 3.2, 3.4); same-level blocks
+ * interpolation of a coarser-level neighbour, the current state of a
+ * finer-level one, which has not yet advanced; Sec. 3.2, 3.4); same-level blocks
  * share face fluxes and edge EMFs (the finer side's); when a coarse step
  * ends its boundary fluxes and EMFs are replaced by the finer level's time
  * integrals and the cells next to corrected faces are inverted again

@@ -2027,16 +2027,15 @@ Src amr_src(const ora_amr* m, int b, int n, int sigma, long s) {
     } else if (N.lat == R.lat && sigma == 1) {
         r.Pa = N.Ph.data();
         r.Ba = N.Bh.data();
-    } else if (N.lat < R.lat && sigma == 1) {
-        /* a finer neighbour has not yet advanced (coarse first): its state at
-         * the receiver's midpoint is extrapolated linearly in time from its
-         * last two states, t - 2^Ln and t */
-        r.Pa = N.Pold.data();
-        r.Ba = N.Bold.data();
-        r.Pb = N.g->prim.data();
-        r.Bb = N.g->bface.data();
-        r.w = 1.0 + 0.5 * (double)(1L << R.lat) / (double)(1L << N.lat);
     } else {
+        /* a same-level source at the predictor, or a finer one at either
+         * stage: its current state. A finer neighbour has not yet advanced
+         * (coarse first), so at the receiver's midpoint this is a first-order
+         * value; the receiver's fluxes through the shared face are replaced by
+         * the finer side's at the end of its step (refluxing). Extrapolating
+         * it linearly in time from its last two states instead amplified
+         * step-to-step oscillations at coarse-fine faces in a magnetised torus
+         * until the inversions failed. */
         r.Pa = N.g->prim.data();
         r.Ba = N.g->bface.data();
     }

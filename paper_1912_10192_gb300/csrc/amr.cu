@@ -8,8 +8,11 @@
 // plus offset x MINMOD slope when it is coarser (slopes whose stencil leaves
 // the source interior are 0). A coarser-level source is interpolated in time
 // between its old and new state; a same-level source is read at the same
-// stage; a finer-level source at its current state, extrapolated in time
-// from its last two states at the coarse midpoint stage.
+// stage; a finer-level source, which has not yet advanced (coarse first), at
+// its current state at both stages (the coarse fluxes through the shared
+// faces are replaced by the finer ones at the end of the coarse step; an
+// extrapolation in time to the coarse midpoint amplified step-to-step
+// oscillations at coarse-fine faces of a magnetised torus).
 //
 // Same-level blocks stepped together share face fluxes (the coarser side
 // takes the finer side's average) and edge EMFs (the dominant block's:
@@ -135,13 +138,7 @@ __device__ inline SrcView source_view(const DevBlock& R, const DevBlock& N, int 
     } else if (N.lat == R.lat && sigma == 1) {
         v.Pa = N.Ph;
         v.Ba = N.Bh;
-    } else if (N.lat < R.lat && sigma == 1) {
-        v.Pa = N.Pold;
-        v.Ba = N.Bold;
-        v.Pb = N.P;
-        v.Bb = N.B;
-        v.w = 1.0 + 0.5 * (double)(1 << R.lat) / (double)(1 << N.lat);
-    } else {
+    } else {  // same level at the predictor, or finer: its current state
         v.Pa = N.P;
         v.Ba = N.B;
     }

@@ -1333,7 +1333,7 @@ __global__ void kb_dt_reduce(const DevBlock* tab, const int* list, PhysArgs ph) 
     b_dt_reduce(D.v, ph, D.P, D.dmax, tidx());
 }
 
-// state at the start of a step (interpolation and extrapolation source), status reset
+// state at the start of a step (the source of finer neighbours' time interpolation), status reset
 __global__ void kb_save_old(const DevBlock* tab, const int* list) {
     const DevBlock& D = tab[list[blockIdx.y]];
     const long t = tidx();
