@@ -446,18 +446,20 @@ def options_leg(args, hamr, torch, blk, dprim, dbf, cells, stream):
 SHAPE_KEYS = ("recon_seg", "recon_x1_sweep", "bs_recon", "bs_flux", "bs_update")
 
 
-def amr_leg(hamr, torch, precision=0, tune=True, nper=3, reps=2):
+def amr_leg(hamr, torch, precision=0, tune=True, nper=3, reps=2, smr=0):
     """The 512-block C3 torus tree (two refinement levels, 6-way polar children, LAT levels 0..3),
     whole LAT periods replayed from one CUDA graph. Every timing starts from the same initial state
     (restored), runs one untimed period (graph capture) and times nper periods. With tune: the
     autotuner runs on a representative state, then the default and the tuned launch shapes are timed
     alternately, reps times each, from the same initial state; the tuned shapes are used only if their
     median beats the default's by more than the spread of the repetitions. tune=False times the
-    default shapes only."""
+    default shapes only. smr > 0 adds that many levels of internal SMR in the polar rows (Sec. 3.3.2),
+    which lifts the CFL step of the polar blocks; the simulated time per period (the CFL fine step
+    of the last timed period x 2^lmax) and per wall-clock second show what that buys."""
     from paper_1912_10192_gb300 import workloads as W
-    blocks = W.c3_tree(n=32)
+    blocks = W.c3_tree(n=32, smr=smr)
     states = W.torus_blocks(blocks, seed=3)
-    g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], precision=precision)
+    g = hamr.Grid([hamr.block_from_dict(b) for b in blocks], precision=precision, smr=smr)
     lmax = max(b["lat"] for b in blocks)
     per = 2 ** lmax
 
@@ -482,15 +484,20 @@ def amr_leg(hamr, torch, precision=0, tune=True, nper=3, reps=2):
     base = {"workload": "C3: 512-block torus tree (8x4x4 base of 32^3, 16 disk blocks to level 1, 16 of those "
                         "to level 2, 32 polar blocks split 6-way, polar rows derefined in phi), %d cells, "
                         "1024x512x512 effective, seed 3" % summary["cells"],
-            "precision": "mixed" if precision else "fp64", "tree": summary,
+            "precision": "mixed" if precision else "fp64", "internal_smr_levels": smr, "tree": summary,
             "fine_substeps_per_period": per, "real_zone_cycles_per_period": real}
+
+    def sim_time(ms):  # the CFL fine step of the last period timed
+        t = g.stats()["dt_used"] * per
+        return {"sim_time_per_period": t, "sim_time_per_s": t / (ms * 1e-3)}
     default = g.launch_shapes()
     default = {k: default[k] for k in SHAPE_KEYS}
     if not tune:
         ms = time_periods()
+        st = sim_time(ms)
         g.close()
         return dict(base, ms_per_period_default_shapes=ms, real_zone_cycles_per_s=real / (ms * 1e-3),
-                    lat_effective_zone_cycles_per_s=eff / (ms * 1e-3))
+                    lat_effective_zone_cycles_per_s=eff / (ms * 1e-3), **st)
     restore()
     g.batch_step(per)
     rep = g.autotune()
@@ -506,6 +513,7 @@ def amr_leg(hamr, torch, precision=0, tune=True, nper=3, reps=2):
     use_tuned = mt < md - spread
     ms = mt if use_tuned else md
     g.set_launch_shapes(**(tuned if use_tuned else default))
+    st = sim_time(ms)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     g.regrid([hamr.block_from_dict(b) for b in blocks])  # onto the same tree: allocation + device fill
@@ -517,7 +525,7 @@ def amr_leg(hamr, torch, precision=0, tune=True, nper=3, reps=2):
                 autotuner_groups_ms={"default": round(rep["ms_default"], 3), "tuned": round(rep["ms_tuned"], 3),
                                      "spread": round(rep["ms_spread"], 3)},
                 regrid_same_tree_ms=round(regrid_ms, 1),
-                real_zone_cycles_per_s=real / (ms * 1e-3), lat_effective_zone_cycles_per_s=eff / (ms * 1e-3))
+                real_zone_cycles_per_s=real / (ms * 1e-3), lat_effective_zone_cycles_per_s=eff / (ms * 1e-3), **st)
 
 
 def run_ours(args, rank, world, local):
@@ -589,7 +597,8 @@ def run_ours(args, rank, world, local):
     if not args.no_extra and world == 1:
         extra["mlp"] = mlp_leg(args, hamr, torch, blk, dprim, dbf, cells, stream)
         extra["options"] = options_leg(args, hamr, torch, blk, dprim, dbf, cells, stream)
-        extra["amr_lat"] = [amr_leg(hamr, torch, 0), amr_leg(hamr, torch, 1)]
+        extra["amr_lat"] = [amr_leg(hamr, torch, 0), amr_leg(hamr, torch, 1),
+                            amr_leg(hamr, torch, 1, tune=False, smr=2)]
 
     # ---- end to end: host buffers through the C ABI, copies inside the timed region
     e2e_steps = min(args.steps, 10)
@@ -681,6 +690,9 @@ def main():
     ap.add_argument("--amr-periods", type=int, default=0, metavar="P",
                     help="only time P LAT periods of the 512-block FP64 tree at the default launch shapes "
                          "(for launch lists) and print them")
+    ap.add_argument("--amr-precision", type=int, default=0, choices=[0, 1, 2],
+                    help="with --amr-periods: 0 FP64, 1 and 2 the mixed forms")
+    ap.add_argument("--amr-smr", type=int, default=0, help="with --amr-periods: internal SMR levels")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -689,7 +701,8 @@ def main():
         import torch
         from paper_1912_10192_gb300 import _build, hamr
         _build.build()
-        print(json.dumps(amr_leg(hamr, torch, 0, tune=False, nper=args.amr_periods)), flush=True)
+        print(json.dumps(amr_leg(hamr, torch, args.amr_precision, tune=False, nper=args.amr_periods,
+                                 smr=args.amr_smr)), flush=True)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

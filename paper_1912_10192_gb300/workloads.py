@@ -547,20 +547,49 @@ def _touch(a, b, period3):
     return True
 
 
-def assign_lat_levels(blocks, lmax=3, period3=2.0 * math.pi):
+def smr_row_widths(blocks, smr):
+    """Internal SMR (Sec. 3.3.2): the group width in x3 of every row of every block (1 where not
+    grouped), by the rows and phi ranges of the coarsest polar blocks: a row at distance jp (in the
+    coarsest polar blocks' rows) from a polar face is grouped 2^n wide, n the largest level with
+    jp < 2^(smr - n); a block with 2^l2 times finer x2 cells and 2^l3 times finer x3 cells groups
+    2^l3 times as many of its own cells. Returns one array of n2 widths per block."""
+    polar = [b for b in blocks if 2 in (b["bc"][2], b["bc"][3])]
+    out = []
+    for b in blocks:
+        w = np.ones(b["n2"], dtype=int)
+        if smr > 0 and b in polar:
+            l2 = int(round(math.log2(max(p["dx2"] for p in polar) / b["dx2"])))
+            l3 = int(round(math.log2(max(p["dx3"] for p in polar) / b["dx3"])))
+            for j in range(b["n2"]):
+                jp = 1 << 30
+                if b["bc"][2] == 2:
+                    jp = j
+                if b["bc"][3] == 2:
+                    jp = min(jp, b["n2"] - 1 - j)
+                for lev in range(smr, 0, -1):
+                    if (jp >> l2) < 2 ** (smr - lev):
+                        w[j] = 2 ** lev * 2 ** l3
+                        break
+        out.append(w)
+    return out
+
+
+def assign_lat_levels(blocks, lmax=3, period3=2.0 * math.pi, smr=0):
     """LAT levels from the light-crossing time of each block's smallest cell
     in Kerr-Schild internal coordinates, dt_b ~ min over cells of
-    1 / (1/(r dx1) + 1/(r dx2) + 1/(r sin(theta) dx3)) (a state-independent
-    stand-in for the CFL condition, Sec. 3.4), level = min(lmax,
-    floor(log2(dt_b / min dt))); then smoothed so that blocks that touch differ
-    by at most one level and a spatially finer block is never on a coarser
-    time level than a block it touches."""
+    1 / (1/(r dx1) + 1/(r dx2) + 1/(r sin(theta) dx3 w)) (a state-independent
+    stand-in for the CFL condition, Sec. 3.4; w the row's internal-SMR group
+    width, 1 without), level = min(lmax, floor(log2(dt_b / min dt))); then
+    smoothed so that blocks that touch differ by at most one level and a
+    spatially finer block is never on a coarser time level than a block it
+    touches."""
     dts = []
-    for b in blocks:
+    widths = smr_row_widths(blocks, smr)
+    for b, w in zip(blocks, widths):
         x1 = _centres(b["x1min"], b["dx1"], b["n1"])
         x2 = _centres(b["x2min"], b["dx2"], b["n2"])
         R, TH = np.meshgrid(np.exp(x1), x2, indexing="ij")
-        inv = 1.0 / (R * b["dx1"]) + 1.0 / (R * b["dx2"]) + 1.0 / (R * np.abs(np.sin(TH)) * b["dx3"])
+        inv = 1.0 / (R * b["dx1"]) + 1.0 / (R * b["dx2"]) + 1.0 / (R * np.abs(np.sin(TH)) * b["dx3"] * w[None, :])
         dts.append(float((1.0 / inv).min()))
     dmin = min(dts)
     lat = [min(lmax, int(math.floor(math.log2(d / dmin) + 1e-9))) for d in dts]
@@ -726,19 +755,20 @@ def nesting_violations(blocks, period3=2.0 * math.pi):
     return out
 
 
-def c3_tree(rin=1.2, rout=50.0, n=32):
+def c3_tree(rin=1.2, rout=50.0, n=32, smr=0):
     """The 512-block torus tree of the batched AMR/LAT configuration (C3): a base of 8 x 4 x 4 blocks;
     the 16 disk blocks (r index 3-4, theta index 1-2) refined to level 1, the 16 level-1 blocks at
     global r index 8, theta index 3-4 refined to level 2 (the finest level: a 1024 x 512 x 512
     effective grid at n = 32); the 32 polar base blocks at r index 2-5 split 6-way; the polar base
     rows derefined in phi. Cell counts: base and levels 1-2 n^3, polar blocks n x n x n/2
     (13,107,200 cells at n = 32). Checked: no face or edge neighbours more than a factor 2 apart
-    in any direction; LAT levels from assign_lat_levels."""
+    in any direction; LAT levels from assign_lat_levels (with smr internal SMR levels: the grouped
+    polar rows' wider cells in phi)."""
     blocks = c3_blocks(n=n, rin=rin, rout=rout)
     bad = nesting_violations(blocks)
     if bad:
         raise ValueError("C3 tree violates the nesting rule: %s" % bad[:4])
-    return assign_lat_levels(blocks)
+    return assign_lat_levels(blocks, smr=smr)
 
 
 def tree_summary(blocks):

@@ -60,3 +60,39 @@ def test_literal_polar_shapes_break_the_nesting_rule():
     assert bad[("polar base", "base", 3)] > 0            # phi cells 4x wider than the equatorial base's
     assert bad[("polar child on the axis", "polar child off the axis", 3)] > 0
     assert any(k[0] == "polar base" and k[1].startswith("polar child") and k[2] == 2 for k in bad)
+
+
+def test_c3_tree_with_internal_smr_widths_and_levels():
+    """Internal SMR (Sec. 3.3.2) in the C3 polar rows: the first row of the coarsest polar blocks
+    is grouped 4 wide with two levels, the second 2 wide, the rest not; the on-axis children (x2
+    cells twice finer, x3 as coarse) group their first two rows 4 wide and the next two 2 wide;
+    blocks off the axis group nothing. Wider cells in phi lift the light-crossing step of the polar
+    rows (by about 3x with two levels, the r and theta terms left), and the tree keeps its LAT levels."""
+    blocks = W.c3_tree(n=32)
+    ws = W.smr_row_widths(blocks, 2)
+    for b, w in zip(blocks, ws):
+        if b["group"] == "polar base":
+            first = list(w[:3]) if b["bc"][2] == 2 else list(w[::-1][:3])
+            assert first == [4, 2, 1] and (w == 1).sum() == 30
+        elif b["group"] == "polar child on the axis":
+            first = list(w[:5]) if b["bc"][2] == 2 else list(w[::-1][:5])
+            assert first == [4, 4, 2, 2, 1] and (w == 1).sum() == 28
+        else:
+            assert (w == 1).all(), b["group"]
+    assert all((w == 1).all() for w in W.smr_row_widths(blocks, 0))
+    lat0 = [b["lat"] for b in blocks]
+    for smr in (1, 2, 3):
+        assert [b["lat"] for b in W.c3_tree(n=32, smr=smr)] == lat0
+
+    def fine_dt(smr):
+        bl = W.c3_tree(n=32, smr=smr)
+        out = []
+        for b, w in zip(bl, W.smr_row_widths(bl, smr)):
+            r = [math.exp(b["x1min"] + (i + 0.5) * b["dx1"]) for i in range(b["n1"])]
+            th = [b["x2min"] + (j + 0.5) * b["dx2"] for j in range(b["n2"])]
+            inv = max(1 / (ri * b["dx1"]) + 1 / (ri * b["dx2"]) + 1 / (ri * abs(math.sin(t)) * b["dx3"] * wj)
+                      for ri in r for t, wj in zip(th, w))
+            out.append(1 / inv / 2 ** b["lat"])
+        return min(out)
+    gain = fine_dt(2) / fine_dt(0)
+    assert 2.5 < gain < 4.0, gain
