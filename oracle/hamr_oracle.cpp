@@ -2042,8 +2042,10 @@ Src amr_src(const ora_amr* m, int b, int n, int sigma, long s) {
     return r;
 }
 
+/* MINMOD: the argument of smaller magnitude where both have the same strict
+ * sign, else 0 */
 double minmod(double a, double b) {
-    if (a * b <= 0.0) return 0.0;
+    if (!((a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0))) return 0.0;
     return fabs(a) < fabs(b) ? a : b;
 }
 

@@ -124,17 +124,24 @@ struct SrcView {
     __device__ double B(long i) const { return Bb ? Ba[i] + w * (Bb[i] - Ba[i]) : Ba[i]; }
 };
 
+// 2^e as a double, built from its bits (-1022 <= e <= 1023): exact, and no work for the FP64 pipe
+__device__ inline double pow2i(int e) { return __hiloint2double((1023 + e) << 20, 0); }
+
 __device__ inline SrcView source_view(const DevBlock& R, const DevBlock& N, int sigma, int s) {
     SrcView v;
     v.Pb = v.Bb = nullptr;
     v.w = 0.0;
     if (N.lat > R.lat) {
+        // w = (s - s0 + sigma 2^Lr / 2) / 2^Ln = (2 (s - s0) + sigma 2^Lr) 2^-(Ln+1), exact
         const int s0 = (s >> N.lat) << N.lat;
+        const int k = 2 * (s - s0) + sigma * (1 << R.lat);
         v.Pa = N.Pold;
         v.Ba = N.Bold;
-        v.Pb = N.P;
-        v.Bb = N.B;
-        v.w = ((double)(s - s0) + sigma * 0.5 * (double)(1 << R.lat)) / (double)(1 << N.lat);
+        if (k != 0) {  // else the source's old state itself
+            v.Pb = N.P;
+            v.Bb = N.B;
+            v.w = (double)k * pow2i(-(N.lat + 1));
+        }
     } else if (N.lat == R.lat && sigma == 1) {
         v.Pa = N.Ph;
         v.Ba = N.Bh;
@@ -145,9 +152,22 @@ __device__ inline SrcView source_view(const DevBlock& R, const DevBlock& N, int 
     return v;
 }
 
+// MINMOD: the argument of smaller magnitude where both have the same strict sign, else 0. On the
+// bit patterns (the order of non-negative doubles is that of their patterns as integers), so
+// that it costs the FP64 pipe nothing
 __device__ inline double minmod_(double a, double b) {
-    if (a * b <= 0.0) return 0.0;
-    return fabs(a) < fabs(b) ? a : b;
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    const long long ma = ia & 0x7fffffffffffffffLL, mb = ib & 0x7fffffffffffffffLL;
+    if ((ia ^ ib) < 0 || ma == 0 || mb == 0) return 0.0;
+    return ma < mb ? a : b;
+}
+
+// 1 / (c1 c2 c3) for footprint counts: built from its bits when the product is a power of two
+// (every footprint of a 2:1 tree), else divided
+__device__ inline double inv_count(int c1, int c2, int c3) {
+    const int p = c1 * c2 * c3;
+    if ((p & (p - 1)) == 0) return pow2i(-(31 - __clz(p)));
+    return 1.0 / (double)p;
 }
 
 // ------------------------------------------------------------------ ghost kernels
@@ -243,25 +263,34 @@ __device__ inline void ghost_cell_apply(const AmrDomain& A, const DevBlock& R, c
     const SrcView S = source_view(R, N, sigma, s);
     const long sj = N.v.n1p, sk = (long)N.v.n1p * N.v.n2p;
     const long st[4] = {0, 1, sj, sk};
-    const double inv = 1.0 / (double)(G.cnt[1] * G.cnt[2] * G.cnt[3]);
+    const bool one = G.cnt[1] * G.cnt[2] * G.cnt[3] == 1;
+    const double inv = inv_count(G.cnt[1], G.cnt[2], G.cnt[3]);
+    double f[4];  // the prolongation offsets in source cells (multiples of 1/8: exact)
+    for (int d = 1; d <= 3; d++) f[d] = (G.e8[d] == 0) ? 0.0 : (double)G.e8[d] * 0.125;
     double* out = sigma ? R.Ph : R.P;
+    // source cell c of primitive q, with its MINMOD slopes where prolonged
+    auto cell = [&](int q, long c) {
+        const double q0 = S.P(q * N.v.nc + c);
+        double val = q0;
+        for (int d = 1; d <= 3; d++) {
+            if (G.e8[d] == 0) continue;
+            const double qm = S.P(q * N.v.nc + c - st[d]);
+            const double qp = S.P(q * N.v.nc + c + st[d]);
+            val += f[d] * minmod_(q0 - qm, qp - q0);
+        }
+        return val;
+    };
     for (int q = 0; q < NPRIM; q++) {
-        double sum = 0.0;
-        for (int c3 = 0; c3 < G.cnt[3]; c3++)
-            for (int c2 = 0; c2 < G.cnt[2]; c2++)
-                for (int c1 = 0; c1 < G.cnt[1]; c1++) {
-                    const long c = G.c0 + c1 + c2 * sj + c3 * sk;
-                    const double q0 = S.P(q * N.v.nc + c);
-                    double val = q0;
-                    for (int d = 1; d <= 3; d++) {
-                        if (G.e8[d] == 0) continue;
-                        const double qm = S.P(q * N.v.nc + c - st[d]);
-                        const double qp = S.P(q * N.v.nc + c + st[d]);
-                        val += (G.e8[d] * 0.125) * minmod_(q0 - qm, qp - q0);
-                    }
-                    sum += val;
-                }
-        double o = sum * inv;
+        double o;
+        if (one) {  // a copy or a prolongation: one source cell, no sum
+            o = cell(q, G.c0);
+        } else {  // the mean of the covered finer cells
+            double sum = 0.0;
+            for (int c3 = 0; c3 < G.cnt[3]; c3++)
+                for (int c2 = 0; c2 < G.cnt[2]; c2++)
+                    for (int c1 = 0; c1 < G.cnt[1]; c1++) sum += cell(q, G.c0 + c1 + c2 * sj + c3 * sk);
+            o = sum * inv;
+        }
         if (G.neg && (q == U2 || q == B2)) o = -o;
         if (q == U1) {
             if (G.clamp > 0 && o < 0.0) o = 0.0;
@@ -317,21 +346,28 @@ __device__ inline void ghost_face_apply(const AmrDomain& A, const DevBlock& R, c
     const int fd = G.fd;
     const long sj = N.v.n1p, sk = (long)N.v.n1p * N.v.n2p;
     const long st = (fd == 1) ? 1 : ((fd == 2) ? sj : sk);
-    const double fr = G.e8[fd] * 0.125;
-    const double inv = 1.0 / (double)(G.cnt[1] * G.cnt[2] * G.cnt[3]);
-    double sum = 0.0;
-    for (int c3 = 0; c3 < G.cnt[3]; c3++)
-        for (int c2 = 0; c2 < G.cnt[2]; c2++)
-            for (int c1 = 0; c1 < G.cnt[1]; c1++) {
-                const long c = G.c0 + c1 + c2 * sj + c3 * sk;
-                double q = S.B((fd - 1) * N.v.nc + c);
-                if (fr != 0.0) {
-                    const double q1 = S.B((fd - 1) * N.v.nc + c + st);
-                    q = q + fr * (q1 - q);
-                }
-                sum += q;
-            }
-    const double val = sum * inv;
+    const int e8 = G.e8[fd];
+    const double fr = (e8 == 0) ? 0.0 : (double)e8 * 0.125;
+    const bool one = G.cnt[1] * G.cnt[2] * G.cnt[3] == 1;
+    const double inv = inv_count(G.cnt[1], G.cnt[2], G.cnt[3]);
+    auto face = [&](long c) {  // source face c, linear toward the next where between two
+        double q = S.B((fd - 1) * N.v.nc + c);
+        if (e8 != 0) {
+            const double q1 = S.B((fd - 1) * N.v.nc + c + st);
+            q = q + fr * (q1 - q);
+        }
+        return q;
+    };
+    double val;
+    if (one) {
+        val = face(G.c0);
+    } else {
+        double sum = 0.0;
+        for (int c3 = 0; c3 < G.cnt[3]; c3++)
+            for (int c2 = 0; c2 < G.cnt[2]; c2++)
+                for (int c1 = 0; c1 < G.cnt[1]; c1++) sum += face(G.c0 + c1 + c2 * sj + c3 * sk);
+        val = sum * inv;
+    }
     double* out = sigma ? R.Bh : R.B;
     out[(fd - 1) * R.v.nc + t] = (G.neg && fd == 2) ? -val : val;
 }
