@@ -280,17 +280,25 @@ __device__ inline void ghost_cell_apply(const AmrDomain& A, const DevBlock& R, c
         }
         return val;
     };
-    for (int q = 0; q < NPRIM; q++) {
-        double o;
-        if (one) {  // a copy or a prolongation: one source cell, no sum
-            o = cell(q, G.c0);
-        } else {  // the mean of the covered finer cells
+    // every primitive is formed before any is stored, so that the gathers of all eight are in
+    // flight together (a store between them could alias the next source and would serialise them)
+    double ov[NPRIM];
+    if (one) {  // a copy or a prolongation: one source cell, no sum
+#pragma unroll
+        for (int q = 0; q < NPRIM; q++) ov[q] = cell(q, G.c0);
+    } else {  // the mean of the covered finer cells
+#pragma unroll
+        for (int q = 0; q < NPRIM; q++) {
             double sum = 0.0;
             for (int c3 = 0; c3 < G.cnt[3]; c3++)
                 for (int c2 = 0; c2 < G.cnt[2]; c2++)
                     for (int c1 = 0; c1 < G.cnt[1]; c1++) sum += cell(q, G.c0 + c1 + c2 * sj + c3 * sk);
-            o = sum * inv;
+            ov[q] = sum * inv;
         }
+    }
+#pragma unroll
+    for (int q = 0; q < NPRIM; q++) {
+        double o = ov[q];
         if (G.neg && (q == U2 || q == B2)) o = -o;
         if (q == U1) {
             if (G.clamp > 0 && o < 0.0) o = 0.0;
